@@ -1,0 +1,322 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle, the tests and the bench.
+
+This module holds input generation only: structured Kuhn tetrahedral meshes, the layered
+cylindrical "shoulder" phantom and the 12^3 sphere phantom, z-directed dipole rings, seeded
+box partitions for the Schwarz preconditioner and the counter-based random generator used for
+tear placement and measurement noise.  None of the method's arithmetic (element matrices,
+assembly, solves, S-parameters, gradients) lives here.
+
+The paper's anatomical CAD shoulder (Sec. IV-A) and its waveguide array (Sec. III) are not
+available, so the phantoms below stand in for them with the same tissue classes, a matching
+medium around the body, and a ring of antennas around the arm; the tear is an ellipsoid of
+synovial fluid inside the tendon band, as in Sec. IV-A.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# ----------------------------------------------------------------------------------------
+# Counter-based generator: splitmix64 (Steele, Lea, Flood 2014), uniform doubles from the top
+# 53 bits, normals by the Box-Muller transform.
+# ----------------------------------------------------------------------------------------
+_MASK = (1 << 64) - 1
+
+
+class SplitMix64:
+    def __init__(self, seed: int):
+        self.state = seed & _MASK
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+        return z ^ (z >> 31)
+
+    def uniform(self) -> float:
+        """Uniform double in [0, 1)."""
+        return (self.next_u64() >> 11) * (1.0 / 9007199254740992.0)
+
+    def uniform_open(self) -> float:
+        """Uniform double in (0, 1]."""
+        return ((self.next_u64() >> 11) + 1) * (1.0 / 9007199254740992.0)
+
+    def normal_pair(self) -> tuple[float, float]:
+        u1 = self.uniform_open()
+        u2 = self.uniform()
+        r = math.sqrt(-2.0 * math.log(u1))
+        return r * math.cos(2.0 * math.pi * u2), r * math.sin(2.0 * math.pi * u2)
+
+    def normals(self, n: int) -> np.ndarray:
+        out = np.empty(n)
+        for i in range(0, n, 2):
+            a, b = self.normal_pair()
+            out[i] = a
+            if i + 1 < n:
+                out[i + 1] = b
+        return out
+
+
+# ----------------------------------------------------------------------------------------
+# Kuhn meshes
+# ----------------------------------------------------------------------------------------
+@dataclass
+class Mesh:
+    nx: int
+    ny: int
+    nz: int
+    lo: tuple
+    hi: tuple
+    xyz: np.ndarray  # [V, 3] float64, metres
+    tets: np.ndarray  # [T, 4] int32, vertex ids in Kuhn path order (not sorted)
+
+    @property
+    def n_vert(self) -> int:
+        return self.xyz.shape[0]
+
+    @property
+    def n_tet(self) -> int:
+        return self.tets.shape[0]
+
+    @property
+    def h(self) -> tuple:
+        return tuple((self.hi[d] - self.lo[d]) / (self.nx, self.ny, self.nz)[d] for d in range(3))
+
+    def centroids(self) -> np.ndarray:
+        return self.xyz[self.tets].mean(axis=1)
+
+
+# The six axis permutations; tet (p1, p2, p3) walks v000 -> +e_p1 -> +e_p2 -> v111.
+_PERMS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def kuhn_mesh(nx: int, ny: int, nz: int, lo=(-0.06, -0.06, -0.06), hi=(0.06, 0.06, 0.06)) -> Mesh:
+    """Box [lo, hi] split into nx*ny*nz cells, each cut into 6 tets along its main diagonal.
+
+    Vertex id = (k*(ny+1) + j)*(nx+1) + i.  Tets are ordered by cell (i fastest, then j, k) and
+    within a cell by the permutation table above; each tet lists its vertices in path order.
+    """
+    xs = np.linspace(lo[0], hi[0], nx + 1)
+    ys = np.linspace(lo[1], hi[1], ny + 1)
+    zs = np.linspace(lo[2], hi[2], nz + 1)
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    xyz = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    i = i.ravel().astype(np.int64)
+    j = j.ravel().astype(np.int64)
+    k = k.ravel().astype(np.int64)
+
+    def vid(di, dj, dk):
+        return ((k + dk) * (ny + 1) + (j + dj)) * (nx + 1) + (i + di)
+
+    tets = np.empty((i.size, 6, 4), dtype=np.int64)
+    for t, perm in enumerate(_PERMS):
+        off = [0, 0, 0]
+        tets[:, t, 0] = vid(*off)
+        for s in range(3):
+            off[perm[s]] += 1
+            tets[:, t, s + 1] = vid(*off)
+    return Mesh(nx, ny, nz, tuple(lo), tuple(hi), xyz, tets.reshape(-1, 4).astype(np.int32))
+
+
+# ----------------------------------------------------------------------------------------
+# Dielectric data (relative complex permittivity, e^{i omega t} convention: Im < 0 = loss)
+# ----------------------------------------------------------------------------------------
+EPS_MATCHING = 44.0 - 20.0j
+EPS_SKIN = 41.0 - 16.0j
+EPS_FAT = 5.5 - 1.0j
+EPS_MUSCLE = 55.0 - 17.0j
+EPS_BONE = 12.4 - 2.8j
+EPS_TENDON = 45.8 - 13.0j
+EPS_FLUID = 68.0 - 35.0j
+EPS_SPHERE = 50.0 - 15.0j
+
+# Tissue labels used by the shoulder phantom.
+MATCHING, SKIN, FAT, MUSCLE, BONE, TENDON, FLUID = range(7)
+LABEL_EPS = {MATCHING: EPS_MATCHING, SKIN: EPS_SKIN, FAT: EPS_FAT, MUSCLE: EPS_MUSCLE,
+             BONE: EPS_BONE, TENDON: EPS_TENDON, FLUID: EPS_FLUID}
+
+
+def eps_to_pairs(eps: np.ndarray) -> np.ndarray:
+    """Complex per-tet permittivity -> [T, 2] float64 (re, im)."""
+    return np.ascontiguousarray(np.stack([eps.real, eps.imag], axis=1).astype(np.float64))
+
+
+# ----------------------------------------------------------------------------------------
+# Antennas: z-directed dipoles on a ring
+# ----------------------------------------------------------------------------------------
+def dipole_ring(n: int, rho: float, z: float, center=(0.0, 0.0)) -> tuple[np.ndarray, np.ndarray]:
+    ang = 2.0 * np.pi * np.arange(n) / n
+    pos = np.stack([center[0] + rho * np.cos(ang), center[1] + rho * np.sin(ang), np.full(n, z)], 1)
+    direc = np.tile(np.array([0.0, 0.0, 1.0]), (n, 1))
+    return pos, direc
+
+
+# ----------------------------------------------------------------------------------------
+# Phantoms
+# ----------------------------------------------------------------------------------------
+def sphere_phantom(mesh: Mesh, seed: int = 1, radius: float = 0.015,
+                   eps_bg: complex = EPS_MATCHING, eps_sph: complex = EPS_SPHERE):
+    """Homogeneous box with one sphere; centre uniform in the disc rho <= 20 mm, |z| <= 20 mm."""
+    g = SplitMix64(seed)
+    r = 0.020 * math.sqrt(g.uniform())
+    th = 2.0 * math.pi * g.uniform()
+    zc = -0.020 + 0.040 * g.uniform()
+    c = np.array([r * math.cos(th), r * math.sin(th), zc])
+    cen = mesh.centroids()
+    eps = np.full(mesh.n_tet, eps_bg, dtype=np.complex128)
+    eps[np.linalg.norm(cen - c, axis=1) <= radius] = eps_sph
+    return eps, c
+
+
+ARM_CENTER = (0.0, 0.0)
+ARM_R = 0.05
+TORSO_CENTER = (-0.28, 0.0)
+TORSO_R = 0.15
+SKIN_T = 0.002
+FAT_T = 0.003
+BONE_R = 0.015
+TENDON_RHO = (0.032, 0.042)
+TENDON_THETA_DEG = (150.0, 210.0)
+TENDON_HALF_Z = 0.030
+SHOULDER_LO = (-0.18, -0.18, -0.0765)
+SHOULDER_HI = (0.18, 0.18, 0.0765)
+
+
+@dataclass
+class Tear:
+    center: tuple
+    semi_axes: tuple
+    eps: complex
+
+
+def shoulder_labels(points: np.ndarray, tear: Tear | None = None) -> np.ndarray:
+    """Tissue label of each point of the layered cylindrical shoulder phantom."""
+    x, y, z = points[:, 0], points[:, 1], points[:, 2]
+    rho_a = np.hypot(x - ARM_CENTER[0], y - ARM_CENTER[1])
+    rho_t = np.hypot(x - TORSO_CENTER[0], y - TORSO_CENTER[1])
+    depth = np.maximum(ARM_R - rho_a, TORSO_R - rho_t)
+    lab = np.full(points.shape[0], MATCHING, dtype=np.int32)
+    inside = depth > 0
+    lab[inside] = MUSCLE
+    lab[inside & (depth <= SKIN_T + FAT_T)] = FAT
+    lab[inside & (depth <= SKIN_T)] = SKIN
+    theta = np.degrees(np.arctan2(y - ARM_CENTER[1], x - ARM_CENTER[0])) % 360.0
+    band = ((rho_a >= TENDON_RHO[0]) & (rho_a <= TENDON_RHO[1]) & (theta >= TENDON_THETA_DEG[0])
+            & (theta <= TENDON_THETA_DEG[1]) & (np.abs(z) <= TENDON_HALF_Z))
+    lab[band & (lab == MUSCLE)] = TENDON
+    lab[rho_a <= BONE_R] = BONE
+    if tear is not None:
+        c, a = np.asarray(tear.center), np.asarray(tear.semi_axes)
+        q = (((points - c) / a) ** 2).sum(axis=1) <= 1.0
+        lab[q & ((lab == TENDON) | (lab == MUSCLE))] = FLUID
+    return lab
+
+
+def shoulder_eps(mesh: Mesh, tear: Tear | None = None) -> np.ndarray:
+    lab = shoulder_labels(mesh.centroids(), tear)
+    eps = np.empty(mesh.n_tet, dtype=np.complex128)
+    for k, v in LABEL_EPS.items():
+        eps[lab == k] = v
+    if tear is not None:
+        eps[lab == FLUID] = tear.eps
+    return eps
+
+
+def random_tear(seed: int, eps_range=None) -> Tear:
+    """Tear centre uniform inside the tendon band, semi-axes uniform in 1-5 mm (full axes
+    2-10 mm), axis aligned; fluid permittivity fixed, or uniform in the given (re, im) box."""
+    g = SplitMix64(seed)
+    rho = TENDON_RHO[0] + (TENDON_RHO[1] - TENDON_RHO[0]) * g.uniform()
+    th = math.radians(TENDON_THETA_DEG[0] + (TENDON_THETA_DEG[1] - TENDON_THETA_DEG[0]) * g.uniform())
+    zc = -TENDON_HALF_Z + 2.0 * TENDON_HALF_Z * g.uniform()
+    axes = tuple(0.001 + 0.004 * g.uniform() for _ in range(3))
+    if eps_range is None:
+        eps = EPS_FLUID
+    else:
+        (r0, r1), (i0, i1) = eps_range
+        eps = complex(r0 + (r1 - r0) * g.uniform(), -(i0 + (i1 - i0) * g.uniform()))
+    return Tear((ARM_CENTER[0] + rho * math.cos(th), ARM_CENTER[1] + rho * math.sin(th), zc), axes, eps)
+
+
+# ----------------------------------------------------------------------------------------
+# Partitions for the overlapping Schwarz preconditioner
+# ----------------------------------------------------------------------------------------
+def box_partition(mesh: Mesh, parts: tuple, seed: int = 7, jitter: float = 0.25) -> np.ndarray:
+    """Tet -> subdomain id from a px*py*pz box grid with seeded uneven cuts.
+
+    Cut positions are the uniform cuts moved by up to +-jitter of a box width, snapped to cell
+    boundaries; subdomain id = (bz*py + by)*px + bx.
+    """
+    g = SplitMix64(seed)
+    n = (mesh.nx, mesh.ny, mesh.nz)
+    cen = mesh.centroids()
+    idx = []
+    for d in range(3):
+        p = parts[d]
+        w = n[d] / p
+        cuts = [0]
+        for c in range(1, p):
+            pos = c * w + jitter * w * (2.0 * g.uniform() - 1.0)
+            cuts.append(int(round(min(max(pos, cuts[-1] + 1), n[d] - (p - c)))))
+        cuts.append(n[d])
+        cell = np.floor((cen[:, d] - mesh.lo[d]) / ((mesh.hi[d] - mesh.lo[d]) / n[d])).astype(np.int64)
+        idx.append(np.searchsorted(np.asarray(cuts[1:-1]), cell, side="right"))
+    return ((idx[2] * parts[1] + idx[1]) * parts[0] + idx[0]).astype(np.int32)
+
+
+def add_noise(S: np.ndarray, snr_db: float, seed: int) -> np.ndarray:
+    """S + 10^(-snr/20) |S| (xi + i eta)/sqrt(2), xi, eta ~ N(0,1) from splitmix64/Box-Muller,
+    drawn in row-major order of S (xi then eta per entry)."""
+    g = SplitMix64(seed)
+    flat = S.ravel()
+    nrm = g.normals(2 * flat.size).reshape(-1, 2)
+    amp = 10.0 ** (-snr_db / 20.0) * np.abs(flat)
+    out = flat + amp * (nrm[:, 0] + 1j * nrm[:, 1]) / math.sqrt(2.0)
+    return out.reshape(S.shape)
+
+
+# ----------------------------------------------------------------------------------------
+# Named workloads
+# ----------------------------------------------------------------------------------------
+@dataclass
+class Workload:
+    name: str
+    mesh: Mesh
+    eps: np.ndarray          # complex [T]
+    eps_bg: complex
+    freqs: tuple
+    src_pos: np.ndarray
+    src_dir: np.ndarray
+    parts: tuple | None = None
+    overlap: int = 1
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_src(self) -> int:
+        return self.src_pos.shape[0]
+
+
+def sphere_box(cells: int = 12, seed: int = 1, n_src: int = 8) -> Workload:
+    """12^3 Kuhn cells on [-0.06, 0.06]^3 (h = 10 mm), one sphere, 8 dipoles at rho = 50 mm."""
+    m = kuhn_mesh(cells, cells, cells)
+    eps, c = sphere_phantom(m, seed)
+    h = 0.12 / cells
+    pos, d = dipole_ring(n_src, 0.05, h / 2 if cells % 2 == 0 else 0.0)
+    return Workload(f"sphere_box_{cells}", m, eps, EPS_MATCHING, (1.0e9,), pos, d,
+                    extra={"sphere_center": c})
+
+
+def shoulder(cells=(80, 80, 34), n_src: int = 32, freqs=(1.0e9,), tear: Tear | None = None,
+             parts=None, overlap: int = 1, name: str = "shoulder") -> Workload:
+    m = kuhn_mesh(*cells, lo=SHOULDER_LO, hi=SHOULDER_HI)
+    eps = shoulder_eps(m, tear)
+    hz = (SHOULDER_HI[2] - SHOULDER_LO[2]) / cells[2]
+    z = hz / 2 if cells[2] % 2 == 0 else 0.0
+    pos, d = dipole_ring(n_src, 0.10, z, ARM_CENTER)
+    return Workload(name, m, eps, EPS_MATCHING, tuple(freqs), pos, d, parts=parts, overlap=overlap,
+                    extra={"tear": tear})
