@@ -1,0 +1,208 @@
+/*
+ * libmw - GB300-native hot path of the microwave-tomography method of arXiv 2311.05322
+ * ("Numerical Modeling for Shoulder Injury Detection Using Microwave Imaging").
+ *
+ * The library solves the time-harmonic Maxwell problem of Eq. (m1)/(m2) with lowest-order
+ * Nedelec (Whitney) edge elements on tetrahedra (Sec. IV-D), one solve per transmitter, by
+ * GMRES with a one-level ORAS domain-decomposition preconditioner (Sec. IV-C), computes the
+ * S-matrix (dipole form of Eq. s1), the cost of Eq. (sahar:2), its adjoint gradient and an
+ * L-BFGS inversion step (Sec. IV-D).  All arithmetic of these steps runs in the library's own
+ * sm_103a kernels; the host side only validates, orchestrates and runs L-BFGS in FP64.
+ *
+ * Conventions
+ *   - Every call returns an mw_status; MW_OK == 0.  No exception crosses the ABI.  On error,
+ *     mw_last_error(ctx) holds a one-line message (valid until the next call on ctx).
+ *   - Complex numbers are interleaved (re, im) pairs of double (or float where stated), layout
+ *     compatible with C99 double _Complex and std::complex<double>.
+ *   - Time convention e^{i omega t} (Sec. IV-B): lossy media have Im eps_r < 0.
+ *   - Indices are int32_t, counts int64_t.  Host input arrays are owned by the caller and
+ *     copied in before the call returns.  Device pointers are caller-owned CUDA allocations on
+ *     the context's device.  The context owns every internal device buffer.
+ *   - All device work is enqueued on the stream given to mw_create.  Calls that return host
+ *     data synchronise that stream before returning; the others return after enqueueing.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - Edge numbering: a global edge is the vertex pair (lo, hi), lo < hi, numbered by
+ *     lexicographic rank; local tet edges are (0,1) (0,2) (0,3) (1,2) (1,3) (2,3) and carry
+ *     sign +1 when the local tail has the smaller global vertex id.  The matrix pattern holds
+ *     every pair of edges sharing a tet, columns ascending.
+ */
+#ifndef MW_H
+#define MW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mw_status;
+enum {
+  MW_OK = 0,
+  MW_EINVAL = 1,    /* invalid argument (null pointer, size or index out of range, bad mesh) */
+  MW_ECUDA = 2,     /* a CUDA runtime call or kernel launch failed */
+  MW_ENOMEM = 3,    /* device allocation failed (or would exceed the context's memory cap) */
+  MW_ENOCONV = 4,   /* a solve stopped before reaching its tolerance; outputs hold the last iterate */
+  MW_ETIMEOUT = 5,  /* a device-side bounded wait ran out; the kernel returned early */
+  MW_ESTATE = 6,    /* call out of order (e.g. solve before assemble) */
+  MW_ESINGULAR = 7  /* a subdomain matrix had a (near-)zero pivot */
+};
+
+typedef enum { MW_PREC_FP64 = 0, MW_PREC_FP32 = 1, MW_PREC_BF16 = 2 } mw_precision;
+typedef enum { MW_MODE_FP64 = 0, MW_MODE_MIXED = 1 } mw_mode;
+
+typedef struct mw_ctx mw_ctx;
+
+typedef struct {
+  int64_t n_vert, n_tet, n_edge, n_face, n_bface, nnz;
+} mw_mesh_info;
+
+/* Options of one solve phase (GMRES(m) + ORAS, Sec. IV-C).
+ *   mode      MW_MODE_FP64: FP64 everywhere (operator, preconditioner apply, Krylov basis).
+ *             MW_MODE_MIXED: GMRES-IR - FP64 outer residual b - A x and update of x; inner
+ *             flexible GMRES with FP32 operator and basis, preconditioner applied in the
+ *             precision chosen at setup (BF16 on the tensor cores, or FP32), FP64 Hessenberg
+ *             least squares.
+ *   restart   Krylov dimension m per cycle (<= 64).
+ *   batch     columns per Krylov launch; 0 = all columns of a frequency in one block launch.
+ *   max_it    cap on Arnoldi steps per column over the whole solve.
+ *   tol       target FP64 true relative residual ||b - A x||_2 / ||b||_2 per column.
+ *   inner_tol mixed mode: relative residual reduction asked of each inner cycle.
+ *   max_outer mixed mode: cap on outer refinement steps.
+ *   use_precond 1 = ORAS (mw_setup_preconditioner first), 0 = unpreconditioned. */
+typedef struct {
+  int32_t mode;
+  int32_t restart;
+  int32_t batch;
+  int32_t max_it;
+  double tol;
+  double inner_tol;
+  int32_t max_outer;
+  int32_t use_precond;
+} mw_solve_opts;
+
+/* Per-solve statistics.  iters/relres are optional caller arrays of n_cols entries. */
+typedef struct {
+  int32_t n_cols;          /* columns solved (n_freq * n_src) */
+  int32_t n_converged;     /* columns with FP64 true relres <= tol */
+  int32_t outer_steps;     /* outer residual evaluations */
+  int32_t arnoldi_steps;   /* Arnoldi steps executed (max over columns of a launch, summed) */
+  double max_relres;       /* largest final FP64 true relative residual */
+  double solve_ms;         /* device time of the solve phase (CUDA events on the stream) */
+  int32_t* iters;          /* [n_cols] Arnoldi steps per column, or NULL */
+  double* relres;          /* [n_cols] final true relative residual per column, or NULL */
+} mw_solve_stats;
+
+/* ---- context ---------------------------------------------------------------------- */
+/* Create a context on CUDA device `device`; all work goes to `cuda_stream` (a cudaStream_t,
+ * NULL = the legacy default stream). */
+mw_status mw_create(mw_ctx** ctx, int device, void* cuda_stream);
+void mw_destroy(mw_ctx* ctx);
+const char* mw_last_error(const mw_ctx* ctx);
+/* Cap on the context's device allocations in bytes (0 = no cap).  Exceeding it gives MW_ENOMEM. */
+mw_status mw_set_memory_cap(mw_ctx* ctx, int64_t bytes);
+
+/* ---- mesh (Sec. IV-A; Nedelec r = 1, Sec. IV-D) ------------------------------------- */
+/* xyz [n_vert][3] metres; tet_vert [n_tet][4] vertex ids (any orientation, non-degenerate).
+ * Builds the canonical edges, signs, faces, the CSR pattern and the assembly maps on the
+ * host, uploads them and computes the element matrices on the GPU.  Fills *out. */
+mw_status mw_set_mesh(mw_ctx* ctx, int64_t n_vert, const double* xyz, int64_t n_tet,
+                      const int32_t* tet_vert, mw_mesh_info* out);
+/* Copies of the topology (any pointer may be NULL): edge_vert [E][2] (lo < hi), tet_edge
+ * [T][6], tet_sign [T][6], row_ptr [E+1], col_idx [nnz]. */
+mw_status mw_get_topology(mw_ctx* ctx, int32_t* edge_vert, int32_t* tet_edge, int8_t* tet_sign,
+                          int64_t* row_ptr, int32_t* col_idx);
+/* Element matrices from the GPU (parity hook): K, M [T][6][6] and volumes [T] (any may be NULL). */
+mw_status mw_get_element_matrices(mw_ctx* ctx, double* K, double* M, double* vol);
+
+/* ---- assembly, Eq. (m2) with k^2 = k0^2 eps_r ---------------------------------------- */
+/* A_f = K - k0_f^2 sum_T eps_T M^T + i k0_f sqrt(eps_bg) B for each frequency (Hz);
+ * eps_r [n_tet][2] (re, im), eps_bg[2].  Re-run whenever eps changes. */
+mw_status mw_assemble(mw_ctx* ctx, int32_t n_freq, const double* freq_hz, const double* eps_r,
+                      const double* eps_bg);
+/* Values of A_f in the canonical pattern, host complex128 [nnz] (parity hook). */
+mw_status mw_get_matrix(mw_ctx* ctx, int32_t f, double* values);
+/* Y = A_f X on the device for n_cols columns, layout [E][n_cols] (column fastest),
+ * complex128 (prec = MW_PREC_FP64, FP64 arithmetic) or complex64 (MW_PREC_FP32, FP32). */
+mw_status mw_apply_matrix(mw_ctx* ctx, int32_t f, int32_t prec, const void* x_dev, void* y_dev,
+                          int32_t n_cols);
+
+/* ---- sources (volume-source reading of Eq. m1) ----------------------------------------- */
+/* z-directed dipoles: pos/dir [n_src][3].  Each maps to the z-directed edge whose midpoint is
+ * nearest (ties: lowest edge id); outputs (optional) the edge and its sign (+1 when the
+ * edge lo -> hi points along dir).  RHS b_j = -i omega mu0 s_j e_edge(j). */
+mw_status mw_set_sources(mw_ctx* ctx, int32_t n_src, const double* pos, const double* dir,
+                         int32_t* src_edge_out, int8_t* src_sign_out);
+
+/* ---- ORAS preconditioner (Sec. IV-C) ------------------------------------------------ */
+/* tet_part [n_tet] in [0, n_sub); overlap_layers >= 0 vertex-neighbour layers; inv_prec
+ * selects the stored precision of the subdomain inverses (FP64: FP64 factorisation, applied
+ * in FP64; FP32: FP32 factorisation, FP32 apply; BF16: FP32 factorisation, BF16 tensor-core
+ * apply).  Builds for every assembled frequency from the current eps. */
+mw_status mw_setup_preconditioner(mw_ctx* ctx, int32_t n_sub, const int32_t* tet_part,
+                                  int32_t overlap_layers, int32_t inv_prec);
+/* z = M_f^{-1} r on the device, complex128 [E][n_cols] in and out (parity hook). */
+mw_status mw_apply_preconditioner(mw_ctx* ctx, int32_t f, const void* r_dev, void* z_dev,
+                                  int32_t n_cols);
+/* Owner subdomain of each edge [E] and unknowns per subdomain [n_sub] (either may be NULL). */
+mw_status mw_get_partition(mw_ctx* ctx, int32_t* edge_owner, int32_t* sub_size);
+
+/* ---- solves -------------------------------------------------------------------------- */
+/* Forward solves for all n_freq * n_src dipole columns (column c = f * n_src + j).
+ * fields_dev: NULL, or device complex128 [n_cols][E] receiving the fields.
+ * S: NULL, or host complex128 [n_freq][n_src][n_src], S[f][i][j] = p_i^T x_{f,j}.
+ * Returns MW_ENOCONV if some column missed tol (outputs then hold the last iterate). */
+mw_status mw_solve(mw_ctx* ctx, const mw_solve_opts* opts, void* fields_dev, double* S,
+                   mw_solve_stats* stats);
+/* Solve A_f x = b for arbitrary right-hand sides: b_dev/x_dev device complex128
+ * [n_freq][n_cols][E] (n_cols per frequency). */
+mw_status mw_solve_rhs(mw_ctx* ctx, const mw_solve_opts* opts, int32_t n_cols, const void* b_dev,
+                       void* x_dev, mw_solve_stats* stats);
+
+/* ---- cost and gradient (Eq. sahar:2, Sec. IV-D) ------------------------------------- */
+/* Forward solve, cost J = 1/2 sum w |S - S_obs|^2 + alpha R with w = 1/|S_empty|^2, adjoint
+ * solve with sources c_ij = w_ij conj(S_ij - S_obs_ij), per-tet gradient
+ * dJ/dRe eps_T = sum_f k0_f^2 Re G_T, dJ/dIm eps_T = -sum_f k0_f^2 Im G_T,
+ * G_T = sum_j lambda_j^T M^T x_j, plus alpha dR (face-jump Tikhonov).
+ * S_obs, S_empty host complex128 [n_freq][n_src][n_src]; grad host [n_tet][2] (may be NULL);
+ * S_out (may be NULL) receives the forward S. */
+mw_status mw_gradient(mw_ctx* ctx, const mw_solve_opts* opts, const double* S_obs,
+                      const double* S_empty, double alpha, double* J_out, double* grad,
+                      double* S_out);
+/* Tikhonov term R and alpha-free gradient dR [n_tet][2] for eps [n_tet][2] (device kernel). */
+mw_status mw_tikhonov(mw_ctx* ctx, const double* eps_r, double* R_out, double* grad);
+
+/* ---- L-BFGS (Sec. IV-D) ------------------------------------------------------------ */
+typedef struct {
+  int32_t m;            /* history pairs (8) */
+  int32_t max_it;       /* iterations */
+  double c1;            /* Armijo constant (1e-4) */
+  int32_t max_ls;       /* backtracking trials (10) */
+  double first_step;    /* first step scaled so max_k |d_k| = first_step (1.0) */
+  double alpha;         /* Tikhonov weight */
+  double target_J;      /* stop once J <= target_J (0 = off) */
+} mw_inv_opts;
+
+typedef struct {
+  int32_t iterations;    /* accepted iterates */
+  int32_t evaluations;   /* cost+gradient evaluations */
+  double* J;             /* [max_it + 1] cost per accepted iterate (J[0] at the start), or NULL */
+  double* seconds;       /* [max_it + 1] wall time at each accepted iterate, or NULL */
+} mw_inv_history;
+
+/* Reverse-communication L-BFGS on a host vector x[n] (FP64): create, then call step with the
+ * cost f and gradient g at the x it last asked for.  *request = 1: evaluate at x (written into
+ * x_io); 0: converged or stopped, x_io holds the final iterate. */
+typedef struct mw_lbfgs mw_lbfgs;
+mw_status mw_lbfgs_create(mw_lbfgs** st, int64_t n, const mw_inv_opts* opts);
+mw_status mw_lbfgs_step(mw_lbfgs* st, double* x_io, double f, const double* g, int32_t* request);
+void mw_lbfgs_destroy(mw_lbfgs* st);
+/* Full inversion: L-BFGS over [Re eps; Im eps] with mw_assemble + mw_gradient per
+ * evaluation; eps_inout [n_tet][2].  The preconditioner set up before the call is reused. */
+mw_status mw_invert(mw_ctx* ctx, const mw_inv_opts* opts, const mw_solve_opts* sopts,
+                    const double* S_obs, const double* S_empty, double* eps_inout,
+                    mw_inv_history* hist);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MW_H */

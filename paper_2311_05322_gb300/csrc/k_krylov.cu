@@ -1,0 +1,551 @@
+// K6-K8, K15: batched Arnoldi (classical Gram-Schmidt), Givens least squares and solution update
+// of restarted, right-preconditioned (flexible) GMRES, all columns of a block at once.
+//
+// Layout: Krylov vectors V[i] are [E][R] (column index fastest) at V + i * vstride.  All
+// reductions are deterministic: per-block partial sums reduced in a fixed order.  Dot products
+// of FP32 vectors multiply and sum in FP32 over chunks of kChunk rows and accumulate the chunk
+// sums in FP64; FP64 vectors use FP64 throughout.
+//
+// Per-column GMRES state (one entry per column c of the block, m = restart length):
+//   H[c][j][i]   Hessenberg column j (i <= j+1) after rotations, complex FP64, (m+1) per column j
+//   cs[c][2j], cs[c][2j+1]   Givens pair (c_j, s_j) mapping (a, b) -> (sqrt(|a|^2+|b|^2), 0)
+//   g[c][i]      rotated right-hand side beta e_1
+//   target[c]    residual-estimate target of this cycle
+//   done[c]      1 once the column stopped (converged, breakdown or out of steps)
+//   kcol[c]      Arnoldi steps used by the column in this cycle
+#include "mw_internal.h"
+
+namespace mwk {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxVecPerWarp = 8;   // restart m <= 63 => nvec <= 64 = 8 warps x 8
+constexpr int kChunk = 16;          // FP32 rows summed before promotion to FP64
+constexpr int kBlocks = 152 * 4;
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+template <typename T>
+struct Traits;
+template <>
+struct Traits<double2> {
+  using S = double;
+};
+template <>
+struct Traits<float2> {
+  using S = float;
+};
+
+struct Shape {
+  int cpl, tpr_log2;
+};
+inline Shape shape_for(int R) {
+  int cpl = (R + 31) / 32;
+  if (cpl > 2) cpl = 4;
+  int tpr = (R + cpl - 1) / cpl;
+  int l = 0;
+  while ((1 << l) < tpr) ++l;
+  return {cpl, l};
+}
+
+// h_part[p][i][c] = sum over the rows of part p of conj(V_i[e][c]) * w[e][c].
+// Warp k of a block serves vectors i = k, k + 8, ... when nvec >= 8; otherwise the 8 warps
+// split into S = 8 / nvec row slots per vector.  Part index p = block * S + slot.
+template <typename T, int CPL>
+__global__ void __launch_bounds__(kThreads) cgs_dots_kernel(const T* __restrict__ V, int64_t vstride, int nvec,
+                                                            const T* __restrict__ w, int64_t E, int R, int tpr_log2,
+                                                            int S, double2* __restrict__ part) {
+  using Sc = typename Traits<T>::S;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tpr = 1 << tpr_log2;
+  const int rpw = 32 >> tpr_log2;          // rows per warp pass
+  const int lrow = lane >> tpr_log2;
+  const int c0 = (lane & (tpr - 1)) * CPL;
+  int i_first, i_step, slot;
+  if (nvec >= kWarps) {
+    i_first = warp;
+    i_step = kWarps;
+    slot = 0;
+  } else {
+    if (warp >= nvec * S) return;
+    i_first = warp % nvec;
+    i_step = 1 << 30;
+    slot = warp / nvec;
+  }
+  const int nmine = i_first < nvec ? (nvec - 1 - i_first) / i_step + 1 : 0;
+  double2 acc[kMaxVecPerWarp][CPL];
+#pragma unroll
+  for (int a = 0; a < kMaxVecPerWarp; ++a)
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) acc[a][q] = make_double2(0.0, 0.0);
+
+  const int64_t rows_per_iter = (int64_t)gridDim.x * S * rpw;
+  const int64_t row0 = ((int64_t)blockIdx.x * S + slot) * rpw + lrow;
+  const bool active_c = c0 < R;
+  // chunked loop over rows
+  for (int64_t base = row0; base < E; base += rows_per_iter * kChunk) {
+#pragma unroll
+    for (int a = 0; a < kMaxVecPerWarp; ++a) {
+      if (a >= nmine) break;
+      const int i = i_first + a * i_step;
+      const T* Vi = V + (int64_t)i * vstride;
+      Sc sr[CPL], si[CPL];
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) sr[q] = si[q] = (Sc)0;
+      for (int k = 0; k < kChunk; ++k) {
+        const int64_t row = base + (int64_t)k * rows_per_iter;
+        if (row >= E || !active_c) break;
+        const T* vr = Vi + row * R + c0;
+        const T* wr = w + row * R + c0;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+          if (c0 + q < R) {
+            const T v = vr[q], x = wr[q];
+            // conj(v) * x
+            sr[q] = fma(v.x, x.x, sr[q]);
+            sr[q] = fma(v.y, x.y, sr[q]);
+            si[q] = fma(v.x, x.y, si[q]);
+            si[q] = fma(-v.y, x.x, si[q]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        acc[a][q].x += (double)sr[q];
+        acc[a][q].y += (double)si[q];
+      }
+    }
+  }
+  // reduce over the rows of the warp (lanes with equal column)
+#pragma unroll
+  for (int a = 0; a < kMaxVecPerWarp; ++a) {
+    if (a >= nmine) break;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      double x = acc[a][q].x, y = acc[a][q].y;
+      for (int off = tpr; off < 32; off <<= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, off);
+        y += __shfl_xor_sync(0xffffffffu, y, off);
+      }
+      acc[a][q] = make_double2(x, y);
+    }
+  }
+  if (lrow == 0 && active_c) {
+    const int64_t p = (int64_t)blockIdx.x * S + slot;
+    for (int a = 0; a < nmine; ++a) {
+      const int i = i_first + a * i_step;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+        if (c0 + q < R) part[(p * nvec + i) * R + c0 + q] = acc[a][q];
+    }
+  }
+}
+
+__global__ void reduce_h_kernel(const double2* __restrict__ part, int nparts, int nvec, int R, double2* __restrict__ h) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nvec * R) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int p = 0; p < nparts; ++p) s = cadd(s, part[(int64_t)p * nvec * R + t]);
+  h[t] = s;
+}
+
+// w[e][c] -= sum_i h[i][c] V_i[e][c]; partial sums of |w|^2 per block and column.
+template <typename T, int CPL>
+__global__ void __launch_bounds__(kThreads) cgs_update_kernel(const T* __restrict__ V, int64_t vstride, int nvec,
+                                                              const double2* __restrict__ h, T* __restrict__ w,
+                                                              int64_t E, int R, int tpr_log2,
+                                                              double* __restrict__ npart) {
+  using Sc = typename Traits<T>::S;
+  extern __shared__ unsigned char smem_raw[];
+  T* hs = reinterpret_cast<T*>(smem_raw);                          // [nvec][R]
+  double* red = reinterpret_cast<double*>(smem_raw + sizeof(T) * nvec * R + 16);  // [kThreads][CPL]
+  for (int t = threadIdx.x; t < nvec * R; t += kThreads) {
+    const double2 v = h[t];
+    hs[t] = T{(Sc)v.x, (Sc)v.y};
+  }
+  __syncthreads();
+  const int tpr = 1 << tpr_log2;
+  const int rows_per_block = kThreads >> tpr_log2;
+  const int lc = threadIdx.x & (tpr - 1);
+  const int c0 = lc * CPL;
+  double nrm[CPL];
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) nrm[q] = 0.0;
+  if (c0 < R) {
+    for (int64_t row = (int64_t)blockIdx.x * rows_per_block + (threadIdx.x >> tpr_log2); row < E;
+         row += (int64_t)gridDim.x * rows_per_block) {
+      T acc[CPL];
+      T* wr = w + row * R + c0;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+        if (c0 + q < R) acc[q] = wr[q];
+      for (int i = 0; i < nvec; ++i) {
+        const T* vr = V + (int64_t)i * vstride + row * R + c0;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+          if (c0 + q < R) {
+            const T v = vr[q], hh = hs[i * R + c0 + q];
+            acc[q].x = fma(-hh.x, v.x, acc[q].x);
+            acc[q].x = fma(hh.y, v.y, acc[q].x);
+            acc[q].y = fma(-hh.x, v.y, acc[q].y);
+            acc[q].y = fma(-hh.y, v.x, acc[q].y);
+          }
+      }
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+        if (c0 + q < R) {
+          wr[q] = acc[q];
+          nrm[q] += (double)(acc[q].x * acc[q].x + acc[q].y * acc[q].y);
+        }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) red[threadIdx.x * CPL + q] = nrm[q];
+  __syncthreads();
+  if ((int)threadIdx.x < tpr) {
+    for (int q = 0; q < CPL; ++q) {
+      const int c = c0 + q;
+      if (c >= R) continue;
+      double s = 0.0;
+      for (int r = 0; r < rows_per_block; ++r) s += red[(r * tpr + lc) * CPL + q];
+      npart[(int64_t)blockIdx.x * R + c] = s;
+    }
+  }
+}
+
+template <typename T, int CPL>
+__global__ void __launch_bounds__(kThreads) colnorm2_kernel(const T* __restrict__ x, int64_t E, int R, int tpr_log2,
+                                                            double* __restrict__ npart) {
+  __shared__ double red[kThreads * CPL];
+  const int tpr = 1 << tpr_log2;
+  const int rows_per_block = kThreads >> tpr_log2;
+  const int lc = threadIdx.x & (tpr - 1);
+  const int c0 = lc * CPL;
+  double nrm[CPL];
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) nrm[q] = 0.0;
+  if (c0 < R)
+    for (int64_t row = (int64_t)blockIdx.x * rows_per_block + (threadIdx.x >> tpr_log2); row < E;
+         row += (int64_t)gridDim.x * rows_per_block)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+        if (c0 + q < R) {
+          const T v = x[row * R + c0 + q];
+          nrm[q] += (double)v.x * v.x + (double)v.y * v.y;
+        }
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) red[threadIdx.x * CPL + q] = nrm[q];
+  __syncthreads();
+  if ((int)threadIdx.x < tpr)
+    for (int q = 0; q < CPL; ++q) {
+      const int c = c0 + q;
+      if (c >= R) continue;
+      double s = 0.0;
+      for (int r = 0; r < rows_per_block; ++r) s += red[(r * tpr + lc) * CPL + q];
+      npart[(int64_t)blockIdx.x * R + c] = s;
+    }
+}
+
+__global__ void reduce_cols_kernel(const double* __restrict__ part, int nparts, int R, double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  double s = 0.0;
+  for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * R + c];
+  out[c] = s;
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// One thread per column: Hessenberg column j from h[0..j] and ||w||, previous rotations,
+// new rotation, residual estimate |g[j+1]| against the target.
+__global__ void givens_kernel(const double2* __restrict__ h, const double* __restrict__ npart, int nparts, int j,
+                              int m, int R, double2* __restrict__ H, double2* __restrict__ cs, double2* __restrict__ g,
+                              const double* __restrict__ target, int32_t* __restrict__ done,
+                              int32_t* __restrict__ kcol, double* __restrict__ scale, int32_t* __restrict__ active) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  if (done[c]) {
+    scale[c] = 0.0;
+    return;
+  }
+  double nn = 0.0;
+  for (int p = 0; p < nparts; ++p) nn += npart[(int64_t)p * R + c];
+  const double hn = sqrt(nn);
+  double2* Hc = H + ((int64_t)c * m + j) * (m + 1);
+  for (int i = 0; i <= j; ++i) Hc[i] = h[i * R + c];
+  Hc[j + 1] = make_double2(hn, 0.0);
+  double2* csc = cs + (int64_t)c * 2 * m;
+  for (int i = 0; i < j; ++i) {
+    const double2 ci = csc[2 * i], si = csc[2 * i + 1];
+    const double2 a = Hc[i], b = Hc[i + 1];
+    const double2 t = cadd(cmul(ci, a), cmul(si, b));
+    const double2 u = cadd(cmul(make_double2(-si.x, si.y), a), cmul(conjd(ci), b));  // -conj(s) a + conj(c) b
+    Hc[i] = t;
+    Hc[i + 1] = u;
+  }
+  const double2 a = Hc[j], b = Hc[j + 1];
+  const double den = sqrt(cabs2(a) + cabs2(b));
+  double2 cj, sj;
+  if (den == 0.0) {
+    cj = make_double2(1.0, 0.0);
+    sj = make_double2(0.0, 0.0);
+  } else {
+    cj = make_double2(a.x / den, -a.y / den);   // conj(a)/den
+    sj = make_double2(b.x / den, -b.y / den);   // conj(b)/den
+  }
+  csc[2 * j] = cj;
+  csc[2 * j + 1] = sj;
+  Hc[j] = make_double2(den, 0.0);
+  Hc[j + 1] = make_double2(0.0, 0.0);
+  double2* gc = g + (int64_t)c * (m + 1);
+  const double2 gj = gc[j];
+  gc[j + 1] = cmul(make_double2(-sj.x, sj.y), gj);   // -conj(s) g_j
+  gc[j] = cmul(cj, gj);
+  const double res = sqrt(cabs2(gc[j + 1]));
+  const bool stop = (res <= target[c]) || (hn == 0.0) || (j + 1 >= m) || !(res == res);
+  kcol[c] = j + 1;
+  if (stop) {
+    done[c] = 1;
+    scale[c] = 0.0;
+  } else {
+    scale[c] = 1.0 / hn;
+    atomicAdd(active, 1);
+  }
+}
+
+template <typename T>
+__global__ void scale_cols_kernel(T* __restrict__ v, const double* __restrict__ sc, int64_t E, int R) {
+  using Sc = typename Traits<T>::S;
+  const int64_t n = E * R;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const Sc s = (Sc)sc[i % R];
+    T x = v[i];
+    x.x *= s;
+    x.y *= s;
+    v[i] = x;
+  }
+}
+
+// Start of a cycle: ||r|| from partials, per-column target and state; columns already within
+// tol of ||b|| are marked done.
+__global__ void start_state_kernel(const double* __restrict__ npart, int nparts, int R, const double* __restrict__ bnorm,
+                                   double tol, double inner_tol, int fp64_mode, double* __restrict__ rnorm,
+                                   double2* __restrict__ g, double* __restrict__ target, int32_t* __restrict__ done,
+                                   int32_t* __restrict__ kcol, int m) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  double nn = 0.0;
+  for (int p = 0; p < nparts; ++p) nn += npart[(int64_t)p * R + c];
+  const double rn = sqrt(nn);
+  rnorm[c] = rn;
+  const double goal = tol * bnorm[c];
+  const bool conv = !(rn > goal);
+  done[c] = conv ? 1 : 0;
+  kcol[c] = 0;
+  double2* gc = g + (int64_t)c * (m + 1);
+  for (int i = 0; i <= m; ++i) gc[i] = make_double2(0.0, 0.0);
+  gc[0] = make_double2(rn, 0.0);
+  // FP64 mode: aim a little below tol so the recomputed true residual passes;
+  // mixed mode: reduce the residual by inner_tol (never below half the final goal).
+  target[c] = fp64_mode ? 0.5 * goal : fmax(inner_tol * rn, 0.5 * goal);
+}
+
+template <typename T>
+__global__ void normalize_start_kernel(const double2* __restrict__ r, const double* __restrict__ rnorm,
+                                       const int32_t* __restrict__ done, int64_t E, int R, T* __restrict__ v0) {
+  using Sc = typename Traits<T>::S;
+  const int64_t n = E * R;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % R);
+    const double s = done[c] ? 0.0 : 1.0 / rnorm[c];
+    const double2 x = r[i];
+    v0[i] = T{(Sc)(x.x * s), (Sc)(x.y * s)};
+  }
+}
+
+// Back substitution R y = g per column (R upper triangular after the rotations).
+__global__ void hessenberg_solve_kernel(const double2* __restrict__ H, const double2* __restrict__ g,
+                                        const int32_t* __restrict__ kcol, int m, int R, double2* __restrict__ y) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  const int k = kcol[c];
+  double2* yc = y + (int64_t)c * m;
+  const double2* gc = g + (int64_t)c * (m + 1);
+  for (int i = k; i < m; ++i) yc[i] = make_double2(0.0, 0.0);
+  for (int i = k - 1; i >= 0; --i) {
+    double2 s = gc[i];
+    for (int l = i + 1; l < k; ++l) {
+      const double2 hv = H[((int64_t)c * m + l) * (m + 1) + i];
+      const double2 p = cmul(hv, yc[l]);
+      s.x -= p.x;
+      s.y -= p.y;
+    }
+    const double2 d = H[((int64_t)c * m + i) * (m + 1) + i];
+    const double dd = cabs2(d);
+    yc[i] = dd > 0.0 ? make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd)
+                     : make_double2(0.0, 0.0);
+  }
+}
+
+// x[e][c] += sum_{i < kcol[c]} y[c][i] Z_i[e][c]; correction formed in the basis precision,
+// added to x in FP64.
+template <typename T>
+__global__ void update_x_kernel(const T* __restrict__ Z, int64_t zstride, const double2* __restrict__ y,
+                                const int32_t* __restrict__ kcol, int m, double2* __restrict__ x, int64_t E, int R) {
+  using Sc = typename Traits<T>::S;
+  const int64_t n = E * R;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % R);
+    const int k = kcol[c];
+    Sc dr = 0, di = 0;
+    for (int l = 0; l < k; ++l) {
+      const T z = Z[(int64_t)l * zstride + i];
+      const double2 yy = y[(int64_t)c * m + l];
+      const Sc yr = (Sc)yy.x, yi = (Sc)yy.y;
+      dr = fma(yr, z.x, dr);
+      dr = fma(-yi, z.y, dr);
+      di = fma(yr, z.y, di);
+      di = fma(yi, z.x, di);
+    }
+    double2 xv = x[i];
+    xv.x += (double)dr;
+    xv.y += (double)di;
+    x[i] = xv;
+  }
+}
+
+inline int gs_blocks(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
+}
+
+template <typename T>
+int dots_launch(const T* V, int64_t vstride, int nvec, const T* w, int64_t E, int R, double2* part, cudaStream_t s) {
+  Shape sh = shape_for(R);
+  const int S = nvec >= kWarps ? 1 : kWarps / nvec;
+  switch (sh.cpl) {
+    case 1:
+      cgs_dots_kernel<T, 1><<<kBlocks, kThreads, 0, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
+      break;
+    case 2:
+      cgs_dots_kernel<T, 2><<<kBlocks, kThreads, 0, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
+      break;
+    default:
+      cgs_dots_kernel<T, 4><<<kBlocks, kThreads, 0, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
+      break;
+  }
+  return kBlocks * S;
+}
+
+template <typename T>
+int update_launch(const T* V, int64_t vstride, int nvec, const double2* h, T* w, int64_t E, int R, double* npart,
+                  cudaStream_t s) {
+  Shape sh = shape_for(R);
+  const size_t smem = sizeof(T) * nvec * R + 16 + sizeof(double) * kThreads * sh.cpl;
+  static bool attr = false;
+  if (!attr) {
+    const int mx = 200 * 1024;
+    cudaFuncSetAttribute(cgs_update_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(cgs_update_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(cgs_update_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    attr = true;
+  }
+  switch (sh.cpl) {
+    case 1:
+      cgs_update_kernel<T, 1><<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, h, w, E, R, sh.tpr_log2, npart);
+      break;
+    case 2:
+      cgs_update_kernel<T, 2><<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, h, w, E, R, sh.tpr_log2, npart);
+      break;
+    default:
+      cgs_update_kernel<T, 4><<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, h, w, E, R, sh.tpr_log2, npart);
+      break;
+  }
+  return kBlocks;
+}
+
+}  // namespace
+
+int cgs_dots_f64(const double2* V, int64_t vstride, int nvec, const double2* w, int64_t E, int R, double2* part,
+                 cudaStream_t s) {
+  return dots_launch<double2>(V, vstride, nvec, w, E, R, part, s);
+}
+int cgs_dots_f32(const float2* V, int64_t vstride, int nvec, const float2* w, int64_t E, int R, double2* part,
+                 cudaStream_t s) {
+  return dots_launch<float2>(V, vstride, nvec, w, E, R, part, s);
+}
+void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s) {
+  const int n = nvec * R;
+  reduce_h_kernel<<<(n + 127) / 128, 128, 0, s>>>(part, nparts, nvec, R, h);
+}
+int cgs_update_f64(const double2* V, int64_t vstride, int nvec, const double2* h, double2* w, int64_t E, int R,
+                   double* npart, cudaStream_t s) {
+  return update_launch<double2>(V, vstride, nvec, h, w, E, R, npart, s);
+}
+int cgs_update_f32(const float2* V, int64_t vstride, int nvec, const double2* h, float2* w, int64_t E, int R,
+                   double* npart, cudaStream_t s) {
+  return update_launch<float2>(V, vstride, nvec, h, w, E, R, npart, s);
+}
+int colnorm2_f64(const double2* x, int64_t E, int R, double* npart, cudaStream_t s) {
+  Shape sh = shape_for(R);
+  switch (sh.cpl) {
+    case 1:
+      colnorm2_kernel<double2, 1><<<kBlocks, kThreads, 0, s>>>(x, E, R, sh.tpr_log2, npart);
+      break;
+    case 2:
+      colnorm2_kernel<double2, 2><<<kBlocks, kThreads, 0, s>>>(x, E, R, sh.tpr_log2, npart);
+      break;
+    default:
+      colnorm2_kernel<double2, 4><<<kBlocks, kThreads, 0, s>>>(x, E, R, sh.tpr_log2, npart);
+      break;
+  }
+  return kBlocks;
+}
+void reduce_cols(const double* part, int nparts, int R, double* out, cudaStream_t s) {
+  reduce_cols_kernel<<<(R + 127) / 128, 128, 0, s>>>(part, nparts, R, out);
+}
+void givens_step(const double2* h, const double* npart, int nparts, int j, int m, int R, double2* H, double2* cs,
+                 double2* gvec, double* target, int32_t* done, int32_t* kcol, double* scale, int32_t* active_count,
+                 cudaStream_t s) {
+  givens_kernel<<<(R + 127) / 128, 128, 0, s>>>(h, npart, nparts, j, m, R, H, cs, gvec, target, done, kcol, scale,
+                                                 active_count);
+}
+void scale_cols_f64(double2* v, const double* scale, int64_t E, int R, cudaStream_t s) {
+  scale_cols_kernel<double2><<<gs_blocks(E * R), 256, 0, s>>>(v, scale, E, R);
+}
+void scale_cols_f32(float2* v, const double* scale, int64_t E, int R, cudaStream_t s) {
+  scale_cols_kernel<float2><<<gs_blocks(E * R), 256, 0, s>>>(v, scale, E, R);
+}
+void start_state(const double* npart, int nparts, int R, const double* bnorm, double tol, double inner_tol,
+                 int fp64_mode, double* rnorm, double2* gvec, double* target, int32_t* done, int32_t* kcol, int m,
+                 cudaStream_t s) {
+  start_state_kernel<<<(R + 127) / 128, 128, 0, s>>>(npart, nparts, R, bnorm, tol, inner_tol, fp64_mode, rnorm, gvec,
+                                                      target, done, kcol, m);
+}
+void normalize_start_f64(const double2* r, const double* rnorm, const int32_t* done, int64_t E, int R, double2* v0,
+                         cudaStream_t s) {
+  normalize_start_kernel<double2><<<gs_blocks(E * R), 256, 0, s>>>(r, rnorm, done, E, R, v0);
+}
+void normalize_start_f32(const double2* r, const double* rnorm, const int32_t* done, int64_t E, int R, float2* v0,
+                         cudaStream_t s) {
+  normalize_start_kernel<float2><<<gs_blocks(E * R), 256, 0, s>>>(r, rnorm, done, E, R, v0);
+}
+void solve_hessenberg(const double2* H, const double2* gvec, const int32_t* kcol, int m, int R, double2* y,
+                      cudaStream_t s) {
+  hessenberg_solve_kernel<<<(R + 127) / 128, 128, 0, s>>>(H, gvec, kcol, m, R, y);
+}
+void update_x_f64(const double2* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x,
+                  int64_t E, int R, cudaStream_t s) {
+  update_x_kernel<double2><<<gs_blocks(E * R), 256, 0, s>>>(Z, zstride, y, kcol, m, x, E, R);
+}
+void update_x_f32(const float2* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x,
+                  int64_t E, int R, cudaStream_t s) {
+  update_x_kernel<float2><<<gs_blocks(E * R), 256, 0, s>>>(Z, zstride, y, kcol, m, x, E, R);
+}
+
+}  // namespace mwk

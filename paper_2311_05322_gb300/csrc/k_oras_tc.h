@@ -1,0 +1,40 @@
+// BF16 tensor-core (tcgen05) form of the ORAS apply (K4): layout plan and launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <functional>
+
+namespace mw {
+struct Subdomains;
+}
+
+namespace mwk {
+struct OrasTopo;
+struct OrasBatch;
+
+// Pre-tiled BF16 layout of the owned-row inverses W_s (see k_oras_tc.cu).
+struct TcPlan {
+  bool built = false;
+  int n_sub = 0;
+  int64_t n_mtiles = 0;       // sum_s ceil(n_own_s / 128)
+  int64_t n_ktiles_total = 0; // sum_s ceil(2 n_s / 64)
+  int64_t w_tiles = 0;        // sum_s mtiles_s * ktiles_s (16 KB each)
+  // device arrays
+  int32_t* mt_sub = nullptr;     // [n_mtiles] subdomain of each 128-row tile
+  int32_t* mt_row0 = nullptr;    // [n_mtiles] first owned row
+  int64_t* sub_wtile = nullptr;  // [n_sub] first W tile of s
+  int64_t* sub_gtile = nullptr;  // [n_sub] first gathered-operand k tile of s
+  int32_t* sub_kt = nullptr;     // [n_sub] k tiles of s
+};
+
+bool tc_plan_build(TcPlan& p, const mw::Subdomains& sd, const std::function<void*(size_t)>& alloc, cudaStream_t s);
+void tc_plan_free(TcPlan& p, const std::function<void(void*)>& dfree);
+size_t tc_w_bytes(const TcPlan& p);
+size_t tc_scratch_bytes(const TcPlan& p, int R);
+void tc_extract(const TcPlan& p, const OrasBatch& bt, const OrasTopo& tp, int ws_prec, const void* ws, void* W,
+                cudaStream_t s);
+void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
+                   void* scratch, cudaStream_t s);
+
+}  // namespace mwk

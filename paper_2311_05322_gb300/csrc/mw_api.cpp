@@ -1,0 +1,1306 @@
+// libmw C-ABI: context, validation and orchestration of the hot path of arXiv 2311.05322.
+// All arithmetic of the method runs in the kernels of k_*.cu; this file moves data, sizes
+// workspaces, runs the GMRES control flow and the FP64 L-BFGS recursion on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "k_adjoint.h"
+#include "k_oras.h"
+#include "k_oras_tc.h"
+#include "mw_internal.h"
+
+using mw::Error;
+
+namespace mwk {
+void start_state(const double* npart, int nparts, int R, const double* bnorm, double tol, double inner_tol,
+                 int fp64_mode, double* rnorm, double2* gvec, double* target, int32_t* done, int32_t* kcol, int m,
+                 cudaStream_t s);
+void normalize_start_f64(const double2* r, const double* rnorm, const int32_t* done, int64_t E, int R, double2* v0,
+                         cudaStream_t s);
+void normalize_start_f32(const double2* r, const double* rnorm, const int32_t* done, int64_t E, int R, float2* v0,
+                         cudaStream_t s);
+}  // namespace mwk
+
+namespace mwimpl {
+
+constexpr int kMaxRestart = 63;
+constexpr int kDotParts = 152 * 4 * 8;  // cgs_dots: blocks x max slots
+constexpr int kRedBlocks = 152 * 4;
+
+struct Ctx;
+
+struct Prec {
+  bool ready = false;
+  int apply_prec = 0;    // 0 FP64, 1 FP32, 2 BF16 (tensor cores)
+  int factor_prec = 0;   // 0 FP64, 1 FP32
+  mw::Subdomains sd;
+  // device copies
+  int64_t *dof_ptr = nullptr, *own_ptr = nullptr, *tet_ptr = nullptr, *surf_ptr = nullptr;
+  int32_t *dofs = nullptr, *own_local = nullptr, *own_glob = nullptr, *tet_ids = nullptr, *tet_loc = nullptr,
+          *surf_loc = nullptr, *surf_tet = nullptr, *surf_vert = nullptr;
+  double* Bsurf = nullptr;
+  int n_tiles = 0;
+  int32_t *tile_sub = nullptr, *tile_row0 = nullptr;
+  int64_t* w_off = nullptr;          // element offsets of W_s (cc layouts)
+  std::vector<void*> W;              // per frequency
+  mwk::TcPlan tc;                    // BF16 tensor-core layout
+  mwk::OrasTopo topo() const {
+    return {dof_ptr, dofs, own_ptr, own_local, own_glob, tet_ptr, tet_ids, tet_loc, surf_ptr, surf_loc, surf_tet};
+  }
+};
+
+struct Work {
+  int64_t E = 0;
+  int R = 0, m = 0, prec = -1;
+  void *V = nullptr, *Z = nullptr;
+  double2 *r = nullptr, *x = nullptr, *part = nullptr, *h = nullptr, *H = nullptr, *cs = nullptr, *g = nullptr,
+          *y = nullptr, *bblk = nullptr;
+  double *npart = nullptr, *target = nullptr, *rnorm = nullptr, *bnorm = nullptr, *scale = nullptr;
+  int32_t *done = nullptr, *kcol = nullptr, *active = nullptr;
+  int32_t* h_active = nullptr;  // pinned
+  double* h_vec = nullptr;      // pinned [R]
+  int32_t* h_ivec = nullptr;    // pinned [R]
+  void* tc_scratch = nullptr;   // BF16 gathered operand
+  size_t tc_bytes = 0;
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int64_t mem_cap = 0, mem_used = 0;
+  std::map<void*, size_t> allocs;
+
+  bool has_mesh = false;
+  mw::Topology topo;
+  std::vector<double> xyz;
+  double* d_xyz = nullptr;
+  int32_t *d_tets = nullptr, *d_col = nullptr, *d_contrib = nullptr, *d_bface_vert = nullptr, *d_tet_edge = nullptr,
+          *d_tet_nb = nullptr;
+  int8_t* d_sign = nullptr;
+  int64_t *d_row = nullptr, *d_cptr = nullptr;
+  double *d_KM = nullptr, *d_vol = nullptr, *d_Bf = nullptr, *d_tikw = nullptr;
+
+  int n_freq = 0;
+  std::vector<double> freqs;
+  double eps_bg[2] = {0, 0};
+  std::vector<double> eps;
+  double* d_eps = nullptr;
+  std::vector<double2*> A64;
+  std::vector<float2*> A32;
+
+  int n_src = 0;
+  std::vector<int32_t> src_edge;
+  std::vector<int8_t> src_sign;
+  int32_t* d_src_edge = nullptr;
+  int8_t* d_src_sign = nullptr;
+
+  Prec prec;
+  Work work;
+  std::vector<double2*> Xf;    // forward fields per frequency [E][n_src]
+  std::vector<double2*> Lf;    // adjoint fields per frequency
+  double2* d_B = nullptr;      // RHS scratch [E][n_src]
+  double* d_red = nullptr;     // reduction scratch
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+struct Fail {
+  mw_status code;
+  std::string msg;
+};
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) throw Fail{MW_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Fail{MW_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+template <typename T>
+T* dalloc(Ctx* c, size_t n) {
+  size_t bytes = std::max<size_t>(n * sizeof(T), 16);
+  if (c->mem_cap > 0 && c->mem_used + (int64_t)bytes > c->mem_cap)
+    throw Fail{MW_ENOMEM, "device memory cap exceeded (" + std::to_string(bytes) + " bytes requested)"};
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Fail{MW_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e)};
+  }
+  c->allocs[p] = bytes;
+  c->mem_used += bytes;
+  return (T*)p;
+}
+
+void dfree(Ctx* c, void* p) {
+  if (!p) return;
+  auto it = c->allocs.find(p);
+  if (it != c->allocs.end()) {
+    c->mem_used -= it->second;
+    c->allocs.erase(it);
+  }
+  cudaFree(p);
+}
+
+template <typename T>
+T* upload(Ctx* c, const T* h, size_t n) {
+  T* d = dalloc<T>(c, n);
+  if (n) CK(cudaMemcpyAsync(d, h, n * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  return d;
+}
+
+template <typename F>
+mw_status guard(Ctx* c, F&& f) {
+  if (!c) return MW_EINVAL;
+  try {
+    CK(cudaSetDevice(c->device));
+    c->err.clear();
+    f();
+    return MW_OK;
+  } catch (const Fail& e) {
+    c->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    c->err = "host allocation failed";
+    return MW_ENOMEM;
+  } catch (const std::exception& e) {
+    c->err = e.what();
+    return MW_EINVAL;
+  }
+}
+
+void require(bool cond, mw_status code, const std::string& msg) {
+  if (!cond) throw Fail{code, msg};
+}
+
+double k0_of(double f) { return 2.0 * mw::kPi * f / mw::kC0; }
+
+void free_work(Ctx* c) {
+  Work& w = c->work;
+  for (void* p : {(void*)w.V, (void*)w.Z, (void*)w.r, (void*)w.x, (void*)w.part, (void*)w.h, (void*)w.H, (void*)w.cs,
+                  (void*)w.g, (void*)w.y, (void*)w.npart, (void*)w.target, (void*)w.rnorm, (void*)w.bnorm,
+                  (void*)w.scale, (void*)w.done, (void*)w.kcol, (void*)w.active, (void*)w.bblk, w.tc_scratch})
+    dfree(c, p);
+  if (w.h_active) cudaFreeHost(w.h_active);
+  if (w.h_vec) cudaFreeHost(w.h_vec);
+  if (w.h_ivec) cudaFreeHost(w.h_ivec);
+  w = Work();
+}
+
+void ensure_work(Ctx* c, int R, int m, int prec) {
+  Work& w = c->work;
+  const int64_t E = c->topo.n_edge;
+  if (w.E == E && w.R >= R && w.m >= m && w.prec == prec) return;
+  free_work(c);
+  const size_t es = prec == 0 ? sizeof(double2) : sizeof(float2);
+  const size_t n = (size_t)E * R;
+  w.E = E;
+  w.R = R;
+  w.m = m;
+  w.prec = prec;
+  w.V = dalloc<unsigned char>(c, es * n * (m + 1));
+  w.Z = dalloc<unsigned char>(c, es * n * m);
+  w.r = dalloc<double2>(c, n);
+  w.x = dalloc<double2>(c, n);
+  w.bblk = dalloc<double2>(c, n);
+  w.part = dalloc<double2>(c, (size_t)kDotParts * 8 * R > (size_t)kRedBlocks * (kMaxRestart + 1) * R
+                                  ? (size_t)kDotParts * 8 * R
+                                  : (size_t)kRedBlocks * (kMaxRestart + 1) * R);
+  w.h = dalloc<double2>(c, (size_t)(kMaxRestart + 1) * R);
+  w.H = dalloc<double2>(c, (size_t)R * m * (m + 1));
+  w.cs = dalloc<double2>(c, (size_t)R * 2 * m);
+  w.g = dalloc<double2>(c, (size_t)R * (m + 1));
+  w.y = dalloc<double2>(c, (size_t)R * m);
+  w.npart = dalloc<double>(c, (size_t)kRedBlocks * R);
+  w.target = dalloc<double>(c, R);
+  w.rnorm = dalloc<double>(c, R);
+  w.bnorm = dalloc<double>(c, R);
+  w.scale = dalloc<double>(c, R);
+  w.done = dalloc<int32_t>(c, R);
+  w.kcol = dalloc<int32_t>(c, R);
+  w.active = dalloc<int32_t>(c, 1);
+  CK(cudaMallocHost(&w.h_active, sizeof(int32_t)));
+  CK(cudaMallocHost(&w.h_vec, sizeof(double) * R));
+  CK(cudaMallocHost(&w.h_ivec, sizeof(int32_t) * R));
+}
+
+// ---------------------------------------------------------------------------------------
+// preconditioner apply on basis vectors of the working precision
+// ---------------------------------------------------------------------------------------
+void apply_prec(Ctx* c, int f, int work_prec, const void* v, void* z, int R) {
+  Prec& p = c->prec;
+  cudaStream_t s = c->stream;
+  if (p.apply_prec == 2) {
+    require(work_prec == 1, MW_EINVAL, "BF16 preconditioner needs the mixed-precision solve");
+    Work& w = c->work;
+    size_t need = mwk::tc_scratch_bytes(p.tc, R);
+    if (w.tc_bytes < need) {
+      dfree(c, w.tc_scratch);
+      w.tc_scratch = dalloc<unsigned char>(c, need);
+      w.tc_bytes = need;
+    }
+    mwk::oras_apply_tc(p.tc, p.topo(), p.W[f], (const float2*)v, (float2*)z, R, w.tc_scratch, s);
+  } else {
+    const int need = work_prec;  // 0 FP64, 1 FP32
+    require(p.apply_prec == need, MW_EINVAL,
+            "preconditioner precision does not match the solve mode (FP64 mode needs an FP64-applied inverse)");
+    require(R <= 64, MW_EINVAL, "the CUDA-core preconditioner apply takes at most 64 columns per launch");
+    mwk::oras_apply_cc(p.topo(), p.n_tiles, p.tile_sub, p.tile_row0, p.apply_prec, p.w_off, p.W[f], v, z, R, s);
+  }
+  check_launch("oras apply");
+}
+
+int read_active(Ctx* c) {
+  CK(cudaMemcpyAsync(c->work.h_active, c->work.active, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return *c->work.h_active;
+}
+
+struct BlockStats {
+  int outer = 0, steps = 0;
+};
+
+// Solve A_f X = B for a block of R columns ([E][R] layout, FP64 in and out).
+BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const mw_solve_opts& o,
+                       std::vector<int32_t>& its_out) {
+  const int64_t E = c->topo.n_edge;
+  const int m = o.restart;
+  const int wp = o.mode == MW_MODE_FP64 ? 0 : 1;
+  const bool use_p = o.use_precond != 0;
+  require(!use_p || c->prec.ready, MW_ESTATE, "preconditioner requested but not set up");
+  ensure_work(c, R, m, wp);
+  Work& w = c->work;
+  cudaStream_t s = c->stream;
+  const int64_t vstride = E * R;
+  const size_t es = wp == 0 ? sizeof(double2) : sizeof(float2);
+  auto Vp = [&](int i) { return (void*)((unsigned char*)w.V + es * vstride * i); };
+  auto Zp = [&](int i) { return use_p ? (void*)((unsigned char*)w.Z + es * vstride * i) : Vp(i); };
+
+  CK(cudaMemsetAsync(X, 0, sizeof(double2) * E * R, s));
+  int nb = mwk::colnorm2_f64(B, E, R, w.npart, s);
+  mwk::reduce_cols(w.npart, nb, R, w.bnorm, s);
+  mwk::sqrt_inplace(w.bnorm, R, s);
+  std::vector<int32_t> its(R, 0);
+  BlockStats st;
+  const int max_outer = o.mode == MW_MODE_FP64 ? (o.max_it + m - 1) / m + 1 : std::max(1, o.max_outer);
+  int total = 0;
+  for (int outer = 0; outer < max_outer; ++outer) {
+    nb = mwk::residual_f64(c->d_row, c->d_col, c->A64[f], X, B, w.r, w.npart, E, R, s);
+    CK(cudaMemsetAsync(w.active, 0, sizeof(int32_t), s));
+    mwk::start_state(w.npart, nb, R, w.bnorm, o.tol, o.inner_tol, wp == 0, w.rnorm, w.g, w.target, w.done, w.kcol,
+                     m, s);
+    mwk::count_active(w.done, R, w.active, s);
+    check_launch("cycle start");
+    st.outer++;
+    if (read_active(c) == 0 || total >= o.max_it) break;
+    if (wp == 0)
+      mwk::normalize_start_f64(w.r, w.rnorm, w.done, E, R, (double2*)Vp(0), s);
+    else
+      mwk::normalize_start_f32(w.r, w.rnorm, w.done, E, R, (float2*)Vp(0), s);
+    int j = 0;
+    for (; j < m; ++j) {
+      if (use_p) apply_prec(c, f, wp, Vp(j), Zp(j), R);
+      if (wp == 0)
+        mwk::spmm_f64(c->d_row, c->d_col, c->A64[f], (const double2*)Zp(j), (double2*)Vp(j + 1), E, R, s);
+      else
+        mwk::spmm_f32(c->d_row, c->d_col, c->A32[f], (const float2*)Zp(j), (float2*)Vp(j + 1), E, R, s);
+      int np = wp == 0 ? mwk::cgs_dots_f64((const double2*)w.V, vstride, j + 1, (const double2*)Vp(j + 1), E, R,
+                                           w.part, s)
+                       : mwk::cgs_dots_f32((const float2*)w.V, vstride, j + 1, (const float2*)Vp(j + 1), E, R,
+                                           w.part, s);
+      mwk::reduce_h(w.part, np, j + 1, R, w.h, s);
+      int nu = wp == 0 ? mwk::cgs_update_f64((const double2*)w.V, vstride, j + 1, w.h, (double2*)Vp(j + 1), E, R,
+                                             w.npart, s)
+                       : mwk::cgs_update_f32((const float2*)w.V, vstride, j + 1, w.h, (float2*)Vp(j + 1), E, R,
+                                             w.npart, s);
+      CK(cudaMemsetAsync(w.active, 0, sizeof(int32_t), s));
+      mwk::givens_step(w.h, w.npart, nu, j, m, R, w.H, w.cs, w.g, w.target, w.done, w.kcol, w.scale, w.active, s);
+      if (wp == 0)
+        mwk::scale_cols_f64((double2*)Vp(j + 1), w.scale, E, R, s);
+      else
+        mwk::scale_cols_f32((float2*)Vp(j + 1), w.scale, E, R, s);
+      check_launch("arnoldi step");
+      ++total;
+      st.steps++;
+      if (read_active(c) == 0 || total >= o.max_it) {
+        ++j;
+        break;
+      }
+    }
+    mwk::solve_hessenberg(w.H, w.g, w.kcol, m, R, w.y, s);
+    if (wp == 0)
+      mwk::update_x_f64((const double2*)Zp(0), vstride, w.y, w.kcol, m, X, E, R, s);
+    else
+      mwk::update_x_f32((const float2*)Zp(0), vstride, w.y, w.kcol, m, X, E, R, s);
+    check_launch("solution update");
+    CK(cudaMemcpyAsync(w.h_ivec, w.kcol, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int q = 0; q < R; ++q) its[q] += w.h_ivec[q];
+  }
+  its_out = its;
+  return st;
+}
+
+// final true relative residuals of a block (FP64), into rel[R] on the host
+void true_relres(Ctx* c, int f, int R, const double2* B, const double2* X, double* rel) {
+  Work& w = c->work;
+  cudaStream_t s = c->stream;
+  const int64_t E = c->topo.n_edge;
+  int nb = mwk::residual_f64(c->d_row, c->d_col, c->A64[f], X, B, w.r, w.npart, E, R, s);
+  mwk::reduce_cols(w.npart, nb, R, w.rnorm, s);
+  nb = mwk::colnorm2_f64(B, E, R, w.npart, s);
+  mwk::reduce_cols(w.npart, nb, R, w.bnorm, s);
+  std::vector<double> a(R), b(R);
+  CK(cudaMemcpyAsync(a.data(), w.rnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(b.data(), w.bnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int q = 0; q < R; ++q) rel[q] = b[q] > 0 ? std::sqrt(a[q] / b[q]) : std::sqrt(a[q]);
+}
+
+mw_solve_opts norm_opts(const mw_solve_opts* o) {
+  mw_solve_opts d{};
+  d.mode = MW_MODE_FP64;
+  d.restart = 50;
+  d.batch = 0;
+  d.max_it = 5000;
+  d.tol = 1e-8;
+  d.inner_tol = 1e-4;
+  d.max_outer = 20;
+  d.use_precond = 1;
+  if (o) d = *o;
+  require(d.mode == MW_MODE_FP64 || d.mode == MW_MODE_MIXED, MW_EINVAL, "unknown solve mode");
+  require(d.restart >= 1 && d.restart <= kMaxRestart, MW_EINVAL, "restart must be in [1, 63]");
+  require(d.tol > 0 && d.max_it >= 1, MW_EINVAL, "tol > 0 and max_it >= 1 required");
+  if (d.inner_tol <= 0) d.inner_tol = 1e-4;
+  if (d.max_outer <= 0) d.max_outer = 20;
+  return d;
+}
+
+// Solve all frequencies for RHS blocks Bf[f] ([E][ncols]) into Xf[f]; fills stats.
+void solve_all(Ctx* c, const mw_solve_opts& o, int ncols, const std::vector<const double2*>& Bf,
+               const std::vector<double2*>& Xf, mw_solve_stats* stats) {
+  const int64_t E = c->topo.n_edge;
+  cudaStream_t s = c->stream;
+  const int bsz = (o.batch <= 0 || o.batch > ncols) ? ncols : o.batch;
+  require(bsz <= 128, MW_EINVAL, "at most 128 columns per Krylov launch (set batch)");
+  std::vector<int32_t> its_all(c->n_freq * ncols, 0);
+  std::vector<double> rel_all(c->n_freq * ncols, 0.0);
+  int outer = 0, steps = 0;
+  CK(cudaEventRecord(c->ev0, s));
+  for (int f = 0; f < c->n_freq; ++f) {
+    for (int c0 = 0; c0 < ncols; c0 += bsz) {
+      const int R = std::min(bsz, ncols - c0);
+      const double2* B = Bf[f] + c0;
+      double2* X = Xf[f] + c0;
+      std::vector<int32_t> its;
+      if (R == ncols) {
+        BlockStats bs = solve_block(c, f, R, B, X, o, its);
+        outer += bs.outer;
+        steps += bs.steps;
+        true_relres(c, f, R, B, X, rel_all.data() + f * ncols + c0);
+      } else {
+        ensure_work(c, R, o.restart, o.mode == MW_MODE_FP64 ? 0 : 1);
+        Work& w = c->work;
+        CK(cudaMemcpy2DAsync(w.bblk, sizeof(double2) * R, B, sizeof(double2) * ncols, sizeof(double2) * R, E,
+                             cudaMemcpyDeviceToDevice, s));
+        // w.x is reused as the block solution
+        BlockStats bs = solve_block(c, f, R, w.bblk, w.x, o, its);
+        outer += bs.outer;
+        steps += bs.steps;
+        true_relres(c, f, R, w.bblk, w.x, rel_all.data() + f * ncols + c0);
+        CK(cudaMemcpy2DAsync(X, sizeof(double2) * ncols, w.x, sizeof(double2) * R, sizeof(double2) * R, E,
+                             cudaMemcpyDeviceToDevice, s));
+      }
+      for (int q = 0; q < R; ++q) its_all[f * ncols + c0 + q] = its[q];
+    }
+  }
+  CK(cudaEventRecord(c->ev1, s));
+  CK(cudaEventSynchronize(c->ev1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  int nconv = 0;
+  double mx = 0;
+  for (double r : rel_all) {
+    if (r <= o.tol) ++nconv;
+    mx = std::max(mx, r);
+  }
+  if (stats) {
+    stats->n_cols = c->n_freq * ncols;
+    stats->n_converged = nconv;
+    stats->outer_steps = outer;
+    stats->arnoldi_steps = steps;
+    stats->max_relres = mx;
+    stats->solve_ms = ms;
+    if (stats->iters) std::memcpy(stats->iters, its_all.data(), sizeof(int32_t) * its_all.size());
+    if (stats->relres) std::memcpy(stats->relres, rel_all.data(), sizeof(double) * rel_all.size());
+  }
+  if (nconv < c->n_freq * ncols)
+    throw Fail{MW_ENOCONV, "GMRES: " + std::to_string(c->n_freq * ncols - nconv) + " columns missed tol (max relres " +
+                               std::to_string(mx) + ")"};
+}
+
+void build_dipole_rhs(Ctx* c, int f, double2* B) {
+  const double om = 2.0 * mw::kPi * c->freqs[f];
+  mwk::dipole_rhs(c->d_src_edge, c->d_src_sign, c->n_src, -om * mw::kMu0, B, c->topo.n_edge, c->stream);
+  check_launch("dipole rhs");
+}
+
+void alloc_fields(Ctx* c, std::vector<double2*>& v) {
+  const int64_t n = c->topo.n_edge * (int64_t)c->n_src;
+  if ((int)v.size() == c->n_freq && !v.empty()) return;
+  for (auto p : v) dfree(c, p);
+  v.assign(c->n_freq, nullptr);
+  for (int f = 0; f < c->n_freq; ++f) v[f] = dalloc<double2>(c, n);
+}
+
+void forward(Ctx* c, const mw_solve_opts& o, mw_solve_stats* stats) {
+  require(c->has_mesh && c->n_freq > 0, MW_ESTATE, "assemble first");
+  require(c->n_src > 0, MW_ESTATE, "set sources first");
+  alloc_fields(c, c->Xf);
+  const int64_t E = c->topo.n_edge;
+  std::vector<const double2*> Bs(c->n_freq);
+  std::vector<double2*> Bown(c->n_freq, nullptr);
+  for (int f = 0; f < c->n_freq; ++f) {
+    Bown[f] = dalloc<double2>(c, E * c->n_src);
+    build_dipole_rhs(c, f, Bown[f]);
+    Bs[f] = Bown[f];
+  }
+  try {
+    solve_all(c, o, c->n_src, Bs, c->Xf, stats);
+  } catch (...) {
+    for (auto p : Bown) dfree(c, p);
+    throw;
+  }
+  for (auto p : Bown) dfree(c, p);
+}
+
+void release_prec(Ctx* c) {
+  Prec& p = c->prec;
+  for (void* q : {(void*)p.dof_ptr, (void*)p.own_ptr, (void*)p.tet_ptr, (void*)p.surf_ptr, (void*)p.dofs,
+                  (void*)p.own_local, (void*)p.own_glob, (void*)p.tet_ids, (void*)p.tet_loc, (void*)p.surf_loc,
+                  (void*)p.surf_tet, (void*)p.surf_vert, (void*)p.Bsurf, (void*)p.tile_sub, (void*)p.tile_row0,
+                  (void*)p.w_off})
+    dfree(c, q);
+  for (void* q : p.W) dfree(c, q);
+  mwk::tc_plan_free(p.tc, [&](void* q) { dfree(c, q); });
+  p = Prec();
+}
+
+void release_mesh(Ctx* c) {
+  release_prec(c);
+  free_work(c);
+  for (auto p : c->Xf) dfree(c, p);
+  for (auto p : c->Lf) dfree(c, p);
+  c->Xf.clear();
+  c->Lf.clear();
+  for (auto p : c->A64) dfree(c, p);
+  for (auto p : c->A32) dfree(c, p);
+  c->A64.clear();
+  c->A32.clear();
+  for (void* q : {(void*)c->d_xyz, (void*)c->d_tets, (void*)c->d_col, (void*)c->d_contrib, (void*)c->d_bface_vert,
+                  (void*)c->d_tet_edge, (void*)c->d_tet_nb, (void*)c->d_sign, (void*)c->d_row, (void*)c->d_cptr,
+                  (void*)c->d_KM, (void*)c->d_vol, (void*)c->d_Bf, (void*)c->d_tikw, (void*)c->d_eps,
+                  (void*)c->d_src_edge, (void*)c->d_src_sign, (void*)c->d_B, (void*)c->d_red})
+    dfree(c, q);
+  c->d_xyz = nullptr;
+  c->d_tets = c->d_col = c->d_contrib = c->d_bface_vert = c->d_tet_edge = c->d_tet_nb = nullptr;
+  c->d_sign = nullptr;
+  c->d_row = c->d_cptr = nullptr;
+  c->d_KM = c->d_vol = c->d_Bf = c->d_tikw = c->d_eps = nullptr;
+  c->d_src_edge = nullptr;
+  c->d_src_sign = nullptr;
+  c->d_B = nullptr;
+  c->d_red = nullptr;
+  c->has_mesh = false;
+  c->n_freq = 0;
+  c->n_src = 0;
+}
+
+}  // namespace mwimpl
+
+using namespace mwimpl;
+
+// =======================================================================================
+// C ABI
+// =======================================================================================
+struct mw_ctx : Ctx {};
+
+extern "C" {
+
+mw_status mw_create(mw_ctx** out, int device, void* stream) {
+  if (!out) return MW_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return MW_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return MW_ECUDA;
+  std::unique_ptr<mw_ctx> c(new mw_ctx());
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return MW_ECUDA;
+  *out = c.release();
+  return MW_OK;
+}
+
+void mw_destroy(mw_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  release_mesh(c);
+  for (auto& kv : c->allocs) cudaFree(kv.first);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+}
+
+const char* mw_last_error(const mw_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+mw_status mw_set_memory_cap(mw_ctx* c, int64_t bytes) {
+  return guard(c, [&] {
+    require(bytes >= 0, MW_EINVAL, "cap must be >= 0");
+    c->mem_cap = bytes;
+  });
+}
+
+mw_status mw_set_mesh(mw_ctx* c, int64_t n_vert, const double* xyz, int64_t n_tet, const int32_t* tv,
+                      mw_mesh_info* out) {
+  return guard(c, [&] {
+    require(xyz && tv, MW_EINVAL, "null mesh arrays");
+    release_mesh(c);
+    Error err{MW_OK, ""};
+    if (!mw::build_topology(n_vert, n_tet, tv, c->topo, err)) throw Fail{err.code, err.msg};
+    for (int64_t i = 0; i < 3 * n_vert; ++i) require(std::isfinite(xyz[i]), MW_EINVAL, "non-finite vertex coordinate");
+    c->xyz.assign(xyz, xyz + 3 * n_vert);
+    mw::Topology& t = c->topo;
+    c->d_xyz = upload(c, xyz, 3 * n_vert);
+    c->d_tets = upload(c, t.tets.data(), t.tets.size());
+    c->d_sign = upload(c, t.tet_sign.data(), t.tet_sign.size());
+    c->d_tet_edge = upload(c, t.tet_edge.data(), t.tet_edge.size());
+    c->d_row = upload(c, t.row_ptr.data(), t.row_ptr.size());
+    c->d_col = upload(c, t.col_idx.data(), t.col_idx.size());
+    c->d_cptr = upload(c, t.contrib_ptr.data(), t.contrib_ptr.size());
+    c->d_contrib = upload(c, t.contrib.data(), t.contrib.size());
+    c->d_bface_vert = upload(c, t.bface_vert.data(), t.bface_vert.size());
+    c->d_tet_nb = upload(c, t.tet_nb.data(), t.tet_nb.size());
+    c->d_KM = dalloc<double>(c, 42 * n_tet);
+    c->d_vol = dalloc<double>(c, n_tet);
+    c->d_Bf = dalloc<double>(c, 6 * std::max<int64_t>(t.n_bface, 1));
+    c->d_tikw = dalloc<double>(c, 4 * n_tet);
+    c->d_red = dalloc<double>(c, 4096);
+    mwk::elem_geom(c->d_xyz, c->d_tets, c->d_sign, n_tet, c->d_KM, c->d_vol, c->stream);
+    mwk::face_geom(c->d_xyz, c->d_bface_vert, t.n_bface, c->d_Bf, c->stream);
+    mwk::tikhonov_weights(c->d_xyz, c->d_tets, c->d_tet_nb, n_tet, c->d_tikw, c->stream);
+    check_launch("element geometry");
+    // reject degenerate tets
+    std::vector<double> vol(n_tet);
+    CK(cudaMemcpyAsync(vol.data(), c->d_vol, sizeof(double) * n_tet, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int64_t e = 0; e < n_tet; ++e) require(vol[e] > 0 && std::isfinite(vol[e]), MW_EINVAL, "degenerate tet");
+    c->has_mesh = true;
+    if (out) *out = {t.n_vert, t.n_tet, t.n_edge, t.n_face, t.n_bface, t.nnz};
+  });
+}
+
+mw_status mw_get_topology(mw_ctx* c, int32_t* edge_vert, int32_t* tet_edge, int8_t* tet_sign, int64_t* row_ptr,
+                          int32_t* col_idx) {
+  return guard(c, [&] {
+    require(c->has_mesh, MW_ESTATE, "no mesh");
+    const mw::Topology& t = c->topo;
+    if (edge_vert) std::memcpy(edge_vert, t.edge_vert.data(), sizeof(int32_t) * t.edge_vert.size());
+    if (tet_edge) std::memcpy(tet_edge, t.tet_edge.data(), sizeof(int32_t) * t.tet_edge.size());
+    if (tet_sign) std::memcpy(tet_sign, t.tet_sign.data(), t.tet_sign.size());
+    if (row_ptr) std::memcpy(row_ptr, t.row_ptr.data(), sizeof(int64_t) * t.row_ptr.size());
+    if (col_idx) std::memcpy(col_idx, t.col_idx.data(), sizeof(int32_t) * t.col_idx.size());
+  });
+}
+
+mw_status mw_get_element_matrices(mw_ctx* c, double* K, double* M, double* vol) {
+  return guard(c, [&] {
+    require(c->has_mesh, MW_ESTATE, "no mesh");
+    const int64_t T = c->topo.n_tet;
+    std::vector<double> km(42 * T);
+    CK(cudaMemcpyAsync(km.data(), c->d_KM, sizeof(double) * km.size(), cudaMemcpyDeviceToHost, c->stream));
+    if (vol) CK(cudaMemcpyAsync(vol, c->d_vol, sizeof(double) * T, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int64_t e = 0; e < T; ++e)
+      for (int m = 0; m < 6; ++m)
+        for (int n = 0; n < 6; ++n) {
+          if (K) K[36 * e + 6 * m + n] = km[42 * e + mw::packed6(m, n)];
+          if (M) M[36 * e + 6 * m + n] = km[42 * e + 21 + mw::packed6(m, n)];
+        }
+  });
+}
+
+mw_status mw_assemble(mw_ctx* c, int32_t n_freq, const double* freq_hz, const double* eps_r, const double* eps_bg) {
+  return guard(c, [&] {
+    require(c->has_mesh, MW_ESTATE, "set the mesh first");
+    require(n_freq >= 1 && n_freq <= 64 && freq_hz && eps_r && eps_bg, MW_EINVAL, "bad assemble arguments");
+    const int64_t T = c->topo.n_tet, nnz = c->topo.nnz;
+    for (int f = 0; f < n_freq; ++f) require(freq_hz[f] > 0 && std::isfinite(freq_hz[f]), MW_EINVAL, "bad frequency");
+    for (int64_t i = 0; i < 2 * T; ++i) require(std::isfinite(eps_r[i]), MW_EINVAL, "non-finite permittivity");
+    require(std::isfinite(eps_bg[0]) && std::isfinite(eps_bg[1]), MW_EINVAL, "non-finite background permittivity");
+    if (n_freq != c->n_freq) {
+      for (auto p : c->A64) dfree(c, p);
+      for (auto p : c->A32) dfree(c, p);
+      c->A64.assign(n_freq, nullptr);
+      c->A32.assign(n_freq, nullptr);
+      for (int f = 0; f < n_freq; ++f) {
+        c->A64[f] = dalloc<double2>(c, nnz);
+        c->A32[f] = dalloc<float2>(c, nnz);
+      }
+      for (auto p : c->Xf) dfree(c, p);
+      for (auto p : c->Lf) dfree(c, p);
+      c->Xf.clear();
+      c->Lf.clear();
+      if (c->prec.ready && (int)c->prec.W.size() != n_freq) release_prec(c);
+    }
+    c->n_freq = n_freq;
+    c->freqs.assign(freq_hz, freq_hz + n_freq);
+    c->eps_bg[0] = eps_bg[0];
+    c->eps_bg[1] = eps_bg[1];
+    c->eps.assign(eps_r, eps_r + 2 * T);
+    if (!c->d_eps) c->d_eps = dalloc<double>(c, 2 * T);
+    CK(cudaMemcpyAsync(c->d_eps, eps_r, sizeof(double) * 2 * T, cudaMemcpyHostToDevice, c->stream));
+    // i k0 sqrt(eps_bg): principal square root
+    const double r = std::hypot(eps_bg[0], eps_bg[1]);
+    const double sr = std::sqrt(0.5 * (r + eps_bg[0]));
+    double si = std::sqrt(std::max(0.0, 0.5 * (r - eps_bg[0])));
+    if (eps_bg[1] < 0) si = -si;
+    for (int f = 0; f < n_freq; ++f) {
+      const double k0 = k0_of(freq_hz[f]);
+      mwk::reassemble(c->d_cptr, c->d_contrib, nnz, c->d_KM, c->d_Bf, c->d_eps, k0 * k0, -k0 * si, k0 * sr, c->A64[f],
+                      c->A32[f], c->stream);
+    }
+    check_launch("reassemble");
+  });
+}
+
+mw_status mw_get_matrix(mw_ctx* c, int32_t f, double* values) {
+  return guard(c, [&] {
+    require(f >= 0 && f < c->n_freq && values, MW_EINVAL, "bad frequency index or null output");
+    CK(cudaMemcpyAsync(values, c->A64[f], sizeof(double2) * c->topo.nnz, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  });
+}
+
+mw_status mw_apply_matrix(mw_ctx* c, int32_t f, int32_t prec, const void* x, void* y, int32_t n_cols) {
+  return guard(c, [&] {
+    require(f >= 0 && f < c->n_freq && x && y && n_cols >= 1 && n_cols <= 128, MW_EINVAL, "bad apply_matrix args");
+    if (prec == MW_PREC_FP64)
+      mwk::spmm_f64(c->d_row, c->d_col, c->A64[f], (const double2*)x, (double2*)y, c->topo.n_edge, n_cols, c->stream);
+    else if (prec == MW_PREC_FP32)
+      mwk::spmm_f32(c->d_row, c->d_col, c->A32[f], (const float2*)x, (float2*)y, c->topo.n_edge, n_cols, c->stream);
+    else
+      throw Fail{MW_EINVAL, "apply_matrix precision must be FP64 or FP32"};
+    check_launch("spmm");
+  });
+}
+
+mw_status mw_set_sources(mw_ctx* c, int32_t n_src, const double* pos, const double* dir, int32_t* edge_out,
+                         int8_t* sign_out) {
+  return guard(c, [&] {
+    require(c->has_mesh, MW_ESTATE, "set the mesh first");
+    require(n_src >= 1 && n_src <= 4096 && pos && dir, MW_EINVAL, "bad source arguments");
+    const mw::Topology& t = c->topo;
+    std::vector<int32_t> cand;
+    for (int64_t e = 0; e < t.n_edge; ++e) {
+      const double* a = &c->xyz[3 * (int64_t)t.edge_vert[2 * e]];
+      const double* b = &c->xyz[3 * (int64_t)t.edge_vert[2 * e + 1]];
+      const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+      if (dz != 0 && std::fabs(dx) <= 1e-9 * std::fabs(dz) && std::fabs(dy) <= 1e-9 * std::fabs(dz))
+        cand.push_back((int32_t)e);
+    }
+    require(!cand.empty(), MW_EINVAL, "mesh has no z-directed edge");
+    c->src_edge.assign(n_src, 0);
+    c->src_sign.assign(n_src, 1);
+    for (int j = 0; j < n_src; ++j) {
+      require(dir[3 * j] == 0 && dir[3 * j + 1] == 0 && dir[3 * j + 2] != 0, MW_EINVAL, "only z-directed dipoles");
+      double best = INFINITY;
+      int32_t be = -1;
+      for (int32_t e : cand) {
+        const double* a = &c->xyz[3 * (int64_t)t.edge_vert[2 * (int64_t)e]];
+        const double* b = &c->xyz[3 * (int64_t)t.edge_vert[2 * (int64_t)e + 1]];
+        double d2 = 0;
+        for (int k = 0; k < 3; ++k) {
+          const double mid = 0.5 * (a[k] + b[k]);
+          const double d = mid - pos[3 * j + k];
+          d2 = d2 + d * d;
+        }
+        if (d2 < best) {
+          best = d2;
+          be = e;
+        }
+      }
+      const double* a = &c->xyz[3 * (int64_t)t.edge_vert[2 * (int64_t)be]];
+      const double* b = &c->xyz[3 * (int64_t)t.edge_vert[2 * (int64_t)be + 1]];
+      c->src_edge[j] = be;
+      c->src_sign[j] = ((b[2] - a[2]) * dir[3 * j + 2] > 0) ? 1 : -1;
+    }
+    c->n_src = n_src;
+    dfree(c, c->d_src_edge);
+    dfree(c, c->d_src_sign);
+    c->d_src_edge = upload(c, c->src_edge.data(), n_src);
+    c->d_src_sign = upload(c, c->src_sign.data(), n_src);
+    for (auto p : c->Xf) dfree(c, p);
+    for (auto p : c->Lf) dfree(c, p);
+    c->Xf.clear();
+    c->Lf.clear();
+    if (edge_out) std::memcpy(edge_out, c->src_edge.data(), sizeof(int32_t) * n_src);
+    if (sign_out) std::memcpy(sign_out, c->src_sign.data(), n_src);
+  });
+}
+
+mw_status mw_setup_preconditioner(mw_ctx* c, int32_t n_sub, const int32_t* part, int32_t overlap, int32_t inv_prec) {
+  return guard(c, [&] {
+    require(c->has_mesh && c->n_freq > 0, MW_ESTATE, "assemble before setting up the preconditioner");
+    require(inv_prec >= 0 && inv_prec <= 3, MW_EINVAL, "inv_prec must be 0 (FP64), 1 (FP32), 2 (BF16) or 3 (FP32 "
+                                                       "factorisation applied in FP64)");
+    release_prec(c);
+    Prec& p = c->prec;
+    Error err{MW_OK, ""};
+    if (!mw::build_subdomains(c->topo, n_sub, part, overlap, p.sd, err)) throw Fail{err.code, err.msg};
+    const mw::Subdomains& sd = p.sd;
+    p.apply_prec = inv_prec == 3 ? 0 : inv_prec;
+    p.factor_prec = inv_prec == 0 ? 0 : 1;
+    p.dof_ptr = upload(c, sd.dof_ptr.data(), sd.dof_ptr.size());
+    p.dofs = upload(c, sd.dofs.data(), sd.dofs.size());
+    p.own_ptr = upload(c, sd.own_ptr.data(), sd.own_ptr.size());
+    p.own_local = upload(c, sd.own_local.data(), sd.own_local.size());
+    std::vector<int32_t> own_glob(sd.own_local.size());
+    for (int s = 0; s < n_sub; ++s)
+      for (int64_t q = sd.own_ptr[s]; q < sd.own_ptr[s + 1]; ++q)
+        own_glob[q] = sd.dofs[sd.dof_ptr[s] + sd.own_local[q]];
+    p.own_glob = upload(c, own_glob.data(), own_glob.size());
+    p.tet_ptr = upload(c, sd.tet_ptr.data(), sd.tet_ptr.size());
+    p.tet_ids = upload(c, sd.tet_ids.data(), sd.tet_ids.size());
+    p.tet_loc = upload(c, sd.tet_loc.data(), sd.tet_loc.size());
+    p.surf_ptr = upload(c, sd.surf_ptr.data(), sd.surf_ptr.size());
+    p.surf_loc = upload(c, sd.surf_loc.data(), sd.surf_loc.size());
+    p.surf_tet = upload(c, sd.surf_tet.data(), sd.surf_tet.size());
+    p.surf_vert = upload(c, sd.surf_vert.data(), sd.surf_vert.size());
+    const int64_t n_surf = (int64_t)sd.surf_tet.size();
+    p.Bsurf = dalloc<double>(c, 6 * std::max<int64_t>(n_surf, 1));
+    mwk::face_geom(c->d_xyz, p.surf_vert, n_surf, p.Bsurf, c->stream);
+    // W offsets (cc layouts) and apply tiles
+    std::vector<int64_t> woff(n_sub + 1, 0);
+    std::vector<int32_t> tsub, trow;
+    int64_t nmax = 0;
+    for (int s = 0; s < n_sub; ++s) {
+      const int64_t n = sd.dof_ptr[s + 1] - sd.dof_ptr[s], no = sd.own_ptr[s + 1] - sd.own_ptr[s];
+      woff[s + 1] = woff[s] + n * no;
+      nmax = std::max(nmax, n);
+      for (int64_t r0 = 0; r0 < no; r0 += 32) {
+        tsub.push_back(s);
+        trow.push_back((int32_t)r0);
+      }
+    }
+    p.n_tiles = (int)tsub.size();
+    p.tile_sub = upload(c, tsub.data(), tsub.size());
+    p.tile_row0 = upload(c, trow.data(), trow.size());
+    p.w_off = upload(c, woff.data(), woff.size());
+    if (p.apply_prec == 2)
+      require(mwk::tc_plan_build(p.tc, sd, [&](size_t b) { return (void*)dalloc<unsigned char>(c, b); }, c->stream),
+              MW_EINVAL, "BF16 tensor-core apply unavailable for this partition");
+    const size_t wes = p.apply_prec == 0 ? sizeof(double2) : sizeof(float2);
+    const size_t fes = p.factor_prec == 0 ? sizeof(double2) : sizeof(float2);
+    // workspace batches
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 4);
+    budget = std::max<size_t>(budget, (size_t)nmax * nmax * fes);
+    std::vector<int32_t> bsub;
+    std::vector<int64_t> bn, boff;
+    int32_t* d_status = dalloc<int32_t>(c, 1);
+    CK(cudaMemsetAsync(d_status, 0, sizeof(int32_t), c->stream));
+    void* ws = dalloc<unsigned char>(c, budget);
+    int32_t* d_bsub = dalloc<int32_t>(c, n_sub);
+    int64_t* d_bn = dalloc<int64_t>(c, n_sub);
+    int64_t* d_boff = dalloc<int64_t>(c, n_sub);
+    void* dinv = dalloc<unsigned char>(c, (size_t)n_sub * 32 * 32 * fes);
+    p.W.assign(c->n_freq, nullptr);
+    try {
+      for (int f = 0; f < c->n_freq; ++f) {
+        if (p.apply_prec == 2)
+          p.W[f] = dalloc<unsigned char>(c, mwk::tc_w_bytes(p.tc));
+        else
+          p.W[f] = dalloc<unsigned char>(c, wes * std::max<int64_t>(woff[n_sub], 1));
+        const double k0 = k0_of(c->freqs[f]);
+        int s = 0;
+        while (s < n_sub) {
+          bsub.clear();
+          bn.clear();
+          boff.clear();
+          size_t used = 0;
+          int64_t bmax = 0;
+          while (s < n_sub) {
+            const int64_t n = sd.dof_ptr[s + 1] - sd.dof_ptr[s];
+            const size_t need = (size_t)n * n * fes;
+            if (!bsub.empty() && used + need > budget) break;
+            bsub.push_back(s);
+            bn.push_back(n);
+            boff.push_back((int64_t)(used / fes));
+            used += need;
+            used = (used + 255) / 256 * 256;
+            bmax = std::max(bmax, n);
+            ++s;
+          }
+          const int cnt = (int)bsub.size();
+          CK(cudaMemcpyAsync(d_bsub, bsub.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, c->stream));
+          CK(cudaMemcpyAsync(d_bn, bn.data(), sizeof(int64_t) * cnt, cudaMemcpyHostToDevice, c->stream));
+          CK(cudaMemcpyAsync(d_boff, boff.data(), sizeof(int64_t) * cnt, cudaMemcpyHostToDevice, c->stream));
+          mwk::OrasBatch bt{cnt, bmax, d_bsub, d_bn, d_boff};
+          CK(cudaMemsetAsync(ws, 0, used, c->stream));
+          mwk::oras_local_assemble(bt, p.topo(), p.Bsurf, c->d_KM, c->d_eps, k0, c->eps_bg[0], c->eps_bg[1],
+                                   p.factor_prec, ws, c->stream);
+          mwk::oras_invert(bt, p.factor_prec, ws, dinv, d_status, c->stream);
+          if (p.apply_prec == 2)
+            mwk::tc_extract(p.tc, bt, p.topo(), p.factor_prec, ws, p.W[f], c->stream);
+          else
+            mwk::oras_extract(bt, p.topo(), p.factor_prec, ws, p.apply_prec, p.w_off, p.W[f], c->stream);
+          check_launch("oras setup");
+          // host vectors must outlive the async copies
+          CK(cudaStreamSynchronize(c->stream));
+        }
+      }
+      int32_t st = 0;
+      CK(cudaMemcpy(&st, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+      require(st == 0, MW_ESINGULAR, "a subdomain matrix had a near-zero pivot");
+    } catch (...) {
+      dfree(c, ws);
+      dfree(c, dinv);
+      dfree(c, d_status);
+      dfree(c, d_bsub);
+      dfree(c, d_bn);
+      dfree(c, d_boff);
+      release_prec(c);
+      throw;
+    }
+    dfree(c, ws);
+    dfree(c, dinv);
+    dfree(c, d_status);
+    dfree(c, d_bsub);
+    dfree(c, d_bn);
+    dfree(c, d_boff);
+    p.ready = true;
+  });
+}
+
+mw_status mw_apply_preconditioner(mw_ctx* c, int32_t f, const void* r, void* z, int32_t n_cols) {
+  return guard(c, [&] {
+    require(c->prec.ready, MW_ESTATE, "no preconditioner");
+    require(f >= 0 && f < c->n_freq && r && z && n_cols >= 1 && n_cols <= 128, MW_EINVAL, "bad arguments");
+    const int64_t n = c->topo.n_edge * (int64_t)n_cols;
+    if (c->prec.apply_prec == 0) {
+      CK(cudaMemsetAsync(z, 0, sizeof(double2) * n, c->stream));
+      apply_prec(c, f, 0, r, z, n_cols);
+    } else {
+      float2* a = dalloc<float2>(c, n);
+      float2* b = dalloc<float2>(c, n);
+      mwk::cast_f64_to_f32((const double2*)r, a, n, c->stream);
+      CK(cudaMemsetAsync(b, 0, sizeof(float2) * n, c->stream));
+      apply_prec(c, f, 1, a, b, n_cols);
+      mwk::cast_f32_to_f64(b, (double2*)z, n, c->stream);
+      CK(cudaStreamSynchronize(c->stream));
+      dfree(c, a);
+      dfree(c, b);
+    }
+    check_launch("apply preconditioner");
+  });
+}
+
+mw_status mw_get_partition(mw_ctx* c, int32_t* owner, int32_t* sub_size) {
+  return guard(c, [&] {
+    require(c->prec.ready, MW_ESTATE, "no preconditioner");
+    const mw::Subdomains& sd = c->prec.sd;
+    if (owner) std::memcpy(owner, sd.owner.data(), sizeof(int32_t) * sd.owner.size());
+    if (sub_size)
+      for (int s = 0; s < sd.n_sub; ++s) sub_size[s] = (int32_t)(sd.dof_ptr[s + 1] - sd.dof_ptr[s]);
+  });
+}
+
+mw_status mw_solve(mw_ctx* c, const mw_solve_opts* opts, void* fields, double* S, mw_solve_stats* stats) {
+  mw_status st = guard(c, [&] {
+    mw_solve_opts o = norm_opts(opts);
+    mw_status conv = MW_OK;
+    std::string msg;
+    try {
+      forward(c, o, stats);
+    } catch (const Fail& e) {
+      if (e.code != MW_ENOCONV) throw;
+      conv = e.code;
+      msg = e.msg;
+    }
+    const int64_t E = c->topo.n_edge;
+    if (fields)
+      for (int f = 0; f < c->n_freq; ++f)
+        mwk::transpose_out(c->Xf[f], (double2*)fields + (int64_t)f * c->n_src * E, E, c->n_src, c->stream);
+    if (S) {
+      double2* dS = dalloc<double2>(c, (size_t)c->n_freq * c->n_src * c->n_src);
+      for (int f = 0; f < c->n_freq; ++f)
+        mwk::s_extract(c->Xf[f], c->d_src_edge, c->d_src_sign, c->n_src, dS + (size_t)f * c->n_src * c->n_src,
+                       c->stream);
+      CK(cudaMemcpyAsync(S, dS, sizeof(double2) * c->n_freq * c->n_src * c->n_src, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      dfree(c, dS);
+    }
+    check_launch("solve outputs");
+    CK(cudaStreamSynchronize(c->stream));
+    if (conv != MW_OK) throw Fail{conv, msg};
+  });
+  return st;
+}
+
+mw_status mw_solve_rhs(mw_ctx* c, const mw_solve_opts* opts, int32_t n_cols, const void* b, void* x,
+                       mw_solve_stats* stats) {
+  return guard(c, [&] {
+    require(c->has_mesh && c->n_freq > 0, MW_ESTATE, "assemble first");
+    require(n_cols >= 1 && b && x, MW_EINVAL, "bad solve_rhs arguments");
+    mw_solve_opts o = norm_opts(opts);
+    const int64_t E = c->topo.n_edge;
+    std::vector<double2*> Bi(c->n_freq), Xi(c->n_freq);
+    std::vector<const double2*> Bc(c->n_freq);
+    for (int f = 0; f < c->n_freq; ++f) {
+      Bi[f] = dalloc<double2>(c, E * n_cols);
+      Xi[f] = dalloc<double2>(c, E * n_cols);
+      mwk::transpose_in((const double2*)b + (int64_t)f * n_cols * E, Bi[f], E, n_cols, c->stream);
+      Bc[f] = Bi[f];
+    }
+    mw_status conv = MW_OK;
+    std::string msg;
+    try {
+      solve_all(c, o, n_cols, Bc, Xi, stats);
+    } catch (const Fail& e) {
+      if (e.code != MW_ENOCONV) {
+        for (int f = 0; f < c->n_freq; ++f) {
+          dfree(c, Bi[f]);
+          dfree(c, Xi[f]);
+        }
+        throw;
+      }
+      conv = e.code;
+      msg = e.msg;
+    }
+    for (int f = 0; f < c->n_freq; ++f)
+      mwk::transpose_out(Xi[f], (double2*)x + (int64_t)f * n_cols * E, E, n_cols, c->stream);
+    CK(cudaStreamSynchronize(c->stream));
+    for (int f = 0; f < c->n_freq; ++f) {
+      dfree(c, Bi[f]);
+      dfree(c, Xi[f]);
+    }
+    if (conv != MW_OK) throw Fail{conv, msg};
+  });
+}
+
+// ---------------------------------------------------------------------------------------
+// cost, adjoint and gradient
+// ---------------------------------------------------------------------------------------
+static void tikhonov_dev(Ctx* c, const double* d_eps, double* R_out, double* d_grad) {
+  mwk::tikhonov(c->d_tet_nb, c->d_tikw, d_eps, c->topo.n_tet, d_grad, c->d_red, c->stream);
+  double r = 0;
+  CK(cudaMemcpyAsync(&r, c->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *R_out = r;
+}
+
+mw_status mw_tikhonov(mw_ctx* c, const double* eps_r, double* R_out, double* grad) {
+  return guard(c, [&] {
+    require(c->has_mesh && eps_r && R_out, MW_EINVAL, "bad tikhonov arguments");
+    const int64_t T = c->topo.n_tet;
+    double* de = upload(c, eps_r, 2 * T);
+    double* dg = dalloc<double>(c, 2 * T);
+    tikhonov_dev(c, de, R_out, dg);
+    if (grad) {
+      CK(cudaMemcpyAsync(grad, dg, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+    dfree(c, de);
+    dfree(c, dg);
+  });
+}
+
+static void gradient_impl(Ctx* c, const mw_solve_opts& o, const double* S_obs, const double* S_empty, double alpha,
+                          double* J_out, double* grad, double* S_out) {
+  require(c->has_mesh && c->n_freq > 0 && c->n_src > 0, MW_ESTATE, "assemble and set sources first");
+  require(S_obs && S_empty && J_out, MW_EINVAL, "null S_obs / S_empty / J_out");
+  require(c->n_src <= 128, MW_EINVAL, "gradient supports at most 128 sources");
+  const int64_t E = c->topo.n_edge, T = c->topo.n_tet;
+  const int ns = c->n_src, nf = c->n_freq;
+  const size_t nS = (size_t)nf * ns * ns;
+  forward(c, o, nullptr);
+  alloc_fields(c, c->Lf);
+  double2* dS = dalloc<double2>(c, nS);
+  double2* dSo = upload(c, (const double2*)S_obs, nS);
+  double2* dSe = upload(c, (const double2*)S_empty, nS);
+  double2* dC = dalloc<double2>(c, nS);
+  double* dg = dalloc<double>(c, 2 * T);
+  double* dJ = dalloc<double>(c, 1);
+  std::vector<const double2*> Bc(nf);
+  std::vector<double2*> Bs(nf);
+  for (int f = 0; f < nf; ++f) {
+    mwk::s_extract(c->Xf[f], c->d_src_edge, c->d_src_sign, ns, dS + (size_t)f * ns * ns, c->stream);
+  }
+  mwk::adjoint_weights(dS, dSo, dSe, (int64_t)nS, dC, dJ, c->stream);
+  for (int f = 0; f < nf; ++f) {
+    Bs[f] = dalloc<double2>(c, E * ns);
+    mwk::adjoint_rhs(c->d_src_edge, c->d_src_sign, ns, dC + (size_t)f * ns * ns, Bs[f], E, c->stream);
+    Bc[f] = Bs[f];
+  }
+  check_launch("adjoint sources");
+  solve_all(c, o, ns, Bc, c->Lf, nullptr);
+  CK(cudaMemsetAsync(dg, 0, sizeof(double) * 2 * T, c->stream));
+  for (int f = 0; f < nf; ++f) {
+    const double k0 = k0_of(c->freqs[f]);
+    mwk::grad_tet(c->d_tet_edge, c->d_KM, T, c->Lf[f], c->Xf[f], ns, k0 * k0, dg, c->stream);
+  }
+  check_launch("gradient");
+  double Jd = 0;
+  CK(cudaMemcpyAsync(&Jd, dJ, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double> gh(2 * T);
+  CK(cudaMemcpyAsync(gh.data(), dg, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost, c->stream));
+  if (S_out) CK(cudaMemcpyAsync(S_out, dS, sizeof(double2) * nS, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  double J = Jd;
+  if (alpha != 0.0) {
+    double R = 0;
+    tikhonov_dev(c, c->d_eps, &R, dg);
+    std::vector<double> gr(2 * T);
+    CK(cudaMemcpyAsync(gr.data(), dg, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    J += alpha * R;
+    for (int64_t i = 0; i < 2 * T; ++i) gh[i] += alpha * gr[i];
+  }
+  *J_out = J;
+  if (grad) std::memcpy(grad, gh.data(), sizeof(double) * 2 * T);
+  for (auto p : Bs) dfree(c, p);
+  for (void* p : {(void*)dS, (void*)dSo, (void*)dSe, (void*)dC, (void*)dg, (void*)dJ}) dfree(c, p);
+}
+
+mw_status mw_gradient(mw_ctx* c, const mw_solve_opts* opts, const double* S_obs, const double* S_empty, double alpha,
+                      double* J_out, double* grad, double* S_out) {
+  return guard(c, [&] {
+    mw_solve_opts o = norm_opts(opts);
+    gradient_impl(c, o, S_obs, S_empty, alpha, J_out, grad, S_out);
+  });
+}
+
+// ---------------------------------------------------------------------------------------
+// L-BFGS, reverse communication (Sec. IV-D): mirrors the recursion stated in mw.h.
+// ---------------------------------------------------------------------------------------
+struct mw_lbfgs {
+  int64_t n = 0;
+  mw_inv_opts o{};
+  int phase = 0;            // 0: expecting f(x0); 1: line search
+  std::vector<double> x, g, d, xn;
+  double f = 0, gd = 0, t = 1;
+  int trials = 0, it = 0;
+  std::vector<std::vector<double>> S, Y;
+};
+
+static double dotv(const std::vector<double>& a, const std::vector<double>& b) {
+  double s = 0;
+  for (size_t i = 0; i < a.size(); ++i) s += a[i] * b[i];
+  return s;
+}
+
+static void lbfgs_direction(mw_lbfgs* st) {
+  const int64_t n = st->n;
+  std::vector<double>& d = st->d;
+  auto steepest = [&]() {
+    double mx = 0;
+    for (int64_t i = 0; i < n; ++i) mx = std::max(mx, std::fabs(st->g[i]));
+    mx = std::max(mx, 1e-300);
+    for (int64_t i = 0; i < n; ++i) d[i] = -st->g[i] * (st->o.first_step / mx);
+  };
+  d.assign(n, 0.0);
+  if (st->S.empty()) {
+    steepest();
+  } else {
+    std::vector<double> q = st->g;
+    const int k = (int)st->S.size();
+    std::vector<double> rho(k), al(k);
+    for (int i = k - 1; i >= 0; --i) {
+      rho[i] = 1.0 / dotv(st->Y[i], st->S[i]);
+      al[i] = rho[i] * dotv(st->S[i], q);
+      for (int64_t e = 0; e < n; ++e) q[e] -= al[i] * st->Y[i][e];
+    }
+    const double gamma = dotv(st->S[k - 1], st->Y[k - 1]) / dotv(st->Y[k - 1], st->Y[k - 1]);
+    for (int64_t e = 0; e < n; ++e) q[e] *= gamma;
+    for (int i = 0; i < k; ++i) {
+      const double b = rho[i] * dotv(st->Y[i], q);
+      for (int64_t e = 0; e < n; ++e) q[e] += (al[i] - b) * st->S[i][e];
+    }
+    for (int64_t e = 0; e < n; ++e) d[e] = -q[e];
+  }
+  st->gd = dotv(st->g, d);
+  if (!(st->gd < 0.0)) {
+    steepest();
+    st->gd = dotv(st->g, d);
+  }
+  st->t = 1.0;
+  st->trials = 0;
+}
+
+extern "C" mw_status mw_lbfgs_create(mw_lbfgs** out, int64_t n, const mw_inv_opts* opts) {
+  if (!out || n <= 0) return MW_EINVAL;
+  mw_lbfgs* st = new (std::nothrow) mw_lbfgs();
+  if (!st) return MW_ENOMEM;
+  st->n = n;
+  mw_inv_opts d{};
+  d.m = 8;
+  d.max_it = 20;
+  d.c1 = 1e-4;
+  d.max_ls = 10;
+  d.first_step = 1.0;
+  if (opts) d = *opts;
+  if (d.m <= 0) d.m = 8;
+  if (d.max_ls <= 0) d.max_ls = 10;
+  if (d.c1 <= 0) d.c1 = 1e-4;
+  if (d.first_step <= 0) d.first_step = 1.0;
+  st->o = d;
+  *out = st;
+  return MW_OK;
+}
+
+extern "C" void mw_lbfgs_destroy(mw_lbfgs* st) { delete st; }
+
+extern "C" mw_status mw_lbfgs_step(mw_lbfgs* st, double* x_io, double f, const double* g, int32_t* request) {
+  if (!st || !x_io || !g || !request) return MW_EINVAL;
+  if (!std::isfinite(f)) return MW_EINVAL;
+  const int64_t n = st->n;
+  auto propose = [&]() {
+    st->xn.resize(n);
+    for (int64_t i = 0; i < n; ++i) st->xn[i] = st->x[i] + st->t * st->d[i];
+    std::memcpy(x_io, st->xn.data(), sizeof(double) * n);
+    *request = 1;
+  };
+  auto finish = [&]() {
+    std::memcpy(x_io, st->x.data(), sizeof(double) * n);
+    *request = 0;
+  };
+  if (st->phase == 0) {
+    st->x.assign(x_io, x_io + n);
+    st->g.assign(g, g + n);
+    st->f = f;
+    st->it = 0;
+    if (st->o.max_it <= 0 || (st->o.target_J > 0 && f <= st->o.target_J)) {
+      finish();
+      return MW_OK;
+    }
+    lbfgs_direction(st);
+    st->phase = 1;
+    propose();
+    return MW_OK;
+  }
+  // line search: f, g at xn
+  st->trials++;
+  if (f <= st->f + st->o.c1 * st->t * st->gd) {
+    std::vector<double> s(n), y(n);
+    for (int64_t i = 0; i < n; ++i) {
+      s[i] = st->xn[i] - st->x[i];
+      y[i] = g[i] - st->g[i];
+    }
+    const double sy = dotv(s, y);
+    if (sy > 1e-12 * std::sqrt(dotv(s, s)) * std::sqrt(dotv(y, y))) {
+      st->S.push_back(s);
+      st->Y.push_back(y);
+      if ((int)st->S.size() > st->o.m) {
+        st->S.erase(st->S.begin());
+        st->Y.erase(st->Y.begin());
+      }
+    }
+    st->x = st->xn;
+    st->g.assign(g, g + n);
+    st->f = f;
+    st->it++;
+    if (st->it >= st->o.max_it || (st->o.target_J > 0 && f <= st->o.target_J)) {
+      finish();
+      return MW_OK;
+    }
+    lbfgs_direction(st);
+    propose();
+    return MW_OK;
+  }
+  if (st->trials >= st->o.max_ls) {
+    finish();
+    return MW_OK;
+  }
+  st->t *= 0.5;
+  propose();
+  return MW_OK;
+}
+
+extern "C" mw_status mw_invert(mw_ctx* c, const mw_inv_opts* opts, const mw_solve_opts* sopts, const double* S_obs,
+                               const double* S_empty, double* eps_io, mw_inv_history* hist) {
+  return guard(c, [&] {
+    require(c->has_mesh && c->n_freq > 0 && c->n_src > 0, MW_ESTATE, "assemble and set sources first");
+    require(opts && S_obs && S_empty && eps_io, MW_EINVAL, "bad invert arguments");
+    mw_solve_opts so = norm_opts(sopts);
+    const int64_t T = c->topo.n_tet;
+    mw_lbfgs* st = nullptr;
+    if (mw_lbfgs_create(&st, 2 * T, opts) != MW_OK) throw Fail{MW_ENOMEM, "lbfgs state"};
+    std::unique_ptr<mw_lbfgs, void (*)(mw_lbfgs*)> hold(st, mw_lbfgs_destroy);
+    std::vector<double> x(eps_io, eps_io + 2 * T), g(2 * T);
+    std::vector<double> freqs = c->freqs;
+    const double ebg[2] = {c->eps_bg[0], c->eps_bg[1]};
+    int32_t req = 1;
+    int evals = 0, accepted = 0;
+    cudaEvent_t e0;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventRecord(e0, c->stream));
+    auto elapsed = [&]() {
+      CK(cudaEventRecord(c->ev1, c->stream));
+      CK(cudaEventSynchronize(c->ev1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, c->ev1));
+      return ms * 1e-3;
+    };
+    int last_it = -1;
+    while (req) {
+      mw_status a = mw_assemble(c, c->n_freq, freqs.data(), x.data(), ebg);
+      if (a != MW_OK) throw Fail{a, c->err};
+      double J = 0;
+      gradient_impl(c, so, S_obs, S_empty, opts->alpha, &J, g.data(), nullptr);
+      ++evals;
+      if (st->phase == 0 || st->it != last_it) {
+        // first evaluation is the start point; accepted iterates are recorded below
+      }
+      const int it_before = st->it;
+      const int phase_before = st->phase;
+      mw_status s = mw_lbfgs_step(st, x.data(), J, g.data(), &req);
+      if (s != MW_OK) throw Fail{s, "lbfgs step"};
+      if (phase_before == 0) {
+        if (hist && hist->J) hist->J[0] = J;
+        if (hist && hist->seconds) hist->seconds[0] = elapsed();
+      } else if (st->it != it_before) {
+        ++accepted;
+        if (hist && hist->J) hist->J[accepted] = J;
+        if (hist && hist->seconds) hist->seconds[accepted] = elapsed();
+      }
+      last_it = st->it;
+    }
+    cudaEventDestroy(e0);
+    std::memcpy(eps_io, x.data(), sizeof(double) * 2 * T);
+    mw_status a = mw_assemble(c, c->n_freq, freqs.data(), x.data(), ebg);
+    if (a != MW_OK) throw Fail{a, c->err};
+    if (hist) {
+      hist->iterations = accepted;
+      hist->evaluations = evals;
+    }
+  });
+}
+
+}  // extern "C"

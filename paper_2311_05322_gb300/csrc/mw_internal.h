@@ -1,0 +1,151 @@
+// Internal declarations of libmw: context, host topology, device buffers and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mw.h"
+
+namespace mw {
+
+// Physical constants (SI).  Time convention e^{i omega t}.
+constexpr double kC0 = 299792458.0;
+constexpr double kMu0 = 4.0e-7 * 3.14159265358979323846;
+constexpr double kPi = 3.14159265358979323846;
+
+// Packed index of the symmetric 6x6 element matrix entry (m <= n): row-major upper triangle.
+__host__ __device__ inline int packed6(int m, int n) {
+  if (m > n) { int t = m; m = n; n = t; }
+  return m * 6 - (m * (m - 1)) / 2 + (n - m);
+}
+// Packed index of the symmetric 3x3 face matrix entry.
+__host__ __device__ inline int packed3(int m, int n) {
+  if (m > n) { int t = m; m = n; n = t; }
+  return m * 3 - (m * (m - 1)) / 2 + (n - m);
+}
+
+struct Error {
+  mw_status code;
+  std::string msg;
+};
+
+// ------------------------------------------------------------------------------------
+// Host topology (canonical rules of the public header)
+// ------------------------------------------------------------------------------------
+struct Topology {
+  int64_t n_vert = 0, n_tet = 0, n_edge = 0, n_face = 0, n_bface = 0, nnz = 0;
+  std::vector<int32_t> tets;        // [T][4]
+  std::vector<int32_t> edge_vert;   // [E][2]
+  std::vector<int32_t> tet_edge;    // [T][6]
+  std::vector<int8_t> tet_sign;     // [T][6]
+  std::vector<int64_t> row_ptr;     // [E+1]
+  std::vector<int32_t> col_idx;     // [nnz]
+  // pull map: for each nnz position, contributions in tet order then face order;
+  // code >= 0: tet t, local (m,n) -> t*36 + m*6 + n; code < 0: -(f*9 + m*3 + n) - 1.
+  std::vector<int64_t> contrib_ptr; // [nnz+1]
+  std::vector<int32_t> contrib;     // [36 T + 9 F_b]
+  std::vector<int32_t> bface_vert;  // [F_b][3] sorted vertex ids
+  std::vector<int32_t> bface_edge;  // [F_b][3] global edges (q0q1, q0q2, q1q2)
+  std::vector<int32_t> tet_nb;      // [T][4] neighbour across the face opposite local vertex k, -1 = none
+};
+
+// Builds the topology; returns false and fills err on a bad mesh.
+bool build_topology(int64_t n_vert, int64_t n_tet, const int32_t* tet_vert, Topology& topo, Error& err);
+
+// Subdomains of the overlapping Schwarz preconditioner (host side).
+struct Subdomains {
+  int32_t n_sub = 0;
+  std::vector<int32_t> owner;        // [E]
+  std::vector<int64_t> dof_ptr;      // [n_sub+1]
+  std::vector<int32_t> dofs;         // concatenated, ascending per subdomain
+  std::vector<int64_t> own_ptr;      // [n_sub+1]
+  std::vector<int32_t> own_local;    // local row index of each owned dof (ascending)
+  std::vector<int64_t> tet_ptr;      // [n_sub+1]
+  std::vector<int32_t> tet_ids;      // overlapped tets, ascending
+  std::vector<int32_t> tet_loc;      // [sum tets][6] local dof index of each tet edge
+  std::vector<int64_t> surf_ptr;     // [n_sub+1]
+  std::vector<int32_t> surf_vert;    // [sum surf][3] sorted vertex ids of each surface face
+  std::vector<int32_t> surf_loc;     // [sum surf][3] local dofs of the face edges (q0q1, q0q2, q1q2)
+  std::vector<int32_t> surf_tet;     // [sum surf] inside tet (interface) or -1 (outer boundary)
+};
+
+bool build_subdomains(const Topology& topo, int32_t n_sub, const int32_t* tet_part, int32_t overlap,
+                      Subdomains& sd, Error& err);
+
+// ------------------------------------------------------------------------------------
+// Host L-BFGS (reverse communication)
+// ------------------------------------------------------------------------------------
+}  // namespace mw
+
+// ------------------------------------------------------------------------------------
+// Kernel launchers (k_*.cu).  All take the stream; none synchronises.
+// ------------------------------------------------------------------------------------
+namespace mwk {
+
+struct c64 { float x, y; };
+
+// K1 element geometry: Ke/Me [T][21] packed (signs applied), vol [T]; Bf [F][6] packed.
+void elem_geom(const double* xyz, const int32_t* tets, const int8_t* sign, int64_t T, double* KM,
+               double* vol, cudaStream_t s);
+void face_geom(const double* xyz, const int32_t* face_vert, int64_t F, double* Bf, cudaStream_t s);
+void tikhonov_weights(const double* xyz, const int32_t* tets, const int32_t* tet_nb, int64_t T, double* w,
+                      cudaStream_t s);
+// K2 reassembly for one frequency: A64/A32 [nnz].
+void reassemble(const int64_t* cptr, const int32_t* contrib, int64_t nnz, const double* KM, const double* Bf,
+                const double* eps, double k0sq, double zb_re, double zb_im, double2* A64, float2* A32,
+                cudaStream_t s);
+// K3 SpMM: Y = A X, [E][R] layout with leading dimension ld (>= R).
+void spmm_f64(const int64_t* rp, const int32_t* ci, const double2* A, const double2* X, double2* Y, int64_t E,
+              int R, cudaStream_t s);
+void spmm_f32(const int64_t* rp, const int32_t* ci, const float2* A, const float2* X, float2* Y, int64_t E, int R,
+              cudaStream_t s);
+// r = b - A x (FP64) and per-column partial ||r||^2 into part[nblk][R]; returns nblk used.
+int residual_f64(const int64_t* rp, const int32_t* ci, const double2* A, const double2* X, const double2* B,
+                 double2* Rv, double* part, int64_t E, int R, cudaStream_t s);
+
+// Krylov (K6-K8, K15)
+int cgs_dots_f64(const double2* V, int64_t vstride, int nvec, const double2* w, int64_t E, int R,
+                 double2* part, cudaStream_t s);
+int cgs_dots_f32(const float2* V, int64_t vstride, int nvec, const float2* w, int64_t E, int R,
+                 double2* part, cudaStream_t s);
+void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s);
+int cgs_update_f64(const double2* V, int64_t vstride, int nvec, const double2* h, double2* w, int64_t E, int R,
+                   double* npart, cudaStream_t s);
+int cgs_update_f32(const float2* V, int64_t vstride, int nvec, const double2* h, float2* w, int64_t E, int R,
+                   double* npart, cudaStream_t s);
+int colnorm2_f64(const double2* x, int64_t E, int R, double* npart, cudaStream_t s);
+// Givens step for Arnoldi column j; see k_krylov.cu for the state layout.
+void givens_step(const double2* h, const double* npart, int nparts, int j, int m, int R, double2* H,
+                 double2* cs, double2* gvec, double* target, int32_t* done, int32_t* kcol, double* scale,
+                 int32_t* active_count, cudaStream_t s);
+void scale_cols_f64(double2* v, const double* scale, int64_t E, int R, cudaStream_t s);
+void scale_cols_f32(float2* v, const double* scale, int64_t E, int R, cudaStream_t s);
+// v0 = r / ||r|| per column (with cast); norms from npart.
+void start_cycle_f64(const double2* r, const double* npart, int nparts, int R, const double* bnorm, double tol,
+                     double inner_tol, int fp64_mode, double2* v0, double* rnorm, double2* gvec, double* target,
+                     int32_t* done, int32_t* kcol, int m, cudaStream_t s);
+void start_cycle_f32(const double2* r, const double* rnorm, int64_t E, int R, float2* v0, cudaStream_t s);
+void copy_v0_f64(const double2* r, const double* rnorm, int64_t E, int R, double2* v0, cudaStream_t s);
+void solve_hessenberg(const double2* H, const double2* gvec, const int32_t* kcol, int m, int R, double2* y,
+                      cudaStream_t s);
+void update_x_f64(const double2* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x,
+                  int64_t E, int R, cudaStream_t s);
+void update_x_f32(const float2* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x,
+                  int64_t E, int R, cudaStream_t s);
+void reduce_cols(const double* part, int nparts, int R, double* out, cudaStream_t s);
+
+// layout conversions
+void cast_f64_to_f32(const double2* a, float2* b, int64_t n, cudaStream_t s);
+void cast_f32_to_f64(const float2* a, double2* b, int64_t n, cudaStream_t s);
+// [R][E] (column-major, ABI) <-> [E][R] (internal)
+void transpose_in(const double2* src, double2* dst, int64_t E, int R, cudaStream_t s);
+void transpose_out(const double2* src, double2* dst, int64_t E, int R, cudaStream_t s);
+
+// sources
+void dipole_rhs(const int32_t* edge, const int8_t* sign, int n_src, double scale_im, double2* B, int64_t E,
+                cudaStream_t s);
+
+}  // namespace mwk
