@@ -1,0 +1,400 @@
+"""Benchmark of the microwave-tomography hot path on GB300: Maxwell RHS-solves/s at rel.res 1e-8.
+
+One step = one evaluation of the regularised inversion (Sec. IV-D) on the shoulder-scale
+phantom: eps -> matrix reassembly, 32 forward dipole solves, S-matrix, cost and adjoint
+sources, 32 adjoint solves (GMRES(50) + ORAS, FP64 true relative residual <= 1e-8 per column),
+per-tet adjoint gradient and Tikhonov term.  RHS-solves per step = 2 x transmitters x frequencies.
+
+  value  device-resident: eps, S_obs, S_empty and the gradient stay in HBM (CUDA events on the
+         library's stream around K steps).
+  e2e    the public host-buffer API (mw_assemble + mw_gradient): eps and S in from pinned host
+         memory, gradient and cost back to the host, inside the timed region.
+Under torchrun each rank runs its own independent evaluation (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Maxwell RHS-solves/s at rel.res 1e-8"
+UNIT = "RHS-solves/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--cells", default="80x80x34")
+    ap.add_argument("--n-src", type=int, default=32)
+    ap.add_argument("--parts", default="16x16x7")
+    ap.add_argument("--overlap", type=int, default=1)
+    ap.add_argument("--prec", default="fp32", choices=["bf16", "fp32"])
+    ap.add_argument("--alpha", type=float, default=1e-3)
+    ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--plain-cols", type=int, default=1, help="columns timed on the plain FP64 path (0 = skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-subdomains", type=int, default=24)
+    return ap.parse_args()
+
+
+def _dims(s):
+    return tuple(int(x) for x in s.split("x"))
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------------------
+def make_workload(a):
+    from phantom import box_partition, random_tear, shoulder
+    cells = _dims(a.cells)
+    healthy = shoulder(cells, n_src=a.n_src, freqs=(1.0e9,))
+    injured = shoulder(cells, n_src=a.n_src, freqs=(1.0e9,), tear=random_tear(2001))
+    parts = _dims(a.parts)
+    part = box_partition(healthy.mesh, parts, seed=7)
+    return healthy, injured, parts, part
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), d.get("bf16_tflops"), d.get("bf16_tflops_sustained"), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle sample (baseline, not a target)
+# ---------------------------------------------------------------------------------------
+def oracle_sample(w, part, n_sub, overlap, iters_per_col, n_sample_subs, seed=0):
+    """Oracle cost of one column solve, from timed pieces of one Arnoldi step on the full
+    workload: the oracle's FP64 matvec, its ORAS subdomain solves on a random sample of
+    subdomains (scaled to all), one modified Gram-Schmidt pass at the mean Krylov depth;
+    times the Arnoldi steps per column.  Returns (seconds per column, details)."""
+    import scipy.sparse.linalg as spla
+
+    from oracle import assemble as asm
+    from oracle import oras as ooras
+    t0 = time.perf_counter()
+    sysm = asm.build_system(w.mesh.xyz, w.mesh.tets)
+    vals = asm.assemble(sysm, w.eps, w.freqs[0], w.eps_bg)
+    A = sysm.csr(vals)
+    subs, _ = ooras.build_subdomains(sysm, part, n_sub, overlap)
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(n_sub, size=min(n_sample_subs, n_sub), replace=False)
+    lus = [(subs[s], spla.splu(ooras.local_matrix(sysm, subs[s], w.eps, w.freqs[0], w.eps_bg))) for s in pick]
+    setup = time.perf_counter() - t0
+    E = sysm.topo.n_edge
+    x = rng.normal(size=E) + 1j * rng.normal(size=E)
+    t = time.perf_counter()
+    for _ in range(3):
+        y = A @ x
+    t_mv = (time.perf_counter() - t) / 3
+    z = np.zeros(E, dtype=complex)
+    t = time.perf_counter()
+    for sub, lu in lus:
+        yy = lu.solve(np.ascontiguousarray(x[sub.dofs]))
+        z[sub.dofs[sub.owned]] = yy[sub.owned]
+    t_p = (time.perf_counter() - t) * n_sub / len(lus)
+    depth = max(1, int(round(min(iters_per_col, 50) / 2)))
+    V = rng.normal(size=(depth, E)) + 0j
+    t = time.perf_counter()
+    wv = y.copy()
+    for i in range(depth):
+        h = np.vdot(V[i], wv)
+        wv = wv - h * V[i]
+    t_gs = time.perf_counter() - t
+    per_step = t_mv + t_p + t_gs
+    return per_step * iters_per_col, {"setup_s": setup, "matvec_s": t_mv, "oras_s": t_p, "gs_s": t_gs,
+                                      "timed_s": 3 * t_mv + t_p * len(lus) / n_sub + t_gs}
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+def run_mine(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2311_05322_gb300 import mw
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+
+    healthy, injured, parts, part = make_workload(a)
+    n_sub = int(np.prod(parts))
+    freqs = list(healthy.freqs)
+    eps0 = np.stack([healthy.eps.real, healthy.eps.imag], 1)
+    c = mw.Context(local, stream.cuda_stream)
+    setup = {}
+    t = time.perf_counter()
+    info = c.set_mesh(healthy.mesh.xyz, healthy.mesh.tets)
+    torch.cuda.synchronize()
+    setup["mesh_s"] = time.perf_counter() - t
+    c.set_sources(healthy.src_pos, healthy.src_dir)
+    hom = np.tile([healthy.eps_bg.real, healthy.eps_bg.imag], (healthy.mesh.n_tet, 1))
+    # preconditioner of the background medium, reused stale for every eps (as in an inversion)
+    c.assemble(freqs, hom, healthy.eps_bg)
+    prec = {"bf16": mw.MW_PREC_BF16, "fp32": mw.MW_PREC_FP32}[a.prec]
+    t = time.perf_counter()
+    c.setup_preconditioner(n_sub, part, a.overlap, prec)
+    torch.cuda.synchronize()
+    setup["preconditioner_s"] = time.perf_counter() - t
+    _, sizes = c.get_partition()
+    opts = mw.solve_opts(mode=mw.MW_MODE_MIXED, restart=50, tol=1e-8, inner_tol=a.inner_tol, max_it=2000)
+    # synthetic measurements: injured phantom (observed) and empty chamber (normalisation)
+    t = time.perf_counter()
+    S_empty, _ = c.solve(opts)
+    c.assemble(freqs, np.stack([injured.eps.real, injured.eps.imag], 1), injured.eps_bg)
+    S_obs, _ = c.solve(opts)
+    c.assemble(freqs, eps0, healthy.eps_bg)
+    setup["data_s"] = time.perf_counter() - t
+
+    dev = torch.device("cuda", local)
+    eps_d = torch.from_numpy(eps0).to(dev)
+    So_d = torch.from_numpy(S_obs).to(dev)
+    Se_d = torch.from_numpy(S_empty).to(dev)
+    g_d = torch.empty((healthy.mesh.n_tet, 2), dtype=torch.float64, device=dev)
+    units = 2 * a.n_src * len(freqs)
+
+    def step_dev():
+        c.assemble_dev(freqs, eps_d, healthy.eps_bg)
+        return c.gradient_dev(So_d, Se_d, g_d, a.alpha, opts)
+
+    for _ in range(a.warmup):
+        step_dev()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    c.profile_enable((1 << mw.MW_K_NCLASS) - 1)
+    l0 = mw.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(a.steps):
+            J = step_dev()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = mw.kernel_launches() - l0
+    prof = c.profile_read()
+    c.profile_enable(0)
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = units * a.steps * world / (ms * 1e-3)
+
+    # ---- e2e through the host-buffer API --------------------------------------------------
+    eps_h = torch.from_numpy(eps0).pin_memory().numpy()
+    So_h = torch.from_numpy(S_obs).pin_memory().numpy()
+    Se_h = torch.from_numpy(S_empty).pin_memory().numpy()
+    c.assemble(freqs, eps_h, healthy.eps_bg)
+    c.gradient(So_h, Se_h, a.alpha, opts)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t = time.perf_counter()
+    for _ in range(a.steps):
+        c.assemble(freqs, eps_h, healthy.eps_bg)
+        Jh, gh = c.gradient(So_h, Se_h, a.alpha, opts)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    T = healthy.mesh.n_tet
+    h2d = eps0.nbytes + S_obs.nbytes + S_empty.nbytes
+    d2h = 16 * T + 8
+
+    # ---- plain FP64 path (FP64 everything, one RHS per Krylov launch) ---------------------
+    plain = None
+    if a.plain_cols > 0 and rank == 0:
+        try:
+            c.assemble(freqs, hom, healthy.eps_bg)
+            t = time.perf_counter()
+            c.setup_preconditioner(n_sub, part, a.overlap, mw.MW_PREC_FP64_FROM_FP32)
+            torch.cuda.synchronize()
+            ps = time.perf_counter() - t
+            c.assemble(freqs, eps0, healthy.eps_bg)
+            E = info.n_edge
+            rhs = np.zeros((a.plain_cols, E), dtype=np.complex128)
+            for j in range(a.plain_cols):
+                b = np.zeros(E, dtype=np.complex128)
+                b[c.src_edges[j]] = -1j * 2 * np.pi * freqs[0] * 4e-7 * np.pi * c.src_signs[j]
+                rhs[j] = b
+            b_d = torch.from_numpy(rhs).to(dev)
+            x_d = torch.empty_like(b_d)
+            po = mw.solve_opts(mode=mw.MW_MODE_FP64, restart=50, batch=1, tol=1e-8, max_it=2000)
+            st = c.solve_rhs(a.plain_cols, b_d, x_d, po)
+            plain = {"value": a.plain_cols / (st["solve_ms"] * 1e-3), "unit": UNIT, "cols": a.plain_cols,
+                     "solve_ms": st["solve_ms"], "arnoldi_steps": st["arnoldi_steps"],
+                     "max_relres": st["max_relres"], "preconditioner_setup_s": ps,
+                     "note": "FP64 operator, FP64 Krylov basis, FP64 apply of FP32-factorised subdomain inverses, "
+                             "one column per launch"}
+        except Exception as e:  # report, do not hide
+            plain = {"error": str(e)}
+
+    # ---- roofline of the dominant kernel class ---------------------------------------------
+    hbm, bf16, bf16s, src = peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_source": src, "traffic": None,
+            "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
+            "avg_launch_ms": d["ms"] / max(d["launches"], 1),
+            "share_of_step": d["ms"] / ms,
+            "classes": {k: {"ms": v["ms"], "launches": v["launches"],
+                            "GBs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0}
+                        for k, v in prof.items()}}
+
+    # ---- CPU oracle sample -------------------------------------------------------------------
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        its = max(1.0, prof["cgs_dots"]["launches"] / max(1, a.steps * 2 * len(freqs)))
+        col_s, det = oracle_sample(healthy, part, n_sub, a.overlap, its, a.cpu_sample_subdomains)
+        cpu = {"value": 1.0 / col_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"oracle (numpy/scipy FP64) one Arnoldi step of one column on the full workload: "
+                          f"FP64 matvec, ORAS sparse-LU solves on {a.cpu_sample_subdomains} random subdomains "
+                          f"scaled to {n_sub}, MGS at depth {int(round(min(its, 50) / 2))}; "
+                          f"x {its:.1f} Arnoldi steps per column (the GPU solve's count)"),
+               "details": det}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64+bf16 inner / c128 outer" if prec == mw.MW_PREC_BF16 else "c64 inner / c128 outer",
+            "data": "synthetic",
+            "config": {"workload": f"shoulder phantom {a.cells} Kuhn cells ({info.n_edge} edges, {info.n_tet} tets), "
+                                   f"{a.n_src} z-dipoles, 1 GHz, one inversion evaluation (forward+adjoint)",
+                       "edges": info.n_edge, "nnz": info.nnz, "transmitters": a.n_src, "freqs_hz": freqs,
+                       "rhs_solves_per_step": units, "subdomains": n_sub, "overlap": a.overlap,
+                       "n_s_mean": float(sizes.mean()), "n_s_max": int(sizes.max()),
+                       "solver": "GMRES-IR: FP64 outer residual, FGMRES(50) inner FP32 + ORAS",
+                       "preconditioner_apply": {2: "bf16 tcgen05", 1: "fp32 cuda-core"}.get(prec, str(prec)),
+                       "tol": 1e-8, "inner_tol": a.inner_tol, "alpha": a.alpha,
+                       "l2": "inputs larger than L2 (subdomain inverses and Krylov basis are GBs)"},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": units * a.steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches), "clocks": clk.summary(), "setup_s": setup, "plain_fp64": plain,
+            "J_last": J,
+        }
+        print(json.dumps(line), flush=True)
+    c.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------------------
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    healthy, injured, parts, part = make_workload(a)
+    n_sub = int(np.prod(parts))
+    # the oracle's own GMRES+ORAS would need minutes per column at this size; the step is the
+    # same bounded per-column sample as the GPU arm's cpu_baseline, with 30 Arnoldi steps per
+    # column (the order the oracle's own GMRES needs on this lossy problem)
+    its = 30.0
+    vals = []
+    det = None
+    for k in range(a.warmup + a.steps):
+        col_s, det = oracle_sample(healthy, part, n_sub, a.overlap, its, a.cpu_sample_subdomains, seed=k)
+        if k >= a.warmup:
+            vals.append(1.0 / col_s)
+    v = statistics.mean(vals)
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+                      "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "data": "synthetic",
+                      "config": {"workload": f"shoulder phantom {a.cells}", "subdomains": n_sub},
+                      "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": UNIT,
+                                       "sample": "per-column oracle estimate from one sampled Arnoldi step x 30"},
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mine(args)

@@ -202,6 +202,36 @@ mw_status mw_invert(mw_ctx* ctx, const mw_inv_opts* opts, const mw_solve_opts* s
                     const double* S_obs, const double* S_empty, double* eps_inout,
                     mw_inv_history* hist);
 
+/* ---- device-resident variants (same operations, device pointers) ------------------- */
+/* mw_assemble with eps_r on the device ([n_tet][2] doubles); needs a prior mw_assemble with the
+ * same number of frequencies (which sized the matrices). */
+mw_status mw_assemble_dev(mw_ctx* ctx, int32_t n_freq, const double* freq_hz, const void* eps_dev,
+                          const double* eps_bg);
+/* mw_gradient with S_obs / S_empty on the device and the gradient [n_tet][2] written to the
+ * device; the cost J is returned to the host. */
+mw_status mw_gradient_dev(mw_ctx* ctx, const mw_solve_opts* opts, const void* S_obs_dev,
+                          const void* S_empty_dev, double alpha, double* J_out, void* grad_dev);
+
+/* ---- diagnostics ------------------------------------------------------------------- */
+/* Kernel launches issued by this library in the process so far. */
+int64_t mw_kernel_launches(void);
+/* Kernel classes timed by the optional event profiler. */
+enum {
+  MW_K_SPMM = 0,        /* Arnoldi SpMM (K3) */
+  MW_K_ORAS = 1,        /* ORAS apply (K4) */
+  MW_K_CGS_DOTS = 2,    /* Gram-Schmidt dot products and their reduction (K6) */
+  MW_K_CGS_UPDATE = 3,  /* Gram-Schmidt update and norm (K6) */
+  MW_K_RESIDUAL = 4,    /* FP64 residual b - A x (K8) */
+  MW_K_NCLASS = 5
+};
+/* Record CUDA events around the launches of the classes in mask (bit k = class k); 0 = off.
+ * Events cost a few microseconds each. */
+mw_status mw_profile_enable(mw_ctx* ctx, uint32_t class_mask);
+/* Per class since enable: summed durations (ms), launch count and algorithmic bytes (the
+ * bytes each launch must move at minimum: operands read once, results written once; bytes may
+ * be NULL); resets the counters. */
+mw_status mw_profile_read(mw_ctx* ctx, double* ms, int64_t* launches, double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -164,19 +164,23 @@ __global__ void count_active_kernel(const int32_t* done, int R, int32_t* active)
 }  // namespace
 
 void s_extract(const double2* X, const int32_t* edge, const int8_t* sign, int ns, double2* S, cudaStream_t s) {
+  note_launch(1);
   s_extract_kernel<<<(ns * ns + 255) / 256, 256, 0, s>>>(X, edge, sign, ns, S);
 }
 void adjoint_weights(const double2* S, const double2* So, const double2* Se, int64_t n, double2* C, double* J,
                      cudaStream_t s) {
+  note_launch(1);
   adjoint_weights_kernel<<<1, 256, 0, s>>>(S, So, Se, n, C, J);
 }
 void adjoint_rhs(const int32_t* edge, const int8_t* sign, int ns, const double2* C, double2* B, int64_t E,
                  cudaStream_t s) {
+  note_launch(1);
   cudaMemsetAsync(B, 0, sizeof(double2) * E * ns, s);
   adjoint_rhs_kernel<<<(ns + 63) / 64, 64, 0, s>>>(edge, sign, ns, C, B);
 }
 void grad_tet(const int32_t* tet_edge, const double* KM, int64_t T, const double2* L, const double2* X, int ns,
               double k0sq, double* g, cudaStream_t s) {
+  note_launch(1);
   const int64_t threads = T * 32;
   const int blocks = (int)((threads + 255) / 256);
   if (ns <= 32)
@@ -188,12 +192,35 @@ void grad_tet(const int32_t* tet_edge, const double* KM, int64_t T, const double
 }
 void tikhonov(const int32_t* tet_nb, const double* w, const double* eps, int64_t T, double* grad, double* red,
               cudaStream_t s) {
+  note_launch(2);
   tikhonov_kernel<<<kTikBlocks, 256, 0, s>>>(tet_nb, w, eps, T, grad, red);
   final_sum_kernel<<<1, 256, 0, s>>>(red, kTikBlocks);
 }
-void sqrt_inplace(double* x, int n, cudaStream_t s) { sqrt_kernel<<<(n + 127) / 128, 128, 0, s>>>(x, n); }
+void sqrt_inplace(double* x, int n, cudaStream_t s) {
+  note_launch(1);
+  sqrt_kernel<<<(n + 127) / 128, 128, 0, s>>>(x, n); }
 void count_active(const int32_t* done, int R, int32_t* active, cudaStream_t s) {
+  note_launch(1);
   count_active_kernel<<<(R + 127) / 128, 128, 0, s>>>(done, R, active);
 }
 
+}  // namespace mwk
+
+namespace mwk {
+namespace {
+__global__ void axpy_kernel(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+__global__ void add_scaled_scalar_kernel(double* J, double a, const double* r) { *J += a * r[0]; }
+}  // namespace
+void axpy_f64(double a, const double* x, double* y, int64_t n, cudaStream_t s) {
+  note_launch(1);
+  int64_t b = (n + 255) / 256;
+  axpy_kernel<<<(int)(b < 1216 ? b : 1216), 256, 0, s>>>(a, x, y, n);
+}
+void add_scaled_scalar(double* J, double a, const double* r, cudaStream_t s) {
+  note_launch(1);
+  add_scaled_scalar_kernel<<<1, 1, 0, s>>>(J, a, r);
+}
 }  // namespace mwk

@@ -15,4 +15,6 @@ void tikhonov(const int32_t* tet_nb, const double* w, const double* eps, int64_t
               cudaStream_t s);
 void sqrt_inplace(double* x, int n, cudaStream_t s);
 void count_active(const int32_t* done, int R, int32_t* active, cudaStream_t s);
+void axpy_f64(double a, const double* x, double* y, int64_t n, cudaStream_t s);
+void add_scaled_scalar(double* J, double a, const double* r, cudaStream_t s);
 }  // namespace mwk

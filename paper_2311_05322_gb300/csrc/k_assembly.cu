@@ -217,38 +217,47 @@ inline int grid_stride_blocks(int64_t n) {
 
 void elem_geom(const double* xyz, const int32_t* tets, const int8_t* sign, int64_t T, double* KM, double* vol,
                cudaStream_t s) {
+  note_launch(1);
   elem_geom_kernel<<<blocks_for(T, kGeomThreads), kGeomThreads, 0, s>>>(xyz, tets, sign, T, KM, vol);
 }
 void face_geom(const double* xyz, const int32_t* fv, int64_t F, double* Bf, cudaStream_t s) {
+  if (F > 0) note_launch(1);
   if (F > 0) face_geom_kernel<<<blocks_for(F, 128), 128, 0, s>>>(xyz, fv, F, Bf);
 }
 void tikhonov_weights(const double* xyz, const int32_t* tets, const int32_t* nb, int64_t T, double* w,
                       cudaStream_t s) {
+  note_launch(1);
   tikhonov_weights_kernel<<<blocks_for(T, 128), 128, 0, s>>>(xyz, tets, nb, T, w);
 }
 void reassemble(const int64_t* cptr, const int32_t* contrib, int64_t nnz, const double* KM, const double* Bf,
                 const double* eps, double k0sq, double zb_re, double zb_im, double2* A64, float2* A32,
                 cudaStream_t s) {
+  note_launch(1);
   reassemble_kernel<<<blocks_for(nnz, 256), 256, 0, s>>>(cptr, contrib, nnz, KM, Bf, eps, k0sq, zb_re, zb_im, A64,
                                                           A32);
 }
 void dipole_rhs(const int32_t* edge, const int8_t* sign, int n_src, double s_im, double2* B, int64_t E,
                 cudaStream_t s) {
+  note_launch(1);
   cudaMemsetAsync(B, 0, sizeof(double2) * E * n_src, s);
   dipole_rhs_kernel<<<blocks_for(n_src, 64), 64, 0, s>>>(edge, sign, n_src, s_im, B);
 }
 void cast_f64_to_f32(const double2* a, float2* b, int64_t n, cudaStream_t s) {
+  note_launch(1);
   cast64to32_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(a, b, n);
 }
 void cast_f32_to_f64(const float2* a, double2* b, int64_t n, cudaStream_t s) {
+  note_launch(1);
   cast32to64_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(a, b, n);
 }
 void transpose_in(const double2* src, double2* dst, int64_t E, int R, cudaStream_t s) {
+  note_launch(1);
   // src [R][E] -> dst [E][R]
   const int64_t tiles = ((R + 31) / 32) * ((E + 31) / 32);
   transpose_kernel<<<(unsigned)tiles, dim3(32, 8), 0, s>>>(src, dst, R, E);
 }
 void transpose_out(const double2* src, double2* dst, int64_t E, int R, cudaStream_t s) {
+  note_launch(1);
   // src [E][R] -> dst [R][E]
   const int64_t tiles = ((R + 31) / 32) * ((E + 31) / 32);
   transpose_kernel<<<(unsigned)tiles, dim3(32, 8), 0, s>>>(src, dst, E, R);

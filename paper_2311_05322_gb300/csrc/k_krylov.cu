@@ -426,6 +426,7 @@ inline int gs_blocks(int64_t n) {
 
 template <typename T>
 int dots_launch(const T* V, int64_t vstride, int nvec, const T* w, int64_t E, int R, double2* part, cudaStream_t s) {
+  note_launch(1);
   Shape sh = shape_for(R);
   const int S = nvec >= kWarps ? 1 : kWarps / nvec;
   switch (sh.cpl) {
@@ -445,6 +446,7 @@ int dots_launch(const T* V, int64_t vstride, int nvec, const T* w, int64_t E, in
 template <typename T>
 int update_launch(const T* V, int64_t vstride, int nvec, const double2* h, T* w, int64_t E, int R, double* npart,
                   cudaStream_t s) {
+  note_launch(1);
   Shape sh = shape_for(R);
   const size_t smem = sizeof(T) * nvec * R + 16 + sizeof(double) * kThreads * sh.cpl;
   static bool attr = false;
@@ -480,6 +482,7 @@ int cgs_dots_f32(const float2* V, int64_t vstride, int nvec, const float2* w, in
   return dots_launch<float2>(V, vstride, nvec, w, E, R, part, s);
 }
 void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s) {
+  note_launch(1);
   const int n = nvec * R;
   reduce_h_kernel<<<(n + 127) / 128, 128, 0, s>>>(part, nparts, nvec, R, h);
 }
@@ -492,6 +495,7 @@ int cgs_update_f32(const float2* V, int64_t vstride, int nvec, const double2* h,
   return update_launch<float2>(V, vstride, nvec, h, w, E, R, npart, s);
 }
 int colnorm2_f64(const double2* x, int64_t E, int R, double* npart, cudaStream_t s) {
+  note_launch(1);
   Shape sh = shape_for(R);
   switch (sh.cpl) {
     case 1:
@@ -507,44 +511,54 @@ int colnorm2_f64(const double2* x, int64_t E, int R, double* npart, cudaStream_t
   return kBlocks;
 }
 void reduce_cols(const double* part, int nparts, int R, double* out, cudaStream_t s) {
+  note_launch(1);
   reduce_cols_kernel<<<(R + 127) / 128, 128, 0, s>>>(part, nparts, R, out);
 }
 void givens_step(const double2* h, const double* npart, int nparts, int j, int m, int R, double2* H, double2* cs,
                  double2* gvec, double* target, int32_t* done, int32_t* kcol, double* scale, int32_t* active_count,
                  cudaStream_t s) {
+  note_launch(1);
   givens_kernel<<<(R + 127) / 128, 128, 0, s>>>(h, npart, nparts, j, m, R, H, cs, gvec, target, done, kcol, scale,
                                                  active_count);
 }
 void scale_cols_f64(double2* v, const double* scale, int64_t E, int R, cudaStream_t s) {
+  note_launch(1);
   scale_cols_kernel<double2><<<gs_blocks(E * R), 256, 0, s>>>(v, scale, E, R);
 }
 void scale_cols_f32(float2* v, const double* scale, int64_t E, int R, cudaStream_t s) {
+  note_launch(1);
   scale_cols_kernel<float2><<<gs_blocks(E * R), 256, 0, s>>>(v, scale, E, R);
 }
 void start_state(const double* npart, int nparts, int R, const double* bnorm, double tol, double inner_tol,
                  int fp64_mode, double* rnorm, double2* gvec, double* target, int32_t* done, int32_t* kcol, int m,
                  cudaStream_t s) {
+  note_launch(1);
   start_state_kernel<<<(R + 127) / 128, 128, 0, s>>>(npart, nparts, R, bnorm, tol, inner_tol, fp64_mode, rnorm, gvec,
                                                       target, done, kcol, m);
 }
 void normalize_start_f64(const double2* r, const double* rnorm, const int32_t* done, int64_t E, int R, double2* v0,
                          cudaStream_t s) {
+  note_launch(1);
   normalize_start_kernel<double2><<<gs_blocks(E * R), 256, 0, s>>>(r, rnorm, done, E, R, v0);
 }
 void normalize_start_f32(const double2* r, const double* rnorm, const int32_t* done, int64_t E, int R, float2* v0,
                          cudaStream_t s) {
+  note_launch(1);
   normalize_start_kernel<float2><<<gs_blocks(E * R), 256, 0, s>>>(r, rnorm, done, E, R, v0);
 }
 void solve_hessenberg(const double2* H, const double2* gvec, const int32_t* kcol, int m, int R, double2* y,
                       cudaStream_t s) {
+  note_launch(1);
   hessenberg_solve_kernel<<<(R + 127) / 128, 128, 0, s>>>(H, gvec, kcol, m, R, y);
 }
 void update_x_f64(const double2* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x,
                   int64_t E, int R, cudaStream_t s) {
+  note_launch(1);
   update_x_kernel<double2><<<gs_blocks(E * R), 256, 0, s>>>(Z, zstride, y, kcol, m, x, E, R);
 }
 void update_x_f32(const float2* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x,
                   int64_t E, int R, cudaStream_t s) {
+  note_launch(1);
   update_x_kernel<float2><<<gs_blocks(E * R), 256, 0, s>>>(Z, zstride, y, kcol, m, x, E, R);
 }
 

@@ -393,6 +393,7 @@ void gj_all(const OrasBatch& bt, T* ws, T* dinv, int32_t* status, cudaStream_t s
     attr_set = true;
   }
   for (int64_t kb = 0; kb < nmax; kb += NB) {
+    note_launch(4);
     gj_diag_kernel<T><<<nb, 256, 0, st>>>(bt.d_n, bt.d_off, ws, kb, dinv, status);
     dim3 g1((unsigned)((nmax + 255) / 256), nb);
     gj_rowpanel_kernel<T><<<g1, 256, 0, st>>>(bt.d_n, bt.d_off, ws, kb, dinv);
@@ -406,6 +407,7 @@ void gj_all(const OrasBatch& bt, T* ws, T* dinv, int32_t* status, cudaStream_t s
 
 void oras_local_assemble(const OrasBatch& bt, const OrasTopo& tp, const double* Bsurf, const double* KM,
                          const double* eps, double k0, double ebr, double ebi, int prec, void* ws, cudaStream_t s) {
+  note_launch(1);
   if (prec == 0)
     local_assemble_kernel<double2><<<bt.count, 32, 0, s>>>(bt.d_sub, tp.dof_ptr, tp.tet_ptr, tp.tet_ids, tp.tet_loc,
                                                             tp.surf_ptr, tp.surf_loc, tp.surf_tet, Bsurf, KM, eps, k0,
@@ -425,6 +427,7 @@ void oras_invert(const OrasBatch& bt, int prec, void* ws, void* dinv, int32_t* s
 
 void oras_extract(const OrasBatch& bt, const OrasTopo& tp, int ws_prec, const void* ws, int w_prec,
                   const int64_t* w_off, void* W, cudaStream_t s) {
+  note_launch(1);
   dim3 g(256, bt.count);
   if (ws_prec == 0 && w_prec == 0)
     extract_owned_kernel<double2, double2><<<g, 256, 0, s>>>(bt.d_n, bt.d_off, (const double2*)ws, bt.d_sub,
@@ -442,6 +445,7 @@ void oras_extract(const OrasBatch& bt, const OrasTopo& tp, int ws_prec, const vo
 
 void oras_apply_cc(const OrasTopo& tp, int n_tiles, const int32_t* tile_sub, const int32_t* tile_row0, int prec,
                    const int64_t* w_off, const void* W, const void* r, void* z, int R, cudaStream_t s) {
+  note_launch(1);
   if (prec == 0) {
     if (R <= 8)
       oras_apply_kernel<double2, 8><<<n_tiles, 256, 0, s>>>(tile_sub, tile_row0, tp.dof_ptr, tp.dofs, tp.own_ptr,

@@ -1,15 +1,448 @@
-// BF16 tensor-core ORAS apply: implemented in a later step.
-#include "k_oras_tc.h"
+// K4 on the tensor cores: z[own_s] = W_s r[dofs_s] for every subdomain s, as BF16 x BF16 -> FP32
+// tcgen05 MMAs with the accumulator in tensor memory (Sec. IV-C: the subdomain solves of the
+// one-level ORAS preconditioner, applied through precomputed owned-row inverses).
+//
+// Complex product as one real GEMM.  With W = Wr + i Wi stored interleaved along K
+// (A'[m][2k] = Wr[m][k], A'[m][2k+1] = Wi[m][k]) and the gathered input g = gr + i gi written as
+//   B'[2k][2r] = gr,  B'[2k+1][2r] = -gi,  B'[2k][2r+1] = gi,  B'[2k+1][2r+1] = gr,
+// D = A' B' holds Re z in column 2r and Im z in column 2r+1: the interleaved complex output.
+//
+// Layouts.  Both operands are K-major with the 128-byte swizzle: a tile row holds 64 BF16 of K
+// (128 B); the 16-byte chunk c of row r sits at chunk c ^ (r % 8); 8-row groups are 1024 B
+// apart.  W_s is pre-tiled at setup into 128-row x 64-K tiles (16 KB each, contiguous, in that
+// swizzled order), so one bulk copy moves a tile into shared memory without a tensor map.  The
+// gathered operand of each subdomain is written per apply into N x 64-K tiles (N = 2 R_pad).
+//
+// Kernel roles (192 threads): warp 0 lane 0 issues the bulk copies, warp 1 allocates tensor
+// memory and lane 0 issues the MMAs, warps 2-5 read the accumulator (tcgen05.ld) and scatter
+// the owned rows.  Every mbarrier wait is bounded; on timeout the kernel records an error code,
+// drains its outstanding copies (again bounded), frees tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <vector>
+
 #include "k_oras.h"
+#include "k_oras_tc.h"
 #include "mw_internal.h"
 
 namespace mwk {
-bool tc_plan_build(TcPlan&, const mw::Subdomains&, const std::function<void*(size_t)>&, cudaStream_t) {
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kTileKc = 32;                  // complex K per tile (64 real)
+constexpr int kATileBytes = kTileM * 128;    // 16 KB
+constexpr int kThreadsTc = 192;
+constexpr long long kSpinLimit = 1ll << 26;  // bounded waits (~ seconds with backoff)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 64) __nanosleep(32);
+  }
   return false;
 }
-void tc_plan_free(TcPlan& p, const std::function<void(void*)>&) { p = TcPlan(); }
-size_t tc_w_bytes(const TcPlan&) { return 16; }
-size_t tc_scratch_bytes(const TcPlan&, int) { return 16; }
-void tc_extract(const TcPlan&, const OrasBatch&, const OrasTopo&, int, const void*, void*, cudaStream_t) {}
-void oras_apply_tc(const TcPlan&, const OrasTopo&, const void*, const float2*, float2*, int, void*, cudaStream_t) {}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M = 128, N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of (row, k) in a K-major, 128-byte-swizzled tile with 64 BF16 per row.
+__host__ __device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t k) {
+  return row * 128u + ((((k >> 3) ^ (row & 7u)) & 7u) << 4) + ((k & 7u) << 1);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// ---------------------------------------------------------------------------------------
+// Setup: owned rows of B_s^{-1} (FP32 or FP64 workspace) -> swizzled BF16 tiles.
+// One block per (subdomain of the batch, m tile, k tile); one 32-bit word (re, im) per entry.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void pack_w_kernel(const int64_t* __restrict__ nmat, const int64_t* __restrict__ off,
+                              const T* __restrict__ ws, const int32_t* __restrict__ sub_ids,
+                              const int64_t* __restrict__ own_ptr, const int32_t* __restrict__ own_local,
+                              const int64_t* __restrict__ sub_wtile, const int32_t* __restrict__ sub_kt,
+                              uint8_t* __restrict__ W) {
+  const int b = blockIdx.z;
+  const int s = sub_ids[b];
+  const int64_t n = nmat[b];
+  const int64_t nown = own_ptr[s + 1] - own_ptr[s];
+  const int mt = blockIdx.y, kt = blockIdx.x;
+  const int KT = sub_kt[s];
+  if (kt >= KT || (int64_t)mt * kTileM >= nown) return;
+  const T* A = ws + off[b];
+  uint8_t* tile = W + ((size_t)sub_wtile[s] + (size_t)mt * KT + kt) * kATileBytes;
+  for (int w = threadIdx.x; w < kTileM * kTileKc; w += blockDim.x) {
+    const int r = w / kTileKc, kc = w % kTileKc;
+    const int64_t q = (int64_t)mt * kTileM + r, k = (int64_t)kt * kTileKc + kc;
+    float re = 0.f, im = 0.f;
+    if (q < nown && k < n) {
+      const T v = A[(int64_t)own_local[own_ptr[s] + q] * n + k];
+      re = (float)v.x;
+      im = (float)v.y;
+    }
+    *reinterpret_cast<uint32_t*>(tile + swz(r, 2 * kc)) = pack_bf16(re, im);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Apply, step 1: gathered operand tiles B' for every (subdomain, k tile).
+// ---------------------------------------------------------------------------------------
+__global__ void gather_b_kernel(const int32_t* __restrict__ gt_sub, const int32_t* __restrict__ gt_kt,
+                                const int64_t* __restrict__ dof_ptr, const int32_t* __restrict__ dofs,
+                                const float2* __restrict__ r, int R, int Rp, uint8_t* __restrict__ Bt) {
+  const int64_t g = blockIdx.x;
+  const int s = gt_sub[g], kt = gt_kt[g];
+  const int64_t n = dof_ptr[s + 1] - dof_ptr[s];
+  const int N = 2 * Rp;
+  uint8_t* tile = Bt + (size_t)g * N * 128;
+  const int32_t* dv = dofs + dof_ptr[s];
+  for (int idx = threadIdx.x; idx < kTileKc * Rp; idx += blockDim.x) {
+    const int kc = idx / Rp, c = idx % Rp;
+    const int64_t k = (int64_t)kt * kTileKc + kc;
+    float2 v = make_float2(0.f, 0.f);
+    if (k < n && c < R) v = r[(int64_t)dv[k] * R + c];
+    const uint32_t n0 = 2 * c, n1 = 2 * c + 1;
+    *reinterpret_cast<uint32_t*>(tile + swz(n0, 2 * kc)) = pack_bf16(v.x, -v.y);
+    *reinterpret_cast<uint32_t*>(tile + swz(n1, 2 * kc)) = pack_bf16(v.y, v.x);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Apply, step 2: one CTA per 128-row output tile of one subdomain.
+// ---------------------------------------------------------------------------------------
+struct TcArgs {
+  const int32_t* mt_sub;
+  const int32_t* mt_row0;
+  const int64_t* sub_wtile;
+  const int64_t* sub_gtile;
+  const int32_t* sub_kt;
+  const int64_t* own_ptr;
+  const int32_t* own_glob;
+  const uint8_t* W;
+  const uint8_t* Bt;
+  float2* z;
+  int R, N, stages;
+  uint32_t tmem_cols;
+  int32_t* err;
+};
+
+__global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) {
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t full_bar[8];
+  __shared__ __align__(8) uint64_t empty_bar[8];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x;
+  const int s = a.mt_sub[t];
+  const int row0 = a.mt_row0[t];
+  const int KT = a.sub_kt[s];
+  const int S = a.stages;
+  const uint32_t b_bytes = (uint32_t)a.N * 128u;
+  const uint32_t stage_bytes = kATileBytes + b_bytes;
+  const uint8_t* Wt = a.W + ((size_t)a.sub_wtile[s] + (size_t)(row0 / kTileM) * KT) * kATileBytes;
+  const uint8_t* Bs = a.Bt + (size_t)a.sub_gtile[s] * b_bytes;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&empty_bar[i], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: bulk copies of (W tile, B' tile) per k tile
+      int issued = 0;
+      for (int kt = 0; kt < KT; ++kt) {
+        const int st = kt % S;
+        if (kt >= S) {
+          if (!mbar_wait(&empty_bar[st], ((kt / S) + 1) & 1)) {
+            atomicCAS(a.err, 0, 1);
+            abort_flag = 1;
+            break;
+          }
+        }
+        if (*(volatile int*)&abort_flag) break;
+        uint8_t* sa = base + (size_t)st * stage_bytes;
+        uint8_t* sb = sa + kATileBytes;
+        mbar_expect_tx(&full_bar[st], stage_bytes);
+        bulk_g2s(sa, Wt + (size_t)kt * kATileBytes, kATileBytes, &full_bar[st]);
+        bulk_g2s(sb, Bs + (size_t)kt * b_bytes, b_bytes, &full_bar[st]);
+        ++issued;
+      }
+      // drain: every issued copy has completed before this thread leaves
+      for (int kt = (issued > S ? issued - S : 0); kt < issued; ++kt) {
+        if (!mbar_wait(&full_bar[kt % S], (kt / S) & 1)) atomicCAS(a.err, 0, 2);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(a.N);
+      for (int kt = 0; kt < KT; ++kt) {
+        const int st = kt % S;
+        if (!mbar_wait(&full_bar[st], (kt / S) & 1)) {
+          atomicCAS(a.err, 0, 3);
+          abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = smem_u32(base + (size_t)st * stage_bytes);
+        const uint32_t sb = sa + kATileBytes;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_bf16(tmem, smem_desc(sa + 32u * k), smem_desc(sb + 32u * k), idesc, (kt > 0 || k > 0) ? 1u : 0u);
+        mma_commit(&empty_bar[st]);
+      }
+      mma_commit(&done_bar);
+    }
+  } else {
+    // epilogue: warps 2..5 cover tensor-memory lane quadrants (warp % 4)
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    bool ok = mbar_wait(&done_bar, 0);
+    ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
+    if (!ok && lane == 0) atomicCAS(a.err, 0, 4);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int64_t nown = a.own_ptr[s + 1] - a.own_ptr[s];
+    const int64_t q = (int64_t)row0 + row;
+    const bool valid = ok && !abort_flag && q < nown;
+    float2* zr = valid ? a.z + (int64_t)a.own_glob[a.own_ptr[s] + q] * a.R : nullptr;
+    for (int c0 = 0; c0 < a.N; c0 += 16) {
+      float v[16];
+      if (ok) {
+        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+      }
+      if (valid) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int col = c0 / 2 + i;
+          if (col < a.R) zr[col] = make_float2(v[2 * i], v[2 * i + 1]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  }
+}
+
+inline int rpad(int R) { return (R + 7) / 8 * 8; }
+
+}  // namespace
+
+bool tc_plan_build(TcPlan& p, const mw::Subdomains& sd, const std::function<void*(size_t)>& alloc, cudaStream_t s) {
+  p = TcPlan();
+  const int ns = sd.n_sub;
+  std::vector<int32_t> mt_sub, mt_row0, sub_kt(ns), gt_sub, gt_kt;
+  std::vector<int64_t> sub_wtile(ns), sub_gtile(ns);
+  int64_t wt = 0, gtile = 0;
+  for (int q = 0; q < ns; ++q) {
+    const int64_t n = sd.dof_ptr[q + 1] - sd.dof_ptr[q];
+    const int64_t no = sd.own_ptr[q + 1] - sd.own_ptr[q];
+    const int KT = (int)((n + kTileKc - 1) / kTileKc);
+    const int MT = (int)((no + kTileM - 1) / kTileM);
+    sub_kt[q] = KT;
+    sub_wtile[q] = wt;
+    sub_gtile[q] = gtile;
+    for (int m = 0; m < MT; ++m) {
+      mt_sub.push_back(q);
+      mt_row0.push_back(m * kTileM);
+    }
+    for (int k = 0; k < KT; ++k) {
+      gt_sub.push_back(q);
+      gt_kt.push_back(k);
+    }
+    wt += (int64_t)MT * KT;
+    gtile += KT;
+  }
+  p.n_sub = ns;
+  p.n_mtiles = (int64_t)mt_sub.size();
+  p.n_ktiles_total = gtile;
+  p.w_tiles = wt;
+  auto up = [&](const void* h, size_t bytes) {
+    void* d = alloc(bytes);
+    cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s);
+    return d;
+  };
+  p.mt_sub = (int32_t*)up(mt_sub.data(), sizeof(int32_t) * std::max<size_t>(mt_sub.size(), 1));
+  p.mt_row0 = (int32_t*)up(mt_row0.data(), sizeof(int32_t) * std::max<size_t>(mt_row0.size(), 1));
+  p.sub_wtile = (int64_t*)up(sub_wtile.data(), sizeof(int64_t) * ns);
+  p.sub_gtile = (int64_t*)up(sub_gtile.data(), sizeof(int64_t) * ns);
+  p.sub_kt = (int32_t*)up(sub_kt.data(), sizeof(int32_t) * ns);
+  p.gt_sub = (int32_t*)up(gt_sub.data(), sizeof(int32_t) * std::max<size_t>(gt_sub.size(), 1));
+  p.gt_kt = (int32_t*)up(gt_kt.data(), sizeof(int32_t) * std::max<size_t>(gt_kt.size(), 1));
+  p.err = (int32_t*)alloc(sizeof(int32_t));
+  cudaMemsetAsync(p.err, 0, sizeof(int32_t), s);
+  cudaStreamSynchronize(s);  // host vectors go out of scope
+  p.max_kt = 0;
+  for (int q = 0; q < ns; ++q) p.max_kt = std::max(p.max_kt, sub_kt[q]);
+  p.built = true;
+  return true;
+}
+
+void tc_plan_free(TcPlan& p, const std::function<void(void*)>& dfree) {
+  for (void* q : {(void*)p.mt_sub, (void*)p.mt_row0, (void*)p.sub_wtile, (void*)p.sub_gtile, (void*)p.sub_kt,
+                  (void*)p.gt_sub, (void*)p.gt_kt, (void*)p.err})
+    if (q) dfree(q);
+  p = TcPlan();
+}
+
+size_t tc_w_bytes(const TcPlan& p) { return (size_t)std::max<int64_t>(p.w_tiles, 1) * kATileBytes; }
+
+size_t tc_scratch_bytes(const TcPlan& p, int R) {
+  return (size_t)std::max<int64_t>(p.n_ktiles_total, 1) * 2 * rpad(R) * 128;
+}
+
+void tc_extract(const TcPlan& p, const OrasBatch& bt, const OrasTopo& tp, int ws_prec, const void* ws, void* W,
+                cudaStream_t s) {
+  note_launch(1);
+  // grid: k tiles x m tiles of the largest subdomain in the batch x batch
+  const int ktmax = (int)((bt.nmax + kTileKc - 1) / kTileKc);
+  const int mtmax = (int)((bt.nmax + kTileM - 1) / kTileM);
+  dim3 grid(ktmax, mtmax, bt.count);
+  if (ws_prec == 0)
+    pack_w_kernel<double2><<<grid, 256, 0, s>>>(bt.d_n, bt.d_off, (const double2*)ws, bt.d_sub, tp.own_ptr,
+                                                 tp.own_local, p.sub_wtile, p.sub_kt, (uint8_t*)W);
+  else
+    pack_w_kernel<float2><<<grid, 256, 0, s>>>(bt.d_n, bt.d_off, (const float2*)ws, bt.d_sub, tp.own_ptr,
+                                                tp.own_local, p.sub_wtile, p.sub_kt, (uint8_t*)W);
+}
+
+int tc_stages(int N);
+size_t tc_smem_bytes(int N);
+
+int tc_stages(int N) {
+  // about 100 KB of stages per CTA so that two CTAs share an SM
+  const int stage = kATileBytes + N * 128;
+  int st = (100 * 1024) / stage;
+  return st > 6 ? 6 : (st < 2 ? 2 : st);
+}
+
+size_t tc_smem_bytes(int N) { return (size_t)tc_stages(N) * (kATileBytes + N * 128) + 1024; }
+
+void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
+                   void* scratch, cudaStream_t s) {
+  const int Rp = rpad(R);
+  const int N = 2 * Rp;
+  note_launch(2);
+  gather_b_kernel<<<(unsigned)p.n_ktiles_total, 256, 0, s>>>(p.gt_sub, p.gt_kt, tp.dof_ptr, tp.dofs, r, R, Rp,
+                                                             (uint8_t*)scratch);
+  TcArgs a;
+  a.mt_sub = p.mt_sub;
+  a.mt_row0 = p.mt_row0;
+  a.sub_wtile = p.sub_wtile;
+  a.sub_gtile = p.sub_gtile;
+  a.sub_kt = p.sub_kt;
+  a.own_ptr = tp.own_ptr;
+  a.own_glob = tp.own_glob;
+  a.W = (const uint8_t*)W;
+  a.Bt = (const uint8_t*)scratch;
+  a.z = z;
+  a.R = R;
+  a.N = N;
+  a.stages = tc_stages(N);
+  uint32_t cols = 32;
+  while ((int)cols < N) cols <<= 1;
+  a.tmem_cols = cols;
+  a.err = p.err;
+  const size_t smem = tc_smem_bytes(N);
+  static size_t attr = 0;
+  if (smem > attr) {
+    cudaFuncSetAttribute(oras_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = smem;
+  }
+  oras_tc_kernel<<<(unsigned)p.n_mtiles, kThreadsTc, smem, s>>>(a);
+}
+
 }  // namespace mwk

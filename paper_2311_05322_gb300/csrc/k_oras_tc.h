@@ -26,6 +26,10 @@ struct TcPlan {
   int64_t* sub_wtile = nullptr;  // [n_sub] first W tile of s
   int64_t* sub_gtile = nullptr;  // [n_sub] first gathered-operand k tile of s
   int32_t* sub_kt = nullptr;     // [n_sub] k tiles of s
+  int32_t* gt_sub = nullptr;     // [n_ktiles_total] subdomain of each gathered-operand tile
+  int32_t* gt_kt = nullptr;      // [n_ktiles_total] its k tile
+  int32_t* err = nullptr;        // device error word: nonzero after a timed-out wait
+  int max_kt = 0;
 };
 
 bool tc_plan_build(TcPlan& p, const mw::Subdomains& sd, const std::function<void*(size_t)>& alloc, cudaStream_t s);

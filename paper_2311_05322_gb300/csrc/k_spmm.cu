@@ -117,6 +117,7 @@ inline Shape shape_for(int R) {
 template <typename T>
 void spmm_launch(const int64_t* rp, const int32_t* ci, const T* A, const T* X, T* Y, int64_t E, int R,
                  cudaStream_t s) {
+  note_launch(1);
   Shape sh = shape_for(R);
   if (R > 128) {
     // wide blocks: process 128 columns at a time is not supported by the layout; caller splits.
@@ -150,6 +151,7 @@ void spmm_f32(const int64_t* rp, const int32_t* ci, const float2* A, const float
 
 int residual_f64(const int64_t* rp, const int32_t* ci, const double2* A, const double2* X, const double2* B,
                  double2* Rv, double* part, int64_t E, int R, cudaStream_t s) {
+  note_launch(1);
   Shape sh = shape_for(R);
   const int blocks = 152 * 4;
   switch (sh.cpl) {

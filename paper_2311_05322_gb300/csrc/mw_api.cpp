@@ -17,7 +17,12 @@
 #include "k_oras_tc.h"
 #include "mw_internal.h"
 
+#include <atomic>
+
 using mw::Error;
+
+static std::atomic<long long> g_launches{0};
+void mwk::note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace mwk {
 void start_state(const double* npart, int nparts, int R, const double* bnorm, double tol, double inner_tol,
@@ -52,6 +57,7 @@ struct Prec {
   int64_t* w_off = nullptr;          // element offsets of W_s (cc layouts)
   std::vector<void*> W;              // per frequency
   mwk::TcPlan tc;                    // BF16 tensor-core layout
+  double sum_own_n = 0, sum_n = 0;   // sum_s n_own,s n_s and sum_s n_s
   mwk::OrasTopo topo() const {
     return {dof_ptr, dofs, own_ptr, own_local, own_glob, tet_ptr, tet_ids, tet_loc, surf_ptr, surf_loc, surf_tet};
   }
@@ -72,8 +78,26 @@ struct Work {
   size_t tc_bytes = 0;
 };
 
+// Optional per-kernel-class timing with CUDA events on the context stream.
+struct Profiler {
+  uint32_t mask = 0;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  double bytes[MW_K_NCLASS] = {0, 0, 0, 0, 0};
+  cudaEvent_t get() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+};
+
 struct Ctx {
   int device = 0;
+  Profiler prof;
   cudaStream_t stream = nullptr;
   std::string err;
   int64_t mem_cap = 0, mem_used = 0;
@@ -108,6 +132,9 @@ struct Ctx {
   std::vector<double2*> Xf;    // forward fields per frequency [E][n_src]
   std::vector<double2*> Lf;    // adjoint fields per frequency
   double2* d_B = nullptr;      // RHS scratch [E][n_src]
+  double2 *d_S = nullptr, *d_C = nullptr, *d_So = nullptr, *d_Se = nullptr;
+  double *d_J = nullptr, *d_grad = nullptr, *d_gR = nullptr;
+  std::vector<double2*> d_Badj;
   double* d_red = nullptr;     // reduction scratch
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -262,6 +289,37 @@ void apply_prec(Ctx* c, int f, int work_prec, const void* v, void* z, int R) {
   check_launch("oras apply");
 }
 
+// Records an event pair around the enclosed launches when the class is enabled.
+struct ProfScope {
+  Ctx* c;
+  int cls;
+  cudaEvent_t a = nullptr;
+  // bytes: algorithmic bytes moved by the enclosed launches (for roofline fractions)
+  ProfScope(Ctx* c_, int k, double bytes) : c(c_), cls(k) {
+    if (c->prof.mask & (1u << k)) {
+      a = c->prof.get();
+      cudaEventRecord(a, c->stream);
+      c->prof.bytes[k] += bytes;
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = c->prof.get();
+      cudaEventRecord(b, c->stream);
+      c->prof.marks.push_back({cls, {a, b}});
+    }
+  }
+};
+
+// Algorithmic bytes of one preconditioner apply on R columns: the owned-row inverses once,
+// the gathered subdomain inputs and the owned outputs.
+double oras_bytes(Ctx* c, int R) {
+  const Prec& p = c->prec;
+  const double wb = p.apply_prec == 0 ? 16.0 : (p.apply_prec == 1 ? 8.0 : 4.0);
+  const double vb = p.apply_prec == 0 ? 16.0 : 8.0;
+  return wb * p.sum_own_n + vb * R * (p.sum_n + (double)c->topo.n_edge);
+}
+
 int read_active(Ctx* c) {
   CK(cudaMemcpyAsync(c->work.h_active, c->work.active, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -297,7 +355,10 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
   const int max_outer = o.mode == MW_MODE_FP64 ? (o.max_it + m - 1) / m + 1 : std::max(1, o.max_outer);
   int total = 0;
   for (int outer = 0; outer < max_outer; ++outer) {
-    nb = mwk::residual_f64(c->d_row, c->d_col, c->A64[f], X, B, w.r, w.npart, E, R, s);
+    {
+      ProfScope ps(c, MW_K_RESIDUAL, (double)c->topo.nnz * 20 + 8.0 * (E + 1) + 3.0 * 16 * E * R);
+      nb = mwk::residual_f64(c->d_row, c->d_col, c->A64[f], X, B, w.r, w.npart, E, R, s);
+    }
     CK(cudaMemsetAsync(w.active, 0, sizeof(int32_t), s));
     mwk::start_state(w.npart, nb, R, w.bnorm, o.tol, o.inner_tol, wp == 0, w.rnorm, w.g, w.target, w.done, w.kcol,
                      m, s);
@@ -311,20 +372,34 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
       mwk::normalize_start_f32(w.r, w.rnorm, w.done, E, R, (float2*)Vp(0), s);
     int j = 0;
     for (; j < m; ++j) {
-      if (use_p) apply_prec(c, f, wp, Vp(j), Zp(j), R);
-      if (wp == 0)
-        mwk::spmm_f64(c->d_row, c->d_col, c->A64[f], (const double2*)Zp(j), (double2*)Vp(j + 1), E, R, s);
-      else
-        mwk::spmm_f32(c->d_row, c->d_col, c->A32[f], (const float2*)Zp(j), (float2*)Vp(j + 1), E, R, s);
-      int np = wp == 0 ? mwk::cgs_dots_f64((const double2*)w.V, vstride, j + 1, (const double2*)Vp(j + 1), E, R,
-                                           w.part, s)
-                       : mwk::cgs_dots_f32((const float2*)w.V, vstride, j + 1, (const float2*)Vp(j + 1), E, R,
-                                           w.part, s);
-      mwk::reduce_h(w.part, np, j + 1, R, w.h, s);
-      int nu = wp == 0 ? mwk::cgs_update_f64((const double2*)w.V, vstride, j + 1, w.h, (double2*)Vp(j + 1), E, R,
-                                             w.npart, s)
-                       : mwk::cgs_update_f32((const float2*)w.V, vstride, j + 1, w.h, (float2*)Vp(j + 1), E, R,
-                                             w.npart, s);
+      if (use_p) {
+        ProfScope ps(c, MW_K_ORAS, oras_bytes(c, R));
+        apply_prec(c, f, wp, Vp(j), Zp(j), R);
+      }
+      {
+        ProfScope ps(c, MW_K_SPMM, (double)c->topo.nnz * (es + 4) + 8.0 * (E + 1) + 2.0 * es * E * R);
+        if (wp == 0)
+          mwk::spmm_f64(c->d_row, c->d_col, c->A64[f], (const double2*)Zp(j), (double2*)Vp(j + 1), E, R, s);
+        else
+          mwk::spmm_f32(c->d_row, c->d_col, c->A32[f], (const float2*)Zp(j), (float2*)Vp(j + 1), E, R, s);
+      }
+      int np;
+      {
+        ProfScope ps(c, MW_K_CGS_DOTS, (double)es * E * R * (j + 2));
+        np = wp == 0 ? mwk::cgs_dots_f64((const double2*)w.V, vstride, j + 1, (const double2*)Vp(j + 1), E, R,
+                                         w.part, s)
+                     : mwk::cgs_dots_f32((const float2*)w.V, vstride, j + 1, (const float2*)Vp(j + 1), E, R,
+                                         w.part, s);
+        mwk::reduce_h(w.part, np, j + 1, R, w.h, s);
+      }
+      int nu;
+      {
+        ProfScope ps(c, MW_K_CGS_UPDATE, (double)es * E * R * (j + 3));
+        nu = wp == 0 ? mwk::cgs_update_f64((const double2*)w.V, vstride, j + 1, w.h, (double2*)Vp(j + 1), E, R,
+                                           w.npart, s)
+                     : mwk::cgs_update_f32((const float2*)w.V, vstride, j + 1, w.h, (float2*)Vp(j + 1), E, R,
+                                           w.npart, s);
+      }
       CK(cudaMemsetAsync(w.active, 0, sizeof(int32_t), s));
       mwk::givens_step(w.h, w.npart, nu, j, m, R, w.H, w.cs, w.g, w.target, w.done, w.kcol, w.scale, w.active, s);
       if (wp == 0)
@@ -430,6 +505,14 @@ void solve_all(Ctx* c, const mw_solve_opts& o, int ncols, const std::vector<cons
   CK(cudaEventSynchronize(c->ev1));
   float ms = 0;
   CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  if (c->prec.ready && c->prec.apply_prec == 2 && c->prec.tc.err) {
+    int32_t e = 0;
+    CK(cudaMemcpy(&e, c->prec.tc.err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+      CK(cudaMemsetAsync(c->prec.tc.err, 0, sizeof(int32_t), s));
+      throw Fail{MW_ETIMEOUT, "tensor-core preconditioner apply: bounded wait ran out (code " + std::to_string(e) + ")"};
+    }
+  }
   int nconv = 0;
   double mx = 0;
   for (double r : rel_all) {
@@ -512,8 +595,13 @@ void release_mesh(Ctx* c) {
   for (void* q : {(void*)c->d_xyz, (void*)c->d_tets, (void*)c->d_col, (void*)c->d_contrib, (void*)c->d_bface_vert,
                   (void*)c->d_tet_edge, (void*)c->d_tet_nb, (void*)c->d_sign, (void*)c->d_row, (void*)c->d_cptr,
                   (void*)c->d_KM, (void*)c->d_vol, (void*)c->d_Bf, (void*)c->d_tikw, (void*)c->d_eps,
-                  (void*)c->d_src_edge, (void*)c->d_src_sign, (void*)c->d_B, (void*)c->d_red})
+                  (void*)c->d_src_edge, (void*)c->d_src_sign, (void*)c->d_B, (void*)c->d_red, (void*)c->d_S,
+                  (void*)c->d_C, (void*)c->d_So, (void*)c->d_Se, (void*)c->d_J, (void*)c->d_grad, (void*)c->d_gR})
     dfree(c, q);
+  for (auto p : c->d_Badj) dfree(c, p);
+  c->d_Badj.clear();
+  c->d_S = c->d_C = c->d_So = c->d_Se = nullptr;
+  c->d_J = c->d_grad = c->d_gR = nullptr;
   c->d_xyz = nullptr;
   c->d_tets = c->d_col = c->d_contrib = c->d_bface_vert = c->d_tet_edge = c->d_tet_nb = nullptr;
   c->d_sign = nullptr;
@@ -802,6 +890,8 @@ mw_status mw_setup_preconditioner(mw_ctx* c, int32_t n_sub, const int32_t* part,
     for (int s = 0; s < n_sub; ++s) {
       const int64_t n = sd.dof_ptr[s + 1] - sd.dof_ptr[s], no = sd.own_ptr[s + 1] - sd.own_ptr[s];
       woff[s + 1] = woff[s] + n * no;
+      p.sum_own_n += (double)n * no;
+      p.sum_n += (double)n;
       nmax = std::max(nmax, n);
       for (int64_t r0 = 0; r0 < no; r0 += 32) {
         tsub.push_back(s);
@@ -1032,32 +1122,31 @@ mw_status mw_tikhonov(mw_ctx* c, const double* eps_r, double* R_out, double* gra
   });
 }
 
-static void gradient_impl(Ctx* c, const mw_solve_opts& o, const double* S_obs, const double* S_empty, double alpha,
-                          double* J_out, double* grad, double* S_out) {
+// Device-resident gradient: S_obs/S_empty on the device, grad [T][2] device output, J to the host.
+static void gradient_dev_impl(Ctx* c, const mw_solve_opts& o, const double2* dSo, const double2* dSe, double alpha,
+                              double* J_out, double* dg) {
   require(c->has_mesh && c->n_freq > 0 && c->n_src > 0, MW_ESTATE, "assemble and set sources first");
-  require(S_obs && S_empty && J_out, MW_EINVAL, "null S_obs / S_empty / J_out");
   require(c->n_src <= 128, MW_EINVAL, "gradient supports at most 128 sources");
   const int64_t E = c->topo.n_edge, T = c->topo.n_tet;
   const int ns = c->n_src, nf = c->n_freq;
   const size_t nS = (size_t)nf * ns * ns;
   forward(c, o, nullptr);
   alloc_fields(c, c->Lf);
-  double2* dS = dalloc<double2>(c, nS);
-  double2* dSo = upload(c, (const double2*)S_obs, nS);
-  double2* dSe = upload(c, (const double2*)S_empty, nS);
-  double2* dC = dalloc<double2>(c, nS);
-  double* dg = dalloc<double>(c, 2 * T);
-  double* dJ = dalloc<double>(c, 1);
-  std::vector<const double2*> Bc(nf);
-  std::vector<double2*> Bs(nf);
-  for (int f = 0; f < nf; ++f) {
-    mwk::s_extract(c->Xf[f], c->d_src_edge, c->d_src_sign, ns, dS + (size_t)f * ns * ns, c->stream);
+  if (!c->d_S) c->d_S = dalloc<double2>(c, 64 * 128 * 128);
+  if (!c->d_C) c->d_C = dalloc<double2>(c, 64 * 128 * 128);
+  if (!c->d_J) c->d_J = dalloc<double>(c, 4);
+  if (c->d_Badj.size() != (size_t)nf) {
+    for (auto p : c->d_Badj) dfree(c, p);
+    c->d_Badj.assign(nf, nullptr);
+    for (int f = 0; f < nf; ++f) c->d_Badj[f] = dalloc<double2>(c, E * ns);
   }
-  mwk::adjoint_weights(dS, dSo, dSe, (int64_t)nS, dC, dJ, c->stream);
+  for (int f = 0; f < nf; ++f)
+    mwk::s_extract(c->Xf[f], c->d_src_edge, c->d_src_sign, ns, c->d_S + (size_t)f * ns * ns, c->stream);
+  mwk::adjoint_weights(c->d_S, dSo, dSe, (int64_t)nS, c->d_C, c->d_J, c->stream);
+  std::vector<const double2*> Bc(nf);
   for (int f = 0; f < nf; ++f) {
-    Bs[f] = dalloc<double2>(c, E * ns);
-    mwk::adjoint_rhs(c->d_src_edge, c->d_src_sign, ns, dC + (size_t)f * ns * ns, Bs[f], E, c->stream);
-    Bc[f] = Bs[f];
+    mwk::adjoint_rhs(c->d_src_edge, c->d_src_sign, ns, c->d_C + (size_t)f * ns * ns, c->d_Badj[f], E, c->stream);
+    Bc[f] = c->d_Badj[f];
   }
   check_launch("adjoint sources");
   solve_all(c, o, ns, Bc, c->Lf, nullptr);
@@ -1067,26 +1156,34 @@ static void gradient_impl(Ctx* c, const mw_solve_opts& o, const double* S_obs, c
     mwk::grad_tet(c->d_tet_edge, c->d_KM, T, c->Lf[f], c->Xf[f], ns, k0 * k0, dg, c->stream);
   }
   check_launch("gradient");
-  double Jd = 0;
-  CK(cudaMemcpyAsync(&Jd, dJ, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  std::vector<double> gh(2 * T);
-  CK(cudaMemcpyAsync(gh.data(), dg, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost, c->stream));
-  if (S_out) CK(cudaMemcpyAsync(S_out, dS, sizeof(double2) * nS, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  double J = Jd;
+  double J = 0;
   if (alpha != 0.0) {
-    double R = 0;
-    tikhonov_dev(c, c->d_eps, &R, dg);
-    std::vector<double> gr(2 * T);
-    CK(cudaMemcpyAsync(gr.data(), dg, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    J += alpha * R;
-    for (int64_t i = 0; i < 2 * T; ++i) gh[i] += alpha * gr[i];
+    if (!c->d_gR) c->d_gR = dalloc<double>(c, 2 * T);
+    mwk::tikhonov(c->d_tet_nb, c->d_tikw, c->d_eps, T, c->d_gR, c->d_red, c->stream);
+    mwk::axpy_f64(alpha, c->d_gR, dg, 2 * T, c->stream);
+    mwk::add_scaled_scalar(c->d_J, alpha, c->d_red, c->stream);
+    check_launch("tikhonov");
   }
+  CK(cudaMemcpyAsync(&J, c->d_J, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   *J_out = J;
-  if (grad) std::memcpy(grad, gh.data(), sizeof(double) * 2 * T);
-  for (auto p : Bs) dfree(c, p);
-  for (void* p : {(void*)dS, (void*)dSo, (void*)dSe, (void*)dC, (void*)dg, (void*)dJ}) dfree(c, p);
+}
+
+static void gradient_impl(Ctx* c, const mw_solve_opts& o, const double* S_obs, const double* S_empty, double alpha,
+                          double* J_out, double* grad, double* S_out) {
+  require(c->has_mesh && c->n_freq > 0 && c->n_src > 0, MW_ESTATE, "assemble and set sources first");
+  require(S_obs && S_empty && J_out, MW_EINVAL, "null S_obs / S_empty / J_out");
+  const int64_t T = c->topo.n_tet;
+  const size_t nS = (size_t)c->n_freq * c->n_src * c->n_src;
+  if (!c->d_So) c->d_So = dalloc<double2>(c, 64 * 128 * 128);
+  if (!c->d_Se) c->d_Se = dalloc<double2>(c, 64 * 128 * 128);
+  if (!c->d_grad) c->d_grad = dalloc<double>(c, 2 * T);
+  CK(cudaMemcpyAsync(c->d_So, S_obs, sizeof(double2) * nS, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_Se, S_empty, sizeof(double2) * nS, cudaMemcpyHostToDevice, c->stream));
+  gradient_dev_impl(c, o, c->d_So, c->d_Se, alpha, J_out, c->d_grad);
+  if (grad) CK(cudaMemcpyAsync(grad, c->d_grad, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost, c->stream));
+  if (S_out) CK(cudaMemcpyAsync(S_out, c->d_S, sizeof(double2) * nS, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
 }
 
 mw_status mw_gradient(mw_ctx* c, const mw_solve_opts* opts, const double* S_obs, const double* S_empty, double alpha,
@@ -1300,6 +1397,72 @@ extern "C" mw_status mw_invert(mw_ctx* c, const mw_inv_opts* opts, const mw_solv
       hist->iterations = accepted;
       hist->evaluations = evals;
     }
+  });
+}
+
+
+int64_t mw_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+mw_status mw_profile_enable(mw_ctx* c, uint32_t mask) {
+  return guard(c, [&] {
+    c->prof.mask = mask;
+    c->prof.marks.clear();
+    c->prof.used = 0;
+    for (int k = 0; k < MW_K_NCLASS; ++k) c->prof.bytes[k] = 0;
+  });
+}
+
+mw_status mw_profile_read(mw_ctx* c, double* ms, int64_t* launches, double* bytes) {
+  return guard(c, [&] {
+    require(ms && launches, MW_EINVAL, "null outputs");
+    for (int k = 0; k < MW_K_NCLASS; ++k) {
+      ms[k] = 0;
+      launches[k] = 0;
+      if (bytes) bytes[k] = c->prof.bytes[k];
+      c->prof.bytes[k] = 0;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    for (auto& m : c->prof.marks) {
+      float t = 0;
+      CK(cudaEventElapsedTime(&t, m.second.first, m.second.second));
+      if (m.first >= 0 && m.first < MW_K_NCLASS) {
+        ms[m.first] += t;
+        launches[m.first] += 1;
+      }
+    }
+    c->prof.marks.clear();
+    c->prof.used = 0;
+  });
+}
+
+mw_status mw_assemble_dev(mw_ctx* c, int32_t n_freq, const double* freq_hz, const void* eps_dev, const double* eps_bg) {
+  return guard(c, [&] {
+    require(c->has_mesh && c->n_freq == n_freq && n_freq >= 1 && freq_hz && eps_dev && eps_bg, MW_EINVAL,
+            "assemble_dev needs a prior host assemble with the same frequency count");
+    const int64_t T = c->topo.n_tet, nnz = c->topo.nnz;
+    CK(cudaMemcpyAsync(c->d_eps, eps_dev, sizeof(double) * 2 * T, cudaMemcpyDeviceToDevice, c->stream));
+    const double r = std::hypot(eps_bg[0], eps_bg[1]);
+    const double sr = std::sqrt(0.5 * (r + eps_bg[0]));
+    double si = std::sqrt(std::max(0.0, 0.5 * (r - eps_bg[0])));
+    if (eps_bg[1] < 0) si = -si;
+    c->freqs.assign(freq_hz, freq_hz + n_freq);
+    c->eps_bg[0] = eps_bg[0];
+    c->eps_bg[1] = eps_bg[1];
+    for (int f = 0; f < n_freq; ++f) {
+      const double k0 = k0_of(freq_hz[f]);
+      mwk::reassemble(c->d_cptr, c->d_contrib, nnz, c->d_KM, c->d_Bf, c->d_eps, k0 * k0, -k0 * si, k0 * sr, c->A64[f],
+                      c->A32[f], c->stream);
+    }
+    check_launch("reassemble");
+  });
+}
+
+mw_status mw_gradient_dev(mw_ctx* c, const mw_solve_opts* opts, const void* S_obs_dev, const void* S_empty_dev,
+                          double alpha, double* J_out, void* grad_dev) {
+  return guard(c, [&] {
+    mw_solve_opts o = norm_opts(opts);
+    require(S_obs_dev && S_empty_dev && J_out && grad_dev, MW_EINVAL, "null device argument");
+    gradient_dev_impl(c, o, (const double2*)S_obs_dev, (const double2*)S_empty_dev, alpha, J_out, (double*)grad_dev);
   });
 }
 

@@ -85,6 +85,9 @@ bool build_subdomains(const Topology& topo, int32_t n_sub, const int32_t* tet_pa
 // ------------------------------------------------------------------------------------
 namespace mwk {
 
+// Count of kernel launches issued by the library (diagnostic; read through mw_kernel_launches).
+void note_launch(int n);
+
 struct c64 { float x, y; };
 
 // K1 element geometry: Ke/Me [T][21] packed (signs applied), vol [T]; Bf [F][6] packed.

@@ -79,7 +79,15 @@ _SIGS = {
     "mw_lbfgs_destroy": (None, [_P]),
     "mw_invert": (C.c_int32, [_P, C.POINTER(mw_inv_opts), C.POINTER(mw_solve_opts), _P, _P, _P,
                               C.POINTER(mw_inv_history)]),
+    "mw_assemble_dev": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
+    "mw_gradient_dev": (C.c_int32, [_P, C.POINTER(mw_solve_opts), _P, _P, C.c_double, C.POINTER(C.c_double), _P]),
+    "mw_kernel_launches": (C.c_int64, []),
+    "mw_profile_enable": (C.c_int32, [_P, C.c_uint32]),
+    "mw_profile_read": (C.c_int32, [_P, _P, _P, _P]),
 }
+
+MW_K_SPMM, MW_K_ORAS, MW_K_CGS_DOTS, MW_K_CGS_UPDATE, MW_K_RESIDUAL, MW_K_NCLASS = range(6)
+K_CLASS_NAMES = ("spmm", "oras_apply", "cgs_dots", "cgs_update", "residual_fp64")
 
 _lib = None
 
@@ -207,6 +215,7 @@ class Context:
         s = np.empty(n, np.int8)
         self._check(self.lib.mw_set_sources(self.h, n, _ptr(pos), _ptr(direc), _ptr(e), _ptr(s)))
         self.n_src = n
+        self.src_edges, self.src_signs = e, s
         return e, s
 
     # -- preconditioner -------------------------------------------------------------------
@@ -270,6 +279,31 @@ class Context:
         self._check(self.lib.mw_tikhonov(self.h, _ptr(e), C.byref(R), _ptr(g)))
         return R.value, g
 
+    # -- device-resident variants -----------------------------------------------------------
+    def assemble_dev(self, freqs, eps_dev, eps_bg: complex):
+        fr = _c(np.atleast_1d(freqs), np.float64)
+        bg = np.array([complex(eps_bg).real, complex(eps_bg).imag])
+        self._check(self.lib.mw_assemble_dev(self.h, fr.size, _ptr(fr), _ptr(eps_dev), _ptr(bg)))
+
+    def gradient_dev(self, S_obs_dev, S_empty_dev, grad_dev, alpha: float = 0.0, opts: mw_solve_opts | None = None):
+        o = opts or solve_opts()
+        J = C.c_double()
+        self._check(self.lib.mw_gradient_dev(self.h, C.byref(o), _ptr(S_obs_dev), _ptr(S_empty_dev), alpha,
+                                             C.byref(J), _ptr(grad_dev)))
+        return J.value
+
+    # -- event profiler -----------------------------------------------------------------------
+    def profile_enable(self, mask: int):
+        self._check(self.lib.mw_profile_enable(self.h, mask))
+
+    def profile_read(self):
+        ms = np.zeros(MW_K_NCLASS)
+        n = np.zeros(MW_K_NCLASS, np.int64)
+        b = np.zeros(MW_K_NCLASS)
+        self._check(self.lib.mw_profile_read(self.h, _ptr(ms), _ptr(n), _ptr(b)))
+        return {K_CLASS_NAMES[k]: {"ms": float(ms[k]), "launches": int(n[k]), "bytes": float(b[k])}
+                for k in range(MW_K_NCLASS)}
+
     def invert(self, S_obs, S_empty, eps0, inv: mw_inv_opts, opts: mw_solve_opts | None = None):
         o = opts or solve_opts()
         So = _c(S_obs, np.complex128)
@@ -282,6 +316,10 @@ class Context:
         k = hist.iterations
         return eps, {"iterations": k, "evaluations": hist.evaluations, "J": Jh[:k + 1].copy(),
                      "seconds": th[:k + 1].copy()}
+
+
+def kernel_launches() -> int:
+    return int(load_library().mw_kernel_launches())
 
 
 class LBFGS:
