@@ -42,9 +42,9 @@ def _args():
     ap.add_argument("--n-src", type=int, default=32)
     ap.add_argument("--parts", default="16x16x7")
     ap.add_argument("--overlap", type=int, default=1)
-    ap.add_argument("--prec", default="fp32", choices=["bf16", "fp32"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--alpha", type=float, default=1e-3)
-    ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--plain-cols", type=int, default=1, help="columns timed on the plain FP64 path (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-subdomains", type=int, default=24)

@@ -50,8 +50,13 @@ inline Shape shape_for(int R) {
 }
 
 // h_part[p][i][c] = sum over the rows of part p of conj(V_i[e][c]) * w[e][c].
-// Warp k of a block serves vectors i = k, k + 8, ... when nvec >= 8; otherwise the 8 warps
-// split into S = 8 / nvec row slots per vector.  Part index p = block * S + slot.
+// Warp k of a block serves vectors i = k, k + 8, ... (nvec >= 8); for nvec < 8 the 8 warps
+// split into S = 8 / nvec row slots per vector.  A warp walks its rows in passes of kUnroll
+// rows with all loads of a pass issued together (V_i from HBM, w shared by the block's warps
+// through L1); each pass is summed in the vector precision and added to an FP64 accumulator.
+// No block-level synchronisation.  Part index p = block * S + slot.
+constexpr int kUnroll = 8;
+
 template <typename T, int CPL>
 __global__ void __launch_bounds__(kThreads) cgs_dots_kernel(const T* __restrict__ V, int64_t vstride, int nvec,
                                                             const T* __restrict__ w, int64_t E, int R, int tpr_log2,
@@ -59,68 +64,69 @@ __global__ void __launch_bounds__(kThreads) cgs_dots_kernel(const T* __restrict_
   using Sc = typename Traits<T>::S;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tpr = 1 << tpr_log2;
-  const int rpw = 32 >> tpr_log2;          // rows per warp pass
+  const int rpw = 32 >> tpr_log2;           // rows per warp pass
   const int lrow = lane >> tpr_log2;
   const int c0 = (lane & (tpr - 1)) * CPL;
   int i_first, i_step, slot;
+  bool idle = false;
   if (nvec >= kWarps) {
     i_first = warp;
     i_step = kWarps;
     slot = 0;
   } else {
-    if (warp >= nvec * S) return;
+    idle = warp >= nvec * S;
     i_first = warp % nvec;
     i_step = 1 << 30;
     slot = warp / nvec;
   }
-  const int nmine = i_first < nvec ? (nvec - 1 - i_first) / i_step + 1 : 0;
+  const int nmine = idle ? 0 : (i_first < nvec ? (nvec - 1 - i_first) / i_step + 1 : 0);
   double2 acc[kMaxVecPerWarp][CPL];
 #pragma unroll
   for (int a = 0; a < kMaxVecPerWarp; ++a)
 #pragma unroll
     for (int q = 0; q < CPL; ++q) acc[a][q] = make_double2(0.0, 0.0);
-
-  const int64_t rows_per_iter = (int64_t)gridDim.x * S * rpw;
-  const int64_t row0 = ((int64_t)blockIdx.x * S + slot) * rpw + lrow;
-  const bool active_c = c0 < R;
-  // chunked loop over rows
-  for (int64_t base = row0; base < E; base += rows_per_iter * kChunk) {
+  const bool active_c = c0 < R && !idle;
+  // row r of pass base: base + u * stride, u < kUnroll; passes advance by kUnroll * stride
+  const int64_t stride = (int64_t)gridDim.x * S * rpw;
+  const int64_t first = ((int64_t)blockIdx.x * S + slot) * rpw + lrow;
+  if (active_c) {
+    for (int64_t base = first; base < E; base += stride * kUnroll) {
 #pragma unroll
-    for (int a = 0; a < kMaxVecPerWarp; ++a) {
-      if (a >= nmine) break;
-      const int i = i_first + a * i_step;
-      const T* Vi = V + (int64_t)i * vstride;
-      Sc sr[CPL], si[CPL];
+      for (int a = 0; a < kMaxVecPerWarp; ++a) {
+        if (a < nmine) {
+          const int i = i_first + a * i_step;
+          const T* Vi = V + (int64_t)i * vstride;
+          T vv[kUnroll][CPL], xx[kUnroll][CPL];
 #pragma unroll
-      for (int q = 0; q < CPL; ++q) sr[q] = si[q] = (Sc)0;
-      for (int k = 0; k < kChunk; ++k) {
-        const int64_t row = base + (int64_t)k * rows_per_iter;
-        if (row >= E || !active_c) break;
-        const T* vr = Vi + row * R + c0;
-        const T* wr = w + row * R + c0;
+          for (int u = 0; u < kUnroll; ++u) {
+            const int64_t row = base + u * stride;
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) {
-          if (c0 + q < R) {
-            const T v = vr[q], x = wr[q];
-            // conj(v) * x
-            sr[q] = fma(v.x, x.x, sr[q]);
-            sr[q] = fma(v.y, x.y, sr[q]);
-            si[q] = fma(v.x, x.y, si[q]);
-            si[q] = fma(-v.y, x.x, si[q]);
+            for (int q = 0; q < CPL; ++q) {
+              const bool ok = row < E && c0 + q < R;
+              vv[u][q] = ok ? Vi[row * R + c0 + q] : T{0, 0};
+              xx[u][q] = ok ? __ldg(&w[row * R + c0 + q]) : T{0, 0};
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < CPL; ++q) {
+            Sc sr = 0, si = 0;
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+              sr = fma(vv[u][q].x, xx[u][q].x, sr);
+              sr = fma(vv[u][q].y, xx[u][q].y, sr);
+              si = fma(vv[u][q].x, xx[u][q].y, si);
+              si = fma(-vv[u][q].y, xx[u][q].x, si);
+            }
+            acc[a][q].x += (double)sr;
+            acc[a][q].y += (double)si;
           }
         }
-      }
-#pragma unroll
-      for (int q = 0; q < CPL; ++q) {
-        acc[a][q].x += (double)sr[q];
-        acc[a][q].y += (double)si[q];
       }
     }
   }
   // reduce over the rows of the warp (lanes with equal column)
 #pragma unroll
   for (int a = 0; a < kMaxVecPerWarp; ++a) {
-    if (a >= nmine) break;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
       double x = acc[a][q].x, y = acc[a][q].y;
@@ -133,21 +139,35 @@ __global__ void __launch_bounds__(kThreads) cgs_dots_kernel(const T* __restrict_
   }
   if (lrow == 0 && active_c) {
     const int64_t p = (int64_t)blockIdx.x * S + slot;
-    for (int a = 0; a < nmine; ++a) {
-      const int i = i_first + a * i_step;
 #pragma unroll
-      for (int q = 0; q < CPL; ++q)
-        if (c0 + q < R) part[(p * nvec + i) * R + c0 + q] = acc[a][q];
+    for (int a = 0; a < kMaxVecPerWarp; ++a) {
+      if (a < nmine) {
+        const int i = i_first + a * i_step;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+          if (c0 + q < R) part[(p * nvec + i) * R + c0 + q] = acc[a][q];
+      }
     }
   }
 }
 
+// h[i][c] = sum_p part[p][i][c]: one warp per entry, lanes take parts lane, lane + 32, ...,
+// then a fixed shuffle tree (deterministic).
 __global__ void reduce_h_kernel(const double2* __restrict__ part, int nparts, int nvec, int R, double2* __restrict__ h) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (t >= nvec * R) return;
-  double2 s = make_double2(0.0, 0.0);
-  for (int p = 0; p < nparts; ++p) s = cadd(s, part[(int64_t)p * nvec * R + t]);
-  h[t] = s;
+  double x = 0.0, y = 0.0;
+  for (int p = lane; p < nparts; p += 32) {
+    const double2 v = part[(int64_t)p * nvec * R + t];
+    x += v.x;
+    y += v.y;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, off);
+    y += __shfl_xor_sync(0xffffffffu, y, off);
+  }
+  if (lane == 0) h[t] = make_double2(x, y);
 }
 
 // w[e][c] -= sum_i h[i][c] V_i[e][c]; partial sums of |w|^2 per block and column.
@@ -429,15 +449,16 @@ int dots_launch(const T* V, int64_t vstride, int nvec, const T* w, int64_t E, in
   note_launch(1);
   Shape sh = shape_for(R);
   const int S = nvec >= kWarps ? 1 : kWarps / nvec;
+  const size_t smem = 0;
   switch (sh.cpl) {
     case 1:
-      cgs_dots_kernel<T, 1><<<kBlocks, kThreads, 0, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
+      cgs_dots_kernel<T, 1><<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
       break;
     case 2:
-      cgs_dots_kernel<T, 2><<<kBlocks, kThreads, 0, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
+      cgs_dots_kernel<T, 2><<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
       break;
     default:
-      cgs_dots_kernel<T, 4><<<kBlocks, kThreads, 0, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
+      cgs_dots_kernel<T, 4><<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
       break;
   }
   return kBlocks * S;
@@ -484,7 +505,7 @@ int cgs_dots_f32(const float2* V, int64_t vstride, int nvec, const float2* w, in
 void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s) {
   note_launch(1);
   const int n = nvec * R;
-  reduce_h_kernel<<<(n + 127) / 128, 128, 0, s>>>(part, nparts, nvec, R, h);
+  reduce_h_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(part, nparts, nvec, R, h);
 }
 int cgs_update_f64(const double2* V, int64_t vstride, int nvec, const double2* h, double2* w, int64_t E, int R,
                    double* npart, cudaStream_t s) {

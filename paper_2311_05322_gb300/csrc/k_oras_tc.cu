@@ -163,6 +163,9 @@ __global__ void pack_w_kernel(const int64_t* __restrict__ nmat, const int64_t* _
 __global__ void gather_b_kernel(const int32_t* __restrict__ gt_sub, const int32_t* __restrict__ gt_kt,
                                 const int64_t* __restrict__ dof_ptr, const int32_t* __restrict__ dofs,
                                 const float2* __restrict__ r, int R, int Rp, uint8_t* __restrict__ Bt) {
+  // the tile is assembled in shared memory (4-byte swizzled stores) and written out with
+  // coalesced 16-byte stores
+  extern __shared__ __align__(16) uint8_t tsm[];
   const int64_t g = blockIdx.x;
   const int s = gt_sub[g], kt = gt_kt[g];
   const int64_t n = dof_ptr[s + 1] - dof_ptr[s];
@@ -175,9 +178,13 @@ __global__ void gather_b_kernel(const int32_t* __restrict__ gt_sub, const int32_
     float2 v = make_float2(0.f, 0.f);
     if (k < n && c < R) v = r[(int64_t)dv[k] * R + c];
     const uint32_t n0 = 2 * c, n1 = 2 * c + 1;
-    *reinterpret_cast<uint32_t*>(tile + swz(n0, 2 * kc)) = pack_bf16(v.x, -v.y);
-    *reinterpret_cast<uint32_t*>(tile + swz(n1, 2 * kc)) = pack_bf16(v.y, v.x);
+    *reinterpret_cast<uint32_t*>(tsm + swz(n0, 2 * kc)) = pack_bf16(v.x, -v.y);
+    *reinterpret_cast<uint32_t*>(tsm + swz(n1, 2 * kc)) = pack_bf16(v.y, v.x);
   }
+  __syncthreads();
+  const int nvec16 = N * 128 / 16;
+  for (int i = threadIdx.x; i < nvec16; i += blockDim.x)
+    reinterpret_cast<uint4*>(tile)[i] = reinterpret_cast<const uint4*>(tsm)[i];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -416,8 +423,14 @@ void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const flo
   const int Rp = rpad(R);
   const int N = 2 * Rp;
   note_launch(2);
-  gather_b_kernel<<<(unsigned)p.n_ktiles_total, 256, 0, s>>>(p.gt_sub, p.gt_kt, tp.dof_ptr, tp.dofs, r, R, Rp,
-                                                             (uint8_t*)scratch);
+  const size_t gsm = (size_t)N * 128;
+  static size_t gattr = 0;
+  if (gsm > 48 * 1024 && gsm > gattr) {
+    cudaFuncSetAttribute(gather_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+    gattr = gsm;
+  }
+  gather_b_kernel<<<(unsigned)p.n_ktiles_total, 256, gsm, s>>>(p.gt_sub, p.gt_kt, tp.dof_ptr, tp.dofs, r, R, Rp,
+                                                               (uint8_t*)scratch);
   TcArgs a;
   a.mt_sub = p.mt_sub;
   a.mt_row0 = p.mt_row0;
