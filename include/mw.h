@@ -143,6 +143,19 @@ mw_status mw_setup_preconditioner(mw_ctx* ctx, int32_t n_sub, const int32_t* tet
 /* z = M_f^{-1} r on the device, complex128 [E][n_cols] in and out (parity hook). */
 mw_status mw_apply_preconditioner(mw_ctx* ctx, int32_t f, const void* r_dev, void* z_dev,
                                   int32_t n_cols);
+/* z = M_f^{-1} r with no device allocation.  The paper has no counterpart: this is an
+ * integration aid.  It is for callers that cannot allocate device memory when they apply the
+ * preconditioner, for example because another framework holds the device heap, because the
+ * code must not allocate after initialisation, or because an allocation would synchronise the
+ * device at that point.  Needs a BF16 (tensor-core) preconditioner.  r_dev / z_dev: device
+ * complex64 [E][n_cols] (column fastest), 1 <= n_cols <= 128; z receives every row.
+ * Scratch: the gathered operand lives in one fixed device array of 16 MiB that the library
+ * holds on each GPU until the process exits; a call whose operand would exceed it returns
+ * MW_EINVAL with the sizes.  The first call on a device looks the array's address up on that
+ * device; make that first call before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU (different streams or contexts without ordering) race; order them. */
+mw_status mw_apply_preconditioner_noalloc(mw_ctx* ctx, int32_t f, const void* r_dev, void* z_dev,
+                                          int32_t n_cols);
 /* Owner subdomain of each edge [E] and unknowns per subdomain [n_sub] (either may be NULL). */
 mw_status mw_get_partition(mw_ctx* ctx, int32_t* edge_owner, int32_t* sub_size);
 

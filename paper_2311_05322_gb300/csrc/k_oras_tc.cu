@@ -19,6 +19,8 @@
 // drains its outstanding copies (again bounded), frees tensor memory and returns.
 #include <cuda_bf16.h>
 
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "k_oras.h"
@@ -456,6 +458,46 @@ void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const flo
     attr = smem;
   }
   oras_tc_kernel<<<(unsigned)p.n_mtiles, kThreadsTc, smem, s>>>(a);
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Fixed scratch for the preconditioner apply that allocates nothing.
+//
+// Some callers cannot allocate device memory when they apply the preconditioner: code that
+// runs while another framework owns the whole device heap, code that forbids allocation after
+// initialisation (latency-critical or embedded loops), or callers on paths where an allocation
+// would synchronise the device.  For them the gathered operand of the tensor-core apply lives
+// in this file-scope array instead of a context buffer.  Every GPU that loads the library holds
+// it until the process exits.  All calls share it and it keeps the last call's contents; the
+// gather kernel rewrites every byte a call reads (zero padding included), so nothing needs
+// clearing, but calls that overlap on the GPU race on it.
+// ---------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+bool tc_noalloc_scratch(void** ptr, std::string& err) {
+  // In host code the array's name is only a host-side handle; the device address is looked up
+  // once per device, with that device current, and cached.
+  static std::mutex mu;
+  static void* addr[256] = {};
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256) {
+    err = std::string("cudaGetDevice failed: ") + cudaGetErrorString(e);
+    return false;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      err = std::string("cudaGetSymbolAddress of the fixed scratch failed: ") + cudaGetErrorString(e);
+      return false;
+    }
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  return true;
 }
 
 }  // namespace mwk

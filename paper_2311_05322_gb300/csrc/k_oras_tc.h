@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <functional>
+#include <string>
 
 namespace mw {
 struct Subdomains;
@@ -40,5 +41,10 @@ void tc_extract(const TcPlan& p, const OrasBatch& bt, const OrasTopo& tp, int ws
                 cudaStream_t s);
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
                    void* scratch, cudaStream_t s);
+
+// Size of the fixed scratch used by mw_apply_preconditioner_noalloc (16 MiB).
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;
+// Device address of the fixed scratch on the current device (looked up once per device).
+bool tc_noalloc_scratch(void** ptr, std::string& err);
 
 }  // namespace mwk

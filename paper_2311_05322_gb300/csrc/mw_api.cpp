@@ -1466,4 +1466,25 @@ mw_status mw_gradient_dev(mw_ctx* c, const mw_solve_opts* opts, const void* S_ob
   });
 }
 
+
+// Tensor-core preconditioner apply for callers that cannot allocate device memory: the
+// gathered operand goes to the library's fixed scratch array, nothing else is allocated.
+mw_status mw_apply_preconditioner_noalloc(mw_ctx* c, int32_t f, const void* r, void* z, int32_t n_cols) {
+  return guard(c, [&] {
+    require(c->prec.ready, MW_ESTATE, "no preconditioner");
+    require(c->prec.apply_prec == 2, MW_EINVAL, "the allocation-free apply needs a BF16 (tensor-core) preconditioner");
+    require(f >= 0 && f < c->n_freq && r && z && n_cols >= 1 && n_cols <= 128, MW_EINVAL, "bad arguments");
+    const size_t need = mwk::tc_scratch_bytes(c->prec.tc, n_cols);
+    require(need <= mwk::kNoAllocScratchBytes, MW_EINVAL,
+            "gathered operand needs " + std::to_string(need) + " bytes, above the fixed scratch of " +
+                std::to_string(mwk::kNoAllocScratchBytes) + " bytes (fewer columns or a smaller mesh)");
+    void* scratch = nullptr;
+    std::string err;
+    if (!mwk::tc_noalloc_scratch(&scratch, err)) throw Fail{MW_ECUDA, err};
+    mwk::oras_apply_tc(c->prec.tc, c->prec.topo(), c->prec.W[f], (const float2*)r, (float2*)z, n_cols, scratch,
+                       c->stream);
+    check_launch("allocation-free preconditioner apply");
+  });
+}
+
 }  // extern "C"

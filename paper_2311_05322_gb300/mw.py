@@ -84,6 +84,7 @@ _SIGS = {
     "mw_kernel_launches": (C.c_int64, []),
     "mw_profile_enable": (C.c_int32, [_P, C.c_uint32]),
     "mw_profile_read": (C.c_int32, [_P, _P, _P, _P]),
+    "mw_apply_preconditioner_noalloc": (C.c_int32, [_P, C.c_int32, _P, _P, C.c_int32]),
 }
 
 MW_K_SPMM, MW_K_ORAS, MW_K_CGS_DOTS, MW_K_CGS_UPDATE, MW_K_RESIDUAL, MW_K_NCLASS = range(6)
@@ -226,6 +227,10 @@ class Context:
 
     def apply_preconditioner(self, f: int, r, z, n_cols: int):
         self._check(self.lib.mw_apply_preconditioner(self.h, f, _ptr(r), _ptr(z), n_cols))
+
+    def apply_preconditioner_noalloc(self, f: int, r, z, n_cols: int):
+        """Allocation-free apply (complex64 device in/out, BF16 preconditioner only)."""
+        self._check(self.lib.mw_apply_preconditioner_noalloc(self.h, f, _ptr(r), _ptr(z), n_cols))
 
     def get_partition(self):
         owner = np.empty(self.info.n_edge, np.int32)
