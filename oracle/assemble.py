@@ -37,16 +37,21 @@ class System:
         return sp.csr_matrix((values, self.topo.col_idx, self.topo.row_ptr), shape=(E, E))
 
 
-def build_system(xyz: np.ndarray, tets: np.ndarray) -> System:
-    topo = build_topology(xyz.shape[0], tets)
+def build_system(xyz: np.ndarray, tets: np.ndarray, with_pattern: bool = True) -> System:
+    """Topology, element and boundary-face matrices; with_pattern=False skips the CSR pattern
+    and the assembly positions (enough for element-wise operator applies and subdomains)."""
+    topo = build_topology(xyz.shape[0], tets, with_pattern=with_pattern)
     K, M, vol = tet_matrices(xyz, tets, topo.tet_sign)
     te = topo.tet_edge
-    rows = np.repeat(te, 6, axis=1)
-    cols = np.tile(te, (1, 6))
-    pos_tet = topo.nnz_position(rows.ravel(), cols.ravel()).reshape(-1, 36)
     fe, fs = topo.face_edges(topo.bface)
     BF, _ = face_matrices(xyz, topo.faces[topo.bface], fs)
-    pos_face = topo.nnz_position(np.repeat(fe, 3, axis=1).ravel(), np.tile(fe, (1, 3)).ravel()).reshape(-1, 9)
+    if with_pattern:
+        rows = np.repeat(te, 6, axis=1)
+        cols = np.tile(te, (1, 6))
+        pos_tet = topo.nnz_position(rows.ravel(), cols.ravel()).reshape(-1, 36)
+        pos_face = topo.nnz_position(np.repeat(fe, 3, axis=1).ravel(), np.tile(fe, (1, 3)).ravel()).reshape(-1, 9)
+    else:
+        pos_tet = pos_face = None
     return System(topo, xyz, np.asarray(tets), K, M, vol, pos_tet, fe, BF, pos_face)
 
 
@@ -69,3 +74,32 @@ def assemble_parts(sysm: System):
         np.add.at(v, pos.ravel(), elem.reshape(-1))
         out.append(sysm.csr(v))
     return out
+
+
+def apply_system(sysm: System, eps: np.ndarray, freq_hz: float, eps_bg: complex, X: np.ndarray) -> np.ndarray:
+    """A_f X as the sum of element contributions (no assembled matrix): for each tet,
+    (K^T - k0^2 eps_T M^T) acting on its 6 edge values, plus i k0 sqrt(eps_bg) B^F on each
+    boundary face; scattered into the rows of the edges.  Same operator as assemble()."""
+    k0 = constants.k0(freq_hz)
+    te = sysm.topo.tet_edge
+    Y = np.zeros(X.shape, dtype=np.complex128)
+    for t0 in range(0, te.shape[0], 200000):
+        sl = slice(t0, t0 + 200000)
+        elem = sysm.K[sl].astype(np.complex128) - (k0 * k0) * eps[sl, None, None] * sysm.M[sl]
+        yt = np.einsum("tmn,tnr->tmr", elem, X[te[sl]])
+        np.add.at(Y, te[sl].ravel(), yt.reshape(-1, X.shape[1]))
+    fe = sysm.bface_edges
+    zb = 1j * k0 * np.sqrt(complex(eps_bg))
+    yf = np.einsum("fmn,fnr->fmr", zb * sysm.BF, X[fe])
+    np.add.at(Y, fe.ravel(), yf.reshape(-1, X.shape[1]))
+    return Y
+
+
+def apply_elementwise(xyz, tets, topo: Topology, eps: np.ndarray, freq_hz: float, eps_bg: complex,
+                      X: np.ndarray) -> np.ndarray:
+    """apply_system for a mesh given by its topology (element matrices computed here)."""
+    K, M, vol = tet_matrices(xyz, tets, topo.tet_sign)
+    fe, fs = topo.face_edges(topo.bface)
+    BF, _ = face_matrices(xyz, topo.faces[topo.bface], fs)
+    sysm = System(topo, xyz, np.asarray(tets), K, M, vol, None, fe, BF, None)
+    return apply_system(sysm, eps, freq_hz, eps_bg, X)

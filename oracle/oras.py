@@ -38,18 +38,18 @@ class Subdomain:
     iface_tet: np.ndarray   # the inside tet of each interface face
 
 
-def build_subdomains(sysm: asm.System, tet_part: np.ndarray, n_sub: int, overlap: int):
+def build_subdomains(sysm: asm.System, tet_part: np.ndarray, n_sub: int, overlap: int, which=None):
+    """Subdomains (all, or the ids in `which`) and the owner of every edge."""
     topo = sysm.topo
     tets = sysm.tets
-    T = topo.n_tet
-    owner = np.full(topo.n_edge, -1, dtype=np.int64)
+    # owner of an edge = lowest subdomain id among the non-overlapping tets that touch it
+    owner = np.full(topo.n_edge, np.iinfo(np.int64).max, dtype=np.int64)
+    np.minimum.at(owner, topo.tet_edge.ravel(), np.repeat(np.asarray(tet_part, dtype=np.int64), 6))
     subs = []
-    for s in range(n_sub):
-        inner = tet_part == s
-        fresh = owner[topo.tet_edge[inner]].ravel() == -1
-        e_in = topo.tet_edge[inner].ravel()[fresh]
-        owner[e_in] = s
-    for s in range(n_sub):
+    ids = range(n_sub) if which is None else which
+    ft = topo.face_tets
+    has1 = ft[:, 1] >= 0
+    for s in ids:
         cur = tet_part == s
         for _ in range(overlap):
             vmask = np.zeros(topo.n_vert, dtype=bool)
@@ -58,14 +58,12 @@ def build_subdomains(sysm: asm.System, tet_part: np.ndarray, n_sub: int, overlap
         tl = np.nonzero(cur)[0]
         dofs = np.unique(topo.tet_edge[tl])
         owned = np.nonzero(owner[dofs] == s)[0]
-        ft = topo.face_tets
         in0 = cur[ft[:, 0]]
-        in1 = np.where(ft[:, 1] >= 0, cur[np.maximum(ft[:, 1], 0)], False)
-        has1 = ft[:, 1] >= 0
+        in1 = np.where(has1, cur[np.maximum(ft[:, 1], 0)], False)
         iface = np.nonzero(has1 & (in0 != in1))[0]
         iface_tet = np.where(in0[iface], ft[iface, 0], ft[iface, 1])
         subs.append(Subdomain(tl, dofs, owned, iface, iface_tet))
-    assert np.all(owner >= 0)
+    assert np.all(owner < n_sub)
     return subs, owner
 
 

@@ -17,8 +17,8 @@ from dataclasses import dataclass
 import numpy as np
 
 LOCAL_EDGES = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
-# local faces of a tet, as local vertex triples (face i is opposite local vertex 3-i... any
-# fixed order works; faces are canonicalised by sorting global ids)
+# local faces of a tet, as local vertex triples; face k is opposite local vertex k (faces are
+# canonicalised by sorting their global vertex ids)
 LOCAL_FACES = ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2))
 
 
@@ -69,7 +69,8 @@ class Topology:
         return pos
 
 
-def build_topology(n_vert: int, tets: np.ndarray) -> Topology:
+def edge_numbering(n_vert: int, tets: np.ndarray):
+    """Canonical edges (lexicographic (lo, hi)), tet -> 6 edges and their signs."""
     tets = np.asarray(tets, dtype=np.int64)
     T = tets.shape[0]
     a = tets[:, [p for p, _ in LOCAL_EDGES]]
@@ -81,16 +82,12 @@ def build_topology(n_vert: int, tets: np.ndarray) -> Topology:
     edge_vert = np.stack([uniq // n_vert, uniq % n_vert], axis=1)
     tet_edge = inv.reshape(T, 6)
     tet_sign = np.where(a < b, 1, -1).astype(np.int8)
-    E = edge_vert.shape[0]
+    return edge_vert, tet_edge, tet_sign
 
-    r = np.repeat(tet_edge, 6, axis=1).ravel()
-    c = np.tile(tet_edge, (1, 6)).ravel()
-    pk = np.unique(r * E + c)
-    rows = pk // E
-    col_idx = pk % E
-    row_ptr = np.zeros(E + 1, dtype=np.int64)
-    np.cumsum(np.bincount(rows, minlength=E), out=row_ptr[1:])
 
+def face_list(n_vert: int, tets: np.ndarray):
+    """Sorted vertex triples in lexicographic order, their adjacent tets, boundary face ids."""
+    tets = np.asarray(tets, dtype=np.int64)
     fv = np.sort(tets[:, LOCAL_FACES], axis=2).reshape(-1, 3)      # [4T, 3]
     fkey = (fv[:, 0] * n_vert + fv[:, 1]) * n_vert + fv[:, 2]
     order = np.argsort(fkey, kind="stable")
@@ -105,4 +102,28 @@ def build_topology(n_vert: int, tets: np.ndarray) -> Topology:
     face_tets[two, 1] = tet_of[start[two] + 1]
     assert cnt.max() <= 2, "non-manifold mesh"
     bface = np.nonzero(cnt == 1)[0]
-    return Topology(n_vert, T, edge_vert, tet_edge, tet_sign, row_ptr, col_idx, faces, face_tets, bface)
+    return faces, face_tets, bface
+
+
+def matrix_pattern(n_edge: int, tet_edge: np.ndarray):
+    """CSR pattern: all pairs of edges sharing a tet, columns ascending."""
+    E = n_edge
+    r = np.repeat(tet_edge, 6, axis=1).ravel()
+    c = np.tile(tet_edge, (1, 6)).ravel()
+    pk = np.unique(r * E + c)
+    rows = pk // E
+    col_idx = pk % E
+    row_ptr = np.zeros(E + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=E), out=row_ptr[1:])
+    return row_ptr, col_idx
+
+
+def build_topology(n_vert: int, tets: np.ndarray, with_pattern: bool = True) -> Topology:
+    tets = np.asarray(tets, dtype=np.int64)
+    edge_vert, tet_edge, tet_sign = edge_numbering(n_vert, tets)
+    if with_pattern:
+        row_ptr, col_idx = matrix_pattern(edge_vert.shape[0], tet_edge)
+    else:
+        row_ptr, col_idx = np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int64)
+    faces, face_tets, bface = face_list(n_vert, tets)
+    return Topology(n_vert, tets.shape[0], edge_vert, tet_edge, tet_sign, row_ptr, col_idx, faces, face_tets, bface)

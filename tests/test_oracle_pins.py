@@ -173,6 +173,16 @@ def test_whitney_reproduces_linear_fields(box_system):
         assert abs(uc @ (B @ uc) - exact_b) <= 1e-12 * exact_b
 
 
+def test_elementwise_apply_equals_assembled_operator(box_system):
+    m, sysm = box_system
+    eps = np.full(m.n_tet, EPS_MATCHING) + np.random.default_rng(6).uniform(-3, 3, m.n_tet)
+    X = np.random.default_rng(7).normal(size=(sysm.topo.n_edge, 3)) + 0j
+    ref = sysm.csr(asm.assemble(sysm, eps, 1.1e9, EPS_MATCHING)) @ X
+    topo = build_topology(m.n_vert, m.tets, with_pattern=False)
+    Y = asm.apply_elementwise(m.xyz, m.tets, topo, eps, 1.1e9, EPS_MATCHING, X)
+    assert np.linalg.norm(Y - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
 def test_matrix_complex_symmetric_and_matches_dense_solve(box_system):
     m, sysm = box_system
     eps = np.full(m.n_tet, EPS_MATCHING) + np.random.default_rng(2).uniform(-3, 3, m.n_tet)
