@@ -50,18 +50,22 @@ inline Shape shape_for(int R) {
 }
 
 // h_part[p][i][c] = sum over the rows of part p of conj(V_i[e][c]) * w[e][c].
-// Warp k of a block serves vectors i = k, k + 8, ... (nvec >= 8); for nvec < 8 the 8 warps
-// split into S = 8 / nvec row slots per vector.  A warp walks its rows in passes of kUnroll
+// Warp k of a block serves vectors i = k, k + 16, ... (nvec >= 16); for nvec < 16 the 16
+// warps split into S = 16 / nvec row slots per vector.  A warp walks its rows in passes of kUnroll
 // rows with all loads of a pass issued together (V_i from HBM, w shared by the block's warps
 // through L1); each pass is summed in the vector precision and added to an FP64 accumulator.
 // No block-level synchronisation.  Part index p = block * S + slot.
-constexpr int kUnroll = 8;
+constexpr int kDotThreads = 512;
+constexpr int kDotWarps = kDotThreads / 32;
+constexpr int kDotVecPerWarp = 4;   // nvec <= 64 = 16 warps x 4
 
 template <typename T, int CPL>
-__global__ void __launch_bounds__(kThreads) cgs_dots_kernel(const T* __restrict__ V, int64_t vstride, int nvec,
+__global__ void __launch_bounds__(kDotThreads) cgs_dots_kernel(const T* __restrict__ V, int64_t vstride, int nvec,
                                                             const T* __restrict__ w, int64_t E, int R, int tpr_log2,
                                                             int S, double2* __restrict__ part) {
   using Sc = typename Traits<T>::S;
+  // rows in flight per thread: the same bytes per thread for every CPL and precision
+  constexpr int kUnroll = (16 / CPL) / (sizeof(T) / 8) > 0 ? (16 / CPL) / (sizeof(T) / 8) : 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tpr = 1 << tpr_log2;
   const int rpw = 32 >> tpr_log2;           // rows per warp pass
@@ -69,9 +73,9 @@ __global__ void __launch_bounds__(kThreads) cgs_dots_kernel(const T* __restrict_
   const int c0 = (lane & (tpr - 1)) * CPL;
   int i_first, i_step, slot;
   bool idle = false;
-  if (nvec >= kWarps) {
+  if (nvec >= kDotWarps) {
     i_first = warp;
-    i_step = kWarps;
+    i_step = kDotWarps;
     slot = 0;
   } else {
     idle = warp >= nvec * S;
@@ -80,26 +84,28 @@ __global__ void __launch_bounds__(kThreads) cgs_dots_kernel(const T* __restrict_
     slot = warp / nvec;
   }
   const int nmine = idle ? 0 : (i_first < nvec ? (nvec - 1 - i_first) / i_step + 1 : 0);
-  double2 acc[kMaxVecPerWarp][CPL];
+  double2 acc[kDotVecPerWarp][CPL];
 #pragma unroll
-  for (int a = 0; a < kMaxVecPerWarp; ++a)
+  for (int a = 0; a < kDotVecPerWarp; ++a)
 #pragma unroll
     for (int q = 0; q < CPL; ++q) acc[a][q] = make_double2(0.0, 0.0);
   const bool active_c = c0 < R && !idle;
-  // row r of pass base: base + u * stride, u < kUnroll; passes advance by kUnroll * stride
-  const int64_t stride = (int64_t)gridDim.x * S * rpw;
-  const int64_t first = ((int64_t)blockIdx.x * S + slot) * rpw + lrow;
+  // Block iterations take contiguous chunks of kUnroll * rpw * S rows; slot q of the chunk owns
+  // the contiguous sub-range [q * kUnroll * rpw, (q + 1) * kUnroll * rpw), and thread (lrow, u)
+  // reads row sub + u * rpw + lrow, so a warp streams kUnroll * rpw consecutive rows.
+  const int64_t chunk = (int64_t)kUnroll * rpw * S;
   if (active_c) {
-    for (int64_t base = first; base < E; base += stride * kUnroll) {
+    for (int64_t cb = (int64_t)blockIdx.x * chunk; cb < E; cb += (int64_t)gridDim.x * chunk) {
+      const int64_t sub = cb + (int64_t)slot * kUnroll * rpw + lrow;
 #pragma unroll
-      for (int a = 0; a < kMaxVecPerWarp; ++a) {
+      for (int a = 0; a < kDotVecPerWarp; ++a) {
         if (a < nmine) {
           const int i = i_first + a * i_step;
           const T* Vi = V + (int64_t)i * vstride;
           T vv[kUnroll][CPL], xx[kUnroll][CPL];
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
-            const int64_t row = base + u * stride;
+            const int64_t row = sub + (int64_t)u * rpw;
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
               const bool ok = row < E && c0 + q < R;
@@ -126,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) cgs_dots_kernel(const T* __restrict_
   }
   // reduce over the rows of the warp (lanes with equal column)
 #pragma unroll
-  for (int a = 0; a < kMaxVecPerWarp; ++a) {
+  for (int a = 0; a < kDotVecPerWarp; ++a) {
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
       double x = acc[a][q].x, y = acc[a][q].y;
@@ -140,7 +146,7 @@ __global__ void __launch_bounds__(kThreads) cgs_dots_kernel(const T* __restrict_
   if (lrow == 0 && active_c) {
     const int64_t p = (int64_t)blockIdx.x * S + slot;
 #pragma unroll
-    for (int a = 0; a < kMaxVecPerWarp; ++a) {
+    for (int a = 0; a < kDotVecPerWarp; ++a) {
       if (a < nmine) {
         const int i = i_first + a * i_step;
 #pragma unroll
@@ -448,17 +454,16 @@ template <typename T>
 int dots_launch(const T* V, int64_t vstride, int nvec, const T* w, int64_t E, int R, double2* part, cudaStream_t s) {
   note_launch(1);
   Shape sh = shape_for(R);
-  const int S = nvec >= kWarps ? 1 : kWarps / nvec;
-  const size_t smem = 0;
+  const int S = nvec >= kDotWarps ? 1 : kDotWarps / nvec;
   switch (sh.cpl) {
     case 1:
-      cgs_dots_kernel<T, 1><<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
+      cgs_dots_kernel<T, 1><<<kBlocks, kDotThreads, 0, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
       break;
     case 2:
-      cgs_dots_kernel<T, 2><<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
+      cgs_dots_kernel<T, 2><<<kBlocks, kDotThreads, 0, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
       break;
     default:
-      cgs_dots_kernel<T, 4><<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
+      cgs_dots_kernel<T, 4><<<kBlocks, kDotThreads, 0, s>>>(V, vstride, nvec, w, E, R, sh.tpr_log2, S, part);
       break;
   }
   return kBlocks * S;

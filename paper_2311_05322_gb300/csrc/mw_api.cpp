@@ -328,6 +328,7 @@ int read_active(Ctx* c) {
 
 struct BlockStats {
   int outer = 0, steps = 0;
+  bool have_relres = false;  // the last action was a residual check of the final x
 };
 
 // Solve A_f X = B for a block of R columns ([E][R] layout, FP64 in and out).
@@ -365,7 +366,9 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
     mwk::count_active(w.done, R, w.active, s);
     check_launch("cycle start");
     st.outer++;
+    st.have_relres = true;
     if (read_active(c) == 0 || total >= o.max_it) break;
+    st.have_relres = false;
     if (wp == 0)
       mwk::normalize_start_f64(w.r, w.rnorm, w.done, E, R, (double2*)Vp(0), s);
     else
@@ -425,7 +428,23 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
     for (int q = 0; q < R; ++q) its[q] += w.h_ivec[q];
   }
   its_out = its;
+  if (!st.have_relres) {
+    // the loop ended after an update: measure the final residual
+    nb = mwk::residual_f64(c->d_row, c->d_col, c->A64[f], X, B, w.r, w.npart, E, R, s);
+    mwk::reduce_cols(w.npart, nb, R, w.rnorm, s);
+    mwk::sqrt_inplace(w.rnorm, R, s);
+  }
   return st;
+}
+
+// True relative residuals of the block after solve_block (w.rnorm / w.bnorm, both sqrt'ed).
+void block_relres(Ctx* c, int R, double* rel) {
+  Work& w = c->work;
+  std::vector<double> a(R), b(R);
+  CK(cudaMemcpyAsync(a.data(), w.rnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(b.data(), w.bnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int q = 0; q < R; ++q) rel[q] = b[q] > 0 ? a[q] / b[q] : a[q];
 }
 
 // final true relative residuals of a block (FP64), into rel[R] on the host
@@ -484,7 +503,7 @@ void solve_all(Ctx* c, const mw_solve_opts& o, int ncols, const std::vector<cons
         BlockStats bs = solve_block(c, f, R, B, X, o, its);
         outer += bs.outer;
         steps += bs.steps;
-        true_relres(c, f, R, B, X, rel_all.data() + f * ncols + c0);
+        block_relres(c, R, rel_all.data() + f * ncols + c0);
       } else {
         ensure_work(c, R, o.restart, o.mode == MW_MODE_FP64 ? 0 : 1);
         Work& w = c->work;
@@ -494,7 +513,7 @@ void solve_all(Ctx* c, const mw_solve_opts& o, int ncols, const std::vector<cons
         BlockStats bs = solve_block(c, f, R, w.bblk, w.x, o, its);
         outer += bs.outer;
         steps += bs.steps;
-        true_relres(c, f, R, w.bblk, w.x, rel_all.data() + f * ncols + c0);
+        block_relres(c, R, rel_all.data() + f * ncols + c0);
         CK(cudaMemcpy2DAsync(X, sizeof(double2) * ncols, w.x, sizeof(double2) * R, sizeof(double2) * R, E,
                              cudaMemcpyDeviceToDevice, s));
       }
