@@ -215,6 +215,41 @@ mw_status mw_invert(mw_ctx* ctx, const mw_inv_opts* opts, const mw_solve_opts* s
                     const double* S_obs, const double* S_empty, double* eps_inout,
                     mw_inv_history* hist);
 
+/* ---- learned initialiser (BASELINE config 5; the paper has no learned part) ----------- */
+/* Network: x [n_in] -> relu(W1 x + b1) -> relu(W2 . + b2) (1024 wide) -> reshape 16x4x4x4 ->
+ * convT(16->16) -> relu -> convT(16->8) -> relu -> convT(8->2) -> [2][32][32][32] (Re, Im of
+ * Delta eps on a grid); convT = 3D transposed convolution, kernel 4, stride 2, padding 1.
+ * W1 and W2 are applied in BF16, every sum accumulates in FP32.  Parameters are one flat FP32
+ * vector: W1 [1024][n_in], b1, W2 [1024][1024], b2, C1 [16][16][4][4][4], c1, C2 [16][8][..],
+ * c2, C3 [8][2][..], c3.  Initial values are the caller's (random draws stay outside). */
+typedef struct {
+  int32_t batch;       /* minibatch size */
+  int32_t epochs;
+  float lr, beta1, beta2, eps;   /* Adam */
+  uint64_t seed;       /* splitmix64 seed of the per-epoch shuffles */
+} mw_nn_opts;
+typedef struct {
+  int32_t epochs_run;
+  double* epoch_loss;  /* [epochs] mean training loss per epoch, or NULL */
+  double seconds;      /* device time of the training loop */
+} mw_nn_stats;
+/* Number of parameters for an input width (-1 if invalid). */
+int64_t mw_nn_param_count(int32_t n_in);
+/* (Re)create the network with parameters theta (host FP32, copied). Resets Adam. */
+mw_status mw_nn_init(mw_ctx* ctx, int32_t n_in, const float* theta);
+mw_status mw_nn_get_params(mw_ctx* ctx, float* theta);
+/* Mean-squared-error loss of the network on n samples (x [n][n_in], t [n][2][32][32][32], host)
+ * and its gradient with respect to the parameters (host, may be NULL). */
+mw_status mw_nn_loss_grad(mw_ctx* ctx, int64_t n, const float* x, const float* t, double* loss, float* grad);
+/* Minibatch Adam training on n samples (host arrays, copied to the device once). */
+mw_status mw_nn_train(mw_ctx* ctx, const mw_nn_opts* opts, int64_t n, const float* x, const float* t,
+                      mw_nn_stats* stats);
+/* Network outputs y [n][2][32][32][32] for inputs x [n][n_in] (host). */
+mw_status mw_nn_infer(mw_ctx* ctx, int64_t n, const float* x, float* y);
+/* Trilinear samples of a cell-centred grid [2][G][G][G] over box {lo x,y,z, hi x,y,z} at the tet
+ * centroids of the context's mesh (0 outside the box): deps [n_tet][2] (host). */
+mw_status mw_nn_grid_to_tets(mw_ctx* ctx, const float* grid, int32_t G, const double* box, double* deps);
+
 /* ---- device-resident variants (same operations, device pointers) ------------------- */
 /* mw_assemble with eps_r on the device ([n_tet][2] doubles); needs a prior mw_assemble with the
  * same number of frequencies (which sized the matrices). */

@@ -1,0 +1,393 @@
+// Learned initialiser (BASELINE config 5; no counterpart in the paper): forward and backward
+// kernels of  x -> relu(W1 x + b1) -> relu(W2 . + b2) -> reshape 16x4^3 -> convT(16->16) -> relu
+// -> convT(16->8) -> relu -> convT(8->2) -> 32^3 x 2,  convT = 3D transposed convolution with
+// kernel 4, stride 2, padding 1:  out[co][o] = b[co] + sum_ci sum_k in[ci][i] w[ci][co][k],
+// o = 2 i - 1 + k per axis.  W1, W2 are read as BF16, everything accumulates in FP32.  All
+// reductions are deterministic (fixed per-thread order, fixed trees, no atomics).
+#include <cuda_bf16.h>
+
+#include "k_nn.h"
+#include "mw_internal.h"
+
+namespace mwk {
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16;
+
+template <typename TB>
+__device__ __forceinline__ float ldb(const TB* p) {
+  return (float)*p;
+}
+template <>
+__device__ __forceinline__ float ldb<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+
+// C[m][n] = sum_k A(m, k) B(k, n) (+ bias[n]); A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn].
+// Optional ReLU copy H.  64 x 64 tiles, 4 x 4 outputs per thread.
+template <typename TB>
+__global__ void __launch_bounds__(256) gemm_kernel(const float* __restrict__ A, int64_t sam, int64_t sak,
+                                                   const TB* __restrict__ B, int64_t sbk, int64_t sbn,
+                                                   const float* __restrict__ bias, float* __restrict__ C,
+                                                   float* __restrict__ H, int M, int N, int Kd) {
+  __shared__ float As[TK][TM + 1];
+  __shared__ float Bs[TK][TN + 1];
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < Kd; k0 += TK) {
+    for (int e = threadIdx.x; e < TK * TM; e += 256) {
+      // consecutive threads walk the contiguous axis of each operand
+      int k, m;
+      if (sak == 1) {
+        k = e % TK;
+        m = e / TK;
+      } else {
+        m = e % TM;
+        k = e / TM;
+      }
+      const int gm = m0 + m, gk = k0 + k;
+      As[k][m] = (gm < M && gk < Kd) ? A[(int64_t)gm * sam + (int64_t)gk * sak] : 0.f;
+    }
+    for (int e = threadIdx.x; e < TK * TN; e += 256) {
+      int k, n;
+      if (sbk == 1) {
+        k = e % TK;
+        n = e / TK;
+      } else {
+        n = e % TN;
+        k = e / TN;
+      }
+      const int gn = n0 + n, gk = k0 + k;
+      Bs[k][n] = (gn < N && gk < Kd) ? ldb(B + (int64_t)gk * sbk + (int64_t)gn * sbn) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < TK; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][tr + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tc + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + tr + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tc + 16 * j;
+      if (gn >= N) continue;
+      const float v = acc[i][j] + (bias ? bias[gn] : 0.f);
+      C[(int64_t)gm * N + gn] = v;
+      if (H) H[(int64_t)gm * N + gn] = v > 0.f ? v : 0.f;
+    }
+  }
+}
+
+// Column sums of dZ [B][N] -> db [N] (fixed order).
+__global__ void colsum_kernel(const float* __restrict__ dz, int B, int N, float* __restrict__ db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s += dz[(int64_t)b * N + n];
+  db[n] = s;
+}
+
+__global__ void relu_back_kernel(const float* __restrict__ z, const float* __restrict__ dh, float* __restrict__ dz,
+                                 int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dz[i] = z[i] > 0.f ? dh[i] : 0.f;
+}
+
+// convT forward, gather form: one thread per output; per axis the inputs i with o = 2i - 1 + k
+// are i = (o + 1 - k) / 2 for the two k of matching parity.
+__global__ void convT_fwd_kernel(const float* __restrict__ x, const float* __restrict__ w, const float* __restrict__ b,
+                                 float* __restrict__ a, float* __restrict__ g, int B, int Ci, int Co, int D) {
+  const int Do = 2 * D;
+  const int64_t total = (int64_t)B * Co * Do * Do * Do;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = t;
+    const int ox = (int)(r % Do);
+    r /= Do;
+    const int oy = (int)(r % Do);
+    r /= Do;
+    const int oz = (int)(r % Do);
+    r /= Do;
+    const int co = (int)(r % Co);
+    const int bb = (int)(r / Co);
+    float s = b[co];
+    for (int ci = 0; ci < Ci; ++ci) {
+      const float* xc = x + ((int64_t)bb * Ci + ci) * D * D * D;
+      const float* wc = w + ((int64_t)ci * Co + co) * 64;
+      for (int kz = (oz + 1) & 1; kz < 4; kz += 2) {
+        const int iz = (oz + 1 - kz) >> 1;
+        if (iz < 0 || iz >= D) continue;
+        for (int ky = (oy + 1) & 1; ky < 4; ky += 2) {
+          const int iy = (oy + 1 - ky) >> 1;
+          if (iy < 0 || iy >= D) continue;
+          for (int kx = (ox + 1) & 1; kx < 4; kx += 2) {
+            const int ix = (ox + 1 - kx) >> 1;
+            if (ix < 0 || ix >= D) continue;
+            s = fmaf(xc[(iz * D + iy) * D + ix], wc[(kz * 4 + ky) * 4 + kx], s);
+          }
+        }
+      }
+    }
+    a[t] = s;
+    if (g) g[t] = s > 0.f ? s : 0.f;
+  }
+}
+
+// convT backward-data: dx[b][ci][i] = sum_co sum_k w[ci][co][k] dy[b][co][2i - 1 + k].
+__global__ void convT_bwd_data_kernel(const float* __restrict__ dy, const float* __restrict__ w,
+                                      float* __restrict__ dx, int B, int Ci, int Co, int D) {
+  const int Do = 2 * D;
+  const int64_t total = (int64_t)B * Ci * D * D * D;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = t;
+    const int ix = (int)(r % D);
+    r /= D;
+    const int iy = (int)(r % D);
+    r /= D;
+    const int iz = (int)(r % D);
+    r /= D;
+    const int ci = (int)(r % Ci);
+    const int bb = (int)(r / Ci);
+    float s = 0.f;
+    for (int co = 0; co < Co; ++co) {
+      const float* yc = dy + ((int64_t)bb * Co + co) * Do * Do * Do;
+      const float* wc = w + ((int64_t)ci * Co + co) * 64;
+      for (int kz = 0; kz < 4; ++kz) {
+        const int oz = 2 * iz - 1 + kz;
+        if (oz < 0 || oz >= Do) continue;
+        for (int ky = 0; ky < 4; ++ky) {
+          const int oy = 2 * iy - 1 + ky;
+          if (oy < 0 || oy >= Do) continue;
+          for (int kx = 0; kx < 4; ++kx) {
+            const int ox = 2 * ix - 1 + kx;
+            if (ox < 0 || ox >= Do) continue;
+            s = fmaf(yc[(oz * Do + oy) * Do + ox], wc[(kz * 4 + ky) * 4 + kx], s);
+          }
+        }
+      }
+    }
+    dx[t] = s;
+  }
+}
+
+// convT backward-weights: one block per (ci, co, k); threads over (b, i); tree reduction.
+__global__ void convT_bwd_w_kernel(const float* __restrict__ x, const float* __restrict__ dy, float* __restrict__ dw,
+                                   int B, int Ci, int Co, int D) {
+  __shared__ float red[256];
+  const int widx = blockIdx.x;
+  const int k = widx % 64, co = (widx / 64) % Co, ci = widx / (64 * Co);
+  const int kz = k / 16, ky = (k / 4) % 4, kx = k % 4;
+  const int Do = 2 * D;
+  const int64_t total = (int64_t)B * D * D * D;
+  float s = 0.f;
+  for (int64_t t = threadIdx.x; t < total; t += 256) {
+    int64_t r = t;
+    const int ix = (int)(r % D);
+    r /= D;
+    const int iy = (int)(r % D);
+    r /= D;
+    const int iz = (int)(r % D);
+    const int bb = (int)(r / D);
+    const int oz = 2 * iz - 1 + kz, oy = 2 * iy - 1 + ky, ox = 2 * ix - 1 + kx;
+    if (oz < 0 || oz >= Do || oy < 0 || oy >= Do || ox < 0 || ox >= Do) continue;
+    s = fmaf(x[(((int64_t)bb * Ci + ci) * D + iz) * D * D + iy * D + ix],
+             dy[(((int64_t)bb * Co + co) * Do + oz) * Do * Do + oy * Do + ox], s);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dw[widx] = red[0];
+}
+
+// per-channel sums of dy [B][Co][V] -> db [Co]; one block per channel, tree reduction.
+__global__ void chansum_kernel(const float* __restrict__ dy, int B, int Co, int64_t V, float* __restrict__ db) {
+  __shared__ float red[256];
+  const int co = blockIdx.x;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b)
+    for (int64_t v = threadIdx.x; v < V; v += 256) s += dy[((int64_t)b * Co + co) * V + v];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[co] = red[0];
+}
+
+// MSE: dy = 2 (y - t) / n, per-block partial sums of (y - t)^2 in FP64.
+__global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ t, int64_t n, float* __restrict__ dy,
+                           double* __restrict__ part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  const float sc = 2.0f / (float)n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float d = y[i] - t[i];
+    dy[i] = sc * d;
+    s += (double)d * d;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void sum_parts_kernel(const double* __restrict__ part, int n, double scale, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0] * scale;
+}
+
+// Adam (Kingma & Ba) with bias correction; bc1 = 1 - b1^t, bc2 = 1 - b2^t.
+__global__ void adam_kernel(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float bc1,
+                            float bc2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    th[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16_rn(a[i]);
+}
+
+__global__ void gather_rows_kernel(const float* __restrict__ src, const int32_t* __restrict__ idx, int n,
+                                   int64_t width, float* __restrict__ dst) {
+  const int64_t total = (int64_t)n * width;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / width, c = t % width;
+    dst[t] = src[(int64_t)idx[r] * width + c];
+  }
+}
+
+// Trilinear sample of a [2][G][G][G] grid (cell-centred on box [lo, hi]) at tet centroids;
+// outside the box the value is 0.  out [T][2] += (Re, Im).
+__global__ void grid_to_tets_kernel(const float* __restrict__ grid, int G, double lx, double ly, double lz, double hx,
+                                    double hy, double hz, const double* __restrict__ xyz,
+                                    const int32_t* __restrict__ tets, int64_t T, double* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  double c[3] = {0, 0, 0};
+  for (int v = 0; v < 4; ++v)
+    for (int d = 0; d < 3; ++d) c[d] += 0.25 * xyz[3 * (int64_t)tets[4 * t + v] + d];
+  const double lo[3] = {lx, ly, lz}, hi[3] = {hx, hy, hz};
+  double f[3];
+  int i0[3];
+  for (int d = 0; d < 3; ++d) {
+    if (c[d] < lo[d] || c[d] > hi[d]) return;
+    const double u = (c[d] - lo[d]) / (hi[d] - lo[d]) * G - 0.5;   // cell-centred coordinate
+    double fl = floor(u);
+    fl = fmin(fmax(fl, 0.0), (double)(G - 2));
+    i0[d] = (int)fl;
+    f[d] = fmin(fmax(u - fl, 0.0), 1.0);
+  }
+  for (int ch = 0; ch < 2; ++ch) {
+    double s = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const double wgt = (dz ? f[2] : 1 - f[2]) * (dy ? f[1] : 1 - f[1]) * (dx ? f[0] : 1 - f[0]);
+          s += wgt * grid[(((int64_t)ch * G + i0[2] + dz) * G + i0[1] + dy) * G + i0[0] + dx];
+        }
+    out[2 * t + ch] += s;
+  }
+}
+
+inline int gsb(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+}
+
+}  // namespace
+
+void nn_gemm_bf16(const float* A, int64_t sam, int64_t sak, const void* Bw, int64_t sbk, int64_t sbn,
+                  const float* bias, float* C, float* H, int M, int N, int K, cudaStream_t s) {
+  note_launch(1);
+  dim3 g((N + TN - 1) / TN, (M + TM - 1) / TM);
+  gemm_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(A, sam, sak, (const __nv_bfloat16*)Bw, sbk, sbn, bias, C, H, M, N, K);
+}
+void nn_gemm_f32(const float* A, int64_t sam, int64_t sak, const float* Bf, int64_t sbk, int64_t sbn,
+                 const float* bias, float* C, float* H, int M, int N, int K, cudaStream_t s) {
+  note_launch(1);
+  dim3 g((N + TN - 1) / TN, (M + TM - 1) / TM);
+  gemm_kernel<float><<<g, 256, 0, s>>>(A, sam, sak, Bf, sbk, sbn, bias, C, H, M, N, K);
+}
+void nn_colsum(const float* dz, int B, int N, float* db, cudaStream_t s) {
+  note_launch(1);
+  colsum_kernel<<<(N + 255) / 256, 256, 0, s>>>(dz, B, N, db);
+}
+void nn_relu_back(const float* z, const float* dh, float* dz, int64_t n, cudaStream_t s) {
+  note_launch(1);
+  relu_back_kernel<<<gsb(n), 256, 0, s>>>(z, dh, dz, n);
+}
+void nn_convT_fwd(const float* x, const float* w, const float* b, float* a, float* g, int B, int Ci, int Co, int D,
+                  cudaStream_t s) {
+  note_launch(1);
+  convT_fwd_kernel<<<gsb((int64_t)B * Co * 8 * D * D * D), 256, 0, s>>>(x, w, b, a, g, B, Ci, Co, D);
+}
+void nn_convT_bwd(const float* x, const float* w, const float* dy, float* dx, float* dw, float* db, int B, int Ci,
+                  int Co, int D, cudaStream_t s) {
+  note_launch(dx ? 3 : 2);
+  if (dx) convT_bwd_data_kernel<<<gsb((int64_t)B * Ci * D * D * D), 256, 0, s>>>(dy, w, dx, B, Ci, Co, D);
+  convT_bwd_w_kernel<<<Ci * Co * 64, 256, 0, s>>>(x, dy, dw, B, Ci, Co, D);
+  chansum_kernel<<<Co, 256, 0, s>>>(dy, B, Co, (int64_t)8 * D * D * D, db);
+}
+void nn_mse(const float* y, const float* t, int64_t n, float* dy, double* part, double* loss, cudaStream_t s) {
+  note_launch(2);
+  const int nb = 256;
+  mse_kernel<<<nb, 256, 0, s>>>(y, t, n, dy, part);
+  sum_parts_kernel<<<1, 256, 0, s>>>(part, nb, 1.0 / (double)n, loss);
+}
+void nn_adam(float* th, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps, int step,
+             cudaStream_t s) {
+  note_launch(1);
+  const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
+  adam_kernel<<<gsb(n), 256, 0, s>>>(th, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
+}
+void nn_to_bf16(const float* a, void* b, int64_t n, cudaStream_t s) {
+  note_launch(1);
+  to_bf16_kernel<<<gsb(n), 256, 0, s>>>(a, (__nv_bfloat16*)b, n);
+}
+void nn_gather_rows(const float* src, const int32_t* idx, int n, int64_t width, float* dst, cudaStream_t s) {
+  note_launch(1);
+  gather_rows_kernel<<<gsb((int64_t)n * width), 256, 0, s>>>(src, idx, n, width, dst);
+}
+void nn_grid_to_tets(const float* grid, int G, const double* box, const double* xyz, const int32_t* tets, int64_t T,
+                     double* out, cudaStream_t s) {
+  note_launch(1);
+  grid_to_tets_kernel<<<(unsigned)((T + 127) / 128), 128, 0, s>>>(grid, G, box[0], box[1], box[2], box[3], box[4],
+                                                                   box[5], xyz, tets, T, out);
+}
+
+}  // namespace mwk

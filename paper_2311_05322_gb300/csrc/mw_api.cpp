@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "k_adjoint.h"
+#include "k_nn.h"
 #include "k_oras.h"
 #include "k_oras_tc.h"
 #include "mw_internal.h"
@@ -95,9 +96,31 @@ struct Profiler {
   }
 };
 
+// Learned-initialiser state: FP32 master parameters, BF16 copies of W1/W2, Adam moments,
+// activations and gradients for up to `bcap` samples, and the resident training set.
+struct NnState {
+  int n_in = 0;
+  int64_t np = 0;
+  int bcap = 0;
+  int step = 0;
+  float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+  void *W1b = nullptr, *W2b = nullptr;
+  float *x = nullptr, *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *a1 = nullptr, *g1 = nullptr,
+        *a2 = nullptr, *g2 = nullptr, *y = nullptr, *t = nullptr;
+  float *dy = nullptr, *dg2 = nullptr, *da2 = nullptr, *dg1 = nullptr, *da1 = nullptr, *dh2 = nullptr,
+        *dz2 = nullptr, *dh1 = nullptr, *dz1 = nullptr;
+  double *part = nullptr, *loss = nullptr;
+  float *data_x = nullptr, *data_t = nullptr;
+  int64_t data_n = 0;
+  int32_t* idx = nullptr;
+  // parameter offsets (floats) in the flat layout W1 b1 W2 b2 C1 c1 C2 c2 C3 c3
+  int64_t oW1, ob1, oW2, ob2, oC1, oc1, oC2, oc2, oC3, oc3;
+};
+
 struct Ctx {
   int device = 0;
   Profiler prof;
+  NnState nn;
   cudaStream_t stream = nullptr;
   std::string err;
   int64_t mem_cap = 0, mem_used = 0;
@@ -1503,6 +1526,256 @@ mw_status mw_apply_preconditioner_noalloc(mw_ctx* c, int32_t f, const void* r, v
     mwk::oras_apply_tc(c->prec.tc, c->prec.topo(), c->prec.W[f], (const float2*)r, (float2*)z, n_cols, scratch,
                        c->stream);
     check_launch("allocation-free preconditioner apply");
+  });
+}
+
+
+// =======================================================================================
+// Learned initialiser (BASELINE config 5): MLP + transposed-convolution decoder
+// =======================================================================================
+static constexpr int kHid = 1024, kG = 32, kOut = 2 * kG * kG * kG;
+
+int64_t mw_nn_param_count(int32_t n_in) {
+  if (n_in <= 0) return -1;
+  return (int64_t)kHid * n_in + kHid + (int64_t)kHid * kHid + kHid + 16 * 16 * 64 + 16 + 16 * 8 * 64 + 8 + 8 * 2 * 64 +
+         2;
+}
+
+static void nn_free(Ctx* c) {
+  NnState& n = c->nn;
+  for (void* p : {(void*)n.theta, (void*)n.grad, (void*)n.m, (void*)n.v, n.W1b, n.W2b, (void*)n.x, (void*)n.z1,
+                  (void*)n.h1, (void*)n.z2, (void*)n.h2, (void*)n.a1, (void*)n.g1, (void*)n.a2, (void*)n.g2,
+                  (void*)n.y, (void*)n.t, (void*)n.dy, (void*)n.dg2, (void*)n.da2, (void*)n.dg1, (void*)n.da1,
+                  (void*)n.dh2, (void*)n.dz2, (void*)n.dh1, (void*)n.dz1, (void*)n.part, (void*)n.loss,
+                  (void*)n.data_x, (void*)n.data_t, (void*)n.idx})
+    dfree(c, p);
+  n = NnState();
+}
+
+static void nn_batch_buffers(Ctx* c, int B) {
+  NnState& n = c->nn;
+  if (B <= n.bcap) return;
+  for (void* p : {(void*)n.x, (void*)n.z1, (void*)n.h1, (void*)n.z2, (void*)n.h2, (void*)n.a1, (void*)n.g1, (void*)n.a2,
+                  (void*)n.g2, (void*)n.y, (void*)n.t, (void*)n.dy, (void*)n.dg2, (void*)n.da2, (void*)n.dg1,
+                  (void*)n.da1, (void*)n.dh2, (void*)n.dz2, (void*)n.dh1, (void*)n.dz1, (void*)n.idx})
+    dfree(c, p);
+  n.x = dalloc<float>(c, (size_t)B * n.n_in);
+  n.z1 = dalloc<float>(c, (size_t)B * kHid);
+  n.h1 = dalloc<float>(c, (size_t)B * kHid);
+  n.z2 = dalloc<float>(c, (size_t)B * kHid);
+  n.h2 = dalloc<float>(c, (size_t)B * kHid);
+  n.a1 = dalloc<float>(c, (size_t)B * 16 * 512);
+  n.g1 = dalloc<float>(c, (size_t)B * 16 * 512);
+  n.a2 = dalloc<float>(c, (size_t)B * 8 * 4096);
+  n.g2 = dalloc<float>(c, (size_t)B * 8 * 4096);
+  n.y = dalloc<float>(c, (size_t)B * kOut);
+  n.t = dalloc<float>(c, (size_t)B * kOut);
+  n.dy = dalloc<float>(c, (size_t)B * kOut);
+  n.dg2 = dalloc<float>(c, (size_t)B * 8 * 4096);
+  n.da2 = dalloc<float>(c, (size_t)B * 8 * 4096);
+  n.dg1 = dalloc<float>(c, (size_t)B * 16 * 512);
+  n.da1 = dalloc<float>(c, (size_t)B * 16 * 512);
+  n.dh2 = dalloc<float>(c, (size_t)B * kHid);
+  n.dz2 = dalloc<float>(c, (size_t)B * kHid);
+  n.dh1 = dalloc<float>(c, (size_t)B * kHid);
+  n.dz1 = dalloc<float>(c, (size_t)B * kHid);
+  n.idx = dalloc<int32_t>(c, (size_t)B);
+  n.bcap = B;
+}
+
+static void nn_refresh_bf16(Ctx* c) {
+  NnState& n = c->nn;
+  mwk::nn_to_bf16(n.theta + n.oW1, n.W1b, (int64_t)kHid * n.n_in, c->stream);
+  mwk::nn_to_bf16(n.theta + n.oW2, n.W2b, (int64_t)kHid * kHid, c->stream);
+}
+
+// forward on n.x[0..B) -> n.y
+static void nn_forward(Ctx* c, int B) {
+  NnState& n = c->nn;
+  const float* th = n.theta;
+  cudaStream_t s = c->stream;
+  mwk::nn_gemm_bf16(n.x, n.n_in, 1, n.W1b, 1, n.n_in, th + n.ob1, n.z1, n.h1, B, kHid, n.n_in, s);
+  mwk::nn_gemm_bf16(n.h1, kHid, 1, n.W2b, 1, kHid, th + n.ob2, n.z2, n.h2, B, kHid, kHid, s);
+  mwk::nn_convT_fwd(n.h2, th + n.oC1, th + n.oc1, n.a1, n.g1, B, 16, 16, 4, s);
+  mwk::nn_convT_fwd(n.g1, th + n.oC2, th + n.oc2, n.a2, n.g2, B, 16, 8, 8, s);
+  mwk::nn_convT_fwd(n.g2, th + n.oC3, th + n.oc3, n.y, nullptr, B, 8, 2, 16, s);
+}
+
+// loss against n.t and gradient into n.grad
+static void nn_backward(Ctx* c, int B) {
+  NnState& n = c->nn;
+  const float* th = n.theta;
+  float* g = n.grad;
+  cudaStream_t s = c->stream;
+  mwk::nn_mse(n.y, n.t, (int64_t)B * kOut, n.dy, n.part, n.loss, s);
+  mwk::nn_convT_bwd(n.g2, th + n.oC3, n.dy, n.dg2, g + n.oC3, g + n.oc3, B, 8, 2, 16, s);
+  mwk::nn_relu_back(n.a2, n.dg2, n.da2, (int64_t)B * 8 * 4096, s);
+  mwk::nn_convT_bwd(n.g1, th + n.oC2, n.da2, n.dg1, g + n.oC2, g + n.oc2, B, 16, 8, 8, s);
+  mwk::nn_relu_back(n.a1, n.dg1, n.da1, (int64_t)B * 16 * 512, s);
+  mwk::nn_convT_bwd(n.h2, th + n.oC1, n.da1, n.dh2, g + n.oC1, g + n.oc1, B, 16, 16, 4, s);
+  mwk::nn_relu_back(n.z2, n.dh2, n.dz2, (int64_t)B * kHid, s);
+  mwk::nn_gemm_f32(n.dz2, 1, kHid, n.h1, kHid, 1, nullptr, g + n.oW2, nullptr, kHid, kHid, B, s);
+  mwk::nn_colsum(n.dz2, B, kHid, g + n.ob2, s);
+  mwk::nn_gemm_bf16(n.dz2, kHid, 1, n.W2b, kHid, 1, nullptr, n.dh1, nullptr, B, kHid, kHid, s);
+  mwk::nn_relu_back(n.z1, n.dh1, n.dz1, (int64_t)B * kHid, s);
+  mwk::nn_gemm_f32(n.dz1, 1, kHid, n.x, n.n_in, 1, nullptr, g + n.oW1, nullptr, kHid, n.n_in, B, s);
+  mwk::nn_colsum(n.dz1, B, kHid, g + n.ob1, s);
+}
+
+mw_status mw_nn_init(mw_ctx* c, int32_t n_in, const float* theta) {
+  return guard(c, [&] {
+    require(n_in >= 1 && n_in <= (1 << 20) && theta, MW_EINVAL, "bad network arguments");
+    nn_free(c);
+    NnState& n = c->nn;
+    n.n_in = n_in;
+    n.np = mw_nn_param_count(n_in);
+    int64_t o = 0;
+    n.oW1 = o; o += (int64_t)kHid * n_in;
+    n.ob1 = o; o += kHid;
+    n.oW2 = o; o += (int64_t)kHid * kHid;
+    n.ob2 = o; o += kHid;
+    n.oC1 = o; o += 16 * 16 * 64;
+    n.oc1 = o; o += 16;
+    n.oC2 = o; o += 16 * 8 * 64;
+    n.oc2 = o; o += 8;
+    n.oC3 = o; o += 8 * 2 * 64;
+    n.oc3 = o; o += 2;
+    for (int64_t i = 0; i < n.np; ++i) require(std::isfinite(theta[i]), MW_EINVAL, "non-finite parameter");
+    n.theta = upload(c, theta, n.np);
+    n.grad = dalloc<float>(c, n.np);
+    n.m = dalloc<float>(c, n.np);
+    n.v = dalloc<float>(c, n.np);
+    CK(cudaMemsetAsync(n.m, 0, sizeof(float) * n.np, c->stream));
+    CK(cudaMemsetAsync(n.v, 0, sizeof(float) * n.np, c->stream));
+    n.W1b = dalloc<uint16_t>(c, (size_t)kHid * n_in);
+    n.W2b = dalloc<uint16_t>(c, (size_t)kHid * kHid);
+    n.part = dalloc<double>(c, 256);
+    n.loss = dalloc<double>(c, 1);
+    nn_refresh_bf16(c);
+    check_launch("nn init");
+    CK(cudaStreamSynchronize(c->stream));
+  });
+}
+
+mw_status mw_nn_get_params(mw_ctx* c, float* theta) {
+  return guard(c, [&] {
+    require(c->nn.theta && theta, MW_ESTATE, "network not initialised");
+    CK(cudaMemcpyAsync(theta, c->nn.theta, sizeof(float) * c->nn.np, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  });
+}
+
+mw_status mw_nn_loss_grad(mw_ctx* c, int64_t nsamp, const float* x, const float* t, double* loss, float* grad) {
+  return guard(c, [&] {
+    NnState& n = c->nn;
+    require(n.theta, MW_ESTATE, "network not initialised");
+    require(nsamp >= 1 && nsamp <= 4096 && x && t && loss, MW_EINVAL, "bad arguments");
+    nn_batch_buffers(c, (int)nsamp);
+    CK(cudaMemcpyAsync(n.x, x, sizeof(float) * nsamp * n.n_in, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(n.t, t, sizeof(float) * nsamp * kOut, cudaMemcpyHostToDevice, c->stream));
+    nn_forward(c, (int)nsamp);
+    nn_backward(c, (int)nsamp);
+    check_launch("nn loss/grad");
+    CK(cudaMemcpyAsync(loss, n.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (grad) CK(cudaMemcpyAsync(grad, n.grad, sizeof(float) * n.np, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  });
+}
+
+static uint64_t splitmix64_next(uint64_t& st) {
+  st += 0x9E3779B97F4A7C15ull;
+  uint64_t z = st;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+mw_status mw_nn_train(mw_ctx* c, const mw_nn_opts* o, int64_t nsamp, const float* x, const float* t,
+                      mw_nn_stats* st) {
+  return guard(c, [&] {
+    NnState& n = c->nn;
+    require(n.theta, MW_ESTATE, "network not initialised");
+    require(o && nsamp >= 1 && x && t, MW_EINVAL, "bad training arguments");
+    require(o->batch >= 1 && o->batch <= 4096 && o->epochs >= 0 && o->lr > 0, MW_EINVAL, "bad training options");
+    for (auto p : {(void*)n.data_x, (void*)n.data_t}) dfree(c, p);
+    n.data_x = upload(c, x, (size_t)nsamp * n.n_in);
+    n.data_t = upload(c, t, (size_t)nsamp * kOut);
+    n.data_n = nsamp;
+    const int B = (int)std::min<int64_t>(o->batch, nsamp);
+    nn_batch_buffers(c, B);
+    std::vector<int32_t> perm(nsamp);
+    cudaEvent_t e0;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventRecord(e0, c->stream));
+    for (int ep = 0; ep < o->epochs; ++ep) {
+      uint64_t rs = o->seed + 0x632BE59BD9B4E019ull * (uint64_t)(ep + 1);
+      for (int64_t i = 0; i < nsamp; ++i) perm[i] = (int32_t)i;
+      for (int64_t i = nsamp - 1; i > 0; --i) {                 // Fisher-Yates
+        const int64_t j = (int64_t)(splitmix64_next(rs) % (uint64_t)(i + 1));
+        std::swap(perm[i], perm[j]);
+      }
+      double ep_loss = 0;
+      for (int64_t b0 = 0; b0 < nsamp; b0 += B) {
+        const int nb = (int)std::min<int64_t>(B, nsamp - b0);
+        CK(cudaMemcpyAsync(n.idx, perm.data() + b0, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, c->stream));
+        mwk::nn_gather_rows(n.data_x, n.idx, nb, n.n_in, n.x, c->stream);
+        mwk::nn_gather_rows(n.data_t, n.idx, nb, kOut, n.t, c->stream);
+        nn_forward(c, nb);
+        nn_backward(c, nb);
+        n.step++;
+        mwk::nn_adam(n.theta, n.grad, n.m, n.v, n.np, o->lr, o->beta1, o->beta2, o->eps, n.step, c->stream);
+        nn_refresh_bf16(c);
+        double l = 0;
+        CK(cudaMemcpyAsync(&l, n.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));   // perm slice and loss are host memory
+        ep_loss += l * nb;
+      }
+      check_launch("nn train");
+      if (st && st->epoch_loss) st->epoch_loss[ep] = ep_loss / (double)nsamp;
+    }
+    CK(cudaEventRecord(c->ev1, c->stream));
+    CK(cudaEventSynchronize(c->ev1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, c->ev1));
+    cudaEventDestroy(e0);
+    if (st) {
+      st->epochs_run = o->epochs;
+      st->seconds = ms * 1e-3;
+    }
+  });
+}
+
+mw_status mw_nn_infer(mw_ctx* c, int64_t nsamp, const float* x, float* y) {
+  return guard(c, [&] {
+    NnState& n = c->nn;
+    require(n.theta, MW_ESTATE, "network not initialised");
+    require(nsamp >= 1 && x && y, MW_EINVAL, "bad inference arguments");
+    const int B = (int)std::min<int64_t>(nsamp, 256);
+    nn_batch_buffers(c, B);
+    for (int64_t b0 = 0; b0 < nsamp; b0 += B) {
+      const int nb = (int)std::min<int64_t>(B, nsamp - b0);
+      CK(cudaMemcpyAsync(n.x, x + b0 * n.n_in, sizeof(float) * nb * n.n_in, cudaMemcpyHostToDevice, c->stream));
+      nn_forward(c, nb);
+      CK(cudaMemcpyAsync(y + b0 * kOut, n.y, sizeof(float) * nb * kOut, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+    check_launch("nn infer");
+  });
+}
+
+mw_status mw_nn_grid_to_tets(mw_ctx* c, const float* grid, int32_t G, const double* box, double* deps) {
+  return guard(c, [&] {
+    require(c->has_mesh && grid && box && deps && G >= 2 && G <= 1024, MW_EINVAL, "bad grid arguments");
+    const int64_t T = c->topo.n_tet;
+    float* dg = upload(c, grid, (size_t)2 * G * G * G);
+    double* out = dalloc<double>(c, 2 * T);
+    CK(cudaMemsetAsync(out, 0, sizeof(double) * 2 * T, c->stream));
+    mwk::nn_grid_to_tets(dg, G, box, c->d_xyz, c->d_tets, T, out, c->stream);
+    check_launch("grid to tets");
+    CK(cudaMemcpyAsync(deps, out, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c, dg);
+    dfree(c, out);
   });
 }
 

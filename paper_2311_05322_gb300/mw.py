@@ -44,6 +44,15 @@ class mw_solve_stats(C.Structure):
                 ("iters", C.POINTER(C.c_int32)), ("relres", C.POINTER(C.c_double))]
 
 
+class mw_nn_opts(C.Structure):
+    _fields_ = [("batch", C.c_int32), ("epochs", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64)]
+
+
+class mw_nn_stats(C.Structure):
+    _fields_ = [("epochs_run", C.c_int32), ("epoch_loss", C.POINTER(C.c_double)), ("seconds", C.c_double)]
+
+
 class mw_inv_opts(C.Structure):
     _fields_ = [("m", C.c_int32), ("max_it", C.c_int32), ("c1", C.c_double), ("max_ls", C.c_int32),
                 ("first_step", C.c_double), ("alpha", C.c_double), ("target_J", C.c_double)]
@@ -85,6 +94,13 @@ _SIGS = {
     "mw_profile_enable": (C.c_int32, [_P, C.c_uint32]),
     "mw_profile_read": (C.c_int32, [_P, _P, _P, _P]),
     "mw_apply_preconditioner_noalloc": (C.c_int32, [_P, C.c_int32, _P, _P, C.c_int32]),
+    "mw_nn_param_count": (C.c_int64, [C.c_int32]),
+    "mw_nn_init": (C.c_int32, [_P, C.c_int32, _P]),
+    "mw_nn_get_params": (C.c_int32, [_P, _P]),
+    "mw_nn_loss_grad": (C.c_int32, [_P, C.c_int64, _P, _P, C.POINTER(C.c_double), _P]),
+    "mw_nn_train": (C.c_int32, [_P, C.POINTER(mw_nn_opts), C.c_int64, _P, _P, C.POINTER(mw_nn_stats)]),
+    "mw_nn_infer": (C.c_int32, [_P, C.c_int64, _P, _P]),
+    "mw_nn_grid_to_tets": (C.c_int32, [_P, _P, C.c_int32, _P, _P]),
 }
 
 MW_K_SPMM, MW_K_ORAS, MW_K_CGS_DOTS, MW_K_CGS_UPDATE, MW_K_RESIDUAL, MW_K_NCLASS = range(6)
@@ -283,6 +299,48 @@ class Context:
         g = np.empty_like(e)
         self._check(self.lib.mw_tikhonov(self.h, _ptr(e), C.byref(R), _ptr(g)))
         return R.value, g
+
+    # -- learned initialiser -----------------------------------------------------------------
+    def nn_init(self, n_in: int, theta: np.ndarray):
+        th = _c(theta, np.float32)
+        assert th.size == self.lib.mw_nn_param_count(n_in)
+        self._check(self.lib.mw_nn_init(self.h, n_in, _ptr(th)))
+        self.nn_in = n_in
+
+    def nn_get_params(self) -> np.ndarray:
+        th = np.empty(self.lib.mw_nn_param_count(self.nn_in), np.float32)
+        self._check(self.lib.mw_nn_get_params(self.h, _ptr(th)))
+        return th
+
+    def nn_loss_grad(self, x, t):
+        x = _c(x, np.float32)
+        t = _c(t, np.float32)
+        L = C.c_double()
+        g = np.empty(self.lib.mw_nn_param_count(self.nn_in), np.float32)
+        self._check(self.lib.mw_nn_loss_grad(self.h, x.shape[0], _ptr(x), _ptr(t), C.byref(L), _ptr(g)))
+        return L.value, g
+
+    def nn_train(self, x, t, batch=64, epochs=10, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=1):
+        x = _c(x, np.float32)
+        t = _c(t, np.float32)
+        losses = np.zeros(max(epochs, 1))
+        st = mw_nn_stats(0, losses.ctypes.data_as(C.POINTER(C.c_double)), 0.0)
+        o = mw_nn_opts(batch, epochs, lr, beta1, beta2, eps, seed)
+        self._check(self.lib.mw_nn_train(self.h, C.byref(o), x.shape[0], _ptr(x), _ptr(t), C.byref(st)))
+        return losses[:epochs].copy(), st.seconds
+
+    def nn_infer(self, x) -> np.ndarray:
+        x = _c(x, np.float32)
+        y = np.empty((x.shape[0], 2, 32, 32, 32), np.float32)
+        self._check(self.lib.mw_nn_infer(self.h, x.shape[0], _ptr(x), _ptr(y)))
+        return y
+
+    def nn_grid_to_tets(self, grid, box) -> np.ndarray:
+        g = _c(grid, np.float32)
+        b = _c(box, np.float64)
+        out = np.empty((self.info.n_tet, 2))
+        self._check(self.lib.mw_nn_grid_to_tets(self.h, _ptr(g), g.shape[-1], _ptr(b), _ptr(out)))
+        return out
 
     # -- device-resident variants -----------------------------------------------------------
     def assemble_dev(self, freqs, eps_dev, eps_bg: complex):
