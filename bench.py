@@ -48,6 +48,8 @@ def _args(argv=None):
     ap.add_argument("--plain-cols", type=int, default=1, help="columns timed on the plain FP64 path (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-subdomains", type=int, default=24)
+    ap.add_argument("--inversion", default=None, choices=["tiny", "reduced", "full"],
+                    help="time-to-misfit of the regularised inversion instead of RHS-solves/s")
     return ap.parse_args(argv)
 
 
@@ -391,9 +393,26 @@ def run_reference(a):
           flush=True)
 
 
+def run_inversion(a):
+    """Second metric: inversion time-to-misfit (plain FP64 vs mixed vs mixed + learned start)."""
+    from paper_2311_05322_gb300 import inversion
+    r = inversion.run(a.inversion, seed=3)
+    inv = r["inversion"]
+    line = {"metric": "inversion time-to-misfit", "unit": "s", "higher_is_better": False, "n_gpus": 1,
+            "value": inv["mixed_learned"]["time_to_target_s"], "data": "synthetic",
+            "config": {"workload": f"differential inversion, scale {a.inversion}", **r["config"]},
+            "time_to_target_s": {k: v["time_to_target_s"] for k, v in inv.items()},
+            "target_J": r["target_J"], "target_from": r["target_from"], "network": r["network"],
+            "J": {k: v["J"] for k, v in inv.items()}, "seconds": {k: v["seconds"] for k, v in inv.items()},
+            "learned_start_dJ0": r["learned_start_dJ0"], "total_s": r["total_s"]}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     args = _args()
-    if args.impl == "reference":
+    if args.inversion:
+        run_inversion(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_mine(args)

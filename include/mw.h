@@ -246,8 +246,9 @@ mw_status mw_nn_train(mw_ctx* ctx, const mw_nn_opts* opts, int64_t n, const floa
                       mw_nn_stats* stats);
 /* Network outputs y [n][2][32][32][32] for inputs x [n][n_in] (host). */
 mw_status mw_nn_infer(mw_ctx* ctx, int64_t n, const float* x, float* y);
-/* Trilinear samples of a cell-centred grid [2][G][G][G] over box {lo x,y,z, hi x,y,z} at the tet
- * centroids of the context's mesh (0 outside the box): deps [n_tet][2] (host). */
+/* Average of a cell-centred grid [2][G][G][G] over box {lo x,y,z, hi x,y,z} on each tet of the
+ * context's mesh: the mean of its trilinear interpolant (0 outside the box) over the 35 points of
+ * the order-4 barycentric lattice of the tet; deps [n_tet][2] (host). */
 mw_status mw_nn_grid_to_tets(mw_ctx* ctx, const float* grid, int32_t G, const double* box, double* deps);
 
 /* ---- device-resident variants (same operations, device pointers) ------------------- */

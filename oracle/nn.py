@@ -168,3 +168,20 @@ def grid_to_points(grid: np.ndarray, box, pts: np.ndarray) -> np.ndarray:
                 acc += w[:, None] * grid[:, i0[:, 2] + dz, i0[:, 1] + dy, i0[:, 0] + dx].T
     out[inside] = acc
     return out
+
+
+def grid_to_tets(grid: np.ndarray, box, xyz: np.ndarray, tets: np.ndarray) -> np.ndarray:
+    """Average of the grid over each tet: mean of grid_to_points over the 35 points of the
+    order-4 barycentric lattice (i v0 + j v1 + k v2 + l v3) / 4, i + j + k + l = 4.  [T][2]."""
+    P = xyz[np.asarray(tets)]
+    acc = np.zeros((P.shape[0], 2))
+    n = 0
+    for i in range(5):
+        for j in range(5 - i):
+            for k in range(5 - i - j):
+                l = 4 - i - j - k
+                pts = (i * P[:, 0] + j * P[:, 1] + k * P[:, 2] + l * P[:, 3]) / 4.0
+                acc += grid_to_points(grid, box, pts)
+                n += 1
+    assert n == 35
+    return acc / 35.0

@@ -291,37 +291,49 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, const int32_t*
   }
 }
 
-// Trilinear sample of a [2][G][G][G] grid (cell-centred on box [lo, hi]) at tet centroids;
-// outside the box the value is 0.  out [T][2] += (Re, Im).
+// Mean over the 35 points of the order-4 barycentric lattice of each tet (points
+// (i v0 + j v1 + k v2 + l v3) / 4, i + j + k + l = 4) of the trilinear interpolant of a
+// cell-centred [2][G][G][G] grid over box [lo, hi] (0 outside the box): an average of the grid
+// over the tet.  out [T][2] += (Re, Im).
 __global__ void grid_to_tets_kernel(const float* __restrict__ grid, int G, double lx, double ly, double lz, double hx,
                                     double hy, double hz, const double* __restrict__ xyz,
                                     const int32_t* __restrict__ tets, int64_t T, double* __restrict__ out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= T) return;
-  double c[3] = {0, 0, 0};
-  for (int v = 0; v < 4; ++v)
-    for (int d = 0; d < 3; ++d) c[d] += 0.25 * xyz[3 * (int64_t)tets[4 * t + v] + d];
+  double v[4][3];
+  for (int a = 0; a < 4; ++a)
+    for (int d = 0; d < 3; ++d) v[a][d] = xyz[3 * (int64_t)tets[4 * t + a] + d];
   const double lo[3] = {lx, ly, lz}, hi[3] = {hx, hy, hz};
-  double f[3];
-  int i0[3];
-  for (int d = 0; d < 3; ++d) {
-    if (c[d] < lo[d] || c[d] > hi[d]) return;
-    const double u = (c[d] - lo[d]) / (hi[d] - lo[d]) * G - 0.5;   // cell-centred coordinate
-    double fl = floor(u);
-    fl = fmin(fmax(fl, 0.0), (double)(G - 2));
-    i0[d] = (int)fl;
-    f[d] = fmin(fmax(u - fl, 0.0), 1.0);
-  }
-  for (int ch = 0; ch < 2; ++ch) {
-    double s = 0.0;
-    for (int dz = 0; dz < 2; ++dz)
-      for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx) {
-          const double wgt = (dz ? f[2] : 1 - f[2]) * (dy ? f[1] : 1 - f[1]) * (dx ? f[0] : 1 - f[0]);
-          s += wgt * grid[(((int64_t)ch * G + i0[2] + dz) * G + i0[1] + dy) * G + i0[0] + dx];
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int i = 0; i <= 4; ++i)
+    for (int j = 0; i + j <= 4; ++j)
+      for (int k = 0; i + j + k <= 4; ++k) {
+        const int l = 4 - i - j - k;
+        double c[3];
+        for (int d = 0; d < 3; ++d) c[d] = (i * v[0][d] + j * v[1][d] + k * v[2][d] + l * v[3][d]) * 0.25;
+        bool in = true;
+        double f[3];
+        int i0[3];
+        for (int d = 0; d < 3; ++d) {
+          if (c[d] < lo[d] || c[d] > hi[d]) in = false;
+          const double u = (c[d] - lo[d]) / (hi[d] - lo[d]) * G - 0.5;
+          double fl = floor(u);
+          fl = fmin(fmax(fl, 0.0), (double)(G - 2));
+          i0[d] = (int)fl;
+          f[d] = fmin(fmax(u - fl, 0.0), 1.0);
         }
-    out[2 * t + ch] += s;
-  }
+        if (!in) continue;
+        for (int dz = 0; dz < 2; ++dz)
+          for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+              const double wgt = (dz ? f[2] : 1 - f[2]) * (dy ? f[1] : 1 - f[1]) * (dx ? f[0] : 1 - f[0]);
+              const int64_t cell = ((int64_t)(i0[2] + dz) * G + i0[1] + dy) * G + i0[0] + dx;
+              acc0 += wgt * grid[cell];
+              acc1 += wgt * grid[(int64_t)G * G * G + cell];
+            }
+      }
+  out[2 * t] += acc0 / 35.0;
+  out[2 * t + 1] += acc1 / 35.0;
 }
 
 inline int gsb(int64_t n) {

@@ -1,0 +1,222 @@
+"""Inversion time-to-misfit and the learned initialiser (Sec. IV-D; BASELINE configs 4 and 5).
+
+Differential reading of the inversion: the healthy anatomy is known (a prior scan), the data are
+the S-parameters of the injured shoulder computed on a finer "data" mesh with complex Gaussian
+noise, and L-BFGS reconstructs eps on a coarser "inverse" mesh (different meshes, as Sec. IV-D
+asks, to avoid the inverse crime) starting from the healthy permittivity.  The fit is to the
+differential data (S_obs - S_healthy on the data mesh, plus S_healthy on the inverse mesh), so the
+mesh-to-mesh modelling error of the healthy anatomy cancels to first order.  The learned
+initialiser maps the normalised difference Delta S = S_injured - S_healthy to Delta eps on a
+32^3 grid over the tendon band; its tet averages are added to the start.
+
+Everything numerical runs in libmw (solves, S, gradient, L-BFGS, network training/inference,
+grid-to-tet averaging); this module only wires the calls together and generates seeded inputs.
+Usage: python -m paper_2311_05322_gb300.inversion --scale reduced
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from phantom import (EPS_MATCHING, ROI_BOX, ROI_GRID, add_noise, box_partition, dipole_ring, kuhn_mesh, random_tear,
+                     shoulder_eps, SHOULDER_HI, SHOULDER_LO, ARM_CENTER, tear_target_grid)
+
+from . import mw
+
+SCALES = {
+    # data mesh, inverse mesh, transmitters, frequencies, partitions (data, inverse), samples, epochs, iterations
+    "tiny": dict(data=(24, 24, 10), inv=(18, 18, 8), n_src=16, freqs=(1.0e9,), pdata=(4, 4, 2), pinv=(3, 3, 2),
+                 samples=96, epochs=60, iters=6, alpha=0.0),
+    "reduced": dict(data=(44, 44, 17), inv=(30, 30, 13), n_src=32, freqs=(1.0e9,), pdata=(9, 9, 4), pinv=(6, 6, 3),
+                    samples=600, epochs=200, iters=10, alpha=0.0),
+    # the reduced configuration with fewer samples and iterations (GPU test of the learned gain)
+    "test": dict(data=(44, 44, 17), inv=(30, 30, 13), n_src=32, freqs=(1.0e9,), pdata=(9, 9, 4), pinv=(6, 6, 3),
+                 samples=256, epochs=120, iters=5, alpha=0.0),
+    "full": dict(data=(55, 55, 24), inv=(44, 44, 17), n_src=64, freqs=(0.8e9, 1.0e9, 1.2e9), pdata=(11, 11, 5),
+                 pinv=(9, 9, 4), samples=2000, epochs=100, iters=20, alpha=0.0),
+}
+TARGET_SCALE = 20.0      # Delta eps is trained in units of 20
+TARGET_BLUR_M = 0.003    # targets are blurred to about the resolution the inverse mesh can carry
+FLUID_RANGE = ((60.0, 75.0), (25.0, 40.0))
+
+
+def _mesh(cells):
+    return kuhn_mesh(*cells, lo=SHOULDER_LO, hi=SHOULDER_HI)
+
+
+def _sources(cells, n_src):
+    hz = (SHOULDER_HI[2] - SHOULDER_LO[2]) / cells[2]
+    return dipole_ring(n_src, 0.10, hz / 2 if cells[2] % 2 == 0 else 0.0, ARM_CENTER)
+
+
+def _pairs(e):
+    return np.stack([e.real, e.imag], 1)
+
+
+@dataclass
+class Forward:
+    """A context on one mesh with a stale background preconditioner."""
+    ctx: mw.Context
+    mesh: object
+    freqs: tuple
+    opts: object
+
+    @classmethod
+    def build(cls, cells, n_src, freqs, parts, eps_ref, prec=mw.MW_PREC_BF16, mode=mw.MW_MODE_MIXED):
+        m = _mesh(cells)
+        c = mw.Context(0)
+        c.set_mesh(m.xyz, m.tets)
+        c.assemble(list(freqs), _pairs(eps_ref), EPS_MATCHING)
+        c.setup_preconditioner(int(np.prod(parts)), box_partition(m, parts, seed=7), 1, prec)
+        pos, d = _sources(cells, n_src)
+        c.set_sources(pos, d)
+        return cls(c, m, tuple(freqs), mw.solve_opts(mode=mode, tol=1e-8, inner_tol=1e-4))
+
+    def S(self, eps):
+        self.ctx.assemble(list(self.freqs), _pairs(eps), EPS_MATCHING)
+        S, _ = self.ctx.solve(self.opts)
+        return S
+
+
+def nn_input(dS: np.ndarray, S_empty: np.ndarray) -> np.ndarray:
+    r = dS / np.abs(S_empty)
+    return np.concatenate([r.real.ravel(), r.imag.ravel()]).astype(np.float32)
+
+
+def he_init(n_in: int, seed: int) -> np.ndarray:
+    """He-normal weights, zero biases, in the flat layout of mw_nn_init."""
+    rng = np.random.default_rng(seed)
+    hid, k3 = 1024, 64
+    parts = [rng.normal(size=1024 * n_in) * np.sqrt(2.0 / n_in), np.zeros(hid),
+             rng.normal(size=hid * hid) * np.sqrt(2.0 / hid), np.zeros(hid),
+             rng.normal(size=16 * 16 * k3) * np.sqrt(2.0 / (16 * 8)), np.zeros(16),
+             rng.normal(size=16 * 8 * k3) * np.sqrt(2.0 / (16 * 8)), np.zeros(8),
+             rng.normal(size=8 * 2 * k3) * np.sqrt(1.0 / (8 * 8)), np.zeros(2)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def blurred_target(tear) -> np.ndarray:
+    """Delta eps of the tear on the ROI grid, Gaussian-blurred (sigma TARGET_BLUR_M per axis)."""
+    from scipy.ndimage import gaussian_filter
+    g = tear_target_grid(tear)
+    h = [(ROI_BOX[3 + d] - ROI_BOX[d]) / ROI_GRID for d in range(3)]
+    sig = (TARGET_BLUR_M / h[2], TARGET_BLUR_M / h[1], TARGET_BLUR_M / h[0])     # grid axes z, y, x
+    return np.stack([gaussian_filter(g[c], sig, mode="constant") for c in range(2)])
+
+
+def make_dataset(fwd: Forward, S_healthy, S_empty, n: int, seed0: int, f_index: int, snr_db: float):
+    """Noisy injured-minus-healthy S differences (inputs) and blurred Delta eps grids (targets)."""
+    X, T, tears, rel = [], [], [], []
+    for k in range(n):
+        tear = random_tear(seed0 + k, eps_range=FLUID_RANGE)
+        S = fwd.S(shoulder_eps(fwd.mesh, tear))
+        dS = S[f_index] - S_healthy[f_index]
+        rel.append(np.linalg.norm(dS) / np.linalg.norm(S_healthy[f_index]))
+        Sn = add_noise(S[f_index], snr_db, seed=500_000 + seed0 + k)
+        X.append(nn_input(Sn - S_healthy[f_index], S_empty[f_index]))
+        T.append((blurred_target(tear) / TARGET_SCALE).astype(np.float32))
+        tears.append(tear)
+    return np.stack(X), np.stack(T), tears, float(np.median(rel))
+
+
+def first_time_below(J, secs, target):
+    for j, s in zip(J, secs):
+        if j <= target:
+            return float(s)
+    return None
+
+
+def run(scale: str = "reduced", seed: int = 3, plain: bool | None = None, snr_db: float = 40.0, verbose=False):
+    cfg = SCALES[scale]
+    out = {"scale": scale, "config": {k: v for k, v in cfg.items()}}
+    f_nn = len(cfg["freqs"]) // 2                       # network sees the middle frequency
+    t0 = time.time()
+    data_mesh = _mesh(cfg["data"])
+    eps_h = shoulder_eps(data_mesh)
+    hom = np.full(data_mesh.n_tet, EPS_MATCHING, dtype=complex)
+
+    # --- training data on the data mesh, one frequency ------------------------------------------
+    gen = Forward.build(cfg["data"], cfg["n_src"], (cfg["freqs"][f_nn],), cfg["pdata"], eps_h)
+    S_h1 = gen.S(eps_h)
+    S_e1 = gen.S(hom)
+    n = cfg["samples"]
+    X, T, _, rel = make_dataset(gen, S_h1, S_e1, n, 10_000 + 1000 * seed, 0, snr_db)
+    n_tr = int(round(0.9 * n))
+    mu, sd = X[:n_tr].mean(axis=0), X[:n_tr].std(axis=0) + 1e-12     # per-feature standardisation
+    X = ((X - mu) / sd).astype(np.float32)
+    out["data_generation_s"] = time.time() - t0
+    # --- training ---------------------------------------------------------------------------------
+    n_in = X.shape[1]
+    gen.ctx.nn_init(n_in, he_init(n_in, seed))
+    losses, train_s = gen.ctx.nn_train(X[:n_tr], T[:n_tr], batch=64, epochs=cfg["epochs"], lr=1e-3, seed=seed)
+    Y = gen.ctx.nn_infer(X[n_tr:])
+    mse_nn = float(np.mean((Y - T[n_tr:]) ** 2)) * TARGET_SCALE ** 2
+    mse_zero = float(np.mean(T[n_tr:] ** 2)) * TARGET_SCALE ** 2
+    out["network"] = {"median_rel_dS": rel, "n_in": n_in, "train": n_tr, "test": n - n_tr, "epoch_loss_first_last": [losses[0], losses[-1]],
+                      "train_s": train_s, "test_mse": mse_nn, "zero_predictor_mse": mse_zero,
+                      "gain": 1.0 - mse_nn / mse_zero}
+    theta = gen.ctx.nn_get_params()
+
+    # --- observed data: a held-out tear on the data mesh, all frequencies, noise ------------------
+    data = Forward.build(cfg["data"], cfg["n_src"], cfg["freqs"], cfg["pdata"], eps_h)
+    tear = random_tear(99_000 + seed, eps_range=FLUID_RANGE)
+    S_inj = data.S(shoulder_eps(data_mesh, tear))
+    S_emp = data.S(hom)
+    S_obs = add_noise(S_inj, snr_db, seed=7_000 + seed)
+    S_hd = data.S(eps_h)
+    data.ctx.close()
+
+    # --- inversions on the inverse mesh -------------------------------------------------------------
+    inv_mesh = _mesh(cfg["inv"])
+    eps0 = shoulder_eps(inv_mesh)
+    inv = Forward.build(cfg["inv"], cfg["n_src"], cfg["freqs"], cfg["pinv"], eps0)
+    inv.ctx.nn_init(n_in, theta)
+    x_obs = ((nn_input(S_obs[f_nn] - S_hd[f_nn], S_emp[f_nn]) - mu) / sd).astype(np.float32)
+    grid = inv.ctx.nn_infer(x_obs[None])[0] * TARGET_SCALE
+    d_eps = inv.ctx.nn_grid_to_tets(grid, np.asarray(ROI_BOX))
+    learned0 = _pairs(eps0) + d_eps
+    io = mw.inv_opts(m=8, max_it=cfg["iters"], alpha=cfg["alpha"], first_step=1.0)
+    # differential data: fit S(eps) - S(eps_healthy) on the inverse mesh to S_obs - S_healthy on
+    # the data mesh, i.e. S(eps) against S_obs - S_hd + S(eps_healthy, inverse mesh)
+    S_hinv = inv.S(eps0)
+    S_fit = S_obs - S_hd + S_hinv
+
+    def invert(start, sopts):
+        e, h = inv.ctx.invert(S_fit, S_emp, start, io, sopts)
+        return {"J": h["J"].tolist(), "seconds": h["seconds"].tolist(), "evaluations": h["evaluations"]}
+
+    mixed = mw.solve_opts(mode=mw.MW_MODE_MIXED, tol=1e-8, inner_tol=1e-4)
+    res = {"mixed": invert(_pairs(eps0), mixed), "mixed_learned": invert(learned0, mixed)}
+    if plain is None:
+        plain = scale != "full"
+    if plain:
+        inv.ctx.assemble(list(cfg["freqs"]), _pairs(eps0), EPS_MATCHING)
+        inv.ctx.setup_preconditioner(int(np.prod(cfg["pinv"])), box_partition(inv.mesh, cfg["pinv"], seed=7), 1,
+                                     mw.MW_PREC_FP64_FROM_FP32)
+        res["plain_fp64"] = invert(_pairs(eps0), mw.solve_opts(mode=mw.MW_MODE_FP64, tol=1e-8))
+    ref = res["plain_fp64"] if plain else res["mixed"]
+    target = ref["J"][-1]
+    for k, v in res.items():
+        v["time_to_target_s"] = first_time_below(v["J"], v["seconds"], target)
+    out["inversion"] = res
+    out["target_J"] = target
+    out["target_from"] = "plain_fp64 after max_it" if plain else "mixed after max_it"
+    out["tear"] = {"center": tear.center, "semi_axes": tear.semi_axes, "eps": [tear.eps.real, tear.eps.imag]}
+    out["learned_start_dJ0"] = res["mixed_learned"]["J"][0] - res["mixed"]["J"][0]
+    out["total_s"] = time.time() - t0
+    gen.ctx.close()
+    inv.ctx.close()
+    return out
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--scale", default="reduced", choices=list(SCALES))
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--no-plain", action="store_true")
+    a = ap.parse_args()
+    print(json.dumps(run(a.scale, a.seed, plain=False if a.no_plain else None)), flush=True)

@@ -228,13 +228,14 @@ def shoulder_eps(mesh: Mesh, tear: Tear | None = None) -> np.ndarray:
 
 
 def random_tear(seed: int, eps_range=None) -> Tear:
-    """Tear centre uniform inside the tendon band, semi-axes uniform in 1-5 mm (full axes
-    2-10 mm), axis aligned; fluid permittivity fixed, or uniform in the given (re, im) box."""
+    """Tear centre uniform inside the tendon band, semi-axes uniform in 2-10 mm (volumes from
+    about 0.03 to 4 mL, spanning the paper's 1 mL and 5 mL tears), axis aligned; fluid
+    permittivity fixed, or uniform in the given (re, im) box."""
     g = SplitMix64(seed)
     rho = TENDON_RHO[0] + (TENDON_RHO[1] - TENDON_RHO[0]) * g.uniform()
     th = math.radians(TENDON_THETA_DEG[0] + (TENDON_THETA_DEG[1] - TENDON_THETA_DEG[0]) * g.uniform())
     zc = -TENDON_HALF_Z + 2.0 * TENDON_HALF_Z * g.uniform()
-    axes = tuple(0.001 + 0.004 * g.uniform() for _ in range(3))
+    axes = tuple(0.002 + 0.008 * g.uniform() for _ in range(3))
     if eps_range is None:
         eps = EPS_FLUID
     else:
@@ -320,3 +321,35 @@ def shoulder(cells=(80, 80, 34), n_src: int = 32, freqs=(1.0e9,), tear: Tear | N
     pos, d = dipole_ring(n_src, 0.10, z, ARM_CENTER)
     return Workload(name, m, eps, EPS_MATCHING, tuple(freqs), pos, d, parts=parts, overlap=overlap,
                     extra={"tear": tear})
+
+
+def shoulder_eps_at(points: np.ndarray, tear: Tear | None = None) -> np.ndarray:
+    """Relative permittivity of the shoulder phantom at arbitrary points (complex)."""
+    lab = shoulder_labels(points, tear)
+    eps = np.empty(points.shape[0], dtype=np.complex128)
+    for k, v in LABEL_EPS.items():
+        eps[lab == k] = v
+    if tear is not None:
+        eps[lab == FLUID] = tear.eps
+    return eps
+
+
+# Region of interest of the learned initialiser: a cell-centred 32^3 grid over the bounding box
+# of the tendon band (x, y, z lo; x, y, z hi), where tears occur.
+ROI_BOX = (-0.045, -0.025, -0.035, -0.025, 0.025, 0.035)
+ROI_GRID = 32
+
+
+def roi_centres(G: int = ROI_GRID, box=ROI_BOX) -> np.ndarray:
+    """Cell centres [G^3][3] of the ROI grid, z slowest, x fastest."""
+    lo, hi = np.asarray(box[:3]), np.asarray(box[3:])
+    c = [lo[d] + (np.arange(G) + 0.5) * (hi[d] - lo[d]) / G for d in range(3)]
+    Z, Y, X = np.meshgrid(c[2], c[1], c[0], indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+
+def tear_target_grid(tear: Tear, G: int = ROI_GRID, box=ROI_BOX) -> np.ndarray:
+    """Delta eps = eps(injured) - eps(healthy) at the ROI cell centres: [2][G][G][G] (Re, Im)."""
+    p = roi_centres(G, box)
+    d = shoulder_eps_at(p, tear) - shoulder_eps_at(p, None)
+    return np.stack([d.real, d.imag]).reshape(2, G, G, G)

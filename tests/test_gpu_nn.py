@@ -92,6 +92,6 @@ def test_grid_to_tets(ctx):
     grid = rng.normal(size=(2, 32, 32, 32)).astype(np.float32)
     box = np.array([-0.03, -0.02, -0.025, 0.02, 0.03, 0.02])
     got = ctx.nn_grid_to_tets(grid, box)
-    ref = nn.grid_to_points(grid.astype(np.float64), box, m.centroids())
+    ref = nn.grid_to_tets(grid.astype(np.float64), box, m.xyz, m.tets)
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
     assert np.count_nonzero(np.abs(ref).sum(1)) > 100

@@ -79,3 +79,23 @@ def test_bf16_round_bit_patterns():
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -7
     assert r[3] == -2.5 and r[4] == 3.140625
     assert abs(r[5] - 1e-3) <= 2 ** -9 * 1e-3
+
+
+def test_grid_to_points_exact_for_linear_fields_and_at_centres():
+    G = 8
+    box = np.array([-1.0, -2.0, 0.0, 1.0, 2.0, 3.0])
+    lo, hi = box[:3], box[3:]
+    centres = [lo[d] + (np.arange(G) + 0.5) * (hi[d] - lo[d]) / G for d in range(3)]
+    Z, Y, X = np.meshgrid(centres[2], centres[1], centres[0], indexing="ij")
+    a = np.array([0.3, -1.2, 2.0])
+    grid = np.stack([a[0] * X + a[1] * Y + a[2] * Z + 1.0, -X]).astype(np.float64)
+    rng = np.random.default_rng(0)
+    inner_lo = np.array([c[0] for c in centres])
+    inner_hi = np.array([c[-1] for c in centres])
+    pts = inner_lo + rng.uniform(size=(50, 3)) * (inner_hi - inner_lo)
+    v = nn.grid_to_points(grid, box, pts)
+    np.testing.assert_allclose(v[:, 0], pts @ a + 1.0, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(v[:, 1], -pts[:, 0], rtol=1e-12, atol=1e-12)
+    cpt = np.array([[centres[0][3], centres[1][5], centres[2][1]]])
+    assert abs(nn.grid_to_points(grid, box, cpt)[0, 1] - grid[1, 1, 5, 3]) < 1e-14
+    assert np.all(nn.grid_to_points(grid, box, np.array([[5.0, 0.0, 1.0]])) == 0.0)
