@@ -262,6 +262,10 @@ mw_status mw_gradient_dev(mw_ctx* ctx, const mw_solve_opts* opts, const void* S_
                           const void* S_empty_dev, double alpha, double* J_out, void* grad_dev);
 
 /* ---- diagnostics ------------------------------------------------------------------- */
+/* Self-test of the device-side bounded waits used by the tensor-core kernels: one thread waits
+ * on an mbarrier whose phase never completes, gives up after `spins` polls and writes
+ * MW_ETIMEOUT into *code_out (0 would mean the phase completed).  The context stays usable. */
+mw_status mw_selftest_bounded_wait(mw_ctx* ctx, int64_t spins, int32_t* code_out);
 /* Kernel launches issued by this library in the process so far. */
 int64_t mw_kernel_launches(void);
 /* Kernel classes timed by the optional event profiler. */

@@ -55,8 +55,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long i = 0; i < kSpinLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kSpinLimit) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if (i > 64) __nanosleep(32);
   }
@@ -326,6 +326,19 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
   }
 }
 
+// Self-test of the bounded wait: waits on an mbarrier that expects two arrivals but receives
+// one, so the phase never completes; the wait gives up after `limit` polls and the kernel
+// reports MW_ETIMEOUT (5) in *code instead of hanging.
+__global__ void bounded_wait_probe_kernel(long long limit, int32_t* code) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 2);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+    *code = mbar_wait(&bar, 0, limit) ? 0 : 5;
+  }
+}
+
 inline int rpad(int R) { return (R + 7) / 8 * 8; }
 
 }  // namespace
@@ -385,6 +398,11 @@ void tc_plan_free(TcPlan& p, const std::function<void(void*)>& dfree) {
                   (void*)p.gt_sub, (void*)p.gt_kt, (void*)p.err})
     if (q) dfree(q);
   p = TcPlan();
+}
+
+void bounded_wait_probe(long long limit, int32_t* code, cudaStream_t s) {
+  note_launch(1);
+  bounded_wait_probe_kernel<<<1, 32, 0, s>>>(limit, code);
 }
 
 size_t tc_w_bytes(const TcPlan& p) { return (size_t)std::max<int64_t>(p.w_tiles, 1) * kATileBytes; }

@@ -42,6 +42,9 @@ void tc_extract(const TcPlan& p, const OrasBatch& bt, const OrasTopo& tp, int ws
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
                    void* scratch, cudaStream_t s);
 
+// Launches the bounded-wait self-test (see k_oras_tc.cu); *code (device) gets 0 or 5.
+void bounded_wait_probe(long long limit, int32_t* code, cudaStream_t s);
+
 // Size of the fixed scratch used by mw_apply_preconditioner_noalloc (16 MiB).
 constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;
 // Device address of the fixed scratch on the current device (looked up once per device).

@@ -1779,4 +1779,18 @@ mw_status mw_nn_grid_to_tets(mw_ctx* c, const float* grid, int32_t G, const doub
   });
 }
 
+
+mw_status mw_selftest_bounded_wait(mw_ctx* c, int64_t spins, int32_t* code_out) {
+  return guard(c, [&] {
+    require(code_out && spins >= 1 && spins <= (int64_t)1 << 26, MW_EINVAL, "spins in [1, 2^26]");
+    int32_t* d = dalloc<int32_t>(c, 1);
+    CK(cudaMemsetAsync(d, 0xff, sizeof(int32_t), c->stream));
+    mwk::bounded_wait_probe((long long)spins, d, c->stream);
+    check_launch("bounded wait probe");
+    CK(cudaMemcpyAsync(code_out, d, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c, d);
+  });
+}
+
 }  // extern "C"

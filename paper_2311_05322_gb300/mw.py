@@ -94,6 +94,7 @@ _SIGS = {
     "mw_profile_enable": (C.c_int32, [_P, C.c_uint32]),
     "mw_profile_read": (C.c_int32, [_P, _P, _P, _P]),
     "mw_apply_preconditioner_noalloc": (C.c_int32, [_P, C.c_int32, _P, _P, C.c_int32]),
+    "mw_selftest_bounded_wait": (C.c_int32, [_P, C.c_int64, C.POINTER(C.c_int32)]),
     "mw_nn_param_count": (C.c_int64, [C.c_int32]),
     "mw_nn_init": (C.c_int32, [_P, C.c_int32, _P]),
     "mw_nn_get_params": (C.c_int32, [_P, _P]),
@@ -159,6 +160,8 @@ class Context:
         self.h = _P()
         self._check(self.lib.mw_create(C.byref(self.h), device, stream))
         self.info = None
+        self.n_freq = 0
+        self.n_src = 0
 
     def close(self):
         if self.h:
@@ -299,6 +302,11 @@ class Context:
         g = np.empty_like(e)
         self._check(self.lib.mw_tikhonov(self.h, _ptr(e), C.byref(R), _ptr(g)))
         return R.value, g
+
+    def selftest_bounded_wait(self, spins: int) -> int:
+        code = C.c_int32()
+        self._check(self.lib.mw_selftest_bounded_wait(self.h, spins, C.byref(code)))
+        return code.value
 
     # -- learned initialiser -----------------------------------------------------------------
     def nn_init(self, n_in: int, theta: np.ndarray):

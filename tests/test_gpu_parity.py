@@ -265,3 +265,33 @@ def test_lbfgs_matches_oracle_iterates():
     # final iterate and the sequence of accepted points that the oracle reports
     xf = x.copy()
     assert np.linalg.norm(xf - xs_ref[-1]) <= 1e-10 * max(1.0, np.linalg.norm(xs_ref[-1]))
+
+
+def test_invert_matches_oracle_lbfgs_trajectory(ragged):
+    """mw_invert (GPU solves, gradient, host L-BFGS) against the oracle's L-BFGS driven by the
+    oracle's direct-solve gradient: the same cost at every accepted iterate."""
+    mw = _mw()
+    m, eps, pos, direc, sysm = ragged
+    freqs = [1.0e9]
+    e, s = sources.dipole_edges(m.xyz, sysm.topo.edge_vert, pos, direc)
+    truth = eps.copy()
+    truth[40:70] += 9 - 6j
+    S_obs = solve.forward(sysm, truth, freqs, EPS_MATCHING, e, s)[1]
+    S_emp = solve.forward(sysm, np.full(m.n_tet, EPS_MATCHING, dtype=complex), freqs, EPS_MATCHING, e, s)[1]
+    pairs, w = inverse.tikhonov_weights(sysm)
+    alpha = 1e-4
+
+    def fg(x):
+        e2 = x.reshape(-1, 2)
+        J, g, *_ = inverse.gradient(sysm, e2[:, 0] + 1j * e2[:, 1], freqs, EPS_MATCHING, e, s, S_obs, S_emp)
+        R, gR = inverse.tikhonov(pairs, w, e2)
+        return J + alpha * R, (g + alpha * gR).ravel()
+
+    x0 = np.stack([eps.real, eps.imag], 1).ravel()
+    _, hist_ref, _ = inverse.lbfgs(fg, x0, m=8, max_it=4)
+    c = _ctx(m, eps, freqs, pos, direc)
+    c.setup_preconditioner(4, box_partition(m, (2, 2, 1), seed=7), 1, mw.MW_PREC_FP64)
+    eps_out, h = c.invert(S_obs, S_emp, x0.reshape(-1, 2), mw.inv_opts(m=8, max_it=4, alpha=alpha),
+                          mw.solve_opts(tol=1e-11))
+    assert len(h["J"]) == len(hist_ref)
+    np.testing.assert_allclose(h["J"], hist_ref, rtol=1e-7)
