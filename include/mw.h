@@ -122,7 +122,9 @@ mw_status mw_assemble(mw_ctx* ctx, int32_t n_freq, const double* freq_hz, const 
 /* Values of A_f in the canonical pattern, host complex128 [nnz] (parity hook). */
 mw_status mw_get_matrix(mw_ctx* ctx, int32_t f, double* values);
 /* Y = A_f X on the device for n_cols columns, layout [E][n_cols] (column fastest),
- * complex128 (prec = MW_PREC_FP64, FP64 arithmetic) or complex64 (MW_PREC_FP32, FP32). */
+ * complex128 (prec = MW_PREC_FP64, FP64 arithmetic) or complex64 (MW_PREC_FP32, FP32); prec = 3
+ * takes complex128 in and out and computes in double-float arithmetic on the FP32 pipes (the
+ * mixed solver's outer residual). */
 mw_status mw_apply_matrix(mw_ctx* ctx, int32_t f, int32_t prec, const void* x_dev, void* y_dev,
                           int32_t n_cols);
 

@@ -169,3 +169,129 @@ int residual_f64(const int64_t* rp, const int32_t* ci, const double2* A, const d
 }
 
 }  // namespace mwk
+
+// ---------------------------------------------------------------------------------------
+// FP64-accurate residual on the FP32 pipes (double-float arithmetic).
+//
+// GB300 runs FP64 at about 1/64 of its FP32 rate, so the outer residual r = b - A x of the
+// mixed solver keeps A and x as unevaluated sums of two floats (hi + lo, about 48 significant
+// bits) and forms every product with the exact FMA product error and every sum with Knuth's
+// error-free two-sum; only b - (s_hi + s_lo) and |r|^2 are FP64.  The intrinsics (__fmul_rn,
+// __fadd_rn, __fsub_rn) are never contracted, which keeps the transformations exact.
+// ---------------------------------------------------------------------------------------
+namespace mwk {
+namespace {
+
+// (s_h, s_l) += (a_h + a_l) * (x_h + x_l), the a_l * x_l term dropped.
+__device__ __forceinline__ void df_mac(float& s_h, float& s_l, float a_h, float a_l, float x_h, float x_l) {
+  const float p_h = __fmul_rn(a_h, x_h);
+  const float p_e = fmaf(a_h, x_h, -p_h);                 // exact error of the product
+  const float p_l = fmaf(a_h, x_l, fmaf(a_l, x_h, p_e));
+  const float t = __fadd_rn(s_h, p_h);                     // two-sum(s_h, p_h)
+  const float bp = __fsub_rn(t, s_h);
+  const float e = __fadd_rn(__fsub_rn(s_h, __fsub_rn(t, bp)), __fsub_rn(p_h, bp));
+  s_l = __fadd_rn(s_l, __fadd_rn(p_l, e));
+  s_h = t;
+}
+
+// A_df[k] = (re_hi, re_lo, im_hi, im_lo) of a complex FP64 value.
+__global__ void split_df_kernel(const double2* __restrict__ a, float4* __restrict__ o, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = a[i];
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    o[i] = make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+  }
+}
+
+// r = b - A x (or y = A x when B is null) with per-block, per-column partial |r|^2, as
+// residual_kernel but in double-float arithmetic.
+template <int CPL>
+__global__ void __launch_bounds__(256) residual_df_kernel(const int64_t* __restrict__ rp,
+                                                          const int32_t* __restrict__ ci,
+                                                          const float4* __restrict__ A, const float4* __restrict__ X,
+                                                          const double2* __restrict__ B, double2* __restrict__ Rv,
+                                                          double* __restrict__ part, int64_t E, int R, int tpr_log2) {
+  __shared__ double red[256 * CPL];
+  const int tpr = 1 << tpr_log2;
+  const int rows_per_block = 256 >> tpr_log2;
+  const int lane_c = threadIdx.x & (tpr - 1);
+  const int c0 = lane_c * CPL;
+  double nrm[CPL];
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) nrm[q] = 0.0;
+  for (int64_t row = (int64_t)blockIdx.x * rows_per_block + (threadIdx.x >> tpr_log2); row < E;
+       row += (int64_t)gridDim.x * rows_per_block) {
+    if (c0 >= R) continue;
+    float rh[CPL], rl[CPL], ih[CPL], il[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
+    for (int64_t k = rp[row]; k < rp[row + 1]; ++k) {
+      const float4 a = A[k];
+      const float4* xr = X + (int64_t)ci[k] * R + c0;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+        if (c0 + q < R) {
+          const float4 x = xr[q];
+          df_mac(rh[q], rl[q], a.x, a.y, x.x, x.y);       // + ar xr
+          df_mac(rh[q], rl[q], -a.z, -a.w, x.z, x.w);     // - ai xi
+          df_mac(ih[q], il[q], a.x, a.y, x.z, x.w);       // + ar xi
+          df_mac(ih[q], il[q], a.z, a.w, x.x, x.y);       // + ai xr
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPL; ++q)
+      if (c0 + q < R) {
+        const double yr = (double)rh[q] + (double)rl[q], yi = (double)ih[q] + (double)il[q];
+        double2 r;
+        if (B) {
+          const double2 bb = B[row * R + c0 + q];
+          r = make_double2(bb.x - yr, bb.y - yi);
+        } else {
+          r = make_double2(yr, yi);
+        }
+        Rv[row * R + c0 + q] = r;
+        nrm[q] += r.x * r.x + r.y * r.y;
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) red[threadIdx.x * CPL + q] = nrm[q];
+  __syncthreads();
+  if ((int)threadIdx.x < tpr) {
+    for (int q = 0; q < CPL; ++q) {
+      const int c = c0 + q;
+      if (c >= R) continue;
+      double s = 0.0;
+      for (int r = 0; r < rows_per_block; ++r) s += red[(r * tpr + lane_c) * CPL + q];
+      part[(int64_t)blockIdx.x * R + c] = s;
+    }
+  }
+}
+
+}  // namespace
+
+void split_df(const double2* a, float4* o, int64_t n, cudaStream_t s) {
+  note_launch(1);
+  int64_t b = (n + 255) / 256;
+  split_df_kernel<<<(int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16), 256, 0, s>>>(a, o, n);
+}
+
+int residual_df(const int64_t* rp, const int32_t* ci, const float4* A, const float4* X, const double2* B, double2* Rv,
+                double* part, int64_t E, int R, cudaStream_t s) {
+  note_launch(1);
+  Shape sh = shape_for(R);
+  const int blocks = 152 * 4;
+  switch (sh.cpl) {
+    case 1:
+      residual_df_kernel<1><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
+      break;
+    case 2:
+      residual_df_kernel<2><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
+      break;
+    default:
+      residual_df_kernel<4><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
+      break;
+  }
+  return blocks;
+}
+
+}  // namespace mwk

@@ -105,6 +105,12 @@ void spmm_f64(const int64_t* rp, const int32_t* ci, const double2* A, const doub
               int R, cudaStream_t s);
 void spmm_f32(const int64_t* rp, const int32_t* ci, const float2* A, const float2* X, float2* Y, int64_t E, int R,
               cudaStream_t s);
+// Split complex FP64 values into double-float (re_hi, re_lo, im_hi, im_lo).
+void split_df(const double2* a, float4* o, int64_t n, cudaStream_t s);
+// r = b - A x (y = A x when B is null) in double-float arithmetic on the FP32 pipes, with
+// per-block partial |r|^2 as residual_f64; returns the number of blocks.
+int residual_df(const int64_t* rp, const int32_t* ci, const float4* A, const float4* X, const double2* B,
+                double2* Rv, double* part, int64_t E, int R, cudaStream_t s);
 // r = b - A x (FP64) and per-column partial ||r||^2 into part[nblk][R]; returns nblk used.
 int residual_f64(const int64_t* rp, const int32_t* ci, const double2* A, const double2* X, const double2* B,
                  double2* Rv, double* part, int64_t E, int R, cudaStream_t s);

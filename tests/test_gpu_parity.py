@@ -102,6 +102,9 @@ def test_spmm(ragged, ncols):
     yd = torch.empty_like(xd)
     c.apply_matrix(0, mw.MW_PREC_FP64, xd, yd, ncols)
     assert _relerr(yd.cpu().numpy(), ref) <= 1e-13
+    ydf = torch.empty_like(xd)
+    c.apply_matrix(0, 3, xd, ydf, ncols)                  # double-float arithmetic, FP64 accuracy class
+    assert _relerr(ydf.cpu().numpy(), ref) <= 1e-13
     x32 = xd.to(torch.complex64)
     y32 = torch.empty_like(x32)
     c.apply_matrix(0, mw.MW_PREC_FP32, x32, y32, ncols)
