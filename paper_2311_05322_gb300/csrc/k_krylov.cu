@@ -13,6 +13,10 @@
 //   target[c]    residual-estimate target of this cycle
 //   done[c]      1 once the column stopped (converged, breakdown or out of steps)
 //   kcol[c]      Arnoldi steps used by the column in this cycle
+#include <algorithm>
+#include <cstdint>
+
+#include "mw_async.cuh"
 #include "mw_internal.h"
 
 namespace mwk {
@@ -154,6 +158,190 @@ __global__ void __launch_bounds__(kDotThreads) cgs_dots_kernel(const T* __restri
           if (c0 + q < R) part[(p * nvec + i) * R + c0 + q] = acc[a][q];
       }
     }
+  }
+}
+
+// Streaming form of the same dots for 16 <= R <= 128 with 16-byte aligned vectors.  The rows
+// are cut into tiles of TR = G * bd_rows<T>() rows (G = 256 / R row groups), about 16 KB per
+// vector; block b takes a contiguous range of tiles.  Warp 0 lane 0 streams, per tile, w and
+// then V_i0 .. V_i0+nv-1 through a ring of kBdStages shared-memory stages with bulk copies;
+// the 256 consumer threads (warps 1-8) map thread (c, g) = (t % R, t / R) to column c and the
+// tile rows g, g + G, ...  Each consumer keeps its w rows in registers for the whole tile,
+// forms its FP32 (FP64) partial of conj(V_i) w over its bd_rows<T>() rows, and the G partials of a
+// column are summed in the vector precision in a fixed order by thread (c, i % G), which adds
+// the tile sum to an FP64 accumulator in shared memory (so FP32 vectors are summed in FP32 over
+// chunks of TR rows; FP64 instructions, slow on this part, stay at a few per tile and column).
+// Vector groups of VG = min(64, 2048 / R) vectors are swept in turn (w is re-read per sweep).
+// Part index p = block.  The element beyond the last 16-byte boundary of a ragged last tile
+// (odd rows * R in FP32) is read from global memory.  Every wait is bounded; on timeout the
+// kernel records an error code, skips the remaining waits and copies (still executing the
+// same named barriers), drains its outstanding copies and returns.
+constexpr int kBdConsumers = 256;
+constexpr int kBdThreads = kBdConsumers + 32;
+constexpr int kBdStages = 4;
+constexpr int kBdStageBytes = 16384;
+template <typename T>
+__host__ __device__ constexpr int bd_rows() {
+  return 64 / (int)sizeof(T);   // 8 rows (FP32 complex), 4 rows (FP64 complex)
+}
+// VG * R <= 2048 accumulators of 16 bytes
+inline size_t bd_smem_bytes(int R) {
+  const int VG = std::min(64, 2048 / R);
+  return (size_t)kBdStages * kBdStageBytes + 2 * kBdConsumers * sizeof(double2) + (size_t)VG * R * sizeof(double2) +
+         2 * kBdStages * sizeof(uint64_t) + 16;
+}
+constexpr size_t kBdMaxSmem = (size_t)kBdStages * kBdStageBytes + 2 * kBdConsumers * sizeof(double2) +
+                              2048 * sizeof(double2) + 2 * kBdStages * sizeof(uint64_t) + 16;
+
+template <typename T>
+__global__ void __launch_bounds__(kBdThreads, 2)
+    cgs_dots_bulk_kernel(const T* __restrict__ V, int64_t vstride, int nvec, const T* __restrict__ w, int64_t E,
+                         int R, int G, int VG, double2* __restrict__ part, int32_t* __restrict__ err) {
+  using Sc = typename Traits<T>::S;
+  constexpr int RPT = bd_rows<T>();
+  constexpr int kStageElems = kBdStageBytes / (int)sizeof(T);
+  extern __shared__ __align__(128) uint8_t bd_smem[];
+  T* stage = reinterpret_cast<T*>(bd_smem);
+  T* red = reinterpret_cast<T*>(bd_smem + (size_t)kBdStages * kBdStageBytes);
+  double2* acc = reinterpret_cast<double2*>(bd_smem + (size_t)kBdStages * kBdStageBytes +
+                                            2 * kBdConsumers * sizeof(double2));
+  uint64_t* full = reinterpret_cast<uint64_t*>(acc + (size_t)VG * R);
+  uint64_t* empty = full + kBdStages;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kBdStages);
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int i = 0; i < kBdStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kBdConsumers);
+    }
+    *abort_flag = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+
+  const int TR = G * RPT;
+  const int64_t nt = (E + TR - 1) / TR;
+  const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
+  const int nsweep = (nvec + VG - 1) / VG;
+
+  if (tid < 32) {
+    if (tid != 0) return;
+    // producer
+    int64_t it = 0;
+    bool stop = false;
+    for (int sw = 0; sw < nsweep && !stop; ++sw) {
+      const int i0 = sw * VG, nv = min(VG, nvec - i0);
+      for (int64_t t = t0; t < t1 && !stop; ++t) {
+        const int64_t r0 = t * TR;
+        const int64_t rows = E - r0 < TR ? E - r0 : (int64_t)TR;
+        const uint32_t bytes = (uint32_t)((rows * R * (int64_t)sizeof(T)) & ~(int64_t)15);
+        for (int q = -1; q < nv; ++q) {
+          const int st = (int)(it % kBdStages);
+          const int64_t use = it / kBdStages;
+          if (use > 0 && !mbar_wait(&empty[st], (uint32_t)((use - 1) & 1))) {
+            atomicCAS(err, 0, 11);
+            *abort_flag = 1;
+          }
+          if (*abort_flag) {
+            stop = true;
+            break;
+          }
+          const T* src = (q < 0 ? w : V + (int64_t)(i0 + q) * vstride) + r0 * R;
+          if (bytes > 0) {
+            mbar_expect_tx(&full[st], bytes);
+            bulk_g2s(stage + (size_t)st * kStageElems, src, bytes, &full[st]);
+          } else {
+            mbar_arrive(&full[st]);
+          }
+          ++it;
+        }
+      }
+    }
+    // drain: every issued copy has landed before this thread leaves
+    for (int64_t k = (it > kBdStages ? it - kBdStages : 0); k < it; ++k)
+      if (!mbar_wait(&full[k % kBdStages], (uint32_t)((k / kBdStages) & 1))) atomicCAS(err, 0, 12);
+    return;
+  }
+
+  // consumers
+  const int ct = tid - 32;
+  const int c = ct % R, g = ct / R;
+  const bool act = g < G;
+  int64_t it = 0, nred = 0;
+  auto wait_full = [&](int st, int64_t use) {
+    if (*abort_flag) return;
+    if (!mbar_wait(&full[st], (uint32_t)(use & 1))) {
+      atomicCAS(err, 0, 13);
+      *abort_flag = 1;
+    }
+  };
+  for (int sw = 0; sw < nsweep; ++sw) {
+    const int i0 = sw * VG, nv = min(VG, nvec - i0);
+    if (act)
+      for (int q = g; q < nv; q += G) acc[q * R + c] = make_double2(0.0, 0.0);
+    for (int64_t t = t0; t < t1; ++t) {
+      const int64_t r0 = t * TR;
+      const int64_t rows = E - r0 < TR ? E - r0 : (int64_t)TR;
+      const int64_t ncop = ((rows * R * (int64_t)sizeof(T)) & ~(int64_t)15) / (int64_t)sizeof(T);
+      // w tile -> registers
+      T wr[RPT];
+      {
+        const int st = (int)(it % kBdStages);
+        wait_full(st, it / kBdStages);
+        const T* sm = stage + (size_t)st * kStageElems;
+        const T* gl = w + r0 * R;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+          const int row = k * G + g;
+          const int f = row * R + c;
+          wr[k] = T{0, 0};
+          if (act && row < rows) wr[k] = f < ncop ? sm[f] : gl[f];
+        }
+        mbar_arrive(&empty[st]);
+        ++it;
+      }
+      for (int q = 0; q < nv; ++q) {
+        const int st = (int)(it % kBdStages);
+        wait_full(st, it / kBdStages);
+        const T* sm = stage + (size_t)st * kStageElems;
+        const T* gl = V + (int64_t)(i0 + q) * vstride + r0 * R;
+        Sc pr = 0, pi = 0;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+          const int row = k * G + g;
+          const int f = row * R + c;
+          if (act && row < rows) {
+            const T v = f < ncop ? sm[f] : gl[f];
+            pr = fma(v.x, wr[k].x, pr);
+            pr = fma(v.y, wr[k].y, pr);
+            pi = fma(v.x, wr[k].y, pi);
+            pi = fma(-v.y, wr[k].x, pi);
+          }
+        }
+        mbar_arrive(&empty[st]);
+        ++it;
+        T* rb = red + (nred & 1) * kBdConsumers;
+        rb[ct] = T{pr, pi};
+        ++nred;
+        asm volatile("bar.sync 1, %0;" ::"n"(kBdConsumers) : "memory");
+        if (act && g == q % G) {
+          Sc sr = 0, si = 0;
+#pragma unroll 8
+          for (int g2 = 0; g2 < G; ++g2) {
+            const T v = rb[g2 * R + c];
+            sr += v.x;
+            si += v.y;
+          }
+          double2 a = acc[q * R + c];
+          a.x += (double)sr;
+          a.y += (double)si;
+          acc[q * R + c] = a;
+        }
+      }
+    }
+    if (act)
+      for (int q = g; q < nv; q += G) part[((int64_t)blockIdx.x * nvec + i0 + q) * R + c] = acc[q * R + c];
   }
 }
 
@@ -451,8 +639,25 @@ inline int gs_blocks(int64_t n) {
 }
 
 template <typename T>
-int dots_launch(const T* V, int64_t vstride, int nvec, const T* w, int64_t E, int R, double2* part, cudaStream_t s) {
+int dots_launch(const T* V, int64_t vstride, int nvec, const T* w, int64_t E, int R, double2* part, int32_t* err,
+                cudaStream_t s) {
   note_launch(1);
+  const bool aligned = ((uintptr_t)V % 16 == 0) && ((uintptr_t)w % 16 == 0) && ((vstride * sizeof(T)) % 16 == 0);
+  if (err && aligned && R >= 16 && R <= 128 && nvec >= 1) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(cgs_dots_bulk_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kBdMaxSmem);
+      cudaFuncSetAttribute(cgs_dots_bulk_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kBdMaxSmem);
+      attr = true;
+    }
+    const int G = kBdConsumers / R;
+    const int VG = std::min(64, 2048 / R);
+    const int nb = 152 * 2;
+    cgs_dots_bulk_kernel<T><<<nb, kBdThreads, bd_smem_bytes(R), s>>>(V, vstride, nvec, w, E, R, G, VG, part, err);
+    return nb;
+  }
   Shape sh = shape_for(R);
   const int S = nvec >= kDotWarps ? 1 : kDotWarps / nvec;
   switch (sh.cpl) {
@@ -500,12 +705,12 @@ int update_launch(const T* V, int64_t vstride, int nvec, const double2* h, T* w,
 }  // namespace
 
 int cgs_dots_f64(const double2* V, int64_t vstride, int nvec, const double2* w, int64_t E, int R, double2* part,
-                 cudaStream_t s) {
-  return dots_launch<double2>(V, vstride, nvec, w, E, R, part, s);
+                 int32_t* err, cudaStream_t s) {
+  return dots_launch<double2>(V, vstride, nvec, w, E, R, part, err, s);
 }
 int cgs_dots_f32(const float2* V, int64_t vstride, int nvec, const float2* w, int64_t E, int R, double2* part,
-                 cudaStream_t s) {
-  return dots_launch<float2>(V, vstride, nvec, w, E, R, part, s);
+                 int32_t* err, cudaStream_t s) {
+  return dots_launch<float2>(V, vstride, nvec, w, E, R, part, err, s);
 }
 void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s) {
   note_launch(1);

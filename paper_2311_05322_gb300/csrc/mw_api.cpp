@@ -38,7 +38,11 @@ void normalize_start_f32(const double2* r, const double* rnorm, const int32_t* d
 namespace mwimpl {
 
 constexpr int kMaxRestart = 63;
-constexpr int kDotParts = 152 * 4 * 8;  // cgs_dots: blocks x max slots
+constexpr int kDotParts = mwk::kCgsDotsMaxParts;
+
+// Distance between consecutive Krylov vectors, in complex elements: E * R rounded up to 32, so
+// every vector starts on a 256-byte boundary (bulk copies need 16).
+inline int64_t krylov_stride(int64_t E, int R) { return (E * R + 31) / 32 * 32; }
 constexpr int kRedBlocks = 152 * 4;
 
 struct Ctx;
@@ -67,7 +71,8 @@ struct Prec {
 struct Work {
   int64_t E = 0;
   int R = 0, m = 0, prec = -1;
-  void *V = nullptr, *Z = nullptr;
+  void *V = nullptr, *Z = nullptr;   // Krylov and preconditioned bases, vectors krylov_stride apart
+  int32_t* kerr = nullptr;     // bounded-wait error code of the streaming Gram-Schmidt kernel
   float4* xdf = nullptr;       // double-float copy of the iterate (mixed mode)
   double2 *r = nullptr, *x = nullptr, *part = nullptr, *h = nullptr, *H = nullptr, *cs = nullptr, *g = nullptr,
           *y = nullptr, *bblk = nullptr;
@@ -244,7 +249,7 @@ void free_work(Ctx* c) {
   Work& w = c->work;
   for (void* p : {(void*)w.V, (void*)w.Z, (void*)w.xdf, (void*)w.r, (void*)w.x, (void*)w.part, (void*)w.h, (void*)w.H, (void*)w.cs,
                   (void*)w.g, (void*)w.y, (void*)w.npart, (void*)w.target, (void*)w.rnorm, (void*)w.bnorm,
-                  (void*)w.scale, (void*)w.done, (void*)w.kcol, (void*)w.active, (void*)w.bblk, w.tc_scratch})
+                  (void*)w.scale, (void*)w.done, (void*)w.kcol, (void*)w.active, (void*)w.bblk, (void*)w.kerr, w.tc_scratch})
     dfree(c, p);
   if (w.h_active) cudaFreeHost(w.h_active);
   if (w.h_vec) cudaFreeHost(w.h_vec);
@@ -263,8 +268,11 @@ void ensure_work(Ctx* c, int R, int m, int prec) {
   w.R = R;
   w.m = m;
   w.prec = prec;
-  w.V = dalloc<unsigned char>(c, es * n * (m + 1));
-  w.Z = dalloc<unsigned char>(c, es * n * m);
+  const size_t nv = (size_t)krylov_stride(E, R);
+  w.V = dalloc<unsigned char>(c, es * nv * (m + 1));
+  w.Z = dalloc<unsigned char>(c, es * nv * m);
+  w.kerr = dalloc<int32_t>(c, 1);
+  CK(cudaMemsetAsync(w.kerr, 0, sizeof(int32_t), c->stream));
   w.r = dalloc<double2>(c, n);
   w.x = dalloc<double2>(c, n);
   if (prec == 1) w.xdf = dalloc<float4>(c, n);
@@ -379,7 +387,7 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
   ensure_work(c, R, m, wp);
   Work& w = c->work;
   cudaStream_t s = c->stream;
-  const int64_t vstride = E * R;
+  const int64_t vstride = krylov_stride(E, R);
   const size_t es = wp == 0 ? sizeof(double2) : sizeof(float2);
   auto Vp = [&](int i) { return (void*)((unsigned char*)w.V + es * vstride * i); };
   auto Zp = [&](int i) { return use_p ? (void*)((unsigned char*)w.Z + es * vstride * i) : Vp(i); };
@@ -427,9 +435,9 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
       {
         ProfScope ps(c, MW_K_CGS_DOTS, (double)es * E * R * (j + 2));
         np = wp == 0 ? mwk::cgs_dots_f64((const double2*)w.V, vstride, j + 1, (const double2*)Vp(j + 1), E, R,
-                                         w.part, s)
+                                         w.part, w.kerr, s)
                      : mwk::cgs_dots_f32((const float2*)w.V, vstride, j + 1, (const float2*)Vp(j + 1), E, R,
-                                         w.part, s);
+                                         w.part, w.kerr, s);
         mwk::reduce_h(w.part, np, j + 1, R, w.h, s);
       }
       int nu;
@@ -567,6 +575,14 @@ void solve_all(Ctx* c, const mw_solve_opts& o, int ncols, const std::vector<cons
     if (e != 0) {
       CK(cudaMemsetAsync(c->prec.tc.err, 0, sizeof(int32_t), s));
       throw Fail{MW_ETIMEOUT, "tensor-core preconditioner apply: bounded wait ran out (code " + std::to_string(e) + ")"};
+    }
+  }
+  if (c->work.kerr) {
+    int32_t e = 0;
+    CK(cudaMemcpy(&e, c->work.kerr, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+      CK(cudaMemsetAsync(c->work.kerr, 0, sizeof(int32_t), s));
+      throw Fail{MW_ETIMEOUT, "streaming Gram-Schmidt dots: bounded wait ran out (code " + std::to_string(e) + ")"};
     }
   }
   int nconv = 0;

@@ -116,10 +116,14 @@ int residual_f64(const int64_t* rp, const int32_t* ci, const double2* A, const d
                  double2* Rv, double* part, int64_t E, int R, cudaStream_t s);
 
 // Krylov (K6-K8, K15)
+// h_part = V^H w per part; returns the number of parts written.  `err` (device int, may be null)
+// receives a nonzero code if a bounded wait of the streaming kernel gave up.
 int cgs_dots_f64(const double2* V, int64_t vstride, int nvec, const double2* w, int64_t E, int R,
-                 double2* part, cudaStream_t s);
+                 double2* part, int32_t* err, cudaStream_t s);
 int cgs_dots_f32(const float2* V, int64_t vstride, int nvec, const float2* w, int64_t E, int R,
-                 double2* part, cudaStream_t s);
+                 double2* part, int32_t* err, cudaStream_t s);
+// Largest part count cgs_dots can return.
+constexpr int kCgsDotsMaxParts = 152 * 4 * 8;
 void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s);
 int cgs_update_f64(const double2* V, int64_t vstride, int nvec, const double2* h, double2* w, int64_t E, int R,
                    double* npart, cudaStream_t s);
