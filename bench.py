@@ -48,6 +48,7 @@ def _args(argv=None):
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--plain-cols", type=int, default=1, help="columns timed on the plain FP64 path (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graphs", action="store_true", help="replay restart cycles from captured CUDA graphs")
     ap.add_argument("--cpu-sample-subdomains", type=int, default=24)
     ap.add_argument("--inversion", default=None, choices=["tiny", "reduced", "full"],
                     help="time-to-misfit of the regularised inversion instead of RHS-solves/s")
@@ -237,6 +238,7 @@ def run_mine(a):
     eps0 = np.stack([healthy.eps.real, healthy.eps.imag], 1)
     c = mw.Context(local, stream.cuda_stream)
     setup = {}
+    c.set_graphs(a.graphs)
     t = time.perf_counter()
     info = c.set_mesh(healthy.mesh.xyz, healthy.mesh.tets)
     torch.cuda.synchronize()
@@ -271,12 +273,15 @@ def run_mine(a):
         c.assemble_dev(freqs, eps_d, healthy.eps_bg)
         return c.gradient_dev(So_d, Se_d, g_d, a.alpha, opts)
 
+    # the profiler is on during warm-up too, so the restart cycles the timed steps replay (captured
+    # with their profiling events) are captured here, outside the timed region
+    c.profile_enable((1 << mw.MW_K_NCLASS) - 1)
     for _ in range(a.warmup):
         step_dev()
     torch.cuda.synchronize()
+    c.profile_read()            # discard the warm-up samples
     if world > 1:
         dist.barrier()
-    c.profile_enable((1 << mw.MW_K_NCLASS) - 1)
     l0 = mw.kernel_launches()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -382,6 +387,7 @@ def run_mine(a):
                        "rhs_solves_per_step": units, "subdomains": n_sub, "overlap": a.overlap,
                        "n_s_mean": float(sizes.mean()), "n_s_max": int(sizes.max()),
                        "solver": "GMRES-IR: FP64 outer residual, FGMRES(50) inner FP32 + ORAS",
+                       "cycles": "CUDA graph per restart cycle (conditional nodes)" if a.graphs else "eager",
                        "preconditioner_apply": {2: "bf16 tcgen05", 1: "fp32 cuda-core"}.get(prec, str(prec)),
                        "tol": 1e-8, "inner_tol": a.inner_tol, "alpha": a.alpha,
                        "l2": "inputs larger than L2 (subdomain inverses and Krylov basis are GBs)"},

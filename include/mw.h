@@ -100,6 +100,17 @@ void mw_destroy(mw_ctx* ctx);
 const char* mw_last_error(const mw_ctx* ctx);
 /* Cap on the context's device allocations in bytes (0 = no cap).  Exceeding it gives MW_ENOMEM. */
 mw_status mw_set_memory_cap(mw_ctx* ctx, int64_t bytes);
+/* Restart cycles as CUDA graphs (default off).  With enable != 0, a Krylov cycle that may run all
+ * `restart` steps is captured once (per frequency, block width, restart length, precision,
+ * output buffer and profiler mask) and replayed with one launch and one host synchronisation
+ * per cycle: each Arnoldi step's kernels sit in conditional graph nodes that run while a column
+ * of the block is still active (Sec. IV-C's GMRES, unchanged arithmetic: same kernels, same
+ * order, bit-identical results).  Capture is part of setup; a capture is dropped when a buffer
+ * it names is freed (new mesh, preconditioner or workspace).  Every captured step slot costs a
+ * few microseconds of conditional-node evaluation even when skipped, so cycles that stop well
+ * before `restart` steps run faster eagerly.  enable = 0 (the default) runs cycles eagerly, with
+ * a host check of the active-column count after every step, and frees the graphs. */
+mw_status mw_set_graphs(mw_ctx* ctx, int32_t enable);
 
 /* ---- mesh (Sec. IV-A; Nedelec r = 1, Sec. IV-D) ------------------------------------- */
 /* xyz [n_vert][3] metres; tet_vert [n_tet][4] vertex ids (any orientation, non-degenerate).

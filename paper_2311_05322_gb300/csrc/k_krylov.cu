@@ -702,7 +702,26 @@ int update_launch(const T* V, int64_t vstride, int nvec, const double2* h, T* w,
   return kBlocks;
 }
 
+// Sets the conditional handles of one captured Arnoldi step: the step's bodies run while some
+// column of the block is still active.
+struct StepHandles {
+  cudaGraphConditionalHandle h[kMaxStepHandles];
+  int n;
+};
+__global__ void set_step_conditions_kernel(StepHandles sh, const int32_t* __restrict__ active) {
+  const unsigned v = *active != 0 ? 1u : 0u;
+  for (int i = 0; i < sh.n; ++i) cudaGraphSetConditional(sh.h[i], v);
+}
+
 }  // namespace
+
+void set_step_conditions(const unsigned long long* handles, int n, const int32_t* active, cudaStream_t s) {
+  note_launch(1);
+  StepHandles sh;
+  sh.n = n < kMaxStepHandles ? n : kMaxStepHandles;
+  for (int i = 0; i < sh.n; ++i) sh.h[i] = (cudaGraphConditionalHandle)handles[i];
+  set_step_conditions_kernel<<<1, 1, 0, s>>>(sh, active);
+}
 
 int cgs_dots_f64(const double2* V, int64_t vstride, int nvec, const double2* w, int64_t E, int R, double2* part,
                  int32_t* err, cudaStream_t s) {

@@ -92,6 +92,9 @@ struct Profiler {
   size_t used = 0;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
   double bytes[MW_K_NCLASS] = {0, 0, 0, 0, 0};
+  // device time and launches of classes timed inside replayed cycle graphs
+  double graph_ms[MW_K_NCLASS] = {0, 0, 0, 0, 0};
+  int64_t graph_launches[MW_K_NCLASS] = {0, 0, 0, 0, 0};
   cudaEvent_t get() {
     if (used == pool.size()) {
       cudaEvent_t e;
@@ -121,6 +124,28 @@ struct NnState {
   int32_t* idx = nullptr;
   // parameter offsets (floats) in the flat layout W1 b1 W2 b2 C1 c1 C2 c2 C3 c3
   int64_t oW1, ob1, oW2, ob2, oC1, oc1, oC2, oc2, oC3, oc3;
+};
+
+// One restart cycle of the batched FGMRES captured as a CUDA graph: the start vector, m
+// Arnoldi steps whose kernel segments sit in conditional (IF) nodes that run while a column of
+// the block is active, the least-squares solve, the solution update and the copy of the
+// per-column step counts to the host.  Valid while no device buffer it names has been freed
+// (generation `gen`) and for the key below.
+struct CycleGraph {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t gen = 0, last_use = 0;
+  int f = -1, R = 0, m = 0, wp = -1;
+  bool use_p = false;
+  const void* X = nullptr;
+  uint32_t mask = 0;
+  struct Mark {
+    int cls, step;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<Mark> marks;           // profiler events around the segments of each step
+  int64_t fixed_launches = 0;        // kernels outside the steps
+  int64_t step_launches = 0;         // kernels inside one step's conditional bodies
 };
 
 struct Ctx {
@@ -168,6 +193,12 @@ struct Ctx {
   std::vector<double2*> d_Badj;
   double* d_red = nullptr;     // reduction scratch
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // captured restart cycles
+  bool graphs_on = false;
+  uint64_t graph_gen = 1, graph_clock = 0;
+  std::vector<CycleGraph> graphs;
+  cudaStream_t cap_s = nullptr, body_s = nullptr;  // private capture streams
 };
 
 struct Fail {
@@ -204,6 +235,7 @@ T* dalloc(Ctx* c, size_t n) {
 
 void dfree(Ctx* c, void* p) {
   if (!p) return;
+  c->graph_gen++;  // a captured cycle may name this buffer
   auto it = c->allocs.find(p);
   if (it != c->allocs.end()) {
     c->mem_used -= it->second;
@@ -301,18 +333,27 @@ void ensure_work(Ctx* c, int R, int m, int prec) {
 // ---------------------------------------------------------------------------------------
 // preconditioner apply on basis vectors of the working precision
 // ---------------------------------------------------------------------------------------
+// Size the tensor-core apply's gathered-operand scratch before a capture (no allocation may
+// happen while the stream is captured).
+void ensure_prec_scratch(Ctx* c, int R) {
+  Prec& p = c->prec;
+  if (!p.ready || p.apply_prec != 2) return;
+  Work& w = c->work;
+  const size_t need = mwk::tc_scratch_bytes(p.tc, R);
+  if (w.tc_bytes < need) {
+    dfree(c, w.tc_scratch);
+    w.tc_scratch = dalloc<unsigned char>(c, need);
+    w.tc_bytes = need;
+  }
+}
+
 void apply_prec(Ctx* c, int f, int work_prec, const void* v, void* z, int R) {
   Prec& p = c->prec;
   cudaStream_t s = c->stream;
   if (p.apply_prec == 2) {
     require(work_prec == 1, MW_EINVAL, "BF16 preconditioner needs the mixed-precision solve");
     Work& w = c->work;
-    size_t need = mwk::tc_scratch_bytes(p.tc, R);
-    if (w.tc_bytes < need) {
-      dfree(c, w.tc_scratch);
-      w.tc_scratch = dalloc<unsigned char>(c, need);
-      w.tc_bytes = need;
-    }
+    ensure_prec_scratch(c, R);
     mwk::oras_apply_tc(p.tc, p.topo(), p.W[f], (const float2*)v, (float2*)z, R, w.tc_scratch, s);
   } else {
     const int need = work_prec;  // 0 FP64, 1 FP32
@@ -377,6 +418,253 @@ struct BlockStats {
 };
 
 // Solve A_f X = B for a block of R columns ([E][R] layout, FP64 in and out).
+// Arguments of one restart cycle.
+struct CycleArgs {
+  int f, R, m, wp;
+  bool use_p;
+  double2* X;
+  int64_t E, vstride;
+  size_t es;
+  void* Vp(const Work& w, int i) const { return (unsigned char*)w.V + es * vstride * i; }
+  void* Zp(const Work& w, int i) const { return use_p ? (unsigned char*)w.Z + es * vstride * i : Vp(w, i); }
+};
+
+// Arnoldi step j as segments (preconditioner apply, SpMM, Gram-Schmidt dots, Gram-Schmidt
+// update, Givens and scaling); seg(cls, bytes, fn) runs fn, which launches on c->stream.
+template <class Seg>
+void arnoldi_step(Ctx* c, const CycleArgs& a, int j, Seg&& seg) {
+  Work& w = c->work;
+  const int64_t E = a.E;
+  const int R = a.R;
+  if (a.use_p) seg(MW_K_ORAS, oras_bytes(c, R), [&] { apply_prec(c, a.f, a.wp, a.Vp(w, j), a.Zp(w, j), R); });
+  seg(MW_K_SPMM, (double)c->topo.nnz * (a.es + 4) + 8.0 * (E + 1) + 2.0 * a.es * E * R, [&] {
+    if (a.wp == 0)
+      mwk::spmm_f64(c->d_row, c->d_col, c->A64[a.f], (const double2*)a.Zp(w, j), (double2*)a.Vp(w, j + 1), E, R,
+                    c->stream);
+    else
+      mwk::spmm_f32(c->d_row, c->d_col, c->A32[a.f], (const float2*)a.Zp(w, j), (float2*)a.Vp(w, j + 1), E, R,
+                    c->stream);
+  });
+  seg(MW_K_CGS_DOTS, (double)a.es * E * R * (j + 2), [&] {
+    const int np = a.wp == 0 ? mwk::cgs_dots_f64((const double2*)w.V, a.vstride, j + 1,
+                                                 (const double2*)a.Vp(w, j + 1), E, R, w.part, w.kerr, c->stream)
+                             : mwk::cgs_dots_f32((const float2*)w.V, a.vstride, j + 1,
+                                                 (const float2*)a.Vp(w, j + 1), E, R, w.part, w.kerr, c->stream);
+    mwk::reduce_h(w.part, np, j + 1, R, w.h, c->stream);
+  });
+  int nu = 0;
+  seg(MW_K_CGS_UPDATE, (double)a.es * E * R * (j + 3), [&] {
+    nu = a.wp == 0 ? mwk::cgs_update_f64((const double2*)w.V, a.vstride, j + 1, w.h, (double2*)a.Vp(w, j + 1), E,
+                                         R, w.npart, c->stream)
+                   : mwk::cgs_update_f32((const float2*)w.V, a.vstride, j + 1, w.h, (float2*)a.Vp(w, j + 1), E,
+                                         R, w.npart, c->stream);
+  });
+  seg(-1, 0.0, [&] {
+    CK(cudaMemsetAsync(w.active, 0, sizeof(int32_t), c->stream));
+    mwk::givens_step(w.h, w.npart, nu, j, a.m, R, w.H, w.cs, w.g, w.target, w.done, w.kcol, w.scale, w.active,
+                     c->stream);
+    if (a.wp == 0)
+      mwk::scale_cols_f64((double2*)a.Vp(w, j + 1), w.scale, E, R, c->stream);
+    else
+      mwk::scale_cols_f32((float2*)a.Vp(w, j + 1), w.scale, E, R, c->stream);
+  });
+}
+constexpr int kStepSegments = 5;
+
+void cycle_start(Ctx* c, const CycleArgs& a) {
+  Work& w = c->work;
+  if (a.wp == 0)
+    mwk::normalize_start_f64(w.r, w.rnorm, w.done, a.E, a.R, (double2*)a.Vp(w, 0), c->stream);
+  else
+    mwk::normalize_start_f32(w.r, w.rnorm, w.done, a.E, a.R, (float2*)a.Vp(w, 0), c->stream);
+}
+
+// Least squares, x += Z y, and the per-column step counts into w.h_ivec (not yet synchronised).
+void cycle_finish(Ctx* c, const CycleArgs& a) {
+  Work& w = c->work;
+  mwk::solve_hessenberg(w.H, w.g, w.kcol, a.m, a.R, w.y, c->stream);
+  if (a.wp == 0)
+    mwk::update_x_f64((const double2*)a.Zp(w, 0), a.vstride, w.y, w.kcol, a.m, a.X, a.E, a.R, c->stream);
+  else
+    mwk::update_x_f32((const float2*)a.Zp(w, 0), a.vstride, w.y, w.kcol, a.m, a.X, a.E, a.R, c->stream);
+  check_launch("solution update");
+  CK(cudaMemcpyAsync(w.h_ivec, w.kcol, sizeof(int32_t) * a.R, cudaMemcpyDeviceToHost, c->stream));
+}
+
+// Eager cycle: the host reads the active-column count after every step.  Returns the steps run.
+int cycle_eager(Ctx* c, const CycleArgs& a, int max_steps) {
+  cycle_start(c, a);
+  int j = 0;
+  while (j < a.m) {
+    arnoldi_step(c, a, j, [&](int cls, double bytes, auto&& fn) {
+      if (cls >= 0) {
+        ProfScope ps(c, cls, bytes);
+        fn();
+      } else {
+        fn();
+      }
+    });
+    check_launch("arnoldi step");
+    ++j;
+    if (read_active(c) == 0 || j >= max_steps) break;
+  }
+  cycle_finish(c, a);
+  CK(cudaStreamSynchronize(c->stream));
+  return j;
+}
+
+void destroy_graph(CycleGraph& G) {
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  for (auto& mk : G.marks) {
+    cudaEventDestroy(mk.a);
+    cudaEventDestroy(mk.b);
+  }
+  G = CycleGraph();
+}
+
+void drop_graphs(Ctx* c) {
+  for (auto& G : c->graphs) destroy_graph(G);
+  c->graphs.clear();
+}
+
+// Captures one cycle for the arguments `a` into conditional graph nodes.
+CycleGraph capture_cycle(Ctx* c, const CycleArgs& a) {
+  if (!c->cap_s) CK(cudaStreamCreateWithFlags(&c->cap_s, cudaStreamNonBlocking));
+  if (!c->body_s) CK(cudaStreamCreateWithFlags(&c->body_s, cudaStreamNonBlocking));
+  if (a.use_p) ensure_prec_scratch(c, a.R);
+  Work& w = c->work;
+  CycleGraph G;
+  G.f = a.f;
+  G.R = a.R;
+  G.m = a.m;
+  G.wp = a.wp;
+  G.use_p = a.use_p;
+  G.X = a.X;
+  G.mask = c->prof.mask;
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  const cudaStream_t user = c->stream;
+  const long long l0 = g_launches.load();
+  bool capturing = false, body_capturing = false;
+  try {
+    CK(cudaStreamBeginCaptureToGraph(c->cap_s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capturing = true;
+    c->stream = c->cap_s;
+    cycle_start(c, a);
+    long long body = 0;
+    for (int j = 0; j < a.m; ++j) {
+      unsigned long long hs[kStepSegments];
+      for (int k = 0; k < kStepSegments; ++k) {
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+        hs[k] = (unsigned long long)h;
+      }
+      mwk::set_step_conditions(hs, kStepSegments, w.active, c->cap_s);
+      int k = 0;
+      const long long ls = g_launches.load();
+      arnoldi_step(c, a, j, [&](int cls, double bytes, auto&& fn) {
+        const bool prof = cls >= 0 && (c->prof.mask & (1u << cls));
+        CycleGraph::Mark mk{cls, j, nullptr, nullptr, bytes};
+        if (prof) {
+          CK(cudaEventCreate(&mk.a));
+          CK(cudaEventCreate(&mk.b));
+          G.marks.push_back(mk);
+          CK(cudaEventRecordWithFlags(mk.a, c->cap_s, cudaEventRecordExternal));
+        }
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        CK(cudaStreamGetCaptureInfo(c->cap_s, &cst, nullptr, &cg, &deps, nullptr, &nd));
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = (cudaGraphConditionalHandle)hs[k++];
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np));
+        CK(cudaStreamUpdateCaptureDependencies(c->cap_s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        CK(cudaStreamBeginCaptureToGraph(c->body_s, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed));
+        body_capturing = true;
+        c->stream = c->body_s;
+        fn();
+        check_launch("captured arnoldi segment");
+        c->stream = c->cap_s;
+        cudaGraph_t bg = nullptr;
+        CK(cudaStreamEndCapture(c->body_s, &bg));
+        body_capturing = false;
+        if (prof) CK(cudaEventRecordWithFlags(mk.b, c->cap_s, cudaEventRecordExternal));
+      });
+      if (j == 0) body = g_launches.load() - ls;
+    }
+    cycle_finish(c, a);
+    cudaGraph_t out = nullptr;
+    CK(cudaStreamEndCapture(c->cap_s, &out));
+    capturing = false;
+    c->stream = user;
+    G.step_launches = body;
+    G.fixed_launches = (g_launches.load() - l0) - (long long)a.m * body;
+    g_launches.fetch_sub(g_launches.load() - l0);  // nothing ran yet
+    CK(cudaGraphInstantiate(&G.exec, g, 0));
+    cudaGraphDestroy(g);
+  } catch (...) {
+    c->stream = user;
+    cudaGraph_t t = nullptr;
+    if (body_capturing) cudaStreamEndCapture(c->body_s, &t);
+    if (capturing) cudaStreamEndCapture(c->cap_s, &t);
+    cudaGraphDestroy(g);
+    g_launches.fetch_sub(g_launches.load() - l0);
+    destroy_graph(G);
+    cudaGetLastError();
+    throw;
+  }
+  G.gen = c->graph_gen;
+  return G;
+}
+
+// Graph cycle: one launch and one host synchronisation per restart cycle.  Returns the steps run
+// (the largest per-column step count).
+int cycle_graph(Ctx* c, const CycleArgs& a) {
+  CycleGraph* G = nullptr;
+  for (auto& g : c->graphs)
+    if (g.gen == c->graph_gen && g.f == a.f && g.R == a.R && g.m == a.m && g.wp == a.wp && g.use_p == a.use_p &&
+        g.X == a.X && g.mask == c->prof.mask) {
+      G = &g;
+      break;
+    }
+  if (!G) {
+    // stale graphs name freed buffers; the cache holds a handful of live ones
+    std::vector<CycleGraph> keep;
+    for (auto& g : c->graphs) {
+      if (g.gen == c->graph_gen && keep.size() < 7)
+        keep.push_back(g);
+      else
+        destroy_graph(g);
+    }
+    c->graphs.swap(keep);
+    c->graphs.push_back(capture_cycle(c, a));
+    G = &c->graphs.back();
+  }
+  G->last_use = ++c->graph_clock;
+  CK(cudaGraphLaunch(G->exec, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  Work& w = c->work;
+  int steps = 0;
+  for (int q = 0; q < a.R; ++q) steps = std::max(steps, (int)w.h_ivec[q]);
+  g_launches.fetch_add(G->fixed_launches + (long long)steps * G->step_launches);
+  for (auto& mk : G->marks) {
+    if (mk.step >= steps) continue;
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, mk.a, mk.b));
+    c->prof.graph_ms[mk.cls] += t;
+    c->prof.graph_launches[mk.cls] += 1;
+    c->prof.bytes[mk.cls] += mk.bytes;
+  }
+  return steps;
+}
+
+// Solve A_f X = B for a block of R columns ([E][R] layout, FP64 in and out).
 BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const mw_solve_opts& o,
                        std::vector<int32_t>& its_out) {
   const int64_t E = c->topo.n_edge;
@@ -387,10 +675,7 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
   ensure_work(c, R, m, wp);
   Work& w = c->work;
   cudaStream_t s = c->stream;
-  const int64_t vstride = krylov_stride(E, R);
-  const size_t es = wp == 0 ? sizeof(double2) : sizeof(float2);
-  auto Vp = [&](int i) { return (void*)((unsigned char*)w.V + es * vstride * i); };
-  auto Zp = [&](int i) { return use_p ? (void*)((unsigned char*)w.Z + es * vstride * i) : Vp(i); };
+  CycleArgs a{f, R, m, wp, use_p, X, E, krylov_stride(E, R), wp == 0 ? sizeof(double2) : sizeof(float2)};
 
   CK(cudaMemsetAsync(X, 0, sizeof(double2) * E * R, s));
   int nb = mwk::colnorm2_f64(B, E, R, w.npart, s);
@@ -414,62 +699,10 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
     st.have_relres = true;
     if (read_active(c) == 0 || total >= o.max_it) break;
     st.have_relres = false;
-    if (wp == 0)
-      mwk::normalize_start_f64(w.r, w.rnorm, w.done, E, R, (double2*)Vp(0), s);
-    else
-      mwk::normalize_start_f32(w.r, w.rnorm, w.done, E, R, (float2*)Vp(0), s);
-    int j = 0;
-    for (; j < m; ++j) {
-      if (use_p) {
-        ProfScope ps(c, MW_K_ORAS, oras_bytes(c, R));
-        apply_prec(c, f, wp, Vp(j), Zp(j), R);
-      }
-      {
-        ProfScope ps(c, MW_K_SPMM, (double)c->topo.nnz * (es + 4) + 8.0 * (E + 1) + 2.0 * es * E * R);
-        if (wp == 0)
-          mwk::spmm_f64(c->d_row, c->d_col, c->A64[f], (const double2*)Zp(j), (double2*)Vp(j + 1), E, R, s);
-        else
-          mwk::spmm_f32(c->d_row, c->d_col, c->A32[f], (const float2*)Zp(j), (float2*)Vp(j + 1), E, R, s);
-      }
-      int np;
-      {
-        ProfScope ps(c, MW_K_CGS_DOTS, (double)es * E * R * (j + 2));
-        np = wp == 0 ? mwk::cgs_dots_f64((const double2*)w.V, vstride, j + 1, (const double2*)Vp(j + 1), E, R,
-                                         w.part, w.kerr, s)
-                     : mwk::cgs_dots_f32((const float2*)w.V, vstride, j + 1, (const float2*)Vp(j + 1), E, R,
-                                         w.part, w.kerr, s);
-        mwk::reduce_h(w.part, np, j + 1, R, w.h, s);
-      }
-      int nu;
-      {
-        ProfScope ps(c, MW_K_CGS_UPDATE, (double)es * E * R * (j + 3));
-        nu = wp == 0 ? mwk::cgs_update_f64((const double2*)w.V, vstride, j + 1, w.h, (double2*)Vp(j + 1), E, R,
-                                           w.npart, s)
-                     : mwk::cgs_update_f32((const float2*)w.V, vstride, j + 1, w.h, (float2*)Vp(j + 1), E, R,
-                                           w.npart, s);
-      }
-      CK(cudaMemsetAsync(w.active, 0, sizeof(int32_t), s));
-      mwk::givens_step(w.h, w.npart, nu, j, m, R, w.H, w.cs, w.g, w.target, w.done, w.kcol, w.scale, w.active, s);
-      if (wp == 0)
-        mwk::scale_cols_f64((double2*)Vp(j + 1), w.scale, E, R, s);
-      else
-        mwk::scale_cols_f32((float2*)Vp(j + 1), w.scale, E, R, s);
-      check_launch("arnoldi step");
-      ++total;
-      st.steps++;
-      if (read_active(c) == 0 || total >= o.max_it) {
-        ++j;
-        break;
-      }
-    }
-    mwk::solve_hessenberg(w.H, w.g, w.kcol, m, R, w.y, s);
-    if (wp == 0)
-      mwk::update_x_f64((const double2*)Zp(0), vstride, w.y, w.kcol, m, X, E, R, s);
-    else
-      mwk::update_x_f32((const float2*)Zp(0), vstride, w.y, w.kcol, m, X, E, R, s);
-    check_launch("solution update");
-    CK(cudaMemcpyAsync(w.h_ivec, w.kcol, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    // a cycle that may run all m steps is replayed from its captured graph
+    const int steps = (c->graphs_on && o.max_it - total >= m) ? cycle_graph(c, a) : cycle_eager(c, a, o.max_it - total);
+    total += steps;
+    st.steps += steps;
     for (int q = 0; q < R; ++q) its[q] += w.h_ivec[q];
   }
   its_out = its;
@@ -646,6 +879,7 @@ void release_prec(Ctx* c) {
 }
 
 void release_mesh(Ctx* c) {
+  drop_graphs(c);
   release_prec(c);
   free_work(c);
   for (auto p : c->Xf) dfree(c, p);
@@ -718,6 +952,8 @@ void mw_destroy(mw_ctx* c) {
   cudaStreamSynchronize(c->stream);
   release_mesh(c);
   for (auto& kv : c->allocs) cudaFree(kv.first);
+  if (c->cap_s) cudaStreamDestroy(c->cap_s);
+  if (c->body_s) cudaStreamDestroy(c->body_s);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
@@ -729,6 +965,13 @@ mw_status mw_set_memory_cap(mw_ctx* c, int64_t bytes) {
   return guard(c, [&] {
     require(bytes >= 0, MW_EINVAL, "cap must be >= 0");
     c->mem_cap = bytes;
+  });
+}
+
+mw_status mw_set_graphs(mw_ctx* c, int32_t enable) {
+  return guard(c, [&] {
+    c->graphs_on = enable != 0;
+    if (!c->graphs_on) drop_graphs(c);
   });
 }
 
@@ -1496,7 +1739,11 @@ mw_status mw_profile_enable(mw_ctx* c, uint32_t mask) {
     c->prof.mask = mask;
     c->prof.marks.clear();
     c->prof.used = 0;
-    for (int k = 0; k < MW_K_NCLASS; ++k) c->prof.bytes[k] = 0;
+    for (int k = 0; k < MW_K_NCLASS; ++k) {
+      c->prof.bytes[k] = 0;
+      c->prof.graph_ms[k] = 0;
+      c->prof.graph_launches[k] = 0;
+    }
   });
 }
 
@@ -1504,10 +1751,12 @@ mw_status mw_profile_read(mw_ctx* c, double* ms, int64_t* launches, double* byte
   return guard(c, [&] {
     require(ms && launches, MW_EINVAL, "null outputs");
     for (int k = 0; k < MW_K_NCLASS; ++k) {
-      ms[k] = 0;
-      launches[k] = 0;
+      ms[k] = c->prof.graph_ms[k];
+      launches[k] = c->prof.graph_launches[k];
       if (bytes) bytes[k] = c->prof.bytes[k];
       c->prof.bytes[k] = 0;
+      c->prof.graph_ms[k] = 0;
+      c->prof.graph_launches[k] = 0;
     }
     CK(cudaStreamSynchronize(c->stream));
     for (auto& m : c->prof.marks) {

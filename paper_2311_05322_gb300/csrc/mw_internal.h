@@ -124,6 +124,10 @@ int cgs_dots_f32(const float2* V, int64_t vstride, int nvec, const float2* w, in
                  double2* part, int32_t* err, cudaStream_t s);
 // Largest part count cgs_dots can return.
 constexpr int kCgsDotsMaxParts = 152 * 4 * 8;
+// Sets conditional-node handles (cudaGraphConditionalHandle values) of one captured Arnoldi
+// step to (*active != 0); at most kMaxStepHandles handles.
+constexpr int kMaxStepHandles = 8;
+void set_step_conditions(const unsigned long long* handles, int n, const int32_t* active, cudaStream_t s);
 void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s);
 int cgs_update_f64(const double2* V, int64_t vstride, int nvec, const double2* h, double2* w, int64_t E, int R,
                    double* npart, cudaStream_t s);

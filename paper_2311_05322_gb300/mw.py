@@ -69,6 +69,7 @@ _SIGS = {
     "mw_destroy": (None, [_P]),
     "mw_last_error": (C.c_char_p, [_P]),
     "mw_set_memory_cap": (C.c_int32, [_P, C.c_int64]),
+    "mw_set_graphs": (C.c_int32, [_P, C.c_int32]),
     "mw_set_mesh": (C.c_int32, [_P, C.c_int64, _P, C.c_int64, _P, C.POINTER(mw_mesh_info)]),
     "mw_get_topology": (C.c_int32, [_P, _P, _P, _P, _P, _P]),
     "mw_get_element_matrices": (C.c_int32, [_P, _P, _P, _P]),
@@ -191,6 +192,10 @@ class Context:
 
     def set_memory_cap(self, nbytes: int):
         self._check(self.lib.mw_set_memory_cap(self.h, int(nbytes)))
+
+    def set_graphs(self, enable: bool):
+        """Replay restart cycles from captured CUDA graphs, or run them eagerly (the default)."""
+        self._check(self.lib.mw_set_graphs(self.h, 1 if enable else 0))
 
     def get_topology(self):
         i = self.info

@@ -221,6 +221,57 @@ def test_solve_rhs_wide_blocks(ragged, ncols, mode, prec):
     assert _relerr(xd.cpu().numpy().T, Xref) <= (1e-8 if mode == 0 else 1e-6)
 
 
+@pytest.mark.parametrize("mode,prec,ncols", [(0, 0, 5), (1, 2, 5), (1, 2, 32)])
+def test_graph_cycles_match_eager(ragged, mode, prec, ncols):
+    """Restart cycles replayed from captured CUDA graphs (each Arnoldi step in conditional nodes
+    that run while a column is active) run the same kernels in the same order as the eager
+    cycles: fields bit-identical, same per-column Arnoldi steps, on capture and on replay."""
+    mw = _mw()
+    m, eps, pos, direc, sysm = ragged
+    c = _ctx(m, eps, [1e9], pos, direc)
+    c.setup_preconditioner(4, box_partition(m, (2, 2, 1), seed=7), 1, prec)
+    E = sysm.topo.n_edge
+    rng = np.random.default_rng(300 + ncols)
+    B = rng.normal(size=(ncols, E)) + 1j * rng.normal(size=(ncols, E))
+    bd = torch.from_numpy(B).cuda()
+    opts = mw.solve_opts(mode=mode, tol=1e-10)
+    runs = []
+    for graphs in (False, True, True):          # eager, capture + replay, cached replay
+        c.set_graphs(graphs)
+        xd = torch.empty_like(bd)
+        st = c.solve_rhs(ncols, bd, xd, opts)
+        runs.append((xd.cpu().numpy(), st))
+    x0, s0 = runs[0]
+    assert s0["n_converged"] == ncols
+    for x, st in runs[1:]:
+        assert np.array_equal(x, x0)
+        assert np.array_equal(st["iters"], s0["iters"])
+        assert st["arnoldi_steps"] == s0["arnoldi_steps"]
+
+
+def test_graph_cycles_profiled(ragged):
+    """The per-class profiler sees the kernels of replayed graphs: one timed preconditioner
+    apply, SpMM, dots and update per executed Arnoldi step, as in eager cycles."""
+    mw = _mw()
+    m, eps, pos, direc, sysm = ragged
+    c = _ctx(m, eps, [1e9], pos, direc)
+    c.setup_preconditioner(4, box_partition(m, (2, 2, 1), seed=7), 1, 2)
+    opts = mw.solve_opts(mode=mw.MW_MODE_MIXED, tol=1e-10)
+    prof = {}
+    for graphs in (False, True):
+        c.set_graphs(graphs)
+        c.profile_enable((1 << mw.MW_K_NCLASS) - 1)
+        _, st = c.solve(opts)
+        prof[graphs] = (c.profile_read(), st["arnoldi_steps"])
+        c.profile_enable(0)
+    for graphs, (p, steps) in prof.items():
+        for k in ("oras_apply", "spmm", "cgs_dots", "cgs_update"):
+            assert p[k]["launches"] == steps and p[k]["ms"] > 0 and p[k]["bytes"] > 0
+    assert prof[True][1] == prof[False][1]
+    for k in ("oras_apply", "spmm", "cgs_dots", "cgs_update"):
+        assert prof[True][0][k]["bytes"] == prof[False][0][k]["bytes"]
+
+
 def test_solve_rhs_and_reciprocity(ragged):
     mw = _mw()
     m, eps, pos, direc, sysm = ragged
