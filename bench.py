@@ -252,6 +252,9 @@ def run_mine(a):
     c.setup_preconditioner(n_sub, part, a.overlap, prec)
     torch.cuda.synchronize()
     setup["preconditioner_s"] = time.perf_counter() - t
+    t = time.perf_counter()
+    tune = c.autotune(a.n_src, mw.MW_MODE_MIXED, 50)      # launch shapes of the timed solves
+    setup["autotune_s"] = time.perf_counter() - t
     _, sizes = c.get_partition()
     opts = mw.solve_opts(mode=mw.MW_MODE_MIXED, restart=50, tol=1e-8, inner_tol=a.inner_tol, max_it=2000)
     # synthetic measurements: injured phantom (observed) and empty chamber (normalisation)
@@ -388,6 +391,7 @@ def run_mine(a):
                        "n_s_mean": float(sizes.mean()), "n_s_max": int(sizes.max()),
                        "solver": "GMRES-IR: FP64 outer residual, FGMRES(50) inner FP32 + ORAS",
                        "cycles": "CUDA graph per restart cycle (conditional nodes)" if a.graphs else "eager",
+                       "launch_shapes": {k: tune[k] for k in ("tc_stages", "dots_stages", "spmm_threads")},
                        "preconditioner_apply": {2: "bf16 tcgen05", 1: "fp32 cuda-core"}.get(prec, str(prec)),
                        "tol": 1e-8, "inner_tol": a.inner_tol, "alpha": a.alpha,
                        "l2": "inputs larger than L2 (subdomain inverses and Krylov basis are GBs)"},

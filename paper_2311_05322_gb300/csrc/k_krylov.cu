@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kDotThreads) cgs_dots_kernel(const T* __restri
 // Streaming form of the same dots for 16 <= R <= 128 with 16-byte aligned vectors.  The rows
 // are cut into tiles of TR = G * bd_rows<T>() rows (G = 256 / R row groups), about 16 KB per
 // vector; block b takes a contiguous range of tiles.  Warp 0 lane 0 streams, per tile, w and
-// then V_i0 .. V_i0+nv-1 through a ring of kBdStages shared-memory stages with bulk copies;
+// then V_i0 .. V_i0+nv-1 through a ring of NS shared-memory stages with bulk copies;
 // the 256 consumer threads (warps 1-8) map thread (c, g) = (t % R, t / R) to column c and the
 // tile rows g, g + G, ...  Each consumer keeps its w rows in registers for the whole tile,
 // forms its FP32 (FP64) partial of conj(V_i) w over its bd_rows<T>() rows, and the G partials of a
@@ -178,40 +178,41 @@ __global__ void __launch_bounds__(kDotThreads) cgs_dots_kernel(const T* __restri
 // same named barriers), drains its outstanding copies and returns.
 constexpr int kBdConsumers = 256;
 constexpr int kBdThreads = kBdConsumers + 32;
-constexpr int kBdStages = 4;
+constexpr int kBdStages = 4;      // default ring depth; 2..kBdMaxStages accepted (same result)
+constexpr int kBdMaxStages = 6;
 constexpr int kBdStageBytes = 16384;
 template <typename T>
 __host__ __device__ constexpr int bd_rows() {
   return 64 / (int)sizeof(T);   // 8 rows (FP32 complex), 4 rows (FP64 complex)
 }
 // VG * R <= 2048 accumulators of 16 bytes
-inline size_t bd_smem_bytes(int R) {
+inline size_t bd_smem_bytes(int R, int NS) {
   const int VG = std::min(64, 2048 / R);
-  return (size_t)kBdStages * kBdStageBytes + 2 * kBdConsumers * sizeof(double2) + (size_t)VG * R * sizeof(double2) +
-         2 * kBdStages * sizeof(uint64_t) + 16;
+  return (size_t)NS * kBdStageBytes + 2 * kBdConsumers * sizeof(double2) + (size_t)VG * R * sizeof(double2) +
+         2 * NS * sizeof(uint64_t) + 16;
 }
-constexpr size_t kBdMaxSmem = (size_t)kBdStages * kBdStageBytes + 2 * kBdConsumers * sizeof(double2) +
-                              2048 * sizeof(double2) + 2 * kBdStages * sizeof(uint64_t) + 16;
+constexpr size_t kBdMaxSmem = (size_t)kBdMaxStages * kBdStageBytes + 2 * kBdConsumers * sizeof(double2) +
+                              2048 * sizeof(double2) + 2 * kBdMaxStages * sizeof(uint64_t) + 16;
 
 template <typename T>
 __global__ void __launch_bounds__(kBdThreads, 2)
     cgs_dots_bulk_kernel(const T* __restrict__ V, int64_t vstride, int nvec, const T* __restrict__ w, int64_t E,
-                         int R, int G, int VG, double2* __restrict__ part, int32_t* __restrict__ err) {
+                         int R, int G, int VG, int NS, double2* __restrict__ part, int32_t* __restrict__ err) {
   using Sc = typename Traits<T>::S;
   constexpr int RPT = bd_rows<T>();
   constexpr int kStageElems = kBdStageBytes / (int)sizeof(T);
   extern __shared__ __align__(128) uint8_t bd_smem[];
   T* stage = reinterpret_cast<T*>(bd_smem);
-  T* red = reinterpret_cast<T*>(bd_smem + (size_t)kBdStages * kBdStageBytes);
-  double2* acc = reinterpret_cast<double2*>(bd_smem + (size_t)kBdStages * kBdStageBytes +
+  T* red = reinterpret_cast<T*>(bd_smem + (size_t)NS * kBdStageBytes);
+  double2* acc = reinterpret_cast<double2*>(bd_smem + (size_t)NS * kBdStageBytes +
                                             2 * kBdConsumers * sizeof(double2));
   uint64_t* full = reinterpret_cast<uint64_t*>(acc + (size_t)VG * R);
-  uint64_t* empty = full + kBdStages;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kBdStages);
+  uint64_t* empty = full + NS;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NS);
 
   const int tid = threadIdx.x;
   if (tid == 0) {
-    for (int i = 0; i < kBdStages; ++i) {
+    for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], kBdConsumers);
     }
@@ -227,8 +228,10 @@ __global__ void __launch_bounds__(kBdThreads, 2)
 
   if (tid < 32) {
     if (tid != 0) return;
-    // producer
+    // producer: ring position st with phase bit ph (st advances per item, ph flips per lap)
     int64_t it = 0;
+    int st = 0;
+    uint32_t ph = 0;
     bool stop = false;
     for (int sw = 0; sw < nsweep && !stop; ++sw) {
       const int i0 = sw * VG, nv = min(VG, nvec - i0);
@@ -237,9 +240,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
         const int64_t rows = E - r0 < TR ? E - r0 : (int64_t)TR;
         const uint32_t bytes = (uint32_t)((rows * R * (int64_t)sizeof(T)) & ~(int64_t)15);
         for (int q = -1; q < nv; ++q) {
-          const int st = (int)(it % kBdStages);
-          const int64_t use = it / kBdStages;
-          if (use > 0 && !mbar_wait(&empty[st], (uint32_t)((use - 1) & 1))) {
+          if (it >= NS && !mbar_wait(&empty[st], ph ^ 1u)) {
             atomicCAS(err, 0, 11);
             *abort_flag = 1;
           }
@@ -255,12 +256,19 @@ __global__ void __launch_bounds__(kBdThreads, 2)
             mbar_arrive(&full[st]);
           }
           ++it;
+          if (++st == NS) {
+            st = 0;
+            ph ^= 1u;
+          }
         }
       }
     }
-    // drain: every issued copy has landed before this thread leaves
-    for (int64_t k = (it > kBdStages ? it - kBdStages : 0); k < it; ++k)
-      if (!mbar_wait(&full[k % kBdStages], (uint32_t)((k / kBdStages) & 1))) atomicCAS(err, 0, 12);
+    // drain: every issued copy has landed before this thread leaves (the latest use of stage
+    // k < st is in the current lap, of stage k >= st in the previous one, if any)
+    for (int k = 0; k < NS; ++k) {
+      if (k >= st && it < NS) continue;
+      if (!mbar_wait(&full[k], k < st ? ph : ph ^ 1u)) atomicCAS(err, 0, 12);
+    }
     return;
   }
 
@@ -268,12 +276,20 @@ __global__ void __launch_bounds__(kBdThreads, 2)
   const int ct = tid - 32;
   const int c = ct % R, g = ct / R;
   const bool act = g < G;
-  int64_t it = 0, nred = 0;
-  auto wait_full = [&](int st, int64_t use) {
+  int st = 0;        // ring position and phase bit, as the producer's
+  uint32_t ph = 0;
+  int64_t nred = 0;
+  auto wait_full = [&]() {
     if (*abort_flag) return;
-    if (!mbar_wait(&full[st], (uint32_t)(use & 1))) {
+    if (!mbar_wait(&full[st], ph)) {
       atomicCAS(err, 0, 13);
       *abort_flag = 1;
+    }
+  };
+  auto advance = [&]() {
+    if (++st == NS) {
+      st = 0;
+      ph ^= 1u;
     }
   };
   for (int sw = 0; sw < nsweep; ++sw) {
@@ -287,8 +303,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
       // w tile -> registers
       T wr[RPT];
       {
-        const int st = (int)(it % kBdStages);
-        wait_full(st, it / kBdStages);
+        wait_full();
         const T* sm = stage + (size_t)st * kStageElems;
         const T* gl = w + r0 * R;
 #pragma unroll
@@ -299,11 +314,10 @@ __global__ void __launch_bounds__(kBdThreads, 2)
           if (act && row < rows) wr[k] = f < ncop ? sm[f] : gl[f];
         }
         mbar_arrive(&empty[st]);
-        ++it;
+        advance();
       }
-      for (int q = 0; q < nv; ++q) {
-        const int st = (int)(it % kBdStages);
-        wait_full(st, it / kBdStages);
+      for (int q = 0, qg = 0; q < nv; ++q, qg = (qg + 1 == G ? 0 : qg + 1)) {
+        wait_full();
         const T* sm = stage + (size_t)st * kStageElems;
         const T* gl = V + (int64_t)(i0 + q) * vstride + r0 * R;
         Sc pr = 0, pi = 0;
@@ -320,12 +334,12 @@ __global__ void __launch_bounds__(kBdThreads, 2)
           }
         }
         mbar_arrive(&empty[st]);
-        ++it;
+        advance();
         T* rb = red + (nred & 1) * kBdConsumers;
         rb[ct] = T{pr, pi};
         ++nred;
         asm volatile("bar.sync 1, %0;" ::"n"(kBdConsumers) : "memory");
-        if (act && g == q % G) {
+        if (act && g == qg) {
           Sc sr = 0, si = 0;
 #pragma unroll 8
           for (int g2 = 0; g2 < G; ++g2) {
@@ -640,7 +654,7 @@ inline int gs_blocks(int64_t n) {
 
 template <typename T>
 int dots_launch(const T* V, int64_t vstride, int nvec, const T* w, int64_t E, int R, double2* part, int32_t* err,
-                cudaStream_t s) {
+                cudaStream_t s, int stages) {
   note_launch(1);
   const bool aligned = ((uintptr_t)V % 16 == 0) && ((uintptr_t)w % 16 == 0) && ((vstride * sizeof(T)) % 16 == 0);
   if (err && aligned && R >= 16 && R <= 128 && nvec >= 1) {
@@ -655,7 +669,9 @@ int dots_launch(const T* V, int64_t vstride, int nvec, const T* w, int64_t E, in
     const int G = kBdConsumers / R;
     const int VG = std::min(64, 2048 / R);
     const int nb = 152 * 2;
-    cgs_dots_bulk_kernel<T><<<nb, kBdThreads, bd_smem_bytes(R), s>>>(V, vstride, nvec, w, E, R, G, VG, part, err);
+    const int NS = stages >= 2 && stages <= kBdMaxStages ? stages : kBdStages;
+    cgs_dots_bulk_kernel<T>
+        <<<nb, kBdThreads, bd_smem_bytes(R, NS), s>>>(V, vstride, nvec, w, E, R, G, VG, NS, part, err);
     return nb;
   }
   Shape sh = shape_for(R);
@@ -702,6 +718,18 @@ int update_launch(const T* V, int64_t vstride, int nvec, const double2* h, T* w,
   return kBlocks;
 }
 
+// Deterministic pseudo-random fill in [-1, 1) (timing inputs of the launch-shape tuner).
+template <typename F>
+__global__ void fill_pattern_kernel(F* __restrict__ x, int64_t n, uint32_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)i * 2654435761u ^ seed;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    x[i] = (F)((double)(h >> 8) * (1.0 / 8388608.0) - 1.0);
+  }
+}
+
 // Sets the conditional handles of one captured Arnoldi step: the step's bodies run while some
 // column of the block is still active.
 struct StepHandles {
@@ -715,6 +743,15 @@ __global__ void set_step_conditions_kernel(StepHandles sh, const int32_t* __rest
 
 }  // namespace
 
+void fill_pattern_f32(float* x, int64_t n, uint32_t seed, cudaStream_t s) {
+  note_launch(1);
+  fill_pattern_kernel<float><<<gs_blocks(n), 256, 0, s>>>(x, n, seed);
+}
+void fill_pattern_f64(double* x, int64_t n, uint32_t seed, cudaStream_t s) {
+  note_launch(1);
+  fill_pattern_kernel<double><<<gs_blocks(n), 256, 0, s>>>(x, n, seed);
+}
+
 void set_step_conditions(const unsigned long long* handles, int n, const int32_t* active, cudaStream_t s) {
   note_launch(1);
   StepHandles sh;
@@ -724,12 +761,12 @@ void set_step_conditions(const unsigned long long* handles, int n, const int32_t
 }
 
 int cgs_dots_f64(const double2* V, int64_t vstride, int nvec, const double2* w, int64_t E, int R, double2* part,
-                 int32_t* err, cudaStream_t s) {
-  return dots_launch<double2>(V, vstride, nvec, w, E, R, part, err, s);
+                 int32_t* err, cudaStream_t s, int stages) {
+  return dots_launch<double2>(V, vstride, nvec, w, E, R, part, err, s, stages);
 }
 int cgs_dots_f32(const float2* V, int64_t vstride, int nvec, const float2* w, int64_t E, int R, double2* part,
-                 int32_t* err, cudaStream_t s) {
-  return dots_launch<float2>(V, vstride, nvec, w, E, R, part, err, s);
+                 int32_t* err, cudaStream_t s, int stages) {
+  return dots_launch<float2>(V, vstride, nvec, w, E, R, part, err, s, stages);
 }
 void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s) {
   note_launch(1);

@@ -387,7 +387,7 @@ void tc_extract(const TcPlan& p, const OrasBatch& bt, const OrasTopo& tp, int ws
 }
 
 int tc_stages(int N);
-size_t tc_smem_bytes(int N);
+size_t tc_smem_bytes(int N, int stages);
 
 int tc_stages(int N) {
   // about 100 KB of stages per CTA so that two CTAs share an SM
@@ -396,12 +396,25 @@ int tc_stages(int N) {
   return st > 6 ? 6 : (st < 2 ? 2 : st);
 }
 
-size_t tc_smem_bytes(int N) { return (size_t)tc_stages(N) * (kATileBytes + N * 128) + 1024; }
+size_t tc_smem_bytes(int N, int stages) { return (size_t)stages * (kATileBytes + N * 128) + 1024; }
+
+int tc_default_stages(int R) { return tc_stages(2 * rpad(R)); }
+
+int tc_max_stages(int R) {
+  // the kernel holds 8 stage barriers; 1 KB of the 227 KB is left for its static shared memory
+  const int N = 2 * rpad(R);
+  int st = tc_min_stages;
+  while (st < 8 && tc_smem_bytes(N, st + 1) <= (size_t)226 * 1024) ++st;
+  return st;
+}
 
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
-                   void* scratch, cudaStream_t s) {
+                   void* scratch, cudaStream_t s, int stages) {
   const int Rp = rpad(R);
   const int N = 2 * Rp;
+  if (stages <= 0) stages = tc_stages(N);
+  if (stages < tc_min_stages) stages = tc_min_stages;
+  if (stages > tc_max_stages(R)) stages = tc_max_stages(R);
   note_launch(2);
   const size_t gsm = (size_t)N * 128;
   static size_t gattr = 0;
@@ -424,12 +437,12 @@ void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const flo
   a.z = z;
   a.R = R;
   a.N = N;
-  a.stages = tc_stages(N);
+  a.stages = stages;
   uint32_t cols = 32;
   while ((int)cols < N) cols <<= 1;
   a.tmem_cols = cols;
   a.err = p.err;
-  const size_t smem = tc_smem_bytes(N);
+  const size_t smem = tc_smem_bytes(N, stages);
   static size_t attr = 0;
   if (smem > attr) {
     cudaFuncSetAttribute(oras_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -39,8 +39,15 @@ size_t tc_w_bytes(const TcPlan& p);
 size_t tc_scratch_bytes(const TcPlan& p, int R);
 void tc_extract(const TcPlan& p, const OrasBatch& bt, const OrasTopo& tp, int ws_prec, const void* ws, void* W,
                 cudaStream_t s);
+// stages: shared-memory pipeline depth of the MMA kernel (0 = default; the result does not depend
+// on it, only the speed).
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
-                   void* scratch, cudaStream_t s);
+                   void* scratch, cudaStream_t s, int stages = 0);
+// Pipeline depths the MMA kernel accepts for R columns: [tc_min_stages, tc_max_stages(R)]; the
+// default depth for R columns.
+constexpr int tc_min_stages = 2;
+int tc_max_stages(int R);
+int tc_default_stages(int R);
 
 // Launches the bounded-wait self-test (see k_oras_tc.cu); *code (device) gets 0 or 5.
 void bounded_wait_probe(long long limit, int32_t* code, cudaStream_t s);

@@ -27,7 +27,7 @@ __device__ __forceinline__ void cmac(T& acc, T a, T x) {
 }
 
 template <typename T, int CPL>
-__global__ void __launch_bounds__(256) spmm_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+__global__ void __launch_bounds__(512) spmm_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                                    const T* __restrict__ A, const T* __restrict__ X, T* __restrict__ Y,
                                                    int64_t E, int R, int tpr_log2) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -116,24 +116,25 @@ inline Shape shape_for(int R) {
 
 template <typename T>
 void spmm_launch(const int64_t* rp, const int32_t* ci, const T* A, const T* X, T* Y, int64_t E, int R,
-                 cudaStream_t s) {
+                 cudaStream_t s, int threads) {
+  if (threads != 128 && threads != 256 && threads != 512) threads = 256;
   note_launch(1);
   Shape sh = shape_for(R);
   if (R > 128) {
     // wide blocks: process 128 columns at a time is not supported by the layout; caller splits.
     return;
   }
-  const int64_t threads = E << sh.tpr_log2;
-  const int blocks = (int)((threads + 255) / 256);
+  const int64_t nthr = E << sh.tpr_log2;
+  const int blocks = (int)((nthr + threads - 1) / threads);
   switch (sh.cpl) {
     case 1:
-      spmm_kernel<T, 1><<<blocks, 256, 0, s>>>(rp, ci, A, X, Y, E, R, sh.tpr_log2);
+      spmm_kernel<T, 1><<<blocks, threads, 0, s>>>(rp, ci, A, X, Y, E, R, sh.tpr_log2);
       break;
     case 2:
-      spmm_kernel<T, 2><<<blocks, 256, 0, s>>>(rp, ci, A, X, Y, E, R, sh.tpr_log2);
+      spmm_kernel<T, 2><<<blocks, threads, 0, s>>>(rp, ci, A, X, Y, E, R, sh.tpr_log2);
       break;
     default:
-      spmm_kernel<T, 4><<<blocks, 256, 0, s>>>(rp, ci, A, X, Y, E, R, sh.tpr_log2);
+      spmm_kernel<T, 4><<<blocks, threads, 0, s>>>(rp, ci, A, X, Y, E, R, sh.tpr_log2);
       break;
   }
 }
@@ -141,12 +142,12 @@ void spmm_launch(const int64_t* rp, const int32_t* ci, const T* A, const T* X, T
 }  // namespace
 
 void spmm_f64(const int64_t* rp, const int32_t* ci, const double2* A, const double2* X, double2* Y, int64_t E, int R,
-              cudaStream_t s) {
-  spmm_launch<double2>(rp, ci, A, X, Y, E, R, s);
+              cudaStream_t s, int threads) {
+  spmm_launch<double2>(rp, ci, A, X, Y, E, R, s, threads);
 }
 void spmm_f32(const int64_t* rp, const int32_t* ci, const float2* A, const float2* X, float2* Y, int64_t E, int R,
-              cudaStream_t s) {
-  spmm_launch<float2>(rp, ci, A, X, Y, E, R, s);
+              cudaStream_t s, int threads) {
+  spmm_launch<float2>(rp, ci, A, X, Y, E, R, s, threads);
 }
 
 int residual_f64(const int64_t* rp, const int32_t* ci, const double2* A, const double2* X, const double2* B,

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -126,6 +127,15 @@ struct NnState {
   int64_t oW1, ob1, oW2, ob2, oC1, oc1, oC2, oc2, oC3, oc3;
 };
 
+// Launch shapes of the solve kernels for one block shape, picked by timing; none of them changes
+// the arithmetic (see mw_autotune).  0 = default shape.
+struct Tuned {
+  int R = 0, wp = -1, m = 0;
+  bool tc = false;                 // BF16 tensor-core preconditioner in use
+  int tc_stages = 0, dots_stages = 0, spmm_threads = 256;
+  std::vector<std::pair<int, double>> tc_t, dots_t, spmm_t;  // (candidate, ms per launch)
+};
+
 // One restart cycle of the batched FGMRES captured as a CUDA graph: the start vector, m
 // Arnoldi steps whose kernel segments sit in conditional (IF) nodes that run while a column of
 // the block is active, the least-squares solve, the solution update and the copy of the
@@ -193,6 +203,10 @@ struct Ctx {
   std::vector<double2*> d_Badj;
   double* d_red = nullptr;     // reduction scratch
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // tuned launch shapes
+  bool autotune_on = true;
+  std::vector<Tuned> tuned;
 
   // captured restart cycles
   bool graphs_on = false;
@@ -347,14 +361,14 @@ void ensure_prec_scratch(Ctx* c, int R) {
   }
 }
 
-void apply_prec(Ctx* c, int f, int work_prec, const void* v, void* z, int R) {
+void apply_prec(Ctx* c, int f, int work_prec, const void* v, void* z, int R, int stages = 0) {
   Prec& p = c->prec;
   cudaStream_t s = c->stream;
   if (p.apply_prec == 2) {
     require(work_prec == 1, MW_EINVAL, "BF16 preconditioner needs the mixed-precision solve");
     Work& w = c->work;
     ensure_prec_scratch(c, R);
-    mwk::oras_apply_tc(p.tc, p.topo(), p.W[f], (const float2*)v, (float2*)z, R, w.tc_scratch, s);
+    mwk::oras_apply_tc(p.tc, p.topo(), p.W[f], (const float2*)v, (float2*)z, R, w.tc_scratch, s, stages);
   } else {
     const int need = work_prec;  // 0 FP64, 1 FP32
     require(p.apply_prec == need, MW_EINVAL,
@@ -425,6 +439,7 @@ struct CycleArgs {
   double2* X;
   int64_t E, vstride;
   size_t es;
+  Tuned t;
   void* Vp(const Work& w, int i) const { return (unsigned char*)w.V + es * vstride * i; }
   void* Zp(const Work& w, int i) const { return use_p ? (unsigned char*)w.Z + es * vstride * i : Vp(w, i); }
 };
@@ -436,20 +451,23 @@ void arnoldi_step(Ctx* c, const CycleArgs& a, int j, Seg&& seg) {
   Work& w = c->work;
   const int64_t E = a.E;
   const int R = a.R;
-  if (a.use_p) seg(MW_K_ORAS, oras_bytes(c, R), [&] { apply_prec(c, a.f, a.wp, a.Vp(w, j), a.Zp(w, j), R); });
+  if (a.use_p)
+    seg(MW_K_ORAS, oras_bytes(c, R), [&] { apply_prec(c, a.f, a.wp, a.Vp(w, j), a.Zp(w, j), R, a.t.tc_stages); });
   seg(MW_K_SPMM, (double)c->topo.nnz * (a.es + 4) + 8.0 * (E + 1) + 2.0 * a.es * E * R, [&] {
     if (a.wp == 0)
       mwk::spmm_f64(c->d_row, c->d_col, c->A64[a.f], (const double2*)a.Zp(w, j), (double2*)a.Vp(w, j + 1), E, R,
-                    c->stream);
+                    c->stream, a.t.spmm_threads);
     else
       mwk::spmm_f32(c->d_row, c->d_col, c->A32[a.f], (const float2*)a.Zp(w, j), (float2*)a.Vp(w, j + 1), E, R,
-                    c->stream);
+                    c->stream, a.t.spmm_threads);
   });
   seg(MW_K_CGS_DOTS, (double)a.es * E * R * (j + 2), [&] {
     const int np = a.wp == 0 ? mwk::cgs_dots_f64((const double2*)w.V, a.vstride, j + 1,
-                                                 (const double2*)a.Vp(w, j + 1), E, R, w.part, w.kerr, c->stream)
+                                                 (const double2*)a.Vp(w, j + 1), E, R, w.part, w.kerr, c->stream,
+                                                 a.t.dots_stages)
                              : mwk::cgs_dots_f32((const float2*)w.V, a.vstride, j + 1,
-                                                 (const float2*)a.Vp(w, j + 1), E, R, w.part, w.kerr, c->stream);
+                                                 (const float2*)a.Vp(w, j + 1), E, R, w.part, w.kerr, c->stream,
+                                                 a.t.dots_stages);
     mwk::reduce_h(w.part, np, j + 1, R, w.h, c->stream);
   });
   int nu = 0;
@@ -664,6 +682,110 @@ int cycle_graph(Ctx* c, const CycleArgs& a) {
   return steps;
 }
 
+// Mean device time per launch of fn (one untimed warm-up launch, then `reps` timed launches).
+double time_launch(Ctx* c, const std::function<void()>& fn, int reps = 3) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  fn();
+  CK(cudaEventRecord(a, c->stream));
+  for (int i = 0; i < reps; ++i) fn();
+  CK(cudaEventRecord(b, c->stream));
+  CK(cudaEventSynchronize(b));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  check_launch("launch-shape tuning");
+  return ms / reps;
+}
+
+// Times every accepted launch shape of the preconditioner apply, the Gram-Schmidt dots and the
+// SpMM for one block shape on pseudo-random inputs (frequency 0's operator and inverses) and
+// keeps the fastest of each.  Uses the Krylov workspace as scratch.
+Tuned autotune(Ctx* c, int R, int wp, int m, bool use_p) {
+  const int64_t E = c->topo.n_edge;
+  ensure_work(c, R, m, wp);
+  Work& w = c->work;
+  Tuned t;
+  t.R = R;
+  t.wp = wp;
+  t.m = m;
+  t.tc = use_p && c->prec.ready && c->prec.apply_prec == 2 && wp == 1;
+  const int64_t vstride = krylov_stride(E, R);
+  const size_t es = wp == 0 ? sizeof(double2) : sizeof(float2);
+  auto Vp = [&](int i) { return (void*)((unsigned char*)w.V + es * vstride * i); };
+  const int nvec = (m + 1) / 2;             // mid-cycle depth of the Gram-Schmidt pass
+  const int out = std::min(nvec + 1, m);    // SpMM output vector (inside the m + 1 of the basis)
+  for (int i = 0; i <= nvec; ++i) {
+    if (wp == 0)
+      mwk::fill_pattern_f64((double*)Vp(i), 2 * E * R, 977u * (i + 1), c->stream);
+    else
+      mwk::fill_pattern_f32((float*)Vp(i), 2 * E * R, 977u * (i + 1), c->stream);
+  }
+  auto pick = [](const std::vector<std::pair<int, double>>& v) {
+    int best = v.front().first;
+    double bt = v.front().second;
+    for (auto& p : v)
+      if (p.second < bt) {
+        bt = p.second;
+        best = p.first;
+      }
+    return best;
+  };
+  for (int th : {128, 256, 512}) {
+    const double ms = time_launch(c, [&] {
+      if (wp == 0)
+        mwk::spmm_f64(c->d_row, c->d_col, c->A64[0], (const double2*)Vp(0), (double2*)Vp(out), E, R, c->stream,
+                      th);
+      else
+        mwk::spmm_f32(c->d_row, c->d_col, c->A32[0], (const float2*)Vp(0), (float2*)Vp(out), E, R, c->stream,
+                      th);
+    });
+    t.spmm_t.push_back({th, ms});
+  }
+  t.spmm_threads = pick(t.spmm_t);
+  if (R >= 16 && R <= 128) {
+    for (int st = mwk::kCgsDotsMinStages; st <= mwk::kCgsDotsMaxStages; ++st) {
+      const double ms = time_launch(c, [&] {
+        if (wp == 0)
+          mwk::cgs_dots_f64((const double2*)w.V, vstride, nvec, (const double2*)Vp(nvec), E, R, w.part, w.kerr,
+                            c->stream, st);
+        else
+          mwk::cgs_dots_f32((const float2*)w.V, vstride, nvec, (const float2*)Vp(nvec), E, R, w.part, w.kerr,
+                            c->stream, st);
+      });
+      t.dots_t.push_back({st, ms});
+    }
+    t.dots_stages = pick(t.dots_t);
+  }
+  if (t.tc) {
+    ensure_prec_scratch(c, R);
+    for (int st = mwk::tc_min_stages; st <= mwk::tc_max_stages(R); ++st) {
+      const double ms = time_launch(c, [&] { apply_prec(c, 0, wp, Vp(0), (unsigned char*)w.Z, R, st); });
+      t.tc_t.push_back({st, ms});
+    }
+    t.tc_stages = pick(t.tc_t);
+  }
+  return t;
+}
+
+// Tuned launch shapes for a block shape (default shapes while automatic tuning is off).
+Tuned tuned_for(Ctx* c, int R, int wp, int m, bool use_p) {
+  if (!c->autotune_on) {
+    Tuned d;
+    d.R = R;
+    d.wp = wp;
+    d.m = m;
+    return d;
+  }
+  const bool tc = use_p && c->prec.ready && c->prec.apply_prec == 2 && wp == 1;
+  for (auto& t : c->tuned)
+    if (t.R == R && t.wp == wp && t.m == m && t.tc == tc) return t;
+  c->tuned.push_back(autotune(c, R, wp, m, use_p));
+  return c->tuned.back();
+}
+
 // Solve A_f X = B for a block of R columns ([E][R] layout, FP64 in and out).
 BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const mw_solve_opts& o,
                        std::vector<int32_t>& its_out) {
@@ -675,7 +797,8 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
   ensure_work(c, R, m, wp);
   Work& w = c->work;
   cudaStream_t s = c->stream;
-  CycleArgs a{f, R, m, wp, use_p, X, E, krylov_stride(E, R), wp == 0 ? sizeof(double2) : sizeof(float2)};
+  CycleArgs a{f, R, m, wp, use_p, X, E, krylov_stride(E, R), wp == 0 ? sizeof(double2) : sizeof(float2),
+              tuned_for(c, R, wp, m, use_p)};
 
   CK(cudaMemsetAsync(X, 0, sizeof(double2) * E * R, s));
   int nb = mwk::colnorm2_f64(B, E, R, w.npart, s);
@@ -767,6 +890,13 @@ void solve_all(Ctx* c, const mw_solve_opts& o, int ncols, const std::vector<cons
   cudaStream_t s = c->stream;
   const int bsz = (o.batch <= 0 || o.batch > ncols) ? ncols : o.batch;
   require(bsz <= 128, MW_EINVAL, "at most 128 columns per Krylov launch (set batch)");
+  {
+    // launch shapes are tuned (once per shape) before the solve phase is timed
+    const int wp = o.mode == MW_MODE_FP64 ? 0 : 1;
+    require(o.use_precond == 0 || c->prec.ready, MW_ESTATE, "preconditioner requested but not set up");
+    tuned_for(c, bsz, wp, o.restart, o.use_precond != 0);
+    if (ncols % bsz) tuned_for(c, ncols % bsz, wp, o.restart, o.use_precond != 0);
+  }
   std::vector<int32_t> its_all(c->n_freq * ncols, 0);
   std::vector<double> rel_all(c->n_freq * ncols, 0.0);
   int outer = 0, steps = 0;
@@ -876,6 +1006,7 @@ void release_prec(Ctx* c) {
   for (void* q : p.W) dfree(c, q);
   mwk::tc_plan_free(p.tc, [&](void* q) { dfree(c, q); });
   p = Prec();
+  c->tuned.clear();
 }
 
 void release_mesh(Ctx* c) {
@@ -972,6 +1103,83 @@ mw_status mw_set_graphs(mw_ctx* c, int32_t enable) {
   return guard(c, [&] {
     c->graphs_on = enable != 0;
     if (!c->graphs_on) drop_graphs(c);
+  });
+}
+
+mw_status mw_set_autotune(mw_ctx* c, int32_t enable) {
+  return guard(c, [&] {
+    c->autotune_on = enable != 0;
+    if (!c->autotune_on) c->tuned.clear();
+  });
+}
+
+mw_status mw_set_launch_shapes(mw_ctx* c, int32_t n_cols, int32_t mode, int32_t restart, int32_t tc_stages,
+                               int32_t dots_stages, int32_t spmm_threads) {
+  return guard(c, [&] {
+    require(n_cols >= 1 && n_cols <= 128, MW_EINVAL, "n_cols must be in 1..128");
+    require(mode == MW_MODE_FP64 || mode == MW_MODE_MIXED, MW_EINVAL, "bad mode");
+    require(restart >= 1 && restart <= kMaxRestart, MW_EINVAL, "restart must be in 1..63");
+    require(tc_stages == 0 || (tc_stages >= mwk::tc_min_stages && tc_stages <= mwk::tc_max_stages(n_cols)),
+            MW_EINVAL, "tc_stages outside the accepted range for this block width");
+    require(dots_stages == 0 || (dots_stages >= mwk::kCgsDotsMinStages && dots_stages <= mwk::kCgsDotsMaxStages),
+            MW_EINVAL, "dots_stages must be 0 or 2..6");
+    require(spmm_threads == 0 || spmm_threads == 128 || spmm_threads == 256 || spmm_threads == 512, MW_EINVAL,
+            "spmm_threads must be 0, 128, 256 or 512");
+    const int wp = mode == MW_MODE_FP64 ? 0 : 1;
+    Tuned t;
+    t.R = n_cols;
+    t.wp = wp;
+    t.m = restart;
+    t.tc = c->prec.ready && c->prec.apply_prec == 2 && wp == 1;
+    t.tc_stages = tc_stages;
+    t.dots_stages = dots_stages;
+    t.spmm_threads = spmm_threads == 0 ? 256 : spmm_threads;
+    for (auto& u : c->tuned)
+      if (u.R == t.R && u.wp == t.wp && u.m == t.m && u.tc == t.tc) {
+        u = t;
+        return;
+      }
+    c->tuned.push_back(t);
+  });
+}
+
+mw_status mw_autotune(mw_ctx* c, int32_t n_cols, int32_t mode, int32_t restart, mw_tune_report* out) {
+  return guard(c, [&] {
+    require(c->has_mesh && c->n_freq > 0, MW_ESTATE, "assemble before tuning");
+    require(n_cols >= 1 && n_cols <= 128, MW_EINVAL, "n_cols must be in 1..128");
+    require(mode == MW_MODE_FP64 || mode == MW_MODE_MIXED, MW_EINVAL, "bad mode");
+    require(restart >= 1 && restart <= kMaxRestart, MW_EINVAL, "restart must be in 1..63");
+    const int wp = mode == MW_MODE_FP64 ? 0 : 1;
+    const bool use_p = c->prec.ready;
+    Tuned t = autotune(c, n_cols, wp, restart, use_p);
+    if (c->autotune_on) {
+      bool put = false;
+      for (auto& u : c->tuned)
+        if (u.R == t.R && u.wp == t.wp && u.m == t.m && u.tc == t.tc) {
+          u = t;
+          put = true;
+        }
+      if (!put) c->tuned.push_back(t);
+    }
+    if (out) {
+      *out = mw_tune_report{};
+      out->n_cols = n_cols;
+      out->mode = mode;
+      out->restart = restart;
+      out->tc_stages = t.tc ? t.tc_stages : 0;
+      out->dots_stages = t.dots_t.empty() ? 0 : t.dots_stages;
+      out->spmm_threads = t.spmm_threads;
+      auto put = [](const std::vector<std::pair<int, double>>& v, int32_t* n, int32_t* cand, double* ms) {
+        *n = (int32_t)std::min<size_t>(v.size(), 8);
+        for (int i = 0; i < *n; ++i) {
+          cand[i] = v[i].first;
+          ms[i] = v[i].second;
+        }
+      };
+      put(t.tc_t, &out->n_tc, out->tc_cand, out->tc_ms);
+      put(t.dots_t, &out->n_dots, out->dots_cand, out->dots_ms);
+      put(t.spmm_t, &out->n_spmm, out->spmm_cand, out->spmm_ms);
+    }
   });
 }
 

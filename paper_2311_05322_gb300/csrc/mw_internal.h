@@ -101,10 +101,11 @@ void reassemble(const int64_t* cptr, const int32_t* contrib, int64_t nnz, const 
                 const double* eps, double k0sq, double zb_re, double zb_im, double2* A64, float2* A32,
                 cudaStream_t s);
 // K3 SpMM: Y = A X, [E][R] layout with leading dimension ld (>= R).
+// threads: block size, 128, 256 (default) or 512 (the result does not depend on it).
 void spmm_f64(const int64_t* rp, const int32_t* ci, const double2* A, const double2* X, double2* Y, int64_t E,
-              int R, cudaStream_t s);
+              int R, cudaStream_t s, int threads = 256);
 void spmm_f32(const int64_t* rp, const int32_t* ci, const float2* A, const float2* X, float2* Y, int64_t E, int R,
-              cudaStream_t s);
+              cudaStream_t s, int threads = 256);
 // Split complex FP64 values into double-float (re_hi, re_lo, im_hi, im_lo).
 void split_df(const double2* a, float4* o, int64_t n, cudaStream_t s);
 // r = b - A x (y = A x when B is null) in double-float arithmetic on the FP32 pipes, with
@@ -117,16 +118,21 @@ int residual_f64(const int64_t* rp, const int32_t* ci, const double2* A, const d
 
 // Krylov (K6-K8, K15)
 // h_part = V^H w per part; returns the number of parts written.  `err` (device int, may be null)
-// receives a nonzero code if a bounded wait of the streaming kernel gave up.
+// receives a nonzero code if a bounded wait of the streaming kernel gave up.  stages: ring depth
+// of the streaming kernel, 2..6 (0 = default; the result does not depend on it).
 int cgs_dots_f64(const double2* V, int64_t vstride, int nvec, const double2* w, int64_t E, int R,
-                 double2* part, int32_t* err, cudaStream_t s);
+                 double2* part, int32_t* err, cudaStream_t s, int stages = 0);
 int cgs_dots_f32(const float2* V, int64_t vstride, int nvec, const float2* w, int64_t E, int R,
-                 double2* part, int32_t* err, cudaStream_t s);
+                 double2* part, int32_t* err, cudaStream_t s, int stages = 0);
+constexpr int kCgsDotsMinStages = 2, kCgsDotsMaxStages = 6;
 // Largest part count cgs_dots can return.
 constexpr int kCgsDotsMaxParts = 152 * 4 * 8;
 // Sets conditional-node handles (cudaGraphConditionalHandle values) of one captured Arnoldi
 // step to (*active != 0); at most kMaxStepHandles handles.
 constexpr int kMaxStepHandles = 8;
+// Deterministic pseudo-random values in [-1, 1) (timing inputs of the launch-shape tuner).
+void fill_pattern_f32(float* x, int64_t n, uint32_t seed, cudaStream_t s);
+void fill_pattern_f64(double* x, int64_t n, uint32_t seed, cudaStream_t s);
 void set_step_conditions(const unsigned long long* handles, int n, const int32_t* active, cudaStream_t s);
 void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s);
 int cgs_update_f64(const double2* V, int64_t vstride, int nvec, const double2* h, double2* w, int64_t E, int R,
