@@ -391,7 +391,8 @@ def run_mine(a):
                        "n_s_mean": float(sizes.mean()), "n_s_max": int(sizes.max()),
                        "solver": "GMRES-IR: FP64 outer residual, FGMRES(50) inner FP32 + ORAS",
                        "cycles": "CUDA graph per restart cycle (conditional nodes)" if a.graphs else "eager",
-                       "launch_shapes": {k: tune[k] for k in ("tc_stages", "dots_stages", "spmm_threads")},
+                       "launch_shapes": {k: tune[k] for k in ("tc_stages", "dots_stages", "update_stages",
+                                                              "spmm_threads")},
                        "preconditioner_apply": {2: "bf16 tcgen05", 1: "fp32 cuda-core"}.get(prec, str(prec)),
                        "tol": 1e-8, "inner_tol": a.inner_tol, "alpha": a.alpha,
                        "l2": "inputs larger than L2 (subdomain inverses and Krylov basis are GBs)"},

@@ -115,32 +115,37 @@ mw_status mw_set_graphs(mw_ctx* ctx, int32_t enable);
 /* Launch-shape autotuner for the solve kernels (Sec. IV-C's GMRES + ORAS, arithmetic unchanged).
  * For one block shape (n_cols columns, solve mode, restart length) it times, with CUDA events on
  * the context stream and on pseudo-random inputs of the real operator and inverses, each accepted
- * launch shape of three kernels and keeps the fastest:
- *   tc    pipeline depth (stages) of the BF16 tensor-core ORAS apply, 2..8 by shared memory
- *         (only with a BF16 preconditioner);
- *   dots  ring depth of the streaming Gram-Schmidt dots, 2..6 (blocks of 16..128 columns);
- *   spmm  threads per block of the SpMM, 128 / 256 / 512.
+ * launch shape of four kernels and keeps the fastest:
+ *   tc_stages      pipeline depth of the BF16 tensor-core ORAS apply, 2..8 by shared memory
+ *                  (only with a BF16 preconditioner in mixed mode);
+ *   dots_stages    ring depth of the streaming Gram-Schmidt dots, 2..6 (16..128 columns);
+ *   update_stages  ring depth of the streaming Gram-Schmidt update, 2..6 (16..128 columns);
+ *   spmm_threads   threads per block of the SpMM, 128 / 256 / 512.
  * None of these changes a result bit: the same arithmetic runs in the same order.  The choice is
- * kept per shape until the mesh or preconditioner changes.  Solves tune each new shape on first
- * use while automatic tuning is on (mw_set_autotune, default on); mw_autotune (re)tunes a shape
- * now and reports it.  Needs a mesh, an assembled matrix and, for the tc row, a BF16
- * preconditioner.  Chosen values are 0 for a kernel the shape does not use. */
+ * kept per shape until the mesh or preconditioner changes.  Solves tune each new shape before
+ * their timed phase while automatic tuning is on (mw_set_autotune, default on); mw_autotune
+ * (re)tunes a shape now and reports it.  A value 0 means the kernel's default shape (and, in a
+ * report, that the shape does not use the kernel). */
+typedef struct {
+  int32_t tc_stages, dots_stages, update_stages, spmm_threads;
+} mw_launch_shapes;
+enum { MW_TUNE_TC = 0, MW_TUNE_DOTS = 1, MW_TUNE_UPDATE = 2, MW_TUNE_SPMM = 3, MW_TUNE_NKERNEL = 4 };
 typedef struct {
   int32_t n_cols, mode, restart;
-  int32_t tc_stages, dots_stages, spmm_threads; /* chosen */
-  int32_t n_tc, n_dots, n_spmm;                 /* candidates timed */
-  int32_t tc_cand[8], dots_cand[8], spmm_cand[8];
-  double tc_ms[8], dots_ms[8], spmm_ms[8];      /* mean device time per launch, ms */
+  mw_launch_shapes chosen;
+  int32_t n_cand[MW_TUNE_NKERNEL];   /* candidates timed per kernel (MW_TUNE_*) */
+  int32_t cand[MW_TUNE_NKERNEL][8];  /* candidate values */
+  double ms[MW_TUNE_NKERNEL][8];     /* mean device time per launch, ms */
 } mw_tune_report;
 mw_status mw_autotune(mw_ctx* ctx, int32_t n_cols, int32_t mode, int32_t restart, mw_tune_report* out);
-/* Automatic tuning at the first solve of each block shape: enable != 0 (default) or 0 (default
- * launch shapes; forgets tuned shapes). */
+/* Automatic tuning before the solve phase of each new block shape: enable != 0 (default) or 0
+ * (default launch shapes; forgets tuned shapes). */
 mw_status mw_set_autotune(mw_ctx* ctx, int32_t enable);
-/* Pins the launch shapes of one block shape (same meaning and ranges as mw_tune_report's chosen
- * values; 0 = the kernel's default), replacing any tuned choice until the mesh or preconditioner
- * changes.  Takes effect while automatic tuning is on.  MW_EINVAL for a value outside its range. */
-mw_status mw_set_launch_shapes(mw_ctx* ctx, int32_t n_cols, int32_t mode, int32_t restart, int32_t tc_stages,
-                               int32_t dots_stages, int32_t spmm_threads);
+/* Pins the launch shapes of one block shape (ranges as above, 0 = the kernel's default), replacing
+ * any tuned choice until the mesh or preconditioner changes.  Takes effect while automatic tuning
+ * is on.  MW_EINVAL for a value outside its range. */
+mw_status mw_set_launch_shapes(mw_ctx* ctx, int32_t n_cols, int32_t mode, int32_t restart,
+                               const mw_launch_shapes* shapes);
 
 /* ---- mesh (Sec. IV-A; Nedelec r = 1, Sec. IV-D) ------------------------------------- */
 /* xyz [n_vert][3] metres; tet_vert [n_tet][4] vertex ids (any orientation, non-degenerate).

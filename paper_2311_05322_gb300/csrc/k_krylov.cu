@@ -442,6 +442,175 @@ __global__ void __launch_bounds__(kThreads) cgs_update_kernel(const T* __restric
   }
 }
 
+// Streaming form of the update for 16 <= R <= 128 with 16-byte aligned vectors, on the tiles,
+// ring and thread map of cgs_dots_bulk_kernel: per tile the producer streams w and then V_0 ..
+// V_nvec-1; consumer (c, g) holds its kBdRows w rows of column c in registers, applies
+// w -= h_i V_i for each arriving tile in the order of cgs_update_kernel (the same operations per
+// element, so w is bit-identical), and stores its rows back.  |w|^2 is promoted to FP64 per row
+// and summed per thread; the G row groups of a column are summed in a fixed order at the end
+// (one partial per block and column).  h is staged in shared memory as T.  Bounded waits as in
+// the dots kernel.
+template <typename T>
+__global__ void __launch_bounds__(kBdThreads, 2)
+    cgs_update_bulk_kernel(const T* __restrict__ V, int64_t vstride, int nvec, const double2* __restrict__ h,
+                           T* __restrict__ w, int64_t E, int R, int G, int NS, double* __restrict__ npart,
+                           int32_t* __restrict__ err) {
+  using Sc = typename Traits<T>::S;
+  constexpr int RPT = bd_rows<T>();
+  constexpr int kStageElems = kBdStageBytes / (int)sizeof(T);
+  extern __shared__ __align__(128) uint8_t bu_smem[];
+  T* stage = reinterpret_cast<T*>(bu_smem);
+  T* hs = reinterpret_cast<T*>(bu_smem + (size_t)NS * kBdStageBytes);                 // [nvec][R]
+  double* red = reinterpret_cast<double*>(hs + (size_t)nvec * R + 2);                 // [G][R]
+  uint64_t* full = reinterpret_cast<uint64_t*>(red + (size_t)kBdConsumers);
+  uint64_t* empty = full + NS;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NS);
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kBdConsumers);
+    }
+    *abort_flag = 0;
+    mbar_init_fence();
+  }
+  for (int t = tid; t < nvec * R; t += kBdThreads) {
+    const double2 v = h[t];
+    hs[t] = T{(Sc)v.x, (Sc)v.y};
+  }
+  __syncthreads();
+
+  const int TR = G * RPT;
+  const int64_t nt = (E + TR - 1) / TR;
+  const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
+
+  if (tid < 32) {
+    if (tid != 0) return;
+    // producer: ring position st with phase bit ph
+    int64_t it = 0;
+    int st = 0;
+    uint32_t ph = 0;
+    bool stop = false;
+    for (int64_t t = t0; t < t1 && !stop; ++t) {
+      const int64_t r0 = t * TR;
+      const int64_t rows = E - r0 < TR ? E - r0 : (int64_t)TR;
+      const uint32_t bytes = (uint32_t)((rows * R * (int64_t)sizeof(T)) & ~(int64_t)15);
+      for (int q = -1; q < nvec; ++q) {
+        if (it >= NS && !mbar_wait(&empty[st], ph ^ 1u)) {
+          atomicCAS(err, 0, 21);
+          *abort_flag = 1;
+        }
+        if (*abort_flag) {
+          stop = true;
+          break;
+        }
+        const T* src = (q < 0 ? w : V + (int64_t)q * vstride) + r0 * R;
+        if (bytes > 0) {
+          mbar_expect_tx(&full[st], bytes);
+          bulk_g2s(stage + (size_t)st * kStageElems, src, bytes, &full[st]);
+        } else {
+          mbar_arrive(&full[st]);
+        }
+        ++it;
+        if (++st == NS) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    for (int k = 0; k < NS; ++k) {
+      if (k >= st && it < NS) continue;
+      if (!mbar_wait(&full[k], k < st ? ph : ph ^ 1u)) atomicCAS(err, 0, 22);
+    }
+    return;
+  }
+
+  // consumers
+  const int ct = tid - 32;
+  const int c = ct % R, g = ct / R;
+  const bool act = g < G;
+  int st = 0;
+  uint32_t ph = 0;
+  auto wait_full = [&]() {
+    if (*abort_flag) return;
+    if (!mbar_wait(&full[st], ph)) {
+      atomicCAS(err, 0, 23);
+      *abort_flag = 1;
+    }
+  };
+  auto advance = [&]() {
+    if (++st == NS) {
+      st = 0;
+      ph ^= 1u;
+    }
+  };
+  double nrm = 0.0;
+  for (int64_t t = t0; t < t1; ++t) {
+    const int64_t r0 = t * TR;
+    const int64_t rows = E - r0 < TR ? E - r0 : (int64_t)TR;
+    const int64_t ncop = ((rows * R * (int64_t)sizeof(T)) & ~(int64_t)15) / (int64_t)sizeof(T);
+    T acc[RPT];
+    {
+      wait_full();
+      const T* sm = stage + (size_t)st * kStageElems;
+      const T* gl = w + r0 * R;
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int row = k * G + g;
+        const int f = row * R + c;
+        acc[k] = T{0, 0};
+        if (act && row < rows) acc[k] = f < ncop ? sm[f] : gl[f];
+      }
+      mbar_arrive(&empty[st]);
+      advance();
+    }
+    for (int i = 0; i < nvec; ++i) {
+      wait_full();
+      const T* sm = stage + (size_t)st * kStageElems;
+      const T* gl = V + (int64_t)i * vstride + r0 * R;
+      const T hh = act ? hs[i * R + c] : T{0, 0};
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int row = k * G + g;
+        const int f = row * R + c;
+        if (act && row < rows) {
+          const T v = f < ncop ? sm[f] : gl[f];
+          acc[k].x = fma(-hh.x, v.x, acc[k].x);
+          acc[k].x = fma(hh.y, v.y, acc[k].x);
+          acc[k].y = fma(-hh.x, v.y, acc[k].y);
+          acc[k].y = fma(-hh.y, v.x, acc[k].y);
+        }
+      }
+      mbar_arrive(&empty[st]);
+      advance();
+    }
+    if (act && !*abort_flag) {
+      T* wr = w + r0 * R;
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int row = k * G + g;
+        if (row < rows) {
+          wr[row * R + c] = acc[k];
+          nrm += (double)(acc[k].x * acc[k].x + acc[k].y * acc[k].y);
+        }
+      }
+    }
+  }
+  red[ct] = nrm;
+  asm volatile("bar.sync 1, %0;" ::"n"(kBdConsumers) : "memory");
+  if (act && g == 0) {
+    double sum = 0.0;
+    for (int g2 = 0; g2 < G; ++g2) sum += red[g2 * R + c];
+    npart[(int64_t)blockIdx.x * R + c] = sum;
+  }
+}
+
+inline size_t bu_smem_bytes(int R, int nvec, int NS) {
+  return (size_t)NS * kBdStageBytes + ((size_t)nvec * R + 2) * 16 + kBdConsumers * sizeof(double) +
+         2 * NS * sizeof(uint64_t) + 16;
+}
+
 template <typename T, int CPL>
 __global__ void __launch_bounds__(kThreads) colnorm2_kernel(const T* __restrict__ x, int64_t E, int R, int tpr_log2,
                                                             double* __restrict__ npart) {
@@ -692,8 +861,24 @@ int dots_launch(const T* V, int64_t vstride, int nvec, const T* w, int64_t E, in
 
 template <typename T>
 int update_launch(const T* V, int64_t vstride, int nvec, const double2* h, T* w, int64_t E, int R, double* npart,
-                  cudaStream_t s) {
+                  cudaStream_t s, int32_t* err, int stages) {
   note_launch(1);
+  const bool aligned = ((uintptr_t)V % 16 == 0) && ((uintptr_t)w % 16 == 0) && ((vstride * sizeof(T)) % 16 == 0);
+  if (err && aligned && R >= 16 && R <= 128 && nvec >= 1) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(cgs_update_bulk_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(cgs_update_bulk_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      attr = true;
+    }
+    int NS = stages >= 2 && stages <= kBdMaxStages ? stages : kBdStages;
+    while (NS > 2 && bu_smem_bytes(R, nvec, NS) > (size_t)226 * 1024) --NS;
+    const int G = kBdConsumers / R;
+    const int nb = 152 * 2;
+    cgs_update_bulk_kernel<T>
+        <<<nb, kBdThreads, bu_smem_bytes(R, nvec, NS), s>>>(V, vstride, nvec, h, w, E, R, G, NS, npart, err);
+    return nb;
+  }
   Shape sh = shape_for(R);
   const size_t smem = sizeof(T) * nvec * R + 16 + sizeof(double) * kThreads * sh.cpl;
   static bool attr = false;
@@ -720,13 +905,13 @@ int update_launch(const T* V, int64_t vstride, int nvec, const double2* h, T* w,
 
 // Deterministic pseudo-random fill in [-1, 1) (timing inputs of the launch-shape tuner).
 template <typename F>
-__global__ void fill_pattern_kernel(F* __restrict__ x, int64_t n, uint32_t seed) {
+__global__ void fill_pattern_kernel(F* __restrict__ x, int64_t n, uint32_t seed, double scale) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     uint32_t h = (uint32_t)i * 2654435761u ^ seed;
     h ^= h >> 15;
     h *= 2246822519u;
     h ^= h >> 13;
-    x[i] = (F)((double)(h >> 8) * (1.0 / 8388608.0) - 1.0);
+    x[i] = (F)(scale * ((double)(h >> 8) * (1.0 / 8388608.0) - 1.0));
   }
 }
 
@@ -743,13 +928,13 @@ __global__ void set_step_conditions_kernel(StepHandles sh, const int32_t* __rest
 
 }  // namespace
 
-void fill_pattern_f32(float* x, int64_t n, uint32_t seed, cudaStream_t s) {
+void fill_pattern_f32(float* x, int64_t n, uint32_t seed, cudaStream_t s, double scale) {
   note_launch(1);
-  fill_pattern_kernel<float><<<gs_blocks(n), 256, 0, s>>>(x, n, seed);
+  fill_pattern_kernel<float><<<gs_blocks(n), 256, 0, s>>>(x, n, seed, scale);
 }
-void fill_pattern_f64(double* x, int64_t n, uint32_t seed, cudaStream_t s) {
+void fill_pattern_f64(double* x, int64_t n, uint32_t seed, cudaStream_t s, double scale) {
   note_launch(1);
-  fill_pattern_kernel<double><<<gs_blocks(n), 256, 0, s>>>(x, n, seed);
+  fill_pattern_kernel<double><<<gs_blocks(n), 256, 0, s>>>(x, n, seed, scale);
 }
 
 void set_step_conditions(const unsigned long long* handles, int n, const int32_t* active, cudaStream_t s) {
@@ -774,12 +959,12 @@ void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cuda
   reduce_h_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(part, nparts, nvec, R, h);
 }
 int cgs_update_f64(const double2* V, int64_t vstride, int nvec, const double2* h, double2* w, int64_t E, int R,
-                   double* npart, cudaStream_t s) {
-  return update_launch<double2>(V, vstride, nvec, h, w, E, R, npart, s);
+                   double* npart, cudaStream_t s, int32_t* err, int stages) {
+  return update_launch<double2>(V, vstride, nvec, h, w, E, R, npart, s, err, stages);
 }
 int cgs_update_f32(const float2* V, int64_t vstride, int nvec, const double2* h, float2* w, int64_t E, int R,
-                   double* npart, cudaStream_t s) {
-  return update_launch<float2>(V, vstride, nvec, h, w, E, R, npart, s);
+                   double* npart, cudaStream_t s, int32_t* err, int stages) {
+  return update_launch<float2>(V, vstride, nvec, h, w, E, R, npart, s, err, stages);
 }
 int colnorm2_f64(const double2* x, int64_t E, int R, double* npart, cudaStream_t s) {
   note_launch(1);

@@ -132,8 +132,8 @@ struct NnState {
 struct Tuned {
   int R = 0, wp = -1, m = 0;
   bool tc = false;                 // BF16 tensor-core preconditioner in use
-  int tc_stages = 0, dots_stages = 0, spmm_threads = 256;
-  std::vector<std::pair<int, double>> tc_t, dots_t, spmm_t;  // (candidate, ms per launch)
+  mw_launch_shapes sh{0, 0, 0, 256};
+  std::vector<std::pair<int, double>> t[MW_TUNE_NKERNEL];  // (candidate, ms per launch) per kernel
 };
 
 // One restart cycle of the batched FGMRES captured as a CUDA graph: the start vector, m
@@ -452,30 +452,31 @@ void arnoldi_step(Ctx* c, const CycleArgs& a, int j, Seg&& seg) {
   const int64_t E = a.E;
   const int R = a.R;
   if (a.use_p)
-    seg(MW_K_ORAS, oras_bytes(c, R), [&] { apply_prec(c, a.f, a.wp, a.Vp(w, j), a.Zp(w, j), R, a.t.tc_stages); });
+    seg(MW_K_ORAS, oras_bytes(c, R),
+        [&] { apply_prec(c, a.f, a.wp, a.Vp(w, j), a.Zp(w, j), R, a.t.sh.tc_stages); });
   seg(MW_K_SPMM, (double)c->topo.nnz * (a.es + 4) + 8.0 * (E + 1) + 2.0 * a.es * E * R, [&] {
     if (a.wp == 0)
       mwk::spmm_f64(c->d_row, c->d_col, c->A64[a.f], (const double2*)a.Zp(w, j), (double2*)a.Vp(w, j + 1), E, R,
-                    c->stream, a.t.spmm_threads);
+                    c->stream, a.t.sh.spmm_threads);
     else
       mwk::spmm_f32(c->d_row, c->d_col, c->A32[a.f], (const float2*)a.Zp(w, j), (float2*)a.Vp(w, j + 1), E, R,
-                    c->stream, a.t.spmm_threads);
+                    c->stream, a.t.sh.spmm_threads);
   });
   seg(MW_K_CGS_DOTS, (double)a.es * E * R * (j + 2), [&] {
     const int np = a.wp == 0 ? mwk::cgs_dots_f64((const double2*)w.V, a.vstride, j + 1,
                                                  (const double2*)a.Vp(w, j + 1), E, R, w.part, w.kerr, c->stream,
-                                                 a.t.dots_stages)
+                                                 a.t.sh.dots_stages)
                              : mwk::cgs_dots_f32((const float2*)w.V, a.vstride, j + 1,
                                                  (const float2*)a.Vp(w, j + 1), E, R, w.part, w.kerr, c->stream,
-                                                 a.t.dots_stages);
+                                                 a.t.sh.dots_stages);
     mwk::reduce_h(w.part, np, j + 1, R, w.h, c->stream);
   });
   int nu = 0;
   seg(MW_K_CGS_UPDATE, (double)a.es * E * R * (j + 3), [&] {
     nu = a.wp == 0 ? mwk::cgs_update_f64((const double2*)w.V, a.vstride, j + 1, w.h, (double2*)a.Vp(w, j + 1), E,
-                                         R, w.npart, c->stream)
+                                         R, w.npart, c->stream, w.kerr, a.t.sh.update_stages)
                    : mwk::cgs_update_f32((const float2*)w.V, a.vstride, j + 1, w.h, (float2*)a.Vp(w, j + 1), E,
-                                         R, w.npart, c->stream);
+                                         R, w.npart, c->stream, w.kerr, a.t.sh.update_stages);
   });
   seg(-1, 0.0, [&] {
     CK(cudaMemsetAsync(w.active, 0, sizeof(int32_t), c->stream));
@@ -742,9 +743,9 @@ Tuned autotune(Ctx* c, int R, int wp, int m, bool use_p) {
         mwk::spmm_f32(c->d_row, c->d_col, c->A32[0], (const float2*)Vp(0), (float2*)Vp(out), E, R, c->stream,
                       th);
     });
-    t.spmm_t.push_back({th, ms});
+    t.t[MW_TUNE_SPMM].push_back({th, ms});
   }
-  t.spmm_threads = pick(t.spmm_t);
+  t.sh.spmm_threads = pick(t.t[MW_TUNE_SPMM]);
   if (R >= 16 && R <= 128) {
     for (int st = mwk::kCgsDotsMinStages; st <= mwk::kCgsDotsMaxStages; ++st) {
       const double ms = time_launch(c, [&] {
@@ -755,17 +756,31 @@ Tuned autotune(Ctx* c, int R, int wp, int m, bool use_p) {
           mwk::cgs_dots_f32((const float2*)w.V, vstride, nvec, (const float2*)Vp(nvec), E, R, w.part, w.kerr,
                             c->stream, st);
       });
-      t.dots_t.push_back({st, ms});
+      t.t[MW_TUNE_DOTS].push_back({st, ms});
     }
-    t.dots_stages = pick(t.dots_t);
+    t.sh.dots_stages = pick(t.t[MW_TUNE_DOTS]);
+    // small coefficients keep the repeatedly updated vector bounded
+    mwk::fill_pattern_f64((double*)w.h, 2 * (int64_t)nvec * R, 4099u, c->stream, 1e-3);
+    for (int st = mwk::kCgsDotsMinStages; st <= mwk::kCgsDotsMaxStages; ++st) {
+      const double ms = time_launch(c, [&] {
+        if (wp == 0)
+          mwk::cgs_update_f64((const double2*)w.V, vstride, nvec, w.h, (double2*)Vp(nvec), E, R, w.npart, c->stream,
+                              w.kerr, st);
+        else
+          mwk::cgs_update_f32((const float2*)w.V, vstride, nvec, w.h, (float2*)Vp(nvec), E, R, w.npart, c->stream,
+                              w.kerr, st);
+      });
+      t.t[MW_TUNE_UPDATE].push_back({st, ms});
+    }
+    t.sh.update_stages = pick(t.t[MW_TUNE_UPDATE]);
   }
   if (t.tc) {
     ensure_prec_scratch(c, R);
     for (int st = mwk::tc_min_stages; st <= mwk::tc_max_stages(R); ++st) {
       const double ms = time_launch(c, [&] { apply_prec(c, 0, wp, Vp(0), (unsigned char*)w.Z, R, st); });
-      t.tc_t.push_back({st, ms});
+      t.t[MW_TUNE_TC].push_back({st, ms});
     }
-    t.tc_stages = pick(t.tc_t);
+    t.sh.tc_stages = pick(t.t[MW_TUNE_TC]);
   }
   return t;
 }
@@ -1113,27 +1128,29 @@ mw_status mw_set_autotune(mw_ctx* c, int32_t enable) {
   });
 }
 
-mw_status mw_set_launch_shapes(mw_ctx* c, int32_t n_cols, int32_t mode, int32_t restart, int32_t tc_stages,
-                               int32_t dots_stages, int32_t spmm_threads) {
+mw_status mw_set_launch_shapes(mw_ctx* c, int32_t n_cols, int32_t mode, int32_t restart,
+                               const mw_launch_shapes* shapes) {
   return guard(c, [&] {
+    require(shapes != nullptr, MW_EINVAL, "null shapes");
     require(n_cols >= 1 && n_cols <= 128, MW_EINVAL, "n_cols must be in 1..128");
     require(mode == MW_MODE_FP64 || mode == MW_MODE_MIXED, MW_EINVAL, "bad mode");
     require(restart >= 1 && restart <= kMaxRestart, MW_EINVAL, "restart must be in 1..63");
-    require(tc_stages == 0 || (tc_stages >= mwk::tc_min_stages && tc_stages <= mwk::tc_max_stages(n_cols)),
+    const mw_launch_shapes& q = *shapes;
+    require(q.tc_stages == 0 || (q.tc_stages >= mwk::tc_min_stages && q.tc_stages <= mwk::tc_max_stages(n_cols)),
             MW_EINVAL, "tc_stages outside the accepted range for this block width");
-    require(dots_stages == 0 || (dots_stages >= mwk::kCgsDotsMinStages && dots_stages <= mwk::kCgsDotsMaxStages),
-            MW_EINVAL, "dots_stages must be 0 or 2..6");
-    require(spmm_threads == 0 || spmm_threads == 128 || spmm_threads == 256 || spmm_threads == 512, MW_EINVAL,
-            "spmm_threads must be 0, 128, 256 or 512");
+    for (int v : {q.dots_stages, q.update_stages})
+      require(v == 0 || (v >= mwk::kCgsDotsMinStages && v <= mwk::kCgsDotsMaxStages), MW_EINVAL,
+              "dots_stages and update_stages must be 0 or 2..6");
+    require(q.spmm_threads == 0 || q.spmm_threads == 128 || q.spmm_threads == 256 || q.spmm_threads == 512,
+            MW_EINVAL, "spmm_threads must be 0, 128, 256 or 512");
     const int wp = mode == MW_MODE_FP64 ? 0 : 1;
     Tuned t;
     t.R = n_cols;
     t.wp = wp;
     t.m = restart;
     t.tc = c->prec.ready && c->prec.apply_prec == 2 && wp == 1;
-    t.tc_stages = tc_stages;
-    t.dots_stages = dots_stages;
-    t.spmm_threads = spmm_threads == 0 ? 256 : spmm_threads;
+    t.sh = q;
+    if (t.sh.spmm_threads == 0) t.sh.spmm_threads = 256;
     for (auto& u : c->tuned)
       if (u.R == t.R && u.wp == t.wp && u.m == t.m && u.tc == t.tc) {
         u = t;
@@ -1150,8 +1167,7 @@ mw_status mw_autotune(mw_ctx* c, int32_t n_cols, int32_t mode, int32_t restart, 
     require(mode == MW_MODE_FP64 || mode == MW_MODE_MIXED, MW_EINVAL, "bad mode");
     require(restart >= 1 && restart <= kMaxRestart, MW_EINVAL, "restart must be in 1..63");
     const int wp = mode == MW_MODE_FP64 ? 0 : 1;
-    const bool use_p = c->prec.ready;
-    Tuned t = autotune(c, n_cols, wp, restart, use_p);
+    Tuned t = autotune(c, n_cols, wp, restart, c->prec.ready);
     if (c->autotune_on) {
       bool put = false;
       for (auto& u : c->tuned)
@@ -1166,19 +1182,17 @@ mw_status mw_autotune(mw_ctx* c, int32_t n_cols, int32_t mode, int32_t restart, 
       out->n_cols = n_cols;
       out->mode = mode;
       out->restart = restart;
-      out->tc_stages = t.tc ? t.tc_stages : 0;
-      out->dots_stages = t.dots_t.empty() ? 0 : t.dots_stages;
-      out->spmm_threads = t.spmm_threads;
-      auto put = [](const std::vector<std::pair<int, double>>& v, int32_t* n, int32_t* cand, double* ms) {
-        *n = (int32_t)std::min<size_t>(v.size(), 8);
-        for (int i = 0; i < *n; ++i) {
-          cand[i] = v[i].first;
-          ms[i] = v[i].second;
+      out->chosen = t.sh;
+      if (t.t[MW_TUNE_TC].empty()) out->chosen.tc_stages = 0;
+      if (t.t[MW_TUNE_DOTS].empty()) out->chosen.dots_stages = 0;
+      if (t.t[MW_TUNE_UPDATE].empty()) out->chosen.update_stages = 0;
+      for (int k = 0; k < MW_TUNE_NKERNEL; ++k) {
+        out->n_cand[k] = (int32_t)std::min<size_t>(t.t[k].size(), 8);
+        for (int i = 0; i < out->n_cand[k]; ++i) {
+          out->cand[k][i] = t.t[k][i].first;
+          out->ms[k][i] = t.t[k][i].second;
         }
-      };
-      put(t.tc_t, &out->n_tc, out->tc_cand, out->tc_ms);
-      put(t.dots_t, &out->n_dots, out->dots_cand, out->dots_ms);
-      put(t.spmm_t, &out->n_spmm, out->spmm_cand, out->spmm_ms);
+      }
     }
   });
 }

@@ -130,15 +130,17 @@ constexpr int kCgsDotsMaxParts = 152 * 4 * 8;
 // Sets conditional-node handles (cudaGraphConditionalHandle values) of one captured Arnoldi
 // step to (*active != 0); at most kMaxStepHandles handles.
 constexpr int kMaxStepHandles = 8;
-// Deterministic pseudo-random values in [-1, 1) (timing inputs of the launch-shape tuner).
-void fill_pattern_f32(float* x, int64_t n, uint32_t seed, cudaStream_t s);
-void fill_pattern_f64(double* x, int64_t n, uint32_t seed, cudaStream_t s);
+// Deterministic pseudo-random values in scale * [-1, 1) (timing inputs of the launch-shape tuner).
+void fill_pattern_f32(float* x, int64_t n, uint32_t seed, cudaStream_t s, double scale = 1.0);
+void fill_pattern_f64(double* x, int64_t n, uint32_t seed, cudaStream_t s, double scale = 1.0);
 void set_step_conditions(const unsigned long long* handles, int n, const int32_t* active, cudaStream_t s);
 void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s);
+// w -= sum_i h_i V_i and per-part, per-column |w|^2 into npart[part][R]; returns the part count.
+// err / stages as for cgs_dots (err null: the non-streaming kernel).
 int cgs_update_f64(const double2* V, int64_t vstride, int nvec, const double2* h, double2* w, int64_t E, int R,
-                   double* npart, cudaStream_t s);
+                   double* npart, cudaStream_t s, int32_t* err = nullptr, int stages = 0);
 int cgs_update_f32(const float2* V, int64_t vstride, int nvec, const double2* h, float2* w, int64_t E, int R,
-                   double* npart, cudaStream_t s);
+                   double* npart, cudaStream_t s, int32_t* err = nullptr, int stages = 0);
 int colnorm2_f64(const double2* x, int64_t E, int R, double* npart, cudaStream_t s);
 // Givens step for Arnoldi column j; see k_krylov.cu for the state layout.
 void givens_step(const double2* h, const double* npart, int nparts, int j, int m, int R, double2* H,

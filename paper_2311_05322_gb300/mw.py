@@ -44,12 +44,17 @@ class mw_solve_stats(C.Structure):
                 ("iters", C.POINTER(C.c_int32)), ("relres", C.POINTER(C.c_double))]
 
 
+class mw_launch_shapes(C.Structure):
+    _fields_ = [("tc_stages", C.c_int32), ("dots_stages", C.c_int32), ("update_stages", C.c_int32),
+                ("spmm_threads", C.c_int32)]
+
+
+TUNE_KERNELS = ("tc", "dots", "update", "spmm")   # MW_TUNE_* order
+
+
 class mw_tune_report(C.Structure):
-    _fields_ = [("n_cols", C.c_int32), ("mode", C.c_int32), ("restart", C.c_int32),
-                ("tc_stages", C.c_int32), ("dots_stages", C.c_int32), ("spmm_threads", C.c_int32),
-                ("n_tc", C.c_int32), ("n_dots", C.c_int32), ("n_spmm", C.c_int32),
-                ("tc_cand", C.c_int32 * 8), ("dots_cand", C.c_int32 * 8), ("spmm_cand", C.c_int32 * 8),
-                ("tc_ms", C.c_double * 8), ("dots_ms", C.c_double * 8), ("spmm_ms", C.c_double * 8)]
+    _fields_ = [("n_cols", C.c_int32), ("mode", C.c_int32), ("restart", C.c_int32), ("chosen", mw_launch_shapes),
+                ("n_cand", C.c_int32 * 4), ("cand", (C.c_int32 * 8) * 4), ("ms", (C.c_double * 8) * 4)]
 
 
 class mw_nn_opts(C.Structure):
@@ -79,7 +84,7 @@ _SIGS = {
     "mw_set_memory_cap": (C.c_int32, [_P, C.c_int64]),
     "mw_set_graphs": (C.c_int32, [_P, C.c_int32]),
     "mw_set_autotune": (C.c_int32, [_P, C.c_int32]),
-    "mw_set_launch_shapes": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "mw_set_launch_shapes": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(mw_launch_shapes)]),
     "mw_autotune": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(mw_tune_report)]),
     "mw_set_mesh": (C.c_int32, [_P, C.c_int64, _P, C.c_int64, _P, C.POINTER(mw_mesh_info)]),
     "mw_get_topology": (C.c_int32, [_P, _P, _P, _P, _P, _P]),
@@ -209,21 +214,20 @@ class Context:
         self._check(self.lib.mw_set_autotune(self.h, 1 if enable else 0))
 
     def autotune(self, n_cols: int, mode: int = MW_MODE_MIXED, restart: int = 50) -> dict:
-        """Tune the launch shapes of one block shape now; returns the choices and the timings."""
+        """Tune the launch shapes of one block shape now; returns the choices and, per kernel, the
+        mean device time per launch of every candidate."""
         r = mw_tune_report()
         self._check(self.lib.mw_autotune(self.h, n_cols, mode, restart, C.byref(r)))
-
-        def table(n, cand, ms):
-            return {int(cand[i]): float(ms[i]) for i in range(n)}
-        return {"tc_stages": r.tc_stages, "dots_stages": r.dots_stages, "spmm_threads": r.spmm_threads,
-                "tc_ms": table(r.n_tc, r.tc_cand, r.tc_ms), "dots_ms": table(r.n_dots, r.dots_cand, r.dots_ms),
-                "spmm_ms": table(r.n_spmm, r.spmm_cand, r.spmm_ms)}
+        out = {k: getattr(r.chosen, k) for k, _ in mw_launch_shapes._fields_}
+        for k, name in enumerate(TUNE_KERNELS):
+            out[name + "_ms"] = {int(r.cand[k][i]): float(r.ms[k][i]) for i in range(r.n_cand[k])}
+        return out
 
     def set_launch_shapes(self, n_cols: int, mode: int, restart: int, tc_stages: int = 0, dots_stages: int = 0,
-                          spmm_threads: int = 0):
+                          update_stages: int = 0, spmm_threads: int = 0):
         """Pin the launch shapes of one block shape (0 = the kernel's default)."""
-        self._check(self.lib.mw_set_launch_shapes(self.h, n_cols, mode, restart, tc_stages, dots_stages,
-                                                  spmm_threads))
+        sh = mw_launch_shapes(tc_stages, dots_stages, update_stages, spmm_threads)
+        self._check(self.lib.mw_set_launch_shapes(self.h, n_cols, mode, restart, C.byref(sh)))
 
     def set_graphs(self, enable: bool):
         """Replay restart cycles from captured CUDA graphs, or run them eagerly (the default)."""

@@ -39,15 +39,16 @@ def test_autotune_report(box):
     c = _ctx(m, eps)
     r = c.autotune(32, mw.MW_MODE_MIXED, 50)
     assert set(r["spmm_ms"]) == {128, 256, 512}
-    assert set(r["dots_ms"]) == {2, 3, 4, 5, 6}
+    assert set(r["dots_ms"]) == {2, 3, 4, 5, 6} and set(r["update_ms"]) == {2, 3, 4, 5, 6}
     assert min(r["tc_ms"]) == 2 and max(r["tc_ms"]) >= 4
-    for chosen, table in (("spmm_threads", "spmm_ms"), ("dots_stages", "dots_ms"), ("tc_stages", "tc_ms")):
+    for chosen, table in (("spmm_threads", "spmm_ms"), ("dots_stages", "dots_ms"), ("update_stages", "update_ms"),
+                          ("tc_stages", "tc_ms")):
         t = r[table]
         assert all(v > 0 for v in t.values())
         assert r[chosen] == min(t, key=t.get)
-    # 5 columns: the streaming dots kernel is not used, so it has no candidates
+    # 5 columns: the streaming Gram-Schmidt kernels are not used, so they have no candidates
     r5 = c.autotune(5, mw.MW_MODE_MIXED, 50)
-    assert r5["dots_stages"] == 0 and r5["dots_ms"] == {} and r5["tc_stages"] >= 2
+    assert r5["dots_stages"] == 0 and r5["dots_ms"] == {} and r5["update_ms"] == {} and r5["tc_stages"] >= 2
     # FP64 mode has no tensor-core apply
     r64 = c.autotune(32, mw.MW_MODE_FP64, 50)
     assert r64["tc_stages"] == 0 and r64["tc_ms"] == {}
@@ -72,9 +73,9 @@ def test_launch_shapes_bit_identical(box):
     st_ref = c.solve_rhs(32, bd, x_ref, opts)
     assert st_ref["n_converged"] == 32
     c.set_autotune(True)
-    for tc, dots, spmm in [(2, 2, 128), (tc_max, 6, 512), (3, 5, 256)]:
-        c.set_launch_shapes(32, mw.MW_MODE_MIXED, 50, tc, dots, spmm)
+    for tc, dots, upd, spmm in [(2, 2, 6, 128), (tc_max, 6, 2, 512), (3, 5, 3, 256)]:
+        c.set_launch_shapes(32, mw.MW_MODE_MIXED, 50, tc, dots, upd, spmm)
         x = torch.empty_like(bd)
         st = c.solve_rhs(32, bd, x, opts)
-        assert torch.equal(x, x_ref), (tc, dots, spmm)
+        assert torch.equal(x, x_ref), (tc, dots, upd, spmm)
         assert np.array_equal(st["iters"], st_ref["iters"])
