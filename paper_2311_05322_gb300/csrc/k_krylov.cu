@@ -816,6 +816,174 @@ __global__ void update_x_kernel(const T* __restrict__ Z, int64_t zstride, const 
   }
 }
 
+// Streaming form of the solution update for 16 <= R <= 128 with 16-byte aligned bases, on the tiles,
+// ring and thread map of cgs_dots_bulk_kernel: the producer streams Z_0 .. Z_{kmax-1} per tile
+// (kmax = the largest kcol of the block); consumer (c, g) forms the correction of its rows of
+// column c in the basis precision with the operations of update_x_kernel, in the same order
+// (bit-identical x), and adds it to x in FP64.  y is staged in shared memory as T.
+template <typename T>
+__global__ void __launch_bounds__(kBdThreads, 2)
+    update_x_bulk_kernel(const T* __restrict__ Z, int64_t zstride, const double2* __restrict__ y,
+                         const int32_t* __restrict__ kcol, int m, double2* __restrict__ x, int64_t E, int R, int G,
+                         int NS, int32_t* __restrict__ err) {
+  using Sc = typename Traits<T>::S;
+  constexpr int RPT = bd_rows<T>();
+  constexpr int kStageElems = kBdStageBytes / (int)sizeof(T);
+  extern __shared__ __align__(128) uint8_t ux_smem[];
+  T* stage = reinterpret_cast<T*>(ux_smem);
+  T* ys = reinterpret_cast<T*>(ux_smem + (size_t)NS * kBdStageBytes);   // [m][R]
+  int32_t* ks = reinterpret_cast<int32_t*>(ys + (size_t)m * R);          // [R]
+  uint64_t* full = reinterpret_cast<uint64_t*>(ks + ((R + 3) & ~3));
+  uint64_t* empty = full + NS;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NS);
+  __shared__ int kmax_s;
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kBdConsumers);
+    }
+    *abort_flag = 0;
+    int km = 0;
+    for (int c = 0; c < R; ++c) km = max(km, min(kcol[c], m));
+    kmax_s = km;
+    mbar_init_fence();
+  }
+  for (int t = tid; t < R; t += kBdThreads) ks[t] = kcol[t];
+  for (int t = tid; t < m * R; t += kBdThreads) {
+    const int l = t / R, c = t - l * R;
+    const double2 v = y[(int64_t)c * m + l];
+    ys[t] = T{(Sc)v.x, (Sc)v.y};
+  }
+  __syncthreads();
+  const int kmax = kmax_s;
+
+  const int TR = G * RPT;
+  const int64_t nt = (E + TR - 1) / TR;
+  const int64_t t0 = nt * blockIdx.x / gridDim.x, t1 = nt * (blockIdx.x + 1) / gridDim.x;
+
+  if (tid < 32) {
+    if (tid != 0) return;
+    int64_t it = 0;
+    int st = 0;
+    uint32_t ph = 0;
+    bool stop = false;
+    for (int64_t t = t0; t < t1 && !stop; ++t) {
+      const int64_t r0 = t * TR;
+      const int64_t rows = E - r0 < TR ? E - r0 : (int64_t)TR;
+      const uint32_t bytes = (uint32_t)((rows * R * (int64_t)sizeof(T)) & ~(int64_t)15);
+      for (int l = 0; l < kmax; ++l) {
+        if (it >= NS && !mbar_wait(&empty[st], ph ^ 1u)) {
+          atomicCAS(err, 0, 31);
+          *abort_flag = 1;
+        }
+        if (*abort_flag) {
+          stop = true;
+          break;
+        }
+        const T* src = Z + (int64_t)l * zstride + r0 * R;
+        if (bytes > 0) {
+          mbar_expect_tx(&full[st], bytes);
+          bulk_g2s(stage + (size_t)st * kStageElems, src, bytes, &full[st]);
+        } else {
+          mbar_arrive(&full[st]);
+        }
+        ++it;
+        if (++st == NS) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    for (int k = 0; k < NS; ++k) {
+      if (k >= st && it < NS) continue;
+      if (!mbar_wait(&full[k], k < st ? ph : ph ^ 1u)) atomicCAS(err, 0, 32);
+    }
+    return;
+  }
+
+  const int ct = tid - 32;
+  const int c = ct % R, g = ct / R;
+  const bool act = g < G;
+  const int kc = act ? ks[c] : 0;
+  int st = 0;
+  uint32_t ph = 0;
+  for (int64_t t = t0; t < t1; ++t) {
+    const int64_t r0 = t * TR;
+    const int64_t rows = E - r0 < TR ? E - r0 : (int64_t)TR;
+    const int64_t ncop = ((rows * R * (int64_t)sizeof(T)) & ~(int64_t)15) / (int64_t)sizeof(T);
+    Sc dr[RPT], di[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) dr[k] = di[k] = 0;
+    for (int l = 0; l < kmax; ++l) {
+      if (!*abort_flag && !mbar_wait(&full[st], ph)) {
+        atomicCAS(err, 0, 33);
+        *abort_flag = 1;
+      }
+      if (act && l < kc) {
+        const T* sm = stage + (size_t)st * kStageElems;
+        const T* gl = Z + (int64_t)l * zstride + r0 * R;
+        const T yy = ys[l * R + c];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+          const int row = k * G + g;
+          const int f = row * R + c;
+          if (row < rows) {
+            const T z = f < ncop ? sm[f] : gl[f];
+            dr[k] = fma(yy.x, z.x, dr[k]);
+            dr[k] = fma(-yy.y, z.y, dr[k]);
+            di[k] = fma(yy.x, z.y, di[k]);
+            di[k] = fma(yy.y, z.x, di[k]);
+          }
+        }
+      }
+      mbar_arrive(&empty[st]);
+      if (++st == NS) {
+        st = 0;
+        ph ^= 1u;
+      }
+    }
+    if (act && !*abort_flag) {
+      double2* xr = x + r0 * R;
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int row = k * G + g;
+        if (row < rows) {
+          double2 xv = xr[row * R + c];
+          xv.x += (double)dr[k];
+          xv.y += (double)di[k];
+          xr[row * R + c] = xv;
+        }
+      }
+    }
+  }
+}
+
+inline size_t ux_smem_bytes(int R, int m, int NS) {
+  return (size_t)NS * kBdStageBytes + (size_t)m * R * 16 + ((R + 3) & ~3) * 4 + 2 * NS * sizeof(uint64_t) + 16;
+}
+
+template <typename T>
+bool update_x_bulk(const T* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x, int64_t E,
+                   int R, int32_t* err, cudaStream_t s) {
+  const bool aligned = ((uintptr_t)Z % 16 == 0) && ((zstride * sizeof(T)) % 16 == 0);
+  if (!err || !aligned || R < 16 || R > 128 || m < 1) return false;
+  static bool attr = false;
+  if (!attr) {
+    // 226 KB: the kernel's static shared memory shares the 227 KB per block
+    attr = cudaFuncSetAttribute(update_x_bulk_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                226 * 1024) == cudaSuccess &&
+           cudaFuncSetAttribute(update_x_bulk_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                226 * 1024) == cudaSuccess;
+  }
+  int NS = kBdStages;
+  while (NS > 2 && ux_smem_bytes(R, m, NS) > (size_t)226 * 1024) --NS;
+  update_x_bulk_kernel<T><<<152 * 2, kBdThreads, ux_smem_bytes(R, m, NS), s>>>(Z, zstride, y, kcol, m, x, E, R,
+                                                                              kBdConsumers / R, NS, err);
+  return true;
+}
+
 inline int gs_blocks(int64_t n) {
   int64_t b = (n + 255) / 256;
   return (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
@@ -867,9 +1035,10 @@ int update_launch(const T* V, int64_t vstride, int nvec, const double2* h, T* w,
   if (err && aligned && R >= 16 && R <= 128 && nvec >= 1) {
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(cgs_update_bulk_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      cudaFuncSetAttribute(cgs_update_bulk_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      attr = true;
+      attr = cudaFuncSetAttribute(cgs_update_bulk_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  226 * 1024) == cudaSuccess &&
+             cudaFuncSetAttribute(cgs_update_bulk_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  226 * 1024) == cudaSuccess;
     }
     int NS = stages >= 2 && stages <= kBdMaxStages ? stages : kBdStages;
     while (NS > 2 && bu_smem_bytes(R, nvec, NS) > (size_t)226 * 1024) --NS;
@@ -1024,13 +1193,15 @@ void solve_hessenberg(const double2* H, const double2* gvec, const int32_t* kcol
   hessenberg_solve_kernel<<<(R + 127) / 128, 128, 0, s>>>(H, gvec, kcol, m, R, y);
 }
 void update_x_f64(const double2* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x,
-                  int64_t E, int R, cudaStream_t s) {
+                  int64_t E, int R, cudaStream_t s, int32_t* err) {
   note_launch(1);
+  if (update_x_bulk<double2>(Z, zstride, y, kcol, m, x, E, R, err, s)) return;
   update_x_kernel<double2><<<gs_blocks(E * R), 256, 0, s>>>(Z, zstride, y, kcol, m, x, E, R);
 }
 void update_x_f32(const float2* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x,
-                  int64_t E, int R, cudaStream_t s) {
+                  int64_t E, int R, cudaStream_t s, int32_t* err) {
   note_launch(1);
+  if (update_x_bulk<float2>(Z, zstride, y, kcol, m, x, E, R, err, s)) return;
   update_x_kernel<float2><<<gs_blocks(E * R), 256, 0, s>>>(Z, zstride, y, kcol, m, x, E, R);
 }
 

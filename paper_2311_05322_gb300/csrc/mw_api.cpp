@@ -503,9 +503,9 @@ void cycle_finish(Ctx* c, const CycleArgs& a) {
   Work& w = c->work;
   mwk::solve_hessenberg(w.H, w.g, w.kcol, a.m, a.R, w.y, c->stream);
   if (a.wp == 0)
-    mwk::update_x_f64((const double2*)a.Zp(w, 0), a.vstride, w.y, w.kcol, a.m, a.X, a.E, a.R, c->stream);
+    mwk::update_x_f64((const double2*)a.Zp(w, 0), a.vstride, w.y, w.kcol, a.m, a.X, a.E, a.R, c->stream, w.kerr);
   else
-    mwk::update_x_f32((const float2*)a.Zp(w, 0), a.vstride, w.y, w.kcol, a.m, a.X, a.E, a.R, c->stream);
+    mwk::update_x_f32((const float2*)a.Zp(w, 0), a.vstride, w.y, w.kcol, a.m, a.X, a.E, a.R, c->stream, w.kerr);
   check_launch("solution update");
   CK(cudaMemcpyAsync(w.h_ivec, w.kcol, sizeof(int32_t) * a.R, cudaMemcpyDeviceToHost, c->stream));
 }

@@ -156,10 +156,11 @@ void start_cycle_f32(const double2* r, const double* rnorm, int64_t E, int R, fl
 void copy_v0_f64(const double2* r, const double* rnorm, int64_t E, int R, double2* v0, cudaStream_t s);
 void solve_hessenberg(const double2* H, const double2* gvec, const int32_t* kcol, int m, int R, double2* y,
                       cudaStream_t s);
+// x += sum_{l < kcol[c]} y[c][l] Z_l per column; err as for cgs_dots (null: the non-streaming kernel).
 void update_x_f64(const double2* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x,
-                  int64_t E, int R, cudaStream_t s);
+                  int64_t E, int R, cudaStream_t s, int32_t* err = nullptr);
 void update_x_f32(const float2* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x,
-                  int64_t E, int R, cudaStream_t s);
+                  int64_t E, int R, cudaStream_t s, int32_t* err = nullptr);
 void reduce_cols(const double* part, int nparts, int R, double* out, cudaStream_t s);
 
 // layout conversions
