@@ -765,6 +765,27 @@ __global__ void normalize_start_kernel(const double2* __restrict__ r, const doub
   }
 }
 
+// v0 = r / |r| per column from an FP32 residual (mixed mode): the column scales are formed once
+// per block in shared memory, the column index advances with the grid stride.
+__global__ void normalize_start32_kernel(const float2* __restrict__ r, const double* __restrict__ rnorm,
+                                         const int32_t* __restrict__ done, int64_t E, int R, float2* __restrict__ v0) {
+  extern __shared__ float sc[];
+  for (int c = threadIdx.x; c < R; c += blockDim.x) sc[c] = done[c] ? 0.f : (float)(1.0 / rnorm[c]);
+  __syncthreads();
+  const int64_t n = E * R;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int step = (int)(stride % R);
+  int c = (int)(i0 % R);
+  for (int64_t i = i0; i < n; i += stride) {
+    const float2 x = r[i];
+    const float s = sc[c];
+    v0[i] = make_float2(x.x * s, x.y * s);
+    c += step;
+    if (c >= R) c -= R;
+  }
+}
+
 // Back substitution R y = g per column (R upper triangular after the rotations).
 __global__ void hessenberg_solve_kernel(const double2* __restrict__ H, const double2* __restrict__ g,
                                         const int32_t* __restrict__ kcol, int m, int R, double2* __restrict__ y) {
@@ -1186,6 +1207,11 @@ void normalize_start_f32(const double2* r, const double* rnorm, const int32_t* d
                          cudaStream_t s) {
   note_launch(1);
   normalize_start_kernel<float2><<<gs_blocks(E * R), 256, 0, s>>>(r, rnorm, done, E, R, v0);
+}
+void normalize_start32(const float2* r, const double* rnorm, const int32_t* done, int64_t E, int R, float2* v0,
+                       cudaStream_t s) {
+  note_launch(1);
+  normalize_start32_kernel<<<gs_blocks(E * R), 256, sizeof(float) * R, s>>>(r, rnorm, done, E, R, v0);
 }
 void solve_hessenberg(const double2* H, const double2* gvec, const int32_t* kcol, int m, int R, double2* y,
                       cudaStream_t s) {

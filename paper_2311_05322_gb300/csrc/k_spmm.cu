@@ -268,6 +268,76 @@ __global__ void __launch_bounds__(256) residual_df_kernel(const int64_t* __restr
   }
 }
 
+// (b_h + b_l) - (y_h + y_l) rounded to FP32: the high parts' difference with its exact error
+// (two-sum), then the low parts.
+__device__ __forceinline__ float df_sub_round(float b_h, float b_l, float y_h, float y_l) {
+  const float s = __fsub_rn(b_h, y_h);
+  const float bp = __fsub_rn(s, b_h);
+  const float e = __fadd_rn(__fsub_rn(b_h, __fsub_rn(s, bp)), __fsub_rn(-y_h, bp));
+  return __fadd_rn(s, __fadd_rn(__fsub_rn(b_l, y_l), e));
+}
+
+// The outer residual of the mixed solver: r = b - A x with b, A and x in double-float, every
+// product and sum as in residual_df_kernel, r rounded once to FP32 complex (the inner solver's
+// start vector is FP32) and |r|^2 of the rounded r promoted to FP64 per row (per-block,
+// per-column partials).  Two FP64 operations per element instead of eleven.
+template <int CPL>
+__global__ void __launch_bounds__(256) residual_df32_kernel(const int64_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ ci,
+                                                            const float4* __restrict__ A, const float4* __restrict__ X,
+                                                            const float4* __restrict__ Bdf, float2* __restrict__ Rv,
+                                                            double* __restrict__ part, int64_t E, int R, int tpr_log2) {
+  __shared__ double red[256 * CPL];
+  const int tpr = 1 << tpr_log2;
+  const int rows_per_block = 256 >> tpr_log2;
+  const int lane_c = threadIdx.x & (tpr - 1);
+  const int c0 = lane_c * CPL;
+  double nrm[CPL];
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) nrm[q] = 0.0;
+  for (int64_t row = (int64_t)blockIdx.x * rows_per_block + (threadIdx.x >> tpr_log2); row < E;
+       row += (int64_t)gridDim.x * rows_per_block) {
+    if (c0 >= R) continue;
+    float rh[CPL], rl[CPL], ih[CPL], il[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
+    for (int64_t k = rp[row]; k < rp[row + 1]; ++k) {
+      const float4 a = A[k];
+      const float4* xr = X + (int64_t)ci[k] * R + c0;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+        if (c0 + q < R) {
+          const float4 x = xr[q];
+          df_mac(rh[q], rl[q], a.x, a.y, x.x, x.y);
+          df_mac(rh[q], rl[q], -a.z, -a.w, x.z, x.w);
+          df_mac(ih[q], il[q], a.x, a.y, x.z, x.w);
+          df_mac(ih[q], il[q], a.z, a.w, x.x, x.y);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPL; ++q)
+      if (c0 + q < R) {
+        const float4 bb = Bdf[row * R + c0 + q];
+        const float re = df_sub_round(bb.x, bb.y, rh[q], rl[q]);
+        const float im = df_sub_round(bb.z, bb.w, ih[q], il[q]);
+        Rv[row * R + c0 + q] = make_float2(re, im);
+        nrm[q] += (double)fmaf(re, re, __fmul_rn(im, im));
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) red[threadIdx.x * CPL + q] = nrm[q];
+  __syncthreads();
+  if ((int)threadIdx.x < tpr) {
+    for (int q = 0; q < CPL; ++q) {
+      const int c = c0 + q;
+      if (c >= R) continue;
+      double s = 0.0;
+      for (int r = 0; r < rows_per_block; ++r) s += red[(r * tpr + lane_c) * CPL + q];
+      part[(int64_t)blockIdx.x * R + c] = s;
+    }
+  }
+}
+
 }  // namespace
 
 void split_df(const double2* a, float4* o, int64_t n, cudaStream_t s) {
@@ -290,6 +360,25 @@ int residual_df(const int64_t* rp, const int32_t* ci, const float4* A, const flo
       break;
     default:
       residual_df_kernel<4><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
+      break;
+  }
+  return blocks;
+}
+
+int residual_df32(const int64_t* rp, const int32_t* ci, const float4* A, const float4* X, const float4* Bdf, float2* Rv,
+                  double* part, int64_t E, int R, cudaStream_t s) {
+  note_launch(1);
+  Shape sh = shape_for(R);
+  const int blocks = 152 * 4;
+  switch (sh.cpl) {
+    case 1:
+      residual_df32_kernel<1><<<blocks, 256, 0, s>>>(rp, ci, A, X, Bdf, Rv, part, E, R, sh.tpr_log2);
+      break;
+    case 2:
+      residual_df32_kernel<2><<<blocks, 256, 0, s>>>(rp, ci, A, X, Bdf, Rv, part, E, R, sh.tpr_log2);
+      break;
+    default:
+      residual_df32_kernel<4><<<blocks, 256, 0, s>>>(rp, ci, A, X, Bdf, Rv, part, E, R, sh.tpr_log2);
       break;
   }
   return blocks;

@@ -75,6 +75,8 @@ struct Work {
   void *V = nullptr, *Z = nullptr;   // Krylov and preconditioned bases, vectors krylov_stride apart
   int32_t* kerr = nullptr;     // bounded-wait error code of the streaming Gram-Schmidt kernel
   float4* xdf = nullptr;       // double-float copy of the iterate (mixed mode)
+  float4* bdf = nullptr;       // double-float copy of the block's right-hand sides (mixed mode)
+  float2* r32 = nullptr;       // outer residual rounded to FP32 (mixed mode)
   double2 *r = nullptr, *x = nullptr, *part = nullptr, *h = nullptr, *H = nullptr, *cs = nullptr, *g = nullptr,
           *y = nullptr, *bblk = nullptr;
   double *npart = nullptr, *target = nullptr, *rnorm = nullptr, *bnorm = nullptr, *scale = nullptr;
@@ -295,7 +297,7 @@ void free_work(Ctx* c) {
   Work& w = c->work;
   for (void* p : {(void*)w.V, (void*)w.Z, (void*)w.xdf, (void*)w.r, (void*)w.x, (void*)w.part, (void*)w.h, (void*)w.H, (void*)w.cs,
                   (void*)w.g, (void*)w.y, (void*)w.npart, (void*)w.target, (void*)w.rnorm, (void*)w.bnorm,
-                  (void*)w.scale, (void*)w.done, (void*)w.kcol, (void*)w.active, (void*)w.bblk, (void*)w.kerr, w.tc_scratch})
+                  (void*)w.scale, (void*)w.done, (void*)w.kcol, (void*)w.active, (void*)w.bblk, (void*)w.kerr, (void*)w.bdf, (void*)w.r32, w.tc_scratch})
     dfree(c, p);
   if (w.h_active) cudaFreeHost(w.h_active);
   if (w.h_vec) cudaFreeHost(w.h_vec);
@@ -321,7 +323,11 @@ void ensure_work(Ctx* c, int R, int m, int prec) {
   CK(cudaMemsetAsync(w.kerr, 0, sizeof(int32_t), c->stream));
   w.r = dalloc<double2>(c, n);
   w.x = dalloc<double2>(c, n);
-  if (prec == 1) w.xdf = dalloc<float4>(c, n);
+  if (prec == 1) {
+    w.xdf = dalloc<float4>(c, n);
+    w.bdf = dalloc<float4>(c, n);
+    w.r32 = dalloc<float2>(c, n);
+  }
   w.bblk = dalloc<double2>(c, n);
   w.part = dalloc<double2>(c, (size_t)kDotParts * 8 * R > (size_t)kRedBlocks * (kMaxRestart + 1) * R
                                   ? (size_t)kDotParts * 8 * R
@@ -416,14 +422,16 @@ int read_active(Ctx* c) {
   return *c->work.h_active;
 }
 
-// r = b - A_f x with per-block partial norms: FP64 arithmetic in FP64 mode, double-float
-// arithmetic on the FP32 pipes in mixed mode (same accuracy class, ~5x the throughput).
+// r = b - A_f x with per-block partial norms: FP64 arithmetic into w.r in FP64 mode; in mixed
+// mode double-float arithmetic on the FP32 pipes (same accuracy class) with b taken from w.bdf
+// (split once per block solve) and r rounded to FP32 into w.r32, which is all the inner solver's
+// start vector needs.
 int outer_residual(Ctx* c, int f, int wp, const double2* X, const double2* B, int R) {
   Work& w = c->work;
   const int64_t E = c->topo.n_edge;
   if (wp == 0) return mwk::residual_f64(c->d_row, c->d_col, c->A64[f], X, B, w.r, w.npart, E, R, c->stream);
   mwk::split_df(X, w.xdf, E * R, c->stream);
-  return mwk::residual_df(c->d_row, c->d_col, c->Adf[f], w.xdf, B, w.r, w.npart, E, R, c->stream);
+  return mwk::residual_df32(c->d_row, c->d_col, c->Adf[f], w.xdf, w.bdf, w.r32, w.npart, E, R, c->stream);
 }
 
 struct BlockStats {
@@ -495,7 +503,7 @@ void cycle_start(Ctx* c, const CycleArgs& a) {
   if (a.wp == 0)
     mwk::normalize_start_f64(w.r, w.rnorm, w.done, a.E, a.R, (double2*)a.Vp(w, 0), c->stream);
   else
-    mwk::normalize_start_f32(w.r, w.rnorm, w.done, a.E, a.R, (float2*)a.Vp(w, 0), c->stream);
+    mwk::normalize_start32(w.r32, w.rnorm, w.done, a.E, a.R, (float2*)a.Vp(w, 0), c->stream);
 }
 
 // Least squares, x += Z y, and the per-column step counts into w.h_ivec (not yet synchronised).
@@ -816,6 +824,7 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
               tuned_for(c, R, wp, m, use_p)};
 
   CK(cudaMemsetAsync(X, 0, sizeof(double2) * E * R, s));
+  if (wp == 1) mwk::split_df(B, w.bdf, E * R, s);
   int nb = mwk::colnorm2_f64(B, E, R, w.npart, s);
   mwk::reduce_cols(w.npart, nb, R, w.bnorm, s);
   mwk::sqrt_inplace(w.bnorm, R, s);
