@@ -277,10 +277,21 @@ __device__ __forceinline__ float df_sub_round(float b_h, float b_l, float y_h, f
   return __fadd_rn(s, __fadd_rn(__fsub_rn(b_l, y_l), e));
 }
 
+// (a_h, a_l) += (b_h, b_l): two-sum of the high parts, low parts added to the error.
+__device__ __forceinline__ void df_add(float& a_h, float& a_l, float b_h, float b_l) {
+  const float t = __fadd_rn(a_h, b_h);
+  const float bp = __fsub_rn(t, a_h);
+  const float e = __fadd_rn(__fsub_rn(a_h, __fsub_rn(t, bp)), __fsub_rn(b_h, bp));
+  a_l = __fadd_rn(__fadd_rn(a_l, b_l), e);
+  a_h = t;
+}
+
 // The outer residual of the mixed solver: r = b - A x with b, A and x in double-float, every
 // product and sum as in residual_df_kernel, r rounded once to FP32 complex (the inner solver's
 // start vector is FP32) and |r|^2 of the rounded r promoted to FP64 per row (per-block,
-// per-column partials).  Two FP64 operations per element instead of eleven.
+// per-column partials).  Two FP64 operations per element instead of eleven.  The nonzeros of a
+// row alternate between two independent double-float accumulators (two dependency chains in
+// flight), joined by a double-float add at the end of the row.
 template <int CPL>
 __global__ void __launch_bounds__(256) residual_df32_kernel(const int64_t* __restrict__ rp,
                                                             const int32_t* __restrict__ ci,
@@ -298,10 +309,30 @@ __global__ void __launch_bounds__(256) residual_df32_kernel(const int64_t* __res
   for (int64_t row = (int64_t)blockIdx.x * rows_per_block + (threadIdx.x >> tpr_log2); row < E;
        row += (int64_t)gridDim.x * rows_per_block) {
     if (c0 >= R) continue;
-    float rh[CPL], rl[CPL], ih[CPL], il[CPL];
+    float rh[CPL], rl[CPL], ih[CPL], il[CPL], rh2[CPL], rl2[CPL], ih2[CPL], il2[CPL];
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
-    for (int64_t k = rp[row]; k < rp[row + 1]; ++k) {
+    for (int q = 0; q < CPL; ++q) rh[q] = rl[q] = ih[q] = il[q] = rh2[q] = rl2[q] = ih2[q] = il2[q] = 0.f;
+    const int64_t kb = rp[row], ke = rp[row + 1];
+    int64_t k = kb;
+    for (; k + 1 < ke; k += 2) {
+      const float4 a = A[k], a2 = A[k + 1];
+      const float4* xr = X + (int64_t)ci[k] * R + c0;
+      const float4* xr2 = X + (int64_t)ci[k + 1] * R + c0;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+        if (c0 + q < R) {
+          const float4 x = xr[q], x2 = xr2[q];
+          df_mac(rh[q], rl[q], a.x, a.y, x.x, x.y);
+          df_mac(rh2[q], rl2[q], a2.x, a2.y, x2.x, x2.y);
+          df_mac(ih[q], il[q], a.x, a.y, x.z, x.w);
+          df_mac(ih2[q], il2[q], a2.x, a2.y, x2.z, x2.w);
+          df_mac(rh[q], rl[q], -a.z, -a.w, x.z, x.w);
+          df_mac(rh2[q], rl2[q], -a2.z, -a2.w, x2.z, x2.w);
+          df_mac(ih[q], il[q], a.z, a.w, x.x, x.y);
+          df_mac(ih2[q], il2[q], a2.z, a2.w, x2.x, x2.y);
+        }
+    }
+    if (k < ke) {
       const float4 a = A[k];
       const float4* xr = X + (int64_t)ci[k] * R + c0;
 #pragma unroll
@@ -309,10 +340,15 @@ __global__ void __launch_bounds__(256) residual_df32_kernel(const int64_t* __res
         if (c0 + q < R) {
           const float4 x = xr[q];
           df_mac(rh[q], rl[q], a.x, a.y, x.x, x.y);
-          df_mac(rh[q], rl[q], -a.z, -a.w, x.z, x.w);
           df_mac(ih[q], il[q], a.x, a.y, x.z, x.w);
+          df_mac(rh[q], rl[q], -a.z, -a.w, x.z, x.w);
           df_mac(ih[q], il[q], a.z, a.w, x.x, x.y);
         }
+    }
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      df_add(rh[q], rl[q], rh2[q], rl2[q]);
+      df_add(ih[q], il[q], ih2[q], il2[q]);
     }
 #pragma unroll
     for (int q = 0; q < CPL; ++q)
