@@ -47,6 +47,8 @@ def _args(argv=None):
     ap.add_argument("--alpha", type=float, default=1e-3)
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--plain-cols", type=int, default=1, help="columns timed on the plain FP64 path (0 = skip)")
+    ap.add_argument("--fp64-batch-cols", type=int, default=4,
+                    help="columns timed as one FP64 block (isolates the batching gain; 0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graphs", action="store_true", help="replay restart cycles from captured CUDA graphs")
     ap.add_argument("--cpu-sample-subdomains", type=int, default=24)
@@ -347,6 +349,24 @@ def run_mine(a):
                              "one column per launch"}
         except Exception as e:  # report, do not hide
             plain = {"error": str(e)}
+    # ---- FP64 batched (FP64 everything, several columns in one Krylov launch) ---------------
+    fp64_batched = None
+    if a.plain_cols > 0 and a.fp64_batch_cols > 0 and rank == 0 and plain is not None and "error" not in plain:
+        try:
+            nb = min(a.fp64_batch_cols, a.n_src)
+            rhs = np.zeros((nb, info.n_edge), dtype=np.complex128)
+            for j in range(nb):
+                rhs[j, c.src_edges[j]] = -1j * 2 * np.pi * freqs[0] * 4e-7 * np.pi * c.src_signs[j]
+            b_d = torch.from_numpy(rhs).to(dev)
+            x_d = torch.empty_like(b_d)
+            po = mw.solve_opts(mode=mw.MW_MODE_FP64, restart=50, batch=0, tol=1e-8, max_it=2000)
+            st = c.solve_rhs(nb, b_d, x_d, po)
+            fp64_batched = {"value": nb / (st["solve_ms"] * 1e-3), "unit": UNIT, "cols": nb,
+                            "solve_ms": st["solve_ms"], "arnoldi_steps": st["arnoldi_steps"],
+                            "max_relres": st["max_relres"],
+                            "note": "as plain_fp64, with the columns in one Krylov launch (batching gain alone)"}
+        except Exception as e:
+            fp64_batched = {"error": str(e)}
 
     # ---- roofline of the dominant kernel class ---------------------------------------------
     hbm, bf16, bf16s, src = peaks()
@@ -400,6 +420,7 @@ def run_mine(a):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clk.summary(), "setup_s": setup, "plain_fp64": plain,
+            "fp64_batched": fp64_batched,
             "J_last": J,
         }
         print(json.dumps(line), flush=True)

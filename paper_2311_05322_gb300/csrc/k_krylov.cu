@@ -361,7 +361,9 @@ __global__ void __launch_bounds__(kBdThreads, 2)
 
 // h[i][c] = sum_p part[p][i][c]: one warp per entry, lanes take parts lane, lane + 32, ...,
 // then a fixed shuffle tree (deterministic).
-__global__ void reduce_h_kernel(const double2* __restrict__ part, int nparts, int nvec, int R, double2* __restrict__ h) {
+// With vscale (the basis kept unscaled, V_i = vscale[i][c] * Vu_i), h[i][c] is scaled by it.
+__global__ void reduce_h_kernel(const double2* __restrict__ part, int nparts, int nvec, int R, double2* __restrict__ h,
+                                const double* __restrict__ vscale) {
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (t >= nvec * R) return;
@@ -375,7 +377,10 @@ __global__ void reduce_h_kernel(const double2* __restrict__ part, int nparts, in
     x += __shfl_xor_sync(0xffffffffu, x, off);
     y += __shfl_xor_sync(0xffffffffu, y, off);
   }
-  if (lane == 0) h[t] = make_double2(x, y);
+  if (lane == 0) {
+    const double sc = vscale ? vscale[t] : 1.0;
+    h[t] = make_double2(x * sc, y * sc);
+  }
 }
 
 // w[e][c] -= sum_i h[i][c] V_i[e][c]; partial sums of |w|^2 per block and column.
@@ -383,14 +388,16 @@ template <typename T, int CPL>
 __global__ void __launch_bounds__(kThreads) cgs_update_kernel(const T* __restrict__ V, int64_t vstride, int nvec,
                                                               const double2* __restrict__ h, T* __restrict__ w,
                                                               int64_t E, int R, int tpr_log2,
-                                                              double* __restrict__ npart) {
+                                                              double* __restrict__ npart,
+                                                              const double* __restrict__ vscale) {
   using Sc = typename Traits<T>::S;
   extern __shared__ unsigned char smem_raw[];
   T* hs = reinterpret_cast<T*>(smem_raw);                          // [nvec][R]
   double* red = reinterpret_cast<double*>(smem_raw + sizeof(T) * nvec * R + 16);  // [kThreads][CPL]
   for (int t = threadIdx.x; t < nvec * R; t += kThreads) {
     const double2 v = h[t];
-    hs[t] = T{(Sc)v.x, (Sc)v.y};
+    const double sc = vscale ? vscale[t] : 1.0;   // coefficient of the unscaled basis vector
+    hs[t] = T{(Sc)(v.x * sc), (Sc)(v.y * sc)};
   }
   __syncthreads();
   const int tpr = 1 << tpr_log2;
@@ -454,7 +461,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBdThreads, 2)
     cgs_update_bulk_kernel(const T* __restrict__ V, int64_t vstride, int nvec, const double2* __restrict__ h,
                            T* __restrict__ w, int64_t E, int R, int G, int NS, double* __restrict__ npart,
-                           int32_t* __restrict__ err) {
+                           int32_t* __restrict__ err, const double* __restrict__ vscale) {
   using Sc = typename Traits<T>::S;
   constexpr int RPT = bd_rows<T>();
   constexpr int kStageElems = kBdStageBytes / (int)sizeof(T);
@@ -477,7 +484,8 @@ __global__ void __launch_bounds__(kBdThreads, 2)
   }
   for (int t = tid; t < nvec * R; t += kBdThreads) {
     const double2 v = h[t];
-    hs[t] = T{(Sc)v.x, (Sc)v.y};
+    const double sc = vscale ? vscale[t] : 1.0;   // coefficient of the unscaled basis vector
+    hs[t] = T{(Sc)(v.x * sc), (Sc)(v.y * sc)};
   }
   __syncthreads();
 
@@ -1050,7 +1058,7 @@ int dots_launch(const T* V, int64_t vstride, int nvec, const T* w, int64_t E, in
 
 template <typename T>
 int update_launch(const T* V, int64_t vstride, int nvec, const double2* h, T* w, int64_t E, int R, double* npart,
-                  cudaStream_t s, int32_t* err, int stages) {
+                  cudaStream_t s, int32_t* err, int stages, const double* vscale) {
   note_launch(1);
   const bool aligned = ((uintptr_t)V % 16 == 0) && ((uintptr_t)w % 16 == 0) && ((vstride * sizeof(T)) % 16 == 0);
   if (err && aligned && R >= 16 && R <= 128 && nvec >= 1) {
@@ -1066,7 +1074,7 @@ int update_launch(const T* V, int64_t vstride, int nvec, const double2* h, T* w,
     const int G = kBdConsumers / R;
     const int nb = 152 * 2;
     cgs_update_bulk_kernel<T>
-        <<<nb, kBdThreads, bu_smem_bytes(R, nvec, NS), s>>>(V, vstride, nvec, h, w, E, R, G, NS, npart, err);
+        <<<nb, kBdThreads, bu_smem_bytes(R, nvec, NS), s>>>(V, vstride, nvec, h, w, E, R, G, NS, npart, err, vscale);
     return nb;
   }
   Shape sh = shape_for(R);
@@ -1081,16 +1089,23 @@ int update_launch(const T* V, int64_t vstride, int nvec, const double2* h, T* w,
   }
   switch (sh.cpl) {
     case 1:
-      cgs_update_kernel<T, 1><<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, h, w, E, R, sh.tpr_log2, npart);
+      cgs_update_kernel<T, 1>
+          <<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, h, w, E, R, sh.tpr_log2, npart, vscale);
       break;
     case 2:
-      cgs_update_kernel<T, 2><<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, h, w, E, R, sh.tpr_log2, npart);
+      cgs_update_kernel<T, 2>
+          <<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, h, w, E, R, sh.tpr_log2, npart, vscale);
       break;
     default:
-      cgs_update_kernel<T, 4><<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, h, w, E, R, sh.tpr_log2, npart);
+      cgs_update_kernel<T, 4>
+          <<<kBlocks, kThreads, smem, s>>>(V, vstride, nvec, h, w, E, R, sh.tpr_log2, npart, vscale);
       break;
   }
   return kBlocks;
+}
+
+__global__ void fill_f64_kernel(double* __restrict__ x, int n, double v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = v;
 }
 
 // Deterministic pseudo-random fill in [-1, 1) (timing inputs of the launch-shape tuner).
@@ -1118,6 +1133,10 @@ __global__ void set_step_conditions_kernel(StepHandles sh, const int32_t* __rest
 
 }  // namespace
 
+void fill_f64(double* x, int n, double v, cudaStream_t s) {
+  note_launch(1);
+  fill_f64_kernel<<<(n + 255) / 256 < 64 ? (n + 255) / 256 : 64, 256, 0, s>>>(x, n, v);
+}
 void fill_pattern_f32(float* x, int64_t n, uint32_t seed, cudaStream_t s, double scale) {
   note_launch(1);
   fill_pattern_kernel<float><<<gs_blocks(n), 256, 0, s>>>(x, n, seed, scale);
@@ -1143,18 +1162,18 @@ int cgs_dots_f32(const float2* V, int64_t vstride, int nvec, const float2* w, in
                  int32_t* err, cudaStream_t s, int stages) {
   return dots_launch<float2>(V, vstride, nvec, w, E, R, part, err, s, stages);
 }
-void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s) {
+void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s, const double* vscale) {
   note_launch(1);
   const int n = nvec * R;
-  reduce_h_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(part, nparts, nvec, R, h);
+  reduce_h_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(part, nparts, nvec, R, h, vscale);
 }
 int cgs_update_f64(const double2* V, int64_t vstride, int nvec, const double2* h, double2* w, int64_t E, int R,
-                   double* npart, cudaStream_t s, int32_t* err, int stages) {
-  return update_launch<double2>(V, vstride, nvec, h, w, E, R, npart, s, err, stages);
+                   double* npart, cudaStream_t s, int32_t* err, int stages, const double* vscale) {
+  return update_launch<double2>(V, vstride, nvec, h, w, E, R, npart, s, err, stages, vscale);
 }
 int cgs_update_f32(const float2* V, int64_t vstride, int nvec, const double2* h, float2* w, int64_t E, int R,
-                   double* npart, cudaStream_t s, int32_t* err, int stages) {
-  return update_launch<float2>(V, vstride, nvec, h, w, E, R, npart, s, err, stages);
+                   double* npart, cudaStream_t s, int32_t* err, int stages, const double* vscale) {
+  return update_launch<float2>(V, vstride, nvec, h, w, E, R, npart, s, err, stages, vscale);
 }
 int colnorm2_f64(const double2* x, int64_t E, int R, double* npart, cudaStream_t s) {
   note_launch(1);

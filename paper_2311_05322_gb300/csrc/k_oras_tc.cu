@@ -122,9 +122,12 @@ __global__ void pack_w_kernel(const int64_t* __restrict__ nmat, const int64_t* _
 // ---------------------------------------------------------------------------------------
 // Apply, step 1: gathered operand tiles B' for every (subdomain, k tile).
 // ---------------------------------------------------------------------------------------
+// cscale (may be null): per-column factor of the input (a Krylov vector kept unscaled), applied
+// in FP32 before the BF16 rounding.
 __global__ void gather_b_kernel(const int32_t* __restrict__ gt_sub, const int32_t* __restrict__ gt_kt,
                                 const int64_t* __restrict__ dof_ptr, const int32_t* __restrict__ dofs,
-                                const float2* __restrict__ r, int R, int Rp, uint8_t* __restrict__ Bt) {
+                                const float2* __restrict__ r, int R, int Rp, uint8_t* __restrict__ Bt,
+                                const double* __restrict__ cscale) {
   // the tile is assembled in shared memory (4-byte swizzled stores) and written out with
   // coalesced 16-byte stores
   extern __shared__ __align__(16) uint8_t tsm[];
@@ -138,7 +141,14 @@ __global__ void gather_b_kernel(const int32_t* __restrict__ gt_sub, const int32_
     const int kc = idx / Rp, c = idx % Rp;
     const int64_t k = (int64_t)kt * kTileKc + kc;
     float2 v = make_float2(0.f, 0.f);
-    if (k < n && c < R) v = r[(int64_t)dv[k] * R + c];
+    if (k < n && c < R) {
+      v = r[(int64_t)dv[k] * R + c];
+      if (cscale) {
+        const float sc = (float)cscale[c];
+        v.x *= sc;
+        v.y *= sc;
+      }
+    }
     const uint32_t n0 = 2 * c, n1 = 2 * c + 1;
     *reinterpret_cast<uint32_t*>(tsm + swz(n0, 2 * kc)) = pack_bf16(v.x, -v.y);
     *reinterpret_cast<uint32_t*>(tsm + swz(n1, 2 * kc)) = pack_bf16(v.y, v.x);
@@ -409,7 +419,7 @@ int tc_max_stages(int R) {
 }
 
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
-                   void* scratch, cudaStream_t s, int stages) {
+                   void* scratch, cudaStream_t s, int stages, const double* in_scale) {
   const int Rp = rpad(R);
   const int N = 2 * Rp;
   if (stages <= 0) stages = tc_stages(N);
@@ -423,7 +433,7 @@ void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const flo
     gattr = gsm;
   }
   gather_b_kernel<<<(unsigned)p.n_ktiles_total, 256, gsm, s>>>(p.gt_sub, p.gt_kt, tp.dof_ptr, tp.dofs, r, R, Rp,
-                                                               (uint8_t*)scratch);
+                                                               (uint8_t*)scratch, in_scale);
   TcArgs a;
   a.mt_sub = p.mt_sub;
   a.mt_row0 = p.mt_row0;

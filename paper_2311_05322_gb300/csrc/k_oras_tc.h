@@ -40,9 +40,9 @@ size_t tc_scratch_bytes(const TcPlan& p, int R);
 void tc_extract(const TcPlan& p, const OrasBatch& bt, const OrasTopo& tp, int ws_prec, const void* ws, void* W,
                 cudaStream_t s);
 // stages: shared-memory pipeline depth of the MMA kernel (0 = default; the result does not depend
-// on it, only the speed).
+// on it, only the speed).  in_scale (may be null): per-column factor of r (z = M^{-1}(r * in_scale)).
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
-                   void* scratch, cudaStream_t s, int stages = 0);
+                   void* scratch, cudaStream_t s, int stages = 0, const double* in_scale = nullptr);
 // Pipeline depths the MMA kernel accepts for R columns: [tc_min_stages, tc_max_stages(R)]; the
 // default depth for R columns.
 constexpr int tc_min_stages = 2;

@@ -77,6 +77,7 @@ struct Work {
   float4* xdf = nullptr;       // double-float copy of the iterate (mixed mode)
   float4* bdf = nullptr;       // double-float copy of the block's right-hand sides (mixed mode)
   float2* r32 = nullptr;       // outer residual rounded to FP32 (mixed mode)
+  double* vscale = nullptr;    // [m+1][R] factors of the unscaled basis (BF16 tensor-core apply)
   double2 *r = nullptr, *x = nullptr, *part = nullptr, *h = nullptr, *H = nullptr, *cs = nullptr, *g = nullptr,
           *y = nullptr, *bblk = nullptr;
   double *npart = nullptr, *target = nullptr, *rnorm = nullptr, *bnorm = nullptr, *scale = nullptr;
@@ -297,7 +298,7 @@ void free_work(Ctx* c) {
   Work& w = c->work;
   for (void* p : {(void*)w.V, (void*)w.Z, (void*)w.xdf, (void*)w.r, (void*)w.x, (void*)w.part, (void*)w.h, (void*)w.H, (void*)w.cs,
                   (void*)w.g, (void*)w.y, (void*)w.npart, (void*)w.target, (void*)w.rnorm, (void*)w.bnorm,
-                  (void*)w.scale, (void*)w.done, (void*)w.kcol, (void*)w.active, (void*)w.bblk, (void*)w.kerr, (void*)w.bdf, (void*)w.r32, w.tc_scratch})
+                  (void*)w.scale, (void*)w.done, (void*)w.kcol, (void*)w.active, (void*)w.bblk, (void*)w.kerr, (void*)w.bdf, (void*)w.r32, (void*)w.vscale, w.tc_scratch})
     dfree(c, p);
   if (w.h_active) cudaFreeHost(w.h_active);
   if (w.h_vec) cudaFreeHost(w.h_vec);
@@ -320,6 +321,7 @@ void ensure_work(Ctx* c, int R, int m, int prec) {
   w.V = dalloc<unsigned char>(c, es * nv * (m + 1));
   w.Z = dalloc<unsigned char>(c, es * nv * m);
   w.kerr = dalloc<int32_t>(c, 1);
+  w.vscale = dalloc<double>(c, (size_t)(m + 1) * R);
   CK(cudaMemsetAsync(w.kerr, 0, sizeof(int32_t), c->stream));
   w.r = dalloc<double2>(c, n);
   w.x = dalloc<double2>(c, n);
@@ -367,14 +369,15 @@ void ensure_prec_scratch(Ctx* c, int R) {
   }
 }
 
-void apply_prec(Ctx* c, int f, int work_prec, const void* v, void* z, int R, int stages = 0) {
+void apply_prec(Ctx* c, int f, int work_prec, const void* v, void* z, int R, int stages = 0,
+                const double* in_scale = nullptr) {
   Prec& p = c->prec;
   cudaStream_t s = c->stream;
   if (p.apply_prec == 2) {
     require(work_prec == 1, MW_EINVAL, "BF16 preconditioner needs the mixed-precision solve");
     Work& w = c->work;
     ensure_prec_scratch(c, R);
-    mwk::oras_apply_tc(p.tc, p.topo(), p.W[f], (const float2*)v, (float2*)z, R, w.tc_scratch, s, stages);
+    mwk::oras_apply_tc(p.tc, p.topo(), p.W[f], (const float2*)v, (float2*)z, R, w.tc_scratch, s, stages, in_scale);
   } else {
     const int need = work_prec;  // 0 FP64, 1 FP32
     require(p.apply_prec == need, MW_EINVAL,
@@ -448,6 +451,10 @@ struct CycleArgs {
   int64_t E, vstride;
   size_t es;
   Tuned t;
+  // BF16 tensor-core apply: the basis is kept unscaled, V_i = vscale[i][c] * Vu_i, and the factor
+  // is applied where a vector is read (the apply's gather, the dots' reduction, the update's
+  // coefficients) instead of in a separate pass over each new vector
+  bool lazy;
   void* Vp(const Work& w, int i) const { return (unsigned char*)w.V + es * vstride * i; }
   void* Zp(const Work& w, int i) const { return use_p ? (unsigned char*)w.Z + es * vstride * i : Vp(w, i); }
 };
@@ -459,9 +466,11 @@ void arnoldi_step(Ctx* c, const CycleArgs& a, int j, Seg&& seg) {
   Work& w = c->work;
   const int64_t E = a.E;
   const int R = a.R;
+  const double* vs = a.lazy ? w.vscale : nullptr;
   if (a.use_p)
-    seg(MW_K_ORAS, oras_bytes(c, R),
-        [&] { apply_prec(c, a.f, a.wp, a.Vp(w, j), a.Zp(w, j), R, a.t.sh.tc_stages); });
+    seg(MW_K_ORAS, oras_bytes(c, R), [&] {
+      apply_prec(c, a.f, a.wp, a.Vp(w, j), a.Zp(w, j), R, a.t.sh.tc_stages, vs ? vs + (size_t)j * R : nullptr);
+    });
   seg(MW_K_SPMM, (double)c->topo.nnz * (a.es + 4) + 8.0 * (E + 1) + 2.0 * a.es * E * R, [&] {
     if (a.wp == 0)
       mwk::spmm_f64(c->d_row, c->d_col, c->A64[a.f], (const double2*)a.Zp(w, j), (double2*)a.Vp(w, j + 1), E, R,
@@ -477,23 +486,25 @@ void arnoldi_step(Ctx* c, const CycleArgs& a, int j, Seg&& seg) {
                              : mwk::cgs_dots_f32((const float2*)w.V, a.vstride, j + 1,
                                                  (const float2*)a.Vp(w, j + 1), E, R, w.part, w.kerr, c->stream,
                                                  a.t.sh.dots_stages);
-    mwk::reduce_h(w.part, np, j + 1, R, w.h, c->stream);
+    mwk::reduce_h(w.part, np, j + 1, R, w.h, c->stream, vs);
   });
   int nu = 0;
   seg(MW_K_CGS_UPDATE, (double)a.es * E * R * (j + 3), [&] {
     nu = a.wp == 0 ? mwk::cgs_update_f64((const double2*)w.V, a.vstride, j + 1, w.h, (double2*)a.Vp(w, j + 1), E,
-                                         R, w.npart, c->stream, w.kerr, a.t.sh.update_stages)
+                                         R, w.npart, c->stream, w.kerr, a.t.sh.update_stages, vs)
                    : mwk::cgs_update_f32((const float2*)w.V, a.vstride, j + 1, w.h, (float2*)a.Vp(w, j + 1), E,
-                                         R, w.npart, c->stream, w.kerr, a.t.sh.update_stages);
+                                         R, w.npart, c->stream, w.kerr, a.t.sh.update_stages, vs);
   });
   seg(-1, 0.0, [&] {
     CK(cudaMemsetAsync(w.active, 0, sizeof(int32_t), c->stream));
-    mwk::givens_step(w.h, w.npart, nu, j, a.m, R, w.H, w.cs, w.g, w.target, w.done, w.kcol, w.scale, w.active,
-                     c->stream);
-    if (a.wp == 0)
-      mwk::scale_cols_f64((double2*)a.Vp(w, j + 1), w.scale, E, R, c->stream);
-    else
-      mwk::scale_cols_f32((float2*)a.Vp(w, j + 1), w.scale, E, R, c->stream);
+    mwk::givens_step(w.h, w.npart, nu, j, a.m, R, w.H, w.cs, w.g, w.target, w.done, w.kcol,
+                     vs ? w.vscale + (size_t)(j + 1) * R : w.scale, w.active, c->stream);
+    if (!vs) {
+      if (a.wp == 0)
+        mwk::scale_cols_f64((double2*)a.Vp(w, j + 1), w.scale, E, R, c->stream);
+      else
+        mwk::scale_cols_f32((float2*)a.Vp(w, j + 1), w.scale, E, R, c->stream);
+    }
   });
 }
 constexpr int kStepSegments = 5;
@@ -504,6 +515,7 @@ void cycle_start(Ctx* c, const CycleArgs& a) {
     mwk::normalize_start_f64(w.r, w.rnorm, w.done, a.E, a.R, (double2*)a.Vp(w, 0), c->stream);
   else
     mwk::normalize_start32(w.r32, w.rnorm, w.done, a.E, a.R, (float2*)a.Vp(w, 0), c->stream);
+  if (a.lazy) mwk::fill_f64(w.vscale, a.R, 1.0, c->stream);   // V_0 is stored scaled
 }
 
 // Least squares, x += Z y, and the per-column step counts into w.h_ivec (not yet synchronised).
@@ -821,7 +833,7 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
   Work& w = c->work;
   cudaStream_t s = c->stream;
   CycleArgs a{f, R, m, wp, use_p, X, E, krylov_stride(E, R), wp == 0 ? sizeof(double2) : sizeof(float2),
-              tuned_for(c, R, wp, m, use_p)};
+              tuned_for(c, R, wp, m, use_p), use_p && c->prec.ready && c->prec.apply_prec == 2 && wp == 1};
 
   CK(cudaMemsetAsync(X, 0, sizeof(double2) * E * R, s));
   if (wp == 1) mwk::split_df(B, w.bdf, E * R, s);

@@ -141,13 +141,20 @@ constexpr int kMaxStepHandles = 8;
 void fill_pattern_f32(float* x, int64_t n, uint32_t seed, cudaStream_t s, double scale = 1.0);
 void fill_pattern_f64(double* x, int64_t n, uint32_t seed, cudaStream_t s, double scale = 1.0);
 void set_step_conditions(const unsigned long long* handles, int n, const int32_t* active, cudaStream_t s);
-void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s);
+// h[i][c] = sum_p part[p][i][c], times vscale[i][c] when given (basis kept unscaled).
+void reduce_h(const double2* part, int nparts, int nvec, int R, double2* h, cudaStream_t s,
+              const double* vscale = nullptr);
 // w -= sum_i h_i V_i and per-part, per-column |w|^2 into npart[part][R]; returns the part count.
-// err / stages as for cgs_dots (err null: the non-streaming kernel).
+// err / stages as for cgs_dots (err null: the non-streaming kernel).  With vscale the basis is
+// kept unscaled (V_i = vscale[i][c] Vu_i) and the coefficients become h_i * vscale_i.
 int cgs_update_f64(const double2* V, int64_t vstride, int nvec, const double2* h, double2* w, int64_t E, int R,
-                   double* npart, cudaStream_t s, int32_t* err = nullptr, int stages = 0);
+                   double* npart, cudaStream_t s, int32_t* err = nullptr, int stages = 0,
+                   const double* vscale = nullptr);
 int cgs_update_f32(const float2* V, int64_t vstride, int nvec, const double2* h, float2* w, int64_t E, int R,
-                   double* npart, cudaStream_t s, int32_t* err = nullptr, int stages = 0);
+                   double* npart, cudaStream_t s, int32_t* err = nullptr, int stages = 0,
+                   const double* vscale = nullptr);
+// x[0..n) = v.
+void fill_f64(double* x, int n, double v, cudaStream_t s);
 int colnorm2_f64(const double2* x, int64_t E, int R, double* npart, cudaStream_t s);
 // Givens step for Arnoldi column j; see k_krylov.cu for the state layout.
 void givens_step(const double2* h, const double* npart, int nparts, int j, int m, int R, double2* H,
