@@ -19,6 +19,7 @@
 // drains its outstanding copies (again bounded), frees tensor memory and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -124,39 +125,66 @@ __global__ void pack_w_kernel(const int64_t* __restrict__ nmat, const int64_t* _
 // ---------------------------------------------------------------------------------------
 // cscale (may be null): per-column factor of the input (a Krylov vector kept unscaled), applied
 // in FP32 before the BF16 rounding.
-__global__ void gather_b_kernel(const int32_t* __restrict__ gt_sub, const int32_t* __restrict__ gt_kt,
-                                const int64_t* __restrict__ dof_ptr, const int32_t* __restrict__ dofs,
-                                const float2* __restrict__ r, int R, int Rp, uint8_t* __restrict__ Bt,
-                                const double* __restrict__ cscale) {
-  // the tile is assembled in shared memory (4-byte swizzled stores) and written out with
-  // coalesced 16-byte stores
+__global__ void __launch_bounds__(128, 10) gather_b_kernel(const int32_t* __restrict__ gt_sub,
+                                                       const int32_t* __restrict__ gt_kt,
+                                                       const int64_t* __restrict__ dof_ptr,
+                                                       const int32_t* __restrict__ dofs,
+                                                       const float2* __restrict__ r, int R, int Rp,
+                                                       uint8_t* __restrict__ Bt, const double* __restrict__ cscale,
+                                                       int64_t ntiles) {
+  // Blocks of 4 warps walk the tiles with a grid stride.  Per tile, warp w takes dofs
+  // 8w .. 8w+7 and lane c the columns c, c + 32, ...: the 32 dof indices come in one coalesced
+  // load and are handed out by shuffles, the 8 values of a lane are independent loads, and each
+  // lane writes its rows 2c (re, -im) and 2c+1 (im, re) as four 16-byte swizzled chunks.  The
+  // tile is then copied out with coalesced 16-byte stores.
   extern __shared__ __align__(16) uint8_t tsm[];
-  const int64_t g = blockIdx.x;
-  const int s = gt_sub[g], kt = gt_kt[g];
-  const int64_t n = dof_ptr[s + 1] - dof_ptr[s];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = 2 * Rp;
-  uint8_t* tile = Bt + (size_t)g * N * 128;
-  const int32_t* dv = dofs + dof_ptr[s];
-  for (int idx = threadIdx.x; idx < kTileKc * Rp; idx += blockDim.x) {
-    const int kc = idx / Rp, c = idx % Rp;
-    const int64_t k = (int64_t)kt * kTileKc + kc;
-    float2 v = make_float2(0.f, 0.f);
-    if (k < n && c < R) {
-      v = r[(int64_t)dv[k] * R + c];
-      if (cscale) {
+  const int nq = (Rp + 31) / 32;
+  const int nvec16 = N * 128 / 16;
+  for (int64_t g = blockIdx.x; g < ntiles; g += gridDim.x) {
+    const int s = gt_sub[g], kt = gt_kt[g];
+    const int64_t d0 = dof_ptr[s];
+    const int64_t n = dof_ptr[s + 1] - d0;
+    const int64_t k0 = (int64_t)kt * kTileKc + 8 * warp;
+    const int idx = (lane < 8 && k0 + lane < n) ? dofs[d0 + k0 + lane] : -1;
+    for (int q = 0; q < nq; ++q) {
+      const int c = lane + 32 * q;
+      float2 v[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int e = __shfl_sync(0xffffffffu, idx, jj);
+        v[jj] = (e >= 0 && c < R) ? r[(int64_t)e * R + c] : make_float2(0.f, 0.f);
+      }
+      if (c < R && cscale) {
         const float sc = (float)cscale[c];
-        v.x *= sc;
-        v.y *= sc;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          v[jj].x *= sc;
+          v[jj].y *= sc;
+        }
+      }
+      if (c < Rp) {
+        uint4 a0, a1, b0, b1;
+        a0.x = pack_bf16(v[0].x, -v[0].y); a0.y = pack_bf16(v[1].x, -v[1].y);
+        a0.z = pack_bf16(v[2].x, -v[2].y); a0.w = pack_bf16(v[3].x, -v[3].y);
+        a1.x = pack_bf16(v[4].x, -v[4].y); a1.y = pack_bf16(v[5].x, -v[5].y);
+        a1.z = pack_bf16(v[6].x, -v[6].y); a1.w = pack_bf16(v[7].x, -v[7].y);
+        b0.x = pack_bf16(v[0].y, v[0].x); b0.y = pack_bf16(v[1].y, v[1].x);
+        b0.z = pack_bf16(v[2].y, v[2].x); b0.w = pack_bf16(v[3].y, v[3].x);
+        b1.x = pack_bf16(v[4].y, v[4].x); b1.y = pack_bf16(v[5].y, v[5].x);
+        b1.z = pack_bf16(v[6].y, v[6].x); b1.w = pack_bf16(v[7].y, v[7].x);
+        *reinterpret_cast<uint4*>(tsm + swz(2 * c, 16 * warp)) = a0;
+        *reinterpret_cast<uint4*>(tsm + swz(2 * c, 16 * warp + 8)) = a1;
+        *reinterpret_cast<uint4*>(tsm + swz(2 * c + 1, 16 * warp)) = b0;
+        *reinterpret_cast<uint4*>(tsm + swz(2 * c + 1, 16 * warp + 8)) = b1;
       }
     }
-    const uint32_t n0 = 2 * c, n1 = 2 * c + 1;
-    *reinterpret_cast<uint32_t*>(tsm + swz(n0, 2 * kc)) = pack_bf16(v.x, -v.y);
-    *reinterpret_cast<uint32_t*>(tsm + swz(n1, 2 * kc)) = pack_bf16(v.y, v.x);
+    __syncthreads();
+    uint4* tile = reinterpret_cast<uint4*>(Bt + (size_t)g * N * 128);
+    for (int i = threadIdx.x; i < nvec16; i += blockDim.x) tile[i] = reinterpret_cast<const uint4*>(tsm)[i];
+    __syncthreads();
   }
-  __syncthreads();
-  const int nvec16 = N * 128 / 16;
-  for (int i = threadIdx.x; i < nvec16; i += blockDim.x)
-    reinterpret_cast<uint4*>(tile)[i] = reinterpret_cast<const uint4*>(tsm)[i];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -432,8 +460,9 @@ void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const flo
     cudaFuncSetAttribute(gather_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
     gattr = gsm;
   }
-  gather_b_kernel<<<(unsigned)p.n_ktiles_total, 256, gsm, s>>>(p.gt_sub, p.gt_kt, tp.dof_ptr, tp.dofs, r, R, Rp,
-                                                               (uint8_t*)scratch, in_scale);
+  const int64_t gblocks = std::min<int64_t>(p.n_ktiles_total, 152 * 10);   // one resident wave
+  gather_b_kernel<<<(unsigned)std::max<int64_t>(gblocks, 1), 128, gsm, s>>>(
+      p.gt_sub, p.gt_kt, tp.dof_ptr, tp.dofs, r, R, Rp, (uint8_t*)scratch, in_scale, p.n_ktiles_total);
   TcArgs a;
   a.mt_sub = p.mt_sub;
   a.mt_row0 = p.mt_row0;
