@@ -145,8 +145,10 @@ def oras_traffic_ratio():
         if i < 0:
             return ""
         return text[i:text.index("\n}\n", i) + 3]
-    h = hashlib.sha256((body("__global__ void gather_b_kernel")
-                        + body("__global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel")).encode()).hexdigest()
+    gather, mma = body("gather_b_kernel("), body("__global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel")
+    if not gather or not mma:
+        return None
+    h = hashlib.sha256((gather + mma).encode()).hexdigest()
     if kv.get("kernel_source_sha256", "").strip() != h:
         return None
     return float(kv["traffic_per_algorithmic_byte"])

@@ -2,16 +2,19 @@
 // tcgen05 MMAs with the accumulator in tensor memory (Sec. IV-C: the subdomain solves of the
 // one-level ORAS preconditioner, applied through precomputed owned-row inverses).
 //
-// Complex product as one real GEMM.  With W = Wr + i Wi stored interleaved along K
-// (A'[m][2k] = Wr[m][k], A'[m][2k+1] = Wi[m][k]) and the gathered input g = gr + i gi written as
-//   B'[2k][2r] = gr,  B'[2k+1][2r] = -gi,  B'[2k][2r+1] = gi,  B'[2k+1][2r+1] = gr,
-// D = A' B' holds Re z in column 2r and Im z in column 2r+1: the interleaved complex output.
+// Complex product as two real GEMMs on split planes.  W = Wr + i Wi is stored as two BF16 planes
+// and the gathered input g = gr + i gi once, as B = [gr | gi] (N = 2 R_pad columns: column c
+// holds gr_c, column R_pad + c holds gi_c).  Two accumulators D1 = Wr B and D2 = Wi B give
+//   Re z_c = D1[c] - D2[R_pad + c],   Im z_c = D1[R_pad + c] + D2[c].
+// Each complex input value is staged once (2 BF16), half the bytes of an interleaved real-GEMM
+// form that needs (gr, -gi) and (gi, gr); the FLOPs and the W bytes are the same.
 //
-// Layouts.  Both operands are K-major with the 128-byte swizzle: a tile row holds 64 BF16 of K
-// (128 B); the 16-byte chunk c of row r sits at chunk c ^ (r % 8); 8-row groups are 1024 B
-// apart.  W_s is pre-tiled at setup into 128-row x 64-K tiles (16 KB each, contiguous, in that
-// swizzled order), so one bulk copy moves a tile into shared memory without a tensor map.  The
-// gathered operand of each subdomain is written per apply into N x 64-K tiles (N = 2 R_pad).
+// Layouts.  All operands are K-major with the 128-byte swizzle: a tile row holds 64 BF16 of K
+// (128 B, K = 64 subdomain dofs); the 16-byte chunk c of row r sits at chunk c ^ (r % 8); 8-row
+// groups are 1024 B apart.  W_s is pre-tiled at setup into 128-row x 64-dof tile pairs (Wr tile,
+// then Wi tile: 32 KB contiguous, in that swizzled order), so one bulk copy moves a pair into
+// shared memory without a tensor map.  The gathered operand of each subdomain is written per
+// apply into N x 64-dof tiles.
 //
 // Kernel roles (192 threads): warp 0 lane 0 issues the bulk copies, warp 1 allocates tensor
 // memory and lane 0 issues the MMAs, warps 2-5 read the accumulator (tcgen05.ld) and scatter
@@ -33,7 +36,7 @@ namespace mwk {
 namespace {
 
 constexpr int kTileM = 128;
-constexpr int kTileKc = 32;                  // complex K per tile (64 real)
+constexpr int kTileKd = 64;                  // subdomain dofs (complex K) per tile
 constexpr int kATileBytes = kTileM * 128;    // 16 KB
 constexpr int kThreadsTc = 192;
 // tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
@@ -66,16 +69,14 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Byte offset of (row, k) in a K-major, 128-byte-swizzled tile with 64 BF16 per row.
@@ -89,8 +90,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Setup: owned rows of B_s^{-1} (FP32 or FP64 workspace) -> swizzled BF16 tiles.
-// One block per (subdomain of the batch, m tile, k tile); one 32-bit word (re, im) per entry.
+// Setup: owned rows of B_s^{-1} (FP32 or FP64 workspace) -> swizzled BF16 tile pairs (Wr, Wi).
+// One block per (subdomain of the batch, m tile, k tile); one 32-bit word per two dofs and plane.
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __global__ void pack_w_kernel(const int64_t* __restrict__ nmat, const int64_t* __restrict__ off,
@@ -106,17 +107,26 @@ __global__ void pack_w_kernel(const int64_t* __restrict__ nmat, const int64_t* _
   const int KT = sub_kt[s];
   if (kt >= KT || (int64_t)mt * kTileM >= nown) return;
   const T* A = ws + off[b];
-  uint8_t* tile = W + ((size_t)sub_wtile[s] + (size_t)mt * KT + kt) * kATileBytes;
-  for (int w = threadIdx.x; w < kTileM * kTileKc; w += blockDim.x) {
-    const int r = w / kTileKc, kc = w % kTileKc;
-    const int64_t q = (int64_t)mt * kTileM + r, k = (int64_t)kt * kTileKc + kc;
-    float re = 0.f, im = 0.f;
-    if (q < nown && k < n) {
-      const T v = A[(int64_t)own_local[own_ptr[s] + q] * n + k];
-      re = (float)v.x;
-      im = (float)v.y;
+  uint8_t* tr = W + ((size_t)sub_wtile[s] + ((size_t)mt * KT + kt) * 2) * kATileBytes;
+  uint8_t* ti = tr + kATileBytes;
+  constexpr int kPairs = kTileKd / 2;
+  for (int w = threadIdx.x; w < kTileM * kPairs; w += blockDim.x) {
+    const int r = w / kPairs, kp = w % kPairs;
+    const int64_t q = (int64_t)mt * kTileM + r, k = (int64_t)kt * kTileKd + 2 * kp;
+    float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
+    if (q < nown) {
+      const T* row = A + (int64_t)own_local[own_ptr[s] + q] * n;
+      if (k < n) {
+        re0 = (float)row[k].x;
+        im0 = (float)row[k].y;
+      }
+      if (k + 1 < n) {
+        re1 = (float)row[k + 1].x;
+        im1 = (float)row[k + 1].y;
+      }
     }
-    *reinterpret_cast<uint32_t*>(tile + swz(r, 2 * kc)) = pack_bf16(re, im);
+    *reinterpret_cast<uint32_t*>(tr + swz(r, 2 * kp)) = pack_bf16(re0, re1);
+    *reinterpret_cast<uint32_t*>(ti + swz(r, 2 * kp)) = pack_bf16(im0, im1);
   }
 }
 
@@ -125,17 +135,17 @@ __global__ void pack_w_kernel(const int64_t* __restrict__ nmat, const int64_t* _
 // ---------------------------------------------------------------------------------------
 // cscale (may be null): per-column factor of the input (a Krylov vector kept unscaled), applied
 // in FP32 before the BF16 rounding.
-__global__ void __launch_bounds__(128, 10) gather_b_kernel(const int32_t* __restrict__ gt_sub,
+__global__ void __launch_bounds__(128, 8) gather_b_kernel(const int32_t* __restrict__ gt_sub,
                                                        const int32_t* __restrict__ gt_kt,
                                                        const int64_t* __restrict__ dof_ptr,
                                                        const int32_t* __restrict__ dofs,
                                                        const float2* __restrict__ r, int R, int Rp,
                                                        uint8_t* __restrict__ Bt, const double* __restrict__ cscale,
                                                        int64_t ntiles) {
-  // Blocks of 4 warps walk the tiles with a grid stride.  Per tile, warp w takes dofs
-  // 8w .. 8w+7 and lane c the columns c, c + 32, ...: the 32 dof indices come in one coalesced
-  // load and are handed out by shuffles, the 8 values of a lane are independent loads, and each
-  // lane writes its rows 2c (re, -im) and 2c+1 (im, re) as four 16-byte swizzled chunks.  The
+  // Blocks of 4 warps walk the tiles with a grid stride.  Per tile (64 dofs), warp w takes dofs
+  // 16w .. 16w+15 and lane c the columns c, c + 32, ...: the dof indices come in one coalesced
+  // load and are handed out by shuffles, the 16 values of a lane are independent loads, and each
+  // lane writes its rows c (gr) and R_pad + c (gi) as two 16-byte swizzled chunks each.  The
   // tile is then copied out with coalesced 16-byte stores.
   extern __shared__ __align__(16) uint8_t tsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -146,38 +156,38 @@ __global__ void __launch_bounds__(128, 10) gather_b_kernel(const int32_t* __rest
     const int s = gt_sub[g], kt = gt_kt[g];
     const int64_t d0 = dof_ptr[s];
     const int64_t n = dof_ptr[s + 1] - d0;
-    const int64_t k0 = (int64_t)kt * kTileKc + 8 * warp;
-    const int idx = (lane < 8 && k0 + lane < n) ? dofs[d0 + k0 + lane] : -1;
+    const int64_t k0 = (int64_t)kt * kTileKd + 16 * warp;
+    const int idx = (lane < 16 && k0 + lane < n) ? dofs[d0 + k0 + lane] : -1;
     for (int q = 0; q < nq; ++q) {
       const int c = lane + 32 * q;
-      float2 v[8];
+      float2 v[16];
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
+      for (int jj = 0; jj < 16; ++jj) {
         const int e = __shfl_sync(0xffffffffu, idx, jj);
         v[jj] = (e >= 0 && c < R) ? r[(int64_t)e * R + c] : make_float2(0.f, 0.f);
       }
       if (c < R && cscale) {
         const float sc = (float)cscale[c];
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
+        for (int jj = 0; jj < 16; ++jj) {
           v[jj].x *= sc;
           v[jj].y *= sc;
         }
       }
       if (c < Rp) {
-        uint4 a0, a1, b0, b1;
-        a0.x = pack_bf16(v[0].x, -v[0].y); a0.y = pack_bf16(v[1].x, -v[1].y);
-        a0.z = pack_bf16(v[2].x, -v[2].y); a0.w = pack_bf16(v[3].x, -v[3].y);
-        a1.x = pack_bf16(v[4].x, -v[4].y); a1.y = pack_bf16(v[5].x, -v[5].y);
-        a1.z = pack_bf16(v[6].x, -v[6].y); a1.w = pack_bf16(v[7].x, -v[7].y);
-        b0.x = pack_bf16(v[0].y, v[0].x); b0.y = pack_bf16(v[1].y, v[1].x);
-        b0.z = pack_bf16(v[2].y, v[2].x); b0.w = pack_bf16(v[3].y, v[3].x);
-        b1.x = pack_bf16(v[4].y, v[4].x); b1.y = pack_bf16(v[5].y, v[5].x);
-        b1.z = pack_bf16(v[6].y, v[6].x); b1.w = pack_bf16(v[7].y, v[7].x);
-        *reinterpret_cast<uint4*>(tsm + swz(2 * c, 16 * warp)) = a0;
-        *reinterpret_cast<uint4*>(tsm + swz(2 * c, 16 * warp + 8)) = a1;
-        *reinterpret_cast<uint4*>(tsm + swz(2 * c + 1, 16 * warp)) = b0;
-        *reinterpret_cast<uint4*>(tsm + swz(2 * c + 1, 16 * warp + 8)) = b1;
+        uint4 re0, re1, im0, im1;
+        re0.x = pack_bf16(v[0].x, v[1].x);    re0.y = pack_bf16(v[2].x, v[3].x);
+        re0.z = pack_bf16(v[4].x, v[5].x);    re0.w = pack_bf16(v[6].x, v[7].x);
+        re1.x = pack_bf16(v[8].x, v[9].x);    re1.y = pack_bf16(v[10].x, v[11].x);
+        re1.z = pack_bf16(v[12].x, v[13].x);  re1.w = pack_bf16(v[14].x, v[15].x);
+        im0.x = pack_bf16(v[0].y, v[1].y);    im0.y = pack_bf16(v[2].y, v[3].y);
+        im0.z = pack_bf16(v[4].y, v[5].y);    im0.w = pack_bf16(v[6].y, v[7].y);
+        im1.x = pack_bf16(v[8].y, v[9].y);    im1.y = pack_bf16(v[10].y, v[11].y);
+        im1.z = pack_bf16(v[12].y, v[13].y);  im1.w = pack_bf16(v[14].y, v[15].y);
+        *reinterpret_cast<uint4*>(tsm + swz(c, 16 * warp)) = re0;
+        *reinterpret_cast<uint4*>(tsm + swz(c, 16 * warp + 8)) = re1;
+        *reinterpret_cast<uint4*>(tsm + swz(Rp + c, 16 * warp)) = im0;
+        *reinterpret_cast<uint4*>(tsm + swz(Rp + c, 16 * warp + 8)) = im1;
       }
     }
     __syncthreads();
@@ -221,8 +231,9 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
   const int KT = a.sub_kt[s];
   const int S = a.stages;
   const uint32_t b_bytes = (uint32_t)a.N * 128u;
-  const uint32_t stage_bytes = kATileBytes + b_bytes;
-  const uint8_t* Wt = a.W + ((size_t)a.sub_wtile[s] + (size_t)(row0 / kTileM) * KT) * kATileBytes;
+  const uint32_t a_bytes = 2u * kATileBytes;          // Wr and Wi tiles of one k tile
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  const uint8_t* Wt = a.W + ((size_t)a.sub_wtile[s] + (size_t)(row0 / kTileM) * KT * 2) * kATileBytes;
   const uint8_t* Bs = a.Bt + (size_t)a.sub_gtile[s] * b_bytes;
 
   if (threadIdx.x == 0) {
@@ -247,7 +258,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: bulk copies of (W tile, B' tile) per k tile
+      // producer: bulk copies of (Wr and Wi tiles, B tile) per k tile
       int issued = 0;
       for (int kt = 0; kt < KT; ++kt) {
         const int st = kt % S;
@@ -260,9 +271,9 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
         }
         if (*(volatile int*)&abort_flag) break;
         uint8_t* sa = base + (size_t)st * stage_bytes;
-        uint8_t* sb = sa + kATileBytes;
+        uint8_t* sb = sa + a_bytes;
         mbar_expect_tx(&full_bar[st], stage_bytes);
-        bulk_g2s(sa, Wt + (size_t)kt * kATileBytes, kATileBytes, &full_bar[st]);
+        bulk_g2s(sa, Wt + (size_t)kt * a_bytes, a_bytes, &full_bar[st]);
         bulk_g2s(sb, Bs + (size_t)kt * b_bytes, b_bytes, &full_bar[st]);
         ++issued;
       }
@@ -282,11 +293,15 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sa = smem_u32(base + (size_t)st * stage_bytes);
-        const uint32_t sb = sa + kATileBytes;
+        const uint32_t sar = smem_u32(base + (size_t)st * stage_bytes);
+        const uint32_t sai = sar + kATileBytes;
+        const uint32_t sb = sar + a_bytes;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          mma_bf16(tmem, smem_desc(sa + 32u * k), smem_desc(sb + 32u * k), idesc, (kt > 0 || k > 0) ? 1u : 0u);
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
+          mma_bf16(tmem, smem_desc(sar + 32u * k), smem_desc(sb + 32u * k), idesc, acc);               // D1 = Wr B
+          mma_bf16(tmem + (uint32_t)a.N, smem_desc(sai + 32u * k), smem_desc(sb + 32u * k), idesc, acc);  // D2 = Wi B
+        }
         mma_commit(&empty_bar[st]);
       }
       mma_commit(&done_bar);
@@ -303,16 +318,22 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
     const int64_t q = (int64_t)row0 + row;
     const bool valid = ok && !abort_flag && q < nown;
     float2* zr = valid ? a.z + (int64_t)a.own_glob[a.own_ptr[s] + q] * a.R : nullptr;
-    for (int c0 = 0; c0 < a.N; c0 += 16) {
-      float v[16];
+    const int Rp = a.N / 2;
+    const uint32_t lanes = tmem + ((uint32_t)(quad * 32) << 16);
+    for (int c0 = 0; c0 < Rp; c0 += 8) {
+      // Re z = D1[c] - D2[Rp + c], Im z = D1[Rp + c] + D2[c]
+      float rr[8], ri[8], ir[8], ii[8];
       if (ok) {
-        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld8(lanes + (uint32_t)c0, rr);                          // Wr gr
+        tmem_ld8(lanes + (uint32_t)(Rp + c0), ri);                   // Wr gi
+        tmem_ld8(lanes + (uint32_t)(a.N + c0), ir);                  // Wi gr
+        tmem_ld8(lanes + (uint32_t)(a.N + Rp + c0), ii);             // Wi gi
       }
       if (valid) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int col = c0 / 2 + i;
-          if (col < a.R) zr[col] = make_float2(v[2 * i], v[2 * i + 1]);
+          const int col = c0 + i;
+          if (col < a.R) zr[col] = make_float2(rr[i] - ii[i], ri[i] + ir[i]);
         }
       }
     }
@@ -350,7 +371,7 @@ bool tc_plan_build(TcPlan& p, const mw::Subdomains& sd, const std::function<void
   for (int q = 0; q < ns; ++q) {
     const int64_t n = sd.dof_ptr[q + 1] - sd.dof_ptr[q];
     const int64_t no = sd.own_ptr[q + 1] - sd.own_ptr[q];
-    const int KT = (int)((n + kTileKc - 1) / kTileKc);
+    const int KT = (int)((n + kTileKd - 1) / kTileKd);
     const int MT = (int)((no + kTileM - 1) / kTileM);
     sub_kt[q] = KT;
     sub_wtile[q] = wt;
@@ -363,7 +384,7 @@ bool tc_plan_build(TcPlan& p, const mw::Subdomains& sd, const std::function<void
       gt_sub.push_back(q);
       gt_kt.push_back(k);
     }
-    wt += (int64_t)MT * KT;
+    wt += (int64_t)MT * KT * 2;   // Wr and Wi tile per (m tile, k tile)
     gtile += KT;
   }
   p.n_sub = ns;
@@ -413,7 +434,7 @@ void tc_extract(const TcPlan& p, const OrasBatch& bt, const OrasTopo& tp, int ws
                 cudaStream_t s) {
   note_launch(1);
   // grid: k tiles x m tiles of the largest subdomain in the batch x batch
-  const int ktmax = (int)((bt.nmax + kTileKc - 1) / kTileKc);
+  const int ktmax = (int)((bt.nmax + kTileKd - 1) / kTileKd);
   const int mtmax = (int)((bt.nmax + kTileM - 1) / kTileM);
   dim3 grid(ktmax, mtmax, bt.count);
   if (ws_prec == 0)
@@ -429,12 +450,12 @@ size_t tc_smem_bytes(int N, int stages);
 
 int tc_stages(int N) {
   // about 100 KB of stages per CTA so that two CTAs share an SM
-  const int stage = kATileBytes + N * 128;
+  const int stage = 2 * kATileBytes + N * 128;
   int st = (100 * 1024) / stage;
   return st > 6 ? 6 : (st < 2 ? 2 : st);
 }
 
-size_t tc_smem_bytes(int N, int stages) { return (size_t)stages * (kATileBytes + N * 128) + 1024; }
+size_t tc_smem_bytes(int N, int stages) { return (size_t)stages * (2 * kATileBytes + N * 128) + 1024; }
 
 int tc_default_stages(int R) { return tc_stages(2 * rpad(R)); }
 
@@ -460,7 +481,7 @@ void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const flo
     cudaFuncSetAttribute(gather_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
     gattr = gsm;
   }
-  const int64_t gblocks = std::min<int64_t>(p.n_ktiles_total, 152 * 10);   // one resident wave
+  const int64_t gblocks = std::min<int64_t>(p.n_ktiles_total, 152 * 8);    // one resident wave
   gather_b_kernel<<<(unsigned)std::max<int64_t>(gblocks, 1), 128, gsm, s>>>(
       p.gt_sub, p.gt_kt, tp.dof_ptr, tp.dofs, r, R, Rp, (uint8_t*)scratch, in_scale, p.n_ktiles_total);
   TcArgs a;
@@ -478,10 +499,13 @@ void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const flo
   a.N = N;
   a.stages = stages;
   uint32_t cols = 32;
-  while ((int)cols < N) cols <<= 1;
+  while ((int)cols < 2 * N) cols <<= 1;   // two accumulators of N columns
   a.tmem_cols = cols;
   a.err = p.err;
-  const size_t smem = tc_smem_bytes(N, stages);
+  // two CTAs of an SM must fit their tensor memory (512 columns per SM): above 256 columns the
+  // shared-memory request keeps one CTA per SM
+  size_t smem = tc_smem_bytes(N, stages);
+  if (cols > 256 && smem < (size_t)120 * 1024) smem = (size_t)120 * 1024;
   static size_t attr = 0;
   if (smem > attr) {
     cudaFuncSetAttribute(oras_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
