@@ -185,13 +185,16 @@ template <typename T>
 __host__ __device__ constexpr int bd_rows() {
   return 64 / (int)sizeof(T);   // 8 rows (FP32 complex), 4 rows (FP64 complex)
 }
+constexpr int kBdGroup = 4;     // basis vectors whose partials share one named barrier
+// partial buffer: 2 (double buffer) x kBdGroup x 256 entries of the vector type
+__host__ __device__ inline size_t bd_red_bytes(size_t es) { return 2 * kBdGroup * kBdConsumers * es; }
 // VG * R <= 2048 accumulators of 16 bytes
-inline size_t bd_smem_bytes(int R, int NS) {
+inline size_t bd_smem_bytes(int R, int NS, size_t es) {
   const int VG = std::min(64, 2048 / R);
-  return (size_t)NS * kBdStageBytes + 2 * kBdConsumers * sizeof(double2) + (size_t)VG * R * sizeof(double2) +
+  return (size_t)NS * kBdStageBytes + bd_red_bytes(es) + (size_t)VG * R * sizeof(double2) +
          2 * NS * sizeof(uint64_t) + 16;
 }
-constexpr size_t kBdMaxSmem = (size_t)kBdMaxStages * kBdStageBytes + 2 * kBdConsumers * sizeof(double2) +
+constexpr size_t kBdMaxSmem = (size_t)kBdMaxStages * kBdStageBytes + 2 * kBdGroup * kBdConsumers * sizeof(double2) +
                               2048 * sizeof(double2) + 2 * kBdMaxStages * sizeof(uint64_t) + 16;
 
 template <typename T>
@@ -203,9 +206,8 @@ __global__ void __launch_bounds__(kBdThreads, 2)
   constexpr int kStageElems = kBdStageBytes / (int)sizeof(T);
   extern __shared__ __align__(128) uint8_t bd_smem[];
   T* stage = reinterpret_cast<T*>(bd_smem);
-  T* red = reinterpret_cast<T*>(bd_smem + (size_t)NS * kBdStageBytes);
-  double2* acc = reinterpret_cast<double2*>(bd_smem + (size_t)NS * kBdStageBytes +
-                                            2 * kBdConsumers * sizeof(double2));
+  T* red = reinterpret_cast<T*>(bd_smem + (size_t)NS * kBdStageBytes);   // [2][kBdGroup][256]
+  double2* acc = reinterpret_cast<double2*>(bd_smem + (size_t)NS * kBdStageBytes + bd_red_bytes(sizeof(T)));
   uint64_t* full = reinterpret_cast<uint64_t*>(acc + (size_t)VG * R);
   uint64_t* empty = full + NS;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NS);
@@ -316,42 +318,50 @@ __global__ void __launch_bounds__(kBdThreads, 2)
         mbar_arrive(&empty[st]);
         advance();
       }
-      for (int q = 0, qg = 0; q < nv; ++q, qg = (qg + 1 == G ? 0 : qg + 1)) {
-        wait_full();
-        const T* sm = stage + (size_t)st * kStageElems;
-        const T* gl = V + (int64_t)(i0 + q) * vstride + r0 * R;
-        Sc pr = 0, pi = 0;
+      // partials of up to kBdGroup consecutive vectors, then one barrier and their reductions
+      for (int q0 = 0, qg0 = 0; q0 < nv; q0 += kBdGroup) {
+        const int ng = min(kBdGroup, nv - q0);
+        T* rb = red + (size_t)(nred & 1) * kBdGroup * kBdConsumers;
+        for (int u = 0; u < ng; ++u) {
+          wait_full();
+          const T* sm = stage + (size_t)st * kStageElems;
+          const T* gl = V + (int64_t)(i0 + q0 + u) * vstride + r0 * R;
+          Sc pr = 0, pi = 0;
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-          const int row = k * G + g;
-          const int f = row * R + c;
-          if (act && row < rows) {
-            const T v = f < ncop ? sm[f] : gl[f];
-            pr = fma(v.x, wr[k].x, pr);
-            pr = fma(v.y, wr[k].y, pr);
-            pi = fma(v.x, wr[k].y, pi);
-            pi = fma(-v.y, wr[k].x, pi);
+          for (int k = 0; k < RPT; ++k) {
+            const int row = k * G + g;
+            const int f = row * R + c;
+            if (act && row < rows) {
+              const T v = f < ncop ? sm[f] : gl[f];
+              pr = fma(v.x, wr[k].x, pr);
+              pr = fma(v.y, wr[k].y, pr);
+              pi = fma(v.x, wr[k].y, pi);
+              pi = fma(-v.y, wr[k].x, pi);
+            }
           }
+          mbar_arrive(&empty[st]);
+          advance();
+          rb[u * kBdConsumers + ct] = T{pr, pi};
         }
-        mbar_arrive(&empty[st]);
-        advance();
-        T* rb = red + (nred & 1) * kBdConsumers;
-        rb[ct] = T{pr, pi};
         ++nred;
         asm volatile("bar.sync 1, %0;" ::"n"(kBdConsumers) : "memory");
-        if (act && g == qg) {
-          Sc sr = 0, si = 0;
+        for (int u = 0, qg = qg0; u < ng; ++u, qg = (qg + 1 == G ? 0 : qg + 1)) {
+          if (act && g == qg) {
+            const T* ru = rb + u * kBdConsumers;
+            Sc sr = 0, si = 0;
 #pragma unroll 8
-          for (int g2 = 0; g2 < G; ++g2) {
-            const T v = rb[g2 * R + c];
-            sr += v.x;
-            si += v.y;
+            for (int g2 = 0; g2 < G; ++g2) {
+              const T v = ru[g2 * R + c];
+              sr += v.x;
+              si += v.y;
+            }
+            double2 a = acc[(q0 + u) * R + c];
+            a.x += (double)sr;
+            a.y += (double)si;
+            acc[(q0 + u) * R + c] = a;
           }
-          double2 a = acc[q * R + c];
-          a.x += (double)sr;
-          a.y += (double)si;
-          acc[q * R + c] = a;
         }
+        qg0 = (qg0 + ng) % G;
       }
     }
     if (act)
@@ -1037,7 +1047,7 @@ int dots_launch(const T* V, int64_t vstride, int nvec, const T* w, int64_t E, in
     const int nb = 152 * 2;
     const int NS = stages >= 2 && stages <= kBdMaxStages ? stages : kBdStages;
     cgs_dots_bulk_kernel<T>
-        <<<nb, kBdThreads, bd_smem_bytes(R, NS), s>>>(V, vstride, nvec, w, E, R, G, VG, NS, part, err);
+        <<<nb, kBdThreads, bd_smem_bytes(R, NS, sizeof(T)), s>>>(V, vstride, nvec, w, E, R, G, VG, NS, part, err);
     return nb;
   }
   Shape sh = shape_for(R);
