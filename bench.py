@@ -133,7 +133,7 @@ def oras_traffic_ratio():
     """DRAM traffic per algorithmic byte of the ORAS apply from the committed ncu summary, or
     None when the two kernels' source no longer matches the one the counters were taken on."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "oras_apply_traffic_shoulder32x32x14.md")
+    prof = os.path.join(ROOT, "profiles", "oras_apply_traffic_shoulder80x80x34.md")
     src = os.path.join(ROOT, "paper_2311_05322_gb300", "csrc", "k_oras_tc.cu")
     if not (os.path.exists(prof) and os.path.exists(src)):
         return None
@@ -379,7 +379,8 @@ def run_mine(a):
     traffic = ratio * d["bytes"] / max(d["launches"], 1) if ratio else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_source": src, "traffic": traffic,
-            "traffic_note": "scaled from profiles/oras_apply_traffic_shoulder32x32x14.md" if traffic else None,
+            "traffic_note": ("DRAM bytes per algorithmic byte from profiles/oras_apply_traffic_shoulder80x80x34.md "
+                             "(ncu, one pass, this workload)") if traffic else None,
             "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
             "avg_launch_ms": d["ms"] / max(d["launches"], 1),
             "share_of_step": d["ms"] / ms,

@@ -258,7 +258,12 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: bulk copies of (Wr and Wi tiles, B tile) per k tile
+      // producer: bulk copies of (Wr and Wi tiles, B tile) per k tile.  In the last m tile of a
+      // subdomain only the 8-row swizzle groups that hold owned rows are copied: the other rows
+      // of A feed only accumulator rows that the epilogue does not store.
+      const int64_t nown_p = a.own_ptr[s + 1] - a.own_ptr[s];
+      const int rows_valid = (int)min((int64_t)kTileM, nown_p - (int64_t)row0);
+      const uint32_t a_part = (uint32_t)((rows_valid + 7) / 8) * 1024u;
       int issued = 0;
       for (int kt = 0; kt < KT; ++kt) {
         const int st = kt % S;
@@ -272,8 +277,9 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
         if (*(volatile int*)&abort_flag) break;
         uint8_t* sa = base + (size_t)st * stage_bytes;
         uint8_t* sb = sa + a_bytes;
-        mbar_expect_tx(&full_bar[st], stage_bytes);
-        bulk_g2s(sa, Wt + (size_t)kt * a_bytes, a_bytes, &full_bar[st]);
+        mbar_expect_tx(&full_bar[st], 2u * a_part + b_bytes);
+        bulk_g2s(sa, Wt + (size_t)kt * a_bytes, a_part, &full_bar[st]);
+        bulk_g2s(sa + kATileBytes, Wt + (size_t)kt * a_bytes + kATileBytes, a_part, &full_bar[st]);
         bulk_g2s(sb, Bs + (size_t)kt * b_bytes, b_bytes, &full_bar[st]);
         ++issued;
       }
