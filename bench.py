@@ -309,15 +309,16 @@ def run_mine(a):
     eps_h = torch.from_numpy(eps0).pin_memory().numpy()
     So_h = torch.from_numpy(S_obs).pin_memory().numpy()
     Se_h = torch.from_numpy(S_empty).pin_memory().numpy()
+    g_h = torch.empty((healthy.mesh.n_tet, 2), dtype=torch.float64).pin_memory().numpy()   # the step's result
     c.assemble(freqs, eps_h, healthy.eps_bg)
-    c.gradient(So_h, Se_h, a.alpha, opts)
+    c.gradient(So_h, Se_h, a.alpha, opts, out=g_h)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     t = time.perf_counter()
     for _ in range(a.steps):
         c.assemble(freqs, eps_h, healthy.eps_bg)
-        Jh, gh = c.gradient(So_h, Se_h, a.alpha, opts)
+        Jh, gh = c.gradient(So_h, Se_h, a.alpha, opts, out=g_h)
     torch.cuda.synchronize()
     e2e_value, e2e_s = aggregate(units * a.steps, time.perf_counter() - t, world, dist if world > 1 else None)
     T = healthy.mesh.n_tet

@@ -183,7 +183,6 @@ struct Ctx {
   int n_freq = 0;
   std::vector<double> freqs;
   double eps_bg[2] = {0, 0};
-  std::vector<double> eps;
   double* d_eps = nullptr;
   std::vector<double2*> A64;
   std::vector<float2*> A32;
@@ -290,6 +289,10 @@ mw_status guard(Ctx* c, F&& f) {
 
 void require(bool cond, mw_status code, const std::string& msg) {
   if (!cond) throw Fail{code, msg};
+}
+// Literal messages build a string only on failure (per-element checks of large inputs).
+void require(bool cond, mw_status code, const char* msg) {
+  if (!cond) throw Fail{code, std::string(msg)};
 }
 
 double k0_of(double f) { return 2.0 * mw::kPi * f / mw::kC0; }
@@ -1319,7 +1322,6 @@ mw_status mw_assemble(mw_ctx* c, int32_t n_freq, const double* freq_hz, const do
     c->freqs.assign(freq_hz, freq_hz + n_freq);
     c->eps_bg[0] = eps_bg[0];
     c->eps_bg[1] = eps_bg[1];
-    c->eps.assign(eps_r, eps_r + 2 * T);
     if (!c->d_eps) c->d_eps = dalloc<double>(c, 2 * T);
     CK(cudaMemcpyAsync(c->d_eps, eps_r, sizeof(double) * 2 * T, cudaMemcpyHostToDevice, c->stream));
     // i k0 sqrt(eps_bg): principal square root

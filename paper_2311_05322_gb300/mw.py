@@ -327,12 +327,20 @@ class Context:
                 "arnoldi_steps": st.arnoldi_steps, "iters": its, "relres": rel, "status": code}
 
     # -- cost, gradient, inversion -----------------------------------------------------------
-    def gradient(self, S_obs, S_empty, alpha: float = 0.0, opts: mw_solve_opts | None = None, want_S=False):
+    def gradient(self, S_obs, S_empty, alpha: float = 0.0, opts: mw_solve_opts | None = None, want_S=False,
+                 out: np.ndarray | None = None):
+        """J and dJ/d(Re eps, Im eps) [T, 2]; `out` (float64 [T, 2], C order, e.g. pinned host
+        memory) receives the gradient instead of a new array."""
         o = opts or solve_opts()
         So = _c(S_obs, np.complex128)
         Se = _c(S_empty, np.complex128)
         J = C.c_double()
-        g = np.empty((self.info.n_tet, 2))
+        if out is not None:
+            if out.dtype != np.float64 or out.shape != (self.info.n_tet, 2) or not out.flags.c_contiguous:
+                raise ValueError("out must be a C-contiguous float64 array of shape [n_tet, 2]")
+            g = out
+        else:
+            g = np.empty((self.info.n_tet, 2))
         S = np.empty_like(So) if want_S else None
         self._check(self.lib.mw_gradient(self.h, C.byref(o), _ptr(So), _ptr(Se), alpha, C.byref(J), _ptr(g), _ptr(S)))
         return (J.value, g, S) if want_S else (J.value, g)
