@@ -62,7 +62,7 @@ typedef struct {
  *             flexible GMRES with FP32 operator and basis, preconditioner applied in the
  *             precision chosen at setup (BF16 on the tensor cores, or FP32), FP64 Hessenberg
  *             least squares.
- *   restart   Krylov dimension m per cycle (<= 64).
+ *   restart   Krylov dimension m per cycle (1..63).
  *   batch     columns per Krylov launch; 0 = all columns of a frequency in one block launch.
  *   max_it    cap on Arnoldi steps per column over the whole solve.
  *   tol       target FP64 true relative residual ||b - A x||_2 / ||b||_2 per column.

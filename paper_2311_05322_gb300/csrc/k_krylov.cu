@@ -678,59 +678,77 @@ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.
 
 // One thread per column: Hessenberg column j from h[0..j] and ||w||, previous rotations,
 // new rotation, residual estimate |g[j+1]| against the target.
-__global__ void givens_kernel(const double2* __restrict__ h, const double* __restrict__ npart, int nparts, int j,
-                              int m, int R, double2* __restrict__ H, double2* __restrict__ cs, double2* __restrict__ g,
-                              const double* __restrict__ target, int32_t* __restrict__ done,
-                              int32_t* __restrict__ kcol, double* __restrict__ scale, int32_t* __restrict__ active) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per column: the lanes sum the column's norm partials (fixed order: lane l takes parts
+// l, l + 32, ..., then an xor-shuffle tree) and stage the new Hessenberg column and the stored
+// rotations in shared memory; lane 0 applies the rotations (a sequential chain) and forms the
+// new one; the lanes write the column back.
+constexpr int kGivensWarps = 4;
+__global__ void __launch_bounds__(32 * kGivensWarps) givens_kernel(
+    const double2* __restrict__ h, const double* __restrict__ npart, int nparts, int j, int m, int R,
+    double2* __restrict__ H, double2* __restrict__ cs, double2* __restrict__ g, const double* __restrict__ target,
+    int32_t* __restrict__ done, int32_t* __restrict__ kcol, double* __restrict__ scale, int32_t* __restrict__ active) {
+  __shared__ double2 hs_all[kGivensWarps][64], rc_all[kGivensWarps][64], rs_all[kGivensWarps][64];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kGivensWarps + wib;
   if (c >= R) return;
   if (done[c]) {
-    scale[c] = 0.0;
+    if (lane == 0) scale[c] = 0.0;
     return;
   }
+  double2* hs = hs_all[wib];
+  double2* rc = rc_all[wib];
+  double2* rs = rs_all[wib];
   double nn = 0.0;
-  for (int p = 0; p < nparts; ++p) nn += npart[(int64_t)p * R + c];
+  for (int p = lane; p < nparts; p += 32) nn += npart[(int64_t)p * R + c];
+  for (int off = 16; off > 0; off >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, off);
   const double hn = sqrt(nn);
   double2* Hc = H + ((int64_t)c * m + j) * (m + 1);
-  for (int i = 0; i <= j; ++i) Hc[i] = h[i * R + c];
-  Hc[j + 1] = make_double2(hn, 0.0);
   double2* csc = cs + (int64_t)c * 2 * m;
-  for (int i = 0; i < j; ++i) {
-    const double2 ci = csc[2 * i], si = csc[2 * i + 1];
-    const double2 a = Hc[i], b = Hc[i + 1];
-    const double2 t = cadd(cmul(ci, a), cmul(si, b));
-    const double2 u = cadd(cmul(make_double2(-si.x, si.y), a), cmul(conjd(ci), b));  // -conj(s) a + conj(c) b
-    Hc[i] = t;
-    Hc[i + 1] = u;
+  for (int i = lane; i <= j; i += 32) hs[i] = h[i * R + c];
+  for (int i = lane; i < j; i += 32) {
+    rc[i] = csc[2 * i];
+    rs[i] = csc[2 * i + 1];
   }
-  const double2 a = Hc[j], b = Hc[j + 1];
-  const double den = sqrt(cabs2(a) + cabs2(b));
-  double2 cj, sj;
-  if (den == 0.0) {
-    cj = make_double2(1.0, 0.0);
-    sj = make_double2(0.0, 0.0);
-  } else {
-    cj = make_double2(a.x / den, -a.y / den);   // conj(a)/den
-    sj = make_double2(b.x / den, -b.y / den);   // conj(b)/den
+  __syncwarp();
+  if (lane == 0) {
+    hs[j + 1] = make_double2(hn, 0.0);
+    for (int i = 0; i < j; ++i) {
+      const double2 ci = rc[i], si = rs[i];
+      const double2 a = hs[i], b = hs[i + 1];
+      hs[i] = cadd(cmul(ci, a), cmul(si, b));
+      hs[i + 1] = cadd(cmul(make_double2(-si.x, si.y), a), cmul(conjd(ci), b));  // -conj(s) a + conj(c) b
+    }
+    const double2 a = hs[j], b = hs[j + 1];
+    const double den = sqrt(cabs2(a) + cabs2(b));
+    double2 cj, sj;
+    if (den == 0.0) {
+      cj = make_double2(1.0, 0.0);
+      sj = make_double2(0.0, 0.0);
+    } else {
+      cj = make_double2(a.x / den, -a.y / den);   // conj(a)/den
+      sj = make_double2(b.x / den, -b.y / den);   // conj(b)/den
+    }
+    csc[2 * j] = cj;
+    csc[2 * j + 1] = sj;
+    hs[j] = make_double2(den, 0.0);
+    hs[j + 1] = make_double2(0.0, 0.0);
+    double2* gc = g + (int64_t)c * (m + 1);
+    const double2 gj = gc[j];
+    gc[j + 1] = cmul(make_double2(-sj.x, sj.y), gj);   // -conj(s) g_j
+    gc[j] = cmul(cj, gj);
+    const double res = sqrt(cabs2(gc[j + 1]));
+    const bool stop = (res <= target[c]) || (hn == 0.0) || (j + 1 >= m) || !(res == res);
+    kcol[c] = j + 1;
+    if (stop) {
+      done[c] = 1;
+      scale[c] = 0.0;
+    } else {
+      scale[c] = 1.0 / hn;
+      atomicAdd(active, 1);
+    }
   }
-  csc[2 * j] = cj;
-  csc[2 * j + 1] = sj;
-  Hc[j] = make_double2(den, 0.0);
-  Hc[j + 1] = make_double2(0.0, 0.0);
-  double2* gc = g + (int64_t)c * (m + 1);
-  const double2 gj = gc[j];
-  gc[j + 1] = cmul(make_double2(-sj.x, sj.y), gj);   // -conj(s) g_j
-  gc[j] = cmul(cj, gj);
-  const double res = sqrt(cabs2(gc[j + 1]));
-  const bool stop = (res <= target[c]) || (hn == 0.0) || (j + 1 >= m) || !(res == res);
-  kcol[c] = j + 1;
-  if (stop) {
-    done[c] = 1;
-    scale[c] = 0.0;
-  } else {
-    scale[c] = 1.0 / hn;
-    atomicAdd(active, 1);
-  }
+  __syncwarp();
+  for (int i = lane; i <= j + 1; i += 32) Hc[i] = hs[i];
 }
 
 template <typename T>
@@ -1209,8 +1227,8 @@ void givens_step(const double2* h, const double* npart, int nparts, int j, int m
                  double2* gvec, double* target, int32_t* done, int32_t* kcol, double* scale, int32_t* active_count,
                  cudaStream_t s) {
   note_launch(1);
-  givens_kernel<<<(R + 127) / 128, 128, 0, s>>>(h, npart, nparts, j, m, R, H, cs, gvec, target, done, kcol, scale,
-                                                 active_count);
+  givens_kernel<<<(R + kGivensWarps - 1) / kGivensWarps, 32 * kGivensWarps, 0, s>>>(
+      h, npart, nparts, j, m, R, H, cs, gvec, target, done, kcol, scale, active_count);
 }
 void scale_cols_f64(double2* v, const double* scale, int64_t E, int R, cudaStream_t s) {
   note_launch(1);
