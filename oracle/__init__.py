@@ -14,6 +14,7 @@ paper by eye:
   solve.py     sparse direct solve, S-matrix                          (Eq. s1, dipole form)
   inverse.py   cost, adjoint, per-tet gradient, Tikhonov, L-BFGS      (Eq. sahar:2, Sec. IV-D)
   oras.py      one-level ORAS and right-preconditioned GMRES          (Sec. IV-C)
+  ports.py     TE10 waveguide ports, metal walls, port S-matrix       (Eq. m1-m2 boundary terms, Eq. s1)
   nn.py        FP64 forward/backward of the learned initialiser network
 Functions whose parity has no independent pin say "parity unpinned" in their docstring.
 """

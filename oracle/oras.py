@@ -67,8 +67,10 @@ def build_subdomains(sysm: asm.System, tet_part: np.ndarray, n_sub: int, overlap
     return subs, owner
 
 
-def local_matrix(sysm: asm.System, sub: Subdomain, eps: np.ndarray, freq_hz: float, eps_bg: complex):
-    """B_s as a scipy CSC matrix over sub.dofs."""
+def local_matrix(sysm: asm.System, sub: Subdomain, eps: np.ndarray, freq_hz: float, eps_bg: complex,
+                 zface: np.ndarray | None = None):
+    """B_s as a scipy CSC matrix over sub.dofs.  zface [F_b], when given, replaces the open-boundary
+    coefficient i k0 sqrt(eps_bg) on each outer face (port and metal faces, ports.py)."""
     topo = sysm.topo
     k0 = constants.k0(freq_hz)
     n = sub.dofs.size
@@ -83,7 +85,7 @@ def local_matrix(sysm: asm.System, sub: Subdomain, eps: np.ndarray, freq_hz: flo
     bsel = in_sub[topo.face_tets[topo.bface, 0]]
     if np.any(bsel):
         fl = np.searchsorted(sub.dofs, sysm.bface_edges[bsel])
-        zb = 1j * k0 * np.sqrt(complex(eps_bg))
+        zb = 1j * k0 * np.sqrt(complex(eps_bg)) if zface is None else zface[bsel][:, None, None]
         rows.append(np.repeat(fl, 3, axis=1).ravel())
         cols.append(np.tile(fl, (1, 3)).ravel())
         vals.append((zb * sysm.BF[bsel]).reshape(-1))
@@ -100,17 +102,27 @@ def local_matrix(sysm: asm.System, sub: Subdomain, eps: np.ndarray, freq_hz: flo
 
 
 class ORAS:
-    """M^{-1} = sum_s R_s^T D_s B_s^{-1} R_s with sparse-LU subdomain solves."""
+    """M^{-1} = sum_s R_s^T D_s B_s^{-1} R_s with sparse-LU subdomain solves.
 
-    def __init__(self, sysm, tet_part, n_sub, overlap, eps, freq_hz, eps_bg):
+    With metal edges (ports.py) each B_s keeps only its free edges, and the operator is extended
+    by the identity on the metal edges (z = r there), matching a global matrix whose metal rows
+    and columns are those of the identity."""
+
+    def __init__(self, sysm, tet_part, n_sub, overlap, eps, freq_hz, eps_bg, zface=None, metal=None):
         self.subs, self.owner = build_subdomains(sysm, tet_part, n_sub, overlap)
-        self.lus = [spla.splu(local_matrix(sysm, s, eps, freq_hz, eps_bg)) for s in self.subs]
+        self.free = [np.ones(s.dofs.size, dtype=bool) if metal is None else ~metal[s.dofs] for s in self.subs]
+        self.lus = []
+        for s, fr in zip(self.subs, self.free):
+            B = local_matrix(sysm, s, eps, freq_hz, eps_bg, zface)
+            self.lus.append(spla.splu(B if metal is None else B[fr][:, fr].tocsc()))
         self.n = sysm.topo.n_edge
 
     def apply(self, r: np.ndarray) -> np.ndarray:
         z = np.zeros_like(r, dtype=np.complex128)
-        for sub, lu in zip(self.subs, self.lus):
-            y = lu.solve(np.ascontiguousarray(r[sub.dofs], dtype=np.complex128))
+        for sub, lu, fr in zip(self.subs, self.lus, self.free):
+            rs = np.ascontiguousarray(r[sub.dofs], dtype=np.complex128)
+            y = rs.copy()
+            y[fr] = lu.solve(np.ascontiguousarray(rs[fr]))
             z[sub.dofs[sub.owned]] = y[sub.owned]
         return z
 
@@ -118,7 +130,9 @@ class ORAS:
         """Owned rows of B_s^{-1} (n_own x n_s), the operator the GPU applies as a GEMM."""
         sub = self.subs[s]
         n = sub.dofs.size
-        Binv = self.lus[s].solve(np.eye(n, dtype=np.complex128))
+        fr = self.free[s]
+        Binv = np.eye(n, dtype=np.complex128)
+        Binv[np.ix_(fr, fr)] = self.lus[s].solve(np.eye(int(fr.sum()), dtype=np.complex128))
         return Binv[sub.owned, :]
 
 

@@ -282,6 +282,58 @@ def add_noise(S: np.ndarray, snr_db: float, seed: int) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------------------
+# Waveguide ports: faces of Kuhn meshes and rectangular port apertures
+# ----------------------------------------------------------------------------------------
+_TET_FACES = ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2))
+
+
+def faces_on_plane(mesh: Mesh, axis: int, value: float, lo2, hi2, tol: float = 1e-9) -> np.ndarray:
+    """Sorted vertex triples of the tet faces lying in the plane x[axis] = value with every vertex
+    inside the rectangle [lo2, hi2] of the two other axes (in increasing axis order)."""
+    fv = np.sort(mesh.tets[:, _TET_FACES].reshape(-1, 3).astype(np.int64), axis=1)
+    fv = np.unique(fv, axis=0)
+    P = mesh.xyz[fv]                                            # [F, 3, 3]
+    others = [d for d in range(3) if d != axis]
+    ok = np.all(np.abs(P[:, :, axis] - value) <= tol, axis=1)
+    for k, d in enumerate(others):
+        ok &= np.all((P[:, :, d] >= lo2[k] - tol) & (P[:, :, d] <= hi2[k] + tol), axis=1)
+    return fv[ok]
+
+
+@dataclass
+class PortSet:
+    """Rectangular apertures: corner, unit broad-side direction u (width a), unit narrow-side
+    direction v, and the permittivity filling each guide."""
+    origin: np.ndarray       # [P, 3]
+    u: np.ndarray            # [P, 3]
+    v: np.ndarray            # [P, 3]
+    a: np.ndarray            # [P]
+    eps_fill: np.ndarray     # [P] complex
+
+    @property
+    def n(self) -> int:
+        return self.a.shape[0]
+
+
+def waveguide_section(cells=(8, 4, 12), a: float = 0.02, b: float = 0.01, length: float = 0.03,
+                      eps_fill: complex = 59.0 - 0.0j):
+    """Straight rectangular guide [0, a] x [0, b] x [0, length] on a Kuhn mesh: metal side walls,
+    port 0 at z = 0 and port 1 at z = length, broad side along x, field along y.
+    Returns (mesh, face_vert [n, 3], label [n] (-1 metal, p port), PortSet)."""
+    m = kuhn_mesh(*cells, lo=(0.0, 0.0, 0.0), hi=(a, b, length))
+    walls = [faces_on_plane(m, 0, 0.0, (0, 0), (b, length)), faces_on_plane(m, 0, a, (0, 0), (b, length)),
+             faces_on_plane(m, 1, 0.0, (0, 0), (a, length)), faces_on_plane(m, 1, b, (0, 0), (a, length))]
+    p0 = faces_on_plane(m, 2, 0.0, (0, 0), (a, b))
+    p1 = faces_on_plane(m, 2, length, (0, 0), (a, b))
+    metal = np.concatenate(walls)
+    fv = np.concatenate([metal, p0, p1])
+    lab = np.concatenate([np.full(len(metal), -1), np.zeros(len(p0), np.int64), np.ones(len(p1), np.int64)])
+    ports = PortSet(np.array([[0.0, 0.0, 0.0], [0.0, 0.0, length]]), np.tile([1.0, 0.0, 0.0], (2, 1)),
+                    np.tile([0.0, 1.0, 0.0], (2, 1)), np.array([a, a]), np.array([eps_fill, eps_fill]))
+    return m, fv, lab.astype(np.int32), ports
+
+
+# ----------------------------------------------------------------------------------------
 # Named workloads
 # ----------------------------------------------------------------------------------------
 @dataclass
