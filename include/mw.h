@@ -162,7 +162,9 @@ mw_status mw_get_element_matrices(mw_ctx* ctx, double* K, double* M, double* vol
 
 /* ---- assembly, Eq. (m2) with k^2 = k0^2 eps_r ---------------------------------------- */
 /* A_f = K - k0_f^2 sum_T eps_T M^T + i k0_f sqrt(eps_bg) B for each frequency (Hz);
- * eps_r [n_tet][2] (re, im), eps_bg[2].  Re-run whenever eps changes. */
+ * eps_r [n_tet][2] (re, im), eps_bg[2].  Re-run whenever eps changes.  With boundary classes
+ * (mw_set_ports) B keeps only the open faces, port faces add i beta_p B^F, and metal edges
+ * have identity rows and columns. */
 mw_status mw_assemble(mw_ctx* ctx, int32_t n_freq, const double* freq_hz, const double* eps_r,
                       const double* eps_bg);
 /* Values of A_f in the canonical pattern, host complex128 [nnz] (parity hook). */
@@ -177,9 +179,47 @@ mw_status mw_apply_matrix(mw_ctx* ctx, int32_t f, int32_t prec, const void* x_de
 /* ---- sources (volume-source reading of Eq. m1) ----------------------------------------- */
 /* z-directed dipoles: pos/dir [n_src][3].  Each maps to the z-directed edge whose midpoint is
  * nearest (ties: lowest edge id); outputs (optional) the edge and its sign (+1 when the
- * edge lo -> hi points along dir).  RHS b_j = -i omega mu0 s_j e_edge(j). */
+ * edge lo -> hi points along dir).  RHS b_j = -i omega mu0 s_j e_edge(j), S_ij = s_i x_j[edge_i].
+ * Replaces port sources (port faces keep their boundary term). */
 mw_status mw_set_sources(mw_ctx* ctx, int32_t n_src, const double* pos, const double* dir,
                          int32_t* src_edge_out, int8_t* src_sign_out);
+
+/* ---- waveguide ports and metal walls (Eq. m1-m2 boundary terms, Eq. s1) --------------- */
+/* A rectangular waveguide port on the outer boundary.  Its TE10 mode is
+ *   E_p(x) = sin(pi ((x - origin) . u) / a) v,
+ * with propagation constant beta_p = -i sqrt((pi / a)^2 - k0^2 eps_fill) (principal root, so
+ * Im beta <= 0, and beta > 0 above cut-off in a lossless filling). */
+typedef struct mw_port {
+  double origin[3];   /* corner of the aperture (m) */
+  double u[3];        /* unit broad-side direction: the mode varies along u over [0, a] */
+  double v[3];        /* unit narrow-side direction: the mode's field points along v */
+  double a;           /* broad-side width (m), > 0 */
+  double eps_fill[2]; /* relative permittivity filling the guide (re, im), im <= 0 */
+} mw_port;
+/* Boundary classes of Eq. (m1) (Sec. IV-B).  face_vert [n_face][3] lists faces by vertex ids
+ * (any order) and face_label [n_face] gives each a class:
+ *   -1           metal (Gamma_m), any face of the mesh: every edge of the face is removed from
+ *                the unknowns (kept as an identity row and column with zero right-hand side,
+ *                so every field is zero there);
+ *   p in [0, n)  port p (Gamma_t while p transmits, Gamma_r while it receives), boundary faces
+ *                only: face term i beta_p B^F in place of the open one.
+ * Unlisted boundary faces stay open (Gamma_o, i k0 sqrt(eps_bg) B^F).  With n_port >= 1 the
+ * ports become the transmitters and receivers, replacing any dipoles (Eq. m2 and Eq. s1):
+ *   b_j = 2 i beta_j w_j,   w_j,e = int_{port j} E_j . N_e   (g = 2 i beta E^TE10),
+ *   S_ij = w_i^T x_j / n_i,   n_i = int_{port i} |E_i|^2,
+ * the face integrals by a 10 x 10 collapsed Gauss-Legendre rule per face, on the GPU.
+ * n_port = 0 sets metal faces only and keeps dipole sources.  Call after mw_set_mesh; it
+ * drops the assembled matrices, the preconditioner and stored fields (assemble again).
+ * Errors: MW_ESTATE without a mesh; MW_EINVAL for a vertex out of range, a listed triple
+ * that is not a face of the mesh, a port face that is not a boundary face, a face listed twice
+ * with different labels, a label out of range, a port without faces, a <= 0, u / v not
+ * orthonormal, a non-finite value, or eps_fill with im > 0. */
+mw_status mw_set_ports(mw_ctx* ctx, int32_t n_port, const mw_port* ports, int64_t n_face,
+                       const int32_t* face_vert, const int32_t* face_label);
+/* Port load vectors and norms (parity hook): W host [E][n_port] (w_p, zero on metal edges and
+ * away from port p) and norms [n_port]; either may be NULL.  MW_ESTATE unless ports are the
+ * current sources. */
+mw_status mw_get_port_vectors(mw_ctx* ctx, double* W, double* norms);
 
 /* ---- ORAS preconditioner (Sec. IV-C) ------------------------------------------------ */
 /* tet_part [n_tet] in [0, n_sub); overlap_layers >= 0 vertex-neighbour layers; inv_prec

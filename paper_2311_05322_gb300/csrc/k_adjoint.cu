@@ -1,8 +1,10 @@
 // K9 S-matrix extraction, K10 cost and adjoint sources, K11 per-tet gradient, K12 Tikhonov.
 //
-//   S_ij = p_i^T x_j = s_i x_j[edge_i]                                  (dipole form of Eq. s1)
+//   S_ij = q_i^T x_j,  q_i = w_i / n_i                                    (Eq. s1)
+//     dipoles: w_i = s_i e_edge(i), n_i = 1;  ports: w_i,e = int_{port i} E_i . N_e,
+//     n_i = int_{port i} |E_i|^2
 //   J_data = 1/2 sum w_ij |S_ij - S^obs_ij|^2,  w = 1/|S^empty_ij|^2     (Eq. sahar:2)
-//   c_ij = w_ij conj(S_ij - S^obs_ij),  adjoint sources sum_i c_ij p_i
+//   c_ij = w_ij conj(S_ij - S^obs_ij),  adjoint sources sum_i c_ij q_i
 //   G_T = sum_j lambda_j^T M^T x_j;  dJ/dRe eps_T += k0^2 Re G_T, dJ/dIm eps_T -= k0^2 Im G_T
 //   R = 1/2 sum_{interior F} w_F |eps_T - eps_T'|^2,  w_F = |F| / |c_T - c_T'|
 #include "k_adjoint.h"
@@ -11,14 +13,20 @@
 namespace mwk {
 namespace {
 
-__global__ void s_extract_kernel(const double2* __restrict__ X, const int32_t* __restrict__ edge,
-                                 const int8_t* __restrict__ sign, int ns, double2* __restrict__ S) {
+// One thread per (receiver i, transmitter j); the entries of q_i in list order.
+__global__ void s_project_kernel(const double2* __restrict__ X, const int64_t* __restrict__ ptr,
+                                 const int32_t* __restrict__ edge, const double* __restrict__ w,
+                                 const double* __restrict__ nrm, int ns, double2* __restrict__ S) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ns * ns) return;
   const int i = t / ns, j = t % ns;
-  const double s = (double)sign[i];
-  const double2 x = X[(int64_t)edge[i] * ns + j];
-  S[t] = make_double2(s * x.x, s * x.y);
+  double re = 0.0, im = 0.0;
+  for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+    const double2 x = X[(int64_t)edge[k] * ns + j];
+    re += w[k] * x.x;
+    im += w[k] * x.y;
+  }
+  S[t] = make_double2(re / nrm[i], im / nrm[i]);
 }
 
 // Single block: deterministic tree reduction of the cost.
@@ -42,19 +50,26 @@ __global__ void adjoint_weights_kernel(const double2* __restrict__ S, const doub
   if (threadIdx.x == 0) *J = red[0];
 }
 
-// One thread per transmitter column j; receivers added in index order (deterministic even if
-// two receivers share an edge).
-__global__ void adjoint_rhs_kernel(const int32_t* __restrict__ edge, const int8_t* __restrict__ sign, int ns,
-                                   const double2* __restrict__ C, double2* __restrict__ B) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= ns) return;
-  for (int i = 0; i < ns; ++i) {
-    const double s = (double)sign[i];
+// One thread per (source edge u, column j), over the edge-major transpose of the source
+// vectors: the (receiver i, entry k) pairs at edge u in receiver order, so the sum is
+// deterministic even where receivers share an edge.  B[e_u][j] = sum (c_ij / n_i) w_k.
+__global__ void adjoint_sources_kernel(const int64_t* __restrict__ tptr, const int32_t* __restrict__ tedge,
+                                       const int32_t* __restrict__ tsrc, const int32_t* __restrict__ tk, int64_t nu,
+                                       const double* __restrict__ w, const double* __restrict__ nrm,
+                                       const double2* __restrict__ C, int ns, double2* __restrict__ B) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nu * ns) return;
+  const int64_t u = t / ns;
+  const int j = (int)(t - u * ns);
+  double re = 0.0, im = 0.0;
+  for (int64_t q = tptr[u]; q < tptr[u + 1]; ++q) {
+    const int i = tsrc[q];
     const double2 c = C[i * ns + j];
-    double2* b = B + (int64_t)edge[i] * ns + j;
-    b->x += s * c.x;
-    b->y += s * c.y;
+    const double s = w[tk[q]];
+    re += (c.x / nrm[i]) * s;
+    im += (c.y / nrm[i]) * s;
   }
+  B[(int64_t)tedge[u] * ns + j] = make_double2(re, im);
 }
 
 // One warp per tet, lanes over the transmitter columns; the warp sums lambda_j^T M^T x_j
@@ -163,20 +178,24 @@ __global__ void count_active_kernel(const int32_t* done, int R, int32_t* active)
 
 }  // namespace
 
-void s_extract(const double2* X, const int32_t* edge, const int8_t* sign, int ns, double2* S, cudaStream_t s) {
+void s_project(const double2* X, const int64_t* ptr, const int32_t* edge, const double* w, const double* nrm, int ns,
+               double2* S, cudaStream_t s) {
   note_launch(1);
-  s_extract_kernel<<<(ns * ns + 255) / 256, 256, 0, s>>>(X, edge, sign, ns, S);
+  s_project_kernel<<<(ns * ns + 255) / 256, 256, 0, s>>>(X, ptr, edge, w, nrm, ns, S);
 }
 void adjoint_weights(const double2* S, const double2* So, const double2* Se, int64_t n, double2* C, double* J,
                      cudaStream_t s) {
   note_launch(1);
   adjoint_weights_kernel<<<1, 256, 0, s>>>(S, So, Se, n, C, J);
 }
-void adjoint_rhs(const int32_t* edge, const int8_t* sign, int ns, const double2* C, double2* B, int64_t E,
-                 cudaStream_t s) {
+void adjoint_sources(const int64_t* tptr, const int32_t* tedge, const int32_t* tsrc, const int32_t* tk, int64_t nu,
+                     const double* w, const double* nrm, const double2* C, int ns, double2* B, int64_t E,
+                     cudaStream_t s) {
   note_launch(1);
   cudaMemsetAsync(B, 0, sizeof(double2) * E * ns, s);
-  adjoint_rhs_kernel<<<(ns + 63) / 64, 64, 0, s>>>(edge, sign, ns, C, B);
+  const int64_t n = nu * ns;
+  if (n > 0)
+    adjoint_sources_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tptr, tedge, tsrc, tk, nu, w, nrm, C, ns, B);
 }
 void grad_tet(const int32_t* tet_edge, const double* KM, int64_t T, const double2* L, const double2* X, int ns,
               double k0sq, double* g, cudaStream_t s) {

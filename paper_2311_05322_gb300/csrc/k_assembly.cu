@@ -139,12 +139,17 @@ __global__ void tikhonov_weights_kernel(const double* __restrict__ xyz, const in
 }
 
 // K2: one thread per matrix entry, pulling its contributions in tet order then face order:
-//   A = sum_T (K^T - (k0^2 eps_T) M^T) + sum_F (i k0 sqrt(eps_bg)) B^F.
+//   A = sum_T (K^T - (k0^2 eps_T) M^T) + sum_F z_F B^F,
+// z_F = i k0 sqrt(eps_bg) on every boundary face, or, with face classes (waveguide ports, Eq. m1),
+// z_F = zc[fcls[F]]: i k0 sqrt(eps_bg) (open), 0 (metal), i beta_p (port p).  nzmask (optional)
+// then replaces the rows and columns of metal edges by those of the identity (1: zero, 2: one).
 // Writes the FP64 value and its FP32 rounding.
 __global__ void reassemble_kernel(const int64_t* __restrict__ cptr, const int32_t* __restrict__ contrib, int64_t nnz,
                                   const double* __restrict__ KM, const double* __restrict__ Bf,
                                   const double* __restrict__ eps, double k0sq, double zb_re, double zb_im,
-                                  double2* __restrict__ A64, float2* __restrict__ A32) {
+                                  const int32_t* __restrict__ fcls, const double2* __restrict__ zc,
+                                  const uint8_t* __restrict__ nzmask, double2* __restrict__ A64,
+                                  float2* __restrict__ A32) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nnz) return;
   double re = 0.0, im = 0.0;
@@ -165,18 +170,111 @@ __global__ void reassemble_kernel(const int64_t* __restrict__ cptr, const int32_
       const int64_t f = q / 9;
       const int r = (int)(q - f * 9);
       const double Bv = Bf[6 * f + mw::packed3(r / 3, r % 3)];
-      re = __dadd_rn(re, __dmul_rn(zb_re, Bv));
-      im = __dadd_rn(im, __dmul_rn(zb_im, Bv));
+      double zr = zb_re, zi = zb_im;
+      if (fcls) {
+        const double2 z = zc[fcls[f]];
+        zr = z.x;
+        zi = z.y;
+      }
+      re = __dadd_rn(re, __dmul_rn(zr, Bv));
+      im = __dadd_rn(im, __dmul_rn(zi, Bv));
+    }
+  }
+  if (nzmask) {
+    const uint8_t m = nzmask[p];
+    if (m) {
+      re = m == 2 ? 1.0 : 0.0;
+      im = 0.0;
     }
   }
   A64[p] = make_double2(re, im);
   if (A32) A32[p] = make_float2((float)re, (float)im);
 }
 
-__global__ void dipole_rhs_kernel(const int32_t* edge, const int8_t* sign, int n_src, double s_im, double2* B) {
+// Right-hand sides b_j = c_j w_j of sparse source vectors (CSR over sources, edges distinct
+// within a source): one thread per source.  Dipoles: one entry w = +-1, c = -i omega mu0;
+// ports: the load vector w_j and c_j = 2 i beta_j (g = 2 i beta E^TE10, Eq. m2).
+__global__ void source_rhs_kernel(const int64_t* __restrict__ ptr, const int32_t* __restrict__ edge,
+                                  const double* __restrict__ w, const double2* __restrict__ coef, int ns,
+                                  double2* __restrict__ B) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n_src) return;
-  B[(int64_t)edge[j] * n_src + j] = make_double2(0.0, s_im * (double)sign[j]);
+  if (j >= ns) return;
+  const double2 c = coef[j];
+  for (int64_t k = ptr[j]; k < ptr[j + 1]; ++k) B[(int64_t)edge[k] * ns + j] = make_double2(c.x * w[k], c.y * w[k]);
+}
+
+// Port face moments (Eq. m2 right-hand side and Eq. s1), one thread per port face F of port p:
+//   mom[F][m] = int_F N_m . E_p,   nrm[F] = int_F |E_p|^2,
+// E_p(x) = sin(pi ((x - o).u) / a) v (TE10), N_m = l_a grad l_b - l_b grad l_a for the face edges
+// (q0,q1) (q0,q2) (q1,q2) (sorted vertices, so each points from its lower vertex), surface
+// gradients as in face_geom_kernel.  Collapsed Gauss-Legendre rule: x = q0 + xi e1 + eta e2,
+// eta = (1 - xi) t, dA = 2|F| (1 - xi) dxi dt, nq nodes gx / weights gw on [0, 1] per direction.
+// pdesc [P][10] = origin, u, v, a.
+__global__ void port_face_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ fv,
+                                 const int32_t* __restrict__ fport, int64_t F, const double* __restrict__ pdesc,
+                                 const double* __restrict__ gx, const double* __restrict__ gw, int nq,
+                                 double* __restrict__ mom, double* __restrict__ nrm) {
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const d3 q0 = load3(xyz, fv[3 * f]), q1 = load3(xyz, fv[3 * f + 1]), q2 = load3(xyz, fv[3 * f + 2]);
+  const d3 e1 = sub(q1, q0), e2 = sub(q2, q0);
+  const double g11 = dot(e1, e1), g12 = dot(e1, e2), g22 = dot(e2, e2);
+  const double detg = g11 * g22 - g12 * g12;
+  const double i11 = g22 / detg, i12 = -g12 / detg, i22 = g11 / detg;
+  d3 g[3];
+  g[1] = {i11 * e1.x + i12 * e2.x, i11 * e1.y + i12 * e2.y, i11 * e1.z + i12 * e2.z};
+  g[2] = {i12 * e1.x + i22 * e2.x, i12 * e1.y + i22 * e2.y, i12 * e1.z + i22 * e2.z};
+  g[0] = {-(g[1].x + g[2].x), -(g[1].y + g[2].y), -(g[1].z + g[2].z)};
+  const double jac = sqrt(detg);  // 2|F|
+  const double* P = pdesc + 10 * (int64_t)fport[f];
+  const d3 o = {P[0], P[1], P[2]}, u = {P[3], P[4], P[5]}, v = {P[6], P[7], P[8]};
+  const double inv_a = 1.0 / P[9];
+  // N_m . v for the three face edges is linear in the barycentrics: (N_m . v) = l_a gv_b - l_b gv_a
+  const double gv0 = dot(g[0], v), gv1 = dot(g[1], v), gv2 = dot(g[2], v);
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0, nn = 0.0;
+  for (int i = 0; i < nq; ++i) {
+    const double xi = gx[i];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, an = 0.0;
+    for (int j = 0; j < nq; ++j) {
+      const double eta = (1.0 - xi) * gx[j];
+      const double l0 = 1.0 - xi - eta, l1 = xi, l2 = eta;
+      const d3 x = {q0.x + xi * e1.x + eta * e2.x, q0.y + xi * e1.y + eta * e2.y, q0.z + xi * e1.z + eta * e2.z};
+      const double sv = sinpi(dot(sub(x, o), u) * inv_a);
+      const double wj = gw[j] * sv;
+      a0 += wj * (l0 * gv1 - l1 * gv0);
+      a1 += wj * (l0 * gv2 - l2 * gv0);
+      a2 += wj * (l1 * gv2 - l2 * gv1);
+      an += wj * sv;
+    }
+    const double wi = gw[i] * (1.0 - xi);
+    m0 += wi * a0;
+    m1 += wi * a1;
+    m2 += wi * a2;
+    nn += wi * an;
+  }
+  mom[3 * f + 0] = jac * m0;
+  mom[3 * f + 1] = jac * m1;
+  mom[3 * f + 2] = jac * m2;
+  nrm[f] = jac * nn * dot(v, v);
+}
+
+// Port load vectors: entry k (port p, edge e) sums the face moments listed for it, in face
+// order; one thread per entry.  Port norms: one thread per port sums its faces in order.
+__global__ void port_accumulate_kernel(const int64_t* __restrict__ eptr, const int32_t* __restrict__ econ,
+                                       int64_t n_ent, const double* __restrict__ mom, double* __restrict__ w) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_ent) return;
+  double acc = 0.0;
+  for (int64_t q = eptr[k]; q < eptr[k + 1]; ++q) acc += mom[econ[q]];
+  w[k] = acc;
+}
+__global__ void port_norm_kernel(const int64_t* __restrict__ fptr, int n_port, const double* __restrict__ nrm,
+                                 double* __restrict__ pn) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_port) return;
+  double acc = 0.0;
+  for (int64_t f = fptr[p]; f < fptr[p + 1]; ++f) acc += nrm[f];
+  pn[p] = acc;
 }
 
 __global__ void cast64to32_kernel(const double2* a, float2* b, int64_t n) {
@@ -230,17 +328,28 @@ void tikhonov_weights(const double* xyz, const int32_t* tets, const int32_t* nb,
   tikhonov_weights_kernel<<<blocks_for(T, 128), 128, 0, s>>>(xyz, tets, nb, T, w);
 }
 void reassemble(const int64_t* cptr, const int32_t* contrib, int64_t nnz, const double* KM, const double* Bf,
-                const double* eps, double k0sq, double zb_re, double zb_im, double2* A64, float2* A32,
-                cudaStream_t s) {
+                const double* eps, double k0sq, double zb_re, double zb_im, const int32_t* fcls, const double2* zc,
+                const uint8_t* nzmask, double2* A64, float2* A32, cudaStream_t s) {
   note_launch(1);
-  reassemble_kernel<<<blocks_for(nnz, 256), 256, 0, s>>>(cptr, contrib, nnz, KM, Bf, eps, k0sq, zb_re, zb_im, A64,
-                                                          A32);
+  reassemble_kernel<<<blocks_for(nnz, 256), 256, 0, s>>>(cptr, contrib, nnz, KM, Bf, eps, k0sq, zb_re, zb_im, fcls,
+                                                          zc, nzmask, A64, A32);
 }
-void dipole_rhs(const int32_t* edge, const int8_t* sign, int n_src, double s_im, double2* B, int64_t E,
-                cudaStream_t s) {
+void source_rhs(const int64_t* ptr, const int32_t* edge, const double* w, const double2* coef, int ns, double2* B,
+                int64_t E, cudaStream_t s) {
   note_launch(1);
-  cudaMemsetAsync(B, 0, sizeof(double2) * E * n_src, s);
-  dipole_rhs_kernel<<<blocks_for(n_src, 64), 64, 0, s>>>(edge, sign, n_src, s_im, B);
+  cudaMemsetAsync(B, 0, sizeof(double2) * E * ns, s);
+  source_rhs_kernel<<<blocks_for(ns, 64), 64, 0, s>>>(ptr, edge, w, coef, ns, B);
+}
+void port_face_moments(const double* xyz, const int32_t* fv, const int32_t* fport, int64_t F, const double* pdesc,
+                       const double* gx, const double* gw, int nq, double* mom, double* nrm, cudaStream_t s) {
+  note_launch(1);
+  if (F > 0) port_face_kernel<<<blocks_for(F, 128), 128, 0, s>>>(xyz, fv, fport, F, pdesc, gx, gw, nq, mom, nrm);
+}
+void port_accumulate(const int64_t* eptr, const int32_t* econ, int64_t n_ent, const double* mom, double* w,
+                     const int64_t* fptr, int n_port, const double* nrm, double* pn, cudaStream_t s) {
+  note_launch(2);
+  if (n_ent > 0) port_accumulate_kernel<<<blocks_for(n_ent, 128), 128, 0, s>>>(eptr, econ, n_ent, mom, w);
+  port_norm_kernel<<<blocks_for(n_port, 64), 64, 0, s>>>(fptr, n_port, nrm, pn);
 }
 void cast_f64_to_f32(const double2* a, float2* b, int64_t n, cudaStream_t s) {
   note_launch(1);

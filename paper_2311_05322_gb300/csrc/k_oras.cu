@@ -2,9 +2,12 @@
 //
 // Setup, per subdomain s with n_s unknowns:
 //   1. dense local matrix  B_s = sum_{T in s} (K^T - k0^2 eps_T M^T)
-//                               + sum_{surface faces F of s} i k0 sqrt(eps_F) B^F,
-//      eps_F = eps_bg on the outer boundary, eps of the inside tet on an interface face
-//      (first-order impedance transmission condition of Eq. m1 on the artificial boundary);
+//                               + sum_{surface faces F of s} z_F B^F,
+//      z_F = i k0 sqrt(eps_F) on an interface face, eps_F the eps of the inside tet (first-order
+//      impedance transmission condition of Eq. m1 on the artificial boundary); on an outer face
+//      z_F = i k0 sqrt(eps_bg), or with face classes (waveguide ports) the global boundary's
+//      coefficient of that face (open, metal = 0, port = i beta_p); the rows and columns of
+//      metal edges are then those of the identity, as in the global matrix;
 //   2. in-place blocked Gauss-Jordan inversion without pivoting (the imaginary part of B_s is
 //      symmetric positive definite for lossy media, so every leading block is nonsingular);
 //   3. the owned rows of B_s^{-1} (restricted partition of unity, boolean D_s) are kept as
@@ -37,14 +40,18 @@ __device__ __forceinline__ double2 csqrt_principal(double a, double b) {
 
 // One warp per subdomain; tets then surface faces in list order, entries of one element by
 // different lanes (never the same matrix entry), elements in sequence (ordered by __syncwarp).
+// surf_tet codes: >= 0 inside tet of an interface face; -1 outer face with i k0 sqrt(eps_bg)
+// when zc is null, else -1 - c for an outer face of class c with coefficient zc[c].
 template <typename T>
 __global__ void local_assemble_kernel(const int32_t* __restrict__ sub_ids, const int64_t* __restrict__ dof_ptr,
-                                      const int64_t* __restrict__ tet_ptr, const int32_t* __restrict__ tet_ids,
-                                      const int32_t* __restrict__ tet_loc, const int64_t* __restrict__ surf_ptr,
-                                      const int32_t* __restrict__ surf_loc, const int32_t* __restrict__ surf_tet,
-                                      const double* __restrict__ Bsurf, const double* __restrict__ KM,
-                                      const double* __restrict__ eps, double k0, double eps_bg_re, double eps_bg_im,
-                                      const int64_t* __restrict__ ws_off, T* __restrict__ ws) {
+                                      const int32_t* __restrict__ dofs, const int64_t* __restrict__ tet_ptr,
+                                      const int32_t* __restrict__ tet_ids, const int32_t* __restrict__ tet_loc,
+                                      const int64_t* __restrict__ surf_ptr, const int32_t* __restrict__ surf_loc,
+                                      const int32_t* __restrict__ surf_tet, const double* __restrict__ Bsurf,
+                                      const double* __restrict__ KM, const double* __restrict__ eps, double k0,
+                                      double eps_bg_re, double eps_bg_im, const double2* __restrict__ zc,
+                                      const uint8_t* __restrict__ metal, const int64_t* __restrict__ ws_off,
+                                      T* __restrict__ ws) {
   using Sc = typename Tr<T>::S;
   const int b = blockIdx.x;
   const int s = sub_ids[b];
@@ -74,10 +81,18 @@ __global__ void local_assemble_kernel(const int32_t* __restrict__ sub_ids, const
     if (lane < 9) {
       const int m = lane / 3, nn = lane % 3;
       const int32_t it = surf_tet[q];
-      const double2 sq = it >= 0 ? csqrt_principal(eps[2 * (int64_t)it], eps[2 * (int64_t)it + 1]) : sbg;
-      // i k0 sqrt(eps) = (-k0 Im sqrt, k0 Re sqrt)
       const double Bv = Bsurf[6 * q + mw::packed3(m, nn)];
-      const double re = (-k0 * sq.y) * Bv, im = (k0 * sq.x) * Bv;
+      double re, im;
+      if (it < 0 && zc) {
+        const double2 z = zc[-1 - it];
+        re = z.x * Bv;
+        im = z.y * Bv;
+      } else {
+        const double2 sq = it >= 0 ? csqrt_principal(eps[2 * (int64_t)it], eps[2 * (int64_t)it + 1]) : sbg;
+        // i k0 sqrt(eps) = (-k0 Im sqrt, k0 Re sqrt)
+        re = (-k0 * sq.y) * Bv;
+        im = (k0 * sq.x) * Bv;
+      }
       T* p = A + (int64_t)surf_loc[3 * q + m] * n + surf_loc[3 * q + nn];
       T v = *p;
       v.x += (Sc)re;
@@ -85,6 +100,19 @@ __global__ void local_assemble_kernel(const int32_t* __restrict__ sub_ids, const
       *p = v;
     }
     __syncwarp();
+  }
+  if (metal) {
+    const int32_t* gd = dofs + dof_ptr[s];
+    for (int64_t i = 0; i < n; ++i) {
+      if (!metal[gd[i]]) continue;
+      for (int64_t j = lane; j < n; j += 32) {
+        A[i * n + j] = T{0, 0};
+        A[j * n + i] = T{0, 0};
+      }
+      __syncwarp();
+      if (lane == 0) A[i * n + i] = T{1, 0};
+      __syncwarp();
+    }
   }
 }
 
@@ -406,16 +434,17 @@ void gj_all(const OrasBatch& bt, T* ws, T* dinv, int32_t* status, cudaStream_t s
 }  // namespace
 
 void oras_local_assemble(const OrasBatch& bt, const OrasTopo& tp, const double* Bsurf, const double* KM,
-                         const double* eps, double k0, double ebr, double ebi, int prec, void* ws, cudaStream_t s) {
+                         const double* eps, double k0, double ebr, double ebi, const double2* zc, const uint8_t* metal,
+                         int prec, void* ws, cudaStream_t s) {
   note_launch(1);
   if (prec == 0)
-    local_assemble_kernel<double2><<<bt.count, 32, 0, s>>>(bt.d_sub, tp.dof_ptr, tp.tet_ptr, tp.tet_ids, tp.tet_loc,
-                                                            tp.surf_ptr, tp.surf_loc, tp.surf_tet, Bsurf, KM, eps, k0,
-                                                            ebr, ebi, bt.d_off, (double2*)ws);
+    local_assemble_kernel<double2><<<bt.count, 32, 0, s>>>(bt.d_sub, tp.dof_ptr, tp.dofs, tp.tet_ptr, tp.tet_ids,
+                                                            tp.tet_loc, tp.surf_ptr, tp.surf_loc, tp.surf_tet, Bsurf,
+                                                            KM, eps, k0, ebr, ebi, zc, metal, bt.d_off, (double2*)ws);
   else
-    local_assemble_kernel<float2><<<bt.count, 32, 0, s>>>(bt.d_sub, tp.dof_ptr, tp.tet_ptr, tp.tet_ids, tp.tet_loc,
-                                                           tp.surf_ptr, tp.surf_loc, tp.surf_tet, Bsurf, KM, eps, k0,
-                                                           ebr, ebi, bt.d_off, (float2*)ws);
+    local_assemble_kernel<float2><<<bt.count, 32, 0, s>>>(bt.d_sub, tp.dof_ptr, tp.dofs, tp.tet_ptr, tp.tet_ids,
+                                                           tp.tet_loc, tp.surf_ptr, tp.surf_loc, tp.surf_tet, Bsurf,
+                                                           KM, eps, k0, ebr, ebi, zc, metal, bt.d_off, (float2*)ws);
 }
 
 void oras_invert(const OrasBatch& bt, int prec, void* ws, void* dinv, int32_t* status, cudaStream_t s) {

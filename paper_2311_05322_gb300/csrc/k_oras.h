@@ -29,9 +29,11 @@ struct OrasBatch {
   const int64_t* d_off;   // [count] element offset of each matrix in the workspace
 };
 
+// zc (optional): coefficients of the outer-face classes (surf_tet = -1 - class); metal
+// (optional, [E]): edges whose local rows and columns become those of the identity.
 void oras_local_assemble(const OrasBatch& bt, const OrasTopo& tp, const double* Bsurf, const double* KM,
-                         const double* eps, double k0, double eps_bg_re, double eps_bg_im, int prec, void* ws,
-                         cudaStream_t s);
+                         const double* eps, double k0, double eps_bg_re, double eps_bg_im, const double2* zc,
+                         const uint8_t* metal, int prec, void* ws, cudaStream_t s);
 void oras_invert(const OrasBatch& bt, int prec, void* ws, void* dinv, int32_t* status, cudaStream_t s);
 void oras_extract(const OrasBatch& bt, const OrasTopo& tp, int ws_prec, const void* ws, int w_prec,
                   const int64_t* w_off, void* W, cudaStream_t s);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -189,10 +190,30 @@ struct Ctx {
   std::vector<float4*> Adf;    // double-float copy of A64 for the mixed solver's residual
 
   int n_src = 0;
-  std::vector<int32_t> src_edge;
+  std::vector<int32_t> src_edge;   // dipole sources: edge and sign of each
   std::vector<int8_t> src_sign;
-  int32_t* d_src_edge = nullptr;
-  int8_t* d_src_sign = nullptr;
+  // Sources as sparse vectors (dipoles: one entry each; ports: the port load vectors):
+  // CSR over sources (q_ptr, q_edge, q_w = w_j entries), norms n_j, the edge-major transpose
+  // (qt_ptr over distinct edges, qt_edge, and per pair the source and its entry index), and the
+  // right-hand-side coefficient of each source per frequency (b_j = c_fj w_j).
+  bool src_ports = false;
+  std::vector<int64_t> q_ptr_h;
+  int64_t *d_q_ptr = nullptr, *d_qt_ptr = nullptr;
+  int32_t *d_q_edge = nullptr, *d_qt_edge = nullptr, *d_qt_src = nullptr, *d_qt_k = nullptr;
+  double *d_q_w = nullptr, *d_q_norm = nullptr;
+  int64_t n_qt = 0;
+  std::vector<double2> src_coef;
+  double2* d_src_coef = nullptr;
+
+  // Boundary classes (waveguide ports and metal): empty = every boundary face open.
+  int n_port = 0;
+  std::vector<mw_port> ports;
+  std::vector<int32_t> bface_cls;   // [F_b] 0 open, 1 metal, 2 + p port p
+  std::vector<uint8_t> metal;       // [E] 1 = metal edge (empty: none)
+  int32_t* d_bface_cls = nullptr;
+  uint8_t *d_metal = nullptr, *d_nzmask = nullptr;
+  std::vector<double2> zc_h;        // [n_freq][2 + n_port] face-class coefficients
+  double2* d_zc = nullptr;
 
   Prec prec;
   Work work;
@@ -265,6 +286,30 @@ T* upload(Ctx* c, const T* h, size_t n) {
   T* d = dalloc<T>(c, n);
   if (n) CK(cudaMemcpyAsync(d, h, n * sizeof(T), cudaMemcpyHostToDevice, c->stream));
   return d;
+}
+
+// Uploads a host vector that may be empty (an empty one gets a one-element zeroed buffer).
+template <typename T>
+T* upload_vec(Ctx* c, const std::vector<T>& h) {
+  if (h.empty()) {
+    const std::vector<T> one(1, T{});
+    return upload(c, one.data(), 1);
+  }
+  return upload(c, h.data(), h.size());
+}
+
+// Copies h into d, reallocating d only when its size changes (keeps the address, and so any
+// captured graph that names it, across repeated uploads of the same size).
+template <typename T>
+void upload_reuse(Ctx* c, T*& d, const std::vector<T>& h) {
+  const size_t bytes = std::max<size_t>(h.size() * sizeof(T), 16);
+  auto it = d ? c->allocs.find((void*)d) : c->allocs.end();
+  if (!d || it == c->allocs.end() || it->second != bytes) {
+    dfree(c, d);
+    d = nullptr;
+    d = dalloc<T>(c, h.size());
+  }
+  if (!h.empty()) CK(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
 }
 
 template <typename F>
@@ -1008,10 +1053,132 @@ void solve_all(Ctx* c, const mw_solve_opts& o, int ncols, const std::vector<cons
                                std::to_string(mx) + ")"};
 }
 
-void build_dipole_rhs(Ctx* c, int f, double2* B) {
-  const double om = 2.0 * mw::kPi * c->freqs[f];
-  mwk::dipole_rhs(c->d_src_edge, c->d_src_sign, c->n_src, -om * mw::kMu0, B, c->topo.n_edge, c->stream);
-  check_launch("dipole rhs");
+// i beta of a TE10 port: beta = -i sqrt((pi/a)^2 - k0^2 eps_fill) (principal root), so
+// i beta = sqrt((pi/a)^2 - k0^2 eps_fill); eps_fill has im <= 0, so the radicand has im >= 0.
+double2 port_ibeta(const mw_port& p, double k0) {
+  const double kc = mw::kPi / p.a;
+  const double zr = kc * kc - k0 * k0 * p.eps_fill[0], zi = -k0 * k0 * p.eps_fill[1];
+  const double r = std::hypot(zr, zi);
+  return make_double2(std::sqrt(0.5 * (r + zr)), std::sqrt(std::max(0.0, 0.5 * (r - zr))));
+}
+
+// Right-hand-side coefficients c_fj of every source for every frequency: -i omega mu0 for a
+// dipole, 2 i beta_fj for a port (g = 2 i beta E^TE10).
+void upload_source_coefs(Ctx* c) {
+  const int ns = c->n_src, nf = c->n_freq;
+  const std::vector<double2> old = c->src_coef;
+  c->src_coef.assign((size_t)nf * ns, make_double2(0, 0));
+  for (int f = 0; f < nf; ++f)
+    for (int j = 0; j < ns; ++j) {
+      if (c->src_ports) {
+        const double2 ib = port_ibeta(c->ports[j], k0_of(c->freqs[f]));
+        c->src_coef[(size_t)f * ns + j] = make_double2(2.0 * ib.x, 2.0 * ib.y);
+      } else {
+        c->src_coef[(size_t)f * ns + j] = make_double2(0.0, -2.0 * mw::kPi * c->freqs[f] * mw::kMu0);
+      }
+    }
+  if (c->d_src_coef && old.size() == c->src_coef.size() &&
+      std::memcmp(old.data(), c->src_coef.data(), sizeof(double2) * old.size()) == 0)
+    return;  // unchanged: no copy, so a solve loop keeps its buffers and captured graphs
+  upload_reuse(c, c->d_src_coef, c->src_coef);
+}
+
+void build_source_rhs(Ctx* c, int f, double2* B) {
+  mwk::source_rhs(c->d_q_ptr, c->d_q_edge, c->d_q_w, c->d_src_coef + (size_t)f * c->n_src, c->n_src, B,
+                  c->topo.n_edge, c->stream);
+  check_launch("source rhs");
+}
+
+void free_sources(Ctx* c) {
+  for (void* q : {(void*)c->d_q_ptr, (void*)c->d_qt_ptr, (void*)c->d_q_edge, (void*)c->d_qt_edge, (void*)c->d_qt_src,
+                  (void*)c->d_qt_k, (void*)c->d_q_w, (void*)c->d_q_norm, (void*)c->d_src_coef})
+    dfree(c, q);
+  c->d_q_ptr = c->d_qt_ptr = nullptr;
+  c->d_q_edge = c->d_qt_edge = c->d_qt_src = c->d_qt_k = nullptr;
+  c->d_q_w = c->d_q_norm = nullptr;
+  c->d_src_coef = nullptr;
+  c->n_qt = 0;
+  c->q_ptr_h.clear();
+  for (auto p : c->Xf) dfree(c, p);
+  for (auto p : c->Lf) dfree(c, p);
+  for (auto p : c->Bfwd) dfree(c, p);
+  for (auto p : c->d_Badj) dfree(c, p);
+  c->Xf.clear();
+  c->Lf.clear();
+  c->Bfwd.clear();
+  c->d_Badj.clear();
+  c->n_src = 0;
+}
+
+// Installs n sources given as CSR (host ptr / edges) with entry values and norms already on
+// the device (ownership passes to the context); builds the edge-major transpose.
+void install_sources(Ctx* c, int n, bool ports, const std::vector<int64_t>& ptr, const std::vector<int32_t>& edge,
+                     double* d_w, double* d_norm) {
+  free_sources(c);
+  c->n_src = n;
+  c->src_ports = ports;
+  c->q_ptr_h = ptr;
+  c->d_q_ptr = upload(c, ptr.data(), ptr.size());
+  c->d_q_edge = upload_vec(c, edge);
+  c->d_q_w = d_w;
+  c->d_q_norm = d_norm;
+  // transpose: pairs (edge, source, entry) sorted by edge, then source
+  std::vector<std::array<int32_t, 3>> pr;
+  pr.reserve(edge.size());
+  for (int j = 0; j < n; ++j)
+    for (int64_t k = ptr[j]; k < ptr[j + 1]; ++k) pr.push_back({edge[k], j, (int32_t)k});
+  std::sort(pr.begin(), pr.end());
+  std::vector<int64_t> tptr(1, 0);
+  std::vector<int32_t> tedge, tsrc, tk;
+  for (size_t i = 0; i < pr.size(); ++i) {
+    if (i == 0 || pr[i][0] != pr[i - 1][0]) {
+      if (i) tptr.push_back((int64_t)i);
+      tedge.push_back(pr[i][0]);
+    }
+    tsrc.push_back(pr[i][1]);
+    tk.push_back(pr[i][2]);
+  }
+  if (!pr.empty()) tptr.push_back((int64_t)pr.size());
+  c->n_qt = (int64_t)tedge.size();
+  c->d_qt_ptr = upload(c, tptr.data(), tptr.size());
+  c->d_qt_edge = upload_vec(c, tedge);
+  c->d_qt_src = upload_vec(c, tsrc);
+  c->d_qt_k = upload_vec(c, tk);
+}
+
+// Face-class coefficient table [n_freq][2 + n_port]: i k0 sqrt(eps_bg) (open), 0 (metal),
+// i beta_p (port p), uploaded to d_zc.
+void upload_face_classes(Ctx* c, double si, double sr) {
+  if (c->bface_cls.empty()) return;
+  const int nc = 2 + c->n_port;
+  c->zc_h.assign((size_t)c->n_freq * nc, make_double2(0, 0));
+  for (int f = 0; f < c->n_freq; ++f) {
+    const double k0 = k0_of(c->freqs[f]);
+    c->zc_h[(size_t)f * nc] = make_double2(-k0 * si, k0 * sr);
+    for (int p = 0; p < c->n_port; ++p) c->zc_h[(size_t)f * nc + 2 + p] = port_ibeta(c->ports[p], k0);
+  }
+  upload_reuse(c, c->d_zc, c->zc_h);
+}
+
+// A_f for every frequency from d_eps (Eq. m2 with the boundary classes), plus its FP32 and
+// double-float copies.
+void reassemble_all(Ctx* c) {
+  const int64_t nnz = c->topo.nnz;
+  const double* eb = c->eps_bg;
+  const double r = std::hypot(eb[0], eb[1]);
+  const double sr = std::sqrt(0.5 * (r + eb[0]));
+  double si = std::sqrt(std::max(0.0, 0.5 * (r - eb[0])));
+  if (eb[1] < 0) si = -si;
+  upload_face_classes(c, si, sr);
+  const int nc = 2 + c->n_port;
+  for (int f = 0; f < c->n_freq; ++f) {
+    const double k0 = k0_of(c->freqs[f]);
+    mwk::reassemble(c->d_cptr, c->d_contrib, nnz, c->d_KM, c->d_Bf, c->d_eps, k0 * k0, -k0 * si, k0 * sr,
+                    c->d_bface_cls, c->d_zc ? c->d_zc + (size_t)f * nc : nullptr, c->d_nzmask, c->A64[f], c->A32[f],
+                    c->stream);
+    mwk::split_df(c->A64[f], c->Adf[f], nnz, c->stream);
+  }
+  check_launch("reassemble");
 }
 
 void alloc_fields(Ctx* c, std::vector<double2*>& v) {
@@ -1026,10 +1193,11 @@ void forward(Ctx* c, const mw_solve_opts& o, mw_solve_stats* stats) {
   require(c->has_mesh && c->n_freq > 0, MW_ESTATE, "assemble first");
   require(c->n_src > 0, MW_ESTATE, "set sources first");
   alloc_fields(c, c->Xf);
-  alloc_fields(c, c->Bfwd);   // dipole right-hand sides, kept between evaluations
+  alloc_fields(c, c->Bfwd);   // source right-hand sides, kept between evaluations
+  upload_source_coefs(c);
   std::vector<const double2*> Bs(c->n_freq);
   for (int f = 0; f < c->n_freq; ++f) {
-    build_dipole_rhs(c, f, c->Bfwd[f]);
+    build_source_rhs(c, f, c->Bfwd[f]);
     Bs[f] = c->Bfwd[f];
   }
   solve_all(c, o, c->n_src, Bs, c->Xf, stats);
@@ -1067,7 +1235,8 @@ void release_mesh(Ctx* c) {
   for (void* q : {(void*)c->d_xyz, (void*)c->d_tets, (void*)c->d_col, (void*)c->d_contrib, (void*)c->d_bface_vert,
                   (void*)c->d_tet_edge, (void*)c->d_tet_nb, (void*)c->d_sign, (void*)c->d_row, (void*)c->d_cptr,
                   (void*)c->d_KM, (void*)c->d_vol, (void*)c->d_Bf, (void*)c->d_tikw, (void*)c->d_eps,
-                  (void*)c->d_src_edge, (void*)c->d_src_sign, (void*)c->d_B, (void*)c->d_red, (void*)c->d_S,
+                  (void*)c->d_bface_cls, (void*)c->d_metal, (void*)c->d_nzmask, (void*)c->d_zc, (void*)c->d_B,
+                  (void*)c->d_red, (void*)c->d_S,
                   (void*)c->d_C, (void*)c->d_So, (void*)c->d_Se, (void*)c->d_J, (void*)c->d_grad, (void*)c->d_gR})
     dfree(c, q);
   for (auto p : c->d_Badj) dfree(c, p);
@@ -1079,14 +1248,105 @@ void release_mesh(Ctx* c) {
   c->d_sign = nullptr;
   c->d_row = c->d_cptr = nullptr;
   c->d_KM = c->d_vol = c->d_Bf = c->d_tikw = c->d_eps = nullptr;
-  c->d_src_edge = nullptr;
-  c->d_src_sign = nullptr;
+  c->d_bface_cls = nullptr;
+  c->d_metal = c->d_nzmask = nullptr;
+  c->d_zc = nullptr;
+  free_sources(c);
+  c->src_edge.clear();
+  c->src_sign.clear();
+  c->src_ports = false;
+  c->n_port = 0;
+  c->ports.clear();
+  c->bface_cls.clear();
+  c->metal.clear();
+  c->zc_h.clear();
   c->d_B = nullptr;
   c->d_red = nullptr;
   c->has_mesh = false;
   c->n_freq = 0;
-  c->n_src = 0;
 }
+
+// Drops the assembled matrices, the preconditioner and every stored field (the boundary
+// changed: assemble again).
+void drop_assembly(Ctx* c) {
+  drop_graphs(c);
+  release_prec(c);
+  for (auto p : c->A64) dfree(c, p);
+  for (auto p : c->A32) dfree(c, p);
+  for (auto p : c->Adf) dfree(c, p);
+  c->A64.clear();
+  c->A32.clear();
+  c->Adf.clear();
+  for (auto p : c->Xf) dfree(c, p);
+  for (auto p : c->Lf) dfree(c, p);
+  for (auto p : c->Bfwd) dfree(c, p);
+  for (auto p : c->d_Badj) dfree(c, p);
+  c->Xf.clear();
+  c->Lf.clear();
+  c->Bfwd.clear();
+  c->d_Badj.clear();
+  c->n_freq = 0;
+}
+
+// Boundary face with sorted vertices (a, b, c): index into bface_vert (sorted triples), or -1.
+int64_t find_bface(const mw::Topology& t, int32_t a, int32_t b, int32_t cc) {
+  int64_t lo = 0, hi = t.n_bface;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    const int32_t* q = t.bface_vert.data() + 3 * mid;
+    const bool less = q[0] != a ? q[0] < a : (q[1] != b ? q[1] < b : q[2] < cc);
+    if (less)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo < t.n_bface) {
+    const int32_t* q = t.bface_vert.data() + 3 * lo;
+    if (q[0] == a && q[1] == b && q[2] == cc) return lo;
+  }
+  return -1;
+}
+
+// Edge (lo, hi), lo < hi: its id (the rank of the pair in lexicographic order), or -1.
+int64_t find_edge_id(const mw::Topology& t, int32_t a, int32_t b) {
+  int64_t lo = 0, hi = t.n_edge;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    const int32_t* q = t.edge_vert.data() + 2 * mid;
+    if (q[0] < a || (q[0] == a && q[1] < b))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo < t.n_edge && t.edge_vert[2 * lo] == a && t.edge_vert[2 * lo + 1] == b) return lo;
+  return -1;
+}
+
+// Gauss-Legendre nodes and weights mapped to [0, 1]: Newton's method on P_n from the
+// three-term recurrence (n P_n = (2n - 1) z P_{n-1} - (n - 1) P_{n-2}).
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(mw::kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) <= 1e-16) break;
+    }
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);  // (2 / ((1 - z^2) P_n'^2)) / 2
+  }
+}
+
+constexpr int kPortQuad = 10;  // collapsed Gauss-Legendre points per direction on port faces
 
 }  // namespace mwimpl
 
@@ -1324,18 +1584,7 @@ mw_status mw_assemble(mw_ctx* c, int32_t n_freq, const double* freq_hz, const do
     c->eps_bg[1] = eps_bg[1];
     if (!c->d_eps) c->d_eps = dalloc<double>(c, 2 * T);
     CK(cudaMemcpyAsync(c->d_eps, eps_r, sizeof(double) * 2 * T, cudaMemcpyHostToDevice, c->stream));
-    // i k0 sqrt(eps_bg): principal square root
-    const double r = std::hypot(eps_bg[0], eps_bg[1]);
-    const double sr = std::sqrt(0.5 * (r + eps_bg[0]));
-    double si = std::sqrt(std::max(0.0, 0.5 * (r - eps_bg[0])));
-    if (eps_bg[1] < 0) si = -si;
-    for (int f = 0; f < n_freq; ++f) {
-      const double k0 = k0_of(freq_hz[f]);
-      mwk::reassemble(c->d_cptr, c->d_contrib, nnz, c->d_KM, c->d_Bf, c->d_eps, k0 * k0, -k0 * si, k0 * sr, c->A64[f],
-                      c->A32[f], c->stream);
-      mwk::split_df(c->A64[f], c->Adf[f], nnz, c->stream);
-    }
-    check_launch("reassemble");
+    reassemble_all(c);
   });
 }
 
@@ -1410,21 +1659,239 @@ mw_status mw_set_sources(mw_ctx* c, int32_t n_src, const double* pos, const doub
       c->src_edge[j] = be;
       c->src_sign[j] = ((b[2] - a[2]) * dir[3 * j + 2] > 0) ? 1 : -1;
     }
-    c->n_src = n_src;
-    dfree(c, c->d_src_edge);
-    dfree(c, c->d_src_sign);
-    c->d_src_edge = upload(c, c->src_edge.data(), n_src);
-    c->d_src_sign = upload(c, c->src_sign.data(), n_src);
-    for (auto p : c->Xf) dfree(c, p);
-    for (auto p : c->Lf) dfree(c, p);
-    for (auto p : c->Bfwd) dfree(c, p);
-    for (auto p : c->d_Badj) dfree(c, p);
-    c->Xf.clear();
-    c->Lf.clear();
-    c->Bfwd.clear();
-    c->d_Badj.clear();
+    // one-entry source vectors w_j = s_j e_edge(j), norms 1
+    std::vector<int64_t> ptr(n_src + 1);
+    std::vector<double> w(n_src), nrm(n_src, 1.0);
+    for (int j = 0; j <= n_src; ++j) ptr[j] = j;
+    for (int j = 0; j < n_src; ++j) w[j] = (double)c->src_sign[j];
+    double* d_w = upload(c, w.data(), w.size());
+    double* d_n = nullptr;
+    try {
+      d_n = upload(c, nrm.data(), nrm.size());
+      install_sources(c, n_src, false, ptr, c->src_edge, d_w, d_n);
+    } catch (...) {
+      if (c->d_q_w != d_w) dfree(c, d_w);
+      if (c->d_q_norm != d_n) dfree(c, d_n);
+      throw;
+    }
     if (edge_out) std::memcpy(edge_out, c->src_edge.data(), sizeof(int32_t) * n_src);
     if (sign_out) std::memcpy(sign_out, c->src_sign.data(), n_src);
+  });
+}
+
+mw_status mw_set_ports(mw_ctx* c, int32_t n_port, const mw_port* ports, int64_t n_face, const int32_t* face_vert,
+                       const int32_t* face_label) {
+  return guard(c, [&] {
+    require(c->has_mesh, MW_ESTATE, "set the mesh first");
+    require(n_port >= 0 && n_port <= 4096 && n_face >= 0 && (n_port == 0 || ports) &&
+                (n_face == 0 || (face_vert && face_label)),
+            MW_EINVAL, "bad port arguments");
+    const mw::Topology& t = c->topo;
+    for (int p = 0; p < n_port; ++p) {
+      const mw_port& q = ports[p];
+      bool fin = std::isfinite(q.a) && std::isfinite(q.eps_fill[0]) && std::isfinite(q.eps_fill[1]);
+      for (int k = 0; k < 3; ++k) fin = fin && std::isfinite(q.origin[k]) && std::isfinite(q.u[k]) && std::isfinite(q.v[k]);
+      require(fin, MW_EINVAL, "non-finite port descriptor");
+      require(q.a > 0, MW_EINVAL, "port width a must be > 0");
+      require(q.eps_fill[1] <= 0, MW_EINVAL, "port filling must be passive (Im eps_fill <= 0)");
+      const double uu = q.u[0] * q.u[0] + q.u[1] * q.u[1] + q.u[2] * q.u[2];
+      const double vv = q.v[0] * q.v[0] + q.v[1] * q.v[1] + q.v[2] * q.v[2];
+      const double uv = q.u[0] * q.v[0] + q.u[1] * q.v[1] + q.u[2] * q.v[2];
+      require(std::fabs(uu - 1) <= 1e-9 && std::fabs(vv - 1) <= 1e-9 && std::fabs(uv) <= 1e-9, MW_EINVAL,
+              "port directions u, v must be orthonormal");
+    }
+    // vertex -> tets, to check that a listed inner face is a face of the mesh
+    const int64_t V = t.n_vert, T = t.n_tet, E = t.n_edge;
+    std::vector<int64_t> vtp(V + 1, 0);
+    for (int64_t i = 0; i < 4 * T; ++i) vtp[t.tets[i] + 1]++;
+    for (int64_t v = 0; v < V; ++v) vtp[v + 1] += vtp[v];
+    std::vector<int32_t> vt(4 * T);
+    {
+      std::vector<int64_t> fill(vtp.begin(), vtp.end() - 1);
+      for (int64_t i = 0; i < 4 * T; ++i) vt[fill[t.tets[i]]++] = (int32_t)(i / 4);
+    }
+    std::vector<int32_t> cls(t.n_bface, 0);
+    std::vector<uint8_t> set(t.n_bface, 0), metal(E, 0);
+    bool any_metal = false;
+    for (int64_t k = 0; k < n_face; ++k) {
+      int32_t a = face_vert[3 * k], b = face_vert[3 * k + 1], d = face_vert[3 * k + 2];
+      require(a >= 0 && a < V && b >= 0 && b < V && d >= 0 && d < V, MW_EINVAL, "face vertex out of range");
+      if (a > b) std::swap(a, b);
+      if (b > d) std::swap(b, d);
+      if (a > b) std::swap(a, b);
+      require(a < b && b < d, MW_EINVAL, "face with repeated vertices");
+      const int32_t lab = face_label[k];
+      require(lab >= -1 && lab < n_port, MW_EINVAL, "face label out of range");
+      const int64_t bf = find_bface(t, a, b, d);
+      if (bf < 0) {
+        require(lab == -1, MW_EINVAL, "a port face is not a boundary face");
+        bool found = false;
+        for (int64_t q = vtp[a]; q < vtp[a + 1] && !found; ++q) {
+          const int32_t* tv = &t.tets[4 * (int64_t)vt[q]];
+          bool hb = false, hd = false;
+          for (int m = 0; m < 4; ++m) {
+            hb = hb || tv[m] == b;
+            hd = hd || tv[m] == d;
+          }
+          found = hb && hd;
+        }
+        require(found, MW_EINVAL, "listed face is not a face of the mesh");
+      } else {
+        const int32_t cv = lab == -1 ? 1 : 2 + lab;
+        require(!set[bf] || cls[bf] == cv, MW_EINVAL, "face listed twice with different labels");
+        set[bf] = 1;
+        cls[bf] = cv;
+      }
+      if (lab == -1) {
+        any_metal = true;
+        metal[find_edge_id(t, a, b)] = 1;
+        metal[find_edge_id(t, a, d)] = 1;
+        metal[find_edge_id(t, b, d)] = 1;
+      }
+    }
+    // faces of each port, in boundary-face order; entries (port, edge) with their face moments
+    std::vector<int64_t> fptr(n_port + 1, 0);
+    for (int64_t f = 0; f < t.n_bface; ++f)
+      if (cls[f] >= 2) fptr[cls[f] - 2 + 1]++;
+    for (int p = 0; p < n_port; ++p) {
+      require(fptr[p + 1] > 0, MW_EINVAL, "a port has no face");
+      fptr[p + 1] += fptr[p];
+    }
+    const int64_t Fp = fptr[n_port];
+    std::vector<int32_t> pfv(3 * Fp), pport(Fp);
+    std::vector<int64_t> pbf(Fp);
+    {
+      std::vector<int64_t> fill(fptr.begin(), fptr.end() - 1);
+      for (int64_t f = 0; f < t.n_bface; ++f)
+        if (cls[f] >= 2) {
+          const int64_t i = fill[cls[f] - 2]++;
+          pbf[i] = f;
+          pport[i] = cls[f] - 2;
+          for (int m = 0; m < 3; ++m) pfv[3 * i + m] = t.bface_vert[3 * f + m];
+        }
+    }
+    std::vector<int64_t> qptr(1, 0), eptr(1, 0);
+    std::vector<int32_t> qedge, econ;
+    for (int p = 0; p < n_port; ++p) {
+      std::vector<std::pair<int32_t, int32_t>> pr;  // (edge, moment index) in face order
+      for (int64_t i = fptr[p]; i < fptr[p + 1]; ++i)
+        for (int m = 0; m < 3; ++m) pr.push_back({t.bface_edge[3 * pbf[i] + m], (int32_t)(3 * i + m)});
+      std::stable_sort(pr.begin(), pr.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+      for (size_t i = 0; i < pr.size(); ++i) {
+        if (metal[pr[i].first]) continue;
+        if (qedge.empty() || (int64_t)qedge.size() == qptr.back() || qedge.back() != pr[i].first) {
+          qedge.push_back(pr[i].first);
+          eptr.push_back(eptr.back());
+        }
+        econ.push_back(pr[i].second);
+        eptr.back()++;
+      }
+      qptr.push_back((int64_t)qedge.size());
+    }
+    // identity rows and columns of metal edges
+    std::vector<uint8_t> nzm;
+    if (any_metal) {
+      nzm.assign(t.nnz, 0);
+      for (int64_t r = 0; r < E; ++r)
+        for (int64_t k = t.row_ptr[r]; k < t.row_ptr[r + 1]; ++k) {
+          const int32_t col = t.col_idx[k];
+          if (metal[r] || metal[col]) nzm[k] = col == r ? 2 : 1;
+        }
+    }
+    // commit: the boundary changed, so everything assembled from it goes
+    drop_assembly(c);
+    for (void* q : {(void*)c->d_bface_cls, (void*)c->d_metal, (void*)c->d_nzmask, (void*)c->d_zc}) dfree(c, q);
+    c->d_bface_cls = nullptr;
+    c->d_metal = c->d_nzmask = nullptr;
+    c->d_zc = nullptr;
+    c->n_port = n_port;
+    c->ports.assign(ports, ports + n_port);
+    const bool any_class = n_face > 0;
+    c->bface_cls = any_class ? cls : std::vector<int32_t>();
+    c->metal = any_metal ? metal : std::vector<uint8_t>();
+    if (any_class) c->d_bface_cls = upload(c, cls.data(), cls.size());
+    if (any_metal) {
+      c->d_metal = upload(c, metal.data(), metal.size());
+      c->d_nzmask = upload(c, nzm.data(), nzm.size());
+    }
+    if (c->src_ports) free_sources(c);  // the previous ports' sources are stale
+    if (n_port == 0) return;
+    // port load vectors and norms on the device
+    std::vector<double> pdesc(10 * n_port), gx, gw;
+    for (int p = 0; p < n_port; ++p) {
+      for (int k = 0; k < 3; ++k) {
+        pdesc[10 * p + k] = ports[p].origin[k];
+        pdesc[10 * p + 3 + k] = ports[p].u[k];
+        pdesc[10 * p + 6 + k] = ports[p].v[k];
+      }
+      pdesc[10 * p + 9] = ports[p].a;
+    }
+    gauss_legendre01(kPortQuad, gx, gw);
+    std::vector<void*> tmp;
+    double* d_w = nullptr;
+    double* d_n = nullptr;
+    try {
+      int32_t* d_fv = upload(c, pfv.data(), pfv.size());
+      tmp.push_back(d_fv);
+      int32_t* d_fp = upload(c, pport.data(), pport.size());
+      tmp.push_back(d_fp);
+      double* d_pd = upload(c, pdesc.data(), pdesc.size());
+      tmp.push_back(d_pd);
+      double* d_gx = upload(c, gx.data(), gx.size());
+      tmp.push_back(d_gx);
+      double* d_gw = upload(c, gw.data(), gw.size());
+      tmp.push_back(d_gw);
+      double* d_mom = dalloc<double>(c, 3 * Fp);
+      tmp.push_back(d_mom);
+      double* d_nrm = dalloc<double>(c, Fp);
+      tmp.push_back(d_nrm);
+      int64_t* d_eptr = upload(c, eptr.data(), eptr.size());
+      tmp.push_back(d_eptr);
+      int32_t* d_econ = upload_vec(c, econ);
+      tmp.push_back(d_econ);
+      int64_t* d_fptr = upload(c, fptr.data(), fptr.size());
+      tmp.push_back(d_fptr);
+      d_w = dalloc<double>(c, std::max<size_t>(qedge.size(), 1));
+      d_n = dalloc<double>(c, n_port);
+      mwk::port_face_moments(c->d_xyz, d_fv, d_fp, Fp, d_pd, d_gx, d_gw, kPortQuad, d_mom, d_nrm, c->stream);
+      mwk::port_accumulate(d_eptr, d_econ, (int64_t)qedge.size(), d_mom, d_w, d_fptr, n_port, d_nrm, d_n, c->stream);
+      check_launch("port vectors");
+      std::vector<double> nh(n_port);
+      CK(cudaMemcpyAsync(nh.data(), d_n, sizeof(double) * n_port, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      for (int p = 0; p < n_port; ++p)
+        require(std::isfinite(nh[p]) && nh[p] > 0, MW_EINVAL, "a port mode has zero norm on its faces");
+      for (void* q : tmp) dfree(c, q);
+      tmp.clear();
+      install_sources(c, n_port, true, qptr, qedge, d_w, d_n);
+    } catch (...) {
+      for (void* q : tmp) dfree(c, q);
+      if (c->d_q_w != d_w) dfree(c, d_w);
+      if (c->d_q_norm != d_n) dfree(c, d_n);
+      throw;
+    }
+    c->src_edge.clear();
+    c->src_sign.clear();
+  });
+}
+
+mw_status mw_get_port_vectors(mw_ctx* c, double* W, double* norms) {
+  return guard(c, [&] {
+    require(c->has_mesh && c->src_ports && c->n_src > 0, MW_ESTATE, "no port sources");
+    const int P = c->n_src;
+    const int64_t nq = c->q_ptr_h.back(), E = c->topo.n_edge;
+    std::vector<double> w(std::max<int64_t>(nq, 1)), nh(P);
+    std::vector<int32_t> edge(std::max<int64_t>(nq, 1));
+    CK(cudaMemcpyAsync(w.data(), c->d_q_w, sizeof(double) * nq, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(edge.data(), c->d_q_edge, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(nh.data(), c->d_q_norm, sizeof(double) * P, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (W) {
+      std::fill(W, W + E * P, 0.0);
+      for (int p = 0; p < P; ++p)
+        for (int64_t k = c->q_ptr_h[p]; k < c->q_ptr_h[p + 1]; ++k) W[(int64_t)edge[k] * P + p] = w[k];
+    }
+    if (norms) std::memcpy(norms, nh.data(), sizeof(double) * P);
   });
 }
 
@@ -1454,7 +1921,19 @@ mw_status mw_setup_preconditioner(mw_ctx* c, int32_t n_sub, const int32_t* part,
     p.tet_loc = upload(c, sd.tet_loc.data(), sd.tet_loc.size());
     p.surf_ptr = upload(c, sd.surf_ptr.data(), sd.surf_ptr.size());
     p.surf_loc = upload(c, sd.surf_loc.data(), sd.surf_loc.size());
-    p.surf_tet = upload(c, sd.surf_tet.data(), sd.surf_tet.size());
+    {
+      // outer faces carry their boundary class when classes are set: code -1 - class
+      std::vector<int32_t> code(sd.surf_tet);
+      if (!c->bface_cls.empty())
+        for (size_t q = 0; q < code.size(); ++q)
+          if (code[q] < 0) {
+            const int32_t* v = &sd.surf_vert[3 * q];
+            const int64_t bf = find_bface(c->topo, v[0], v[1], v[2]);
+            require(bf >= 0, MW_EINVAL, "subdomain outer face is not a boundary face");
+            code[q] = -1 - c->bface_cls[bf];
+          }
+      p.surf_tet = upload(c, code.data(), code.size());
+    }
     p.surf_vert = upload(c, sd.surf_vert.data(), sd.surf_vert.size());
     const int64_t n_surf = (int64_t)sd.surf_tet.size();
     p.Bsurf = dalloc<double>(c, 6 * std::max<int64_t>(n_surf, 1));
@@ -1530,8 +2009,9 @@ mw_status mw_setup_preconditioner(mw_ctx* c, int32_t n_sub, const int32_t* part,
           CK(cudaMemcpyAsync(d_boff, boff.data(), sizeof(int64_t) * cnt, cudaMemcpyHostToDevice, c->stream));
           mwk::OrasBatch bt{cnt, bmax, d_bsub, d_bn, d_boff};
           CK(cudaMemsetAsync(ws, 0, used, c->stream));
-          mwk::oras_local_assemble(bt, p.topo(), p.Bsurf, c->d_KM, c->d_eps, k0, c->eps_bg[0], c->eps_bg[1],
-                                   p.factor_prec, ws, c->stream);
+          const double2* zc = c->d_zc ? c->d_zc + (size_t)f * (2 + c->n_port) : nullptr;
+          mwk::oras_local_assemble(bt, p.topo(), p.Bsurf, c->d_KM, c->d_eps, k0, c->eps_bg[0], c->eps_bg[1], zc,
+                                   c->d_metal, p.factor_prec, ws, c->stream);
           mwk::oras_invert(bt, p.factor_prec, ws, dinv, d_status, c->stream);
           if (p.apply_prec == 2)
             mwk::tc_extract(p.tc, bt, p.topo(), p.factor_prec, ws, p.W[f], c->stream);
@@ -1617,8 +2097,8 @@ mw_status mw_solve(mw_ctx* c, const mw_solve_opts* opts, void* fields, double* S
     if (S) {
       double2* dS = dalloc<double2>(c, (size_t)c->n_freq * c->n_src * c->n_src);
       for (int f = 0; f < c->n_freq; ++f)
-        mwk::s_extract(c->Xf[f], c->d_src_edge, c->d_src_sign, c->n_src, dS + (size_t)f * c->n_src * c->n_src,
-                       c->stream);
+        mwk::s_project(c->Xf[f], c->d_q_ptr, c->d_q_edge, c->d_q_w, c->d_q_norm, c->n_src,
+                       dS + (size_t)f * c->n_src * c->n_src, c->stream);
       CK(cudaMemcpyAsync(S, dS, sizeof(double2) * c->n_freq * c->n_src * c->n_src, cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
       dfree(c, dS);
@@ -1717,11 +2197,13 @@ static void gradient_dev_impl(Ctx* c, const mw_solve_opts& o, const double2* dSo
     for (int f = 0; f < nf; ++f) c->d_Badj[f] = dalloc<double2>(c, E * ns);
   }
   for (int f = 0; f < nf; ++f)
-    mwk::s_extract(c->Xf[f], c->d_src_edge, c->d_src_sign, ns, c->d_S + (size_t)f * ns * ns, c->stream);
+    mwk::s_project(c->Xf[f], c->d_q_ptr, c->d_q_edge, c->d_q_w, c->d_q_norm, ns, c->d_S + (size_t)f * ns * ns,
+                   c->stream);
   mwk::adjoint_weights(c->d_S, dSo, dSe, (int64_t)nS, c->d_C, c->d_J, c->stream);
   std::vector<const double2*> Bc(nf);
   for (int f = 0; f < nf; ++f) {
-    mwk::adjoint_rhs(c->d_src_edge, c->d_src_sign, ns, c->d_C + (size_t)f * ns * ns, c->d_Badj[f], E, c->stream);
+    mwk::adjoint_sources(c->d_qt_ptr, c->d_qt_edge, c->d_qt_src, c->d_qt_k, c->n_qt, c->d_q_w, c->d_q_norm,
+                         c->d_C + (size_t)f * ns * ns, ns, c->d_Badj[f], E, c->stream);
     Bc[f] = c->d_Badj[f];
   }
   check_launch("adjoint sources");
@@ -2023,20 +2505,10 @@ mw_status mw_assemble_dev(mw_ctx* c, int32_t n_freq, const double* freq_hz, cons
             "assemble_dev needs a prior host assemble with the same frequency count");
     const int64_t T = c->topo.n_tet, nnz = c->topo.nnz;
     CK(cudaMemcpyAsync(c->d_eps, eps_dev, sizeof(double) * 2 * T, cudaMemcpyDeviceToDevice, c->stream));
-    const double r = std::hypot(eps_bg[0], eps_bg[1]);
-    const double sr = std::sqrt(0.5 * (r + eps_bg[0]));
-    double si = std::sqrt(std::max(0.0, 0.5 * (r - eps_bg[0])));
-    if (eps_bg[1] < 0) si = -si;
     c->freqs.assign(freq_hz, freq_hz + n_freq);
     c->eps_bg[0] = eps_bg[0];
     c->eps_bg[1] = eps_bg[1];
-    for (int f = 0; f < n_freq; ++f) {
-      const double k0 = k0_of(freq_hz[f]);
-      mwk::reassemble(c->d_cptr, c->d_contrib, nnz, c->d_KM, c->d_Bf, c->d_eps, k0 * k0, -k0 * si, k0 * sr, c->A64[f],
-                      c->A32[f], c->stream);
-      mwk::split_df(c->A64[f], c->Adf[f], nnz, c->stream);
-    }
-    check_launch("reassemble");
+    reassemble_all(c);
   });
 }
 

@@ -97,9 +97,11 @@ void face_geom(const double* xyz, const int32_t* face_vert, int64_t F, double* B
 void tikhonov_weights(const double* xyz, const int32_t* tets, const int32_t* tet_nb, int64_t T, double* w,
                       cudaStream_t s);
 // K2 reassembly for one frequency: A64/A32 [nnz].
+// fcls [F_b] (optional): face class 0 open, 1 metal, 2 + p port p, with coefficients zc [2 + P];
+// nzmask [nnz] (optional): 1 = zero the entry, 2 = set it to one (metal rows and columns).
 void reassemble(const int64_t* cptr, const int32_t* contrib, int64_t nnz, const double* KM, const double* Bf,
-                const double* eps, double k0sq, double zb_re, double zb_im, double2* A64, float2* A32,
-                cudaStream_t s);
+                const double* eps, double k0sq, double zb_re, double zb_im, const int32_t* fcls, const double2* zc,
+                const uint8_t* nzmask, double2* A64, float2* A32, cudaStream_t s);
 // K3 SpMM: Y = A X, [E][R] layout with leading dimension ld (>= R).
 // threads: block size, 128, 256 (default) or 512 (the result does not depend on it).
 void spmm_f64(const int64_t* rp, const int32_t* ci, const double2* A, const double2* X, double2* Y, int64_t E,
@@ -185,7 +187,15 @@ void transpose_in(const double2* src, double2* dst, int64_t E, int R, cudaStream
 void transpose_out(const double2* src, double2* dst, int64_t E, int R, cudaStream_t s);
 
 // sources
-void dipole_rhs(const int32_t* edge, const int8_t* sign, int n_src, double scale_im, double2* B, int64_t E,
-                cudaStream_t s);
+// B [E][ns] = 0, then B[edge_k][j] = coef_j w_k for the entries k of source j (CSR ptr [ns+1]).
+void source_rhs(const int64_t* ptr, const int32_t* edge, const double* w, const double2* coef, int ns, double2* B,
+                int64_t E, cudaStream_t s);
+// Port face moments: fv [F][3] sorted vertex ids, fport [F] port of each face, pdesc [P][10]
+// (origin, u, v, a); outputs mom [F][3] and nrm [F].
+void port_face_moments(const double* xyz, const int32_t* fv, const int32_t* fport, int64_t F, const double* pdesc,
+                       const double* gx, const double* gw, int nq, double* mom, double* nrm, cudaStream_t s);
+// w[k] = sum of mom[econ[eptr[k] .. eptr[k+1])]; pn[p] = sum of nrm[fptr[p] .. fptr[p+1]).
+void port_accumulate(const int64_t* eptr, const int32_t* econ, int64_t n_ent, const double* mom, double* w,
+                     const int64_t* fptr, int n_port, const double* nrm, double* pn, cudaStream_t s);
 
 }  // namespace mwk

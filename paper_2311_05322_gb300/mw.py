@@ -32,6 +32,11 @@ class mw_mesh_info(C.Structure):
                 ("n_bface", C.c_int64), ("nnz", C.c_int64)]
 
 
+class mw_port(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("u", C.c_double * 3), ("v", C.c_double * 3), ("a", C.c_double),
+                ("eps_fill", C.c_double * 2)]
+
+
 class mw_solve_opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("restart", C.c_int32), ("batch", C.c_int32), ("max_it", C.c_int32),
                 ("tol", C.c_double), ("inner_tol", C.c_double), ("max_outer", C.c_int32),
@@ -93,6 +98,8 @@ _SIGS = {
     "mw_get_matrix": (C.c_int32, [_P, C.c_int32, _P]),
     "mw_apply_matrix": (C.c_int32, [_P, C.c_int32, C.c_int32, _P, _P, C.c_int32]),
     "mw_set_sources": (C.c_int32, [_P, C.c_int32, _P, _P, _P, _P]),
+    "mw_set_ports": (C.c_int32, [_P, C.c_int32, C.POINTER(mw_port), C.c_int64, _P, _P]),
+    "mw_get_port_vectors": (C.c_int32, [_P, _P, _P]),
     "mw_setup_preconditioner": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, C.c_int32]),
     "mw_apply_preconditioner": (C.c_int32, [_P, C.c_int32, _P, _P, C.c_int32]),
     "mw_get_partition": (C.c_int32, [_P, _P, _P]),
@@ -278,6 +285,30 @@ class Context:
         self.n_src = n
         self.src_edges, self.src_signs = e, s
         return e, s
+
+    def set_ports(self, origin, u, v, a, eps_fill, face_vert, face_label):
+        """Waveguide ports and metal faces (mw_set_ports): per-port origin/u/v [P, 3], width a [P],
+        filling eps_fill [P] complex; faces [n, 3] with labels -1 (metal) or the port index."""
+        a = np.atleast_1d(np.asarray(a, dtype=np.float64))
+        P = a.shape[0]
+        arr = (mw_port * max(P, 1))()
+        for p in range(P):
+            e = complex(np.atleast_1d(eps_fill)[p])
+            arr[p] = mw_port((C.c_double * 3)(*np.asarray(origin[p], float)), (C.c_double * 3)(*np.asarray(u[p], float)),
+                             (C.c_double * 3)(*np.asarray(v[p], float)), float(a[p]), (C.c_double * 2)(e.real, e.imag))
+        fv = _c(np.asarray(face_vert).reshape(-1, 3), np.int32)
+        lab = _c(face_label, np.int32)
+        assert lab.shape[0] == fv.shape[0]
+        self._check(self.lib.mw_set_ports(self.h, P, arr, fv.shape[0], _ptr(fv), _ptr(lab)))
+        if P:
+            self.n_src = P
+        self.n_freq = 0
+
+    def get_port_vectors(self):
+        W = np.empty((self.info.n_edge, self.n_src))
+        n = np.empty(self.n_src)
+        self._check(self.lib.mw_get_port_vectors(self.h, _ptr(W), _ptr(n)))
+        return W, n
 
     # -- preconditioner -------------------------------------------------------------------
     def setup_preconditioner(self, n_sub: int, tet_part: np.ndarray, overlap: int, inv_prec: int):

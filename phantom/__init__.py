@@ -333,6 +333,93 @@ def waveguide_section(cells=(8, 4, 12), a: float = 0.02, b: float = 0.01, length
     return m, fv, lab.astype(np.int32), ports
 
 
+EPS_CERAMIC = 59.0 - 0.6j   # filling of the waveguide antennas
+
+
+def _cell_range_faces(mesh: Mesh, axis: int, idx: int, rng2) -> np.ndarray:
+    """Faces on the grid plane axis = idx (a vertex-index plane) within the cell-index ranges
+    rng2 = ((i0, i1), (j0, j1)) of the two other axes (increasing axis order)."""
+    lo, hi = np.asarray(mesh.lo), np.asarray(mesh.hi)
+    h = (hi - lo) / np.array([mesh.nx, mesh.ny, mesh.nz])
+    others = [d for d in range(3) if d != axis]
+    return faces_on_plane(mesh, axis, lo[axis] + idx * h[axis],
+                          [lo[others[k]] + rng2[k][0] * h[others[k]] for k in range(2)],
+                          [lo[others[k]] + rng2[k][1] * h[others[k]] for k in range(2)])
+
+
+def _setdiff_rows(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    if b.size == 0:
+        return a
+    keep = ~(a[:, None, :] == b[None, :, :]).all(axis=2).any(axis=1)
+    return a[keep]
+
+
+def port_chamber(mesh: Mesh, n_per_wall: int = 8, a_cells: int = 5, b_cells: int = 2, depth: int = 4,
+                 eps_fill: complex = EPS_CERAMIC):
+    """A ring of rectangular waveguide antennas on the four side walls of a Kuhn box.
+
+    Each guide is a stub of a_cells x b_cells cells (broad side horizontal along its wall,
+    narrow side vertical, centred in z) reaching `depth` cells into the box from its wall, filled
+    with eps_fill.  Its four side walls are metal sheets inside the mesh, its back face on the
+    box wall is the port, and its front opening is open to the box.  The rest of the four side
+    walls is metal; the bottom and top faces stay open.  Guides are evenly spaced along each
+    wall; walls in the order x = lo, x = hi, y = lo, y = hi.
+    Returns (face_vert [n, 3], label [n] (-1 metal, p port), PortSet, guide tet mask [T]).
+    """
+    n = (mesh.nx, mesh.ny, mesh.nz)
+    lo, hi = np.asarray(mesh.lo), np.asarray(mesh.hi)
+    h = (hi - lo) / np.array(n)
+    z0 = (n[2] - b_cells) // 2
+    z1 = z0 + b_cells
+    cen = mesh.centroids()
+    cell = np.floor((cen - lo) / h).astype(np.int64)
+    guide = np.zeros(mesh.n_tet, dtype=bool)
+    metal, port_faces, origin, u, width = [], [], [], [], []
+    for wall, (ax, side) in enumerate([(0, 0), (0, 1), (1, 0), (1, 1)]):
+        t = 1 - ax                                   # horizontal axis along this wall
+        wall_idx = 0 if side == 0 else n[ax]
+        d0, d1 = (0, depth) if side == 0 else (n[ax] - depth, n[ax])
+        # full side wall (cell ranges over the two other axes, increasing axis order)
+        full = _cell_range_faces(mesh, ax, wall_idx, ((0, n[t]), (0, n[2])))
+        ap = []
+        for k in range(n_per_wall):
+            c0 = int(round(n[t] * (k + 0.5) / n_per_wall - a_cells / 2))
+            c1 = c0 + a_cells
+            r_t, r_z = (c0, c1), (z0, z1)
+            pf = _cell_range_faces(mesh, ax, wall_idx, (r_t, r_z))
+            ap.append(pf)
+            port_faces.append(pf)
+            # stub side walls (interior metal): t = c0, t = c1 over (depth, z); z = z0, z = z1 over (t, depth)
+            for ti in (c0, c1):
+                rr = ((d0, d1), r_z)                    # axes (ax, 2): ax < 2 always
+                metal.append(_cell_range_faces(mesh, t, ti, rr))
+            for zi in (z0, z1):
+                rr = [None, None]
+                rr[ax] = (d0, d1)
+                rr[t] = r_t
+                metal.append(_cell_range_faces(mesh, 2, zi, tuple(rr)))
+            sel = (cell[:, ax] >= d0) & (cell[:, ax] < d1) & (cell[:, t] >= c0) & (cell[:, t] < c1) & \
+                  (cell[:, 2] >= z0) & (cell[:, 2] < z1)
+            guide |= sel
+            o = lo.copy()
+            o[ax] = lo[ax] + wall_idx * h[ax]
+            o[t] = lo[t] + c0 * h[t]
+            o[2] = lo[2] + z0 * h[2]
+            origin.append(o)
+            e = np.zeros(3)
+            e[t] = 1.0
+            u.append(e)
+            width.append(a_cells * h[t])
+        metal.append(_setdiff_rows(full, np.concatenate(ap)))
+    metal = np.unique(np.concatenate(metal), axis=0)
+    P = len(port_faces)
+    fv = np.concatenate([metal] + port_faces)
+    lab = np.concatenate([np.full(len(metal), -1)] + [np.full(len(pf), p) for p, pf in enumerate(port_faces)])
+    ports = PortSet(np.array(origin), np.array(u), np.tile([0.0, 0.0, 1.0], (P, 1)), np.array(width),
+                    np.full(P, eps_fill, dtype=complex))
+    return fv, lab.astype(np.int32), ports, guide
+
+
 # ----------------------------------------------------------------------------------------
 # Named workloads
 # ----------------------------------------------------------------------------------------
