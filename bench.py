@@ -40,6 +40,8 @@ def _args(argv=None):
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--cells", default="80x80x34")
     ap.add_argument("--n-src", type=int, default=32)
+    ap.add_argument("--antennas", default="dipoles", choices=["dipoles", "waveguides"],
+                    help="z-dipole ring, or ceramic-filled TE10 waveguides on three side walls (Eq. m1 ports)")
     ap.add_argument("--freqs", default="1.0e9", help="comma-separated frequencies (Hz)")
     ap.add_argument("--parts", default="16x16x7")
     ap.add_argument("--overlap", type=int, default=1)
@@ -118,12 +120,24 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------------------
+def waveguide_counts(n_src: int):
+    """Guides per side wall (x = lo, x = hi, y = lo, y = hi): the x = lo wall, where the torso
+    enters the box, stays open; the others share n_src as evenly as they can."""
+    base, rem = divmod(n_src, 3)
+    return (0,) + tuple(base + (1 if k < rem else 0) for k in range(3))
+
+
 def make_workload(a):
-    from phantom import box_partition, random_tear, shoulder
+    from phantom import EPS_CERAMIC, box_partition, port_chamber, random_tear, shoulder
     cells = _dims(a.cells)
     freqs = tuple(float(f) for f in a.freqs.split(","))
     healthy = shoulder(cells, n_src=a.n_src, freqs=freqs)
     injured = shoulder(cells, n_src=a.n_src, freqs=freqs, tear=random_tear(2001))
+    if a.antennas == "waveguides":
+        fv, lab, ps, guide = port_chamber(healthy.mesh, waveguide_counts(a.n_src), a_cells=5, b_cells=2, depth=4)
+        for w in (healthy, injured):
+            w.eps[guide] = EPS_CERAMIC
+            w.extra["ports"] = (fv, lab, ps, guide)
     parts = _dims(a.parts)
     part = box_partition(healthy.mesh, parts, seed=7)
     return healthy, injured, parts, part
@@ -177,7 +191,7 @@ def peaks():
 # ---------------------------------------------------------------------------------------
 # CPU oracle sample (baseline, not a target)
 # ---------------------------------------------------------------------------------------
-def oracle_sample(w, part, n_sub, overlap, iters_per_col, n_sample_subs, seed=0):
+def oracle_sample(w, part, n_sub, overlap, iters_per_col, n_sample_subs, seed=0, ports=None):
     """Oracle cost of one column solve, from timed pieces of one Arnoldi step on the full
     workload: the oracle's FP64 matvec, its ORAS subdomain solves on a random sample of
     subdomains (scaled to all), one modified Gram-Schmidt pass at the mean Krylov depth;
@@ -191,13 +205,29 @@ def oracle_sample(w, part, n_sub, overlap, iters_per_col, n_sample_subs, seed=0)
     rng = np.random.default_rng(seed)
     pick = rng.choice(n_sub, size=min(n_sample_subs, n_sub), replace=False)
     subs, _ = ooras.build_subdomains(sysm, part, n_sub, overlap, which=pick)
-    lus = [(sub, spla.splu(ooras.local_matrix(sysm, sub, w.eps, w.freqs[0], w.eps_bg))) for sub in subs]
+    zface, free = None, None
+    if ports is not None:
+        from oracle import ports as oports
+        fv, lab, ps, _ = ports
+        P = oports.make_ports(ps.origin, ps.u, ps.v, ps.a, ps.eps_fill)
+        bnd = oports.classify(sysm, P, fv, lab)
+        zface = oports.face_coefficients(w.freqs[0], w.eps_bg, bnd)
+        free = ~bnd.metal
+    lus = []
+    for sub in subs:
+        B = ooras.local_matrix(sysm, sub, w.eps, w.freqs[0], w.eps_bg, zface)
+        if free is not None:                       # metal edges are not unknowns
+            fl = np.nonzero(free[sub.dofs])[0]
+            B = B[fl][:, fl].tocsc()
+            sub = ooras.Subdomain(sub.tets, sub.dofs[fl], np.nonzero(np.isin(fl, sub.owned))[0], sub.iface,
+                                  sub.iface_tet)
+        lus.append((sub, spla.splu(B)))
     setup = time.perf_counter() - t0
     E = sysm.topo.n_edge
     x = rng.normal(size=(E, 1)) + 1j * rng.normal(size=(E, 1))
     t = time.perf_counter()
     for _ in range(2):
-        y = asm.apply_system(sysm, w.eps, w.freqs[0], w.eps_bg, x)[:, 0]
+        y = asm.apply_system(sysm, w.eps, w.freqs[0], w.eps_bg, x, zface)[:, 0]
     t_mv = (time.perf_counter() - t) / 2
     x = x[:, 0]
     z = np.zeros(E, dtype=complex)
@@ -247,8 +277,16 @@ def run_mine(a):
     info = c.set_mesh(healthy.mesh.xyz, healthy.mesh.tets)
     torch.cuda.synchronize()
     setup["mesh_s"] = time.perf_counter() - t
-    c.set_sources(healthy.src_pos, healthy.src_dir)
-    hom = np.tile([healthy.eps_bg.real, healthy.eps_bg.imag], (healthy.mesh.n_tet, 1))
+    ports = healthy.extra.get("ports")
+    if ports is None:
+        c.set_sources(healthy.src_pos, healthy.src_dir)
+        hom = np.tile([healthy.eps_bg.real, healthy.eps_bg.imag], (healthy.mesh.n_tet, 1))
+    else:
+        fv, lab, ps, guide = ports
+        c.set_ports(ps.origin, ps.u, ps.v, ps.a, ps.eps_fill, fv, lab)
+        hom_c = np.full(healthy.mesh.n_tet, healthy.eps_bg)
+        hom_c[guide] = ps.eps_fill[0]
+        hom = np.stack([hom_c.real, hom_c.imag], 1)
     # preconditioner of the background medium, reused stale for every eps (as in an inversion)
     c.assemble(freqs, hom, healthy.eps_bg)
     prec = {"bf16": mw.MW_PREC_BF16, "fp32": mw.MW_PREC_FP32}[a.prec]
@@ -327,7 +365,9 @@ def run_mine(a):
 
     # ---- plain FP64 path (FP64 everything, one RHS per Krylov launch) ---------------------
     plain = None
-    if a.plain_cols > 0 and rank == 0:
+    if ports is not None:
+        plain = {"skipped": "dipole-source leg; not run for the waveguide workload"}
+    elif a.plain_cols > 0 and rank == 0:
         try:
             c.assemble(freqs, hom, healthy.eps_bg)
             t = time.perf_counter()
@@ -354,7 +394,9 @@ def run_mine(a):
             plain = {"error": str(e)}
     # ---- FP64 batched (FP64 everything, several columns in one Krylov launch) ---------------
     fp64_batched = None
-    if a.plain_cols > 0 and a.fp64_batch_cols > 0 and rank == 0 and plain is not None and "error" not in plain:
+    if ports is not None:
+        fp64_batched = {"skipped": "dipole-source leg; not run for the waveguide workload"}
+    elif a.plain_cols > 0 and a.fp64_batch_cols > 0 and rank == 0 and plain is not None and "error" not in plain:
         try:
             nb = min(a.fp64_batch_cols, a.n_src)
             rhs = np.zeros((nb, info.n_edge), dtype=np.complex128)
@@ -393,7 +435,7 @@ def run_mine(a):
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         its = max(1.0, prof["cgs_dots"]["launches"] / max(1, a.steps * 2 * len(freqs)))
-        col_s, det = oracle_sample(healthy, part, n_sub, a.overlap, its, a.cpu_sample_subdomains)
+        col_s, det = oracle_sample(healthy, part, n_sub, a.overlap, its, a.cpu_sample_subdomains, ports=ports)
         cpu = {"value": 1.0 / col_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": (f"oracle (numpy/scipy FP64) one Arnoldi step of one column on the full workload: "
                           f"FP64 matvec, ORAS sparse-LU solves on {a.cpu_sample_subdomains} random subdomains "
@@ -408,8 +450,11 @@ def run_mine(a):
             "dtype": "c64+bf16 inner / c128 outer" if prec == mw.MW_PREC_BF16 else "c64 inner / c128 outer",
             "data": "synthetic",
             "config": {"workload": f"shoulder phantom {a.cells} Kuhn cells ({info.n_edge} edges, {info.n_tet} tets), "
-                                   f"{a.n_src} z-dipoles x {len(freqs)} frequencies, one inversion evaluation "
-                                   f"(forward+adjoint)",
+                                   + (f"{a.n_src} z-dipoles" if ports is None else
+                                      f"{a.n_src} TE10 waveguide ports (guides per wall {waveguide_counts(a.n_src)}, "
+                                      f"metal walls)")
+                                   + f" x {len(freqs)} frequencies, one inversion evaluation (forward+adjoint)",
+                       "antennas": a.antennas,
                        "edges": info.n_edge, "nnz": info.nnz, "transmitters": a.n_src, "freqs_hz": freqs,
                        "rhs_solves_per_step": units, "subdomains": n_sub, "overlap": a.overlap,
                        "n_s_mean": float(sizes.mean()), "n_s_max": int(sizes.max()),
@@ -449,13 +494,15 @@ def run_reference(a):
     vals = []
     det = None
     for k in range(a.warmup + a.steps):
-        col_s, det = oracle_sample(healthy, part, n_sub, a.overlap, its, a.cpu_sample_subdomains, seed=k)
+        col_s, det = oracle_sample(healthy, part, n_sub, a.overlap, its, a.cpu_sample_subdomains, seed=k,
+                                   ports=healthy.extra.get("ports"))
         if k >= a.warmup:
             vals.append(1.0 / col_s)
     v = statistics.mean(vals)
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
                       "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "data": "synthetic",
-                      "config": {"workload": f"shoulder phantom {a.cells}", "subdomains": n_sub},
+                      "config": {"workload": f"shoulder phantom {a.cells}", "antennas": a.antennas,
+                                 "subdomains": n_sub},
                       "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": UNIT,
                                        "sample": ("oracle (numpy/scipy FP64) per-column cost: one sampled Arnoldi "
                                                   "step on the full workload x 50 (one GMRES(50) cycle)")},

@@ -76,10 +76,12 @@ def assemble_parts(sysm: System):
     return out
 
 
-def apply_system(sysm: System, eps: np.ndarray, freq_hz: float, eps_bg: complex, X: np.ndarray) -> np.ndarray:
+def apply_system(sysm: System, eps: np.ndarray, freq_hz: float, eps_bg: complex, X: np.ndarray,
+                 zface: np.ndarray | None = None) -> np.ndarray:
     """A_f X as the sum of element contributions (no assembled matrix): for each tet,
     (K^T - k0^2 eps_T M^T) acting on its 6 edge values, plus i k0 sqrt(eps_bg) B^F on each
-    boundary face; scattered into the rows of the edges.  Same operator as assemble()."""
+    boundary face (or zface[F] B^F, the per-face coefficients of ports.py); scattered into the
+    rows of the edges.  Same operator as assemble()."""
     k0 = constants.k0(freq_hz)
     te = sysm.topo.tet_edge
     Y = np.zeros(X.shape, dtype=np.complex128)
@@ -89,7 +91,7 @@ def apply_system(sysm: System, eps: np.ndarray, freq_hz: float, eps_bg: complex,
         yt = np.einsum("tmn,tnr->tmr", elem, X[te[sl]])
         np.add.at(Y, te[sl].ravel(), yt.reshape(-1, X.shape[1]))
     fe = sysm.bface_edges
-    zb = 1j * k0 * np.sqrt(complex(eps_bg))
+    zb = 1j * k0 * np.sqrt(complex(eps_bg)) if zface is None else zface[:, None, None]
     yf = np.einsum("fmn,fnr->fmr", zb * sysm.BF, X[fe])
     np.add.at(Y, fe.ravel(), yf.reshape(-1, X.shape[1]))
     return Y

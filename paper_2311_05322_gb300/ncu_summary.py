@@ -12,7 +12,8 @@ import sys
 from collections import defaultdict
 
 SETUP = ("elem_geom", "face_geom", "tikhonov_weights", "local_assemble", "gj_", "extract_owned", "pack_w",
-         "fill_pattern")  # fill_pattern: timing inputs of the launch-shape tuner
+         "fill_pattern",  # fill_pattern: timing inputs of the launch-shape tuner
+         "port_face", "port_accumulate", "port_norm")  # port load vectors (once per boundary)
 
 
 def short(name: str) -> str:

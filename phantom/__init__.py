@@ -81,6 +81,9 @@ class Mesh:
     def n_tet(self) -> int:
         return self.tets.shape[0]
 
+    def shape_n(self, d: int) -> int:
+        return (self.nx, self.ny, self.nz)[d]
+
     @property
     def h(self) -> tuple:
         return tuple((self.hi[d] - self.lo[d]) / (self.nx, self.ny, self.nz)[d] for d in range(3))
@@ -287,17 +290,60 @@ def add_noise(S: np.ndarray, snr_db: float, seed: int) -> np.ndarray:
 _TET_FACES = ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2))
 
 
+class _PlaneFaces:
+    """The distinct tet faces of a Kuhn mesh that lie in a grid plane, grouped by (axis, vertex
+    index of the plane), with the integer grid indices of their vertices."""
+
+    def __init__(self, mesh: Mesh):
+        V = np.int64(mesh.n_vert)
+        fv = np.sort(mesh.tets[:, _TET_FACES].reshape(-1, 3).astype(np.int64), axis=1)
+        key = np.unique((fv[:, 0] * V + fv[:, 1]) * V + fv[:, 2])
+        fv = np.stack([key // (V * V), (key // V) % V, key % V], axis=1)
+        nx1, ny1 = mesh.nx + 1, mesh.ny + 1
+        grid = np.stack([fv % nx1, (fv // nx1) % ny1, fv // (nx1 * ny1)], axis=2)     # [F, 3 verts, 3 axes]
+        self.groups = {}
+        for d in range(3):
+            on = (grid[:, 0, d] == grid[:, 1, d]) & (grid[:, 1, d] == grid[:, 2, d])
+            idx = np.nonzero(on)[0]
+            plane = grid[idx, 0, d]
+            order = np.argsort(plane, kind="stable")
+            idx, plane = idx[order], plane[order]
+            cuts = np.searchsorted(plane, np.arange(mesh.shape_n(d) + 2))
+            for q in range(mesh.shape_n(d) + 1):
+                sel = idx[cuts[q]:cuts[q + 1]]
+                self.groups[(d, q)] = (fv[sel], grid[sel])
+
+    def query(self, axis: int, q: int, rng2) -> np.ndarray:
+        """Faces in plane axis = q with all vertices inside the vertex-index ranges rng2 (two
+        closed ranges over the other axes, increasing axis order)."""
+        fv, g = self.groups.get((axis, q), (np.zeros((0, 3), np.int64), np.zeros((0, 3, 3), np.int64)))
+        others = [d for d in range(3) if d != axis]
+        ok = np.ones(fv.shape[0], dtype=bool)
+        for k, d in enumerate(others):
+            ok &= np.all((g[:, :, d] >= rng2[k][0]) & (g[:, :, d] <= rng2[k][1]), axis=1)
+        return fv[ok]
+
+
+def _plane_faces(mesh: Mesh) -> _PlaneFaces:
+    pf = getattr(mesh, "_plane_faces", None)
+    if pf is None:
+        pf = _PlaneFaces(mesh)
+        mesh._plane_faces = pf
+    return pf
+
+
 def faces_on_plane(mesh: Mesh, axis: int, value: float, lo2, hi2, tol: float = 1e-9) -> np.ndarray:
     """Sorted vertex triples of the tet faces lying in the plane x[axis] = value with every vertex
     inside the rectangle [lo2, hi2] of the two other axes (in increasing axis order)."""
-    fv = np.sort(mesh.tets[:, _TET_FACES].reshape(-1, 3).astype(np.int64), axis=1)
-    fv = np.unique(fv, axis=0)
-    P = mesh.xyz[fv]                                            # [F, 3, 3]
+    lo, hi = np.asarray(mesh.lo), np.asarray(mesh.hi)
+    h = (hi - lo) / np.array([mesh.nx, mesh.ny, mesh.nz])
+    q = int(round((value - lo[axis]) / h[axis]))
+    if abs(lo[axis] + q * h[axis] - value) > tol or q < 0 or q > mesh.shape_n(axis):
+        return np.zeros((0, 3), dtype=np.int64)
     others = [d for d in range(3) if d != axis]
-    ok = np.all(np.abs(P[:, :, axis] - value) <= tol, axis=1)
-    for k, d in enumerate(others):
-        ok &= np.all((P[:, :, d] >= lo2[k] - tol) & (P[:, :, d] <= hi2[k] + tol), axis=1)
-    return fv[ok]
+    rng2 = [(int(np.ceil((lo2[k] - lo[d]) / h[d] - 1e-9)), int(np.floor((hi2[k] - lo[d]) / h[d] + 1e-9)))
+            for k, d in enumerate(others)]
+    return _plane_faces(mesh).query(axis, q, rng2)
 
 
 @dataclass
@@ -337,14 +383,10 @@ EPS_CERAMIC = 59.0 - 0.6j   # filling of the waveguide antennas
 
 
 def _cell_range_faces(mesh: Mesh, axis: int, idx: int, rng2) -> np.ndarray:
-    """Faces on the grid plane axis = idx (a vertex-index plane) within the cell-index ranges
-    rng2 = ((i0, i1), (j0, j1)) of the two other axes (increasing axis order)."""
-    lo, hi = np.asarray(mesh.lo), np.asarray(mesh.hi)
-    h = (hi - lo) / np.array([mesh.nx, mesh.ny, mesh.nz])
-    others = [d for d in range(3) if d != axis]
-    return faces_on_plane(mesh, axis, lo[axis] + idx * h[axis],
-                          [lo[others[k]] + rng2[k][0] * h[others[k]] for k in range(2)],
-                          [lo[others[k]] + rng2[k][1] * h[others[k]] for k in range(2)])
+    """Faces on the grid plane axis = idx (a vertex-index plane) covering the cell-index ranges
+    rng2 = ((i0, i1), (j0, j1)) of the two other axes (increasing axis order): vertex indices
+    i0..i1 and j0..j1."""
+    return _plane_faces(mesh).query(axis, idx, rng2)
 
 
 def _setdiff_rows(a: np.ndarray, b: np.ndarray) -> np.ndarray:
@@ -354,18 +396,20 @@ def _setdiff_rows(a: np.ndarray, b: np.ndarray) -> np.ndarray:
     return a[keep]
 
 
-def port_chamber(mesh: Mesh, n_per_wall: int = 8, a_cells: int = 5, b_cells: int = 2, depth: int = 4,
+def port_chamber(mesh: Mesh, n_per_wall=8, a_cells: int = 5, b_cells: int = 2, depth: int = 4,
                  eps_fill: complex = EPS_CERAMIC):
-    """A ring of rectangular waveguide antennas on the four side walls of a Kuhn box.
+    """A ring of rectangular waveguide antennas on the side walls of a Kuhn box.
 
     Each guide is a stub of a_cells x b_cells cells (broad side horizontal along its wall,
     narrow side vertical, centred in z) reaching `depth` cells into the box from its wall, filled
     with eps_fill.  Its four side walls are metal sheets inside the mesh, its back face on the
-    box wall is the port, and its front opening is open to the box.  The rest of the four side
-    walls is metal; the bottom and top faces stay open.  Guides are evenly spaced along each
-    wall; walls in the order x = lo, x = hi, y = lo, y = hi.
+    box wall is the port, and its front opening is open to the box.  The rest of a wall with
+    guides is metal; a wall given 0 guides, the bottom and the top stay open.  Guides are evenly
+    spaced along each wall.  n_per_wall: one count for every side wall, or four counts for the
+    walls x = lo, x = hi, y = lo, y = hi (ports are numbered in that order).
     Returns (face_vert [n, 3], label [n] (-1 metal, p port), PortSet, guide tet mask [T]).
     """
+    counts = (n_per_wall,) * 4 if np.isscalar(n_per_wall) else tuple(n_per_wall)
     n = (mesh.nx, mesh.ny, mesh.nz)
     lo, hi = np.asarray(mesh.lo), np.asarray(mesh.hi)
     h = (hi - lo) / np.array(n)
@@ -376,14 +420,17 @@ def port_chamber(mesh: Mesh, n_per_wall: int = 8, a_cells: int = 5, b_cells: int
     guide = np.zeros(mesh.n_tet, dtype=bool)
     metal, port_faces, origin, u, width = [], [], [], [], []
     for wall, (ax, side) in enumerate([(0, 0), (0, 1), (1, 0), (1, 1)]):
+        n_w = counts[wall]
+        if n_w == 0:
+            continue
         t = 1 - ax                                   # horizontal axis along this wall
         wall_idx = 0 if side == 0 else n[ax]
         d0, d1 = (0, depth) if side == 0 else (n[ax] - depth, n[ax])
         # full side wall (cell ranges over the two other axes, increasing axis order)
         full = _cell_range_faces(mesh, ax, wall_idx, ((0, n[t]), (0, n[2])))
         ap = []
-        for k in range(n_per_wall):
-            c0 = int(round(n[t] * (k + 0.5) / n_per_wall - a_cells / 2))
+        for k in range(n_w):
+            c0 = int(round(n[t] * (k + 0.5) / n_w - a_cells / 2))
             c1 = c0 + a_cells
             r_t, r_z = (c0, c1), (z0, z1)
             pf = _cell_range_faces(mesh, ax, wall_idx, (r_t, r_z))
