@@ -54,6 +54,8 @@ def _args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graphs", action="store_true", help="replay restart cycles from captured CUDA graphs")
     ap.add_argument("--cpu-sample-subdomains", type=int, default=24)
+    ap.add_argument("--study", default=None, choices=["tiny", "reduced"],
+                    help="antenna-count design study (Sec. V): err / ctr for N = 96/64/32/16 at 23/15/10 dB")
     ap.add_argument("--inversion", default=None, choices=["tiny", "reduced", "full"],
                     help="time-to-misfit of the regularised inversion instead of RHS-solves/s")
     return ap.parse_args(argv)
@@ -525,9 +527,25 @@ def run_inversion(a):
     print(json.dumps(line), flush=True)
 
 
+def run_study(a):
+    """Third measurement: wall time of the antenna-count design study and its err / ctr rows."""
+    from paper_2311_05322_gb300 import design_study
+    r = design_study.run(a.study, seed=5)
+    secs = [s for row in r["rows"] for s in row["seconds"].values()]
+    line = {"metric": "antenna-count study wall time", "unit": "s", "higher_is_better": False, "n_gpus": 1,
+            "value": r["total_s"], "data": "synthetic",
+            "config": {"workload": f"antenna-count design study, scale {a.study}", **r["config"],
+                       "inverse_tets": r["inverse_tets"], "injury_tets": r["injury_tets"]},
+            "reconstructions": len(secs), "seconds_per_reconstruction": {"min": min(secs), "max": max(secs)},
+            "rows": r["rows"]}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     args = _args()
-    if args.inversion:
+    if args.study:
+        run_study(args)
+    elif args.inversion:
         run_inversion(args)
     elif args.impl == "reference":
         run_reference(args)

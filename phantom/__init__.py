@@ -159,6 +159,39 @@ def dipole_ring(n: int, rho: float, z: float, center=(0.0, 0.0)) -> tuple[np.nda
     return pos, direc
 
 
+# Antenna-count study: four layers around the arm, two full rings and two half rings (on the
+# +x side, away from the torso), split in the proportions 11 : 10 : 6 : 5 of the 32-antenna
+# design; each ring starts half an angular pitch after the ring below it.
+LAYER_WEIGHTS = (5, 11, 10, 6)                 # bottom to top: half, full, full, half
+LAYER_FULL = (False, True, True, False)
+LAYER_Z = (-0.03, -0.01, 0.01, 0.03)
+
+
+def layer_counts(n: int) -> tuple:
+    """Antennas per layer: n split in LAYER_WEIGHTS proportions, largest remainders first."""
+    w = np.asarray(LAYER_WEIGHTS, dtype=np.float64)
+    q = n * w / w.sum()
+    c = np.floor(q).astype(int)
+    for k in np.argsort(-(q - c), kind="stable")[: n - c.sum()]:
+        c[k] += 1
+    return tuple(int(v) for v in c)
+
+
+def antenna_layers(n: int, rho: float = 0.10, center=(0.0, 0.0)) -> tuple[np.ndarray, np.ndarray]:
+    """z-dipole positions and directions of the n-antenna layered design."""
+    pos = []
+    shift = 0.0
+    for cnt, full, z in zip(layer_counts(n), LAYER_FULL, LAYER_Z):
+        span = 2.0 * np.pi if full else np.pi
+        start = 0.0 if full else -0.5 * np.pi
+        pitch = span / cnt
+        ang = start + pitch * (np.arange(cnt) + 0.5 + shift)
+        shift = 0.5 - shift
+        pos.append(np.stack([center[0] + rho * np.cos(ang), center[1] + rho * np.sin(ang), np.full(cnt, z)], 1))
+    pos = np.concatenate(pos)
+    return pos, np.tile(np.array([0.0, 0.0, 1.0]), (n, 1))
+
+
 # ----------------------------------------------------------------------------------------
 # Phantoms
 # ----------------------------------------------------------------------------------------
@@ -228,6 +261,14 @@ def shoulder_eps(mesh: Mesh, tear: Tear | None = None) -> np.ndarray:
     if tear is not None:
         eps[lab == FLUID] = tear.eps
     return eps
+
+
+def study_tear(kind: str) -> Tear:
+    """The two tears of the antenna-count study, centred in the tendon band at theta = 180 deg:
+    partial (about 1 mL) and large (about 5 mL) ellipsoids of synovial fluid."""
+    rho = 0.5 * (TENDON_RHO[0] + TENDON_RHO[1])
+    axes = {"partial": (0.005, 0.005, 0.0095), "large": (0.005, 0.012, 0.020)}[kind]
+    return Tear((ARM_CENTER[0] - rho, ARM_CENTER[1], 0.0), axes, EPS_FLUID)
 
 
 def random_tear(seed: int, eps_range=None) -> Tear:
