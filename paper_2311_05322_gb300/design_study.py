@@ -58,14 +58,14 @@ def lattice(m: int = 5) -> np.ndarray:
     return np.asarray(pts, dtype=np.float64) / m
 
 
-def tet_average_eps(mesh, tear=None, m: int = 5, chunk: int = 20000) -> np.ndarray:
+def tet_average_eps(mesh, tear=None, matching=EPS_MATCHING, m: int = 5, chunk: int = 20000) -> np.ndarray:
     """Per-tet mean of the true permittivity over the lattice points of each tet."""
     lam = lattice(m)
     out = np.empty(mesh.n_tet, dtype=np.complex128)
     for t0 in range(0, mesh.n_tet, chunk):
         X = mesh.xyz[mesh.tets[t0:t0 + chunk]]                     # [t, 4, 3]
         pts = np.einsum("pk,tkd->tpd", lam, X).reshape(-1, 3)
-        out[t0:t0 + chunk] = shoulder_eps_at(pts, tear).reshape(X.shape[0], -1).mean(axis=1)
+        out[t0:t0 + chunk] = shoulder_eps_at(pts, tear, matching).reshape(X.shape[0], -1).mean(axis=1)
     return out
 
 
@@ -120,8 +120,11 @@ def run(scale: str = "reduced", seed: int = 5, verbose: bool = False) -> dict:
         exact[k] = tet_average_eps(inv.mesh, study_tear(k))
         masks[k] = exact[k] != exact["healthy"]
     io = mw.inv_opts(m=8, max_it=cfg["iters"], alpha=0.0, first_step=1.0)
+    hom_inv = np.full(inv.mesh.n_tet, EPS_MATCHING, dtype=complex)
     out = {"scale": scale, "config": dict(cfg), "inverse_tets": int(inv.mesh.n_tet),
-           "injury_tets": {k: int(masks[k].sum()) for k in TEARS}, "rows": []}
+           "injury_tets": {k: int(masks[k].sum()) for k in TEARS},
+           "start_err_total_partial": err(hom_inv, exact["partial"]),
+           "start_err_injury_partial": err(hom_inv, exact["partial"], masks["partial"]), "rows": []}
     for n in cfg["counts"]:
         data.antennas(n)
         inv.antennas(n)

@@ -253,14 +253,8 @@ def shoulder_labels(points: np.ndarray, tear: Tear | None = None) -> np.ndarray:
     return lab
 
 
-def shoulder_eps(mesh: Mesh, tear: Tear | None = None) -> np.ndarray:
-    lab = shoulder_labels(mesh.centroids(), tear)
-    eps = np.empty(mesh.n_tet, dtype=np.complex128)
-    for k, v in LABEL_EPS.items():
-        eps[lab == k] = v
-    if tear is not None:
-        eps[lab == FLUID] = tear.eps
-    return eps
+def shoulder_eps(mesh: Mesh, tear: Tear | None = None, matching: complex = EPS_MATCHING) -> np.ndarray:
+    return shoulder_eps_at(mesh.centroids(), tear, matching)
 
 
 def study_tear(kind: str) -> Tear:
@@ -550,12 +544,13 @@ def shoulder(cells=(80, 80, 34), n_src: int = 32, freqs=(1.0e9,), tear: Tear | N
                     extra={"tear": tear})
 
 
-def shoulder_eps_at(points: np.ndarray, tear: Tear | None = None) -> np.ndarray:
-    """Relative permittivity of the shoulder phantom at arbitrary points (complex)."""
+def shoulder_eps_at(points: np.ndarray, tear: Tear | None = None, matching: complex = EPS_MATCHING) -> np.ndarray:
+    """Relative permittivity of the shoulder phantom at arbitrary points (complex); `matching`
+    fills the medium around the body."""
     lab = shoulder_labels(points, tear)
     eps = np.empty(points.shape[0], dtype=np.complex128)
     for k, v in LABEL_EPS.items():
-        eps[lab == k] = v
+        eps[lab == k] = matching if k == MATCHING else v
     if tear is not None:
         eps[lab == FLUID] = tear.eps
     return eps
