@@ -47,7 +47,7 @@ enum {
   MW_ESINGULAR = 7  /* a subdomain matrix had a (near-)zero pivot */
 };
 
-typedef enum { MW_PREC_FP64 = 0, MW_PREC_FP32 = 1, MW_PREC_BF16 = 2 } mw_precision;
+typedef enum { MW_PREC_FP64 = 0, MW_PREC_FP32 = 1, MW_PREC_BF16 = 2, MW_PREC_SPARSE = 4 } mw_precision;
 typedef enum { MW_MODE_FP64 = 0, MW_MODE_MIXED = 1 } mw_mode;
 
 typedef struct mw_ctx mw_ctx;
@@ -225,7 +225,12 @@ mw_status mw_get_port_vectors(mw_ctx* ctx, double* W, double* norms);
 /* tet_part [n_tet] in [0, n_sub); overlap_layers >= 0 vertex-neighbour layers; inv_prec
  * selects the stored precision of the subdomain inverses (FP64: FP64 factorisation, applied
  * in FP64; FP32: FP32 factorisation, FP32 apply; BF16: FP32 factorisation, BF16 tensor-core
- * apply).  Builds for every assembled frequency from the current eps. */
+ * apply).  MW_PREC_SPARSE keeps no dense inverse: each subdomain matrix is factorised as a
+ * multifrontal LU on a nested-dissection tree (FP32, no pivoting), and the apply runs its
+ * forward and backward sweeps on the GPU (mixed-precision solves only).  Its memory grows like
+ * n_s^(4/3) per subdomain instead of n_s^2, so subdomains of 1e5 unknowns are practical.
+ * Builds for every assembled frequency from the current eps.  MW_ESINGULAR when a pivot
+ * block is numerically singular. */
 mw_status mw_setup_preconditioner(mw_ctx* ctx, int32_t n_sub, const int32_t* tet_part,
                                   int32_t overlap_layers, int32_t inv_prec);
 /* z = M_f^{-1} r on the device, complex128 [E][n_cols] in and out (parity hook). */
@@ -248,9 +253,10 @@ mw_status mw_apply_preconditioner_noalloc(mw_ctx* ctx, int32_t f, const void* r_
 mw_status mw_get_partition(mw_ctx* ctx, int32_t* edge_owner, int32_t* sub_size);
 
 /* ---- solves -------------------------------------------------------------------------- */
-/* Forward solves for all n_freq * n_src dipole columns (column c = f * n_src + j).
+/* Forward solves for all n_freq * n_src source columns (column c = f * n_src + j).
  * fields_dev: NULL, or device complex128 [n_cols][E] receiving the fields.
- * S: NULL, or host complex128 [n_freq][n_src][n_src], S[f][i][j] = p_i^T x_{f,j}.
+ * S: NULL, or host complex128 [n_freq][n_src][n_src], S[f][i][j] = w_i^T x_{f,j} / n_i
+ * (dipoles: p_i^T x_{f,j}; ports: the Eq. s1 projection, see mw_set_ports).
  * Returns MW_ENOCONV if some column missed tol (outputs then hold the last iterate). */
 mw_status mw_solve(mw_ctx* ctx, const mw_solve_opts* opts, void* fields_dev, double* S,
                    mw_solve_stats* stats);

@@ -1,0 +1,308 @@
+// Sparse subdomain solves of the ORAS preconditioner (Sec. IV-C): multifrontal LU on a
+// nested-dissection tree per subdomain, FP32 complex.
+//
+// Factorisation, per subdomain, fronts row-major in a workspace:
+//   1. mf_assemble_kernel: the original entries of B_s (element and face terms, as in the dense
+//      local assembly, plus ones on the diagonal of metal and padding pivots), pulled per front
+//      entry in a fixed order;
+//   2. per tree height, leaves first: mf_extend_add_kernel adds the children's Schur complements
+//      into each front, the partial Gauss-Jordan eliminates its pivots, and mf_extract_kernel keeps
+//      TL | TR (the pivot rows) and BL (the update rows' pivot columns).
+// Solve z = B_s^-1 r for R columns, every subdomain at once, per height:
+//   forward (leaves first):  rhs_k = [r(pivots); 0] + the children's w mapped into the front,
+//                            t_k = TL rhs_k(p),  w_k = rhs_k(u) + BL rhs_k(p);
+//   backward (root first):   x(pivots of k) = t_k - TR x(update dofs of k);
+//   then z(owned) = x(owned).
+// The products are one task-list GEMM launch per height and direction (mf_gemm_kernel).
+#include <algorithm>
+
+#include "k_mf.h"
+#include "mw_internal.h"
+
+namespace mwk {
+namespace {
+
+__device__ __forceinline__ double2 csqrt_pr(double a, double b) {
+  const double r = sqrt(a * a + b * b);
+  const double re = sqrt(0.5 * (r + a));
+  double im = sqrt(fmax(0.0, 0.5 * (r - a)));
+  if (b < 0.0) im = -im;
+  return make_double2(re, im);
+}
+
+// One thread per front entry that receives original contributions; the value is summed in FP64
+// in the code order of the pull map, then rounded to FP32.
+__global__ void mf_assemble_kernel(const int64_t* __restrict__ ptr, const int64_t* __restrict__ target,
+                                   const int32_t* __restrict__ code, int64_t n_t, const int32_t* __restrict__ tet_ids,
+                                   const double* __restrict__ KM, const double* __restrict__ eps, double k0,
+                                   const double* __restrict__ Bsurf, const int32_t* __restrict__ surf_tet,
+                                   double ebr, double ebi, const double2* __restrict__ zc, float2* __restrict__ ws) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_t) return;
+  const double k0sq = k0 * k0;
+  double re = 0.0, im = 0.0;
+  for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) {
+    const int32_t c = code[q];
+    if (c == INT32_MIN) {
+      re += 1.0;
+    } else if (c >= 0) {
+      const int64_t slot = c / 36;
+      const int r = c - (int)slot * 36;
+      const int64_t t = tet_ids[slot];
+      const int pk = mw::packed6(r / 6, r % 6);
+      const double Kv = KM[42 * t + pk], Mv = KM[42 * t + 21 + pk];
+      re += Kv - (k0sq * eps[2 * t]) * Mv;
+      im += -(k0sq * eps[2 * t + 1]) * Mv;
+    } else {
+      const int64_t q9 = -(int64_t)c - 1;
+      const int64_t slot = q9 / 9;
+      const int r = (int)(q9 - slot * 9);
+      const double Bv = Bsurf[6 * slot + mw::packed3(r / 3, r % 3)];
+      const int32_t it = surf_tet[slot];
+      if (it < 0 && zc) {
+        const double2 z = zc[-1 - it];
+        re += z.x * Bv;
+        im += z.y * Bv;
+      } else {
+        const double2 sq = it >= 0 ? csqrt_pr(eps[2 * (int64_t)it], eps[2 * (int64_t)it + 1]) : csqrt_pr(ebr, ebi);
+        re += (-k0 * sq.y) * Bv;
+        im += (k0 * sq.x) * Bv;
+      }
+    }
+  }
+  ws[target[i]] = make_float2((float)re, (float)im);
+}
+
+// Front entry (r, c) of node nodes[blockIdx.y] += sum over its children of S_child(inv(r), inv(c)).
+__global__ void mf_extend_add_kernel(const int32_t* __restrict__ nodes, const int64_t* __restrict__ f,
+                                     const int32_t* __restrict__ p, const int64_t* __restrict__ ws_off,
+                                     const int64_t* __restrict__ child_ptr, const int32_t* __restrict__ child,
+                                     const int64_t* __restrict__ inv_off, const int32_t* __restrict__ inv,
+                                     float2* __restrict__ ws) {
+  const int32_t k = nodes[blockIdx.y];
+  const int64_t fk = f[k];
+  const int64_t c0 = child_ptr[k], c1 = child_ptr[k + 1];
+  if (c0 == c1) return;
+  float2* F = ws + ws_off[k];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < fk * fk; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / fk, c = e - r * fk;
+    float sx = 0.f, sy = 0.f;
+    bool any = false;
+    for (int64_t q = c0; q < c1; ++q) {
+      const int32_t ch = child[q];
+      const int32_t* m = inv + inv_off[ch];
+      const int32_t a = m[r], b = m[c];
+      if (a >= 0 && b >= 0) {
+        const int64_t fc = f[ch], pc = p[ch];
+        const float2 v = ws[ws_off[ch] + (pc + a) * fc + pc + b];
+        sx += v.x;
+        sy += v.y;
+        any = true;
+      }
+    }
+    if (any) {
+      float2 v = F[e];
+      v.x += sx;
+      v.y += sy;
+      F[e] = v;
+    }
+  }
+}
+
+// Keep the factors of nodes[blockIdx.y]: rows [0, p) of the front (TL | TR, p x f) then the
+// pivot columns of rows [p, f) (BL, u x p).
+__global__ void mf_extract_kernel(const int32_t* __restrict__ nodes, const int64_t* __restrict__ f,
+                                  const int32_t* __restrict__ p, const int64_t* __restrict__ ws_off,
+                                  const int64_t* __restrict__ fac_off, const float2* __restrict__ ws,
+                                  float2* __restrict__ fac) {
+  const int32_t k = nodes[blockIdx.y];
+  const int64_t fk = f[k], pk = p[k], uk = fk - pk;
+  const float2* F = ws + ws_off[k];
+  float2* D = fac + fac_off[k];
+  const int64_t n1 = pk * fk, n2 = uk * pk;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n1 + n2; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < n1) {
+      D[e] = F[e];
+    } else {
+      const int64_t q = e - n1, r = q / pk, c = q - r * pk;
+      D[e] = F[(pk + r) * fk + c];
+    }
+  }
+}
+
+// rhs rows of node nodes[blockIdx.y]: r(pivot) for the real pivots, zero elsewhere, plus the
+// children's w rows that map into the front (children in order).
+__global__ void mf_rhs_kernel(const int32_t* __restrict__ nodes, const int64_t* __restrict__ f,
+                              const int32_t* __restrict__ preal, const int64_t* __restrict__ piv_ptr,
+                              const int32_t* __restrict__ piv_glob, const int64_t* __restrict__ child_ptr,
+                              const int32_t* __restrict__ child, const int64_t* __restrict__ inv_off,
+                              const int32_t* __restrict__ inv, const int64_t* __restrict__ rhs_row,
+                              const int64_t* __restrict__ w_row, const float2* __restrict__ in, int R,
+                              float2* __restrict__ arena) {
+  const int32_t k = nodes[blockIdx.y];
+  const int64_t fk = f[k];
+  const int64_t c0 = child_ptr[k], c1 = child_ptr[k + 1];
+  const int col = threadIdx.x % 32;
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; r < fk;
+       r += (int64_t)gridDim.x * (blockDim.x / 32)) {
+    for (int cc = col; cc < R; cc += 32) {
+      float sx = 0.f, sy = 0.f;
+      if (r < preal[k]) {
+        const float2 v = in[(int64_t)piv_glob[piv_ptr[k] + r] * R + cc];
+        sx = v.x;
+        sy = v.y;
+      }
+      for (int64_t q = c0; q < c1; ++q) {
+        const int32_t ch = child[q];
+        const int32_t a = inv[inv_off[ch] + r];
+        if (a >= 0) {
+          const float2 v = arena[(w_row[ch] + a) * R + cc];
+          sx += v.x;
+          sy += v.y;
+        }
+      }
+      arena[(rhs_row[k] + r) * R + cc] = make_float2(sx, sy);
+    }
+  }
+}
+
+// Task-list GEMM: C = C0 + sign * A B for every task, A [m][k] (row stride lda) in the factor
+// store, B [k][R] and C, C0 [m][R] in the vector arena.  Rows of B and C are either consecutive
+// from an arena row or listed (b_idx / c_idx; a negative C row is skipped).  A CTA computes a
+// 64-row x 32-column tile; tile_task / tile_row0 list the 64-row tiles of all tasks.
+constexpr int kMfRows = 64, kMfK = 32, kMfCols = 32;
+
+__global__ void __launch_bounds__(256) mf_gemm_kernel(const MfTask* __restrict__ tasks,
+                                                      const int32_t* __restrict__ tile_task,
+                                                      const int32_t* __restrict__ tile_row0,
+                                                      const float2* __restrict__ fac, const int32_t* __restrict__ idx,
+                                                      int R, float2* __restrict__ arena) {
+  __shared__ float2 As[kMfRows][kMfK + 1];
+  __shared__ float2 Bs[kMfK][kMfCols];
+  const MfTask T = tasks[tile_task[blockIdx.x]];
+  const int64_t row0 = tile_row0[blockIdx.x];
+  const int col0 = blockIdx.y * kMfCols;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // column, row group (8 rows each: ty + 8 i)
+  float2 acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = make_float2(0.f, 0.f);
+  const float2* A = fac + T.a_off;
+  for (int64_t k0 = 0; k0 < T.k; k0 += kMfK) {
+    for (int e = threadIdx.x; e < kMfRows * kMfK; e += 256) {
+      const int r = e / kMfK, kk = e % kMfK;
+      const int64_t gr = row0 + r, gk = k0 + kk;
+      As[r][kk] = (gr < T.m && gk < T.k) ? A[gr * T.lda + gk] : make_float2(0.f, 0.f);
+    }
+    for (int e = threadIdx.x; e < kMfK * kMfCols; e += 256) {
+      const int kk = e / kMfCols, c = e % kMfCols;
+      const int64_t gk = k0 + kk;
+      float2 v = make_float2(0.f, 0.f);
+      if (gk < T.k && col0 + c < R) {
+        const int64_t brow = T.b_idx >= 0 ? (int64_t)idx[T.b_idx + gk] : T.b_row + gk;
+        v = arena[brow * R + col0 + c];
+      }
+      Bs[kk][c] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kMfK; ++kk) {
+      const float2 b = Bs[kk][tx];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float2 a = As[ty + 8 * i][kk];
+        acc[i].x = fmaf(a.x, b.x, acc[i].x);
+        acc[i].x = fmaf(-a.y, b.y, acc[i].x);
+        acc[i].y = fmaf(a.x, b.y, acc[i].y);
+        acc[i].y = fmaf(a.y, b.x, acc[i].y);
+      }
+    }
+    __syncthreads();
+  }
+  const int c = col0 + tx;
+  if (c >= R) return;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t gr = row0 + ty + 8 * i;
+    if (gr >= T.m) continue;
+    const int64_t crow = T.c_idx >= 0 ? (int64_t)idx[T.c_idx + gr] : T.c_row + gr;
+    if (crow < 0) continue;
+    float2 v = make_float2(T.sign * acc[i].x, T.sign * acc[i].y);
+    if (T.c0_row >= 0) {
+      const float2 c0 = arena[(T.c0_row + gr) * R + c];
+      v.x += c0.x;
+      v.y += c0.y;
+    }
+    arena[crow * R + c] = v;
+  }
+}
+
+// z(own_glob[q]) = x(own_row[q]) for every owned dof.
+__global__ void mf_owned_kernel(const int32_t* __restrict__ own_glob, const int64_t* __restrict__ own_row,
+                                int64_t n_own, const float2* __restrict__ arena, int R, float2* __restrict__ z) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_own * R) return;
+  const int64_t q = t / R;
+  const int c = (int)(t - q * R);
+  z[(int64_t)own_glob[q] * R + c] = arena[own_row[q] * R + c];
+}
+
+unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 32) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, cap));
+}
+
+}  // namespace
+
+void mf_assemble(const int64_t* ptr, const int64_t* target, const int32_t* code, int64_t n_t, const int32_t* tet_ids,
+                 const double* KM, const double* eps, double k0, const double* Bsurf, const int32_t* surf_tet,
+                 double ebr, double ebi, const double2* zc, float2* ws, cudaStream_t s) {
+  if (n_t <= 0) return;
+  note_launch(1);
+  mf_assemble_kernel<<<(unsigned)((n_t + 255) / 256), 256, 0, s>>>(ptr, target, code, n_t, tet_ids, KM, eps, k0,
+                                                                    Bsurf, surf_tet, ebr, ebi, zc, ws);
+}
+
+void mf_extend_add(const int32_t* nodes, int n_nodes, int64_t fmax, const int64_t* f, const int32_t* p,
+                   const int64_t* ws_off, const int64_t* child_ptr, const int32_t* child, const int64_t* inv_off,
+                   const int32_t* inv, float2* ws, cudaStream_t s) {
+  if (n_nodes <= 0) return;
+  note_launch(1);
+  dim3 g(grid_for(fmax * fmax, 256, 1024), n_nodes);
+  mf_extend_add_kernel<<<g, 256, 0, s>>>(nodes, f, p, ws_off, child_ptr, child, inv_off, inv, ws);
+}
+
+void mf_extract(const int32_t* nodes, int n_nodes, int64_t max_entries, const int64_t* f, const int32_t* p,
+                const int64_t* ws_off, const int64_t* fac_off, const float2* ws, float2* fac, cudaStream_t s) {
+  if (n_nodes <= 0) return;
+  note_launch(1);
+  dim3 g(grid_for(max_entries, 256, 1024), n_nodes);
+  mf_extract_kernel<<<g, 256, 0, s>>>(nodes, f, p, ws_off, fac_off, ws, fac);
+}
+
+void mf_rhs(const int32_t* nodes, int n_nodes, int64_t fmax, const int64_t* f, const int32_t* preal,
+            const int64_t* piv_ptr, const int32_t* piv_glob, const int64_t* child_ptr, const int32_t* child,
+            const int64_t* inv_off, const int32_t* inv, const int64_t* rhs_row, const int64_t* w_row,
+            const float2* in, int R, float2* arena, cudaStream_t s) {
+  if (n_nodes <= 0) return;
+  note_launch(1);
+  dim3 g(grid_for(fmax, 8, 512), n_nodes);
+  mf_rhs_kernel<<<g, 256, 0, s>>>(nodes, f, preal, piv_ptr, piv_glob, child_ptr, child, inv_off, inv, rhs_row, w_row,
+                                  in, R, arena);
+}
+
+void mf_gemm(const MfTask* tasks, const int32_t* tile_task, const int32_t* tile_row0, int n_tiles, const float2* fac,
+             const int32_t* idx, int R, float2* arena, cudaStream_t s) {
+  if (n_tiles <= 0) return;
+  note_launch(1);
+  dim3 g((unsigned)n_tiles, (unsigned)((R + kMfCols - 1) / kMfCols));
+  mf_gemm_kernel<<<g, 256, 0, s>>>(tasks, tile_task, tile_row0, fac, idx, R, arena);
+}
+
+void mf_owned(const int32_t* own_glob, const int64_t* own_row, int64_t n_own, const float2* arena, int R, float2* z,
+              cudaStream_t s) {
+  if (n_own <= 0) return;
+  note_launch(1);
+  const int64_t n = n_own * R;
+  mf_owned_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(own_glob, own_row, n_own, arena, R, z);
+}
+
+}  // namespace mwk

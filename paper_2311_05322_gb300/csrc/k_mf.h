@@ -1,0 +1,43 @@
+// Launchers of the multifrontal subdomain factorisation and solve (k_mf.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mwk {
+
+// One product C = C0 + sign * A B of the solve (see mf_gemm_kernel).
+struct MfTask {
+  int64_t a_off;   // element offset of A [m][k] in the factor store
+  int64_t lda;     // row stride of A
+  int64_t m, k;
+  int64_t b_row;   // first arena row of B, when b_idx < 0
+  int64_t b_idx;   // offset of B's arena-row list in idx, or -1
+  int64_t c_row;   // first arena row of C, when c_idx < 0
+  int64_t c_idx;   // offset of C's arena-row list in idx (negative rows are skipped), or -1
+  int64_t c0_row;  // first arena row of C0, or -1 (no C0)
+  float sign;
+  int32_t pad;
+};
+
+// Front entries target[i] of the workspace = sum of the contributions code[ptr[i] .. ptr[i+1]).
+void mf_assemble(const int64_t* ptr, const int64_t* target, const int32_t* code, int64_t n_t, const int32_t* tet_ids,
+                 const double* KM, const double* eps, double k0, const double* Bsurf, const int32_t* surf_tet,
+                 double ebr, double ebi, const double2* zc, float2* ws, cudaStream_t s);
+// Adds the children's Schur complements into the fronts of nodes[0 .. n_nodes).
+void mf_extend_add(const int32_t* nodes, int n_nodes, int64_t fmax, const int64_t* f, const int32_t* p,
+                   const int64_t* ws_off, const int64_t* child_ptr, const int32_t* child, const int64_t* inv_off,
+                   const int32_t* inv, float2* ws, cudaStream_t s);
+// Copies TL | TR and BL of the factored fronts into the factor store (max_entries = largest p f + u p).
+void mf_extract(const int32_t* nodes, int n_nodes, int64_t max_entries, const int64_t* f, const int32_t* p,
+                const int64_t* ws_off, const int64_t* fac_off, const float2* ws, float2* fac, cudaStream_t s);
+// Forward right-hand sides of nodes[0 .. n_nodes): arena rows rhs_row[k] .. + f[k].
+void mf_rhs(const int32_t* nodes, int n_nodes, int64_t fmax, const int64_t* f, const int32_t* preal,
+            const int64_t* piv_ptr, const int32_t* piv_glob, const int64_t* child_ptr, const int32_t* child,
+            const int64_t* inv_off, const int32_t* inv, const int64_t* rhs_row, const int64_t* w_row,
+            const float2* in, int R, float2* arena, cudaStream_t s);
+void mf_gemm(const MfTask* tasks, const int32_t* tile_task, const int32_t* tile_row0, int n_tiles, const float2* fac,
+             const int32_t* idx, int R, float2* arena, cudaStream_t s);
+void mf_owned(const int32_t* own_glob, const int64_t* own_row, int64_t n_own, const float2* arena, int R, float2* z,
+              cudaStream_t s);
+
+}  // namespace mwk

@@ -127,14 +127,16 @@ __device__ __forceinline__ T cmul(T a, T b) {
 // into Dinv[b].  Flags a pivot whose modulus is below tiny * (block max modulus).
 template <typename T>
 __global__ void gj_diag_kernel(const int64_t* __restrict__ nmat, const int64_t* __restrict__ off, T* __restrict__ ws,
-                               int64_t kb, T* __restrict__ Dinv, int32_t* __restrict__ status) {
+                               int64_t kb, T* __restrict__ Dinv, int32_t* __restrict__ status,
+                               const int64_t* __restrict__ lim) {
   using Sc = typename Tr<T>::S;
   __shared__ T D[NB][NB + 1];
   __shared__ Sc dmax;
   const int b = blockIdx.x;
   const int64_t n = nmat[b];
-  if (kb >= n) return;
-  const int bs = (int)min((int64_t)NB, n - kb);
+  const int64_t L = lim ? lim[b] : n;
+  if (kb >= L) return;
+  const int bs = (int)min((int64_t)NB, L - kb);
   const T* A = ws + off[b];
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int i = e / NB, j = e % NB;
@@ -189,13 +191,15 @@ __global__ void gj_diag_kernel(const int64_t* __restrict__ nmat, const int64_t* 
 // A[K, j] <- Dinv A[K, j] for every column j outside K.
 template <typename T>
 __global__ void gj_rowpanel_kernel(const int64_t* __restrict__ nmat, const int64_t* __restrict__ off,
-                                   T* __restrict__ ws, int64_t kb, const T* __restrict__ Dinv) {
+                                   T* __restrict__ ws, int64_t kb, const T* __restrict__ Dinv,
+                                   const int64_t* __restrict__ lim) {
   using Sc = typename Tr<T>::S;
   __shared__ T D[NB][NB];
   const int b = blockIdx.y;
   const int64_t n = nmat[b];
-  if (kb >= n) return;
-  const int bs = (int)min((int64_t)NB, n - kb);
+  const int64_t L = lim ? lim[b] : n;
+  if (kb >= L) return;
+  const int bs = (int)min((int64_t)NB, L - kb);
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) D[e / NB][e % NB] = Dinv[(int64_t)b * NB * NB + e];
   __syncthreads();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -222,17 +226,18 @@ __global__ void gj_rowpanel_kernel(const int64_t* __restrict__ nmat, const int64
 template <typename T>
 __global__ void __launch_bounds__(256) gj_update_kernel(const int64_t* __restrict__ nmat,
                                                         const int64_t* __restrict__ off, T* __restrict__ ws,
-                                                        int64_t kb) {
+                                                        int64_t kb, const int64_t* __restrict__ lim) {
   using Sc = typename Tr<T>::S;
   extern __shared__ unsigned char sm[];
   T* As = reinterpret_cast<T*>(sm);            // [64][NB]
   T* Bs = As + 64 * NB;                        // [NB][64]
   const int b = blockIdx.z;
   const int64_t n = nmat[b];
-  if (kb >= n) return;
+  const int64_t L = lim ? lim[b] : n;
+  if (kb >= L) return;
   const int64_t i0 = (int64_t)blockIdx.y * 64, j0 = (int64_t)blockIdx.x * 64;
   if (i0 >= n || j0 >= n) return;
-  const int bs = (int)min((int64_t)NB, n - kb);
+  const int bs = (int)min((int64_t)NB, L - kb);
   T* A = ws + off[b];
   for (int e = threadIdx.x; e < 64 * NB; e += 256) {
     const int r = e / NB, k = e % NB;
@@ -285,12 +290,14 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const int64_t* __restric
 // A[i, K] <- -A[i, K] Dinv for rows outside K, A[K, K] <- Dinv.
 template <typename T>
 __global__ void gj_colpanel_kernel(const int64_t* __restrict__ nmat, const int64_t* __restrict__ off,
-                                   T* __restrict__ ws, int64_t kb, const T* __restrict__ Dinv) {
+                                   T* __restrict__ ws, int64_t kb, const T* __restrict__ Dinv,
+                                   const int64_t* __restrict__ lim) {
   __shared__ T D[NB][NB];
   const int b = blockIdx.y;
   const int64_t n = nmat[b];
-  if (kb >= n) return;
-  const int bs = (int)min((int64_t)NB, n - kb);
+  const int64_t L = lim ? lim[b] : n;
+  if (kb >= L) return;
+  const int bs = (int)min((int64_t)NB, L - kb);
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) D[e / NB][e % NB] = Dinv[(int64_t)b * NB * NB + e];
   __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -410,8 +417,12 @@ __global__ void __launch_bounds__(256) oras_apply_kernel(const int32_t* __restri
     }
 }
 
+// In-place blocked Gauss-Jordan over the first lim[b] pivots of every matrix (all of them when
+// lim is null): the eliminated block becomes its inverse F11^-1, the rows right of it
+// F11^-1 F12, the columns below it -F21 F11^-1 and the rest the Schur complement.
 template <typename T>
-void gj_all(const OrasBatch& bt, T* ws, T* dinv, int32_t* status, cudaStream_t st) {
+void gj_all(const OrasBatch& bt, T* ws, T* dinv, int32_t* status, cudaStream_t st, const int64_t* lim = nullptr,
+            int64_t lim_max = 0) {
   const int nb = bt.count;
   const int64_t nmax = bt.nmax;
   const size_t smem = sizeof(T) * 2 * 64 * NB;
@@ -420,14 +431,15 @@ void gj_all(const OrasBatch& bt, T* ws, T* dinv, int32_t* status, cudaStream_t s
     cudaFuncSetAttribute(gj_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  for (int64_t kb = 0; kb < nmax; kb += NB) {
+  const int64_t kend = lim ? lim_max : nmax;
+  for (int64_t kb = 0; kb < kend; kb += NB) {
     note_launch(4);
-    gj_diag_kernel<T><<<nb, 256, 0, st>>>(bt.d_n, bt.d_off, ws, kb, dinv, status);
+    gj_diag_kernel<T><<<nb, 256, 0, st>>>(bt.d_n, bt.d_off, ws, kb, dinv, status, lim);
     dim3 g1((unsigned)((nmax + 255) / 256), nb);
-    gj_rowpanel_kernel<T><<<g1, 256, 0, st>>>(bt.d_n, bt.d_off, ws, kb, dinv);
+    gj_rowpanel_kernel<T><<<g1, 256, 0, st>>>(bt.d_n, bt.d_off, ws, kb, dinv, lim);
     dim3 g2((unsigned)((nmax + 63) / 64), (unsigned)((nmax + 63) / 64), nb);
-    gj_update_kernel<T><<<g2, 256, smem, st>>>(bt.d_n, bt.d_off, ws, kb);
-    gj_colpanel_kernel<T><<<g1, 256, 0, st>>>(bt.d_n, bt.d_off, ws, kb, dinv);
+    gj_update_kernel<T><<<g2, 256, smem, st>>>(bt.d_n, bt.d_off, ws, kb, lim);
+    gj_colpanel_kernel<T><<<g1, 256, 0, st>>>(bt.d_n, bt.d_off, ws, kb, dinv, lim);
   }
 }
 
@@ -452,6 +464,11 @@ void oras_invert(const OrasBatch& bt, int prec, void* ws, void* dinv, int32_t* s
     gj_all<double2>(bt, (double2*)ws, (double2*)dinv, status, s);
   else
     gj_all<float2>(bt, (float2*)ws, (float2*)dinv, status, s);
+}
+
+void partial_gj_f32(const OrasBatch& bt, const int64_t* lim, int64_t lim_max, float2* ws, float2* dinv,
+                    int32_t* status, cudaStream_t s) {
+  if (bt.count > 0 && lim_max > 0) gj_all<float2>(bt, ws, dinv, status, s, lim, lim_max);
 }
 
 void oras_extract(const OrasBatch& bt, const OrasTopo& tp, int ws_prec, const void* ws, int w_prec,

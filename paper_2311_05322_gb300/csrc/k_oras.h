@@ -35,6 +35,10 @@ void oras_local_assemble(const OrasBatch& bt, const OrasTopo& tp, const double* 
                          const double* eps, double k0, double eps_bg_re, double eps_bg_im, const double2* zc,
                          const uint8_t* metal, int prec, void* ws, cudaStream_t s);
 void oras_invert(const OrasBatch& bt, int prec, void* ws, void* dinv, int32_t* status, cudaStream_t s);
+// Partial in-place Gauss-Jordan (FP32): eliminates the first lim[b] pivots (a multiple of 32) of
+// each matrix of the batch; lim_max = the largest lim.
+void partial_gj_f32(const OrasBatch& bt, const int64_t* lim, int64_t lim_max, float2* ws, float2* dinv,
+                    int32_t* status, cudaStream_t s);
 void oras_extract(const OrasBatch& bt, const OrasTopo& tp, int ws_prec, const void* ws, int w_prec,
                   const int64_t* w_off, void* W, cudaStream_t s);
 void oras_apply_cc(const OrasTopo& tp, int n_tiles, const int32_t* tile_sub, const int32_t* tile_row0, int prec,

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "k_adjoint.h"
+#include "k_mf.h"
 #include "k_nn.h"
 #include "k_oras.h"
 #include "k_oras_tc.h"
@@ -53,6 +54,7 @@ struct Prec {
   bool ready = false;
   int apply_prec = 0;    // 0 FP64, 1 FP32, 2 BF16 (tensor cores)
   int factor_prec = 0;   // 0 FP64, 1 FP32
+  int sparse_leaf = 64;  // nested-dissection leaf size of the sparse solves
   mw::Subdomains sd;
   // device copies
   int64_t *dof_ptr = nullptr, *own_ptr = nullptr, *tet_ptr = nullptr, *surf_ptr = nullptr;
@@ -65,6 +67,24 @@ struct Prec {
   std::vector<void*> W;              // per frequency
   mwk::TcPlan tc;                    // BF16 tensor-core layout
   double sum_own_n = 0, sum_n = 0;   // sum_s n_own,s n_s and sum_s n_s
+  // sparse (multifrontal) subdomain solves, apply_prec 4
+  struct Mf {
+    mw::Multifrontal sym;
+    std::vector<void*> allocs;       // every device table below
+    int64_t *f = nullptr, *ws_off = nullptr, *fac_off = nullptr, *piv_ptr = nullptr, *child_ptr = nullptr,
+            *inv_off = nullptr, *rhs_row = nullptr, *w_row = nullptr, *own_row = nullptr, *asm_ptr = nullptr,
+            *asm_target = nullptr, *sh_f = nullptr, *sh_off = nullptr, *sh_lim = nullptr;
+    int32_t *p = nullptr, *preal = nullptr, *piv_glob = nullptr, *child = nullptr, *inv = nullptr, *idx = nullptr,
+            *asm_code = nullptr, *sh_nodes = nullptr, *h_nodes = nullptr, *tile_task = nullptr, *tile_row0 = nullptr;
+    mwk::MfTask* tasks = nullptr;
+    std::vector<int64_t> sh_ptr;     // [(n_sub * (H + 1)) + 1] node ranges per (subdomain, height)
+    std::vector<int64_t> sh_fmax, sh_pmax, sh_emax;
+    std::vector<int64_t> h_ptr;      // [H + 2] node ranges per height (all subdomains)
+    std::vector<int64_t> h_fmax;
+    std::vector<int64_t> fwd_tiles, bwd_tiles;  // [H + 2] tile ranges per height
+    int64_t arena_rows = 0, ws_max = 0, n_own = 0, max_sh = 0;
+    std::vector<void*> fac;          // factors per frequency (FP32 complex)
+  } mf;
   mwk::OrasTopo topo() const {
     return {dof_ptr, dofs, own_ptr, own_local, own_glob, tet_ptr, tet_ids, tet_loc, surf_ptr, surf_loc, surf_tet};
   }
@@ -88,6 +108,8 @@ struct Work {
   int32_t* h_ivec = nullptr;    // pinned [R]
   void* tc_scratch = nullptr;   // BF16 gathered operand
   size_t tc_bytes = 0;
+  void* mf_arena = nullptr;     // vectors of the sparse subdomain solves
+  size_t mf_bytes = 0;
 };
 
 // Optional per-kernel-class timing with CUDA events on the context stream.
@@ -227,6 +249,8 @@ struct Ctx {
   double* d_red = nullptr;     // reduction scratch
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
+  int mf_leaf = 64;          // nested-dissection leaf size for the next sparse preconditioner
+
   // tuned launch shapes
   bool autotune_on = true;
   std::vector<Tuned> tuned;
@@ -346,7 +370,7 @@ void free_work(Ctx* c) {
   Work& w = c->work;
   for (void* p : {(void*)w.V, (void*)w.Z, (void*)w.xdf, (void*)w.r, (void*)w.x, (void*)w.part, (void*)w.h, (void*)w.H, (void*)w.cs,
                   (void*)w.g, (void*)w.y, (void*)w.npart, (void*)w.target, (void*)w.rnorm, (void*)w.bnorm,
-                  (void*)w.scale, (void*)w.done, (void*)w.kcol, (void*)w.active, (void*)w.bblk, (void*)w.kerr, (void*)w.bdf, (void*)w.r32, (void*)w.vscale, w.tc_scratch})
+                  (void*)w.scale, (void*)w.done, (void*)w.kcol, (void*)w.active, (void*)w.bblk, (void*)w.kerr, (void*)w.bdf, (void*)w.r32, (void*)w.vscale, w.tc_scratch, w.mf_arena})
     dfree(c, p);
   if (w.h_active) cudaFreeHost(w.h_active);
   if (w.h_vec) cudaFreeHost(w.h_vec);
@@ -407,8 +431,18 @@ void ensure_work(Ctx* c, int R, int m, int prec) {
 // happen while the stream is captured).
 void ensure_prec_scratch(Ctx* c, int R) {
   Prec& p = c->prec;
-  if (!p.ready || p.apply_prec != 2) return;
   Work& w = c->work;
+  if (p.ready && p.apply_prec == 4) {
+    const size_t need = (size_t)p.mf.arena_rows * R * sizeof(float2);
+    if (w.mf_bytes < need) {
+      dfree(c, w.mf_arena);
+      w.mf_arena = nullptr;
+      w.mf_arena = dalloc<unsigned char>(c, need);
+      w.mf_bytes = need;
+    }
+    return;
+  }
+  if (!p.ready || p.apply_prec != 2) return;
   const size_t need = mwk::tc_scratch_bytes(p.tc, R);
   if (w.tc_bytes < need) {
     dfree(c, w.tc_scratch);
@@ -417,11 +451,283 @@ void ensure_prec_scratch(Ctx* c, int R) {
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// sparse (multifrontal) subdomain solves
+// ---------------------------------------------------------------------------------------
+// z(owned rows) = sum_s R_s^T D_s B_s^-1 R_s v for R columns (FP32), every subdomain at once.
+void apply_sparse(Ctx* c, int f, const float2* v, float2* z, int R) {
+  Prec::Mf& m = c->prec.mf;
+  Work& w = c->work;
+  cudaStream_t s = c->stream;
+  require(R >= 1 && R <= 128, MW_EINVAL, "the sparse preconditioner takes 1..128 columns");
+  const size_t need = (size_t)m.arena_rows * R * sizeof(float2);
+  if (w.mf_bytes < need) {
+    dfree(c, w.mf_arena);
+    w.mf_arena = nullptr;
+    w.mf_arena = dalloc<unsigned char>(c, need);
+    w.mf_bytes = need;
+  }
+  float2* arena = (float2*)w.mf_arena;
+  const float2* fac = (const float2*)m.fac[f];
+  const int H = m.sym.max_height;
+  for (int h = 0; h <= H; ++h) {
+    const int64_t n0 = m.h_ptr[h], n1 = m.h_ptr[h + 1];
+    mwk::mf_rhs(m.h_nodes + n0, (int)(n1 - n0), m.h_fmax[h], m.f, m.preal, m.piv_ptr, m.piv_glob, m.child_ptr,
+                m.child, m.inv_off, m.inv, m.rhs_row, m.w_row, v, R, arena, s);
+    mwk::mf_gemm(m.tasks, m.tile_task + m.fwd_tiles[h], m.tile_row0 + m.fwd_tiles[h],
+                 (int)(m.fwd_tiles[h + 1] - m.fwd_tiles[h]), fac, m.idx, R, arena, s);
+  }
+  for (int h = H; h >= 0; --h)
+    mwk::mf_gemm(m.tasks, m.tile_task + m.bwd_tiles[h], m.tile_row0 + m.bwd_tiles[h],
+                 (int)(m.bwd_tiles[h + 1] - m.bwd_tiles[h]), fac, m.idx, R, arena, s);
+  mwk::mf_owned(c->prec.own_glob, m.own_row, m.n_own, arena, R, z, s);
+}
+
+template <typename T>
+T* mf_up(Ctx* c, Prec::Mf& m, const std::vector<T>& h) {
+  T* d = upload_vec(c, h);
+  m.allocs.push_back(d);
+  return d;
+}
+
+// Symbolic factorisation on the host, device tables, then the numeric factorisation of every
+// subdomain for every frequency (FP32 fronts in a workspace, partial Gauss-Jordan per height).
+void setup_sparse(Ctx* c) {
+  Prec& P = c->prec;
+  Prec::Mf& m = P.mf;
+  const mw::Subdomains& sd = P.sd;
+  Error err{MW_OK, ""};
+  const uint8_t* metal = c->metal.empty() ? nullptr : c->metal.data();
+  if (!mw::build_multifrontal(c->topo, sd, c->xyz, metal, P.sparse_leaf, m.sym, err)) throw Fail{err.code, err.msg};
+  const mw::Multifrontal& y = m.sym;
+  const int N = y.n_nodes, H = y.max_height, S = sd.n_sub;
+  // arena rows: rhs (f), t (p), w (u) per node, then x (n_s) per subdomain
+  std::vector<int64_t> rhs_row(N), t_row(N), w_row(N), x_row(S);
+  int64_t rows = 0;
+  for (int k = 0; k < N; ++k) { rhs_row[k] = rows; rows += y.f[k]; }
+  for (int k = 0; k < N; ++k) { t_row[k] = rows; rows += y.p[k]; }
+  for (int k = 0; k < N; ++k) { w_row[k] = rows; rows += y.u[k]; }
+  for (int s = 0; s < S; ++s) { x_row[s] = rows; rows += sd.dof_ptr[s + 1] - sd.dof_ptr[s]; }
+  require(rows < INT32_MAX, MW_EINVAL, "sparse preconditioner too large");
+  m.arena_rows = rows;
+  // pivots as global edges (forward input) and as arena rows of x; update dofs as arena rows of x
+  std::vector<int32_t> piv_glob(y.piv_loc.size()), idx;
+  std::vector<int64_t> bidx(N, -1), cidx(N, -1);
+  for (int k = 0; k < N; ++k) {
+    const int sub = y.sub[k];
+    const int64_t d0 = sd.dof_ptr[sub];
+    for (int64_t q = y.piv_ptr[k]; q < y.piv_ptr[k + 1]; ++q) piv_glob[q] = sd.dofs[d0 + y.piv_loc[q]];
+    bidx[k] = (int64_t)idx.size();
+    for (int64_t q = y.upd_ptr[k]; q < y.upd_ptr[k + 1]; ++q) idx.push_back((int32_t)(x_row[sub] + y.upd_loc[q]));
+    cidx[k] = (int64_t)idx.size();
+    const int32_t pr = y.preal[k];
+    for (int32_t i = 0; i < y.p[k]; ++i)
+      idx.push_back(i < pr ? (int32_t)(x_row[sub] + y.piv_loc[y.piv_ptr[k] + i]) : -1);
+  }
+  // nodes per height (all subdomains) and per (subdomain, height)
+  std::vector<int32_t> h_nodes, sh_nodes;
+  std::vector<int64_t> sh_f, sh_off, sh_lim;
+  m.h_ptr.assign(1, 0);
+  m.h_fmax.assign(H + 1, 0);
+  for (int h = 0; h <= H; ++h) {
+    for (int k = 0; k < N; ++k)
+      if (y.height[k] == h) {
+        h_nodes.push_back(k);
+        m.h_fmax[h] = std::max(m.h_fmax[h], y.f[k]);
+      }
+    m.h_ptr.push_back((int64_t)h_nodes.size());
+  }
+  m.sh_ptr.assign(1, 0);
+  for (int s = 0; s < S; ++s)
+    for (int h = 0; h <= H; ++h) {
+      int64_t fm = 0, pm = 0, em = 0;
+      for (int64_t k = y.sub_node_ptr[s]; k < y.sub_node_ptr[s + 1]; ++k)
+        if (y.height[k] == h) {
+          sh_nodes.push_back((int32_t)k);
+          sh_f.push_back(y.f[k]);
+          sh_off.push_back(y.ws_off[k]);
+          sh_lim.push_back(y.p[k]);
+          fm = std::max(fm, y.f[k]);
+          pm = std::max<int64_t>(pm, y.p[k]);
+          em = std::max<int64_t>(em, (int64_t)y.p[k] * y.f[k] + (int64_t)y.u[k] * y.p[k]);
+        }
+      m.sh_ptr.push_back((int64_t)sh_nodes.size());
+      m.sh_fmax.push_back(fm);
+      m.sh_pmax.push_back(pm);
+      m.sh_emax.push_back(em);
+      m.max_sh = std::max<int64_t>(m.max_sh, m.sh_ptr.back() - m.sh_ptr[m.sh_ptr.size() - 2]);
+    }
+  // GEMM tasks and their 64-row tiles, per height: forward t and w, backward x
+  std::vector<mwk::MfTask> tasks;
+  std::vector<int32_t> tile_task, tile_row0;
+  auto add_task = [&](const mwk::MfTask& t) {
+    const int32_t id = (int32_t)tasks.size();
+    tasks.push_back(t);
+    for (int64_t r0 = 0; r0 < t.m; r0 += 64) {
+      tile_task.push_back(id);
+      tile_row0.push_back((int32_t)r0);
+    }
+  };
+  m.fwd_tiles.assign(1, 0);
+  for (int h = 0; h <= H; ++h) {
+    for (int64_t q = m.h_ptr[h]; q < m.h_ptr[h + 1]; ++q) {
+      const int k = h_nodes[q];
+      const int64_t p = y.p[k], u = y.u[k], ff = y.f[k];
+      if (p > 0) add_task({y.fac_off[k], ff, p, p, rhs_row[k], -1, t_row[k], -1, -1, 1.f, 0});
+      if (u > 0) add_task({y.fac_off[k] + p * ff, std::max<int64_t>(p, 1), u, p, rhs_row[k], -1, w_row[k], -1,
+                           rhs_row[k] + p, 1.f, 0});
+    }
+    m.fwd_tiles.push_back((int64_t)tile_task.size());
+  }
+  m.bwd_tiles.assign(1, m.fwd_tiles.back());
+  for (int h = 0; h <= H; ++h) {
+    for (int64_t q = m.h_ptr[h]; q < m.h_ptr[h + 1]; ++q) {
+      const int k = h_nodes[q];
+      const int64_t p = y.p[k], u = y.u[k], ff = y.f[k];
+      if (p > 0) add_task({y.fac_off[k] + p, ff, p, u, -1, bidx[k], -1, cidx[k], t_row[k], -1.f, 0});
+    }
+    m.bwd_tiles.push_back((int64_t)tile_task.size());
+  }
+  // owned rows of x
+  std::vector<int64_t> own_row(sd.own_local.size());
+  for (int s = 0; s < S; ++s)
+    for (int64_t q = sd.own_ptr[s]; q < sd.own_ptr[s + 1]; ++q) own_row[q] = x_row[s] + sd.own_local[q];
+  m.n_own = (int64_t)own_row.size();
+  // every index the kernels will follow, checked against its buffer before the first launch
+  {
+    const char* bad = "internal: sparse preconditioner table out of range";
+    const int64_t n_slot_t = (int64_t)sd.tet_ids.size(), n_slot_f = (int64_t)sd.surf_tet.size();
+    for (int s = 0; s < S; ++s)
+      for (int64_t i = y.asm_sub_ptr[s]; i < y.asm_sub_ptr[s + 1]; ++i) {
+        require(y.asm_target[i] >= 0 && y.asm_target[i] < y.ws_size[s], MW_EINVAL, bad);
+        require(y.asm_ptr[i] <= y.asm_ptr[i + 1] && y.asm_ptr[i + 1] <= (int64_t)y.asm_code.size(), MW_EINVAL, bad);
+        for (int64_t q = y.asm_ptr[i]; q < y.asm_ptr[i + 1]; ++q) {
+          const int32_t cd = y.asm_code[q];
+          if (cd == mw::Multifrontal::kIdentity) continue;
+          if (cd >= 0)
+            require(cd / 36 < n_slot_t, MW_EINVAL, bad);
+          else
+            require((-(int64_t)cd - 1) / 9 < n_slot_f, MW_EINVAL, bad);
+        }
+      }
+    for (int k = 0; k < N; ++k) {
+      const int64_t p = y.p[k], u = y.u[k], ff = y.f[k];
+      require(p % 32 == 0 && p >= y.preal[k] && ff == p + u, MW_EINVAL, bad);
+      require(y.ws_off[k] >= 0 && y.ws_off[k] + ff * ff <= y.ws_size[y.sub[k]], MW_EINVAL, bad);
+      require(y.fac_off[k] >= 0 && y.fac_off[k] + p * ff + u * p <= y.fac_total, MW_EINVAL, bad);
+      require(rhs_row[k] + ff <= rows && t_row[k] + p <= rows && w_row[k] + u <= rows, MW_EINVAL, bad);
+      for (int64_t q = y.child_ptr[k]; q < y.child_ptr[k + 1]; ++q) {
+        const int32_t ch = y.child[q];
+        require(ch >= 0 && ch < N && y.parent[ch] == k && y.sub[ch] == y.sub[k], MW_EINVAL, bad);
+        require(y.inv_off[ch] >= 0 && y.inv_off[ch] + ff <= (int64_t)y.inv.size(), MW_EINVAL, bad);
+        for (int64_t r = 0; r < ff; ++r) {
+          const int32_t a = y.inv[y.inv_off[ch] + r];
+          require(a >= -1 && a < y.u[ch], MW_EINVAL, bad);
+        }
+      }
+    }
+    for (int32_t g : piv_glob) require(g >= 0 && g < c->topo.n_edge, MW_EINVAL, bad);
+    for (int32_t r : idx) require(r >= -1 && r < rows, MW_EINVAL, bad);
+    for (const mwk::MfTask& t : tasks) {
+      if (t.m > 0 && t.k > 0) require(t.a_off >= 0 && t.a_off + (t.m - 1) * t.lda + t.k <= y.fac_total, MW_EINVAL, bad);
+      if (t.b_idx >= 0) {
+        require(t.b_idx + t.k <= (int64_t)idx.size(), MW_EINVAL, bad);
+        for (int64_t i = 0; i < t.k; ++i) require(idx[t.b_idx + i] >= 0, MW_EINVAL, bad);
+      } else
+        require(t.b_row >= 0 && t.b_row + t.k <= rows, MW_EINVAL, bad);
+      if (t.c_idx >= 0)
+        require(t.c_idx + t.m <= (int64_t)idx.size(), MW_EINVAL, bad);
+      else
+        require(t.c_row >= 0 && t.c_row + t.m <= rows, MW_EINVAL, bad);
+      if (t.c0_row >= 0) require(t.c0_row + t.m <= rows, MW_EINVAL, bad);
+    }
+    for (int64_t r : own_row) require(r >= 0 && r < rows, MW_EINVAL, bad);
+  }
+  std::vector<int32_t> pp(y.p.begin(), y.p.end());
+  m.f = mf_up(c, m, y.f);
+  m.ws_off = mf_up(c, m, y.ws_off);
+  m.fac_off = mf_up(c, m, y.fac_off);
+  m.piv_ptr = mf_up(c, m, y.piv_ptr);
+  m.child_ptr = mf_up(c, m, y.child_ptr);
+  m.inv_off = mf_up(c, m, y.inv_off);
+  m.rhs_row = mf_up(c, m, rhs_row);
+  m.w_row = mf_up(c, m, w_row);
+  m.own_row = mf_up(c, m, own_row);
+  m.asm_ptr = mf_up(c, m, y.asm_ptr);
+  m.asm_target = mf_up(c, m, y.asm_target);
+  m.sh_f = mf_up(c, m, sh_f);
+  m.sh_off = mf_up(c, m, sh_off);
+  m.sh_lim = mf_up(c, m, sh_lim);
+  m.p = mf_up(c, m, pp);
+  m.preal = mf_up(c, m, y.preal);
+  m.piv_glob = mf_up(c, m, piv_glob);
+  m.child = mf_up(c, m, y.child);
+  m.inv = mf_up(c, m, y.inv);
+  m.idx = mf_up(c, m, idx);
+  m.asm_code = mf_up(c, m, y.asm_code);
+  m.sh_nodes = mf_up(c, m, sh_nodes);
+  m.h_nodes = mf_up(c, m, h_nodes);
+  m.tile_task = mf_up(c, m, tile_task);
+  m.tile_row0 = mf_up(c, m, tile_row0);
+  m.tasks = mf_up(c, m, tasks);
+  for (int64_t v : y.ws_size) m.ws_max = std::max(m.ws_max, v);
+  // numeric factorisation
+  float2* ws = dalloc<float2>(c, std::max<int64_t>(m.ws_max, 1));
+  float2* dinv = nullptr;
+  int32_t* status = nullptr;
+  try {
+    dinv = dalloc<float2>(c, std::max<int64_t>(m.max_sh, 1) * 32 * 32);
+    status = dalloc<int32_t>(c, 1);
+    CK(cudaMemsetAsync(status, 0, sizeof(int32_t), c->stream));
+    m.fac.assign(c->n_freq, nullptr);
+    for (int f = 0; f < c->n_freq; ++f) {
+      m.fac[f] = dalloc<float2>(c, std::max<int64_t>(y.fac_total, 1));
+      const double k0 = k0_of(c->freqs[f]);
+      const double2* zc = c->d_zc ? c->d_zc + (size_t)f * (2 + c->n_port) : nullptr;
+      for (int s = 0; s < S; ++s) {
+        CK(cudaMemsetAsync(ws, 0, sizeof(float2) * y.ws_size[s], c->stream));
+        const int64_t t0 = y.asm_sub_ptr[s], t1 = y.asm_sub_ptr[s + 1];
+        mwk::mf_assemble(m.asm_ptr + t0, m.asm_target + t0, m.asm_code, t1 - t0, P.tet_ids, c->d_KM, c->d_eps, k0,
+                         P.Bsurf, P.surf_tet, c->eps_bg[0], c->eps_bg[1], zc, ws, c->stream);
+        for (int h = 0; h <= H; ++h) {
+          const size_t b = (size_t)s * (H + 1) + h;
+          const int64_t q0 = m.sh_ptr[b], q1 = m.sh_ptr[b + 1];
+          if (q1 == q0) continue;
+          const int cnt = (int)(q1 - q0);
+          if (h > 0)
+            mwk::mf_extend_add(m.sh_nodes + q0, cnt, m.sh_fmax[b], m.f, m.p, m.ws_off, m.child_ptr, m.child,
+                               m.inv_off, m.inv, ws, c->stream);
+          mwk::OrasBatch bt{cnt, m.sh_fmax[b], m.sh_nodes + q0, m.sh_f + q0, m.sh_off + q0};
+          mwk::partial_gj_f32(bt, m.sh_lim + q0, m.sh_pmax[b], ws, dinv, status, c->stream);
+          mwk::mf_extract(m.sh_nodes + q0, cnt, m.sh_emax[b], m.f, m.p, m.ws_off, m.fac_off, ws, (float2*)m.fac[f],
+                          c->stream);
+        }
+        check_launch("sparse factorisation");
+      }
+    }
+    int32_t st = 0;
+    CK(cudaMemcpyAsync(&st, status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    require(st == 0, MW_ESINGULAR, "a front had a near-zero pivot");
+  } catch (...) {
+    dfree(c, ws);
+    dfree(c, dinv);
+    dfree(c, status);
+    throw;
+  }
+  dfree(c, ws);
+  dfree(c, dinv);
+  dfree(c, status);
+}
+
 void apply_prec(Ctx* c, int f, int work_prec, const void* v, void* z, int R, int stages = 0,
                 const double* in_scale = nullptr) {
   Prec& p = c->prec;
   cudaStream_t s = c->stream;
-  if (p.apply_prec == 2) {
+  if (p.apply_prec == 4) {
+    require(work_prec == 1, MW_EINVAL, "the sparse preconditioner needs the mixed-precision solve");
+    apply_sparse(c, f, (const float2*)v, (float2*)z, R);
+  } else if (p.apply_prec == 2) {
     require(work_prec == 1, MW_EINVAL, "BF16 preconditioner needs the mixed-precision solve");
     Work& w = c->work;
     ensure_prec_scratch(c, R);
@@ -462,6 +768,7 @@ struct ProfScope {
 // the gathered subdomain inputs and the owned outputs.
 double oras_bytes(Ctx* c, int R) {
   const Prec& p = c->prec;
+  if (p.apply_prec == 4) return 8.0 * (double)p.mf.sym.fac_total + 8.0 * R * (p.sum_n + (double)c->topo.n_edge);
   const double wb = p.apply_prec == 0 ? 16.0 : (p.apply_prec == 1 ? 8.0 : 4.0);
   const double vb = p.apply_prec == 0 ? 16.0 : 8.0;
   return wb * p.sum_own_n + vb * R * (p.sum_n + (double)c->topo.n_edge);
@@ -1211,6 +1518,8 @@ void release_prec(Ctx* c) {
                   (void*)p.w_off})
     dfree(c, q);
   for (void* q : p.W) dfree(c, q);
+  for (void* q : p.mf.allocs) dfree(c, q);
+  for (void* q : p.mf.fac) dfree(c, q);
   mwk::tc_plan_free(p.tc, [&](void* q) { dfree(c, q); });
   p = Prec();
   c->tuned.clear();
@@ -1898,8 +2207,8 @@ mw_status mw_get_port_vectors(mw_ctx* c, double* W, double* norms) {
 mw_status mw_setup_preconditioner(mw_ctx* c, int32_t n_sub, const int32_t* part, int32_t overlap, int32_t inv_prec) {
   return guard(c, [&] {
     require(c->has_mesh && c->n_freq > 0, MW_ESTATE, "assemble before setting up the preconditioner");
-    require(inv_prec >= 0 && inv_prec <= 3, MW_EINVAL, "inv_prec must be 0 (FP64), 1 (FP32), 2 (BF16) or 3 (FP32 "
-                                                       "factorisation applied in FP64)");
+    require(inv_prec >= 0 && inv_prec <= 4, MW_EINVAL, "inv_prec must be 0 (FP64), 1 (FP32), 2 (BF16), 3 (FP32 "
+                                                       "factorisation applied in FP64) or 4 (sparse)");
     release_prec(c);
     Prec& p = c->prec;
     Error err{MW_OK, ""};
@@ -1907,6 +2216,7 @@ mw_status mw_setup_preconditioner(mw_ctx* c, int32_t n_sub, const int32_t* part,
     const mw::Subdomains& sd = p.sd;
     p.apply_prec = inv_prec == 3 ? 0 : inv_prec;
     p.factor_prec = inv_prec == 0 ? 0 : 1;
+    p.sparse_leaf = c->mf_leaf;
     p.dof_ptr = upload(c, sd.dof_ptr.data(), sd.dof_ptr.size());
     p.dofs = upload(c, sd.dofs.data(), sd.dofs.size());
     p.own_ptr = upload(c, sd.own_ptr.data(), sd.own_ptr.size());
@@ -1938,6 +2248,17 @@ mw_status mw_setup_preconditioner(mw_ctx* c, int32_t n_sub, const int32_t* part,
     const int64_t n_surf = (int64_t)sd.surf_tet.size();
     p.Bsurf = dalloc<double>(c, 6 * std::max<int64_t>(n_surf, 1));
     mwk::face_geom(c->d_xyz, p.surf_vert, n_surf, p.Bsurf, c->stream);
+    if (inv_prec == 4) {
+      for (int s = 0; s < n_sub; ++s) p.sum_n += (double)(sd.dof_ptr[s + 1] - sd.dof_ptr[s]);
+      try {
+        setup_sparse(c);
+      } catch (...) {
+        release_prec(c);
+        throw;
+      }
+      p.ready = true;
+      return;
+    }
     // W offsets (cc layouts) and apply tiles
     std::vector<int64_t> woff(n_sub + 1, 0);
     std::vector<int32_t> tsub, trow;

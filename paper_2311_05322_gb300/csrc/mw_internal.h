@@ -75,6 +75,48 @@ struct Subdomains {
 bool build_subdomains(const Topology& topo, int32_t n_sub, const int32_t* tet_part, int32_t overlap,
                       Subdomains& sd, Error& err);
 
+// Sparse local solves (multifrontal LU on a nested-dissection tree per subdomain).
+// Every node k of a subdomain's tree owns a front of f_k = p_k + u_k rows: p_k pivots (its
+// separator dofs, preal_k of them, padded with identity rows to a multiple of 32) followed by
+// u_k update dofs (later-eliminated dofs coupled to the pivots or to a descendant's update).
+// Partial Gauss-Jordan on the first p_k pivots leaves the factors
+//   TL = F11^-1 [p][p], TR = F11^-1 F12 [p][u], BL = -F21 F11^-1 [u][p]
+// and the Schur complement F22 - F21 F11^-1 F12, which the parent adds into its front.
+struct Multifrontal {
+  static constexpr int kPad = 32;
+  int32_t n_nodes = 0, max_height = 0;
+  std::vector<int32_t> sub;        // [nodes] subdomain of each node
+  std::vector<int32_t> p, preal, u, height, parent;
+  std::vector<int64_t> f;          // p + u
+  std::vector<int64_t> fac_off;    // element offset of TL|TR ([p][f]) then BL ([u][p])
+  int64_t fac_total = 0;
+  std::vector<int64_t> piv_ptr;    // [nodes+1] real pivots (local dof index within the subdomain)
+  std::vector<int32_t> piv_loc;
+  std::vector<int64_t> upd_ptr;    // [nodes+1] update dofs in elimination order (local index)
+  std::vector<int32_t> upd_loc;
+  std::vector<int64_t> child_ptr;  // [nodes+1] children
+  std::vector<int32_t> child;
+  std::vector<int64_t> inv_off;    // [nodes] offset of the node's map into its parent's front rows
+  std::vector<int32_t> inv;        // for child c: inv[inv_off[c] + r] = update index of parent row r, or -1
+  std::vector<int64_t> sub_node_ptr;  // [n_sub+1] nodes of each subdomain (post-order, contiguous)
+  // front assembly of the original entries, per subdomain: targets (row * f + col within the
+  // node's front, plus the node's workspace offset) and contribution codes, sorted by target;
+  // code >= 0: tet slot * 36 + m * 6 + n; code in [-2^30, 0): -1 - (surface slot * 9 + m * 3 + n);
+  // kIdentity: a one on the diagonal (metal dof or padding pivot)
+  static constexpr int32_t kIdentity = INT32_MIN;
+  std::vector<int64_t> ws_off;     // [nodes] element offset of the front in its subdomain's workspace
+  std::vector<int64_t> ws_size;    // [n_sub] elements of each subdomain's workspace
+  std::vector<int64_t> asm_ptr;    // [targets+1] per subdomain concatenated (see asm_sub_ptr)
+  std::vector<int64_t> asm_target;
+  std::vector<int32_t> asm_code;
+  std::vector<int64_t> asm_sub_ptr;  // [n_sub+1] ranges of targets per subdomain
+};
+
+// Builds the trees, the symbolic factorisation and the assembly maps for every subdomain.
+// metal (optional, [E]): metal edges, whose rows and columns are those of the identity.
+bool build_multifrontal(const Topology& topo, const Subdomains& sd, const std::vector<double>& xyz,
+                        const uint8_t* metal, int leaf, Multifrontal& mf, Error& err);
+
 // ------------------------------------------------------------------------------------
 // Host L-BFGS (reverse communication)
 // ------------------------------------------------------------------------------------
