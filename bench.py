@@ -45,7 +45,9 @@ def _args(argv=None):
     ap.add_argument("--freqs", default="1.0e9", help="comma-separated frequencies (Hz)")
     ap.add_argument("--parts", default="16x16x7")
     ap.add_argument("--overlap", type=int, default=1)
-    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32", "sparse"],
+                    help="subdomain solves: dense inverses applied in BF16 (tensor cores) or FP32, or sparse "
+                         "multifrontal factors (large subdomains)")
     ap.add_argument("--alpha", type=float, default=1e-3)
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--plain-cols", type=int, default=1, help="columns timed on the plain FP64 path (0 = skip)")
@@ -182,6 +184,10 @@ def aggregate(units_per_rank: float, seconds: float, world: int, dist=None):
     return units_per_rank * world / seconds, seconds
 
 
+# FP32 FMA peak of one GB300 from its unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -291,7 +297,7 @@ def run_mine(a):
         hom = np.stack([hom_c.real, hom_c.imag], 1)
     # preconditioner of the background medium, reused stale for every eps (as in an inversion)
     c.assemble(freqs, hom, healthy.eps_bg)
-    prec = {"bf16": mw.MW_PREC_BF16, "fp32": mw.MW_PREC_FP32}[a.prec]
+    prec = {"bf16": mw.MW_PREC_BF16, "fp32": mw.MW_PREC_FP32, "sparse": mw.MW_PREC_SPARSE}[a.prec]
     t = time.perf_counter()
     c.setup_preconditioner(n_sub, part, a.overlap, prec)
     torch.cuda.synchronize()
@@ -420,7 +426,7 @@ def run_mine(a):
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-    ratio = oras_traffic_ratio() if dom == "oras_apply" else None
+    ratio = oras_traffic_ratio() if dom == "oras_apply" and prec != mw.MW_PREC_SPARSE else None
     traffic = ratio * d["bytes"] / max(d["launches"], 1) if ratio else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_source": src, "traffic": traffic,
@@ -432,6 +438,18 @@ def run_mine(a):
             "classes": {k: {"ms": v["ms"], "launches": v["launches"],
                             "GBs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0}
                         for k, v in prof.items()}}
+
+    if prec == mw.MW_PREC_SPARSE and dom == "oras_apply":
+        # the sparse sweeps multiply every stored factor entry by all R columns: 8 flop per complex
+        # entry and column, FP32 CUDA cores (the factor count follows from the algorithmic bytes)
+        per = d["bytes"] / max(d["launches"], 1)
+        fac_entries = (per - 8.0 * a.n_src * (float(sizes.sum()) + info.n_edge)) / 8.0
+        flops = 8.0 * fac_entries * a.n_src * d["launches"]
+        tf = flops / (d["ms"] * 1e-3) / 1e12
+        roof.update({"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": tf / FP32_PEAK_TFLOPS, "traffic": None, "traffic_note": None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "factor_entries": fac_entries})
 
     # ---- CPU oracle sample -------------------------------------------------------------------
     cpu = None
@@ -464,7 +482,8 @@ def run_mine(a):
                        "cycles": "CUDA graph per restart cycle (conditional nodes)" if a.graphs else "eager",
                        "launch_shapes": {k: tune[k] for k in ("tc_stages", "dots_stages", "update_stages",
                                                               "spmm_threads")},
-                       "preconditioner_apply": {2: "bf16 tcgen05", 1: "fp32 cuda-core"}.get(prec, str(prec)),
+                       "preconditioner_apply": {2: "bf16 tcgen05", 1: "fp32 cuda-core",
+                                                4: "fp32 multifrontal sweeps"}.get(prec, str(prec)),
                        "tol": 1e-8, "inner_tol": a.inner_tol, "alpha": a.alpha,
                        "l2": "inputs larger than L2 (subdomain inverses and Krylov basis are GBs)"},
             "roofline": roof, "cpu_baseline": cpu,

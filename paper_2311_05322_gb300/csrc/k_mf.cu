@@ -168,36 +168,47 @@ __global__ void mf_rhs_kernel(const int32_t* __restrict__ nodes, const int64_t* 
 
 // Task-list GEMM: C = C0 + sign * A B for every task, A [m][k] (row stride lda) in the factor
 // store, B [k][R] and C, C0 [m][R] in the vector arena.  Rows of B and C are either consecutive
-// from an arena row or listed (b_idx / c_idx; a negative C row is skipped).  A CTA computes a
-// 64-row x 32-column tile; tile_task / tile_row0 list the 64-row tiles of all tasks.
-constexpr int kMfRows = 64, kMfK = 32, kMfCols = 32;
+// from an arena row or listed (b_idx / c_idx; a negative C row is skipped).  A CTA of 128
+// threads computes a 64-row x 32-column tile, each thread 4 rows x 4 columns (rows tr + 16 i,
+// columns tc + 8 j), over K chunks of 32 staged in shared memory; tile_task / tile_row0 list
+// the 64-row tiles of all tasks.
+constexpr int kMfRows = 64, kMfK = 32, kMfCols = 32, kMfThreads = 128;
 
-__global__ void __launch_bounds__(256) mf_gemm_kernel(const MfTask* __restrict__ tasks,
-                                                      const int32_t* __restrict__ tile_task,
-                                                      const int32_t* __restrict__ tile_row0,
-                                                      const float2* __restrict__ fac, const int32_t* __restrict__ idx,
-                                                      int R, float2* __restrict__ arena) {
+//
+// Split K: a tile with tile_slot >= 0 covers only K range [tile_k0, tile_k1) and writes its raw
+// partial product to partial slot tile_slot ([64][R]); mf_reduce_kernel then sums the slots of
+// each (task, row tile) in slot order and applies C0, the sign and the row list.
+__global__ void __launch_bounds__(kMfThreads) mf_gemm_kernel(const MfTask* __restrict__ tasks,
+                                                             const MfTile* __restrict__ tiles,
+                                                             const float2* __restrict__ fac,
+                                                             const int32_t* __restrict__ idx, int R,
+                                                             float2* __restrict__ arena,
+                                                             float2* __restrict__ partial) {
   __shared__ float2 As[kMfRows][kMfK + 1];
-  __shared__ float2 Bs[kMfK][kMfCols];
-  const MfTask T = tasks[tile_task[blockIdx.x]];
-  const int64_t row0 = tile_row0[blockIdx.x];
+  __shared__ float2 Bs[kMfK][kMfCols + 1];
+  const MfTile tl = tiles[blockIdx.x];
+  const MfTask T = tasks[tl.task];
+  const int64_t row0 = tl.row0;
+  const int64_t kbeg = tl.k0, kend = min((int64_t)tl.k1, T.k);
   const int col0 = blockIdx.y * kMfCols;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // column, row group (8 rows each: ty + 8 i)
-  float2 acc[8];
+  const int tr = threadIdx.x / 8, tc = threadIdx.x % 8;
+  float2 acc[4][4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) acc[i] = make_float2(0.f, 0.f);
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
   const float2* A = fac + T.a_off;
-  for (int64_t k0 = 0; k0 < T.k; k0 += kMfK) {
-    for (int e = threadIdx.x; e < kMfRows * kMfK; e += 256) {
+  for (int64_t k0 = kbeg; k0 < kend; k0 += kMfK) {
+    for (int e = threadIdx.x; e < kMfRows * kMfK; e += kMfThreads) {
       const int r = e / kMfK, kk = e % kMfK;
       const int64_t gr = row0 + r, gk = k0 + kk;
-      As[r][kk] = (gr < T.m && gk < T.k) ? A[gr * T.lda + gk] : make_float2(0.f, 0.f);
+      As[r][kk] = (gr < T.m && gk < kend) ? A[gr * T.lda + gk] : make_float2(0.f, 0.f);
     }
-    for (int e = threadIdx.x; e < kMfK * kMfCols; e += 256) {
+    for (int e = threadIdx.x; e < kMfK * kMfCols; e += kMfThreads) {
       const int kk = e / kMfCols, c = e % kMfCols;
       const int64_t gk = k0 + kk;
       float2 v = make_float2(0.f, 0.f);
-      if (gk < T.k && col0 + c < R) {
+      if (gk < kend && col0 + c < R) {
         const int64_t brow = T.b_idx >= 0 ? (int64_t)idx[T.b_idx + gk] : T.b_row + gk;
         v = arena[brow * R + col0 + c];
       }
@@ -206,27 +217,75 @@ __global__ void __launch_bounds__(256) mf_gemm_kernel(const MfTask* __restrict__
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < kMfK; ++kk) {
-      const float2 b = Bs[kk][tx];
+      float2 a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float2 a = As[ty + 8 * i][kk];
-        acc[i].x = fmaf(a.x, b.x, acc[i].x);
-        acc[i].x = fmaf(-a.y, b.y, acc[i].x);
-        acc[i].y = fmaf(a.x, b.y, acc[i].y);
-        acc[i].y = fmaf(a.y, b.x, acc[i].y);
-      }
+      for (int i = 0; i < 4; ++i) a[i] = As[tr + 16 * i][kk];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tc + 8 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
+          acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
+          acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
+          acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
+        }
     }
     __syncthreads();
   }
-  const int c = col0 + tx;
-  if (c >= R) return;
+  if (tl.slot >= 0) {
+    float2* P = partial + (int64_t)tl.slot * kMfRows * R;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int64_t gr = row0 + ty + 8 * i;
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = col0 + tc + 8 * j;
+        if (c < R) P[(int64_t)(tr + 16 * i) * R + c] = acc[i][j];
+      }
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gr = row0 + tr + 16 * i;
     if (gr >= T.m) continue;
     const int64_t crow = T.c_idx >= 0 ? (int64_t)idx[T.c_idx + gr] : T.c_row + gr;
     if (crow < 0) continue;
-    float2 v = make_float2(T.sign * acc[i].x, T.sign * acc[i].y);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = col0 + tc + 8 * j;
+      if (c >= R) continue;
+      float2 v = make_float2(T.sign * acc[i][j].x, T.sign * acc[i][j].y);
+      if (T.c0_row >= 0) {
+        const float2 c0 = arena[(T.c0_row + gr) * R + c];
+        v.x += c0.x;
+        v.y += c0.y;
+      }
+      arena[crow * R + c] = v;
+    }
+  }
+}
+
+// One CTA per split (task, row tile): the sum of its partial slots in slot order, then the
+// epilogue of mf_gemm_kernel.
+__global__ void mf_reduce_kernel(const MfTask* __restrict__ tasks, const MfSplit* __restrict__ splits,
+                                 const float2* __restrict__ partial, const int32_t* __restrict__ idx, int R,
+                                 float2* __restrict__ arena) {
+  const MfSplit sp = splits[blockIdx.x];
+  const MfTask T = tasks[sp.task];
+  for (int e = threadIdx.x; e < kMfRows * R; e += blockDim.x) {
+    const int r = e / R, c = e % R;
+    const int64_t gr = sp.row0 + r;
+    if (gr >= T.m) continue;
+    const int64_t crow = T.c_idx >= 0 ? (int64_t)idx[T.c_idx + gr] : T.c_row + gr;
+    if (crow < 0) continue;
+    float sx = 0.f, sy = 0.f;
+    for (int q = 0; q < sp.n_slots; ++q) {
+      const float2 v = partial[((int64_t)(sp.slot0 + q) * kMfRows + r) * R + c];
+      sx += v.x;
+      sy += v.y;
+    }
+    float2 v = make_float2(T.sign * sx, T.sign * sy);
     if (T.c0_row >= 0) {
       const float2 c0 = arena[(T.c0_row + gr) * R + c];
       v.x += c0.x;
@@ -289,12 +348,16 @@ void mf_rhs(const int32_t* nodes, int n_nodes, int64_t fmax, const int64_t* f, c
                                   in, R, arena);
 }
 
-void mf_gemm(const MfTask* tasks, const int32_t* tile_task, const int32_t* tile_row0, int n_tiles, const float2* fac,
-             const int32_t* idx, int R, float2* arena, cudaStream_t s) {
+void mf_gemm(const MfTask* tasks, const MfTile* tiles, int n_tiles, const MfSplit* splits, int n_splits,
+             const float2* fac, const int32_t* idx, int R, float2* arena, float2* partial, cudaStream_t s) {
   if (n_tiles <= 0) return;
   note_launch(1);
   dim3 g((unsigned)n_tiles, (unsigned)((R + kMfCols - 1) / kMfCols));
-  mf_gemm_kernel<<<g, 256, 0, s>>>(tasks, tile_task, tile_row0, fac, idx, R, arena);
+  mf_gemm_kernel<<<g, kMfThreads, 0, s>>>(tasks, tiles, fac, idx, R, arena, partial);
+  if (n_splits > 0) {
+    note_launch(1);
+    mf_reduce_kernel<<<n_splits, 256, 0, s>>>(tasks, splits, partial, idx, R, arena);
+  }
 }
 
 void mf_owned(const int32_t* own_glob, const int64_t* own_row, int64_t n_own, const float2* arena, int R, float2* z,

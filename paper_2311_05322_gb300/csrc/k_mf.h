@@ -19,6 +19,23 @@ struct MfTask {
   int32_t pad;
 };
 
+// One 64-row tile of a task over K range [k0, k1); slot >= 0: write the raw partial product to
+// that partial slot (split K), slot < 0: the whole K range, with the task's epilogue.
+struct MfTile {
+  int32_t task;
+  int32_t row0;
+  int32_t k0, k1;
+  int32_t slot;
+};
+// A (task, row tile) whose K range is split: partial slots slot0 .. slot0 + n_slots - 1.
+struct MfSplit {
+  int32_t task;
+  int32_t row0;
+  int32_t slot0, n_slots;
+};
+// Rows of a 64-row tile (the partial slot size is kMfTileRows x R).
+constexpr int kMfTileRows = 64;
+
 // Front entries target[i] of the workspace = sum of the contributions code[ptr[i] .. ptr[i+1]).
 void mf_assemble(const int64_t* ptr, const int64_t* target, const int32_t* code, int64_t n_t, const int32_t* tet_ids,
                  const double* KM, const double* eps, double k0, const double* Bsurf, const int32_t* surf_tet,
@@ -35,8 +52,10 @@ void mf_rhs(const int32_t* nodes, int n_nodes, int64_t fmax, const int64_t* f, c
             const int64_t* piv_ptr, const int32_t* piv_glob, const int64_t* child_ptr, const int32_t* child,
             const int64_t* inv_off, const int32_t* inv, const int64_t* rhs_row, const int64_t* w_row,
             const float2* in, int R, float2* arena, cudaStream_t s);
-void mf_gemm(const MfTask* tasks, const int32_t* tile_task, const int32_t* tile_row0, int n_tiles, const float2* fac,
-             const int32_t* idx, int R, float2* arena, cudaStream_t s);
+// Tiles of one height (and direction) then, when some K ranges are split, the reduction of
+// their partial slots.
+void mf_gemm(const MfTask* tasks, const MfTile* tiles, int n_tiles, const MfSplit* splits, int n_splits,
+             const float2* fac, const int32_t* idx, int R, float2* arena, float2* partial, cudaStream_t s);
 void mf_owned(const int32_t* own_glob, const int64_t* own_row, int64_t n_own, const float2* arena, int R, float2* z,
               cudaStream_t s);
 

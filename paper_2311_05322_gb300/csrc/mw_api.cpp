@@ -75,8 +75,12 @@ struct Prec {
             *inv_off = nullptr, *rhs_row = nullptr, *w_row = nullptr, *own_row = nullptr, *asm_ptr = nullptr,
             *asm_target = nullptr, *sh_f = nullptr, *sh_off = nullptr, *sh_lim = nullptr;
     int32_t *p = nullptr, *preal = nullptr, *piv_glob = nullptr, *child = nullptr, *inv = nullptr, *idx = nullptr,
-            *asm_code = nullptr, *sh_nodes = nullptr, *h_nodes = nullptr, *tile_task = nullptr, *tile_row0 = nullptr;
+            *asm_code = nullptr, *sh_nodes = nullptr, *h_nodes = nullptr;
     mwk::MfTask* tasks = nullptr;
+    mwk::MfTile* tiles = nullptr;
+    mwk::MfSplit* splits = nullptr;
+    std::vector<int64_t> fwd_splits, bwd_splits;  // [H + 2] split ranges per height
+    int64_t max_slots = 0;                         // partial slots of the largest launch
     std::vector<int64_t> sh_ptr;     // [(n_sub * (H + 1)) + 1] node ranges per (subdomain, height)
     std::vector<int64_t> sh_fmax, sh_pmax, sh_emax;
     std::vector<int64_t> h_ptr;      // [H + 2] node ranges per height (all subdomains)
@@ -110,6 +114,8 @@ struct Work {
   size_t tc_bytes = 0;
   void* mf_arena = nullptr;     // vectors of the sparse subdomain solves
   size_t mf_bytes = 0;
+  void* mf_partial = nullptr;   // split-K partial products of the sparse solves
+  size_t mf_pbytes = 0;
 };
 
 // Optional per-kernel-class timing with CUDA events on the context stream.
@@ -370,7 +376,7 @@ void free_work(Ctx* c) {
   Work& w = c->work;
   for (void* p : {(void*)w.V, (void*)w.Z, (void*)w.xdf, (void*)w.r, (void*)w.x, (void*)w.part, (void*)w.h, (void*)w.H, (void*)w.cs,
                   (void*)w.g, (void*)w.y, (void*)w.npart, (void*)w.target, (void*)w.rnorm, (void*)w.bnorm,
-                  (void*)w.scale, (void*)w.done, (void*)w.kcol, (void*)w.active, (void*)w.bblk, (void*)w.kerr, (void*)w.bdf, (void*)w.r32, (void*)w.vscale, w.tc_scratch, w.mf_arena})
+                  (void*)w.scale, (void*)w.done, (void*)w.kcol, (void*)w.active, (void*)w.bblk, (void*)w.kerr, (void*)w.bdf, (void*)w.r32, (void*)w.vscale, w.tc_scratch, w.mf_arena, w.mf_partial})
     dfree(c, p);
   if (w.h_active) cudaFreeHost(w.h_active);
   if (w.h_vec) cudaFreeHost(w.h_vec);
@@ -440,6 +446,13 @@ void ensure_prec_scratch(Ctx* c, int R) {
       w.mf_arena = dalloc<unsigned char>(c, need);
       w.mf_bytes = need;
     }
+    const size_t pneed = (size_t)std::max<int64_t>(p.mf.max_slots, 1) * mwk::kMfTileRows * R * sizeof(float2);
+    if (w.mf_pbytes < pneed) {
+      dfree(c, w.mf_partial);
+      w.mf_partial = nullptr;
+      w.mf_partial = dalloc<unsigned char>(c, pneed);
+      w.mf_pbytes = pneed;
+    }
     return;
   }
   if (!p.ready || p.apply_prec != 2) return;
@@ -460,26 +473,23 @@ void apply_sparse(Ctx* c, int f, const float2* v, float2* z, int R) {
   Work& w = c->work;
   cudaStream_t s = c->stream;
   require(R >= 1 && R <= 128, MW_EINVAL, "the sparse preconditioner takes 1..128 columns");
-  const size_t need = (size_t)m.arena_rows * R * sizeof(float2);
-  if (w.mf_bytes < need) {
-    dfree(c, w.mf_arena);
-    w.mf_arena = nullptr;
-    w.mf_arena = dalloc<unsigned char>(c, need);
-    w.mf_bytes = need;
-  }
+  ensure_prec_scratch(c, R);
   float2* arena = (float2*)w.mf_arena;
+  float2* partial = (float2*)w.mf_partial;
   const float2* fac = (const float2*)m.fac[f];
   const int H = m.sym.max_height;
   for (int h = 0; h <= H; ++h) {
     const int64_t n0 = m.h_ptr[h], n1 = m.h_ptr[h + 1];
     mwk::mf_rhs(m.h_nodes + n0, (int)(n1 - n0), m.h_fmax[h], m.f, m.preal, m.piv_ptr, m.piv_glob, m.child_ptr,
                 m.child, m.inv_off, m.inv, m.rhs_row, m.w_row, v, R, arena, s);
-    mwk::mf_gemm(m.tasks, m.tile_task + m.fwd_tiles[h], m.tile_row0 + m.fwd_tiles[h],
-                 (int)(m.fwd_tiles[h + 1] - m.fwd_tiles[h]), fac, m.idx, R, arena, s);
+    mwk::mf_gemm(m.tasks, m.tiles + m.fwd_tiles[h], (int)(m.fwd_tiles[h + 1] - m.fwd_tiles[h]),
+                 m.splits + m.fwd_splits[h], (int)(m.fwd_splits[h + 1] - m.fwd_splits[h]), fac, m.idx, R, arena,
+                 partial, s);
   }
   for (int h = H; h >= 0; --h)
-    mwk::mf_gemm(m.tasks, m.tile_task + m.bwd_tiles[h], m.tile_row0 + m.bwd_tiles[h],
-                 (int)(m.bwd_tiles[h + 1] - m.bwd_tiles[h]), fac, m.idx, R, arena, s);
+    mwk::mf_gemm(m.tasks, m.tiles + m.bwd_tiles[h], (int)(m.bwd_tiles[h + 1] - m.bwd_tiles[h]),
+                 m.splits + m.bwd_splits[h], (int)(m.bwd_splits[h + 1] - m.bwd_splits[h]), fac, m.idx, R, arena,
+                 partial, s);
   mwk::mf_owned(c->prec.own_glob, m.own_row, m.n_own, arena, R, z, s);
 }
 
@@ -557,36 +567,67 @@ void setup_sparse(Ctx* c) {
       m.sh_emax.push_back(em);
       m.max_sh = std::max<int64_t>(m.max_sh, m.sh_ptr.back() - m.sh_ptr[m.sh_ptr.size() - 2]);
     }
-  // GEMM tasks and their 64-row tiles, per height: forward t and w, backward x
+  // GEMM tasks of each height and direction (forward t and w, backward x) and their 64-row
+  // tiles.  No tile covers more than kMfMaxTileK of K, so tiles of one launch take similar
+  // times; a launch with fewer row tiles than kMfTargetCtas splits K further (chunks of at least
+  // 256, aligned to 32) so that every SM gets work.  Split partial products are summed in slot
+  // order by the reduction.
+  constexpr int64_t kMfTargetCtas = 4 * 152, kMfMinSplitK = 256, kMfMaxTileK = 512;
   std::vector<mwk::MfTask> tasks;
-  std::vector<int32_t> tile_task, tile_row0;
-  auto add_task = [&](const mwk::MfTask& t) {
-    const int32_t id = (int32_t)tasks.size();
-    tasks.push_back(t);
-    for (int64_t r0 = 0; r0 < t.m; r0 += 64) {
-      tile_task.push_back(id);
-      tile_row0.push_back((int32_t)r0);
+  std::vector<mwk::MfTile> tiles;
+  std::vector<mwk::MfSplit> splits;
+  auto emit_launch = [&](const std::vector<mwk::MfTask>& tl) {
+    int64_t row_tiles = 0;
+    for (const auto& t : tl) row_tiles += (t.m + 63) / 64;
+    const int64_t want = row_tiles >= kMfTargetCtas ? 1 : (kMfTargetCtas + row_tiles - 1) / std::max<int64_t>(row_tiles, 1);
+    int32_t slot = 0;
+    for (const auto& t : tl) {
+      const int32_t id = (int32_t)tasks.size();
+      tasks.push_back(t);
+      // split for parallelism in small launches, and always so that no tile's K exceeds kMfMaxTileK
+      const int64_t ns = std::max<int64_t>({(int64_t)1, std::min<int64_t>(want, t.k / kMfMinSplitK),
+                                           (t.k + kMfMaxTileK - 1) / kMfMaxTileK});
+      const int64_t chunk = ns == 1 ? t.k : ((t.k + ns - 1) / ns + 31) / 32 * 32;
+      for (int64_t r0 = 0; r0 < t.m; r0 += 64) {
+        if (ns == 1) {
+          tiles.push_back({id, (int32_t)r0, 0, (int32_t)std::max<int64_t>(t.k, 0), -1});
+          continue;
+        }
+        const int32_t s0 = slot;
+        for (int64_t k0 = 0; k0 < t.k; k0 += chunk)
+          tiles.push_back({id, (int32_t)r0, (int32_t)k0, (int32_t)std::min(t.k, k0 + chunk), slot++});
+        splits.push_back({id, (int32_t)r0, s0, slot - s0});
+      }
     }
+    m.max_slots = std::max<int64_t>(m.max_slots, slot);
   };
   m.fwd_tiles.assign(1, 0);
+  m.fwd_splits.assign(1, 0);
   for (int h = 0; h <= H; ++h) {
+    std::vector<mwk::MfTask> tl;
     for (int64_t q = m.h_ptr[h]; q < m.h_ptr[h + 1]; ++q) {
       const int k = h_nodes[q];
       const int64_t p = y.p[k], u = y.u[k], ff = y.f[k];
-      if (p > 0) add_task({y.fac_off[k], ff, p, p, rhs_row[k], -1, t_row[k], -1, -1, 1.f, 0});
-      if (u > 0) add_task({y.fac_off[k] + p * ff, std::max<int64_t>(p, 1), u, p, rhs_row[k], -1, w_row[k], -1,
-                           rhs_row[k] + p, 1.f, 0});
+      if (p > 0) tl.push_back({y.fac_off[k], ff, p, p, rhs_row[k], -1, t_row[k], -1, -1, 1.f, 0});
+      if (u > 0) tl.push_back({y.fac_off[k] + p * ff, std::max<int64_t>(p, 1), u, p, rhs_row[k], -1, w_row[k], -1,
+                               rhs_row[k] + p, 1.f, 0});
     }
-    m.fwd_tiles.push_back((int64_t)tile_task.size());
+    emit_launch(tl);
+    m.fwd_tiles.push_back((int64_t)tiles.size());
+    m.fwd_splits.push_back((int64_t)splits.size());
   }
   m.bwd_tiles.assign(1, m.fwd_tiles.back());
+  m.bwd_splits.assign(1, m.fwd_splits.back());
   for (int h = 0; h <= H; ++h) {
+    std::vector<mwk::MfTask> tl;
     for (int64_t q = m.h_ptr[h]; q < m.h_ptr[h + 1]; ++q) {
       const int k = h_nodes[q];
       const int64_t p = y.p[k], u = y.u[k], ff = y.f[k];
-      if (p > 0) add_task({y.fac_off[k] + p, ff, p, u, -1, bidx[k], -1, cidx[k], t_row[k], -1.f, 0});
+      if (p > 0) tl.push_back({y.fac_off[k] + p, ff, p, u, -1, bidx[k], -1, cidx[k], t_row[k], -1.f, 0});
     }
-    m.bwd_tiles.push_back((int64_t)tile_task.size());
+    emit_launch(tl);
+    m.bwd_tiles.push_back((int64_t)tiles.size());
+    m.bwd_splits.push_back((int64_t)splits.size());
   }
   // owned rows of x
   std::vector<int64_t> own_row(sd.own_local.size());
@@ -642,6 +683,14 @@ void setup_sparse(Ctx* c) {
       if (t.c0_row >= 0) require(t.c0_row + t.m <= rows, MW_EINVAL, bad);
     }
     for (int64_t r : own_row) require(r >= 0 && r < rows, MW_EINVAL, bad);
+    for (const mwk::MfTile& tl : tiles) {
+      require(tl.task >= 0 && tl.task < (int32_t)tasks.size() && tl.row0 >= 0 && tl.row0 < std::max<int64_t>(tasks[tl.task].m, 1),
+              MW_EINVAL, bad);
+      require(tl.k0 >= 0 && tl.k0 <= tl.k1 && tl.k1 <= tasks[tl.task].k && tl.slot < m.max_slots, MW_EINVAL, bad);
+    }
+    for (const mwk::MfSplit& sp : splits)
+      require(sp.task >= 0 && sp.task < (int32_t)tasks.size() && sp.slot0 >= 0 && sp.slot0 + sp.n_slots <= m.max_slots,
+              MW_EINVAL, bad);
   }
   std::vector<int32_t> pp(y.p.begin(), y.p.end());
   m.f = mf_up(c, m, y.f);
@@ -667,9 +716,9 @@ void setup_sparse(Ctx* c) {
   m.asm_code = mf_up(c, m, y.asm_code);
   m.sh_nodes = mf_up(c, m, sh_nodes);
   m.h_nodes = mf_up(c, m, h_nodes);
-  m.tile_task = mf_up(c, m, tile_task);
-  m.tile_row0 = mf_up(c, m, tile_row0);
   m.tasks = mf_up(c, m, tasks);
+  m.tiles = mf_up(c, m, tiles);
+  m.splits = mf_up(c, m, splits);
   for (int64_t v : y.ws_size) m.ws_max = std::max(m.ws_max, v);
   // numeric factorisation
   float2* ws = dalloc<float2>(c, std::max<int64_t>(m.ws_max, 1));
