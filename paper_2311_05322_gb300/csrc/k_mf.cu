@@ -178,14 +178,25 @@ constexpr int kMfRows = 64, kMfK = 32, kMfCols = 32, kMfThreads = 128;
 // Split K: a tile with tile_slot >= 0 covers only K range [tile_k0, tile_k1) and writes its raw
 // partial product to partial slot tile_slot ([64][R]); mf_reduce_kernel then sums the slots of
 // each (task, row tile) in slot order and applies C0, the sign and the row list.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gmem), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared-memory stages of the sweep GEMM: A [64][33] and B [32][33] complex FP32, two of each.
+constexpr int kMfAStage = kMfRows * (kMfK + 1), kMfBStage = kMfK * (kMfCols + 1);
+constexpr size_t kMfSmem = sizeof(float2) * 2 * (kMfAStage + kMfBStage);
+
 __global__ void __launch_bounds__(kMfThreads) mf_gemm_kernel(const MfTask* __restrict__ tasks,
                                                              const MfTile* __restrict__ tiles,
                                                              const float2* __restrict__ fac,
                                                              const int32_t* __restrict__ idx, int R,
                                                              float2* __restrict__ arena,
                                                              float2* __restrict__ partial) {
-  __shared__ float2 As[kMfRows][kMfK + 1];
-  __shared__ float2 Bs[kMfK][kMfCols + 1];
+  extern __shared__ float2 sm2[];
   const MfTile tl = tiles[blockIdx.x];
   const MfTask T = tasks[tl.task];
   const int64_t row0 = tl.row0;
@@ -198,30 +209,48 @@ __global__ void __launch_bounds__(kMfThreads) mf_gemm_kernel(const MfTask* __res
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
   const float2* A = fac + T.a_off;
-  for (int64_t k0 = kbeg; k0 < kend; k0 += kMfK) {
+  // copies of one K chunk into stage st (out-of-range entries are zero-filled)
+  auto load = [&](int64_t k0, int st) {
+    float2* As = sm2 + st * kMfAStage;
+    float2* Bs = sm2 + 2 * kMfAStage + st * kMfBStage;
     for (int e = threadIdx.x; e < kMfRows * kMfK; e += kMfThreads) {
       const int r = e / kMfK, kk = e % kMfK;
       const int64_t gr = row0 + r, gk = k0 + kk;
-      As[r][kk] = (gr < T.m && gk < kend) ? A[gr * T.lda + gk] : make_float2(0.f, 0.f);
+      const bool ok = gr < T.m && gk < kend;
+      cp_async8(As + r * (kMfK + 1) + kk, ok ? (const void*)(A + gr * T.lda + gk) : (const void*)A, ok);
     }
     for (int e = threadIdx.x; e < kMfK * kMfCols; e += kMfThreads) {
       const int kk = e / kMfCols, c = e % kMfCols;
       const int64_t gk = k0 + kk;
-      float2 v = make_float2(0.f, 0.f);
-      if (gk < kend && col0 + c < R) {
+      const bool ok = gk < kend && col0 + c < R;
+      const float2* src = arena;
+      if (ok) {
         const int64_t brow = T.b_idx >= 0 ? (int64_t)idx[T.b_idx + gk] : T.b_row + gk;
-        v = arena[brow * R + col0 + c];
+        src = arena + brow * R + col0 + c;
       }
-      Bs[kk][c] = v;
+      cp_async8(Bs + kk * (kMfCols + 1) + c, src, ok);
+    }
+    cp_async_commit();
+  };
+  if (kbeg < kend) load(kbeg, 0);
+  int st = 0;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += kMfK, st ^= 1) {
+    if (k0 + kMfK < kend) {
+      load(k0 + kMfK, st ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const float2* As = sm2 + st * kMfAStage;
+    const float2* Bs = sm2 + 2 * kMfAStage + st * kMfBStage;
 #pragma unroll 4
     for (int kk = 0; kk < kMfK; ++kk) {
       float2 a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[tr + 16 * i][kk];
+      for (int i = 0; i < 4; ++i) a[i] = As[(tr + 16 * i) * (kMfK + 1) + kk];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tc + 8 * j];
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk * (kMfCols + 1) + tc + 8 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -352,8 +381,13 @@ void mf_gemm(const MfTask* tasks, const MfTile* tiles, int n_tiles, const MfSpli
              const float2* fac, const int32_t* idx, int R, float2* arena, float2* partial, cudaStream_t s) {
   if (n_tiles <= 0) return;
   note_launch(1);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(mf_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMfSmem);
+    attr = true;
+  }
   dim3 g((unsigned)n_tiles, (unsigned)((R + kMfCols - 1) / kMfCols));
-  mf_gemm_kernel<<<g, kMfThreads, 0, s>>>(tasks, tiles, fac, idx, R, arena, partial);
+  mf_gemm_kernel<<<g, kMfThreads, kMfSmem, s>>>(tasks, tiles, fac, idx, R, arena, partial);
   if (n_splits > 0) {
     note_launch(1);
     mf_reduce_kernel<<<n_splits, 256, 0, s>>>(tasks, splits, partial, idx, R, arena);

@@ -255,7 +255,7 @@ struct Ctx {
   double* d_red = nullptr;     // reduction scratch
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
-  int mf_leaf = 64;          // nested-dissection leaf size for the next sparse preconditioner
+  int mf_leaf = 256;         // nested-dissection leaf size for the next sparse preconditioner
 
   // tuned launch shapes
   bool autotune_on = true;
