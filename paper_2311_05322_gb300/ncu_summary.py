@@ -13,7 +13,8 @@ from collections import defaultdict
 
 SETUP = ("elem_geom", "face_geom", "tikhonov_weights", "local_assemble", "gj_", "extract_owned", "pack_w",
          "fill_pattern",  # fill_pattern: timing inputs of the launch-shape tuner
-         "port_face", "port_accumulate", "port_norm")  # port load vectors (once per boundary)
+         "port_face", "port_accumulate", "port_norm",  # port load vectors (once per boundary)
+         "mf_assemble", "mf_extend_add", "mf_extract")  # sparse subdomain factorisation
 
 
 def short(name: str) -> str:
