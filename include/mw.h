@@ -233,6 +233,17 @@ mw_status mw_get_port_vectors(mw_ctx* ctx, double* W, double* norms);
  * block is numerically singular. */
 mw_status mw_setup_preconditioner(mw_ctx* ctx, int32_t n_sub, const int32_t* tet_part,
                                   int32_t overlap_layers, int32_t inv_prec);
+/* Host-only check of the sparse subdomain plan (no context, no GPU): builds the topology, the
+ * subdomains and the nested-dissection multifrontal structure that MW_PREC_SPARSE would use
+ * with the given leaf size, and verifies its invariants (every dof a pivot exactly once, fronts
+ * of padded pivots plus update dofs, each child's update dofs found in its parent's front at the
+ * rows its map names, roots without update dofs, assembly targets inside the workspace).
+ * stats[6] receives: tree nodes, tree height, largest front, factor entries, largest workspace
+ * (entries), and sum_s n_s^2 (the dense inverses' entries).  MW_ECUDA reports a broken
+ * invariant; MW_EINVAL bad arguments. */
+mw_status mw_sparse_plan_stats(int64_t n_vert, const double* xyz, int64_t n_tet, const int32_t* tet_vert,
+                               int32_t n_sub, const int32_t* tet_part, int32_t overlap_layers, int32_t leaf,
+                               int64_t* stats);
 /* z = M_f^{-1} r on the device, complex128 [E][n_cols] in and out (parity hook). */
 mw_status mw_apply_preconditioner(mw_ctx* ctx, int32_t f, const void* r_dev, void* z_dev,
                                   int32_t n_cols);

@@ -2918,6 +2918,72 @@ mw_status mw_apply_preconditioner_noalloc(mw_ctx* c, int32_t f, const void* r, v
 // =======================================================================================
 static constexpr int kHid = 1024, kG = 32, kOut = 2 * kG * kG * kG;
 
+mw_status mw_sparse_plan_stats(int64_t n_vert, const double* xyz, int64_t n_tet, const int32_t* tet_vert, int32_t n_sub,
+                               const int32_t* part, int32_t overlap, int32_t leaf, int64_t* stats) {
+  if (!xyz || !tet_vert || !part || !stats || leaf < 1) return MW_EINVAL;
+  try {
+    mw::Topology t;
+    Error err{MW_OK, ""};
+    if (!mw::build_topology(n_vert, n_tet, tet_vert, t, err)) return err.code;
+    mw::Subdomains sd;
+    if (!mw::build_subdomains(t, n_sub, part, overlap, sd, err)) return err.code;
+    std::vector<double> xv(xyz, xyz + 3 * n_vert);
+    mw::Multifrontal y;
+    if (!mw::build_multifrontal(t, sd, xv, nullptr, leaf, y, err)) return err.code;
+    // structural invariants of the plan
+    int64_t max_f = 0, dense = 0;
+    for (int s = 0; s < sd.n_sub; ++s) {
+      const int64_t n = sd.dof_ptr[s + 1] - sd.dof_ptr[s];
+      dense += n * n;
+      std::vector<int32_t> seen(n, 0);
+      for (int64_t k = y.sub_node_ptr[s]; k < y.sub_node_ptr[s + 1]; ++k) {
+        for (int64_t q = y.piv_ptr[k]; q < y.piv_ptr[k + 1]; ++q) {
+          const int32_t d = y.piv_loc[q];
+          if (d < 0 || d >= n || seen[d]++) return MW_ECUDA;  // a dof pivots twice (or never, below)
+        }
+        if (y.p[k] % 32 || y.p[k] < y.preal[k] || y.f[k] != (int64_t)y.p[k] + y.u[k]) return MW_ECUDA;
+        if (y.ws_off[k] + y.f[k] * y.f[k] > y.ws_size[s]) return MW_ECUDA;
+        max_f = std::max(max_f, y.f[k]);
+        // every update dof of a child appears in its parent's front at the row its map names
+        const int32_t par = y.parent[k];
+        if (par >= 0) {
+          const int32_t* inv = y.inv.data() + y.inv_off[k];
+          int64_t hit = 0;
+          for (int64_t r = 0; r < y.f[par]; ++r) {
+            const int32_t a = inv[r];
+            if (a < -1 || a >= y.u[k]) return MW_ECUDA;
+            if (a < 0) continue;
+            ++hit;
+            const int32_t dof = y.upd_loc[y.upd_ptr[k] + a];
+            int32_t rowdof = -1;
+            if (r < y.preal[par]) rowdof = y.piv_loc[y.piv_ptr[par] + r];
+            else if (r >= y.p[par]) rowdof = y.upd_loc[y.upd_ptr[par] + (r - y.p[par])];
+            if (rowdof != dof) return MW_ECUDA;
+          }
+          if (hit != y.u[k]) return MW_ECUDA;
+        } else if (y.u[k] != 0) {
+          return MW_ECUDA;                                      // a root has no update dofs
+        }
+      }
+      for (int64_t d = 0; d < n; ++d)
+        if (seen[d] != 1) return MW_ECUDA;
+      for (int64_t i = y.asm_sub_ptr[s]; i < y.asm_sub_ptr[s + 1]; ++i)
+        if (y.asm_target[i] < 0 || y.asm_target[i] >= y.ws_size[s]) return MW_ECUDA;
+    }
+    int64_t ws_max = 0;
+    for (int64_t v : y.ws_size) ws_max = std::max(ws_max, v);
+    stats[0] = y.n_nodes;
+    stats[1] = y.max_height;
+    stats[2] = max_f;
+    stats[3] = y.fac_total;
+    stats[4] = ws_max;
+    stats[5] = dense;
+    return MW_OK;
+  } catch (...) {
+    return MW_ENOMEM;
+  }
+}
+
 int64_t mw_nn_param_count(int32_t n_in) {
   if (n_in <= 0) return -1;
   return (int64_t)kHid * n_in + kHid + (int64_t)kHid * kHid + kHid + 16 * 16 * 64 + 16 + 16 * 8 * 64 + 8 + 8 * 2 * 64 +

@@ -120,6 +120,7 @@ _SIGS = {
     "mw_apply_preconditioner_noalloc": (C.c_int32, [_P, C.c_int32, _P, _P, C.c_int32]),
     "mw_selftest_bounded_wait": (C.c_int32, [_P, C.c_int64, C.POINTER(C.c_int32)]),
     "mw_nn_param_count": (C.c_int64, [C.c_int32]),
+    "mw_sparse_plan_stats": (C.c_int32, [C.c_int64, _P, C.c_int64, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P]),
     "mw_nn_init": (C.c_int32, [_P, C.c_int32, _P]),
     "mw_nn_get_params": (C.c_int32, [_P, _P]),
     "mw_nn_loss_grad": (C.c_int32, [_P, C.c_int64, _P, _P, C.POINTER(C.c_double), _P]),
@@ -467,6 +468,21 @@ class Context:
         k = hist.iterations
         return eps, {"iterations": k, "evaluations": hist.evaluations, "J": Jh[:k + 1].copy(),
                      "seconds": th[:k + 1].copy()}
+
+
+def sparse_plan_stats(xyz, tets, n_sub: int, tet_part, overlap: int, leaf: int = 256) -> dict:
+    """Host-only check and statistics of the sparse subdomain plan (mw_sparse_plan_stats)."""
+    lib = load_library()
+    xyz = _c(xyz, np.float64)
+    tets = _c(tets, np.int32)
+    part = _c(tet_part, np.int32)
+    out = np.zeros(6, np.int64)
+    st = lib.mw_sparse_plan_stats(xyz.shape[0], _ptr(xyz), tets.shape[0], _ptr(tets), n_sub, _ptr(part), overlap,
+                                  leaf, _ptr(out))
+    if st != MW_OK:
+        raise MWError(st, "sparse plan check failed")
+    return dict(zip(("nodes", "height", "max_front", "factor_entries", "max_workspace", "dense_entries"),
+                    (int(v) for v in out)))
 
 
 def kernel_launches() -> int:
