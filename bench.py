@@ -45,7 +45,7 @@ def _args(argv=None):
     ap.add_argument("--freqs", default="1.0e9", help="comma-separated frequencies (Hz)")
     ap.add_argument("--parts", default="16x16x7")
     ap.add_argument("--overlap", type=int, default=1)
-    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32", "sparse"],
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32", "sparse", "sparse_bf16"],
                     help="subdomain solves: dense inverses applied in BF16 (tensor cores) or FP32, or sparse "
                          "multifrontal factors (large subdomains)")
     ap.add_argument("--alpha", type=float, default=1e-3)
@@ -297,7 +297,8 @@ def run_mine(a):
         hom = np.stack([hom_c.real, hom_c.imag], 1)
     # preconditioner of the background medium, reused stale for every eps (as in an inversion)
     c.assemble(freqs, hom, healthy.eps_bg)
-    prec = {"bf16": mw.MW_PREC_BF16, "fp32": mw.MW_PREC_FP32, "sparse": mw.MW_PREC_SPARSE}[a.prec]
+    prec = {"bf16": mw.MW_PREC_BF16, "fp32": mw.MW_PREC_FP32, "sparse": mw.MW_PREC_SPARSE,
+            "sparse_bf16": mw.MW_PREC_SPARSE_BF16}[a.prec]
     t = time.perf_counter()
     c.setup_preconditioner(n_sub, part, a.overlap, prec)
     torch.cuda.synchronize()
@@ -426,7 +427,7 @@ def run_mine(a):
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-    ratio = oras_traffic_ratio() if dom == "oras_apply" and prec != mw.MW_PREC_SPARSE else None
+    ratio = oras_traffic_ratio() if dom == "oras_apply" and prec == mw.MW_PREC_BF16 else None
     traffic = ratio * d["bytes"] / max(d["launches"], 1) if ratio else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_source": src, "traffic": traffic,
@@ -483,7 +484,8 @@ def run_mine(a):
                        "launch_shapes": {k: tune[k] for k in ("tc_stages", "dots_stages", "update_stages",
                                                               "spmm_threads")},
                        "preconditioner_apply": {2: "bf16 tcgen05", 1: "fp32 cuda-core",
-                                                4: "fp32 multifrontal sweeps"}.get(prec, str(prec)),
+                                                4: "fp32 multifrontal sweeps",
+                                                5: "bf16 tcgen05 multifrontal sweeps"}.get(prec, str(prec)),
                        "tol": 1e-8, "inner_tol": a.inner_tol, "alpha": a.alpha,
                        "l2": "inputs larger than L2 (subdomain inverses and Krylov basis are GBs)"},
             "roofline": roof, "cpu_baseline": cpu,

@@ -47,7 +47,13 @@ enum {
   MW_ESINGULAR = 7  /* a subdomain matrix had a (near-)zero pivot */
 };
 
-typedef enum { MW_PREC_FP64 = 0, MW_PREC_FP32 = 1, MW_PREC_BF16 = 2, MW_PREC_SPARSE = 4 } mw_precision;
+typedef enum {
+  MW_PREC_FP64 = 0,
+  MW_PREC_FP32 = 1,
+  MW_PREC_BF16 = 2,
+  MW_PREC_SPARSE = 4,
+  MW_PREC_SPARSE_BF16 = 5
+} mw_precision;
 typedef enum { MW_MODE_FP64 = 0, MW_MODE_MIXED = 1 } mw_mode;
 
 typedef struct mw_ctx mw_ctx;
@@ -229,7 +235,9 @@ mw_status mw_get_port_vectors(mw_ctx* ctx, double* W, double* norms);
  * multifrontal LU on a nested-dissection tree (FP32, no pivoting), and the apply runs its
  * forward and backward sweeps on the GPU (mixed-precision solves only).  Its memory grows like
  * n_s^(4/3) per subdomain instead of n_s^2, so subdomains of 1e5 unknowns are practical.
- * Builds for every assembled frequency from the current eps.  MW_ESINGULAR when a pivot
+ * MW_PREC_SPARSE_BF16 factorises the same way, then stores the factor blocks as BF16 tiles and
+ * runs the sweeps' products on the tensor cores (tcgen05, FP32 accumulation and FP32 vectors). */
+/* Builds for every assembled frequency from the current eps.  MW_ESINGULAR when a pivot
  * block is numerically singular. */
 mw_status mw_setup_preconditioner(mw_ctx* ctx, int32_t n_sub, const int32_t* tet_part,
                                   int32_t overlap_layers, int32_t inv_prec);

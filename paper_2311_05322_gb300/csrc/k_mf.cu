@@ -394,6 +394,13 @@ void mf_gemm(const MfTask* tasks, const MfTile* tiles, int n_tiles, const MfSpli
   }
 }
 
+void mf_reduce(const MfTask* tasks, const MfSplit* splits, int n_splits, const float2* partial, const int32_t* idx,
+               int R, float2* arena, cudaStream_t s) {
+  if (n_splits <= 0) return;
+  note_launch(1);
+  mf_reduce_kernel<<<n_splits, 256, 0, s>>>(tasks, splits, partial, idx, R, arena);
+}
+
 void mf_owned(const int32_t* own_glob, const int64_t* own_row, int64_t n_own, const float2* arena, int R, float2* z,
               cudaStream_t s) {
   if (n_own <= 0) return;

@@ -56,6 +56,9 @@ void mf_rhs(const int32_t* nodes, int n_nodes, int64_t fmax, const int64_t* f, c
 // their partial slots.
 void mf_gemm(const MfTask* tasks, const MfTile* tiles, int n_tiles, const MfSplit* splits, int n_splits,
              const float2* fac, const int32_t* idx, int R, float2* arena, float2* partial, cudaStream_t s);
+// The reduction of mf_gemm alone: C = C0 + sign * (sum of the split's partial slots).
+void mf_reduce(const MfTask* tasks, const MfSplit* splits, int n_splits, const float2* partial, const int32_t* idx,
+               int R, float2* arena, cudaStream_t s);
 void mf_owned(const int32_t* own_glob, const int64_t* own_row, int64_t n_own, const float2* arena, int R, float2* z,
               cudaStream_t s);
 

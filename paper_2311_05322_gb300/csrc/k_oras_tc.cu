@@ -29,6 +29,7 @@
 
 #include "k_oras.h"
 #include "k_oras_tc.h"
+#include "k_mf.h"
 #include "mw_async.cuh"
 #include "mw_internal.h"
 
@@ -123,6 +124,39 @@ __global__ void pack_w_kernel(const int64_t* __restrict__ nmat, const int64_t* _
       if (k + 1 < n) {
         re1 = (float)row[k + 1].x;
         im1 = (float)row[k + 1].y;
+      }
+    }
+    *reinterpret_cast<uint32_t*>(tr + swz(r, 2 * kp)) = pack_bf16(re0, re1);
+    *reinterpret_cast<uint32_t*>(ti + swz(r, 2 * kp)) = pack_bf16(im0, im1);
+  }
+}
+
+// The same tiles from strided FP32 blocks: "subdomain" q of the plan is the product A_q [m][k]
+// (row stride lda, at element a_off of src), one block per (q, m tile, k tile).
+__global__ void pack_w_blocks_kernel(const MfTask* __restrict__ tasks, int q0, const int64_t* __restrict__ sub_wtile,
+                                     const int32_t* __restrict__ sub_kt, const float2* __restrict__ src,
+                                     uint8_t* __restrict__ W) {
+  const int q = q0 + (int)blockIdx.z;
+  const MfTask t = tasks[q];
+  const int mt = blockIdx.y, kt = blockIdx.x;
+  const int KT = sub_kt[q];
+  if (kt >= KT || (int64_t)mt * kTileM >= t.m) return;
+  uint8_t* tr = W + ((size_t)sub_wtile[q] + ((size_t)mt * KT + kt) * 2) * kATileBytes;
+  uint8_t* ti = tr + kATileBytes;
+  constexpr int kPairs = kTileKd / 2;
+  for (int w = threadIdx.x; w < kTileM * kPairs; w += blockDim.x) {
+    const int r = w / kPairs, kp = w % kPairs;
+    const int64_t row = (int64_t)mt * kTileM + r, k = (int64_t)kt * kTileKd + 2 * kp;
+    float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
+    if (row < t.m) {
+      const float2* a = src + t.a_off + row * t.lda;
+      if (k < t.k) {
+        re0 = a[k].x;
+        im0 = a[k].y;
+      }
+      if (k + 1 < t.k) {
+        re1 = a[k + 1].x;
+        im1 = a[k + 1].y;
       }
     }
     *reinterpret_cast<uint32_t*>(tr + swz(r, 2 * kp)) = pack_bf16(re0, re1);
@@ -449,6 +483,16 @@ void tc_extract(const TcPlan& p, const OrasBatch& bt, const OrasTopo& tp, int ws
   else
     pack_w_kernel<float2><<<grid, 256, 0, s>>>(bt.d_n, bt.d_off, (const float2*)ws, bt.d_sub, tp.own_ptr,
                                                 tp.own_local, p.sub_wtile, p.sub_kt, (uint8_t*)W);
+}
+
+void tc_pack_blocks(const TcPlan& p, const MfTask* tasks, int n, int ktmax, int mtmax, const float2* src, void* W,
+                    cudaStream_t s) {
+  for (int q0 = 0; q0 < n; q0 += 65535) {
+    const int cnt = std::min(65535, n - q0);
+    note_launch(1);
+    dim3 grid((unsigned)std::max(ktmax, 1), (unsigned)std::max(mtmax, 1), (unsigned)cnt);
+    pack_w_blocks_kernel<<<grid, 256, 0, s>>>(tasks, q0, p.sub_wtile, p.sub_kt, src, (uint8_t*)W);
+  }
 }
 
 int tc_stages(int N);

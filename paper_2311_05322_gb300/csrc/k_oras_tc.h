@@ -39,6 +39,11 @@ size_t tc_w_bytes(const TcPlan& p);
 size_t tc_scratch_bytes(const TcPlan& p, int R);
 void tc_extract(const TcPlan& p, const OrasBatch& bt, const OrasTopo& tp, int ws_prec, const void* ws, void* W,
                 cudaStream_t s);
+struct MfTask;
+// Packs the FP32 blocks of tasks[0 .. n) (A = src + a_off, [m][k], row stride lda) into the
+// plan's BF16 tiles (plan "subdomain" q = task q); ktmax / mtmax: the largest tile counts.
+void tc_pack_blocks(const TcPlan& p, const MfTask* tasks, int n, int ktmax, int mtmax, const float2* src, void* W,
+                    cudaStream_t s);
 // stages: shared-memory pipeline depth of the MMA kernel (0 = default; the result does not depend
 // on it, only the speed).  in_scale (may be null): per-column factor of r (z = M^{-1}(r * in_scale)).
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,

@@ -87,7 +87,22 @@ struct Prec {
     std::vector<int64_t> h_fmax;
     std::vector<int64_t> fwd_tiles, bwd_tiles;  // [H + 2] tile ranges per height
     int64_t arena_rows = 0, ws_max = 0, n_own = 0, max_sh = 0;
-    std::vector<void*> fac;          // factors per frequency (FP32 complex)
+    std::vector<void*> fac;          // factors per frequency (FP32 complex; freed after BF16 packing)
+    // BF16 tensor-core sweeps (apply_prec 5): one plan per launch (height x direction), whose
+    // "subdomains" are the launch's products with K > 0; outputs go to partial slots that
+    // mf_reduce turns into C = C0 + sign * A B
+    struct TcLaunch {
+      mwk::TcPlan plan;
+      int64_t *dof_ptr = nullptr, *own_ptr = nullptr;
+      int32_t *dofs = nullptr, *own_local = nullptr, *own_glob = nullptr;
+      mwk::MfTask* tasks = nullptr;  // products with K > 0 (plan order), then those with K = 0
+      mwk::MfSplit* splits = nullptr;
+      int n_tc = 0, n_splits = 0, ktmax = 0, mtmax = 0;
+      std::vector<void*> W;          // BF16 tiles per frequency
+    };
+    std::vector<TcLaunch> tcl;       // [2 (H + 1)]: forward heights, then backward heights
+    int64_t tc_slots = 0;            // partial slots of the largest tensor-core launch
+    size_t tc_scratch = 0;           // gathered-operand bytes of the largest plan at 128 columns
   } mf;
   mwk::OrasTopo topo() const {
     return {dof_ptr, dofs, own_ptr, own_local, own_glob, tet_ptr, tet_ids, tet_loc, surf_ptr, surf_loc, surf_tet};
@@ -438,7 +453,7 @@ void ensure_work(Ctx* c, int R, int m, int prec) {
 void ensure_prec_scratch(Ctx* c, int R) {
   Prec& p = c->prec;
   Work& w = c->work;
-  if (p.ready && p.apply_prec == 4) {
+  if (p.ready && (p.apply_prec == 4 || p.apply_prec == 5)) {
     const size_t need = (size_t)p.mf.arena_rows * R * sizeof(float2);
     if (w.mf_bytes < need) {
       dfree(c, w.mf_arena);
@@ -446,12 +461,19 @@ void ensure_prec_scratch(Ctx* c, int R) {
       w.mf_arena = dalloc<unsigned char>(c, need);
       w.mf_bytes = need;
     }
-    const size_t pneed = (size_t)std::max<int64_t>(p.mf.max_slots, 1) * mwk::kMfTileRows * R * sizeof(float2);
+    const int64_t slots = std::max<int64_t>({p.mf.max_slots, p.mf.tc_slots, (int64_t)1});
+    const size_t pneed = (size_t)slots * mwk::kMfTileRows * R * sizeof(float2);
     if (w.mf_pbytes < pneed) {
       dfree(c, w.mf_partial);
       w.mf_partial = nullptr;
       w.mf_partial = dalloc<unsigned char>(c, pneed);
       w.mf_pbytes = pneed;
+    }
+    if (p.apply_prec == 5 && w.tc_bytes < p.mf.tc_scratch) {
+      dfree(c, w.tc_scratch);
+      w.tc_scratch = nullptr;
+      w.tc_scratch = dalloc<unsigned char>(c, p.mf.tc_scratch);
+      w.tc_bytes = p.mf.tc_scratch;
     }
     return;
   }
@@ -476,8 +498,27 @@ void apply_sparse(Ctx* c, int f, const float2* v, float2* z, int R) {
   ensure_prec_scratch(c, R);
   float2* arena = (float2*)w.mf_arena;
   float2* partial = (float2*)w.mf_partial;
-  const float2* fac = (const float2*)m.fac[f];
   const int H = m.sym.max_height;
+  if (c->prec.apply_prec == 5) {
+    auto run = [&](Prec::Mf::TcLaunch& L) {
+      if (L.n_tc > 0) {
+        const mwk::OrasTopo tp{L.dof_ptr, L.dofs, L.own_ptr, L.own_local, L.own_glob, nullptr, nullptr, nullptr,
+                               nullptr, nullptr, nullptr};
+        mwk::oras_apply_tc(L.plan, tp, L.W[f], arena, partial, R, w.tc_scratch, s);
+      }
+      mwk::mf_reduce(L.tasks, L.splits, L.n_splits, partial, m.idx, R, arena, s);
+    };
+    for (int h = 0; h <= H; ++h) {
+      const int64_t n0 = m.h_ptr[h], n1 = m.h_ptr[h + 1];
+      mwk::mf_rhs(m.h_nodes + n0, (int)(n1 - n0), m.h_fmax[h], m.f, m.preal, m.piv_ptr, m.piv_glob, m.child_ptr,
+                  m.child, m.inv_off, m.inv, m.rhs_row, m.w_row, v, R, arena, s);
+      run(m.tcl[h]);
+    }
+    for (int h = H; h >= 0; --h) run(m.tcl[H + 1 + h]);
+    mwk::mf_owned(c->prec.own_glob, m.own_row, m.n_own, arena, R, z, s);
+    return;
+  }
+  const float2* fac = (const float2*)m.fac[f];
   for (int h = 0; h <= H; ++h) {
     const int64_t n0 = m.h_ptr[h], n1 = m.h_ptr[h + 1];
     mwk::mf_rhs(m.h_nodes + n0, (int)(n1 - n0), m.h_fmax[h], m.f, m.preal, m.piv_ptr, m.piv_glob, m.child_ptr,
@@ -499,6 +540,8 @@ T* mf_up(Ctx* c, Prec::Mf& m, const std::vector<T>& h) {
   m.allocs.push_back(d);
   return d;
 }
+
+void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launches, const std::vector<int32_t>& idx);
 
 // Symbolic factorisation on the host, device tables, then the numeric factorisation of every
 // subdomain for every frequency (FP32 fronts in a workspace, partial Gauss-Jordan per height).
@@ -576,7 +619,9 @@ void setup_sparse(Ctx* c) {
   std::vector<mwk::MfTask> tasks;
   std::vector<mwk::MfTile> tiles;
   std::vector<mwk::MfSplit> splits;
+  std::vector<std::vector<mwk::MfTask>> launches;   // forward heights, then backward heights
   auto emit_launch = [&](const std::vector<mwk::MfTask>& tl) {
+    launches.push_back(tl);
     int64_t row_tiles = 0;
     for (const auto& t : tl) row_tiles += (t.m + 63) / 64;
     const int64_t want = row_tiles >= kMfTargetCtas ? 1 : (kMfTargetCtas + row_tiles - 1) / std::max<int64_t>(row_tiles, 1);
@@ -767,13 +812,87 @@ void setup_sparse(Ctx* c) {
   dfree(c, ws);
   dfree(c, dinv);
   dfree(c, status);
+  if (P.apply_prec == 5) build_sparse_tc(c, launches, idx);
+}
+
+// BF16 tensor-core form of the sweeps: per launch, a tile plan whose "subdomains" are the
+// products with K > 0 (inputs: the arena rows of B; outputs: partial slots, one per 64 rows),
+// the BF16 tiles of their FP32 factor blocks for every frequency, and one reduction split per
+// 64-row tile of every product (none for K = 0, so C = C0).  The FP32 factors are then freed.
+void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launches, const std::vector<int32_t>& idx) {
+  Prec& P = c->prec;
+  Prec::Mf& m = P.mf;
+  const char* bad = "internal: sparse tensor-core table out of range";
+  m.tcl.resize(launches.size());
+  for (size_t L = 0; L < launches.size(); ++L) {
+    Prec::Mf::TcLaunch& T = m.tcl[L];
+    std::vector<mwk::MfTask> ord;
+    for (const auto& t : launches[L])
+      if (t.k > 0) ord.push_back(t);
+    T.n_tc = (int)ord.size();
+    for (const auto& t : launches[L])
+      if (t.k <= 0) ord.push_back(t);
+    mw::Subdomains fake;
+    fake.n_sub = T.n_tc;
+    fake.dof_ptr.assign(1, 0);
+    fake.own_ptr.assign(1, 0);
+    std::vector<int32_t> own_glob;
+    std::vector<mwk::MfSplit> sp;
+    int64_t slot = 0;
+    for (int q = 0; q < (int)ord.size(); ++q) {
+      const mwk::MfTask& t = ord[q];
+      if (q < T.n_tc) {
+        for (int64_t i = 0; i < t.k; ++i) {
+          const int64_t row = t.b_idx >= 0 ? (int64_t)idx[t.b_idx + i] : t.b_row + i;
+          require(row >= 0 && row < m.arena_rows, MW_EINVAL, bad);
+          fake.dofs.push_back((int32_t)row);
+        }
+        fake.dof_ptr.push_back((int64_t)fake.dofs.size());
+        for (int64_t r = 0; r < t.m; ++r) {
+          fake.own_local.push_back((int32_t)r);
+          own_glob.push_back((int32_t)(slot * mwk::kMfTileRows + r));
+        }
+        fake.own_ptr.push_back((int64_t)fake.own_local.size());
+        T.ktmax = std::max<int>(T.ktmax, (int)((t.k + 63) / 64));
+        T.mtmax = std::max<int>(T.mtmax, (int)((t.m + 127) / 128));
+      }
+      for (int64_t r0 = 0; r0 < t.m; r0 += mwk::kMfTileRows)
+        sp.push_back({q, (int32_t)r0, q < T.n_tc ? (int32_t)(slot + r0 / mwk::kMfTileRows) : 0, q < T.n_tc ? 1 : 0});
+      if (q < T.n_tc) slot += (t.m + mwk::kMfTileRows - 1) / mwk::kMfTileRows;
+    }
+    require(slot * mwk::kMfTileRows < INT32_MAX, MW_EINVAL, bad);
+    m.tc_slots = std::max<int64_t>(m.tc_slots, slot);
+    T.n_splits = (int)sp.size();
+    T.tasks = mf_up(c, m, ord);
+    T.splits = mf_up(c, m, sp);
+    if (T.n_tc == 0) continue;
+    T.dof_ptr = mf_up(c, m, fake.dof_ptr);
+    T.dofs = mf_up(c, m, fake.dofs);
+    T.own_ptr = mf_up(c, m, fake.own_ptr);
+    T.own_local = mf_up(c, m, fake.own_local);
+    T.own_glob = mf_up(c, m, own_glob);
+    require(mwk::tc_plan_build(T.plan, fake, [&](size_t b) { return (void*)dalloc<unsigned char>(c, b); }, c->stream),
+            MW_EINVAL, "tensor-core plan of the sparse sweeps");
+    m.tc_scratch = std::max(m.tc_scratch, mwk::tc_scratch_bytes(T.plan, 128));
+    T.W.assign(c->n_freq, nullptr);
+    for (int f = 0; f < c->n_freq; ++f) {
+      T.W[f] = dalloc<unsigned char>(c, std::max<size_t>(mwk::tc_w_bytes(T.plan), 16));
+      mwk::tc_pack_blocks(T.plan, T.tasks, T.n_tc, T.ktmax, T.mtmax, (const float2*)m.fac[f], T.W[f], c->stream);
+    }
+    check_launch("sparse tensor-core packing");
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  for (void*& q : m.fac) {
+    dfree(c, q);
+    q = nullptr;
+  }
 }
 
 void apply_prec(Ctx* c, int f, int work_prec, const void* v, void* z, int R, int stages = 0,
                 const double* in_scale = nullptr) {
   Prec& p = c->prec;
   cudaStream_t s = c->stream;
-  if (p.apply_prec == 4) {
+  if (p.apply_prec == 4 || p.apply_prec == 5) {
     require(work_prec == 1, MW_EINVAL, "the sparse preconditioner needs the mixed-precision solve");
     apply_sparse(c, f, (const float2*)v, (float2*)z, R);
   } else if (p.apply_prec == 2) {
@@ -818,6 +937,7 @@ struct ProfScope {
 double oras_bytes(Ctx* c, int R) {
   const Prec& p = c->prec;
   if (p.apply_prec == 4) return 8.0 * (double)p.mf.sym.fac_total + 8.0 * R * (p.sum_n + (double)c->topo.n_edge);
+  if (p.apply_prec == 5) return 4.0 * (double)p.mf.sym.fac_total + 8.0 * R * (p.sum_n + (double)c->topo.n_edge);
   const double wb = p.apply_prec == 0 ? 16.0 : (p.apply_prec == 1 ? 8.0 : 4.0);
   const double vb = p.apply_prec == 0 ? 16.0 : 8.0;
   return wb * p.sum_own_n + vb * R * (p.sum_n + (double)c->topo.n_edge);
@@ -1569,6 +1689,10 @@ void release_prec(Ctx* c) {
   for (void* q : p.W) dfree(c, q);
   for (void* q : p.mf.allocs) dfree(c, q);
   for (void* q : p.mf.fac) dfree(c, q);
+  for (auto& L : p.mf.tcl) {
+    for (void* q : L.W) dfree(c, q);
+    mwk::tc_plan_free(L.plan, [&](void* q) { dfree(c, q); });
+  }
   mwk::tc_plan_free(p.tc, [&](void* q) { dfree(c, q); });
   p = Prec();
   c->tuned.clear();
@@ -2256,8 +2380,9 @@ mw_status mw_get_port_vectors(mw_ctx* c, double* W, double* norms) {
 mw_status mw_setup_preconditioner(mw_ctx* c, int32_t n_sub, const int32_t* part, int32_t overlap, int32_t inv_prec) {
   return guard(c, [&] {
     require(c->has_mesh && c->n_freq > 0, MW_ESTATE, "assemble before setting up the preconditioner");
-    require(inv_prec >= 0 && inv_prec <= 4, MW_EINVAL, "inv_prec must be 0 (FP64), 1 (FP32), 2 (BF16), 3 (FP32 "
-                                                       "factorisation applied in FP64) or 4 (sparse)");
+    require(inv_prec >= 0 && inv_prec <= 5, MW_EINVAL, "inv_prec must be 0 (FP64), 1 (FP32), 2 (BF16), 3 (FP32 "
+                                                       "factorisation applied in FP64), 4 (sparse) or 5 (sparse, "
+                                                       "BF16 tensor-core sweeps)");
     release_prec(c);
     Prec& p = c->prec;
     Error err{MW_OK, ""};
@@ -2297,7 +2422,7 @@ mw_status mw_setup_preconditioner(mw_ctx* c, int32_t n_sub, const int32_t* part,
     const int64_t n_surf = (int64_t)sd.surf_tet.size();
     p.Bsurf = dalloc<double>(c, 6 * std::max<int64_t>(n_surf, 1));
     mwk::face_geom(c->d_xyz, p.surf_vert, n_surf, p.Bsurf, c->stream);
-    if (inv_prec == 4) {
+    if (inv_prec == 4 || inv_prec == 5) {
       for (int s = 0; s < n_sub; ++s) p.sum_n += (double)(sd.dof_ptr[s + 1] - sd.dof_ptr[s]);
       try {
         setup_sparse(c);

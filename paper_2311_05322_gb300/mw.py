@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmw.so")
 
 MW_OK, MW_EINVAL, MW_ECUDA, MW_ENOMEM, MW_ENOCONV, MW_ETIMEOUT, MW_ESTATE, MW_ESINGULAR = range(8)
-MW_PREC_FP64, MW_PREC_FP32, MW_PREC_BF16, MW_PREC_FP64_FROM_FP32, MW_PREC_SPARSE = 0, 1, 2, 3, 4
+MW_PREC_FP64, MW_PREC_FP32, MW_PREC_BF16, MW_PREC_FP64_FROM_FP32, MW_PREC_SPARSE, MW_PREC_SPARSE_BF16 = 0, 1, 2, 3, 4, 5
 MW_MODE_FP64, MW_MODE_MIXED = 0, 1
 STATUS_NAMES = {0: "MW_OK", 1: "MW_EINVAL", 2: "MW_ECUDA", 3: "MW_ENOMEM", 4: "MW_ENOCONV", 5: "MW_ETIMEOUT",
                 6: "MW_ESTATE", 7: "MW_ESINGULAR"}

@@ -51,16 +51,21 @@ def _apply(c, E, R, seed=3):
     return X, zd.cpu().numpy()
 
 
-@pytest.mark.parametrize("cells,parts,overlap,R,tol", [((5, 4, 3), (2, 2, 1), 1, 3, 2e-5),
-                                                       ((12, 10, 8), (2, 1, 1), 2, 32, 1e-4),
-                                                       ((12, 10, 8), (2, 2, 2), 1, 40, 1e-4)])
-def test_sparse_apply_matches_oracle(cells, parts, overlap, R, tol):
+# BF16 tiles (8-bit mantissas) of the factors and of the sweeps' inputs: a few 1e-3 per product,
+# compounded over the tree's heights; a layout or plan error gives O(1) differences.
+@pytest.mark.parametrize("cells,parts,overlap,R,tol,bf16", [((5, 4, 3), (2, 2, 1), 1, 3, 2e-5, False),
+                                                            ((12, 10, 8), (2, 1, 1), 2, 32, 1e-4, False),
+                                                            ((12, 10, 8), (2, 2, 2), 1, 40, 1e-4, False),
+                                                            ((5, 4, 3), (2, 2, 1), 1, 3, 3e-2, True),
+                                                            ((12, 10, 8), (2, 1, 1), 2, 32, 3e-2, True),
+                                                            ((12, 10, 8), (2, 2, 2), 1, 40, 3e-2, True)])
+def test_sparse_apply_matches_oracle(cells, parts, overlap, R, tol, bf16):
     mw = _mw()
     m, eps, sysm = _case(cells, (-0.06, -0.05, -0.04), (0.06, 0.05, 0.04), 11)
     part = box_partition(m, parts, seed=3)
     n_sub = int(np.prod(parts))
     c = _ctx(m, eps, [1e9])
-    c.setup_preconditioner(n_sub, part, overlap, mw.MW_PREC_SPARSE)
+    c.setup_preconditioner(n_sub, part, overlap, mw.MW_PREC_SPARSE_BF16 if bf16 else mw.MW_PREC_SPARSE)
     _, sizes = c.get_partition()
     P = oras.ORAS(sysm, part, n_sub, overlap, eps, 1e9, EPS_MATCHING)
     X, Z = _apply(c, sysm.topo.n_edge, R)
@@ -94,13 +99,14 @@ def test_sparse_apply_with_ports_and_metal():
     assert np.allclose(Z[bnd.metal], X.T[bnd.metal], rtol=1e-6, atol=1e-6)
 
 
-@pytest.mark.parametrize("ncols", [5, 32])
-def test_sparse_preconditioned_solve_matches_direct(ncols):
+@pytest.mark.parametrize("ncols,bf16", [(5, False), (32, False), (5, True), (32, True)])
+def test_sparse_preconditioned_solve_matches_direct(ncols, bf16):
     mw = _mw()
     m, eps, sysm = _case((12, 10, 8), (-0.06, -0.05, -0.04), (0.06, 0.05, 0.04), 5)
     freqs = [0.9e9, 1.1e9]
     c = _ctx(m, eps, freqs)
-    c.setup_preconditioner(2, box_partition(m, (2, 1, 1), seed=3), 2, mw.MW_PREC_SPARSE)
+    c.setup_preconditioner(2, box_partition(m, (2, 1, 1), seed=3), 2,
+                           mw.MW_PREC_SPARSE_BF16 if bf16 else mw.MW_PREC_SPARSE)
     E = sysm.topo.n_edge
     rng = np.random.default_rng(8)
     B = rng.normal(size=(ncols, E)) + 1j * rng.normal(size=(ncols, E))
