@@ -1500,6 +1500,16 @@ void solve_all(Ctx* c, const mw_solve_opts& o, int ncols, const std::vector<cons
       throw Fail{MW_ETIMEOUT, "tensor-core preconditioner apply: bounded wait ran out (code " + std::to_string(e) + ")"};
     }
   }
+  if (c->prec.ready && c->prec.apply_prec == 5)
+    for (auto& L : c->prec.mf.tcl) {
+      if (!L.plan.err) continue;
+      int32_t e = 0;
+      CK(cudaMemcpy(&e, L.plan.err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+      if (e != 0) {
+        CK(cudaMemsetAsync(L.plan.err, 0, sizeof(int32_t), s));
+        throw Fail{MW_ETIMEOUT, "tensor-core sparse sweep: bounded wait ran out (code " + std::to_string(e) + ")"};
+      }
+    }
   if (c->work.kerr) {
     int32_t e = 0;
     CK(cudaMemcpy(&e, c->work.kerr, sizeof(int32_t), cudaMemcpyDeviceToHost));
