@@ -232,3 +232,43 @@ def test_open_box_without_ports_equals_dipole_assembly():
     rng = np.random.default_rng(1)
     eps = 44 + rng.uniform(-5, 5, m.n_tet) - 1j * rng.uniform(5, 20, m.n_tet)
     assert np.array_equal(ports.assemble_values(sysm, eps, 1e9, 44 - 20j, bnd), asm.assemble(sysm, eps, 1e9, 44 - 20j))
+
+
+def _rotation(seed):
+    rng = np.random.default_rng(seed)
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def test_rotated_guide_gives_the_same_s_matrix():
+    """The discrete problem is invariant under a rigid rotation of mesh and port frames."""
+    m, fv, lab, ps = waveguide_section((4, 2, 6), A_W, B_W, LEN, 59.0 - 1.0j)
+    rng = np.random.default_rng(3)
+    eps = 59.0 + rng.uniform(-3, 3, m.n_tet) - 1j * rng.uniform(0.5, 2, m.n_tet)
+    sysm = asm.build_system(m.xyz, m.tets)
+    P = ports.make_ports(ps.origin, ps.u, ps.v, ps.a, ps.eps_fill)
+    _, S0, _ = ports.forward(sysm, eps, [F_HZ], 59.0, ports.classify(sysm, P, fv, lab))
+    Q = _rotation(7)
+    xyz = m.xyz @ Q.T + np.array([0.01, -0.02, 0.005])
+    sysr = asm.build_system(xyz, m.tets)
+    Pr = ports.make_ports(ps.origin @ Q.T + np.array([0.01, -0.02, 0.005]), ps.u @ Q.T, ps.v @ Q.T, ps.a, ps.eps_fill)
+    _, S1, _ = ports.forward(sysr, eps, [F_HZ], 59.0, ports.classify(sysr, Pr, fv, lab))
+    assert np.abs(S1 - S0).max() <= 1e-9 * np.abs(S0).max()
+
+
+def test_mirrored_broad_side_axis_gives_the_same_s_matrix():
+    """sin(pi s / a) is symmetric about the aperture's centre line: origin at the opposite corner
+    with u reversed describes the same mode."""
+    m, sysm, bnd = _guide((4, 2, 6), 59.0 - 1.0j)
+    _, S0, _ = ports.forward(sysm, np.full(m.n_tet, 59.0 - 1.0j), [F_HZ], 59.0, bnd)
+    flipped = [ports.Port(p.origin + p.a * p.u, -p.u, p.v, p.a, p.eps_fill) for p in bnd.ports]
+    b2 = ports.Boundary(flipped, bnd.fcls, bnd.metal)
+    _, S1, _ = ports.forward(sysm, np.full(m.n_tet, 59.0 - 1.0j), [F_HZ], 59.0, b2)
+    assert np.abs(S1 - S0).max() <= 1e-12 * np.abs(S0).max()
+    # the field direction matters: a mode along the broad side (v = u) couples to nothing TE10-like
+    wrong = [ports.Port(p.origin, p.u, p.u, p.a, p.eps_fill) for p in bnd.ports]
+    _, S2, _ = ports.forward(sysm, np.full(m.n_tet, 59.0 - 1.0j), [F_HZ], 59.0, ports.Boundary(wrong, bnd.fcls, bnd.metal))
+    assert np.abs(S2[0, 1, 0]) < 0.5 * np.abs(S0[0, 1, 0])
