@@ -89,6 +89,28 @@ def tikhonov(pairs, w, eps2: np.ndarray):
 # ----------------------------------------------------------------------------------------
 # L-BFGS with Armijo backtracking
 # ----------------------------------------------------------------------------------------
+def two_loop_direction(g: np.ndarray, S: list, Y: list) -> np.ndarray:
+    """d = -H g, H the limited-memory BFGS inverse Hessian of the stored pairs (oldest first in
+    S, Y) started from H0 = gamma I, gamma = s^T y / y^T y of the newest pair.
+
+    Two-loop recursion: the first loop runs newest to oldest and removes each pair's component,
+    q <- q - a_i y_i with a_i = rho_i s_i^T q and rho_i = 1 / y_i^T s_i; after scaling by gamma
+    the second loop runs oldest to newest and adds it back, r <- r + (a_i - rho_i y_i^T r) s_i."""
+    q = g.copy()
+    alphas = []
+    for s, y in zip(reversed(S), reversed(Y)):
+        rho = 1.0 / float(y @ s)
+        a = rho * float(s @ q)
+        q -= a * y
+        alphas.append((rho, a))
+    gamma = float(S[-1] @ Y[-1]) / float(Y[-1] @ Y[-1])
+    r = gamma * q
+    for (s, y), (rho, a) in zip(zip(S, Y), reversed(alphas)):
+        b = rho * float(y @ r)
+        r += (a - b) * s
+    return -r
+
+
 def lbfgs(fg, x0: np.ndarray, m: int = 8, max_it: int = 20, c1: float = 1e-4, max_ls: int = 10,
           first_step_max: float = 1.0, callback=None):
     """Minimise fg(x) -> (f, g) from x0.
@@ -108,19 +130,7 @@ def lbfgs(fg, x0: np.ndarray, m: int = 8, max_it: int = 20, c1: float = 1e-4, ma
     nfev = 1
     for it in range(max_it):
         if S:
-            q = g.copy()
-            alphas = []
-            for s, y in zip(reversed(S), reversed(Y)):
-                rho = 1.0 / float(y @ s)
-                a = rho * float(s @ q)
-                q -= a * y
-                alphas.append((rho, a))
-            gamma = float(S[-1] @ Y[-1]) / float(Y[-1] @ Y[-1])
-            r = gamma * q
-            for (s, y), (rho, a) in zip(zip(S, Y), reversed(alphas)):
-                b = rho * float(y @ r)
-                r += (a - b) * s
-            d = -r
+            d = two_loop_direction(g, S, Y)
         else:
             d = -g * (first_step_max / max(np.max(np.abs(g)), 1e-300))
         gd = float(g @ d)

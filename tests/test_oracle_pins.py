@@ -400,6 +400,88 @@ def test_oras_partition_of_unity_and_gmres_converges(small_problem):
         assert np.linalg.norm(x - X[:, j]) <= 1e-9 * np.linalg.norm(X[:, j])
 
 
+def _standalone_submesh(m, sub):
+    """The overlapped tets of a subdomain as a mesh of their own, vertices renumbered in
+    ascending global order (so edge orientation and lexicographic edge order are kept)."""
+    verts = np.unique(m.tets[sub.tets])
+    loc_tets = np.searchsorted(verts, m.tets[sub.tets])
+    return verts, m.xyz[verts], loc_tets
+
+
+@pytest.mark.parametrize("s", [0, 3, 6])
+def test_oras_local_matrix_is_standalone_impedance_problem(small_problem, s):
+    """With eps = eps_bg on every tet that carries an interface face, the ORAS local problem is
+    the same boundary-value problem (Eq. m1-m2) posed on the overlapped subdomain as a mesh of
+    its own, with the first-order impedance condition on its whole boundary.  The interior
+    keeps a heterogeneous eps."""
+    from phantom import box_partition
+    m, sysm, _, _, eps0 = small_problem
+    part = box_partition(m, (2, 2, 2), seed=7)
+    subs, _ = oras.build_subdomains(sysm, part, 8, 1, which=[s])
+    sub = subs[0]
+    assert sub.iface.size > 0
+    eps = eps0.copy()
+    eps[sub.iface_tet] = EPS_MATCHING
+    f = 1.05e9
+    Bs = oras.local_matrix(sysm, sub, eps, f, EPS_MATCHING).toarray()
+    verts, xyz, ltets = _standalone_submesh(m, sub)
+    ss = asm.build_system(xyz, ltets)
+    assert np.array_equal(verts[ss.topo.edge_vert], sysm.topo.edge_vert[sub.dofs])
+    As = ss.csr(asm.assemble(ss, eps[sub.tets], f, EPS_MATCHING)).toarray()
+    assert np.abs(Bs - As).max() <= 1e-14 * np.abs(As).max()
+    # the interface faces carry a term of the same size as the volume terms: dropping it or
+    # flipping its sign moves B_s far beyond rounding
+    ref = oras.local_matrix(sysm, oras.Subdomain(sub.tets, sub.dofs, sub.owned, sub.iface[:0], sub.iface_tet[:0]),
+                            eps, f, EPS_MATCHING).toarray()
+    assert np.abs(ref - As).max() >= 1e-3 * np.abs(As).max()
+
+
+def test_oras_local_matrix_brute_force_faces(small_problem):
+    """Heterogeneous eps on the interface tets: B_s against a brute-force sum over the faces of
+    the subdomain's tets.  A face whose three vertices belong to no other tet of the mesh is an
+    outer face (i k0 sqrt(eps_bg)); one shared with a tet outside the subdomain is an interface
+    face with i k0 sqrt(eps of the tet inside).  Face integrals by a degree-4 triangle rule of
+    the tangential traces of the inside tet's own Whitney functions."""
+    from phantom import box_partition
+    m, sysm, _, _, eps = small_problem
+    part = box_partition(m, (2, 2, 2), seed=7)
+    subs, _ = oras.build_subdomains(sysm, part, 8, 1, which=[5])
+    sub = subs[0]
+    f = 0.95e9
+    k0 = constants.k0(f)
+    Bs = oras.local_matrix(sysm, sub, eps, f, EPS_MATCHING).toarray()
+    n = sub.dofs.size
+    ref = np.zeros((n, n), dtype=np.complex128)
+    K, M, _ = tet_matrices(m.xyz, m.tets, sysm.topo.tet_sign)
+    in_sub = set(int(t) for t in sub.tets)
+    vsets = [frozenset(int(v) for v in tv) for tv in m.tets]
+    bary3, w = TRI_Q4
+    n_iface = n_outer = 0
+    for t in sub.tets:
+        loc = np.searchsorted(sub.dofs, sysm.topo.tet_edge[t])
+        ref[np.ix_(loc, loc)] += K[t] - k0 * k0 * eps[t] * M[t]
+        P = m.xyz[m.tets[t]]
+        for k in range(4):
+            fv = [q for q in range(4) if q != k]
+            key = frozenset(int(m.tets[t, q]) for q in fv)
+            others = [u for u in range(m.n_tet) if u != t and key <= vsets[u]]
+            if others and others[0] in in_sub:
+                continue
+            z = 1j * k0 * np.sqrt(complex(EPS_MATCHING)) if not others else 1j * k0 * np.sqrt(complex(eps[t]))
+            n_iface += bool(others)
+            n_outer += not others
+            bary = np.zeros((bary3.shape[0], 4))
+            bary[:, fv] = bary3
+            N, _, _ = _whitney_at(P, bary, sysm.topo.tet_sign[t])
+            Q = P[fv]
+            nrm = np.cross(Q[1] - Q[0], Q[2] - Q[0])
+            area = 0.5 * np.linalg.norm(nrm)
+            Nt = np.cross(N, nrm / (2 * area))
+            ref[np.ix_(loc, loc)] += z * area * np.einsum("q,qmi,qni->mn", w, Nt, Nt)
+    assert n_iface == sub.iface.size and n_iface > 0 and n_outer > 0
+    assert np.abs(Bs - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 # ---------------------------------------------------------------------------------------
 # L-BFGS
 # ---------------------------------------------------------------------------------------
@@ -413,3 +495,68 @@ def test_lbfgs_quadratic_minimiser():
     x, hist, nfev = inverse.lbfgs(fg, np.zeros(n), m=8, max_it=200)
     assert np.linalg.norm(x - np.linalg.solve(Q, c)) <= 1e-8 * np.linalg.norm(np.linalg.solve(Q, c))
     assert all(b <= a for a, b in zip(hist, hist[1:]))
+
+
+def _bfgs_inverse_explicit(S, Y, n):
+    """Textbook BFGS inverse-Hessian update applied to the stored pairs, oldest first, from
+    H0 = gamma I with gamma = s^T y / y^T y of the newest pair (Nocedal & Wright, Eq. 7.19):
+    H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T, rho = 1 / y^T s."""
+    gamma = float(S[-1] @ Y[-1]) / float(Y[-1] @ Y[-1])
+    H = gamma * np.eye(n)
+    I = np.eye(n)
+    for s, y in zip(S, Y):
+        rho = 1.0 / float(y @ s)
+        H = (I - rho * np.outer(s, y)) @ H @ (I - rho * np.outer(y, s)) + rho * np.outer(s, s)
+    return H
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 8])
+def test_lbfgs_two_loop_equals_explicit_bfgs_inverse(k):
+    rng = np.random.default_rng(40 + k)
+    n = 12
+    A = rng.normal(size=(n, n))
+    Q = A @ A.T / n + 0.5 * np.eye(n)
+    S = [rng.normal(size=n) for _ in range(k)]
+    Y = [Q @ s + 0.05 * rng.normal(size=n) for s in S]
+    assert all(float(s @ y) > 0 for s, y in zip(S, Y))
+    g = rng.normal(size=n)
+    H = _bfgs_inverse_explicit(S, Y, n)
+    d = inverse.two_loop_direction(g, S, Y)
+    assert np.linalg.norm(d + H @ g) <= 1e-12 * np.linalg.norm(H @ g)
+    # secant condition of the newest pair, a property of every BFGS update order that ends on it
+    Hy = -inverse.two_loop_direction(Y[-1], S, Y)
+    assert np.linalg.norm(Hy - S[-1]) <= 1e-12 * np.linalg.norm(S[-1])
+
+
+@pytest.mark.parametrize("n,m", [(6, 8), (20, 3)])
+def test_lbfgs_iterates_follow_explicit_bfgs_directions(n, m):
+    """Every accepted step of the driver is t d_k with t a power of 1/2 and d_k = -H_k g_k, H_k
+    rebuilt here from the iterates' own pairs (skip rule, newest m kept); the first step is the
+    steepest descent scaled to max |d| = 1.  With n <= m all pairs stay in memory."""
+    rng = np.random.default_rng(n * 10 + m)
+    A = rng.normal(size=(n, n))
+    Q = A @ A.T / n + 0.3 * np.eye(n)
+    c = rng.normal(size=n)
+    fg = lambda x: (0.5 * x @ Q @ x - c @ x, Q @ x - c)
+    xs = [np.zeros(n)]
+    x, hist, nfev = inverse.lbfgs(fg, xs[0], m=m, max_it=12, callback=lambda it, x, f: xs.append(x.copy()))
+    assert len(xs) == 13
+    S, Y = [], []
+    for k in range(len(xs) - 1):
+        g = fg(xs[k])[1]
+        if S:
+            d = -_bfgs_inverse_explicit(S, Y, n) @ g
+        else:
+            d = -g / np.abs(g).max()
+        step = xs[k + 1] - xs[k]
+        t = float(step @ d) / float(d @ d)
+        assert np.linalg.norm(step - t * d) <= 1e-10 * np.linalg.norm(step)
+        assert abs(math.log2(t) - round(math.log2(t))) < 1e-9 and t <= 1.0 + 1e-12
+        s, y = step, fg(xs[k + 1])[1] - g
+        if float(s @ y) > 1e-12 * np.linalg.norm(s) * np.linalg.norm(y):
+            S.append(s)
+            Y.append(y)
+            if len(S) > m:
+                S.pop(0)
+                Y.pop(0)
+    assert len(S) == min(m, len(xs) - 1)
