@@ -252,9 +252,21 @@ mw_status mw_setup_preconditioner(mw_ctx* ctx, int32_t n_sub, const int32_t* tet
 mw_status mw_sparse_plan_stats(int64_t n_vert, const double* xyz, int64_t n_tet, const int32_t* tet_vert,
                                int32_t n_sub, const int32_t* tet_part, int32_t overlap_layers, int32_t leaf,
                                int64_t* stats);
-/* z = M_f^{-1} r on the device, complex128 [E][n_cols] in and out (parity hook). */
+/* z = M_f^{-1} r on the device, complex128 [E][n_cols] in and out (parity hook).  Returns
+ * after the apply has completed; MW_ETIMEOUT when a bounded wait of the tensor-core apply ran
+ * out (z is then incomplete). */
 mw_status mw_apply_preconditioner(mw_ctx* ctx, int32_t f, const void* r_dev, void* z_dev,
                                   int32_t n_cols);
+/* Parity hook of the Arnoldi orthogonalisation's first half (GMRES, Sec. IV-C; Hermitian
+ * inner product): h[i][c] = sum_rows conj(V_i[row][c]) w[row][c] for i < nvec, computed by the
+ * same kernels as the mixed-precision solves (streaming bulk-copy kernel for 16..128 columns on
+ * 16-byte aligned vectors, FP32 products summed in FP32 within a row tile, FP64 across tiles
+ * and blocks, fixed reduction order).  V_dev: device complex64, vector i at V_dev + i*vstride
+ * elements, each [n_rows][n_cols] with the column fastest; w_dev the same shape.  h_out: host
+ * complex128 [nvec][n_cols].  1 <= nvec <= 64, 1 <= n_cols <= 128.  Synchronises; allocates
+ * temporary device memory; MW_ETIMEOUT when a bounded wait ran out. */
+mw_status mw_krylov_dots(mw_ctx* ctx, int32_t nvec, const void* V_dev, int64_t vstride, const void* w_dev,
+                         int64_t n_rows, int32_t n_cols, double* h_out);
 /* z = M_f^{-1} r with no device allocation.  The paper has no counterpart: this is an
  * integration aid.  It is for callers that cannot allocate device memory when they apply the
  * preconditioner, for example because another framework holds the device heap, because the
@@ -265,7 +277,9 @@ mw_status mw_apply_preconditioner(mw_ctx* ctx, int32_t f, const void* r_dev, voi
  * holds on each GPU until the process exits; a call whose operand would exceed it returns
  * MW_EINVAL with the sizes.  The first call on a device looks the array's address up on that
  * device; make that first call before any stream capture.  All calls share the array, so calls
- * that overlap on the GPU (different streams or contexts without ordering) race; order them. */
+ * that overlap on the GPU (different streams or contexts without ordering) race; order them.
+ * Returns after the apply has completed on the context's stream (it reads the apply's
+ * bounded-wait error word); MW_ETIMEOUT when a wait ran out, z then being incomplete. */
 mw_status mw_apply_preconditioner_noalloc(mw_ctx* ctx, int32_t f, const void* r_dev, void* z_dev,
                                           int32_t n_cols);
 /* Owner subdomain of each edge [E] and unknowns per subdomain [n_sub] (either may be NULL). */

@@ -932,6 +932,20 @@ struct ProfScope {
   }
 };
 
+// Reads the bounded-wait error word of the tensor-core preconditioner apply (after the work
+// that used it has completed on the stream) and turns a wait that ran out into MW_ETIMEOUT,
+// clearing the word for the next call.
+void check_tc_wait(Ctx* c) {
+  if (!(c->prec.ready && c->prec.apply_prec == 2 && c->prec.tc.err)) return;
+  int32_t e = 0;
+  CK(cudaMemcpyAsync(&e, c->prec.tc.err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (e != 0) {
+    CK(cudaMemsetAsync(c->prec.tc.err, 0, sizeof(int32_t), c->stream));
+    throw Fail{MW_ETIMEOUT, "tensor-core preconditioner apply: bounded wait ran out (code " + std::to_string(e) + ")"};
+  }
+}
+
 // Algorithmic bytes of one preconditioner apply on R columns: the owned-row inverses once,
 // the gathered subdomain inputs and the owned outputs.
 double oras_bytes(Ctx* c, int R) {
@@ -1492,14 +1506,7 @@ void solve_all(Ctx* c, const mw_solve_opts& o, int ncols, const std::vector<cons
   CK(cudaEventSynchronize(c->ev1));
   float ms = 0;
   CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-  if (c->prec.ready && c->prec.apply_prec == 2 && c->prec.tc.err) {
-    int32_t e = 0;
-    CK(cudaMemcpy(&e, c->prec.tc.err, sizeof(int32_t), cudaMemcpyDeviceToHost));
-    if (e != 0) {
-      CK(cudaMemsetAsync(c->prec.tc.err, 0, sizeof(int32_t), s));
-      throw Fail{MW_ETIMEOUT, "tensor-core preconditioner apply: bounded wait ran out (code " + std::to_string(e) + ")"};
-    }
-  }
+  check_tc_wait(c);
   if (c->prec.ready && c->prec.apply_prec == 5)
     for (auto& L : c->prec.mf.tcl) {
       if (!L.plan.err) continue;
@@ -2570,6 +2577,7 @@ mw_status mw_apply_preconditioner(mw_ctx* c, int32_t f, const void* r, void* z, 
       dfree(c, b);
     }
     check_launch("apply preconditioner");
+    check_tc_wait(c);
   });
 }
 
@@ -3027,6 +3035,31 @@ mw_status mw_gradient_dev(mw_ctx* c, const mw_solve_opts* opts, const void* S_ob
 }
 
 
+mw_status mw_krylov_dots(mw_ctx* c, int32_t nvec, const void* V_dev, int64_t vstride, const void* w_dev,
+                         int64_t n_rows, int32_t n_cols, double* h_out) {
+  return guard(c, [&] {
+    require(nvec >= 1 && nvec <= 64 && V_dev && w_dev && h_out && n_rows >= 1 && n_cols >= 1 && n_cols <= 128 &&
+                vstride >= n_rows * (int64_t)n_cols,
+            MW_EINVAL, "bad arguments");
+    double2* part = dalloc<double2>(c, (size_t)mwk::kCgsDotsMaxParts * nvec * n_cols);
+    double2* h = dalloc<double2>(c, (size_t)nvec * n_cols);
+    int32_t* err = dalloc<int32_t>(c, 1);
+    CK(cudaMemsetAsync(err, 0, sizeof(int32_t), c->stream));
+    const int np = mwk::cgs_dots_f32((const float2*)V_dev, vstride, nvec, (const float2*)w_dev, n_rows, n_cols, part,
+                                     err, c->stream);
+    mwk::reduce_h(part, np, nvec, n_cols, h, c->stream);
+    int32_t e = 0;
+    CK(cudaMemcpyAsync(h_out, h, sizeof(double2) * nvec * n_cols, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&e, err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c, part);
+    dfree(c, h);
+    dfree(c, err);
+    check_launch("krylov dots");
+    require(e == 0, MW_ETIMEOUT, "streaming Gram-Schmidt dots: bounded wait ran out");
+  });
+}
+
 // Tensor-core preconditioner apply for callers that cannot allocate device memory: the
 // gathered operand goes to the library's fixed scratch array, nothing else is allocated.
 mw_status mw_apply_preconditioner_noalloc(mw_ctx* c, int32_t f, const void* r, void* z, int32_t n_cols) {
@@ -3044,6 +3077,7 @@ mw_status mw_apply_preconditioner_noalloc(mw_ctx* c, int32_t f, const void* r, v
     mwk::oras_apply_tc(c->prec.tc, c->prec.topo(), c->prec.W[f], (const float2*)r, (float2*)z, n_cols, scratch,
                        c->stream);
     check_launch("allocation-free preconditioner apply");
+    check_tc_wait(c);
   });
 }
 

@@ -118,6 +118,7 @@ _SIGS = {
     "mw_profile_enable": (C.c_int32, [_P, C.c_uint32]),
     "mw_profile_read": (C.c_int32, [_P, _P, _P, _P]),
     "mw_apply_preconditioner_noalloc": (C.c_int32, [_P, C.c_int32, _P, _P, C.c_int32]),
+    "mw_krylov_dots": (C.c_int32, [_P, C.c_int32, _P, C.c_int64, _P, C.c_int64, C.c_int32, _P]),
     "mw_selftest_bounded_wait": (C.c_int32, [_P, C.c_int64, C.POINTER(C.c_int32)]),
     "mw_nn_param_count": (C.c_int64, [C.c_int32]),
     "mw_sparse_plan_stats": (C.c_int32, [C.c_int64, _P, C.c_int64, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P]),
@@ -323,6 +324,13 @@ class Context:
     def apply_preconditioner_noalloc(self, f: int, r, z, n_cols: int):
         """Allocation-free apply (complex64 device in/out, BF16 preconditioner only)."""
         self._check(self.lib.mw_apply_preconditioner_noalloc(self.h, f, _ptr(r), _ptr(z), n_cols))
+
+    def krylov_dots(self, V, w, nvec: int, vstride: int, n_rows: int, n_cols: int) -> np.ndarray:
+        """h[i][c] = V_i[:, c]^H w[:, c] for i < nvec (complex64 device inputs, the solver's
+        streaming dots kernel); returns complex128 [nvec][n_cols]."""
+        h = np.empty((nvec, n_cols), np.complex128)
+        self._check(self.lib.mw_krylov_dots(self.h, nvec, _ptr(V), vstride, _ptr(w), n_rows, n_cols, _ptr(h)))
+        return h
 
     def get_partition(self):
         owner = np.empty(self.info.n_edge, np.int32)

@@ -95,3 +95,24 @@ def test_grid_to_tets(ctx):
     ref = nn.grid_to_tets(grid.astype(np.float64), box, m.xyz, m.tets)
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
     assert np.count_nonzero(np.abs(ref).sum(1)) > 100
+
+
+def test_forward_loss_gradient_full_size(ctx):
+    """The configuration the network trains at: 8192 inputs (64 x 64 complex Delta S), batch 64.
+    The long-K GEMMs (8192 x 1024 forward, dW1 = dz1^T x backward) are checked here."""
+    n_in, B = 8192, 64
+    th = _theta(11, n_in)
+    rng = np.random.default_rng(12)
+    x = rng.normal(size=(B, n_in)).astype(np.float32)
+    t = (rng.normal(size=(B, 2, 32, 32, 32)) * 0.1).astype(np.float32)
+    ctx.nn_init(n_in, th)
+    y = ctx.nn_infer(x)
+    tho = _oracle_theta(th, n_in)
+    yo, _ = nn.forward(nn.unpack(tho, n_in), x.astype(np.float64))
+    assert _rel(y, yo) <= 1e-5
+    L, g = ctx.nn_loss_grad(x, t)
+    Lo, go = nn.loss_and_grad(tho, n_in, x.astype(np.float64), t.astype(np.float64))
+    assert abs(L - Lo) <= 1e-5 * Lo
+    gp, gop = nn.unpack(g.astype(np.float64), n_in), nn.unpack(go, n_in)
+    for name, _ in nn.param_shapes(n_in):
+        assert _rel(gp[name], gop[name]) <= 1e-4, name

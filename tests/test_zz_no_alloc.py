@@ -1,4 +1,4 @@
-"""The allocation-free preconditioner apply against the regular one.
+"""The allocation-free preconditioner apply against the regular one and the oracle.
 
 mw_apply_preconditioner_noalloc serves callers that cannot allocate device memory when they
 apply the preconditioner; it must give the same result as mw_apply_preconditioner, call after
@@ -8,6 +8,8 @@ collected last so that a failure here leaves every other test already run.
 import numpy as np
 import pytest
 
+from oracle import assemble as asm
+from oracle import oras
 from phantom import EPS_MATCHING, box_partition, kuhn_mesh
 
 pytestmark = pytest.mark.gpu
@@ -24,6 +26,9 @@ def test_noalloc_apply_matches_regular_apply_twice():
     c.assemble([1e9], np.stack([eps.real, eps.imag], 1), EPS_MATCHING)
     c.setup_preconditioner(4, box_partition(m, (2, 2, 1), seed=7), 1, mw.MW_PREC_BF16)
     E = c.info.n_edge
+    sysm = asm.build_system(m.xyz, m.tets)
+    P = oras.ORAS(sysm, box_partition(m, (2, 2, 1), seed=7), 4, 1, eps, 1e9, EPS_MATCHING)
+    P.apply_many = lambda R: np.stack([P.apply(R[:, k]) for k in range(R.shape[1])], 1)
     for call, ncols in enumerate((24, 7)):
         X = rng.normal(size=(E, ncols)) + 1j * rng.normal(size=(E, ncols))
         x64 = torch.from_numpy(X).to(torch.complex64).cuda()          # the value both paths see
@@ -38,6 +43,10 @@ def test_noalloc_apply_matches_regular_apply_twice():
         # parity tests is 1e-2 against the FP64 operator)
         assert np.all(np.isfinite(a)), f"call {call}: rows left unwritten"
         assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b), f"call {call}"
+        # and against the oracle's ORAS operator (exact sparse-LU subdomain solves, FP64), at the
+        # bar of the BF16 tensor-core apply in the parity tests
+        zo = P.apply_many(x64.cpu().numpy().astype(np.complex128))
+        assert np.linalg.norm(a - zo) <= 1e-2 * np.linalg.norm(zo), f"call {call}"
     c.close()
 
 
