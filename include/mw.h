@@ -402,15 +402,22 @@ enum {
   MW_K_CGS_DOTS = 2,    /* Gram-Schmidt dot products and their reduction (K6) */
   MW_K_CGS_UPDATE = 3,  /* Gram-Schmidt update and norm (K6) */
   MW_K_RESIDUAL = 4,    /* FP64 residual b - A x (K8) */
-  MW_K_NCLASS = 5
+  MW_K_REASSEMBLE = 5,  /* eps -> A_f reassembly and the double-float split of A_f (K2) */
+  MW_K_GRADIENT = 6,    /* per-tet adjoint gradient (K11) */
+  MW_K_FACTOR = 7,      /* ORAS subdomain inverses: blocked Gauss-Jordan (K5 setup) */
+  MW_K_NN_GEMM = 8,     /* learned initialiser: dense layers, forward and backward (K13) */
+  MW_K_NN_CONV = 9,     /* learned initialiser: transposed convolutions, forward and backward (K14) */
+  MW_K_NN_OTHER = 10,   /* learned initialiser: loss, activations, bias sums, Adam, batch gathers */
+  MW_K_NCLASS = 11
 };
 /* Record CUDA events around the launches of the classes in mask (bit k = class k); 0 = off.
  * Events cost a few microseconds each. */
 mw_status mw_profile_enable(mw_ctx* ctx, uint32_t class_mask);
-/* Per class since enable: summed durations (ms), launch count and algorithmic bytes (the
- * bytes each launch must move at minimum: operands read once, results written once; bytes may
- * be NULL); resets the counters. */
-mw_status mw_profile_read(mw_ctx* ctx, double* ms, int64_t* launches, double* bytes);
+/* Per class since enable: summed durations (ms), launch count, algorithmic bytes (the bytes
+ * each launch must move at minimum: operands read once, results written once) and algorithmic
+ * floating-point operations (real flops of the defining arithmetic, 0 for classes rated by
+ * bytes); bytes and flops may be NULL; arrays of MW_K_NCLASS entries; resets the counters. */
+mw_status mw_profile_read(mw_ctx* ctx, double* ms, int64_t* launches, double* bytes, double* flops);
 
 #ifdef __cplusplus
 }

@@ -139,10 +139,11 @@ struct Profiler {
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
-  double bytes[MW_K_NCLASS] = {0, 0, 0, 0, 0};
+  double bytes[MW_K_NCLASS] = {};
+  double flops[MW_K_NCLASS] = {};
   // device time and launches of classes timed inside replayed cycle graphs
-  double graph_ms[MW_K_NCLASS] = {0, 0, 0, 0, 0};
-  int64_t graph_launches[MW_K_NCLASS] = {0, 0, 0, 0, 0};
+  double graph_ms[MW_K_NCLASS] = {};
+  int64_t graph_launches[MW_K_NCLASS] = {};
   cudaEvent_t get() {
     if (used == pool.size()) {
       cudaEvent_t e;
@@ -915,12 +916,14 @@ struct ProfScope {
   Ctx* c;
   int cls;
   cudaEvent_t a = nullptr;
-  // bytes: algorithmic bytes moved by the enclosed launches (for roofline fractions)
-  ProfScope(Ctx* c_, int k, double bytes) : c(c_), cls(k) {
+  // bytes / flops: algorithmic bytes moved and flops done by the enclosed launches (for
+  // roofline fractions)
+  ProfScope(Ctx* c_, int k, double bytes, double flops = 0.0) : c(c_), cls(k) {
     if (c->prof.mask & (1u << k)) {
       a = c->prof.get();
       cudaEventRecord(a, c->stream);
       c->prof.bytes[k] += bytes;
+      c->prof.flops[k] += flops;
     }
   }
   ~ProfScope() {
@@ -1664,8 +1667,13 @@ void reassemble_all(Ctx* c) {
   if (eb[1] < 0) si = -si;
   upload_face_classes(c, si, sr);
   const int nc = 2 + c->n_port;
+  const int64_t T = c->topo.n_tet, Fb = c->topo.n_bface;
+  // pull map and offsets, element matrices and eps read once, FP64 and FP32 values written;
+  // the double-float split reads the FP64 values and writes their (hi, lo) pairs
+  const double rbytes = 8.0 * (nnz + 1) + 4.0 * (36.0 * T + 9.0 * Fb) + (42.0 * 8 + 16) * T + 48.0 * Fb + 24.0 * nnz;
   for (int f = 0; f < c->n_freq; ++f) {
     const double k0 = k0_of(c->freqs[f]);
+    ProfScope ps(c, MW_K_REASSEMBLE, rbytes + 32.0 * nnz);
     mwk::reassemble(c->d_cptr, c->d_contrib, nnz, c->d_KM, c->d_Bf, c->d_eps, k0 * k0, -k0 * si, k0 * sr,
                     c->d_bface_cls, c->d_zc ? c->d_zc + (size_t)f * nc : nullptr, c->d_nzmask, c->A64[f], c->A32[f],
                     c->stream);
@@ -2524,7 +2532,13 @@ mw_status mw_setup_preconditioner(mw_ctx* c, int32_t n_sub, const int32_t* part,
           const double2* zc = c->d_zc ? c->d_zc + (size_t)f * (2 + c->n_port) : nullptr;
           mwk::oras_local_assemble(bt, p.topo(), p.Bsurf, c->d_KM, c->d_eps, k0, c->eps_bg[0], c->eps_bg[1], zc,
                                    c->d_metal, p.factor_prec, ws, c->stream);
-          mwk::oras_invert(bt, p.factor_prec, ws, dinv, d_status, c->stream);
+          {
+            // in-place Gauss-Jordan inversion: n^3 complex multiply-adds (8 n^3 real flops)
+            double fl = 0;
+            for (int64_t n : bn) fl += 8.0 * (double)n * n * n;
+            ProfScope ps(c, MW_K_FACTOR, 0.0, fl);
+            mwk::oras_invert(bt, p.factor_prec, ws, dinv, d_status, c->stream);
+          }
           if (p.apply_prec == 2)
             mwk::tc_extract(p.tc, bt, p.topo(), p.factor_prec, ws, p.W[f], c->stream);
           else
@@ -2724,6 +2738,9 @@ static void gradient_dev_impl(Ctx* c, const mw_solve_opts& o, const double2* dSo
   CK(cudaMemsetAsync(dg, 0, sizeof(double) * 2 * T, c->stream));
   for (int f = 0; f < nf; ++f) {
     const double k0 = k0_of(c->freqs[f]);
+    // both fields read once, M^T and the tet's edges once, the gradient read and written; per
+    // tet and column M x (36 real-by-complex FMAs) and lambda . (M x) (6 complex MACs)
+    ProfScope ps(c, MW_K_GRADIENT, 2.0 * 16 * E * ns + (21.0 * 8 + 24 + 32) * T, 192.0 * T * ns);
     mwk::grad_tet(c->d_tet_edge, c->d_KM, T, c->Lf[f], c->Xf[f], ns, k0 * k0, dg, c->stream);
   }
   check_launch("gradient");
@@ -2981,20 +2998,23 @@ mw_status mw_profile_enable(mw_ctx* c, uint32_t mask) {
     c->prof.used = 0;
     for (int k = 0; k < MW_K_NCLASS; ++k) {
       c->prof.bytes[k] = 0;
+      c->prof.flops[k] = 0;
       c->prof.graph_ms[k] = 0;
       c->prof.graph_launches[k] = 0;
     }
   });
 }
 
-mw_status mw_profile_read(mw_ctx* c, double* ms, int64_t* launches, double* bytes) {
+mw_status mw_profile_read(mw_ctx* c, double* ms, int64_t* launches, double* bytes, double* flops) {
   return guard(c, [&] {
     require(ms && launches, MW_EINVAL, "null outputs");
     for (int k = 0; k < MW_K_NCLASS; ++k) {
       ms[k] = c->prof.graph_ms[k];
       launches[k] = c->prof.graph_launches[k];
       if (bytes) bytes[k] = c->prof.bytes[k];
+      if (flops) flops[k] = c->prof.flops[k];
       c->prof.bytes[k] = 0;
+      c->prof.flops[k] = 0;
       c->prof.graph_ms[k] = 0;
       c->prof.graph_launches[k] = 0;
     }
@@ -3212,8 +3232,17 @@ static void nn_forward(Ctx* c, int B) {
   NnState& n = c->nn;
   const float* th = n.theta;
   cudaStream_t s = c->stream;
-  mwk::nn_gemm_bf16(n.x, n.n_in, 1, n.W1b, 1, n.n_in, th + n.ob1, n.z1, n.h1, B, kHid, n.n_in, s);
-  mwk::nn_gemm_bf16(n.h1, kHid, 1, n.W2b, 1, kHid, th + n.ob2, n.z2, n.h2, B, kHid, kHid, s);
+  const double Bd = B, ni = n.n_in, H = kHid;
+  {
+    // BF16 weights, FP32 inputs and biases read once; pre- and post-activation written
+    ProfScope ps(c, MW_K_NN_GEMM, 2.0 * H * (ni + H) + 4.0 * Bd * (ni + H) + 8.0 * H + 16.0 * Bd * H,
+                 2.0 * Bd * H * (ni + H));
+    mwk::nn_gemm_bf16(n.x, n.n_in, 1, n.W1b, 1, n.n_in, th + n.ob1, n.z1, n.h1, B, kHid, n.n_in, s);
+    mwk::nn_gemm_bf16(n.h1, kHid, 1, n.W2b, 1, kHid, th + n.ob2, n.z2, n.h2, B, kHid, kHid, s);
+  }
+  // each input voxel meets 4^3 taps per (ci, co) pair: 16x16 at 4^3, 16x8 at 8^3, 8x2 at 16^3
+  ProfScope ps(c, MW_K_NN_CONV, 4.0 * Bd * (H + 2 * 2 * 16 * 512 + 2 * 8 * 4096 + kOut),
+               2.0 * 64 * Bd * (16 * 16 * 64 + 16 * 8 * 512 + 8 * 2 * 4096));
   mwk::nn_convT_fwd(n.h2, th + n.oC1, th + n.oc1, n.a1, n.g1, B, 16, 16, 4, s);
   mwk::nn_convT_fwd(n.g1, th + n.oC2, th + n.oc2, n.a2, n.g2, B, 16, 8, 8, s);
   mwk::nn_convT_fwd(n.g2, th + n.oC3, th + n.oc3, n.y, nullptr, B, 8, 2, 16, s);
@@ -3225,12 +3254,25 @@ static void nn_backward(Ctx* c, int B) {
   const float* th = n.theta;
   float* g = n.grad;
   cudaStream_t s = c->stream;
-  mwk::nn_mse(n.y, n.t, (int64_t)B * kOut, n.dy, n.part, n.loss, s);
-  mwk::nn_convT_bwd(n.g2, th + n.oC3, n.dy, n.dg2, g + n.oC3, g + n.oc3, B, 8, 2, 16, s);
-  mwk::nn_relu_back(n.a2, n.dg2, n.da2, (int64_t)B * 8 * 4096, s);
-  mwk::nn_convT_bwd(n.g1, th + n.oC2, n.da2, n.dg1, g + n.oC2, g + n.oc2, B, 16, 8, 8, s);
-  mwk::nn_relu_back(n.a1, n.dg1, n.da1, (int64_t)B * 16 * 512, s);
-  mwk::nn_convT_bwd(n.h2, th + n.oC1, n.da1, n.dh2, g + n.oC1, g + n.oc1, B, 16, 16, 4, s);
+  const double Bd = B, ni = n.n_in, H = kHid;
+  {
+    ProfScope ps(c, MW_K_NN_OTHER, 12.0 * Bd * kOut);
+    mwk::nn_mse(n.y, n.t, (int64_t)B * kOut, n.dy, n.part, n.loss, s);
+  }
+  {
+    // backward-data and backward-weight of each transposed convolution (twice the forward
+    // flops; the first layer's input gradient is the reshaped dh2), ReLU masks between them
+    ProfScope ps(c, MW_K_NN_CONV, 4.0 * Bd * (kOut + 3 * 2 * 8 * 4096 + 3 * 2 * 16 * 512 + 2 * H),
+                 4.0 * 64 * Bd * (16 * 16 * 64 + 16 * 8 * 512 + 8 * 2 * 4096));
+    mwk::nn_convT_bwd(n.g2, th + n.oC3, n.dy, n.dg2, g + n.oC3, g + n.oc3, B, 8, 2, 16, s);
+    mwk::nn_relu_back(n.a2, n.dg2, n.da2, (int64_t)B * 8 * 4096, s);
+    mwk::nn_convT_bwd(n.g1, th + n.oC2, n.da2, n.dg1, g + n.oC2, g + n.oc2, B, 16, 8, 8, s);
+    mwk::nn_relu_back(n.a1, n.dg1, n.da1, (int64_t)B * 16 * 512, s);
+    mwk::nn_convT_bwd(n.h2, th + n.oC1, n.da1, n.dh2, g + n.oC1, g + n.oc1, B, 16, 16, 4, s);
+  }
+  // dW2 = dz2^T h1, dh1 = dz2 W2 (BF16 W2), dW1 = dz1^T x; bias sums and ReLU masks between
+  ProfScope ps(c, MW_K_NN_GEMM, 4.0 * H * (H + ni) + 2.0 * H * H + 4.0 * Bd * (ni + 6 * H) + 8.0 * H,
+               2.0 * Bd * H * (2 * H + ni));
   mwk::nn_relu_back(n.z2, n.dh2, n.dz2, (int64_t)B * kHid, s);
   mwk::nn_gemm_f32(n.dz2, 1, kHid, n.h1, kHid, 1, nullptr, g + n.oW2, nullptr, kHid, kHid, B, s);
   mwk::nn_colsum(n.dz2, B, kHid, g + n.ob2, s);
@@ -3336,13 +3378,22 @@ mw_status mw_nn_train(mw_ctx* c, const mw_nn_opts* o, int64_t nsamp, const float
       for (int64_t b0 = 0; b0 < nsamp; b0 += B) {
         const int nb = (int)std::min<int64_t>(B, nsamp - b0);
         CK(cudaMemcpyAsync(n.idx, perm.data() + b0, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, c->stream));
-        mwk::nn_gather_rows(n.data_x, n.idx, nb, n.n_in, n.x, c->stream);
-        mwk::nn_gather_rows(n.data_t, n.idx, nb, kOut, n.t, c->stream);
+        {
+          ProfScope ps(c, MW_K_NN_OTHER, 8.0 * nb * ((double)n.n_in + kOut));
+          mwk::nn_gather_rows(n.data_x, n.idx, nb, n.n_in, n.x, c->stream);
+          mwk::nn_gather_rows(n.data_t, n.idx, nb, kOut, n.t, c->stream);
+        }
         nn_forward(c, nb);
         nn_backward(c, nb);
         n.step++;
-        mwk::nn_adam(n.theta, n.grad, n.m, n.v, n.np, o->lr, o->beta1, o->beta2, o->eps, n.step, c->stream);
-        nn_refresh_bf16(c);
+        {
+          // Adam reads the parameters, gradient and both moments and writes three of them back;
+          // the BF16 copies of W1 and W2 are refreshed from the new parameters
+          ProfScope ps(c, MW_K_NN_OTHER,
+                       28.0 * (double)n.np + 6.0 * (double)kHid * ((double)n.n_in + kHid));
+          mwk::nn_adam(n.theta, n.grad, n.m, n.v, n.np, o->lr, o->beta1, o->beta2, o->eps, n.step, c->stream);
+          nn_refresh_bf16(c);
+        }
         double l = 0;
         CK(cudaMemcpyAsync(&l, n.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));   // perm slice and loss are host memory

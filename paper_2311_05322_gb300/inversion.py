@@ -38,6 +38,9 @@ SCALES = {
                  samples=256, epochs=120, iters=5, alpha=0.0),
     "full": dict(data=(55, 55, 24), inv=(44, 44, 17), n_src=64, freqs=(0.8e9, 1.0e9, 1.2e9), pdata=(11, 11, 5),
                  pinv=(9, 9, 4), samples=2000, epochs=100, iters=20, alpha=0.0),
+    # the reduced meshes with a smaller training set: the time-to-misfit leg of the default bench
+    "bench": dict(data=(44, 44, 17), inv=(30, 30, 13), n_src=32, freqs=(1.0e9,), pdata=(9, 9, 4), pinv=(6, 6, 3),
+                  samples=300, epochs=120, iters=10, alpha=0.0),
 }
 TARGET_SCALE = 20.0      # Delta eps is trained in units of 20
 TARGET_BLUR_M = 0.003    # targets are blurred to about the resolution the inverse mesh can carry
@@ -130,7 +133,32 @@ def first_time_below(J, secs, target):
     return None
 
 
-def run(scale: str = "reduced", seed: int = 3, plain: bool | None = None, snr_db: float = 40.0, verbose=False):
+def held_out_tear(seed: int, k: int, n: int):
+    """The k-th of n held-out tears: centre and fluid drawn from random_tear, semi-axes rescaled
+    so that their mean is 2 + 8 (k + 1/2) / n mm (each clipped to 2-10 mm), which spreads the
+    tears over the whole size range."""
+    t = random_tear(99_000 + seed + 17 * k, eps_range=FLUID_RANGE)
+    target = 0.002 + 0.008 * (k + 0.5) / n
+    f = target / (sum(t.semi_axes) / 3.0)
+    axes = tuple(min(0.010, max(0.002, a * f)) for a in t.semi_axes)
+    return type(t)(t.center, axes, t.eps)
+
+
+def _stats(v):
+    v = [x for x in v if x is not None]
+    if not v:
+        return {"n": 0}
+    return {"n": len(v), "mean": float(np.mean(v)), "std": float(np.std(v, ddof=1)) if len(v) > 1 else 0.0,
+            "min": float(np.min(v)), "max": float(np.max(v))}
+
+
+def run(scale: str = "reduced", seed: int = 3, plain: bool | None = None, snr_db: float = 40.0, tears: int = 1,
+        alphas=(), verbose=False):
+    """Train the network once, then invert `tears` held-out tears from the healthy start and from
+    the network's start (mixed solver; the plain FP64 inversion too on the first tear when
+    `plain`).  Per tear: the target is the reference inversion's J after max_it (plain FP64 on the
+    first tear when run, else the mixed inversion from the healthy start), and each variant's
+    time to reach it.  `alphas`: Tikhonov sweep of the mixed inversion on the first tear."""
     cfg = SCALES[scale]
     out = {"scale": scale, "config": {k: v for k, v in cfg.items()}}
     f_nn = len(cfg["freqs"]) // 2                       # network sees the middle frequency
@@ -156,18 +184,26 @@ def run(scale: str = "reduced", seed: int = 3, plain: bool | None = None, snr_db
     Y = gen.ctx.nn_infer(X[n_tr:])
     mse_nn = float(np.mean((Y - T[n_tr:]) ** 2)) * TARGET_SCALE ** 2
     mse_zero = float(np.mean(T[n_tr:] ** 2)) * TARGET_SCALE ** 2
-    out["network"] = {"median_rel_dS": rel, "n_in": n_in, "train": n_tr, "test": n - n_tr, "epoch_loss_first_last": [losses[0], losses[-1]],
+    out["network"] = {"median_rel_dS": rel, "n_in": n_in, "train": n_tr, "test": n - n_tr,
+                      "epoch_loss_first_last": [losses[0], losses[-1]],
                       "train_s": train_s, "test_mse": mse_nn, "zero_predictor_mse": mse_zero,
                       "gain": 1.0 - mse_nn / mse_zero}
     theta = gen.ctx.nn_get_params()
+    gen.ctx.close()
 
-    # --- observed data: a held-out tear on the data mesh, all frequencies, noise ------------------
+    # --- observed data: held-out tears on the data mesh, all frequencies, noise -------------------
     data = Forward.build(cfg["data"], cfg["n_src"], cfg["freqs"], cfg["pdata"], eps_h)
-    tear = random_tear(99_000 + seed, eps_range=FLUID_RANGE)
-    S_inj = data.S(shoulder_eps(data_mesh, tear))
     S_emp = data.S(hom)
-    S_obs = add_noise(S_inj, snr_db, seed=7_000 + seed)
     S_hd = data.S(eps_h)
+    w = 1.0 / np.abs(S_emp) ** 2                         # the cost's weights (Eq. sahar:2)
+    obs = []
+    for k in range(tears):
+        tear = held_out_tear(seed, k, tears)
+        S_inj = data.S(shoulder_eps(data_mesh, tear))
+        S_obs = add_noise(S_inj, snr_db, seed=7_000 + seed + 31 * k)
+        sig = float(np.sum(w * np.abs(S_inj - S_hd) ** 2))
+        noise = float(np.sum(w * np.abs(S_obs - S_inj) ** 2))
+        obs.append((tear, S_obs, {"tear_signal": sig, "noise": noise, "snr_db": 10.0 * np.log10(sig / noise)}))
     data.ctx.close()
 
     # --- inversions on the inverse mesh -------------------------------------------------------------
@@ -175,40 +211,74 @@ def run(scale: str = "reduced", seed: int = 3, plain: bool | None = None, snr_db
     eps0 = shoulder_eps(inv_mesh)
     inv = Forward.build(cfg["inv"], cfg["n_src"], cfg["freqs"], cfg["pinv"], eps0)
     inv.ctx.nn_init(n_in, theta)
-    x_obs = ((nn_input(S_obs[f_nn] - S_hd[f_nn], S_emp[f_nn]) - mu) / sd).astype(np.float32)
-    grid = inv.ctx.nn_infer(x_obs[None])[0] * TARGET_SCALE
-    d_eps = inv.ctx.nn_grid_to_tets(grid, np.asarray(ROI_BOX))
-    learned0 = _pairs(eps0) + d_eps
-    io = mw.inv_opts(m=8, max_it=cfg["iters"], alpha=cfg["alpha"], first_step=1.0)
     # differential data: fit S(eps) - S(eps_healthy) on the inverse mesh to S_obs - S_healthy on
     # the data mesh, i.e. S(eps) against S_obs - S_hd + S(eps_healthy, inverse mesh)
     S_hinv = inv.S(eps0)
-    S_fit = S_obs - S_hd + S_hinv
+    mixed = mw.solve_opts(mode=mw.MW_MODE_MIXED, tol=1e-8, inner_tol=1e-4)
+    if plain is None:
+        plain = scale != "full"
 
-    def invert(start, sopts):
+    def invert(S_fit, start, sopts, alpha):
+        io = mw.inv_opts(m=8, max_it=cfg["iters"], alpha=alpha, first_step=1.0)
         e, h = inv.ctx.invert(S_fit, S_emp, start, io, sopts)
         return {"J": h["J"].tolist(), "seconds": h["seconds"].tolist(), "evaluations": h["evaluations"]}
 
-    mixed = mw.solve_opts(mode=mw.MW_MODE_MIXED, tol=1e-8, inner_tol=1e-4)
-    res = {"mixed": invert(_pairs(eps0), mixed), "mixed_learned": invert(learned0, mixed)}
-    if plain is None:
-        plain = scale != "full"
-    if plain:
-        inv.ctx.assemble(list(cfg["freqs"]), _pairs(eps0), EPS_MATCHING)
-        inv.ctx.setup_preconditioner(int(np.prod(cfg["pinv"])), box_partition(inv.mesh, cfg["pinv"], seed=7), 1,
-                                     mw.MW_PREC_FP64_FROM_FP32)
-        res["plain_fp64"] = invert(_pairs(eps0), mw.solve_opts(mode=mw.MW_MODE_FP64, tol=1e-8))
-    ref = res["plain_fp64"] if plain else res["mixed"]
-    target = ref["J"][-1]
-    for k, v in res.items():
-        v["time_to_target_s"] = first_time_below(v["J"], v["seconds"], target)
-    out["inversion"] = res
-    out["target_J"] = target
-    out["target_from"] = "plain_fp64 after max_it" if plain else "mixed after max_it"
-    out["tear"] = {"center": tear.center, "semi_axes": tear.semi_axes, "eps": [tear.eps.real, tear.eps.imag]}
-    out["learned_start_dJ0"] = res["mixed_learned"]["J"][0] - res["mixed"]["J"][0]
+    cases = []
+    for k, (tear, S_obs, snr) in enumerate(obs):
+        S_fit = S_obs - S_hd + S_hinv
+        x_obs = ((nn_input(S_obs[f_nn] - S_hd[f_nn], S_emp[f_nn]) - mu) / sd).astype(np.float32)
+        grid = inv.ctx.nn_infer(x_obs[None])[0] * TARGET_SCALE
+        learned0 = _pairs(eps0) + inv.ctx.nn_grid_to_tets(grid, np.asarray(ROI_BOX))
+        res = {"mixed": invert(S_fit, _pairs(eps0), mixed, cfg["alpha"]),
+               "mixed_learned": invert(S_fit, learned0, mixed, cfg["alpha"])}
+        if plain and k == 0:
+            inv.ctx.assemble(list(cfg["freqs"]), _pairs(eps0), EPS_MATCHING)
+            # FP64 factorisation and FP64 apply: the plain path is FP64 throughout (its setup is
+            # outside the inversion's clock, like the mixed path's)
+            t_setup = time.time()
+            inv.ctx.setup_preconditioner(int(np.prod(cfg["pinv"])), box_partition(inv.mesh, cfg["pinv"], seed=7), 1,
+                                         mw.MW_PREC_FP64)
+            out["plain_fp64_setup_s"] = time.time() - t_setup
+            res["plain_fp64"] = invert(S_fit, _pairs(eps0), mw.solve_opts(mode=mw.MW_MODE_FP64, tol=1e-8),
+                                       cfg["alpha"])
+            inv.ctx.assemble(list(cfg["freqs"]), _pairs(eps0), EPS_MATCHING)
+            inv.ctx.setup_preconditioner(int(np.prod(cfg["pinv"])), box_partition(inv.mesh, cfg["pinv"], seed=7), 1,
+                                         mw.MW_PREC_BF16)
+        ref = res["plain_fp64"] if "plain_fp64" in res else res["mixed"]
+        target = ref["J"][-1]
+        for v in res.values():
+            v["time_to_target_s"] = first_time_below(v["J"], v["seconds"], target)
+        cases.append({"tear": {"center": tear.center, "semi_axes": tear.semi_axes,
+                               "eps": [tear.eps.real, tear.eps.imag]},
+                      "inversion": res, "target_J": target,
+                      "target_from": "plain_fp64 after max_it" if "plain_fp64" in res else "mixed after max_it",
+                      "learned_start_dJ0": res["mixed_learned"]["J"][0] - res["mixed"]["J"][0],
+                      "learned_start_rel_dJ0": (res["mixed_learned"]["J"][0] - res["mixed"]["J"][0])
+                      / res["mixed"]["J"][0], **snr})
+        if verbose:
+            print(json.dumps(cases[-1]), flush=True)
+    # the first tear's record keeps the single-tear keys
+    out.update({k: cases[0][k] for k in ("inversion", "target_J", "target_from", "tear", "learned_start_dJ0")})
+    out["cases"] = cases
+    out["summary"] = {
+        "tears": len(cases),
+        "snr_db": _stats([c["snr_db"] for c in cases]),
+        "time_to_target_s": {v: _stats([c["inversion"][v]["time_to_target_s"] for c in cases])
+                             for v in ("mixed", "mixed_learned")},
+        "learned_start_rel_dJ0": _stats([c["learned_start_rel_dJ0"] for c in cases]),
+        "learned_reaches_target_first": sum(
+            1 for c in cases if c["inversion"]["mixed_learned"]["time_to_target_s"] is not None
+            and c["inversion"]["mixed_learned"]["time_to_target_s"] < c["inversion"]["mixed"]["time_to_target_s"]),
+    }
+    sweep = []
+    for a in alphas:
+        tear, S_obs, _ = obs[0]
+        r = invert(S_obs - S_hd + S_hinv, _pairs(eps0), mixed, a)
+        # time until the run is within 5 % of its own final cost
+        r["time_to_5pct_of_final_s"] = first_time_below(r["J"], r["seconds"], 1.05 * r["J"][-1])
+        sweep.append({"alpha": a, **r})
+    out["alpha_sweep"] = sweep
     out["total_s"] = time.time() - t0
-    gen.ctx.close()
     inv.ctx.close()
     return out
 
@@ -218,5 +288,10 @@ if __name__ == "__main__":
     ap.add_argument("--scale", default="reduced", choices=list(SCALES))
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--plain", action="store_true")
+    ap.add_argument("--tears", type=int, default=1)
+    ap.add_argument("--alphas", default="", help="comma-separated Tikhonov weights for the sweep")
     a = ap.parse_args()
-    print(json.dumps(run(a.scale, a.seed, plain=False if a.no_plain else None)), flush=True)
+    plain = False if a.no_plain else (True if a.plain else None)
+    alphas = [float(x) for x in a.alphas.split(",") if x]
+    print(json.dumps(run(a.scale, a.seed, plain=plain, tears=a.tears, alphas=alphas, verbose=True)), flush=True)

@@ -116,7 +116,7 @@ _SIGS = {
     "mw_gradient_dev": (C.c_int32, [_P, C.POINTER(mw_solve_opts), _P, _P, C.c_double, C.POINTER(C.c_double), _P]),
     "mw_kernel_launches": (C.c_int64, []),
     "mw_profile_enable": (C.c_int32, [_P, C.c_uint32]),
-    "mw_profile_read": (C.c_int32, [_P, _P, _P, _P]),
+    "mw_profile_read": (C.c_int32, [_P, _P, _P, _P, _P]),
     "mw_apply_preconditioner_noalloc": (C.c_int32, [_P, C.c_int32, _P, _P, C.c_int32]),
     "mw_krylov_dots": (C.c_int32, [_P, C.c_int32, _P, C.c_int64, _P, C.c_int64, C.c_int32, _P]),
     "mw_selftest_bounded_wait": (C.c_int32, [_P, C.c_int64, C.POINTER(C.c_int32)]),
@@ -130,8 +130,10 @@ _SIGS = {
     "mw_nn_grid_to_tets": (C.c_int32, [_P, _P, C.c_int32, _P, _P]),
 }
 
-MW_K_SPMM, MW_K_ORAS, MW_K_CGS_DOTS, MW_K_CGS_UPDATE, MW_K_RESIDUAL, MW_K_NCLASS = range(6)
-K_CLASS_NAMES = ("spmm", "oras_apply", "cgs_dots", "cgs_update", "residual_fp64")
+(MW_K_SPMM, MW_K_ORAS, MW_K_CGS_DOTS, MW_K_CGS_UPDATE, MW_K_RESIDUAL, MW_K_REASSEMBLE, MW_K_GRADIENT, MW_K_FACTOR,
+ MW_K_NN_GEMM, MW_K_NN_CONV, MW_K_NN_OTHER, MW_K_NCLASS) = range(12)
+K_CLASS_NAMES = ("spmm", "oras_apply", "cgs_dots", "cgs_update", "residual_fp64", "reassemble", "gradient",
+                 "factor", "nn_gemm", "nn_conv", "nn_other")
 
 _lib = None
 
@@ -460,8 +462,10 @@ class Context:
         ms = np.zeros(MW_K_NCLASS)
         n = np.zeros(MW_K_NCLASS, np.int64)
         b = np.zeros(MW_K_NCLASS)
-        self._check(self.lib.mw_profile_read(self.h, _ptr(ms), _ptr(n), _ptr(b)))
-        return {K_CLASS_NAMES[k]: {"ms": float(ms[k]), "launches": int(n[k]), "bytes": float(b[k])}
+        fl = np.zeros(MW_K_NCLASS)
+        self._check(self.lib.mw_profile_read(self.h, _ptr(ms), _ptr(n), _ptr(b), _ptr(fl)))
+        return {K_CLASS_NAMES[k]: {"ms": float(ms[k]), "launches": int(n[k]), "bytes": float(b[k]),
+                                   "flops": float(fl[k])}
                 for k in range(MW_K_NCLASS)}
 
     def invert(self, S_obs, S_empty, eps0, inv: mw_inv_opts, opts: mw_solve_opts | None = None):

@@ -1,5 +1,5 @@
-"""Host helpers of the bench: the waveguide layout per wall, the FP32 ALU peak it reports the
-sparse sweeps against, and the option set of the measured variants."""
+"""Host helpers of the bench: the waveguide layout per wall, the per-class roofline ratings, and
+the option set of the measured variants."""
 import sys
 
 import pytest
@@ -19,9 +19,18 @@ def test_waveguide_counts(bench):
         assert c[0] == 0 and sum(c) == n and max(c[1:]) - min(c[1:]) <= 1
 
 
-def test_fp32_peak_from_unit_counts(bench):
-    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
-    assert bench.FP32_PEAK_TFLOPS == pytest.approx(80.54784, rel=1e-12)
+def test_rate_classes(bench):
+    prof = {"spmm": {"ms": 2.0, "launches": 4, "bytes": 8e9, "flops": 1e9},
+            "gradient": {"ms": 10.0, "launches": 1, "bytes": 1e9, "flops": 8e9},
+            "nn_conv": {"ms": 1.0, "launches": 3, "bytes": 1e6, "flops": 2e10},
+            "factor": {"ms": 0.0, "launches": 0, "bytes": 0.0, "flops": 0.0}}
+    r = bench.rate_classes(prof, 6000.0, {"fp32_tflops": 60.0, "fp64_tflops": 1.0})
+    assert set(r) == {"spmm", "gradient", "nn_conv"}                 # classes that never ran are left out
+    assert r["spmm"]["bound"] == "hbm" and r["spmm"]["achieved"] == pytest.approx(4000.0)
+    assert r["spmm"]["frac"] == pytest.approx(4000.0 / 6000.0)
+    assert r["gradient"]["bound"] == "fp64" and r["gradient"]["achieved"] == pytest.approx(0.8)
+    assert r["gradient"]["frac"] == pytest.approx(0.8)
+    assert r["nn_conv"]["bound"] == "fp32" and r["nn_conv"]["frac"] == pytest.approx(20.0 / 60.0)
 
 
 def test_variant_options_parse(bench):
