@@ -126,7 +126,8 @@ mw_status mw_set_graphs(mw_ctx* ctx, int32_t enable);
  *                  (only with a BF16 preconditioner in mixed mode);
  *   dots_stages    ring depth of the streaming Gram-Schmidt dots, 2..6 (16..128 columns);
  *   update_stages  ring depth of the streaming Gram-Schmidt update, 2..6 (16..128 columns);
- *   spmm_threads   threads per block of the SpMM, 128 / 256 / 512.
+ *   spmm_threads   threads per block of the row-per-warp SpMM, 128 / 256 / 512, or 1 for the
+ *                  halo-tiled SpMM (FP32, even column counts).
  * None of these changes a result bit: the same arithmetic runs in the same order.  The choice is
  * kept per shape until the mesh or preconditioner changes.  Solves tune each new shape before
  * their timed phase while automatic tuning is on (mw_set_autotune, default on); mw_autotune
@@ -178,7 +179,9 @@ mw_status mw_get_matrix(mw_ctx* ctx, int32_t f, double* values);
 /* Y = A_f X on the device for n_cols columns, layout [E][n_cols] (column fastest),
  * complex128 (prec = MW_PREC_FP64, FP64 arithmetic) or complex64 (MW_PREC_FP32, FP32); prec = 3
  * takes complex128 in and out and computes in double-float arithmetic on the FP32 pipes (the
- * mixed solver's outer residual). */
+ * mixed solver's outer residual); prec = 4 is the FP32 product of the halo-tiled kernel (rows
+ * in Morton-ordered blocks whose columns of X are staged in shared memory; even n_cols, x
+ * 16-byte aligned), bit-identical to MW_PREC_FP32. */
 mw_status mw_apply_matrix(mw_ctx* ctx, int32_t f, int32_t prec, const void* x_dev, void* y_dev,
                           int32_t n_cols);
 
@@ -252,6 +255,15 @@ mw_status mw_setup_preconditioner(mw_ctx* ctx, int32_t n_sub, const int32_t* tet
 mw_status mw_sparse_plan_stats(int64_t n_vert, const double* xyz, int64_t n_tet, const int32_t* tet_vert,
                                int32_t n_sub, const int32_t* tet_part, int32_t overlap_layers, int32_t leaf,
                                int64_t* stats);
+/* Host-only check of the halo-tiled SpMM plan (no context, no GPU): builds the topology and the
+ * plan mw_set_mesh uses (rows in the Morton order of their edge midpoints, cut into blocks whose
+ * column sets hold at most halo_max edges) and verifies its invariants: every row once, blocks
+ * in order, each block's halo ascending and within bound, each blocked nonzero mapped to the
+ * canonical nonzero of its row in the same order, and every halo-local column naming that
+ * nonzero's column.  stats[4] receives: blocks, summed halo sizes, largest halo, nonzeros.
+ * MW_ECUDA reports a broken invariant; MW_EINVAL bad arguments (64 <= halo_max <= 65535). */
+mw_status mw_spmm_plan_stats(int64_t n_vert, const double* xyz, int64_t n_tet, const int32_t* tet_vert,
+                             int32_t halo_max, int64_t* stats);
 /* z = M_f^{-1} r on the device, complex128 [E][n_cols] in and out (parity hook).  Returns
  * after the apply has completed; MW_ETIMEOUT when a bounded wait of the tensor-core apply ran
  * out (z is then incomplete). */

@@ -139,6 +139,79 @@ void spmm_launch(const int64_t* rp, const int32_t* ci, const T* A, const T* X, T
   }
 }
 
+// Halo-tiled FP32 SpMM.  One CTA takes one block of the SpMM plan (rows in Morton order whose
+// column set, the halo, holds at most halo_max edges) and one chunk of kHaloCols columns:
+//  1. the halo's rows of X (kHaloCols complex values each) are staged in shared memory by
+//     16-byte cp.async copies, 8 threads per row;
+//  2. each half-warp computes one row: its 16 lanes hold 16 columns; the row's nonzeros
+//     (value and halo-local column) are loaded 16 at a time, one per lane, and broadcast by
+//     shuffles; every product reads X from shared memory.
+// A row's terms are accumulated in the canonical column order with the same complex FMA
+// sequence as spmm_kernel, so both kernels give bit-identical results.
+constexpr int kHaloCols = 16;
+constexpr int kHaloThreads = 256;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__global__ void __launch_bounds__(kHaloThreads, 2)
+    spmm_halo_kernel(const int64_t* __restrict__ blk_row, const int64_t* __restrict__ blk_halo,
+                     const int32_t* __restrict__ halo, const int32_t* __restrict__ rows,
+                     const int64_t* __restrict__ rptr, const uint16_t* __restrict__ lcol,
+                     const float2* __restrict__ A, const float2* __restrict__ X, float2* __restrict__ Y, int R,
+                     int nchunk) {
+  extern __shared__ float4 smx4[];
+  float2* smx = reinterpret_cast<float2*>(smx4);
+  const int64_t b = blockIdx.x / nchunk;
+  const int ch = (int)(blockIdx.x - b * nchunk);
+  const int c0 = ch * kHaloCols;
+  const int ncol = min(kHaloCols, R - c0);       // even: R is even and c0 a multiple of 16
+  const int64_t h0 = blk_halo[b], H = blk_halo[b + 1] - h0;
+  const int part = threadIdx.x & 7;
+  if (2 * part < ncol)
+    for (int64_t i = threadIdx.x >> 3; i < H; i += kHaloThreads / 8)
+      cp_async16(smx + i * kHaloCols + 2 * part, X + (int64_t)halo[h0 + i] * R + c0 + 2 * part);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  const int lane = threadIdx.x & 31, half = lane >> 4, col = lane & 15;
+  const int warp = threadIdx.x >> 5;
+  const int64_t r0 = blk_row[b], r1 = blk_row[b + 1];
+  for (int64_t base = r0 + 2 * warp; base < r1; base += 2 * (kHaloThreads / 32)) {
+    const int64_t i = base + half;
+    const bool valid = i < r1;
+    const int64_t k0 = valid ? rptr[i] : 0;
+    const int n = valid ? (int)(rptr[i + 1] - k0) : 0;
+    const int nmax = max(n, __shfl_xor_sync(0xffffffffu, n, 16));
+    float2 acc = make_float2(0.f, 0.f);
+    for (int kb = 0; kb < nmax; kb += 16) {
+      float2 v = make_float2(0.f, 0.f);
+      int c = 0;
+      if (kb + col < n) {
+        v = A[k0 + kb + col];
+        c = lcol[k0 + kb + col];
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float vx = __shfl_sync(0xffffffffu, v.x, j, 16);
+        const float vy = __shfl_sync(0xffffffffu, v.y, j, 16);
+        const int cj = __shfl_sync(0xffffffffu, c, j, 16);
+        if (kb + j < n) cmac(acc, make_float2(vx, vy), smx[cj * kHaloCols + col]);
+      }
+    }
+    if (valid && col < ncol) Y[(int64_t)rows[i] * R + c0 + col] = acc;
+  }
+}
+
+// out[q] = in[src[q]]: the FP32 values in the plan's blocked order.
+__global__ void gather_f2_kernel(const float2* __restrict__ in, const int32_t* __restrict__ src, int64_t n,
+                                 float2* __restrict__ out) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    out[q] = in[src[q]];
+}
+
 }  // namespace
 
 void spmm_f64(const int64_t* rp, const int32_t* ci, const double2* A, const double2* X, double2* Y, int64_t E, int R,
@@ -148,6 +221,26 @@ void spmm_f64(const int64_t* rp, const int32_t* ci, const double2* A, const doub
 void spmm_f32(const int64_t* rp, const int32_t* ci, const float2* A, const float2* X, float2* Y, int64_t E, int R,
               cudaStream_t s, int threads) {
   spmm_launch<float2>(rp, ci, A, X, Y, E, R, s, threads);
+}
+
+bool spmm_halo_f32(const SpmmDev& p, const float2* A, const float2* X, float2* Y, int R, cudaStream_t s) {
+  if (!p.n_block || R < 2 || R > 128 || (R & 1) || ((uintptr_t)X & 15)) return false;
+  const size_t smem = (size_t)p.halo_max * kHaloCols * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(spmm_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const int nchunk = (R + kHaloCols - 1) / kHaloCols;
+  note_launch(1);
+  spmm_halo_kernel<<<(unsigned)(p.n_block * nchunk), kHaloThreads, smem, s>>>(p.blk_row, p.blk_halo, p.halo, p.rows,
+                                                                           p.rptr, p.lcol, A, X, Y, R, nchunk);
+  return true;
+}
+
+void spmm_plan_values(const SpmmDev& p, const float2* A32, int64_t nnz, float2* out, cudaStream_t s) {
+  note_launch(1);
+  gather_f2_kernel<<<152 * 8, 256, 0, s>>>(A32, p.src, nnz, out);
 }
 
 int residual_f64(const int64_t* rp, const int32_t* ci, const double2* A, const double2* X, const double2* B,

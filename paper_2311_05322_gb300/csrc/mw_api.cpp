@@ -41,6 +41,11 @@ void normalize_start_f32(const double2* r, const double* rnorm, const int32_t* d
 namespace mwimpl {
 
 constexpr int kMaxRestart = 63;
+// Halo bound of the SpMM plan's blocks: 864 rows x 16 complex64 columns = 108 KB of shared
+// memory per CTA, two CTAs per SM.
+constexpr int kSpmmHaloMax = 864;
+// Launch-shape value (mw_launch_shapes.spmm_threads) that selects the halo-tiled SpMM.
+constexpr int kSpmmHaloShape = 1;
 constexpr int kDotParts = mwk::kCgsDotsMaxParts;
 
 // Distance between consecutive Krylov vectors, in complex elements: E * R rounded up to 32, so
@@ -231,6 +236,8 @@ struct Ctx {
   double* d_eps = nullptr;
   std::vector<double2*> A64;
   std::vector<float2*> A32;
+  std::vector<float2*> A32b;       // FP32 values in the SpMM plan's blocked order
+  mwk::SpmmDev spmm;               // halo-tiled SpMM plan (device copy)
   std::vector<float4*> Adf;    // double-float copy of A64 for the mixed solver's residual
 
   int n_src = 0;
@@ -1002,6 +1009,19 @@ struct CycleArgs {
 
 // Arnoldi step j as segments (preconditioner apply, SpMM, Gram-Schmidt dots, Gram-Schmidt
 // update, Givens and scaling); seg(cls, bytes, fn) runs fn, which launches on c->stream.
+// FP32 SpMM of frequency f: the halo-tiled kernel for launch shape kSpmmHaloShape (when the
+// shape allows it), else the row-per-warp kernel with `threads` per block.  Both sum every row
+// in the same order, so the choice never changes a result bit.
+bool spmm_halo_ok(Ctx* c, int R) {
+  return c->spmm.n_block > 0 && R >= 2 && R <= 128 && R % 2 == 0 && (int)c->A32b.size() == c->n_freq;
+}
+void spmm32(Ctx* c, int f, const float2* X, float2* Y, int R, int threads) {
+  if (threads == kSpmmHaloShape && spmm_halo_ok(c, R) && mwk::spmm_halo_f32(c->spmm, c->A32b[f], X, Y, R, c->stream))
+    return;
+  mwk::spmm_f32(c->d_row, c->d_col, c->A32[f], X, Y, c->topo.n_edge, R, c->stream,
+                threads == kSpmmHaloShape ? 256 : threads);
+}
+
 template <class Seg>
 void arnoldi_step(Ctx* c, const CycleArgs& a, int j, Seg&& seg) {
   Work& w = c->work;
@@ -1017,8 +1037,7 @@ void arnoldi_step(Ctx* c, const CycleArgs& a, int j, Seg&& seg) {
       mwk::spmm_f64(c->d_row, c->d_col, c->A64[a.f], (const double2*)a.Zp(w, j), (double2*)a.Vp(w, j + 1), E, R,
                     c->stream, a.t.sh.spmm_threads);
     else
-      mwk::spmm_f32(c->d_row, c->d_col, c->A32[a.f], (const float2*)a.Zp(w, j), (float2*)a.Vp(w, j + 1), E, R,
-                    c->stream, a.t.sh.spmm_threads);
+      spmm32(c, a.f, (const float2*)a.Zp(w, j), (float2*)a.Vp(w, j + 1), R, a.t.sh.spmm_threads);
   });
   seg(MW_K_CGS_DOTS, (double)a.es * E * R * (j + 2), [&] {
     const int np = a.wp == 0 ? mwk::cgs_dots_f64((const double2*)w.V, a.vstride, j + 1,
@@ -1295,14 +1314,14 @@ Tuned autotune(Ctx* c, int R, int wp, int m, bool use_p) {
       }
     return best;
   };
-  for (int th : {128, 256, 512}) {
+  for (int th : {kSpmmHaloShape, 128, 256, 512}) {
+    if (th == kSpmmHaloShape && !(wp == 1 && spmm_halo_ok(c, R))) continue;
     const double ms = time_launch(c, [&] {
       if (wp == 0)
         mwk::spmm_f64(c->d_row, c->d_col, c->A64[0], (const double2*)Vp(0), (double2*)Vp(out), E, R, c->stream,
                       th);
       else
-        mwk::spmm_f32(c->d_row, c->d_col, c->A32[0], (const float2*)Vp(0), (float2*)Vp(out), E, R, c->stream,
-                      th);
+        spmm32(c, 0, (const float2*)Vp(0), (float2*)Vp(out), R, th);
     });
     t.t[MW_TUNE_SPMM].push_back({th, ms});
   }
@@ -1678,6 +1697,7 @@ void reassemble_all(Ctx* c) {
                     c->d_bface_cls, c->d_zc ? c->d_zc + (size_t)f * nc : nullptr, c->d_nzmask, c->A64[f], c->A32[f],
                     c->stream);
     mwk::split_df(c->A64[f], c->Adf[f], nnz, c->stream);
+    if (c->A32b.size() == c->A32.size() && c->A32b[f]) mwk::spmm_plan_values(c->spmm, c->A32[f], nnz, c->A32b[f], c->stream);
   }
   check_launch("reassemble");
 }
@@ -1735,10 +1755,17 @@ void release_mesh(Ctx* c) {
   c->Bfwd.clear();
   for (auto p : c->A64) dfree(c, p);
   for (auto p : c->A32) dfree(c, p);
+  for (auto p : c->A32b) dfree(c, p);
   for (auto p : c->Adf) dfree(c, p);
   c->A64.clear();
   c->A32.clear();
+  c->A32b.clear();
   c->Adf.clear();
+  for (const void* q : {(const void*)c->spmm.blk_row, (const void*)c->spmm.blk_halo, (const void*)c->spmm.halo,
+                        (const void*)c->spmm.rows, (const void*)c->spmm.rptr, (const void*)c->spmm.lcol,
+                        (const void*)c->spmm.src})
+    dfree(c, const_cast<void*>(q));
+  c->spmm = mwk::SpmmDev();
   for (void* q : {(void*)c->d_xyz, (void*)c->d_tets, (void*)c->d_col, (void*)c->d_contrib, (void*)c->d_bface_vert,
                   (void*)c->d_tet_edge, (void*)c->d_tet_nb, (void*)c->d_sign, (void*)c->d_row, (void*)c->d_cptr,
                   (void*)c->d_KM, (void*)c->d_vol, (void*)c->d_Bf, (void*)c->d_tikw, (void*)c->d_eps,
@@ -1780,9 +1807,11 @@ void drop_assembly(Ctx* c) {
   release_prec(c);
   for (auto p : c->A64) dfree(c, p);
   for (auto p : c->A32) dfree(c, p);
+  for (auto p : c->A32b) dfree(c, p);
   for (auto p : c->Adf) dfree(c, p);
   c->A64.clear();
   c->A32.clear();
+  c->A32b.clear();
   c->Adf.clear();
   for (auto p : c->Xf) dfree(c, p);
   for (auto p : c->Lf) dfree(c, p);
@@ -1932,8 +1961,9 @@ mw_status mw_set_launch_shapes(mw_ctx* c, int32_t n_cols, int32_t mode, int32_t 
     for (int v : {q.dots_stages, q.update_stages})
       require(v == 0 || (v >= mwk::kCgsDotsMinStages && v <= mwk::kCgsDotsMaxStages), MW_EINVAL,
               "dots_stages and update_stages must be 0 or 2..6");
-    require(q.spmm_threads == 0 || q.spmm_threads == 128 || q.spmm_threads == 256 || q.spmm_threads == 512,
-            MW_EINVAL, "spmm_threads must be 0, 128, 256 or 512");
+    require(q.spmm_threads == 0 || q.spmm_threads == kSpmmHaloShape || q.spmm_threads == 128 ||
+                q.spmm_threads == 256 || q.spmm_threads == 512,
+            MW_EINVAL, "spmm_threads must be 0, 1, 128, 256 or 512");
     const int wp = mode == MW_MODE_FP64 ? 0 : 1;
     Tuned t;
     t.R = n_cols;
@@ -2008,6 +2038,19 @@ mw_status mw_set_mesh(mw_ctx* c, int64_t n_vert, const double* xyz, int64_t n_te
     c->d_contrib = upload(c, t.contrib.data(), t.contrib.size());
     c->d_bface_vert = upload(c, t.bface_vert.data(), t.bface_vert.size());
     c->d_tet_nb = upload(c, t.tet_nb.data(), t.tet_nb.size());
+    {
+      mw::SpmmPlan sp;
+      if (!mw::build_spmm_plan(t, xyz, kSpmmHaloMax, sp, err)) throw Fail{err.code, err.msg};
+      c->spmm.n_block = sp.n_block;
+      c->spmm.halo_max = kSpmmHaloMax;
+      c->spmm.blk_row = upload(c, sp.blk_row.data(), sp.blk_row.size());
+      c->spmm.blk_halo = upload(c, sp.blk_halo.data(), sp.blk_halo.size());
+      c->spmm.halo = upload(c, sp.halo.data(), sp.halo.size());
+      c->spmm.rows = upload(c, sp.rows.data(), sp.rows.size());
+      c->spmm.rptr = upload(c, sp.rptr.data(), sp.rptr.size());
+      c->spmm.lcol = upload(c, sp.lcol.data(), sp.lcol.size());
+      c->spmm.src = upload(c, sp.src.data(), sp.src.size());
+    }
     c->d_KM = dalloc<double>(c, 42 * n_tet);
     c->d_vol = dalloc<double>(c, n_tet);
     c->d_Bf = dalloc<double>(c, 6 * std::max<int64_t>(t.n_bface, 1));
@@ -2068,13 +2111,16 @@ mw_status mw_assemble(mw_ctx* c, int32_t n_freq, const double* freq_hz, const do
     if (n_freq != c->n_freq) {
       for (auto p : c->A64) dfree(c, p);
       for (auto p : c->A32) dfree(c, p);
+      for (auto p : c->A32b) dfree(c, p);
       for (auto p : c->Adf) dfree(c, p);
       c->A64.assign(n_freq, nullptr);
       c->A32.assign(n_freq, nullptr);
+      c->A32b.assign(n_freq, nullptr);
       c->Adf.assign(n_freq, nullptr);
       for (int f = 0; f < n_freq; ++f) {
         c->A64[f] = dalloc<double2>(c, nnz);
         c->A32[f] = dalloc<float2>(c, nnz);
+        c->A32b[f] = dalloc<float2>(c, nnz);
         c->Adf[f] = dalloc<float4>(c, nnz);
       }
       for (auto p : c->Xf) dfree(c, p);
@@ -2110,6 +2156,12 @@ mw_status mw_apply_matrix(mw_ctx* c, int32_t f, int32_t prec, const void* x, voi
       mwk::spmm_f64(c->d_row, c->d_col, c->A64[f], (const double2*)x, (double2*)y, c->topo.n_edge, n_cols, c->stream);
     else if (prec == MW_PREC_FP32)
       mwk::spmm_f32(c->d_row, c->d_col, c->A32[f], (const float2*)x, (float2*)y, c->topo.n_edge, n_cols, c->stream);
+    else if (prec == 4) {
+      require(spmm_halo_ok(c, n_cols) && ((uintptr_t)x & 15) == 0, MW_EINVAL,
+              "the halo-tiled SpMM takes an even column count up to 128 and a 16-byte aligned x");
+      require(mwk::spmm_halo_f32(c->spmm, c->A32b[f], (const float2*)x, (float2*)y, n_cols, c->stream), MW_EINVAL,
+              "halo-tiled SpMM: unsupported shape");
+    }
     else if (prec == 3) {
       const int64_t n = c->topo.n_edge * (int64_t)n_cols;
       float4* xd = dalloc<float4>(c, n);
@@ -3106,6 +3158,53 @@ mw_status mw_apply_preconditioner_noalloc(mw_ctx* c, int32_t f, const void* r, v
 // Learned initialiser (BASELINE config 5): MLP + transposed-convolution decoder
 // =======================================================================================
 static constexpr int kHid = 1024, kG = 32, kOut = 2 * kG * kG * kG;
+
+mw_status mw_spmm_plan_stats(int64_t n_vert, const double* xyz, int64_t n_tet, const int32_t* tet_vert, int32_t halo_max,
+                             int64_t* stats) {
+  if (!xyz || !tet_vert || !stats) return MW_EINVAL;
+  try {
+    mw::Topology t;
+    Error err{MW_OK, ""};
+    if (!mw::build_topology(n_vert, n_tet, tet_vert, t, err)) return err.code;
+    mw::SpmmPlan p;
+    if (!mw::build_spmm_plan(t, xyz, halo_max, p, err)) return err.code;
+    const int64_t E = t.n_edge;
+    // every row exactly once; blocks cover the rows in order
+    std::vector<int32_t> seen(E, 0);
+    for (int32_t r : p.rows) {
+      if (r < 0 || r >= E || seen[r]++) return MW_ECUDA;
+    }
+    if ((int64_t)p.rows.size() != E || p.blk_row.front() != 0 || p.blk_row.back() != E) return MW_ECUDA;
+    if ((int64_t)p.rptr.size() != E + 1 || p.rptr.back() != t.nnz || (int64_t)p.lcol.size() != t.nnz) return MW_ECUDA;
+    std::vector<int32_t> hit(t.nnz, 0);
+    int64_t halo_sum = 0, halo_big = 0;
+    for (int64_t b = 0; b < p.n_block; ++b) {
+      const int64_t h0 = p.blk_halo[b], H = p.blk_halo[b + 1] - h0;
+      if (H < 1 || H > halo_max || p.blk_row[b + 1] <= p.blk_row[b]) return MW_ECUDA;
+      for (int64_t j = h0 + 1; j < h0 + H; ++j)
+        if (p.halo[j] <= p.halo[j - 1]) return MW_ECUDA;      // ascending, no repeats
+      halo_sum += H;
+      halo_big = std::max(halo_big, H);
+      for (int64_t i = p.blk_row[b]; i < p.blk_row[b + 1]; ++i) {
+        const int32_t r = p.rows[i];
+        if (p.rptr[i + 1] - p.rptr[i] != t.row_ptr[r + 1] - t.row_ptr[r]) return MW_ECUDA;
+        for (int64_t q = p.rptr[i]; q < p.rptr[i + 1]; ++q) {
+          const int64_t k = p.src[q];
+          // the canonical nonzero of the same row, in the same (ascending column) order
+          if (k != t.row_ptr[r] + (q - p.rptr[i]) || hit[k]++) return MW_ECUDA;
+          if (p.lcol[q] >= H || p.halo[h0 + p.lcol[q]] != t.col_idx[k]) return MW_ECUDA;
+        }
+      }
+    }
+    stats[0] = p.n_block;
+    stats[1] = halo_sum;
+    stats[2] = halo_big;
+    stats[3] = t.nnz;
+    return MW_OK;
+  } catch (const std::bad_alloc&) {
+    return MW_ENOMEM;
+  }
+}
 
 mw_status mw_sparse_plan_stats(int64_t n_vert, const double* xyz, int64_t n_tet, const int32_t* tet_vert, int32_t n_sub,
                                const int32_t* part, int32_t overlap, int32_t leaf, int64_t* stats) {

@@ -55,6 +55,22 @@ struct Topology {
 // Builds the topology; returns false and fills err on a bad mesh.
 bool build_topology(int64_t n_vert, int64_t n_tet, const int32_t* tet_vert, Topology& topo, Error& err);
 
+// Blocked layout of the SpMM for the halo-tiled kernel: rows in the Morton order of their edge
+// midpoints, cut greedily into blocks whose column sets (halos) hold at most halo_max edges, so
+// one block's rows of X fit in shared memory.  Each row keeps its nonzeros in the canonical
+// (ascending column) order, so a row's sum runs in the same order as with the canonical CSR.
+struct SpmmPlan {
+  int64_t n_block = 0;
+  std::vector<int64_t> blk_row;    // [n_block+1] offsets into rows
+  std::vector<int64_t> blk_halo;   // [n_block+1] offsets into halo
+  std::vector<int32_t> halo;       // per block, ascending global columns
+  std::vector<int32_t> rows;       // [E] global row of each blocked row
+  std::vector<int64_t> rptr;       // [E+1] offsets of each blocked row's nonzeros
+  std::vector<uint16_t> lcol;      // [nnz] halo-local column of each blocked nonzero
+  std::vector<int32_t> src;        // [nnz] canonical position of each blocked nonzero
+};
+bool build_spmm_plan(const Topology& topo, const double* xyz, int halo_max, SpmmPlan& plan, Error& err);
+
 // Subdomains of the overlapping Schwarz preconditioner (host side).
 struct Subdomains {
   int32_t n_sub = 0;
@@ -150,6 +166,24 @@ void spmm_f64(const int64_t* rp, const int32_t* ci, const double2* A, const doub
               int R, cudaStream_t s, int threads = 256);
 void spmm_f32(const int64_t* rp, const int32_t* ci, const float2* A, const float2* X, float2* Y, int64_t E, int R,
               cudaStream_t s, int threads = 256);
+// Device copy of mw::SpmmPlan (halo_max bounds every block's halo).
+struct SpmmDev {
+  int64_t n_block = 0;
+  int halo_max = 0;
+  const int64_t* blk_row = nullptr;
+  const int64_t* blk_halo = nullptr;
+  const int32_t* halo = nullptr;
+  const int32_t* rows = nullptr;
+  const int64_t* rptr = nullptr;
+  const uint16_t* lcol = nullptr;
+  const int32_t* src = nullptr;
+};
+// Y = A X with the halo-tiled kernel; A_blk holds the FP32 values in the plan's blocked order.
+// Returns false (nothing launched) when the shape is not supported: R odd or above 128, or X
+// not 16-byte aligned.  Bit-identical to spmm_f32.
+bool spmm_halo_f32(const SpmmDev& p, const float2* A_blk, const float2* X, float2* Y, int R, cudaStream_t s);
+// A_blk[q] = A32[src[q]].
+void spmm_plan_values(const SpmmDev& p, const float2* A32, int64_t nnz, float2* A_blk, cudaStream_t s);
 // Split complex FP64 values into double-float (re_hi, re_lo, im_hi, im_lo).
 void split_df(const double2* a, float4* o, int64_t n, cudaStream_t s);
 // r = b - A x (y = A x when B is null) in double-float arithmetic on the FP32 pipes, with

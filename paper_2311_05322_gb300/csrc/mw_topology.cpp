@@ -343,4 +343,105 @@ bool build_subdomains(const Topology& t, int32_t n_sub, const int32_t* part, int
   return true;
 }
 
+namespace {
+// Interleaves the low 21 bits of x, y, z (x in the lowest position).
+uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  auto spread = [](uint64_t v) {
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+  };
+  return spread(x) | (spread(y) << 1) | (spread(z) << 2);
+}
+}  // namespace
+
+bool build_spmm_plan(const Topology& t, const double* xyz, int halo_max, SpmmPlan& p, Error& err) {
+  const int64_t E = t.n_edge;
+  if (halo_max < 64 || halo_max > 65535) {
+    err = {MW_EINVAL, "halo_max out of range"};
+    return false;
+  }
+  // Morton keys of the edge midpoints on the bounding box
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t v = 0; v < t.n_vert; ++v)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], xyz[3 * v + d]);
+      hi[d] = std::max(hi[d], xyz[3 * v + d]);
+    }
+  std::vector<uint64_t> key(E);
+  for (int64_t e = 0; e < E; ++e) {
+    uint32_t q[3];
+    for (int d = 0; d < 3; ++d) {
+      const double m = 0.5 * (xyz[3 * (int64_t)t.edge_vert[2 * e] + d] + xyz[3 * (int64_t)t.edge_vert[2 * e + 1] + d]);
+      const double u = hi[d] > lo[d] ? (m - lo[d]) / (hi[d] - lo[d]) : 0.0;
+      q[d] = (uint32_t)std::min(2097151.0, std::max(0.0, u * 2097151.0));
+    }
+    key[e] = morton3(q[0], q[1], q[2]);
+  }
+  std::vector<int32_t> order(E);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  // greedy blocks along that order
+  p = SpmmPlan();
+  p.rows = order;
+  p.blk_row.push_back(0);
+  std::vector<int64_t> stamp(E, -1);
+  int64_t blk = 0, cnt = 0, nrow = 0;
+  for (int64_t i = 0; i < E; ++i) {
+    const int32_t r = order[i];
+    int64_t fresh = 0;
+    for (int64_t k = t.row_ptr[r]; k < t.row_ptr[r + 1]; ++k) fresh += stamp[t.col_idx[k]] != blk;
+    if (nrow > 0 && cnt + fresh > halo_max) {
+      p.blk_row.push_back(i);
+      ++blk;
+      cnt = 0;
+      nrow = 0;
+      fresh = t.row_ptr[r + 1] - t.row_ptr[r];
+    }
+    for (int64_t k = t.row_ptr[r]; k < t.row_ptr[r + 1]; ++k) stamp[t.col_idx[k]] = blk;
+    cnt += fresh;
+    ++nrow;
+  }
+  p.blk_row.push_back(E);
+  p.n_block = (int64_t)p.blk_row.size() - 1;
+  // halos (ascending), local columns and the value map
+  std::vector<int32_t> loc(E, -1);
+  p.blk_halo.assign(1, 0);
+  p.rptr.assign(1, 0);
+  p.lcol.reserve(t.nnz);
+  p.src.reserve(t.nnz);
+  for (int64_t b = 0; b < p.n_block; ++b) {
+    const size_t h0 = p.halo.size();
+    for (int64_t i = p.blk_row[b]; i < p.blk_row[b + 1]; ++i) {
+      const int32_t r = p.rows[i];
+      for (int64_t k = t.row_ptr[r]; k < t.row_ptr[r + 1]; ++k)
+        if (loc[t.col_idx[k]] < 0) {
+          loc[t.col_idx[k]] = 0;
+          p.halo.push_back(t.col_idx[k]);
+        }
+    }
+    std::sort(p.halo.begin() + h0, p.halo.end());
+    if (p.halo.size() - h0 > (size_t)halo_max) {
+      err = {MW_ECUDA, "SpMM plan: a block's halo exceeds its bound"};
+      return false;
+    }
+    for (size_t j = h0; j < p.halo.size(); ++j) loc[p.halo[j]] = (int32_t)(j - h0);
+    for (int64_t i = p.blk_row[b]; i < p.blk_row[b + 1]; ++i) {
+      const int32_t r = p.rows[i];
+      for (int64_t k = t.row_ptr[r]; k < t.row_ptr[r + 1]; ++k) {
+        p.lcol.push_back((uint16_t)loc[t.col_idx[k]]);
+        p.src.push_back((int32_t)k);
+      }
+      p.rptr.push_back((int64_t)p.lcol.size());
+    }
+    for (size_t j = h0; j < p.halo.size(); ++j) loc[p.halo[j]] = -1;
+    p.blk_halo.push_back((int64_t)p.halo.size());
+  }
+  return true;
+}
+
 }  // namespace mw

@@ -122,6 +122,7 @@ _SIGS = {
     "mw_selftest_bounded_wait": (C.c_int32, [_P, C.c_int64, C.POINTER(C.c_int32)]),
     "mw_nn_param_count": (C.c_int64, [C.c_int32]),
     "mw_sparse_plan_stats": (C.c_int32, [C.c_int64, _P, C.c_int64, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P]),
+    "mw_spmm_plan_stats": (C.c_int32, [C.c_int64, _P, C.c_int64, _P, C.c_int32, _P]),
     "mw_nn_init": (C.c_int32, [_P, C.c_int32, _P]),
     "mw_nn_get_params": (C.c_int32, [_P, _P]),
     "mw_nn_loss_grad": (C.c_int32, [_P, C.c_int64, _P, _P, C.POINTER(C.c_double), _P]),
@@ -480,6 +481,18 @@ class Context:
         k = hist.iterations
         return eps, {"iterations": k, "evaluations": hist.evaluations, "J": Jh[:k + 1].copy(),
                      "seconds": th[:k + 1].copy()}
+
+
+def spmm_plan_stats(xyz, tets, halo_max: int = 864) -> dict:
+    """Host-only check and statistics of the halo-tiled SpMM plan (mw_spmm_plan_stats)."""
+    lib = load_library()
+    xyz = _c(xyz, np.float64)
+    tets = _c(tets, np.int32)
+    out = np.zeros(4, np.int64)
+    st = lib.mw_spmm_plan_stats(xyz.shape[0], _ptr(xyz), tets.shape[0], _ptr(tets), halo_max, _ptr(out))
+    if st != MW_OK:
+        raise MWError(st, "SpMM plan check failed")
+    return dict(zip(("blocks", "halo_total", "halo_max", "nnz"), (int(v) for v in out)))
 
 
 def sparse_plan_stats(xyz, tets, n_sub: int, tet_part, overlap: int, leaf: int = 256) -> dict:

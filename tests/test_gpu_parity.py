@@ -109,6 +109,38 @@ def test_spmm(ragged, ncols):
     y32 = torch.empty_like(x32)
     c.apply_matrix(0, mw.MW_PREC_FP32, x32, y32, ncols)
     assert _relerr(y32.cpu().numpy().astype(np.complex128), ref) <= 2e-6
+    if ncols % 2 == 0:
+        # the halo-tiled kernel sums every row in the same order: bit-identical to the above
+        yh = torch.full_like(x32, float("nan"))
+        c.apply_matrix(0, 4, x32, yh, ncols)
+        assert torch.equal(yh, y32)
+
+
+@pytest.mark.parametrize("cells,ncols", [((7, 6, 5), 2), ((7, 6, 5), 18), ((9, 8, 7), 32), ((9, 8, 7), 48),
+                                         ((12, 9, 7), 64), ((6, 5, 4), 128)])
+def test_spmm_halo_tiled(cells, ncols):
+    """The halo-tiled FP32 SpMM against the oracle's FP64 product (2e-6, as the FP32 SpMM) and
+    bit for bit against the row-per-warp FP32 kernel; column counts that leave a partial 16-column
+    chunk, several blocks per mesh."""
+    mw = _mw()
+    m = kuhn_mesh(*cells, lo=(-0.03, -0.025, -0.02), hi=(0.03, 0.025, 0.02))
+    rng = np.random.default_rng(ncols + cells[0])
+    eps = EPS_MATCHING + rng.uniform(-6, 6, m.n_tet) + 1j * rng.uniform(-4, 4, m.n_tet)
+    sysm = asm.build_system(m.xyz, m.tets)
+    st = mw.spmm_plan_stats(m.xyz, m.tets, 864)
+    c = _ctx(m, eps, [1.1e9])
+    E = sysm.topo.n_edge
+    X = (rng.normal(size=(E, ncols)) + 1j * rng.normal(size=(E, ncols))).astype(np.complex64)
+    ref = sysm.csr(asm.assemble(sysm, eps, 1.1e9, EPS_MATCHING)) @ X.astype(np.complex128)
+    x32 = torch.from_numpy(X).cuda()
+    y32 = torch.empty_like(x32)
+    c.apply_matrix(0, mw.MW_PREC_FP32, x32, y32, ncols)
+    yh = torch.full_like(x32, float("nan"))
+    c.apply_matrix(0, 4, x32, yh, ncols)
+    assert torch.equal(yh, y32), st
+    assert _relerr(yh.cpu().numpy().astype(np.complex128), ref) <= 2e-6
+    with pytest.raises(mw.MWError):
+        c.apply_matrix(0, 4, x32[:, :ncols - 1].contiguous(), yh[:, :ncols - 1].contiguous(), ncols - 1)
 
 
 def test_sources_bit_exact(ragged):

@@ -73,7 +73,7 @@ def test_launch_shapes_bit_identical(box):
     st_ref = c.solve_rhs(32, bd, x_ref, opts)
     assert st_ref["n_converged"] == 32
     c.set_autotune(True)
-    for tc, dots, upd, spmm in [(2, 2, 6, 128), (tc_max, 6, 2, 512), (3, 5, 3, 256)]:
+    for tc, dots, upd, spmm in [(2, 2, 6, 128), (tc_max, 6, 2, 512), (3, 5, 3, 256), (4, 4, 4, 1)]:
         c.set_launch_shapes(32, mw.MW_MODE_MIXED, 50, tc, dots, upd, spmm)
         x = torch.empty_like(bd)
         st = c.solve_rhs(32, bd, x, opts)
