@@ -9,8 +9,10 @@ per-tet adjoint gradient and Tikhonov term.  RHS-solves per step = 2 x transmitt
          library's stream around K steps).
   e2e    the public host-buffer API (mw_assemble + mw_gradient): eps and S in from pinned host
          memory, gradient and cost back to the host, inside the timed region.
-Under torchrun each rank runs its own independent evaluation (weak scaling, no collective on
-the data path); rank 0 prints one JSON line.  `--impl reference` times the CPU oracle instead.
+Under torchrun (N > 1) the ranks split one evaluation by transmitter columns (strong scaling; an
+all-gather of S and an all-reduce of the gradient per evaluation, paper_2311_05322_gb300.sharded);
+`--replicas` runs independent evaluations per rank instead (weak scaling).  Rank 0 prints one
+JSON line.  `--impl reference` times the CPU oracle instead.
 """
 from __future__ import annotations
 
@@ -58,6 +60,8 @@ def _args(argv=None):
     ap.add_argument("--cpu-sample-subdomains", type=int, default=24)
     ap.add_argument("--cpu-cores", type=int, default=0, help="host processes of the oracle baseline (0 = all cores)")
     ap.add_argument("--no-legs", action="store_true", help="skip the config-3, training and time-to-misfit legs")
+    ap.add_argument("--replicas", action="store_true",
+                    help="N > 1: independent evaluations per rank instead of the column split of one evaluation")
     ap.add_argument("--inversion-leg", default="bench", choices=["none", "tiny", "bench", "test", "reduced"],
                     help="scale of the time-to-misfit leg of the default run")
     ap.add_argument("--study", default=None, choices=["tiny", "reduced"],
@@ -533,6 +537,84 @@ def config3_leg(a, local, stream, alu, hbm, src, steps=3, warmup=2):
             "clocks": clocks, "setup_s": L["setup"], "J_last": J}
 
 
+def run_sharded(a, world, rank, local):
+    """N > 1 (under torchrun, one process per GPU): one evaluation split by transmitter columns.
+    Every rank holds the mesh, matrices and preconditioner; rank r solves its window of the
+    columns (mw_forward_cols), the S columns are all-gathered over NCCL, each rank solves its
+    adjoints and forms its share of the gradient (mw_gradient_cols), one all-reduce sums the
+    shares, and the Tikhonov term is added once.  Strong scaling: the job's columns are fixed."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2311_05322_gb300 import mw
+    from paper_2311_05322_gb300.sharded import ColumnShardedEvaluation
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    hbm, _, _, src = peaks()
+    alu = measured_alu_peaks(torch.device("cuda", local))
+    L = _setup_leg(a, local, stream)
+    c, healthy, freqs, opts = L["c"], L["healthy"], L["freqs"], L["opts"]
+    drv = ColumnShardedEvaluation(dist, a.n_src, len(freqs), device=torch.device("cuda", local))
+    eps_h = torch.from_numpy(L["eps0"]).pin_memory().numpy()
+    S_obs, S_empty = L["S_obs"], L["S_empty"]
+    units = 2 * a.n_src * len(freqs)
+
+    def step():
+        c.assemble(freqs, eps_h, healthy.eps_bg)
+        return drv.evaluate(lambda j0, nl: c.forward_cols(j0, nl, opts),
+                            lambda S, So, Se: c.gradient_cols(S, So, Se, opts), S_obs, S_empty, a.alpha,
+                            lambda: c.tikhonov(eps_h))
+
+    c.profile_enable((1 << mw.MW_K_NCLASS) - 1)
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    c.profile_read()
+    dist.barrier()
+    l0 = mw.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(a.steps):
+            J, g, S = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    launches = mw.kernel_launches() - l0
+    prof = c.profile_read()
+    c.profile_enable(0)
+    value, sec = aggregate(units * a.steps, e0.elapsed_time(e1) * 1e-3, world, dist)
+    e2e_value, _ = aggregate(units * a.steps, wall, world, dist)
+    ms = sec * 1e3
+    roof, _ = _dominant_roofline(prof, ms, hbm, src, L["prec"], a, L)
+    roof["classes"] = rate_classes(prof, hbm, alu)
+    info = L["info"]
+    c.close()
+    if rank == 0:
+        nS = len(freqs) * a.n_src * a.n_src
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "c64+bf16 inner / c128 outer", "data": "synthetic",
+            "config": {"workload": f"shoulder phantom {a.cells} Kuhn cells ({info.n_edge} edges), {a.n_src} z-dipoles "
+                                   f"x {len(freqs)} frequencies, one inversion evaluation split by transmitter "
+                                   f"columns over {world} GPUs",
+                       "parallelism": f"transmitter columns over {world} ranks",
+                       "columns_per_rank": drv.nl, "rhs_solves_per_step": units, "subdomains": L["n_sub"],
+                       "exchanges": "all_gather of the S columns, all_reduce of the 2T gradient (NCCL)",
+                       "l2": "inputs larger than L2 (subdomain inverses and Krylov basis are GBs)"},
+            "roofline": roof, "cpu_baseline": None,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": L["eps0"].nbytes + 2 * 16 * nS,
+                    "d2h_bytes_per_step": 16 * info.n_tet + 8 + 16 * nS},
+            "gpu_launches": int(launches), "clocks": clk.summary(), "setup_s": L["setup"], "J_last": J,
+        }
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def run_mine(a):
     import torch
     import torch.distributed as dist
@@ -544,6 +626,8 @@ def run_mine(a):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         dist.init_process_group("nccl")
+        if not a.replicas:
+            return run_sharded(a, world, rank, local)
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     hbm, bf16, bf16s, src = peaks()

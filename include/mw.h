@@ -390,6 +390,26 @@ mw_status mw_nn_infer(mw_ctx* ctx, int64_t n, const float* x, float* y);
  * the order-4 barycentric lattice of the tet; deps [n_tet][2] (host). */
 mw_status mw_nn_grid_to_tets(mw_ctx* ctx, const float* grid, int32_t G, const double* box, double* deps);
 
+/* ---- column-sharded evaluation (one evaluation split over processes by transmitters) ---
+ * The transmitter columns of an evaluation are independent until the cost: process r solves
+ * its own window of columns (mw_forward_cols), the S columns of all windows are all-gathered
+ * by the caller (each process needs the whole S for the cost of Eq. sahar:2 and the adjoint
+ * weights), every process solves the adjoints of its own window and forms that window's part of
+ * the per-tet gradient (mw_gradient_cols), and the caller all-reduces (sums) the parts.  The
+ * sum equals mw_gradient's data gradient; the Tikhonov term (mw_tikhonov) is added once. */
+/* Forward solves of transmitters j0 .. j0+n_cols-1 (all assembled frequencies), kept for the
+ * next mw_gradient_cols; S_cols: host complex128 [n_freq][n_src][n_cols], the S-matrix columns
+ * of the window (Eq. s1: every receiver i, window column j).  1 <= n_cols <= 128, j0 + n_cols
+ * <= n_src.  Synchronises. */
+mw_status mw_forward_cols(mw_ctx* ctx, const mw_solve_opts* opts, int32_t j0, int32_t n_cols, double* S_cols);
+/* For the window of the last mw_forward_cols (same eps): J_out = the data cost of the whole
+ * S_full (host complex128 [n_freq][n_src][n_src], the gathered S), the adjoint solves of the
+ * window's columns with c_ij = w_ij conj(S_full_ij - S_obs_ij), and grad_part (host [n_tet][2])
+ * = that window's share of dJ/d(Re eps, Im eps).  MW_ESTATE without a prior window.
+ * Synchronises. */
+mw_status mw_gradient_cols(mw_ctx* ctx, const mw_solve_opts* opts, const double* S_full, const double* S_obs,
+                           const double* S_empty, double* J_out, double* grad_part);
+
 /* ---- device-resident variants (same operations, device pointers) ------------------- */
 /* mw_assemble with eps_r on the device ([n_tet][2] doubles); needs a prior mw_assemble with the
  * same number of frequencies (which sized the matrices). */

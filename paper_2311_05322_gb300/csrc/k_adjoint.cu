@@ -16,13 +16,13 @@ namespace {
 // One thread per (receiver i, transmitter j); the entries of q_i in list order.
 __global__ void s_project_kernel(const double2* __restrict__ X, const int64_t* __restrict__ ptr,
                                  const int32_t* __restrict__ edge, const double* __restrict__ w,
-                                 const double* __restrict__ nrm, int ns, double2* __restrict__ S) {
+                                 const double* __restrict__ nrm, int ns, int nl, double2* __restrict__ S) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ns * ns) return;
-  const int i = t / ns, j = t % ns;
+  if (t >= ns * nl) return;
+  const int i = t / nl, j = t % nl;
   double re = 0.0, im = 0.0;
   for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
-    const double2 x = X[(int64_t)edge[k] * ns + j];
+    const double2 x = X[(int64_t)edge[k] * nl + j];
     re += w[k] * x.x;
     im += w[k] * x.y;
   }
@@ -56,20 +56,21 @@ __global__ void adjoint_weights_kernel(const double2* __restrict__ S, const doub
 __global__ void adjoint_sources_kernel(const int64_t* __restrict__ tptr, const int32_t* __restrict__ tedge,
                                        const int32_t* __restrict__ tsrc, const int32_t* __restrict__ tk, int64_t nu,
                                        const double* __restrict__ w, const double* __restrict__ nrm,
-                                       const double2* __restrict__ C, int ns, double2* __restrict__ B) {
+                                       const double2* __restrict__ C, int ns, int j0, int nl,
+                                       double2* __restrict__ B) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nu * ns) return;
-  const int64_t u = t / ns;
-  const int j = (int)(t - u * ns);
+  if (t >= nu * nl) return;
+  const int64_t u = t / nl;
+  const int j = (int)(t - u * nl);
   double re = 0.0, im = 0.0;
   for (int64_t q = tptr[u]; q < tptr[u + 1]; ++q) {
     const int i = tsrc[q];
-    const double2 c = C[i * ns + j];
+    const double2 c = C[i * ns + j0 + j];
     const double s = w[tk[q]];
     re += (c.x / nrm[i]) * s;
     im += (c.y / nrm[i]) * s;
   }
-  B[(int64_t)tedge[u] * ns + j] = make_double2(re, im);
+  B[(int64_t)tedge[u] * nl + j] = make_double2(re, im);
 }
 
 // One warp per tet, lanes over the transmitter columns; the warp sums lambda_j^T M^T x_j
@@ -179,9 +180,10 @@ __global__ void count_active_kernel(const int32_t* done, int R, int32_t* active)
 }  // namespace
 
 void s_project(const double2* X, const int64_t* ptr, const int32_t* edge, const double* w, const double* nrm, int ns,
-               double2* S, cudaStream_t s) {
+               double2* S, cudaStream_t s, int nl) {
+  if (nl < 0) nl = ns;
   note_launch(1);
-  s_project_kernel<<<(ns * ns + 255) / 256, 256, 0, s>>>(X, ptr, edge, w, nrm, ns, S);
+  s_project_kernel<<<(ns * nl + 255) / 256, 256, 0, s>>>(X, ptr, edge, w, nrm, ns, nl, S);
 }
 void adjoint_weights(const double2* S, const double2* So, const double2* Se, int64_t n, double2* C, double* J,
                      cudaStream_t s) {
@@ -190,12 +192,14 @@ void adjoint_weights(const double2* S, const double2* So, const double2* Se, int
 }
 void adjoint_sources(const int64_t* tptr, const int32_t* tedge, const int32_t* tsrc, const int32_t* tk, int64_t nu,
                      const double* w, const double* nrm, const double2* C, int ns, double2* B, int64_t E,
-                     cudaStream_t s) {
+                     cudaStream_t s, int j0, int nl) {
+  if (nl < 0) nl = ns;
   note_launch(1);
-  cudaMemsetAsync(B, 0, sizeof(double2) * E * ns, s);
-  const int64_t n = nu * ns;
+  cudaMemsetAsync(B, 0, sizeof(double2) * E * nl, s);
+  const int64_t n = nu * nl;
   if (n > 0)
-    adjoint_sources_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tptr, tedge, tsrc, tk, nu, w, nrm, C, ns, B);
+    adjoint_sources_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tptr, tedge, tsrc, tk, nu, w, nrm, C, ns, j0,
+                                                                        nl, B);
 }
 void grad_tet(const int32_t* tet_edge, const double* KM, int64_t T, const double2* L, const double2* X, int ns,
               double k0sq, double* g, cudaStream_t s) {

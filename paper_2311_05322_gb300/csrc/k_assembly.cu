@@ -195,12 +195,13 @@ __global__ void reassemble_kernel(const int64_t* __restrict__ cptr, const int32_
 // within a source): one thread per source.  Dipoles: one entry w = +-1, c = -i omega mu0;
 // ports: the load vector w_j and c_j = 2 i beta_j (g = 2 i beta E^TE10, Eq. m2).
 __global__ void source_rhs_kernel(const int64_t* __restrict__ ptr, const int32_t* __restrict__ edge,
-                                  const double* __restrict__ w, const double2* __restrict__ coef, int ns,
+                                  const double* __restrict__ w, const double2* __restrict__ coef, int j0, int nl,
                                   double2* __restrict__ B) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= ns) return;
-  const double2 c = coef[j];
-  for (int64_t k = ptr[j]; k < ptr[j + 1]; ++k) B[(int64_t)edge[k] * ns + j] = make_double2(c.x * w[k], c.y * w[k]);
+  if (j >= nl) return;
+  const double2 c = coef[j0 + j];
+  for (int64_t k = ptr[j0 + j]; k < ptr[j0 + j + 1]; ++k)
+    B[(int64_t)edge[k] * nl + j] = make_double2(c.x * w[k], c.y * w[k]);
 }
 
 // Port face moments (Eq. m2 right-hand side and Eq. s1), one thread per port face F of port p:
@@ -335,10 +336,11 @@ void reassemble(const int64_t* cptr, const int32_t* contrib, int64_t nnz, const 
                                                           zc, nzmask, A64, A32);
 }
 void source_rhs(const int64_t* ptr, const int32_t* edge, const double* w, const double2* coef, int ns, double2* B,
-                int64_t E, cudaStream_t s) {
+                int64_t E, cudaStream_t s, int j0, int nl) {
+  if (nl < 0) nl = ns;
   note_launch(1);
-  cudaMemsetAsync(B, 0, sizeof(double2) * E * ns, s);
-  source_rhs_kernel<<<blocks_for(ns, 64), 64, 0, s>>>(ptr, edge, w, coef, ns, B);
+  cudaMemsetAsync(B, 0, sizeof(double2) * E * nl, s);
+  source_rhs_kernel<<<blocks_for(nl, 64), 64, 0, s>>>(ptr, edge, w, coef, j0, nl, B);
 }
 void port_face_moments(const double* xyz, const int32_t* fv, const int32_t* fport, int64_t F, const double* pdesc,
                        const double* gx, const double* gw, int nq, double* mom, double* nrm, cudaStream_t s) {

@@ -271,6 +271,12 @@ struct Ctx {
   std::vector<double2*> Xf;    // forward fields per frequency [E][n_src]
   std::vector<double2*> Lf;    // adjoint fields per frequency
   std::vector<double2*> Bfwd;  // forward right-hand sides per frequency
+  // transmitter window of the column-sharded evaluation (mw_forward_cols / mw_gradient_cols):
+  // fields, adjoint fields and right-hand sides per frequency [E][win_nl], S columns
+  // [n_freq][n_src][win_nl]
+  int win_j0 = 0, win_nl = 0, win_nf = 0, win_ns = 0;
+  std::vector<double2*> Xw, Lw, Bw, Bwa;
+  double2* d_Sp = nullptr;
   double2* d_B = nullptr;      // RHS scratch [E][n_src]
   double2 *d_S = nullptr, *d_C = nullptr, *d_So = nullptr, *d_Se = nullptr;
   double *d_J = nullptr, *d_grad = nullptr, *d_gR = nullptr;
@@ -1743,6 +1749,8 @@ void release_prec(Ctx* c) {
   c->tuned.clear();
 }
 
+void free_window(Ctx* c);
+
 void release_mesh(Ctx* c) {
   drop_graphs(c);
   release_prec(c);
@@ -1775,6 +1783,7 @@ void release_mesh(Ctx* c) {
     dfree(c, q);
   for (auto p : c->d_Badj) dfree(c, p);
   c->d_Badj.clear();
+  free_window(c);
   c->d_S = c->d_C = c->d_So = c->d_Se = nullptr;
   c->d_J = c->d_grad = c->d_gR = nullptr;
   c->d_xyz = nullptr;
@@ -1800,9 +1809,20 @@ void release_mesh(Ctx* c) {
   c->n_freq = 0;
 }
 
+void free_window(Ctx* c) {
+  for (auto* v : {&c->Xw, &c->Lw, &c->Bw, &c->Bwa}) {
+    for (auto p : *v) dfree(c, p);
+    v->clear();
+  }
+  dfree(c, c->d_Sp);
+  c->d_Sp = nullptr;
+  c->win_j0 = c->win_nl = c->win_nf = c->win_ns = 0;
+}
+
 // Drops the assembled matrices, the preconditioner and every stored field (the boundary
 // changed: assemble again).
 void drop_assembly(Ctx* c) {
+  free_window(c);
   drop_graphs(c);
   release_prec(c);
   for (auto p : c->A64) dfree(c, p);
@@ -2807,6 +2827,98 @@ static void gradient_dev_impl(Ctx* c, const mw_solve_opts& o, const double2* dSo
   CK(cudaMemcpyAsync(&J, c->d_J, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   *J_out = J;
+}
+
+// Column-sharded evaluation (one inversion evaluation split by transmitter columns over
+// processes): the forward solves and S columns of transmitters [j0, j0+nl).
+static void forward_cols_impl(Ctx* c, const mw_solve_opts& o, int j0, int nl, double* S_cols) {
+  require(c->has_mesh && c->n_freq > 0 && c->n_src > 0, MW_ESTATE, "assemble and set sources first");
+  require(j0 >= 0 && nl >= 1 && j0 + nl <= c->n_src && nl <= 128 && S_cols, MW_EINVAL, "bad column window");
+  const int64_t E = c->topo.n_edge;
+  const int ns = c->n_src, nf = c->n_freq;
+  if (c->win_nl != nl || c->win_nf != nf || c->win_ns != ns) {
+    free_window(c);
+    for (auto* v : {&c->Xw, &c->Lw, &c->Bw, &c->Bwa}) {
+      v->assign(nf, nullptr);
+      for (int f = 0; f < nf; ++f) (*v)[f] = dalloc<double2>(c, E * nl);
+    }
+    c->d_Sp = dalloc<double2>(c, (size_t)nf * ns * nl);
+    c->win_nl = nl;
+    c->win_nf = nf;
+    c->win_ns = ns;
+  }
+  c->win_j0 = j0;
+  upload_source_coefs(c);
+  std::vector<const double2*> Bs(nf);
+  for (int f = 0; f < nf; ++f) {
+    mwk::source_rhs(c->d_q_ptr, c->d_q_edge, c->d_q_w, c->d_src_coef + (size_t)f * ns, ns, c->Bw[f], E, c->stream,
+                    j0, nl);
+    Bs[f] = c->Bw[f];
+  }
+  check_launch("source rhs (window)");
+  solve_all(c, o, nl, Bs, c->Xw, nullptr);
+  for (int f = 0; f < nf; ++f)
+    mwk::s_project(c->Xw[f], c->d_q_ptr, c->d_q_edge, c->d_q_w, c->d_q_norm, ns, c->d_Sp + (size_t)f * ns * nl,
+                   c->stream, nl);
+  check_launch("S columns");
+  CK(cudaMemcpyAsync(S_cols, c->d_Sp, sizeof(double2) * nf * ns * nl, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+}
+
+// The rest of the sharded evaluation for the window of the last forward_cols: cost and adjoint
+// weights from the whole S, adjoint solves of the window's columns, and their part of the
+// per-tet gradient (no Tikhonov term).
+static void gradient_cols_impl(Ctx* c, const mw_solve_opts& o, const double* S_full, const double* S_obs,
+                               const double* S_empty, double* J_out, double* grad_part) {
+  require(c->win_nl > 0 && c->win_nf == c->n_freq && c->win_ns == c->n_src, MW_ESTATE,
+          "call mw_forward_cols first");
+  require(S_full && S_obs && S_empty && J_out && grad_part, MW_EINVAL, "null argument");
+  const int64_t E = c->topo.n_edge, T = c->topo.n_tet;
+  const int ns = c->n_src, nf = c->n_freq, j0 = c->win_j0, nl = c->win_nl;
+  const size_t nS = (size_t)nf * ns * ns;
+  if (!c->d_S) c->d_S = dalloc<double2>(c, 64 * 128 * 128);
+  if (!c->d_C) c->d_C = dalloc<double2>(c, 64 * 128 * 128);
+  if (!c->d_So) c->d_So = dalloc<double2>(c, 64 * 128 * 128);
+  if (!c->d_Se) c->d_Se = dalloc<double2>(c, 64 * 128 * 128);
+  if (!c->d_J) c->d_J = dalloc<double>(c, 4);
+  if (!c->d_grad) c->d_grad = dalloc<double>(c, 2 * T);
+  CK(cudaMemcpyAsync(c->d_S, S_full, sizeof(double2) * nS, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_So, S_obs, sizeof(double2) * nS, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_Se, S_empty, sizeof(double2) * nS, cudaMemcpyHostToDevice, c->stream));
+  mwk::adjoint_weights(c->d_S, c->d_So, c->d_Se, (int64_t)nS, c->d_C, c->d_J, c->stream);
+  std::vector<const double2*> Bc(nf);
+  for (int f = 0; f < nf; ++f) {
+    mwk::adjoint_sources(c->d_qt_ptr, c->d_qt_edge, c->d_qt_src, c->d_qt_k, c->n_qt, c->d_q_w, c->d_q_norm,
+                         c->d_C + (size_t)f * ns * ns, ns, c->Bwa[f], E, c->stream, j0, nl);
+    Bc[f] = c->Bwa[f];
+  }
+  check_launch("adjoint sources (window)");
+  solve_all(c, o, nl, Bc, c->Lw, nullptr);
+  CK(cudaMemsetAsync(c->d_grad, 0, sizeof(double) * 2 * T, c->stream));
+  for (int f = 0; f < nf; ++f) {
+    const double k0 = k0_of(c->freqs[f]);
+    ProfScope ps(c, MW_K_GRADIENT, 2.0 * 16 * E * nl + (21.0 * 8 + 24 + 32) * T, 192.0 * T * nl);
+    mwk::grad_tet(c->d_tet_edge, c->d_KM, T, c->Lw[f], c->Xw[f], nl, k0 * k0, c->d_grad, c->stream);
+  }
+  check_launch("gradient (window)");
+  CK(cudaMemcpyAsync(J_out, c->d_J, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(grad_part, c->d_grad, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+}
+
+mw_status mw_forward_cols(mw_ctx* c, const mw_solve_opts* opts, int32_t j0, int32_t n_cols, double* S_cols) {
+  return guard(c, [&] {
+    mw_solve_opts o = norm_opts(opts);
+    forward_cols_impl(c, o, j0, n_cols, S_cols);
+  });
+}
+
+mw_status mw_gradient_cols(mw_ctx* c, const mw_solve_opts* opts, const double* S_full, const double* S_obs,
+                           const double* S_empty, double* J_out, double* grad_part) {
+  return guard(c, [&] {
+    mw_solve_opts o = norm_opts(opts);
+    gradient_cols_impl(c, o, S_full, S_obs, S_empty, J_out, grad_part);
+  });
 }
 
 static void gradient_impl(Ctx* c, const mw_solve_opts& o, const double* S_obs, const double* S_empty, double alpha,

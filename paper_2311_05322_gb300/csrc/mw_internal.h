@@ -263,9 +263,10 @@ void transpose_in(const double2* src, double2* dst, int64_t E, int R, cudaStream
 void transpose_out(const double2* src, double2* dst, int64_t E, int R, cudaStream_t s);
 
 // sources
-// B [E][ns] = 0, then B[edge_k][j] = coef_j w_k for the entries k of source j (CSR ptr [ns+1]).
+// B [E][nl] = 0, then B[edge_k][j] = coef_{j0+j} w_k for the entries k of source j0 + j (CSR ptr
+// [ns+1]), j < nl (nl < 0: all ns sources, j0 = 0).
 void source_rhs(const int64_t* ptr, const int32_t* edge, const double* w, const double2* coef, int ns, double2* B,
-                int64_t E, cudaStream_t s);
+                int64_t E, cudaStream_t s, int j0 = 0, int nl = -1);
 // Port face moments: fv [F][3] sorted vertex ids, fport [F] port of each face, pdesc [P][10]
 // (origin, u, v, a); outputs mom [F][3] and nrm [F].
 void port_face_moments(const double* xyz, const int32_t* fv, const int32_t* fport, int64_t F, const double* pdesc,

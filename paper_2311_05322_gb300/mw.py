@@ -112,6 +112,8 @@ _SIGS = {
     "mw_lbfgs_destroy": (None, [_P]),
     "mw_invert": (C.c_int32, [_P, C.POINTER(mw_inv_opts), C.POINTER(mw_solve_opts), _P, _P, _P,
                               C.POINTER(mw_inv_history)]),
+    "mw_forward_cols": (C.c_int32, [_P, C.POINTER(mw_solve_opts), C.c_int32, C.c_int32, _P]),
+    "mw_gradient_cols": (C.c_int32, [_P, C.POINTER(mw_solve_opts), _P, _P, _P, C.POINTER(C.c_double), _P]),
     "mw_assemble_dev": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
     "mw_gradient_dev": (C.c_int32, [_P, C.POINTER(mw_solve_opts), _P, _P, C.c_double, C.POINTER(C.c_double), _P]),
     "mw_kernel_launches": (C.c_int64, []),
@@ -387,6 +389,24 @@ class Context:
         S = np.empty_like(So) if want_S else None
         self._check(self.lib.mw_gradient(self.h, C.byref(o), _ptr(So), _ptr(Se), alpha, C.byref(J), _ptr(g), _ptr(S)))
         return (J.value, g, S) if want_S else (J.value, g)
+
+    def forward_cols(self, j0: int, n_cols: int, opts: mw_solve_opts | None = None) -> np.ndarray:
+        """Forward solves of transmitters j0 .. j0+n_cols-1; returns their S columns
+        [n_freq][n_src][n_cols]."""
+        o = opts or solve_opts()
+        S = np.empty((self.n_freq, self.n_src, n_cols), np.complex128)
+        self._check(self.lib.mw_forward_cols(self.h, C.byref(o), j0, n_cols, _ptr(S)))
+        return S
+
+    def gradient_cols(self, S_full, S_obs, S_empty, opts: mw_solve_opts | None = None):
+        """Cost of the whole S and the last window's share of the data gradient [n_tet][2]."""
+        o = opts or solve_opts()
+        J = C.c_double()
+        g = np.empty((self.info.n_tet, 2))
+        self._check(self.lib.mw_gradient_cols(self.h, C.byref(o), _ptr(_c(S_full, np.complex128)),
+                                              _ptr(_c(S_obs, np.complex128)), _ptr(_c(S_empty, np.complex128)),
+                                              C.byref(J), _ptr(g)))
+        return J.value, g
 
     def tikhonov(self, eps_r):
         e = _c(eps_r, np.float64)
