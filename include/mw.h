@@ -260,7 +260,9 @@ mw_status mw_sparse_plan_stats(int64_t n_vert, const double* xyz, int64_t n_tet,
  * column sets hold at most halo_max edges) and verifies its invariants: every row once, blocks
  * in order, each block's halo ascending and within bound, each blocked nonzero mapped to the
  * canonical nonzero of its row in the same order, and every halo-local column naming that
- * nonzero's column.  stats[4] receives: blocks, summed halo sizes, largest halo, nonzeros.
+ * nonzero's column; with halo_max = 480 (the library's bound) also the library's block bounds of
+ * 512 rows and 4096 nonzeros.  stats[4] receives: blocks, summed halo sizes, largest halo,
+ * nonzeros.
  * MW_ECUDA reports a broken invariant; MW_EINVAL bad arguments (64 <= halo_max <= 65535). */
 mw_status mw_spmm_plan_stats(int64_t n_vert, const double* xyz, int64_t n_tet, const int32_t* tet_vert,
                              int32_t halo_max, int64_t* stats);

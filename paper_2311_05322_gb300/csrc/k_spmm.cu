@@ -140,16 +140,18 @@ void spmm_launch(const int64_t* rp, const int32_t* ci, const T* A, const T* X, T
 }
 
 // Halo-tiled FP32 SpMM.  One CTA takes one block of the SpMM plan (rows in Morton order whose
-// column set, the halo, holds at most halo_max edges) and one chunk of kHaloCols columns:
-//  1. the halo's rows of X (kHaloCols complex values each) are staged in shared memory by
-//     16-byte cp.async copies, 8 threads per row;
-//  2. each half-warp computes one row: its 16 lanes hold 16 columns; the row's nonzeros
-//     (value and halo-local column) are loaded 16 at a time, one per lane, and broadcast by
-//     shuffles; every product reads X from shared memory.
+// column set, the halo, holds at most kHaloMax edges; at most kHaloRows rows and kHaloNnz
+// nonzeros) and one chunk of kHaloCols columns.  Staging, all at the CTA's start:
+//  - the halo's rows of X (kHaloCols complex values each) by 16-byte cp.async copies, 8 threads
+//    per row;
+//  - the block's nonzero values, halo-local columns, row offsets and row ids by coalesced loads.
+// Then each half-warp computes one row from shared memory only: its 16 lanes hold 16 columns.
 // A row's terms are accumulated in the canonical column order with the same complex FMA
 // sequence as spmm_kernel, so both kernels give bit-identical results.
 constexpr int kHaloCols = 16;
 constexpr int kHaloThreads = 256;
+constexpr size_t kHaloSmem = (size_t)kHaloMax * kHaloCols * 8 + (size_t)kHaloNnz * 8 + (kHaloRows + 1) * 4 +
+                             (size_t)kHaloRows * 4 + (size_t)kHaloNnz * 2;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -162,46 +164,42 @@ __global__ void __launch_bounds__(kHaloThreads, 2)
                      const int64_t* __restrict__ rptr, const uint16_t* __restrict__ lcol,
                      const float2* __restrict__ A, const float2* __restrict__ X, float2* __restrict__ Y, int R,
                      int nchunk) {
-  extern __shared__ float4 smx4[];
-  float2* smx = reinterpret_cast<float2*>(smx4);
+  extern __shared__ float4 smem4[];
+  float2* sX = reinterpret_cast<float2*>(smem4);
+  float2* sA = sX + (size_t)kHaloMax * kHaloCols;
+  int32_t* sR = reinterpret_cast<int32_t*>(sA + kHaloNnz);   // local row offsets [nrow + 1]
+  int32_t* sG = sR + kHaloRows + 1;                            // global row ids [nrow]
+  uint16_t* sL = reinterpret_cast<uint16_t*>(sG + kHaloRows);  // halo-local columns [nnz]
   const int64_t b = blockIdx.x / nchunk;
   const int ch = (int)(blockIdx.x - b * nchunk);
   const int c0 = ch * kHaloCols;
   const int ncol = min(kHaloCols, R - c0);       // even: R is even and c0 a multiple of 16
   const int64_t h0 = blk_halo[b], H = blk_halo[b + 1] - h0;
+  const int64_t r0 = blk_row[b], nrow = blk_row[b + 1] - r0;
   const int part = threadIdx.x & 7;
   if (2 * part < ncol)
     for (int64_t i = threadIdx.x >> 3; i < H; i += kHaloThreads / 8)
-      cp_async16(smx + i * kHaloCols + 2 * part, X + (int64_t)halo[h0 + i] * R + c0 + 2 * part);
+      cp_async16(sX + i * kHaloCols + 2 * part, X + (int64_t)halo[h0 + i] * R + c0 + 2 * part);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
+  const int64_t k0 = rptr[r0], nnz = rptr[r0 + nrow] - k0;
+  for (int64_t q = threadIdx.x; q < nnz; q += kHaloThreads) {
+    sA[q] = A[k0 + q];
+    sL[q] = lcol[k0 + q];
+  }
+  for (int64_t i = threadIdx.x; i <= nrow; i += kHaloThreads) {
+    sR[i] = (int32_t)(rptr[r0 + i] - k0);
+    if (i < nrow) sG[i] = rows[r0 + i];
+  }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   const int lane = threadIdx.x & 31, half = lane >> 4, col = lane & 15;
   const int warp = threadIdx.x >> 5;
-  const int64_t r0 = blk_row[b], r1 = blk_row[b + 1];
-  for (int64_t base = r0 + 2 * warp; base < r1; base += 2 * (kHaloThreads / 32)) {
-    const int64_t i = base + half;
-    const bool valid = i < r1;
-    const int64_t k0 = valid ? rptr[i] : 0;
-    const int n = valid ? (int)(rptr[i + 1] - k0) : 0;
-    const int nmax = max(n, __shfl_xor_sync(0xffffffffu, n, 16));
+  for (int i = 2 * warp + half; i < (int)nrow; i += 2 * (kHaloThreads / 32)) {
     float2 acc = make_float2(0.f, 0.f);
-    for (int kb = 0; kb < nmax; kb += 16) {
-      float2 v = make_float2(0.f, 0.f);
-      int c = 0;
-      if (kb + col < n) {
-        v = A[k0 + kb + col];
-        c = lcol[k0 + kb + col];
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float vx = __shfl_sync(0xffffffffu, v.x, j, 16);
-        const float vy = __shfl_sync(0xffffffffu, v.y, j, 16);
-        const int cj = __shfl_sync(0xffffffffu, c, j, 16);
-        if (kb + j < n) cmac(acc, make_float2(vx, vy), smx[cj * kHaloCols + col]);
-      }
-    }
-    if (valid && col < ncol) Y[(int64_t)rows[i] * R + c0 + col] = acc;
+    const int kb = sR[i], ke = sR[i + 1];
+#pragma unroll 4
+    for (int k = kb; k < ke; ++k) cmac(acc, sA[k], sX[(int)sL[k] * kHaloCols + col]);
+    if (col < ncol) Y[(int64_t)sG[i] * R + c0 + col] = acc;
   }
 }
 
@@ -224,8 +222,8 @@ void spmm_f32(const int64_t* rp, const int32_t* ci, const float2* A, const float
 }
 
 bool spmm_halo_f32(const SpmmDev& p, const float2* A, const float2* X, float2* Y, int R, cudaStream_t s) {
-  if (!p.n_block || R < 2 || R > 128 || (R & 1) || ((uintptr_t)X & 15)) return false;
-  const size_t smem = (size_t)p.halo_max * kHaloCols * sizeof(float2);
+  if (!p.n_block || p.halo_max > kHaloMax || R < 2 || R > 128 || (R & 1) || ((uintptr_t)X & 15)) return false;
+  const size_t smem = kHaloSmem;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(spmm_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

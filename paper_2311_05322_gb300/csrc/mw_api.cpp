@@ -41,9 +41,7 @@ void normalize_start_f32(const double2* r, const double* rnorm, const int32_t* d
 namespace mwimpl {
 
 constexpr int kMaxRestart = 63;
-// Halo bound of the SpMM plan's blocks: 864 rows x 16 complex64 columns = 108 KB of shared
-// memory per CTA, two CTAs per SM.
-constexpr int kSpmmHaloMax = 864;
+
 // Launch-shape value (mw_launch_shapes.spmm_threads) that selects the halo-tiled SpMM.
 constexpr int kSpmmHaloShape = 1;
 constexpr int kDotParts = mwk::kCgsDotsMaxParts;
@@ -1024,8 +1022,7 @@ bool spmm_halo_ok(Ctx* c, int R) {
 void spmm32(Ctx* c, int f, const float2* X, float2* Y, int R, int threads) {
   if (threads == kSpmmHaloShape && spmm_halo_ok(c, R) && mwk::spmm_halo_f32(c->spmm, c->A32b[f], X, Y, R, c->stream))
     return;
-  mwk::spmm_f32(c->d_row, c->d_col, c->A32[f], X, Y, c->topo.n_edge, R, c->stream,
-                threads == kSpmmHaloShape ? 256 : threads);
+  mwk::spmm_f32(c->d_row, c->d_col, c->A32[f], X, Y, c->topo.n_edge, R, c->stream, threads < 128 ? 256 : threads);
 }
 
 template <class Seg>
@@ -2060,9 +2057,10 @@ mw_status mw_set_mesh(mw_ctx* c, int64_t n_vert, const double* xyz, int64_t n_te
     c->d_tet_nb = upload(c, t.tet_nb.data(), t.tet_nb.size());
     {
       mw::SpmmPlan sp;
-      if (!mw::build_spmm_plan(t, xyz, kSpmmHaloMax, sp, err)) throw Fail{err.code, err.msg};
+      if (!mw::build_spmm_plan(t, xyz, mwk::kHaloMax, sp, err, mwk::kHaloRows, mwk::kHaloNnz))
+        throw Fail{err.code, err.msg};
       c->spmm.n_block = sp.n_block;
-      c->spmm.halo_max = kSpmmHaloMax;
+      c->spmm.halo_max = mwk::kHaloMax;
       c->spmm.blk_row = upload(c, sp.blk_row.data(), sp.blk_row.size());
       c->spmm.blk_halo = upload(c, sp.blk_halo.data(), sp.blk_halo.size());
       c->spmm.halo = upload(c, sp.halo.data(), sp.halo.size());
@@ -3279,7 +3277,11 @@ mw_status mw_spmm_plan_stats(int64_t n_vert, const double* xyz, int64_t n_tet, c
     Error err{MW_OK, ""};
     if (!mw::build_topology(n_vert, n_tet, tet_vert, t, err)) return err.code;
     mw::SpmmPlan p;
-    if (!mw::build_spmm_plan(t, xyz, halo_max, p, err)) return err.code;
+    // the library's own bounds when halo_max is the library's halo bound
+    const bool lib = halo_max == mwk::kHaloMax;
+    if (!mw::build_spmm_plan(t, xyz, halo_max, p, err, lib ? mwk::kHaloRows : 1 << 30,
+                             lib ? (int64_t)mwk::kHaloNnz : INT64_MAX))
+      return err.code;
     const int64_t E = t.n_edge;
     // every row exactly once; blocks cover the rows in order
     std::vector<int32_t> seen(E, 0);
@@ -3293,6 +3295,9 @@ mw_status mw_spmm_plan_stats(int64_t n_vert, const double* xyz, int64_t n_tet, c
     for (int64_t b = 0; b < p.n_block; ++b) {
       const int64_t h0 = p.blk_halo[b], H = p.blk_halo[b + 1] - h0;
       if (H < 1 || H > halo_max || p.blk_row[b + 1] <= p.blk_row[b]) return MW_ECUDA;
+      if (lib && (p.blk_row[b + 1] - p.blk_row[b] > mwk::kHaloRows ||
+                  p.rptr[p.blk_row[b + 1]] - p.rptr[p.blk_row[b]] > mwk::kHaloNnz))
+        return MW_ECUDA;
       for (int64_t j = h0 + 1; j < h0 + H; ++j)
         if (p.halo[j] <= p.halo[j - 1]) return MW_ECUDA;      // ascending, no repeats
       halo_sum += H;

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <climits>
 
 #include <string>
 #include <vector>
@@ -56,8 +57,8 @@ struct Topology {
 bool build_topology(int64_t n_vert, int64_t n_tet, const int32_t* tet_vert, Topology& topo, Error& err);
 
 // Blocked layout of the SpMM for the halo-tiled kernel: rows in the Morton order of their edge
-// midpoints, cut greedily into blocks whose column sets (halos) hold at most halo_max edges, so
-// one block's rows of X fit in shared memory.  Each row keeps its nonzeros in the canonical
+// midpoints, cut greedily into blocks whose column sets (halos) hold at most halo_max edges (and
+// at most row_max rows and nnz_max nonzeros), so one block fits in shared memory.  Each row keeps its nonzeros in the canonical
 // (ascending column) order, so a row's sum runs in the same order as with the canonical CSR.
 struct SpmmPlan {
   int64_t n_block = 0;
@@ -69,7 +70,8 @@ struct SpmmPlan {
   std::vector<uint16_t> lcol;      // [nnz] halo-local column of each blocked nonzero
   std::vector<int32_t> src;        // [nnz] canonical position of each blocked nonzero
 };
-bool build_spmm_plan(const Topology& topo, const double* xyz, int halo_max, SpmmPlan& plan, Error& err);
+bool build_spmm_plan(const Topology& topo, const double* xyz, int halo_max, SpmmPlan& plan, Error& err,
+                     int row_max = 1 << 30, int64_t nnz_max = INT64_MAX);
 
 // Subdomains of the overlapping Schwarz preconditioner (host side).
 struct Subdomains {
@@ -166,6 +168,8 @@ void spmm_f64(const int64_t* rp, const int32_t* ci, const double2* A, const doub
               int R, cudaStream_t s, int threads = 256);
 void spmm_f32(const int64_t* rp, const int32_t* ci, const float2* A, const float2* X, float2* Y, int64_t E, int R,
               cudaStream_t s, int threads = 256);
+// Bounds of one block of the halo-tiled SpMM plan: columns (halo), rows and nonzeros.
+constexpr int kHaloMax = 480, kHaloRows = 512, kHaloNnz = 4096;
 // Device copy of mw::SpmmPlan (halo_max bounds every block's halo).
 struct SpmmDev {
   int64_t n_block = 0;

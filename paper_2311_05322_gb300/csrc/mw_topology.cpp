@@ -359,7 +359,8 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
 }
 }  // namespace
 
-bool build_spmm_plan(const Topology& t, const double* xyz, int halo_max, SpmmPlan& p, Error& err) {
+bool build_spmm_plan(const Topology& t, const double* xyz, int halo_max, SpmmPlan& p, Error& err, int row_max,
+                     int64_t nnz_max) {
   const int64_t E = t.n_edge;
   if (halo_max < 64 || halo_max > 65535) {
     err = {MW_EINVAL, "halo_max out of range"};
@@ -390,20 +391,27 @@ bool build_spmm_plan(const Topology& t, const double* xyz, int halo_max, SpmmPla
   p.rows = order;
   p.blk_row.push_back(0);
   std::vector<int64_t> stamp(E, -1);
-  int64_t blk = 0, cnt = 0, nrow = 0;
+  int64_t blk = 0, cnt = 0, nrow = 0, nz = 0;
   for (int64_t i = 0; i < E; ++i) {
     const int32_t r = order[i];
+    const int64_t len = t.row_ptr[r + 1] - t.row_ptr[r];
+    if (len > nnz_max || len > halo_max) {
+      err = {MW_EINVAL, "SpMM plan: a row has more nonzeros than a block holds"};
+      return false;
+    }
     int64_t fresh = 0;
     for (int64_t k = t.row_ptr[r]; k < t.row_ptr[r + 1]; ++k) fresh += stamp[t.col_idx[k]] != blk;
-    if (nrow > 0 && cnt + fresh > halo_max) {
+    if (nrow > 0 && (cnt + fresh > halo_max || nrow + 1 > row_max || nz + len > nnz_max)) {
       p.blk_row.push_back(i);
       ++blk;
       cnt = 0;
       nrow = 0;
-      fresh = t.row_ptr[r + 1] - t.row_ptr[r];
+      nz = 0;
+      fresh = len;
     }
     for (int64_t k = t.row_ptr[r]; k < t.row_ptr[r + 1]; ++k) stamp[t.col_idx[k]] = blk;
     cnt += fresh;
+    nz += len;
     ++nrow;
   }
   p.blk_row.push_back(E);

@@ -503,7 +503,7 @@ class Context:
                      "seconds": th[:k + 1].copy()}
 
 
-def spmm_plan_stats(xyz, tets, halo_max: int = 864) -> dict:
+def spmm_plan_stats(xyz, tets, halo_max: int = 480) -> dict:
     """Host-only check and statistics of the halo-tiled SpMM plan (mw_spmm_plan_stats)."""
     lib = load_library()
     xyz = _c(xyz, np.float64)

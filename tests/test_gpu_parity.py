@@ -127,7 +127,7 @@ def test_spmm_halo_tiled(cells, ncols):
     rng = np.random.default_rng(ncols + cells[0])
     eps = EPS_MATCHING + rng.uniform(-6, 6, m.n_tet) + 1j * rng.uniform(-4, 4, m.n_tet)
     sysm = asm.build_system(m.xyz, m.tets)
-    st = mw.spmm_plan_stats(m.xyz, m.tets, 864)
+    st = mw.spmm_plan_stats(m.xyz, m.tets, 480)
     c = _ctx(m, eps, [1.1e9])
     E = sysm.topo.n_edge
     X = (rng.normal(size=(E, ncols)) + 1j * rng.normal(size=(E, ncols))).astype(np.complex64)
