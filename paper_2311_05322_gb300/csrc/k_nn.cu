@@ -6,6 +6,8 @@
 // reductions are deterministic (fixed per-thread order, fixed trees, no atomics).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "k_nn.h"
 #include "mw_internal.h"
 
@@ -24,18 +26,22 @@ __device__ __forceinline__ float ldb<__nv_bfloat16>(const __nv_bfloat16* p) {
 }
 
 // C[m][n] = sum_k A(m, k) B(k, n) (+ bias[n]); A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn].
-// Optional ReLU copy H.  64 x 64 tiles, 4 x 4 outputs per thread.
+// Optional ReLU copy H.  64 x 64 tiles, 4 x 4 outputs per thread.  Split K: the CTA of
+// blockIdx.z sums k in [z kchunk, (z + 1) kchunk) and, when P is given, writes its partial
+// sums to P[z][m][n] for gemm_reduce_kernel (bias and ReLU are applied there).
 template <typename TB>
 __global__ void __launch_bounds__(256) gemm_kernel(const float* __restrict__ A, int64_t sam, int64_t sak,
                                                    const TB* __restrict__ B, int64_t sbk, int64_t sbn,
                                                    const float* __restrict__ bias, float* __restrict__ C,
-                                                   float* __restrict__ H, int M, int N, int Kd) {
+                                                   float* __restrict__ H, int M, int N, int Kfull, int kchunk,
+                                                   float* __restrict__ P) {
   __shared__ float As[TK][TM + 1];
   __shared__ float Bs[TK][TN + 1];
   const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
   const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+  const int kbeg = blockIdx.z * kchunk, Kd = min(Kfull, kbeg + kchunk);
   float acc[4][4] = {};
-  for (int k0 = 0; k0 < Kd; k0 += TK) {
+  for (int k0 = kbeg; k0 < Kd; k0 += TK) {
     for (int e = threadIdx.x; e < TK * TM; e += 256) {
       // consecutive threads walk the contiguous axis of each operand
       int k, m;
@@ -84,10 +90,27 @@ __global__ void __launch_bounds__(256) gemm_kernel(const float* __restrict__ A, 
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tc + 16 * j;
       if (gn >= N) continue;
+      if (P) {
+        P[((int64_t)blockIdx.z * M + gm) * N + gn] = acc[i][j];
+        continue;
+      }
       const float v = acc[i][j] + (bias ? bias[gn] : 0.f);
       C[(int64_t)gm * N + gn] = v;
       if (H) H[(int64_t)gm * N + gn] = v > 0.f ? v : 0.f;
     }
+  }
+}
+
+// C = sum_z P[z] (z ascending) + bias, H = relu(C).
+__global__ void gemm_reduce_kernel(const float* __restrict__ P, int nz, const float* __restrict__ bias,
+                                   float* __restrict__ C, float* __restrict__ H, int M, int N) {
+  const int64_t MN = (int64_t)M * N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
+    float v = 0.f;
+    for (int z = 0; z < nz; ++z) v += P[z * MN + i];
+    if (bias) v += bias[i % N];
+    C[i] = v;
+    if (H) H[i] = v > 0.f ? v : 0.f;
   }
 }
 
@@ -106,26 +129,30 @@ __global__ void relu_back_kernel(const float* __restrict__ z, const float* __res
     dz[i] = z[i] > 0.f ? dh[i] : 0.f;
 }
 
-// convT forward, gather form: one thread per output; per axis the inputs i with o = 2i - 1 + k
-// are i = (o + 1 - k) / 2 for the two k of matching parity.
-__global__ void convT_fwd_kernel(const float* __restrict__ x, const float* __restrict__ w, const float* __restrict__ b,
-                                 float* __restrict__ a, float* __restrict__ g, int B, int Ci, int Co, int D) {
+// convT forward, gather form: one thread per output position (b, o), all Co channels at once;
+// per axis the inputs i with o = 2i - 1 + k are i = (o + 1 - k) / 2 for the two k of matching
+// parity.  The layer's weights sit in shared memory; every input value is read once per output
+// position.  Per output the sum runs over ci, then kz, ky, kx ascending.
+template <int CO>
+__global__ void __launch_bounds__(256) convT_fwd_kernel(const float* __restrict__ x, const float* __restrict__ w,
+                                                        const float* __restrict__ b, float* __restrict__ a,
+                                                        float* __restrict__ g, int B, int Ci, int D) {
+  extern __shared__ float sw[];                     // [Ci][CO][64]
+  for (int q = threadIdx.x; q < Ci * CO * 64; q += blockDim.x) sw[q] = w[q];
+  __syncthreads();
   const int Do = 2 * D;
-  const int64_t total = (int64_t)B * Co * Do * Do * Do;
+  const int64_t V = (int64_t)Do * Do * Do;
+  const int64_t total = (int64_t)B * V;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t r = t;
-    const int ox = (int)(r % Do);
-    r /= Do;
-    const int oy = (int)(r % Do);
-    r /= Do;
-    const int oz = (int)(r % Do);
-    r /= Do;
-    const int co = (int)(r % Co);
-    const int bb = (int)(r / Co);
-    float s = b[co];
+    const int64_t o = t % V;
+    const int bb = (int)(t / V);
+    const int ox = (int)(o % Do), oy = (int)((o / Do) % Do), oz = (int)(o / ((int64_t)Do * Do));
+    float s[CO];
+#pragma unroll
+    for (int co = 0; co < CO; ++co) s[co] = b[co];
     for (int ci = 0; ci < Ci; ++ci) {
       const float* xc = x + ((int64_t)bb * Ci + ci) * D * D * D;
-      const float* wc = w + ((int64_t)ci * Co + co) * 64;
+      const float* wc = sw + ci * CO * 64;
       for (int kz = (oz + 1) & 1; kz < 4; kz += 2) {
         const int iz = (oz + 1 - kz) >> 1;
         if (iz < 0 || iz >= D) continue;
@@ -135,35 +162,45 @@ __global__ void convT_fwd_kernel(const float* __restrict__ x, const float* __res
           for (int kx = (ox + 1) & 1; kx < 4; kx += 2) {
             const int ix = (ox + 1 - kx) >> 1;
             if (ix < 0 || ix >= D) continue;
-            s = fmaf(xc[(iz * D + iy) * D + ix], wc[(kz * 4 + ky) * 4 + kx], s);
+            const float xv = xc[(iz * D + iy) * D + ix];
+            const int kk = (kz * 4 + ky) * 4 + kx;
+#pragma unroll
+            for (int co = 0; co < CO; ++co) s[co] = fmaf(xv, wc[co * 64 + kk], s[co]);
           }
         }
       }
     }
-    a[t] = s;
-    if (g) g[t] = s > 0.f ? s : 0.f;
+#pragma unroll
+    for (int co = 0; co < CO; ++co) {
+      const int64_t idx = ((int64_t)bb * CO + co) * V + o;
+      a[idx] = s[co];
+      if (g) g[idx] = s[co] > 0.f ? s[co] : 0.f;
+    }
   }
 }
 
-// convT backward-data: dx[b][ci][i] = sum_co sum_k w[ci][co][k] dy[b][co][2i - 1 + k].
-__global__ void convT_bwd_data_kernel(const float* __restrict__ dy, const float* __restrict__ w,
-                                      float* __restrict__ dx, int B, int Ci, int Co, int D) {
+// convT backward-data: dx[b][ci][i] = sum_co sum_k w[ci][co][k] dy[b][co][2i - 1 + k]; one thread
+// per input position (b, i), all Ci channels at once, weights in shared memory.  Per output the
+// sum runs over co, then kz, ky, kx ascending.
+template <int CI>
+__global__ void __launch_bounds__(256) convT_bwd_data_kernel(const float* __restrict__ dy,
+                                                             const float* __restrict__ w, float* __restrict__ dx,
+                                                             int B, int Co, int D) {
+  extern __shared__ float sw[];                     // [CI][Co][64]
+  for (int q = threadIdx.x; q < CI * Co * 64; q += blockDim.x) sw[q] = w[q];
+  __syncthreads();
   const int Do = 2 * D;
-  const int64_t total = (int64_t)B * Ci * D * D * D;
+  const int64_t V = (int64_t)D * D * D;
+  const int64_t total = (int64_t)B * V;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t r = t;
-    const int ix = (int)(r % D);
-    r /= D;
-    const int iy = (int)(r % D);
-    r /= D;
-    const int iz = (int)(r % D);
-    r /= D;
-    const int ci = (int)(r % Ci);
-    const int bb = (int)(r / Ci);
-    float s = 0.f;
+    const int64_t i = t % V;
+    const int bb = (int)(t / V);
+    const int ix = (int)(i % D), iy = (int)((i / D) % D), iz = (int)(i / ((int64_t)D * D));
+    float s[CI];
+#pragma unroll
+    for (int ci = 0; ci < CI; ++ci) s[ci] = 0.f;
     for (int co = 0; co < Co; ++co) {
       const float* yc = dy + ((int64_t)bb * Co + co) * Do * Do * Do;
-      const float* wc = w + ((int64_t)ci * Co + co) * 64;
       for (int kz = 0; kz < 4; ++kz) {
         const int oz = 2 * iz - 1 + kz;
         if (oz < 0 || oz >= Do) continue;
@@ -173,12 +210,16 @@ __global__ void convT_bwd_data_kernel(const float* __restrict__ dy, const float*
           for (int kx = 0; kx < 4; ++kx) {
             const int ox = 2 * ix - 1 + kx;
             if (ox < 0 || ox >= Do) continue;
-            s = fmaf(yc[(oz * Do + oy) * Do + ox], wc[(kz * 4 + ky) * 4 + kx], s);
+            const float yv = yc[(oz * Do + oy) * Do + ox];
+            const int kk = (kz * 4 + ky) * 4 + kx;
+#pragma unroll
+            for (int ci = 0; ci < CI; ++ci) s[ci] = fmaf(yv, sw[(ci * Co + co) * 64 + kk], s[ci]);
           }
         }
       }
     }
-    dx[t] = s;
+#pragma unroll
+    for (int ci = 0; ci < CI; ++ci) dx[((int64_t)bb * CI + ci) * V + i] = s[ci];
   }
 }
 
@@ -214,20 +255,28 @@ __global__ void convT_bwd_w_kernel(const float* __restrict__ x, const float* __r
   if (threadIdx.x == 0) dw[widx] = red[0];
 }
 
-// per-channel sums of dy [B][Co][V] -> db [Co]; one block per channel, tree reduction.
-__global__ void chansum_kernel(const float* __restrict__ dy, int B, int Co, int64_t V, float* __restrict__ db) {
+// per-channel sums of dy [B][Co][V] -> db [Co] in two fixed-order passes: block (co, b) writes
+// the tree sum of its (channel, sample) slab to part[co][b]; then db[co] = sum_b part[co][b].
+__global__ void chansum_kernel(const float* __restrict__ dy, int B, int Co, int64_t V, float* __restrict__ part) {
   __shared__ float red[256];
-  const int co = blockIdx.x;
+  const int co = blockIdx.x, b = blockIdx.y;
   float s = 0.f;
-  for (int b = 0; b < B; ++b)
-    for (int64_t v = threadIdx.x; v < V; v += 256) s += dy[((int64_t)b * Co + co) * V + v];
+  for (int64_t v = threadIdx.x; v < V; v += 256) s += dy[((int64_t)b * Co + co) * V + v];
   red[threadIdx.x] = s;
   __syncthreads();
   for (int st = 128; st > 0; st >>= 1) {
     if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) db[co] = red[0];
+  if (threadIdx.x == 0) part[co * B + b] = red[0];
+}
+
+__global__ void chansum_final_kernel(const float* __restrict__ part, int B, int Co, float* __restrict__ db) {
+  const int co = blockIdx.x * blockDim.x + threadIdx.x;
+  if (co >= Co) return;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s += part[co * B + b];
+  db[co] = s;
 }
 
 // MSE: dy = 2 (y - t) / n, per-block partial sums of (y - t)^2 in FP64.
@@ -343,17 +392,43 @@ inline int gsb(int64_t n) {
 
 }  // namespace
 
+// K chunks for a GEMM of `tiles` 64x64 tiles: enough CTAs for two per SM, chunks of at least
+// 256 along K, a whole number of TK steps, and the partials within the workspace.
+static int k_splits(int tiles, int M, int N, int K, size_t ws_floats, int& kchunk) {
+  int z = std::max(1, std::min(K / 256, (2 * 152 + tiles - 1) / tiles));
+  while (z > 1 && (size_t)z * M * N > ws_floats) --z;
+  kchunk = ((K + z - 1) / z + TK - 1) / TK * TK;
+  return (K + kchunk - 1) / kchunk;
+}
+
+template <typename TB>
+static void gemm_launch(const float* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk, int64_t sbn,
+                        const float* bias, float* C, float* H, int M, int N, int K, float* ws, size_t ws_floats,
+                        cudaStream_t s) {
+  const int tiles = ((N + TN - 1) / TN) * ((M + TM - 1) / TM);
+  int kchunk = K;
+  const int z = ws ? k_splits(tiles, M, N, K, ws_floats, kchunk) : 1;
+  dim3 g((N + TN - 1) / TN, (M + TM - 1) / TM, z);
+  if (z == 1) {
+    note_launch(1);
+    gemm_kernel<TB><<<g, 256, 0, s>>>(A, sam, sak, B, sbk, sbn, bias, C, H, M, N, K, K, nullptr);
+    return;
+  }
+  note_launch(2);
+  gemm_kernel<TB><<<g, 256, 0, s>>>(A, sam, sak, B, sbk, sbn, bias, C, H, M, N, K, kchunk, ws);
+  const int64_t MN = (int64_t)M * N;
+  gemm_reduce_kernel<<<(int)std::min<int64_t>((MN + 255) / 256, 152 * 8), 256, 0, s>>>(ws, z, bias, C, H, M, N);
+}
+
 void nn_gemm_bf16(const float* A, int64_t sam, int64_t sak, const void* Bw, int64_t sbk, int64_t sbn,
-                  const float* bias, float* C, float* H, int M, int N, int K, cudaStream_t s) {
-  note_launch(1);
-  dim3 g((N + TN - 1) / TN, (M + TM - 1) / TM);
-  gemm_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(A, sam, sak, (const __nv_bfloat16*)Bw, sbk, sbn, bias, C, H, M, N, K);
+                  const float* bias, float* C, float* H, int M, int N, int K, cudaStream_t s, float* ws,
+                  size_t ws_floats) {
+  gemm_launch<__nv_bfloat16>(A, sam, sak, (const __nv_bfloat16*)Bw, sbk, sbn, bias, C, H, M, N, K, ws, ws_floats, s);
 }
 void nn_gemm_f32(const float* A, int64_t sam, int64_t sak, const float* Bf, int64_t sbk, int64_t sbn,
-                 const float* bias, float* C, float* H, int M, int N, int K, cudaStream_t s) {
-  note_launch(1);
-  dim3 g((N + TN - 1) / TN, (M + TM - 1) / TM);
-  gemm_kernel<float><<<g, 256, 0, s>>>(A, sam, sak, Bf, sbk, sbn, bias, C, H, M, N, K);
+                 const float* bias, float* C, float* H, int M, int N, int K, cudaStream_t s, float* ws,
+                 size_t ws_floats) {
+  gemm_launch<float>(A, sam, sak, Bf, sbk, sbn, bias, C, H, M, N, K, ws, ws_floats, s);
 }
 void nn_colsum(const float* dz, int B, int N, float* db, cudaStream_t s) {
   note_launch(1);
@@ -363,17 +438,53 @@ void nn_relu_back(const float* z, const float* dh, float* dz, int64_t n, cudaStr
   note_launch(1);
   relu_back_kernel<<<gsb(n), 256, 0, s>>>(z, dh, dz, n);
 }
+// The transposed convolutions keep a layer's weights (up to 16 x 16 x 64 floats, 64 KB) in
+// dynamic shared memory.
+static void allow_conv_smem() {
+  static bool done = false;
+  if (done) return;
+  const int sm = 16 * 16 * 64 * (int)sizeof(float);
+  cudaFuncSetAttribute(convT_fwd_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(convT_fwd_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(convT_fwd_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(convT_bwd_data_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(convT_bwd_data_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  done = true;
+}
+
 void nn_convT_fwd(const float* x, const float* w, const float* b, float* a, float* g, int B, int Ci, int Co, int D,
                   cudaStream_t s) {
+  allow_conv_smem();
   note_launch(1);
-  convT_fwd_kernel<<<gsb((int64_t)B * Co * 8 * D * D * D), 256, 0, s>>>(x, w, b, a, g, B, Ci, Co, D);
+  const int64_t n = (int64_t)B * 8 * D * D * D;
+  const size_t sm = sizeof(float) * Ci * Co * 64;
+  switch (Co) {
+    case 2:
+      convT_fwd_kernel<2><<<gsb(n), 256, sm, s>>>(x, w, b, a, g, B, Ci, D);
+      break;
+    case 8:
+      convT_fwd_kernel<8><<<gsb(n), 256, sm, s>>>(x, w, b, a, g, B, Ci, D);
+      break;
+    default:
+      convT_fwd_kernel<16><<<gsb(n), 256, sm, s>>>(x, w, b, a, g, B, Ci, D);
+      break;
+  }
 }
 void nn_convT_bwd(const float* x, const float* w, const float* dy, float* dx, float* dw, float* db, int B, int Ci,
-                  int Co, int D, cudaStream_t s) {
-  note_launch(dx ? 3 : 2);
-  if (dx) convT_bwd_data_kernel<<<gsb((int64_t)B * Ci * D * D * D), 256, 0, s>>>(dy, w, dx, B, Ci, Co, D);
+                  int Co, int D, float* part, cudaStream_t s) {
+  allow_conv_smem();
+  note_launch(dx ? 4 : 3);
+  if (dx) {
+    const int64_t n = (int64_t)B * D * D * D;
+    const size_t sm = sizeof(float) * Ci * Co * 64;
+    if (Ci == 8)
+      convT_bwd_data_kernel<8><<<gsb(n), 256, sm, s>>>(dy, w, dx, B, Co, D);
+    else
+      convT_bwd_data_kernel<16><<<gsb(n), 256, sm, s>>>(dy, w, dx, B, Co, D);
+  }
   convT_bwd_w_kernel<<<Ci * Co * 64, 256, 0, s>>>(x, dy, dw, B, Ci, Co, D);
-  chansum_kernel<<<Co, 256, 0, s>>>(dy, B, Co, (int64_t)8 * D * D * D, db);
+  chansum_kernel<<<dim3(Co, B), 256, 0, s>>>(dy, B, Co, (int64_t)8 * D * D * D, part);
+  chansum_final_kernel<<<1, 32, 0, s>>>(part, B, Co, db);
 }
 void nn_mse(const float* y, const float* t, int64_t n, float* dy, double* part, double* loss, cudaStream_t s) {
   note_launch(2);

@@ -168,6 +168,8 @@ struct NnState {
   void *W1b = nullptr, *W2b = nullptr;
   float *x = nullptr, *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *a1 = nullptr, *g1 = nullptr,
         *a2 = nullptr, *g2 = nullptr, *y = nullptr, *t = nullptr;
+  float* gws = nullptr;       // split-K partial sums of the dense layers [32][bcap][1024]
+  float* cpart = nullptr;     // per-(channel, sample) partial bias sums [bcap][16]
   float *dy = nullptr, *dg2 = nullptr, *da2 = nullptr, *dg1 = nullptr, *da1 = nullptr, *dh2 = nullptr,
         *dz2 = nullptr, *dh1 = nullptr, *dz1 = nullptr;
   double *part = nullptr, *loss = nullptr;
@@ -3401,6 +3403,7 @@ static void nn_free(Ctx* c) {
                   (void*)n.h1, (void*)n.z2, (void*)n.h2, (void*)n.a1, (void*)n.g1, (void*)n.a2, (void*)n.g2,
                   (void*)n.y, (void*)n.t, (void*)n.dy, (void*)n.dg2, (void*)n.da2, (void*)n.dg1, (void*)n.da1,
                   (void*)n.dh2, (void*)n.dz2, (void*)n.dh1, (void*)n.dz1, (void*)n.part, (void*)n.loss,
+                  (void*)n.gws, (void*)n.cpart,
                   (void*)n.data_x, (void*)n.data_t, (void*)n.idx})
     dfree(c, p);
   n = NnState();
@@ -3411,8 +3414,11 @@ static void nn_batch_buffers(Ctx* c, int B) {
   if (B <= n.bcap) return;
   for (void* p : {(void*)n.x, (void*)n.z1, (void*)n.h1, (void*)n.z2, (void*)n.h2, (void*)n.a1, (void*)n.g1, (void*)n.a2,
                   (void*)n.g2, (void*)n.y, (void*)n.t, (void*)n.dy, (void*)n.dg2, (void*)n.da2, (void*)n.dg1,
-                  (void*)n.da1, (void*)n.dh2, (void*)n.dz2, (void*)n.dh1, (void*)n.dz1, (void*)n.idx})
+                  (void*)n.da1, (void*)n.dh2, (void*)n.dz2, (void*)n.dh1, (void*)n.dz1, (void*)n.idx, (void*)n.gws,
+                  (void*)n.cpart})
     dfree(c, p);
+  n.gws = dalloc<float>(c, (size_t)32 * B * kHid);
+  n.cpart = dalloc<float>(c, (size_t)16 * B);
   n.x = dalloc<float>(c, (size_t)B * n.n_in);
   n.z1 = dalloc<float>(c, (size_t)B * kHid);
   n.h1 = dalloc<float>(c, (size_t)B * kHid);
@@ -3453,8 +3459,9 @@ static void nn_forward(Ctx* c, int B) {
     // BF16 weights, FP32 inputs and biases read once; pre- and post-activation written
     ProfScope ps(c, MW_K_NN_GEMM, 2.0 * H * (ni + H) + 4.0 * Bd * (ni + H) + 8.0 * H + 16.0 * Bd * H,
                  2.0 * Bd * H * (ni + H));
-    mwk::nn_gemm_bf16(n.x, n.n_in, 1, n.W1b, 1, n.n_in, th + n.ob1, n.z1, n.h1, B, kHid, n.n_in, s);
-    mwk::nn_gemm_bf16(n.h1, kHid, 1, n.W2b, 1, kHid, th + n.ob2, n.z2, n.h2, B, kHid, kHid, s);
+    const size_t wsf = (size_t)32 * n.bcap * kHid;
+    mwk::nn_gemm_bf16(n.x, n.n_in, 1, n.W1b, 1, n.n_in, th + n.ob1, n.z1, n.h1, B, kHid, n.n_in, s, n.gws, wsf);
+    mwk::nn_gemm_bf16(n.h1, kHid, 1, n.W2b, 1, kHid, th + n.ob2, n.z2, n.h2, B, kHid, kHid, s, n.gws, wsf);
   }
   // each input voxel meets 4^3 taps per (ci, co) pair: 16x16 at 4^3, 16x8 at 8^3, 8x2 at 16^3
   ProfScope ps(c, MW_K_NN_CONV, 4.0 * Bd * (H + 2 * 2 * 16 * 512 + 2 * 8 * 4096 + kOut),
@@ -3480,21 +3487,22 @@ static void nn_backward(Ctx* c, int B) {
     // flops; the first layer's input gradient is the reshaped dh2), ReLU masks between them
     ProfScope ps(c, MW_K_NN_CONV, 4.0 * Bd * (kOut + 3 * 2 * 8 * 4096 + 3 * 2 * 16 * 512 + 2 * H),
                  4.0 * 64 * Bd * (16 * 16 * 64 + 16 * 8 * 512 + 8 * 2 * 4096));
-    mwk::nn_convT_bwd(n.g2, th + n.oC3, n.dy, n.dg2, g + n.oC3, g + n.oc3, B, 8, 2, 16, s);
+    mwk::nn_convT_bwd(n.g2, th + n.oC3, n.dy, n.dg2, g + n.oC3, g + n.oc3, B, 8, 2, 16, n.cpart, s);
     mwk::nn_relu_back(n.a2, n.dg2, n.da2, (int64_t)B * 8 * 4096, s);
-    mwk::nn_convT_bwd(n.g1, th + n.oC2, n.da2, n.dg1, g + n.oC2, g + n.oc2, B, 16, 8, 8, s);
+    mwk::nn_convT_bwd(n.g1, th + n.oC2, n.da2, n.dg1, g + n.oC2, g + n.oc2, B, 16, 8, 8, n.cpart, s);
     mwk::nn_relu_back(n.a1, n.dg1, n.da1, (int64_t)B * 16 * 512, s);
-    mwk::nn_convT_bwd(n.h2, th + n.oC1, n.da1, n.dh2, g + n.oC1, g + n.oc1, B, 16, 16, 4, s);
+    mwk::nn_convT_bwd(n.h2, th + n.oC1, n.da1, n.dh2, g + n.oC1, g + n.oc1, B, 16, 16, 4, n.cpart, s);
   }
   // dW2 = dz2^T h1, dh1 = dz2 W2 (BF16 W2), dW1 = dz1^T x; bias sums and ReLU masks between
   ProfScope ps(c, MW_K_NN_GEMM, 4.0 * H * (H + ni) + 2.0 * H * H + 4.0 * Bd * (ni + 6 * H) + 8.0 * H,
                2.0 * Bd * H * (2 * H + ni));
   mwk::nn_relu_back(n.z2, n.dh2, n.dz2, (int64_t)B * kHid, s);
-  mwk::nn_gemm_f32(n.dz2, 1, kHid, n.h1, kHid, 1, nullptr, g + n.oW2, nullptr, kHid, kHid, B, s);
+  const size_t wsf = (size_t)32 * n.bcap * kHid;
+  mwk::nn_gemm_f32(n.dz2, 1, kHid, n.h1, kHid, 1, nullptr, g + n.oW2, nullptr, kHid, kHid, B, s, n.gws, wsf);
   mwk::nn_colsum(n.dz2, B, kHid, g + n.ob2, s);
-  mwk::nn_gemm_bf16(n.dz2, kHid, 1, n.W2b, kHid, 1, nullptr, n.dh1, nullptr, B, kHid, kHid, s);
+  mwk::nn_gemm_bf16(n.dz2, kHid, 1, n.W2b, kHid, 1, nullptr, n.dh1, nullptr, B, kHid, kHid, s, n.gws, wsf);
   mwk::nn_relu_back(n.z1, n.dh1, n.dz1, (int64_t)B * kHid, s);
-  mwk::nn_gemm_f32(n.dz1, 1, kHid, n.x, n.n_in, 1, nullptr, g + n.oW1, nullptr, kHid, n.n_in, B, s);
+  mwk::nn_gemm_f32(n.dz1, 1, kHid, n.x, n.n_in, 1, nullptr, g + n.oW1, nullptr, kHid, n.n_in, B, s, n.gws, wsf);
   mwk::nn_colsum(n.dz1, B, kHid, g + n.ob1, s);
 }
 
