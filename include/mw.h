@@ -392,6 +392,17 @@ mw_status mw_nn_infer(mw_ctx* ctx, int64_t n, const float* x, float* y);
  * the order-4 barycentric lattice of the tet; deps [n_tet][2] (host). */
 mw_status mw_nn_grid_to_tets(mw_ctx* ctx, const float* grid, int32_t G, const double* box, double* deps);
 
+/* How mw_gradient / mw_gradient_dev / mw_invert obtain the adjoint fields (Sec. IV-D):
+ *   MW_ADJOINT_SOLVE (default): one adjoint solve per transmitter column, A lambda_j =
+ *     sum_i (c_ij / n_i) w_i, with the same solver and preconditioner as the forward solves;
+ *   MW_ADJOINT_RECIPROCAL: the receivers are the transmitters and A = A^T, so
+ *     lambda_j = sum_i c_ij / (n_i coef_i) x_i exactly (coef_i the source coefficient of
+ *     transmitter i), formed from the forward fields in FP64 without any adjoint solve.  The
+ *     gradient is the same up to the forward solves' tolerance.
+ * MW_EINVAL for another value. */
+enum { MW_ADJOINT_SOLVE = 0, MW_ADJOINT_RECIPROCAL = 1 };
+mw_status mw_set_adjoint_mode(mw_ctx* ctx, int32_t mode);
+
 /* ---- column-sharded evaluation (one evaluation split over processes by transmitters) ---
  * The transmitter columns of an evaluation are independent until the cost: process r solves
  * its own window of columns (mw_forward_cols), the S columns of all windows are all-gathered

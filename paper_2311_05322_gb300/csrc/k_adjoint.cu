@@ -73,6 +73,37 @@ __global__ void adjoint_sources_kernel(const int64_t* __restrict__ tptr, const i
   B[(int64_t)tedge[u] * nl + j] = make_double2(re, im);
 }
 
+// Adjoint fields by reciprocity (receivers are the transmitters, A = A^T): the adjoint source
+// of column j is sum_i (c_ij / n_i) w_i and A^-1 w_i = x_i / coef_i, so
+// lambda_j = sum_i D_ij x_i with D_ij = c_ij / (n_i coef_i).  One thread per (edge, column).
+__global__ void reciprocal_weights_kernel(const double2* __restrict__ C, const double* __restrict__ nrm,
+                                          const double2* __restrict__ coef, int ns, double2* __restrict__ D) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ns * ns) return;
+  const int i = t / ns;
+  const double2 c = C[t], q = coef[i];
+  // c / (n_i q)
+  const double den = nrm[i] * (q.x * q.x + q.y * q.y);
+  D[t] = make_double2((c.x * q.x + c.y * q.y) / den, (c.y * q.x - c.x * q.y) / den);
+}
+
+__global__ void reciprocal_combine_kernel(const double2* __restrict__ X, const double2* __restrict__ D, int ns,
+                                          int64_t E, double2* __restrict__ L) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= E * ns) return;
+  const int64_t e = t / ns;
+  const int j = (int)(t - e * ns);
+  double re = 0.0, im = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    const double2 x = X[e * ns + i], d = D[i * ns + j];
+    re = fma(x.x, d.x, re);
+    re = fma(-x.y, d.y, re);
+    im = fma(x.x, d.y, im);
+    im = fma(x.y, d.x, im);
+  }
+  L[t] = make_double2(re, im);
+}
+
 // One warp per tet, lanes over the transmitter columns; the warp sums lambda_j^T M^T x_j
 // over its columns with a fixed shuffle tree.
 template <int CPL>
@@ -212,6 +243,13 @@ void grad_tet(const int32_t* tet_edge, const double* KM, int64_t T, const double
     grad_tet_kernel<2><<<blocks, 256, 0, s>>>(tet_edge, KM, T, L, X, ns, k0sq, g);
   else
     grad_tet_kernel<4><<<blocks, 256, 0, s>>>(tet_edge, KM, T, L, X, ns, k0sq, g);
+}
+void reciprocal_adjoint(const double2* X, const double2* C, const double* nrm, const double2* coef, int ns, int64_t E,
+                        double2* D, double2* L, cudaStream_t s) {
+  note_launch(2);
+  reciprocal_weights_kernel<<<(ns * ns + 255) / 256, 256, 0, s>>>(C, nrm, coef, ns, D);
+  const int64_t n = E * ns;
+  reciprocal_combine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, D, ns, E, L);
 }
 void tikhonov(const int32_t* tet_nb, const double* w, const double* eps, int64_t T, double* grad, double* red,
               cudaStream_t s) {

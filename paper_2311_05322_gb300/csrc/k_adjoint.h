@@ -16,6 +16,10 @@ void adjoint_weights(const double2* S, const double2* S_obs, const double2* S_em
 void adjoint_sources(const int64_t* tptr, const int32_t* tedge, const int32_t* tsrc, const int32_t* tk, int64_t nu,
                      const double* w, const double* nrm, const double2* C, int ns, double2* B, int64_t E,
                      cudaStream_t s, int j0 = 0, int nl = -1);
+// Adjoint fields by reciprocity: L [E][ns] = X D with D_ij = C_ij / (nrm_i coef_i) (D: scratch
+// [ns][ns]); X the forward fields of the same sources, C the adjoint weights [ns][ns].
+void reciprocal_adjoint(const double2* X, const double2* C, const double* nrm, const double2* coef, int ns, int64_t E,
+                        double2* D, double2* L, cudaStream_t s);
 void grad_tet(const int32_t* tet_edge, const double* KM, int64_t T, const double2* L, const double2* X, int ns,
               double k0sq, double* g, cudaStream_t s);
 void tikhonov(const int32_t* tet_nb, const double* w, const double* eps, int64_t T, double* grad, double* red,

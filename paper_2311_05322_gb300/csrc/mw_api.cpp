@@ -275,6 +275,8 @@ struct Ctx {
   // fields, adjoint fields and right-hand sides per frequency [E][win_nl], S columns
   // [n_freq][n_src][win_nl]
   int win_j0 = 0, win_nl = 0, win_nf = 0, win_ns = 0;
+  int adjoint_mode = 0;          // MW_ADJOINT_SOLVE or MW_ADJOINT_RECIPROCAL
+  double2* d_D = nullptr;        // reciprocity weights [n_src][n_src]
   std::vector<double2*> Xw, Lw, Bw, Bwa;
   double2* d_Sp = nullptr;
   double2* d_B = nullptr;      // RHS scratch [E][n_src]
@@ -1783,6 +1785,8 @@ void release_mesh(Ctx* c) {
   for (auto p : c->d_Badj) dfree(c, p);
   c->d_Badj.clear();
   free_window(c);
+  dfree(c, c->d_D);
+  c->d_D = nullptr;
   c->d_S = c->d_C = c->d_So = c->d_Se = nullptr;
   c->d_J = c->d_grad = c->d_gR = nullptr;
   c->d_xyz = nullptr;
@@ -2799,14 +2803,24 @@ static void gradient_dev_impl(Ctx* c, const mw_solve_opts& o, const double2* dSo
     mwk::s_project(c->Xf[f], c->d_q_ptr, c->d_q_edge, c->d_q_w, c->d_q_norm, ns, c->d_S + (size_t)f * ns * ns,
                    c->stream);
   mwk::adjoint_weights(c->d_S, dSo, dSe, (int64_t)nS, c->d_C, c->d_J, c->stream);
-  std::vector<const double2*> Bc(nf);
-  for (int f = 0; f < nf; ++f) {
-    mwk::adjoint_sources(c->d_qt_ptr, c->d_qt_edge, c->d_qt_src, c->d_qt_k, c->n_qt, c->d_q_w, c->d_q_norm,
-                         c->d_C + (size_t)f * ns * ns, ns, c->d_Badj[f], E, c->stream);
-    Bc[f] = c->d_Badj[f];
+  if (c->adjoint_mode == MW_ADJOINT_RECIPROCAL) {
+    // receivers are the transmitters and A = A^T: the adjoint fields are combinations of the
+    // forward fields, no adjoint solve
+    if (!c->d_D) c->d_D = dalloc<double2>(c, 128 * 128);
+    for (int f = 0; f < nf; ++f)
+      mwk::reciprocal_adjoint(c->Xf[f], c->d_C + (size_t)f * ns * ns, c->d_q_norm, c->d_src_coef + (size_t)f * ns,
+                              ns, E, c->d_D, c->Lf[f], c->stream);
+    check_launch("reciprocal adjoint");
+  } else {
+    std::vector<const double2*> Bc(nf);
+    for (int f = 0; f < nf; ++f) {
+      mwk::adjoint_sources(c->d_qt_ptr, c->d_qt_edge, c->d_qt_src, c->d_qt_k, c->n_qt, c->d_q_w, c->d_q_norm,
+                           c->d_C + (size_t)f * ns * ns, ns, c->d_Badj[f], E, c->stream);
+      Bc[f] = c->d_Badj[f];
+    }
+    check_launch("adjoint sources");
+    solve_all(c, o, ns, Bc, c->Lf, nullptr);
   }
-  check_launch("adjoint sources");
-  solve_all(c, o, ns, Bc, c->Lf, nullptr);
   CK(cudaMemsetAsync(dg, 0, sizeof(double) * 2 * T, c->stream));
   for (int f = 0; f < nf; ++f) {
     const double k0 = k0_of(c->freqs[f]);
@@ -2904,6 +2918,13 @@ static void gradient_cols_impl(Ctx* c, const mw_solve_opts& o, const double* S_f
   CK(cudaMemcpyAsync(J_out, c->d_J, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(grad_part, c->d_grad, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+}
+
+mw_status mw_set_adjoint_mode(mw_ctx* c, int32_t mode) {
+  return guard(c, [&] {
+    require(mode == MW_ADJOINT_SOLVE || mode == MW_ADJOINT_RECIPROCAL, MW_EINVAL, "bad adjoint mode");
+    c->adjoint_mode = mode;
+  });
 }
 
 mw_status mw_forward_cols(mw_ctx* c, const mw_solve_opts* opts, int32_t j0, int32_t n_cols, double* S_cols) {

@@ -153,12 +153,14 @@ def _stats(v):
 
 
 def run(scale: str = "reduced", seed: int = 3, plain: bool | None = None, snr_db: float = 40.0, tears: int = 1,
-        alphas=(), verbose=False):
+        alphas=(), verbose=False, reciprocal: bool = True):
     """Train the network once, then invert `tears` held-out tears from the healthy start and from
     the network's start (mixed solver; the plain FP64 inversion too on the first tear when
     `plain`).  Per tear: the target is the reference inversion's J after max_it (plain FP64 on the
     first tear when run, else the mixed inversion from the healthy start), and each variant's
-    time to reach it.  `alphas`: Tikhonov sweep of the mixed inversion on the first tear."""
+    time to reach it.  `alphas`: Tikhonov sweep of the mixed inversion on the first tear.
+    `reciprocal`: on the first tear, also the mixed inversions whose adjoint fields come from the
+    forward fields by reciprocity (mw_set_adjoint_mode) instead of adjoint solves."""
     cfg = SCALES[scale]
     out = {"scale": scale, "config": {k: v for k, v in cfg.items()}}
     f_nn = len(cfg["freqs"]) // 2                       # network sees the middle frequency
@@ -231,6 +233,13 @@ def run(scale: str = "reduced", seed: int = 3, plain: bool | None = None, snr_db
         learned0 = _pairs(eps0) + inv.ctx.nn_grid_to_tets(grid, np.asarray(ROI_BOX))
         res = {"mixed": invert(S_fit, _pairs(eps0), mixed, cfg["alpha"]),
                "mixed_learned": invert(S_fit, learned0, mixed, cfg["alpha"])}
+        if k == 0 and reciprocal:
+            # the same mixed inversions with the adjoint fields formed from the forward fields
+            # by reciprocity instead of adjoint solves
+            inv.ctx.set_adjoint_mode(True)
+            res["mixed_reciprocal"] = invert(S_fit, _pairs(eps0), mixed, cfg["alpha"])
+            res["mixed_learned_reciprocal"] = invert(S_fit, learned0, mixed, cfg["alpha"])
+            inv.ctx.set_adjoint_mode(False)
         if plain and k == 0:
             inv.ctx.assemble(list(cfg["freqs"]), _pairs(eps0), EPS_MATCHING)
             # FP64 factorisation and FP64 apply: the plain path is FP64 throughout (its setup is

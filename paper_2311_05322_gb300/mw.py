@@ -112,6 +112,7 @@ _SIGS = {
     "mw_lbfgs_destroy": (None, [_P]),
     "mw_invert": (C.c_int32, [_P, C.POINTER(mw_inv_opts), C.POINTER(mw_solve_opts), _P, _P, _P,
                               C.POINTER(mw_inv_history)]),
+    "mw_set_adjoint_mode": (C.c_int32, [_P, C.c_int32]),
     "mw_forward_cols": (C.c_int32, [_P, C.POINTER(mw_solve_opts), C.c_int32, C.c_int32, _P]),
     "mw_gradient_cols": (C.c_int32, [_P, C.POINTER(mw_solve_opts), _P, _P, _P, C.POINTER(C.c_double), _P]),
     "mw_assemble_dev": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
@@ -133,6 +134,7 @@ _SIGS = {
     "mw_nn_grid_to_tets": (C.c_int32, [_P, _P, C.c_int32, _P, _P]),
 }
 
+MW_ADJOINT_SOLVE, MW_ADJOINT_RECIPROCAL = 0, 1
 (MW_K_SPMM, MW_K_ORAS, MW_K_CGS_DOTS, MW_K_CGS_UPDATE, MW_K_RESIDUAL, MW_K_REASSEMBLE, MW_K_GRADIENT, MW_K_FACTOR,
  MW_K_NN_GEMM, MW_K_NN_CONV, MW_K_NN_OTHER, MW_K_NCLASS) = range(12)
 K_CLASS_NAMES = ("spmm", "oras_apply", "cgs_dots", "cgs_update", "residual_fp64", "reassemble", "gradient",
@@ -389,6 +391,10 @@ class Context:
         S = np.empty_like(So) if want_S else None
         self._check(self.lib.mw_gradient(self.h, C.byref(o), _ptr(So), _ptr(Se), alpha, C.byref(J), _ptr(g), _ptr(S)))
         return (J.value, g, S) if want_S else (J.value, g)
+
+    def set_adjoint_mode(self, reciprocal: bool):
+        """Adjoint fields by explicit solves (default) or by reciprocity from the forward fields."""
+        self._check(self.lib.mw_set_adjoint_mode(self.h, MW_ADJOINT_RECIPROCAL if reciprocal else MW_ADJOINT_SOLVE))
 
     def forward_cols(self, j0: int, n_cols: int, opts: mw_solve_opts | None = None) -> np.ndarray:
         """Forward solves of transmitters j0 .. j0+n_cols-1; returns their S columns

@@ -348,6 +348,17 @@ def test_gradient_matches_oracle(ragged):
     J2, g2 = c.gradient(S_obs, S_emp, alpha=1e-3, opts=mw.solve_opts(tol=1e-11))
     assert abs(J2 - (J_ref + 1e-3 * R_ref)) <= 1e-8 * abs(J2)
     assert _relerr(g2, g_ref + 1e-3 * gR_ref) <= 1e-6
+    # adjoint fields by reciprocity (no adjoint solves): the same gradient to the solve tolerance,
+    # in FP64 and in the mixed solver
+    c.set_adjoint_mode(True)
+    J3, g3 = c.gradient(S_obs, S_emp, alpha=0.0, opts=mw.solve_opts(tol=1e-11))
+    assert abs(J3 - J_ref) <= 1e-8 * abs(J_ref)
+    assert _relerr(g3, g_ref) <= 1e-6 and _relerr(g3, g) <= 1e-8
+    c.setup_preconditioner(4, box_partition(m, (2, 2, 1), seed=7), 1, mw.MW_PREC_BF16)
+    J4, g4 = c.gradient(S_obs, S_emp, alpha=0.0, opts=mw.solve_opts(mode=mw.MW_MODE_MIXED, tol=1e-10))
+    c.set_adjoint_mode(False)
+    J5, g5 = c.gradient(S_obs, S_emp, alpha=0.0, opts=mw.solve_opts(mode=mw.MW_MODE_MIXED, tol=1e-10))
+    assert _relerr(g4, g_ref) <= 1e-6 and _relerr(g5, g_ref) <= 1e-6
 
 
 def test_lbfgs_matches_oracle_iterates():

@@ -151,6 +151,11 @@ def test_port_gradient_matches_oracle(chamber):
     J, g = c.gradient(S_obs, S_emp, alpha=0.0, opts=mw.solve_opts(tol=1e-11))
     assert abs(J - J_ref) <= 1e-8 * abs(J_ref)
     assert _relerr(g, g_ref) <= 1e-6
+    # the ports receive what they transmit: adjoint fields by reciprocity, no adjoint solves
+    c.set_adjoint_mode(True)
+    J2, g2 = c.gradient(S_obs, S_emp, alpha=0.0, opts=mw.solve_opts(tol=1e-11))
+    assert abs(J2 - J_ref) <= 1e-8 * abs(J_ref)
+    assert _relerr(g2, g_ref) <= 1e-6 and _relerr(g2, g) <= 1e-8
 
 
 def test_straight_guide_te10_on_gpu():
