@@ -223,36 +223,68 @@ __global__ void __launch_bounds__(256) convT_bwd_data_kernel(const float* __rest
   }
 }
 
-// convT backward-weights: one block per (ci, co, k); threads over (b, i); tree reduction.
-__global__ void convT_bwd_w_kernel(const float* __restrict__ x, const float* __restrict__ dy, float* __restrict__ dw,
-                                   int B, int Ci, int Co, int D) {
-  __shared__ float red[256];
-  const int widx = blockIdx.x;
-  const int k = widx % 64, co = (widx / 64) % Co, ci = widx / (64 * Co);
-  const int kz = k / 16, ky = (k / 4) % 4, kx = k % 4;
+// convT backward-weights, dW[ci][co][k] = sum_b sum_i x[b][ci][i] dy[b][co][2i - 1 + k], in two
+// fixed-order passes.  Pass 1: block (ci, co, chunk) walks its chunk of the B D^3 input positions;
+// thread t takes positions t, t + 256, ... and keeps the 64 tap sums in registers; the block
+// then sums the 256 threads' values tap by tap (thread order, 32 taps at a time through shared
+// memory) into part[chunk][ci][co][k].
+// Pass 2 sums the chunks in order.
+constexpr int kBwdWThreads = 256;
+__global__ void __launch_bounds__(kBwdWThreads) convT_bwd_w_kernel(const float* __restrict__ x,
+                                                                   const float* __restrict__ dy,
+                                                                   float* __restrict__ part, int B, int Ci, int Co,
+                                                                   int D, int64_t chunk) {
+  __shared__ float red[kBwdWThreads][33];
+  const int ci = blockIdx.x / Co, co = blockIdx.x % Co;
   const int Do = 2 * D;
-  const int64_t total = (int64_t)B * D * D * D;
-  float s = 0.f;
-  for (int64_t t = threadIdx.x; t < total; t += 256) {
-    int64_t r = t;
-    const int ix = (int)(r % D);
-    r /= D;
-    const int iy = (int)(r % D);
-    r /= D;
-    const int iz = (int)(r % D);
-    const int bb = (int)(r / D);
-    const int oz = 2 * iz - 1 + kz, oy = 2 * iy - 1 + ky, ox = 2 * ix - 1 + kx;
-    if (oz < 0 || oz >= Do || oy < 0 || oy >= Do || ox < 0 || ox >= Do) continue;
-    s = fmaf(x[(((int64_t)bb * Ci + ci) * D + iz) * D * D + iy * D + ix],
-             dy[(((int64_t)bb * Co + co) * Do + oz) * Do * Do + oy * Do + ox], s);
+  const int64_t V = (int64_t)D * D * D, total = (int64_t)B * V;
+  const int64_t p0 = (int64_t)blockIdx.y * chunk, p1 = min(total, p0 + chunk);
+  float acc[64];
+#pragma unroll
+  for (int k = 0; k < 64; ++k) acc[k] = 0.f;
+  for (int64_t t = p0 + threadIdx.x; t < p1; t += kBwdWThreads) {
+    const int64_t i = t % V;
+    const int bb = (int)(t / V);
+    const int ix = (int)(i % D), iy = (int)((i / D) % D), iz = (int)(i / ((int64_t)D * D));
+    const float xv = x[((int64_t)bb * Ci + ci) * V + i];
+    const float* yc = dy + ((int64_t)bb * Co + co) * Do * Do * Do;
+#pragma unroll
+    for (int kz = 0; kz < 4; ++kz) {
+      const int oz = 2 * iz - 1 + kz;
+#pragma unroll
+      for (int ky = 0; ky < 4; ++ky) {
+        const int oy = 2 * iy - 1 + ky;
+#pragma unroll
+        for (int kx = 0; kx < 4; ++kx) {
+          const int ox = 2 * ix - 1 + kx;
+          if (oz >= 0 && oz < Do && oy >= 0 && oy < Do && ox >= 0 && ox < Do)
+            acc[(kz * 4 + ky) * 4 + kx] = fmaf(xv, yc[((int64_t)oz * Do + oy) * Do + ox], acc[(kz * 4 + ky) * 4 + kx]);
+        }
+      }
+    }
   }
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int st = 128; st > 0; st >>= 1) {
-    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+  // two halves of 32 taps through shared memory
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) red[threadIdx.x][k] = acc[32 * h + k];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      float s = 0.f;
+      for (int q = 0; q < kBwdWThreads; ++q) s += red[q][threadIdx.x];
+      part[(((int64_t)blockIdx.y * Ci + ci) * Co + co) * 64 + 32 * h + threadIdx.x] = s;
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) dw[widx] = red[0];
+}
+
+// dw[q] = sum over chunks of part[chunk][q] (chunk order), q over Ci Co 64.
+__global__ void convT_bwd_w_final_kernel(const float* __restrict__ part, int nchunk, int64_t n, float* __restrict__ dw) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  float s = 0.f;
+  for (int c = 0; c < nchunk; ++c) s += part[(int64_t)c * n + q];
+  dw[q] = s;
 }
 
 // per-channel sums of dy [B][Co][V] -> db [Co] in two fixed-order passes: block (co, b) writes
@@ -471,9 +503,9 @@ void nn_convT_fwd(const float* x, const float* w, const float* b, float* a, floa
   }
 }
 void nn_convT_bwd(const float* x, const float* w, const float* dy, float* dx, float* dw, float* db, int B, int Ci,
-                  int Co, int D, float* part, cudaStream_t s) {
+                  int Co, int D, float* part, float* wpart, cudaStream_t s) {
   allow_conv_smem();
-  note_launch(dx ? 4 : 3);
+  note_launch(dx ? 5 : 4);
   if (dx) {
     const int64_t n = (int64_t)B * D * D * D;
     const size_t sm = sizeof(float) * Ci * Co * 64;
@@ -482,7 +514,18 @@ void nn_convT_bwd(const float* x, const float* w, const float* dy, float* dx, fl
     else
       convT_bwd_data_kernel<16><<<gsb(n), 256, sm, s>>>(dy, w, dx, B, Co, D);
   }
-  convT_bwd_w_kernel<<<Ci * Co * 64, 256, 0, s>>>(x, dy, dw, B, Ci, Co, D);
+  {
+    // enough (ci, co, chunk) blocks for every SM twice, chunks of whole thread rounds, at most
+    // kConvChunks chunks (the workspace holds kConvChunks x Ci x Co x 64 partial sums)
+    const int64_t total = (int64_t)B * D * D * D;
+    int nchunk = (int)std::min<int64_t>(kConvChunks, std::max<int64_t>(1, (2 * 152 + Ci * Co - 1) / (Ci * Co)));
+    int64_t chunk = (total + nchunk - 1) / nchunk;
+    chunk = (chunk + kBwdWThreads - 1) / kBwdWThreads * kBwdWThreads;
+    nchunk = (int)((total + chunk - 1) / chunk);
+    convT_bwd_w_kernel<<<dim3(Ci * Co, nchunk), kBwdWThreads, 0, s>>>(x, dy, wpart, B, Ci, Co, D, chunk);
+    const int64_t n = (int64_t)Ci * Co * 64;
+    convT_bwd_w_final_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(wpart, nchunk, n, dw);
+  }
   chansum_kernel<<<dim3(Co, B), 256, 0, s>>>(dy, B, Co, (int64_t)8 * D * D * D, part);
   chansum_final_kernel<<<1, 32, 0, s>>>(part, B, Co, db);
 }

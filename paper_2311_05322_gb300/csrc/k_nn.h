@@ -16,9 +16,11 @@ void nn_colsum(const float* dz, int B, int N, float* db, cudaStream_t s);
 void nn_relu_back(const float* z, const float* dh, float* dz, int64_t n, cudaStream_t s);
 void nn_convT_fwd(const float* x, const float* w, const float* b, float* a, float* g, int B, int Ci, int Co, int D,
                   cudaStream_t s);
-// part: B * Co floats of per-(channel, sample) partial sums for the bias gradient.
+// part: B * Co floats of per-(channel, sample) partial sums for the bias gradient; wpart:
+// kConvChunks * Ci * Co * 64 floats of partial weight-gradient sums.
+constexpr int kConvChunks = 64;
 void nn_convT_bwd(const float* x, const float* w, const float* dy, float* dx, float* dw, float* db, int B, int Ci,
-                  int Co, int D, float* part, cudaStream_t s);
+                  int Co, int D, float* part, float* wpart, cudaStream_t s);
 void nn_mse(const float* y, const float* t, int64_t n, float* dy, double* part, double* loss, cudaStream_t s);
 void nn_adam(float* th, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps, int step,
              cudaStream_t s);

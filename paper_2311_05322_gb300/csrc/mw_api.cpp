@@ -170,6 +170,7 @@ struct NnState {
         *a2 = nullptr, *g2 = nullptr, *y = nullptr, *t = nullptr;
   float* gws = nullptr;       // split-K partial sums of the dense layers [32][bcap][1024]
   float* cpart = nullptr;     // per-(channel, sample) partial bias sums [bcap][16]
+  float* wpart = nullptr;     // partial weight-gradient sums of the decoder [kConvChunks][16][16][64]
   float *dy = nullptr, *dg2 = nullptr, *da2 = nullptr, *dg1 = nullptr, *da1 = nullptr, *dh2 = nullptr,
         *dz2 = nullptr, *dh1 = nullptr, *dz1 = nullptr;
   double *part = nullptr, *loss = nullptr;
@@ -3424,7 +3425,7 @@ static void nn_free(Ctx* c) {
                   (void*)n.h1, (void*)n.z2, (void*)n.h2, (void*)n.a1, (void*)n.g1, (void*)n.a2, (void*)n.g2,
                   (void*)n.y, (void*)n.t, (void*)n.dy, (void*)n.dg2, (void*)n.da2, (void*)n.dg1, (void*)n.da1,
                   (void*)n.dh2, (void*)n.dz2, (void*)n.dh1, (void*)n.dz1, (void*)n.part, (void*)n.loss,
-                  (void*)n.gws, (void*)n.cpart,
+                  (void*)n.gws, (void*)n.cpart, (void*)n.wpart,
                   (void*)n.data_x, (void*)n.data_t, (void*)n.idx})
     dfree(c, p);
   n = NnState();
@@ -3436,8 +3437,9 @@ static void nn_batch_buffers(Ctx* c, int B) {
   for (void* p : {(void*)n.x, (void*)n.z1, (void*)n.h1, (void*)n.z2, (void*)n.h2, (void*)n.a1, (void*)n.g1, (void*)n.a2,
                   (void*)n.g2, (void*)n.y, (void*)n.t, (void*)n.dy, (void*)n.dg2, (void*)n.da2, (void*)n.dg1,
                   (void*)n.da1, (void*)n.dh2, (void*)n.dz2, (void*)n.dh1, (void*)n.dz1, (void*)n.idx, (void*)n.gws,
-                  (void*)n.cpart})
+                  (void*)n.cpart, (void*)n.wpart})
     dfree(c, p);
+  n.wpart = dalloc<float>(c, (size_t)mwk::kConvChunks * 16 * 16 * 64);
   n.gws = dalloc<float>(c, (size_t)32 * B * kHid);
   n.cpart = dalloc<float>(c, (size_t)16 * B);
   n.x = dalloc<float>(c, (size_t)B * n.n_in);
@@ -3508,11 +3510,11 @@ static void nn_backward(Ctx* c, int B) {
     // flops; the first layer's input gradient is the reshaped dh2), ReLU masks between them
     ProfScope ps(c, MW_K_NN_CONV, 4.0 * Bd * (kOut + 3 * 2 * 8 * 4096 + 3 * 2 * 16 * 512 + 2 * H),
                  4.0 * 64 * Bd * (16 * 16 * 64 + 16 * 8 * 512 + 8 * 2 * 4096));
-    mwk::nn_convT_bwd(n.g2, th + n.oC3, n.dy, n.dg2, g + n.oC3, g + n.oc3, B, 8, 2, 16, n.cpart, s);
+    mwk::nn_convT_bwd(n.g2, th + n.oC3, n.dy, n.dg2, g + n.oC3, g + n.oc3, B, 8, 2, 16, n.cpart, n.wpart, s);
     mwk::nn_relu_back(n.a2, n.dg2, n.da2, (int64_t)B * 8 * 4096, s);
-    mwk::nn_convT_bwd(n.g1, th + n.oC2, n.da2, n.dg1, g + n.oC2, g + n.oc2, B, 16, 8, 8, n.cpart, s);
+    mwk::nn_convT_bwd(n.g1, th + n.oC2, n.da2, n.dg1, g + n.oC2, g + n.oc2, B, 16, 8, 8, n.cpart, n.wpart, s);
     mwk::nn_relu_back(n.a1, n.dg1, n.da1, (int64_t)B * 16 * 512, s);
-    mwk::nn_convT_bwd(n.h2, th + n.oC1, n.da1, n.dh2, g + n.oC1, g + n.oc1, B, 16, 16, 4, n.cpart, s);
+    mwk::nn_convT_bwd(n.h2, th + n.oC1, n.da1, n.dh2, g + n.oC1, g + n.oc1, B, 16, 16, 4, n.cpart, n.wpart, s);
   }
   // dW2 = dz2^T h1, dh1 = dz2 W2 (BF16 W2), dW1 = dz1^T x; bias sums and ReLU masks between
   ProfScope ps(c, MW_K_NN_GEMM, 4.0 * H * (H + ni) + 2.0 * H * H + 4.0 * Bd * (ni + 6 * H) + 8.0 * H,
