@@ -166,6 +166,27 @@ __global__ void mf_rhs_kernel(const int32_t* __restrict__ nodes, const int64_t* 
   }
 }
 
+// Front right-hand sides as a pull: arena row out[i] = sum over src[ptr[i] .. ptr[i+1]) of the
+// arena row src (>= 0) or input row -(src + 1), in list order (input first, then the children
+// in child order, as the multifrontal forward sweep assembles them).  One thread per (row,
+// column): a row's R columns are contiguous, so each source row is read coalesced.
+__global__ void mf_pull_kernel(const int64_t* __restrict__ out, const int64_t* __restrict__ ptr,
+                               const int64_t* __restrict__ src, int64_t n, const float2* __restrict__ in, int R,
+                               float2* __restrict__ arena) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * R; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / R;
+    const int c = (int)(t - i * R);
+    float sx = 0.f, sy = 0.f;
+    for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) {
+      const int64_t g = src[q];
+      const float2 v = g >= 0 ? arena[g * R + c] : in[(-g - 1) * R + c];
+      sx += v.x;
+      sy += v.y;
+    }
+    arena[out[i] * R + c] = make_float2(sx, sy);
+  }
+}
+
 // Task-list GEMM: C = C0 + sign * A B for every task, A [m][k] (row stride lda) in the factor
 // store, B [k][R] and C, C0 [m][R] in the vector arena.  Rows of B and C are either consecutive
 // from an arena row or listed (b_idx / c_idx; a negative C row is skipped).  A CTA of 128
@@ -401,6 +422,14 @@ void mf_reduce(const MfTask* tasks, const MfSplit* splits, int n_splits, const f
   mf_reduce_kernel<<<n_splits, 256, 0, s>>>(tasks, splits, partial, idx, R, arena);
 }
 
+void mf_pull(const int64_t* out, const int64_t* ptr, const int64_t* src, int64_t n, const float2* in, int R,
+             float2* arena, cudaStream_t s) {
+  if (n <= 0) return;
+  note_launch(1);
+  const int64_t thr = n * R;
+  const int blocks = (int)std::min<int64_t>((thr + 255) / 256, 152 * 16);
+  mf_pull_kernel<<<blocks, 256, 0, s>>>(out, ptr, src, n, in, R, arena);
+}
 void mf_owned(const int32_t* own_glob, const int64_t* own_row, int64_t n_own, const float2* arena, int R, float2* z,
               cudaStream_t s) {
   if (n_own <= 0) return;

@@ -52,6 +52,10 @@ void mf_rhs(const int32_t* nodes, int n_nodes, int64_t fmax, const int64_t* f, c
             const int64_t* piv_ptr, const int32_t* piv_glob, const int64_t* child_ptr, const int32_t* child,
             const int64_t* inv_off, const int32_t* inv, const int64_t* rhs_row, const int64_t* w_row,
             const float2* in, int R, float2* arena, cudaStream_t s);
+// Front right-hand sides of one forward height as pull lists: arena row out[i] = sum of its
+// listed arena rows (src >= 0) and input rows (-(src + 1)), for i < n (ptr relative to src).
+void mf_pull(const int64_t* out, const int64_t* ptr, const int64_t* src, int64_t n, const float2* in, int R,
+             float2* arena, cudaStream_t s);
 // Tiles of one height (and direction) then, when some K ranges are split, the reduction of
 // their partial slots.
 void mf_gemm(const MfTask* tasks, const MfTile* tiles, int n_tiles, const MfSplit* splits, int n_splits,

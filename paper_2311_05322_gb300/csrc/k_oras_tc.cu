@@ -131,8 +131,9 @@ __global__ void pack_w_kernel(const int64_t* __restrict__ nmat, const int64_t* _
   }
 }
 
-// The same tiles from strided FP32 blocks: "subdomain" q of the plan is the product A_q [m][k]
-// (row stride lda, at element a_off of src), one block per (q, m tile, k tile).
+// The same tiles from strided FP32 blocks: "subdomain" q of the plan is the product sign_q A_q
+// [m][k] (row stride lda, at element a_off of src; the sign of the task, +1 or -1, is exact in
+// BF16), one block per (q, m tile, k tile).
 __global__ void pack_w_blocks_kernel(const MfTask* __restrict__ tasks, int q0, const int64_t* __restrict__ sub_wtile,
                                      const int32_t* __restrict__ sub_kt, const float2* __restrict__ src,
                                      uint8_t* __restrict__ W) {
@@ -151,12 +152,12 @@ __global__ void pack_w_blocks_kernel(const MfTask* __restrict__ tasks, int q0, c
     if (row < t.m) {
       const float2* a = src + t.a_off + row * t.lda;
       if (k < t.k) {
-        re0 = a[k].x;
-        im0 = a[k].y;
+        re0 = t.sign * a[k].x;
+        im0 = t.sign * a[k].y;
       }
       if (k + 1 < t.k) {
-        re1 = a[k + 1].x;
-        im1 = a[k + 1].y;
+        re1 = t.sign * a[k + 1].x;
+        im1 = t.sign * a[k + 1].y;
       }
     }
     *reinterpret_cast<uint32_t*>(tr + swz(r, 2 * kp)) = pack_bf16(re0, re1);
@@ -242,6 +243,7 @@ struct TcArgs {
   const int32_t* sub_kt;
   const int64_t* own_ptr;
   const int32_t* own_glob;
+  const int32_t* c0_glob;   // optional: row of z added to each output row (-1: none)
   const uint8_t* W;
   const uint8_t* Bt;
   float2* z;
@@ -356,24 +358,33 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int64_t nown = a.own_ptr[s + 1] - a.own_ptr[s];
     const int64_t q = (int64_t)row0 + row;
-    const bool valid = ok && !abort_flag && q < nown;
-    float2* zr = valid ? a.z + (int64_t)a.own_glob[a.own_ptr[s] + q] * a.R : nullptr;
+    const int64_t og = (ok && !abort_flag && q < nown) ? (int64_t)a.own_glob[a.own_ptr[s] + q] : -1;
+    const bool valid = og >= 0;          // a negative output row is skipped
+    float2* zr = valid ? a.z + og * a.R : nullptr;
+    const int64_t c0 = (valid && a.c0_glob) ? (int64_t)a.c0_glob[a.own_ptr[s] + q] : -1;
+    const float2* c0r = c0 >= 0 ? a.z + c0 * a.R : nullptr;
     const int Rp = a.N / 2;
     const uint32_t lanes = tmem + ((uint32_t)(quad * 32) << 16);
-    for (int c0 = 0; c0 < Rp; c0 += 8) {
-      // Re z = D1[c] - D2[Rp + c], Im z = D1[Rp + c] + D2[c]
+    for (int cb = 0; cb < Rp; cb += 8) {
+      // Re z = D1[c] - D2[Rp + c], Im z = D1[Rp + c] + D2[c] (plus the C0 row when given)
       float rr[8], ri[8], ir[8], ii[8];
       if (ok) {
-        tmem_ld8(lanes + (uint32_t)c0, rr);                          // Wr gr
-        tmem_ld8(lanes + (uint32_t)(Rp + c0), ri);                   // Wr gi
-        tmem_ld8(lanes + (uint32_t)(a.N + c0), ir);                  // Wi gr
-        tmem_ld8(lanes + (uint32_t)(a.N + Rp + c0), ii);             // Wi gi
+        tmem_ld8(lanes + (uint32_t)cb, rr);                          // Wr gr
+        tmem_ld8(lanes + (uint32_t)(Rp + cb), ri);                   // Wr gi
+        tmem_ld8(lanes + (uint32_t)(a.N + cb), ir);                  // Wi gr
+        tmem_ld8(lanes + (uint32_t)(a.N + Rp + cb), ii);             // Wi gi
       }
       if (valid) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int col = c0 + i;
-          if (col < a.R) zr[col] = make_float2(rr[i] - ii[i], ri[i] + ir[i]);
+          const int col = cb + i;
+          if (col >= a.R) continue;
+          float2 v = make_float2(rr[i] - ii[i], ri[i] + ir[i]);
+          if (c0r) {
+            const float2 b = c0r[col];
+            v = make_float2(v.x + b.x, v.y + b.y);
+          }
+          zr[col] = v;
         }
       }
     }
@@ -518,7 +529,7 @@ int tc_max_stages(int R) {
 }
 
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
-                   void* scratch, cudaStream_t s, int stages, const double* in_scale) {
+                   void* scratch, cudaStream_t s, int stages, const double* in_scale, const int32_t* c0_glob) {
   const int Rp = rpad(R);
   const int N = 2 * Rp;
   if (stages <= 0) stages = tc_stages(N);
@@ -542,6 +553,7 @@ void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const flo
   a.sub_kt = p.sub_kt;
   a.own_ptr = tp.own_ptr;
   a.own_glob = tp.own_glob;
+  a.c0_glob = c0_glob;
   a.W = (const uint8_t*)W;
   a.Bt = (const uint8_t*)scratch;
   a.z = z;

@@ -82,6 +82,10 @@ struct Prec {
     mwk::MfTask* tasks = nullptr;
     mwk::MfTile* tiles = nullptr;
     mwk::MfSplit* splits = nullptr;
+    // front right-hand sides of the forward sweep as pull lists: output arena row, and its
+    // contributions (>= 0: arena row of a child's update; < 0: input row -(g + 1)), per height
+    int64_t *pull_out = nullptr, *pull_ptr = nullptr, *pull_src = nullptr;
+    std::vector<int64_t> pull_h;     // [H + 2] output-row ranges per height
     std::vector<int64_t> fwd_splits, bwd_splits;  // [H + 2] split ranges per height
     int64_t max_slots = 0;                         // partial slots of the largest launch
     std::vector<int64_t> sh_ptr;     // [(n_sub * (H + 1)) + 1] node ranges per (subdomain, height)
@@ -98,6 +102,7 @@ struct Prec {
       mwk::TcPlan plan;
       int64_t *dof_ptr = nullptr, *own_ptr = nullptr;
       int32_t *dofs = nullptr, *own_local = nullptr, *own_glob = nullptr;
+      int32_t* c0_glob = nullptr;    // per output row: arena row of C0, or -1
       mwk::MfTask* tasks = nullptr;  // products with K > 0 (plan order), then those with K = 0
       mwk::MfSplit* splits = nullptr;
       int n_tc = 0, n_splits = 0, ktmax = 0, mtmax = 0;
@@ -519,16 +524,17 @@ void apply_sparse(Ctx* c, int f, const float2* v, float2* z, int R) {
   if (c->prec.apply_prec == 5) {
     auto run = [&](Prec::Mf::TcLaunch& L) {
       if (L.n_tc > 0) {
+        // C = C0 + (sign A) B straight from the MMA epilogue into the arena
         const mwk::OrasTopo tp{L.dof_ptr, L.dofs, L.own_ptr, L.own_local, L.own_glob, nullptr, nullptr, nullptr,
                                nullptr, nullptr, nullptr};
-        mwk::oras_apply_tc(L.plan, tp, L.W[f], arena, partial, R, w.tc_scratch, s);
+        mwk::oras_apply_tc(L.plan, tp, L.W[f], arena, arena, R, w.tc_scratch, s, 0, nullptr, L.c0_glob);
       }
-      mwk::mf_reduce(L.tasks, L.splits, L.n_splits, partial, m.idx, R, arena, s);
+      // products with K = 0: C = C0
+      if (L.n_splits > 0) mwk::mf_reduce(L.tasks, L.splits, L.n_splits, partial, m.idx, R, arena, s);
     };
     for (int h = 0; h <= H; ++h) {
-      const int64_t n0 = m.h_ptr[h], n1 = m.h_ptr[h + 1];
-      mwk::mf_rhs(m.h_nodes + n0, (int)(n1 - n0), m.h_fmax[h], m.f, m.preal, m.piv_ptr, m.piv_glob, m.child_ptr,
-                  m.child, m.inv_off, m.inv, m.rhs_row, m.w_row, v, R, arena, s);
+      mwk::mf_pull(m.pull_out + m.pull_h[h], m.pull_ptr + m.pull_h[h], m.pull_src, m.pull_h[h + 1] - m.pull_h[h], v,
+                   R, arena, s);
       run(m.tcl[h]);
     }
     for (int h = H; h >= 0; --h) run(m.tcl[H + 1 + h]);
@@ -537,9 +543,8 @@ void apply_sparse(Ctx* c, int f, const float2* v, float2* z, int R) {
   }
   const float2* fac = (const float2*)m.fac[f];
   for (int h = 0; h <= H; ++h) {
-    const int64_t n0 = m.h_ptr[h], n1 = m.h_ptr[h + 1];
-    mwk::mf_rhs(m.h_nodes + n0, (int)(n1 - n0), m.h_fmax[h], m.f, m.preal, m.piv_ptr, m.piv_glob, m.child_ptr,
-                m.child, m.inv_off, m.inv, m.rhs_row, m.w_row, v, R, arena, s);
+    mwk::mf_pull(m.pull_out + m.pull_h[h], m.pull_ptr + m.pull_h[h], m.pull_src, m.pull_h[h + 1] - m.pull_h[h], v, R,
+                 arena, s);
     mwk::mf_gemm(m.tasks, m.tiles + m.fwd_tiles[h], (int)(m.fwd_tiles[h + 1] - m.fwd_tiles[h]),
                  m.splits + m.fwd_splits[h], (int)(m.fwd_splits[h + 1] - m.fwd_splits[h]), fac, m.idx, R, arena,
                  partial, s);
@@ -607,6 +612,29 @@ void setup_sparse(Ctx* c) {
       }
     m.h_ptr.push_back((int64_t)h_nodes.size());
   }
+  // pull lists of the front right-hand sides: row r of node k sums its input entry (a real
+  // pivot) and the children's update rows mapped to r, in child order.  The update rows of a
+  // leaf receive nothing (they are zero), so they are not listed, and its w product has no C0.
+  std::vector<int64_t> pull_out, pull_ptr(1, 0), pull_src;
+  m.pull_h.assign(1, 0);
+  for (int h = 0; h <= H; ++h) {
+    for (int64_t q = m.h_ptr[h]; q < m.h_ptr[h + 1]; ++q) {
+      const int k = h_nodes[q];
+      const bool leaf = y.child_ptr[k + 1] == y.child_ptr[k];
+      const int64_t nr = leaf ? y.p[k] : y.f[k];
+      for (int64_t r = 0; r < nr; ++r) {
+        pull_out.push_back(rhs_row[k] + r);
+        if (r < y.preal[k]) pull_src.push_back(-(int64_t)piv_glob[y.piv_ptr[k] + r] - 1);
+        for (int64_t cq = y.child_ptr[k]; cq < y.child_ptr[k + 1]; ++cq) {
+          const int32_t ch = y.child[cq];
+          const int32_t a = y.inv[y.inv_off[ch] + r];
+          if (a >= 0) pull_src.push_back(w_row[ch] + a);
+        }
+        pull_ptr.push_back((int64_t)pull_src.size());
+      }
+    }
+    m.pull_h.push_back((int64_t)pull_out.size());
+  }
   m.sh_ptr.assign(1, 0);
   for (int s = 0; s < S; ++s)
     for (int h = 0; h <= H; ++h) {
@@ -671,8 +699,9 @@ void setup_sparse(Ctx* c) {
       const int k = h_nodes[q];
       const int64_t p = y.p[k], u = y.u[k], ff = y.f[k];
       if (p > 0) tl.push_back({y.fac_off[k], ff, p, p, rhs_row[k], -1, t_row[k], -1, -1, 1.f, 0});
+      const bool leaf = y.child_ptr[k + 1] == y.child_ptr[k];
       if (u > 0) tl.push_back({y.fac_off[k] + p * ff, std::max<int64_t>(p, 1), u, p, rhs_row[k], -1, w_row[k], -1,
-                               rhs_row[k] + p, 1.f, 0});
+                               leaf ? -1 : rhs_row[k] + p, 1.f, 0});
     }
     emit_launch(tl);
     m.fwd_tiles.push_back((int64_t)tiles.size());
@@ -745,6 +774,9 @@ void setup_sparse(Ctx* c) {
       if (t.c0_row >= 0) require(t.c0_row + t.m <= rows, MW_EINVAL, bad);
     }
     for (int64_t r : own_row) require(r >= 0 && r < rows, MW_EINVAL, bad);
+    for (int64_t r : pull_out) require(r >= 0 && r < rows, MW_EINVAL, bad);
+    for (int64_t r : pull_src) require(r < rows && -r - 1 < c->topo.n_edge, MW_EINVAL, bad);
+    require(pull_ptr.size() == pull_out.size() + 1 && pull_ptr.back() == (int64_t)pull_src.size(), MW_EINVAL, bad);
     for (const mwk::MfTile& tl : tiles) {
       require(tl.task >= 0 && tl.task < (int32_t)tasks.size() && tl.row0 >= 0 && tl.row0 < std::max<int64_t>(tasks[tl.task].m, 1),
               MW_EINVAL, bad);
@@ -764,6 +796,9 @@ void setup_sparse(Ctx* c) {
   m.rhs_row = mf_up(c, m, rhs_row);
   m.w_row = mf_up(c, m, w_row);
   m.own_row = mf_up(c, m, own_row);
+  m.pull_out = mf_up(c, m, pull_out);
+  m.pull_ptr = mf_up(c, m, pull_ptr);
+  m.pull_src = mf_up(c, m, pull_src.empty() ? std::vector<int64_t>(1, 0) : pull_src);
   m.asm_ptr = mf_up(c, m, y.asm_ptr);
   m.asm_target = mf_up(c, m, y.asm_target);
   m.sh_f = mf_up(c, m, sh_f);
@@ -833,9 +868,10 @@ void setup_sparse(Ctx* c) {
 }
 
 // BF16 tensor-core form of the sweeps: per launch, a tile plan whose "subdomains" are the
-// products with K > 0 (inputs: the arena rows of B; outputs: partial slots, one per 64 rows),
-// the BF16 tiles of their FP32 factor blocks for every frequency, and one reduction split per
-// 64-row tile of every product (none for K = 0, so C = C0).  The FP32 factors are then freed.
+// products with K > 0 (inputs: the arena rows of B; outputs: the arena rows of C, with the
+// arena rows of C0 added in the MMA epilogue), the BF16 tiles of their FP32 factor blocks times
+// the product's sign for every frequency, and one reduction split per 64-row tile of the
+// products with K = 0 (C = C0).  The FP32 factors are then freed.
 void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launches, const std::vector<int32_t>& idx) {
   Prec& P = c->prec;
   Prec::Mf& m = P.mf;
@@ -853,7 +889,7 @@ void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launch
     fake.n_sub = T.n_tc;
     fake.dof_ptr.assign(1, 0);
     fake.own_ptr.assign(1, 0);
-    std::vector<int32_t> own_glob;
+    std::vector<int32_t> own_glob, c0_glob;
     std::vector<mwk::MfSplit> sp;
     int64_t slot = 0;
     for (int q = 0; q < (int)ord.size(); ++q) {
@@ -866,16 +902,19 @@ void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launch
         }
         fake.dof_ptr.push_back((int64_t)fake.dofs.size());
         for (int64_t r = 0; r < t.m; ++r) {
+          const int64_t crow = t.c_idx >= 0 ? (int64_t)idx[t.c_idx + r] : t.c_row + r;
+          const int64_t c0 = t.c0_row >= 0 ? t.c0_row + r : -1;
+          require(crow >= -1 && crow < m.arena_rows && c0 >= -1 && c0 < m.arena_rows, MW_EINVAL, bad);
           fake.own_local.push_back((int32_t)r);
-          own_glob.push_back((int32_t)(slot * mwk::kMfTileRows + r));
+          own_glob.push_back((int32_t)crow);
+          c0_glob.push_back((int32_t)c0);
         }
         fake.own_ptr.push_back((int64_t)fake.own_local.size());
         T.ktmax = std::max<int>(T.ktmax, (int)((t.k + 63) / 64));
         T.mtmax = std::max<int>(T.mtmax, (int)((t.m + 127) / 128));
+        continue;
       }
-      for (int64_t r0 = 0; r0 < t.m; r0 += mwk::kMfTileRows)
-        sp.push_back({q, (int32_t)r0, q < T.n_tc ? (int32_t)(slot + r0 / mwk::kMfTileRows) : 0, q < T.n_tc ? 1 : 0});
-      if (q < T.n_tc) slot += (t.m + mwk::kMfTileRows - 1) / mwk::kMfTileRows;
+      for (int64_t r0 = 0; r0 < t.m; r0 += mwk::kMfTileRows) sp.push_back({q, (int32_t)r0, 0, 0});
     }
     require(slot * mwk::kMfTileRows < INT32_MAX, MW_EINVAL, bad);
     m.tc_slots = std::max<int64_t>(m.tc_slots, slot);
@@ -888,6 +927,7 @@ void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launch
     T.own_ptr = mf_up(c, m, fake.own_ptr);
     T.own_local = mf_up(c, m, fake.own_local);
     T.own_glob = mf_up(c, m, own_glob);
+    T.c0_glob = mf_up(c, m, c0_glob);
     require(mwk::tc_plan_build(T.plan, fake, [&](size_t b) { return (void*)dalloc<unsigned char>(c, b); }, c->stream),
             MW_EINVAL, "tensor-core plan of the sparse sweeps");
     m.tc_scratch = std::max(m.tc_scratch, mwk::tc_scratch_bytes(T.plan, 128));
