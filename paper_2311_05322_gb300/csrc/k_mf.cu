@@ -187,6 +187,36 @@ __global__ void mf_pull_kernel(const int64_t* __restrict__ out, const int64_t* _
   }
 }
 
+// The same pull with 4 consecutive complex columns per thread (R a multiple of 4): 32-byte loads
+// and stores, and several rows per warp whose index chains run side by side.  The sums are the
+// same, in the same order.
+__global__ void mf_pull4_kernel(const int64_t* __restrict__ out, const int64_t* __restrict__ ptr,
+                                const int64_t* __restrict__ src, int64_t n, const float2* __restrict__ in, int R,
+                                float2* __restrict__ arena) {
+  const int tpr = R / 4;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * tpr) return;
+  const int64_t i = t / tpr;
+  const int c = (int)(t - i * tpr) * 4;
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;    // columns c, c+1 and c+2, c+3
+  for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) {
+    const int64_t g = src[q];
+    const float4* v = reinterpret_cast<const float4*>(g >= 0 ? arena + g * R + c : in + (-g - 1) * R + c);
+    const float4 v0 = v[0], v1 = v[1];
+    a.x += v0.x;
+    a.y += v0.y;
+    a.z += v0.z;
+    a.w += v0.w;
+    b.x += v1.x;
+    b.y += v1.y;
+    b.z += v1.z;
+    b.w += v1.w;
+  }
+  float4* o = reinterpret_cast<float4*>(arena + out[i] * R + c);
+  o[0] = a;
+  o[1] = b;
+}
+
 // Task-list GEMM: C = C0 + sign * A B for every task, A [m][k] (row stride lda) in the factor
 // store, B [k][R] and C, C0 [m][R] in the vector arena.  Rows of B and C are either consecutive
 // from an arena row or listed (b_idx / c_idx; a negative C row is skipped).  A CTA of 128
@@ -426,6 +456,12 @@ void mf_pull(const int64_t* out, const int64_t* ptr, const int64_t* src, int64_t
              float2* arena, cudaStream_t s) {
   if (n <= 0) return;
   note_launch(1);
+  if (R % 4 == 0 && R <= 128 && (((uintptr_t)in | (uintptr_t)arena) & 15) == 0) {
+    // 4 complex columns per thread: a warp takes 32 / (R / 4) rows with independent load chains
+    const int64_t thr = n * (R / 4);
+    mf_pull4_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(out, ptr, src, n, in, R, arena);
+    return;
+  }
   const int64_t thr = n * R;
   const int blocks = (int)std::min<int64_t>((thr + 255) / 256, 152 * 16);
   mf_pull_kernel<<<blocks, 256, 0, s>>>(out, ptr, src, n, in, R, arena);

@@ -349,24 +349,35 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
       mma_commit(&done_bar);
     }
   } else {
-    // epilogue: warps 2..5 cover tensor-memory lane quadrants (warp % 4)
+    // epilogue: warps 2..5 cover tensor-memory lane quadrants (warp % 4).  The output row, the C0
+    // row and C0's first 8 columns are looked up while the MMAs run.
     const int quad = warp & 3;
     const int row = quad * 32 + lane;
+    const int64_t nown = a.own_ptr[s + 1] - a.own_ptr[s];
+    const int64_t q = (int64_t)row0 + row;
+    const int64_t og = q < nown ? (int64_t)a.own_glob[a.own_ptr[s] + q] : -1;   // negative: skipped
+    const int64_t c0 = (og >= 0 && a.c0_glob) ? (int64_t)a.c0_glob[a.own_ptr[s] + q] : -1;
+    const float2* c0r = c0 >= 0 ? a.z + c0 * a.R : nullptr;
+    float2 nxt[8];
+    auto fetch_c0 = [&](int cb) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) nxt[i] = (c0r && cb + i < a.R) ? c0r[cb + i] : make_float2(0.f, 0.f);
+    };
+    fetch_c0(0);
     bool ok = mbar_wait(&done_bar, 0);
     ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
     if (!ok && lane == 0) atomicCAS(a.err, 0, 4);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int64_t nown = a.own_ptr[s + 1] - a.own_ptr[s];
-    const int64_t q = (int64_t)row0 + row;
-    const int64_t og = (ok && !abort_flag && q < nown) ? (int64_t)a.own_glob[a.own_ptr[s] + q] : -1;
-    const bool valid = og >= 0;          // a negative output row is skipped
+    const bool valid = ok && !abort_flag && og >= 0;
     float2* zr = valid ? a.z + og * a.R : nullptr;
-    const int64_t c0 = (valid && a.c0_glob) ? (int64_t)a.c0_glob[a.own_ptr[s] + q] : -1;
-    const float2* c0r = c0 >= 0 ? a.z + c0 * a.R : nullptr;
     const int Rp = a.N / 2;
     const uint32_t lanes = tmem + ((uint32_t)(quad * 32) << 16);
     for (int cb = 0; cb < Rp; cb += 8) {
       // Re z = D1[c] - D2[Rp + c], Im z = D1[Rp + c] + D2[c] (plus the C0 row when given)
+      float2 cur[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) cur[i] = nxt[i];
+      if (cb + 8 < Rp) fetch_c0(cb + 8);
       float rr[8], ri[8], ir[8], ii[8];
       if (ok) {
         tmem_ld8(lanes + (uint32_t)cb, rr);                          // Wr gr
@@ -380,10 +391,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
           const int col = cb + i;
           if (col >= a.R) continue;
           float2 v = make_float2(rr[i] - ii[i], ri[i] + ir[i]);
-          if (c0r) {
-            const float2 b = c0r[col];
-            v = make_float2(v.x + b.x, v.y + b.y);
-          }
+          if (c0r) v = make_float2(v.x + cur[i].x, v.y + cur[i].y);
           zr[col] = v;
         }
       }
