@@ -537,6 +537,28 @@ def config3_leg(a, local, stream, alu, hbm, src, steps=3, warmup=2):
             "clocks": clocks, "setup_s": L["setup"], "J_last": J}
 
 
+def config2_sparse_leg(a, local, stream, alu, hbm, src, steps=3, warmup=3):
+    """The shoulder-scale configuration with its specified decomposition: 80x80x34 (1,558,914
+    edges), 32 dipoles, 16 subdomains of about 132k unknowns with 2 overlap layers, sparse
+    multifrontal subdomain solves with their sweeps on the tensor cores, GMRES-IR to 1e-8."""
+    a2 = _args(["--prec", "sparse_bf16", "--parts", "4x4x1", "--overlap", "2", "--alpha", str(a.alpha)])
+    L = _setup_leg(a2, local, stream)
+    sec, J, prof, launches, clocks = _timed_steps(L, a2, local, stream, steps, warmup, 1, None)
+    units = 2 * a2.n_src * len(L["freqs"])
+    ms = sec * 1e3
+    roof, _ = _dominant_roofline(prof, ms, hbm, src, L["prec"], a2, L)
+    info, sizes = L["info"], L["sizes"]
+    L["c"].close()
+    return {"value": units * steps / sec, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
+            "config": {"workload": f"shoulder phantom 80x80x34 Kuhn cells ({info.n_edge} edges), 32 z-dipoles, "
+                                   f"one inversion evaluation (forward+adjoint); 16 subdomains, 2 overlap layers",
+                       "rhs_solves_per_step": units, "subdomains": L["n_sub"], "n_s_mean": float(sizes.mean()),
+                       "n_s_max": int(sizes.max()),
+                       "preconditioner_apply": "bf16 tcgen05 multifrontal sweeps"},
+            "roofline": roof, "classes": rate_classes(prof, hbm, alu), "gpu_launches": int(launches),
+            "clocks": clocks, "setup_s": L["setup"], "J_last": J}
+
+
 def run_sharded(a, world, rank, local):
     """N > 1 (under torchrun, one process per GPU): one evaluation split by transmitter columns.
     Every rank holds the mesh, matrices and preconditioner; rank r solves its window of the
@@ -738,6 +760,7 @@ def run_mine(a):
     legs = {}
     if rank == 0 and world == 1 and not a.no_legs and ports is None and a.cells == "80x80x34" and a.prec == "bf16":
         for name, fn in (("config3", lambda: config3_leg(a, local, stream, alu, hbm, src)),
+                         ("config2_sparse", lambda: config2_sparse_leg(a, local, stream, alu, hbm, src)),
                          ("nn_training", lambda: nn_leg(local, stream, alu, hbm))):
             try:
                 legs[name] = fn()
