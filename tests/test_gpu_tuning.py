@@ -38,7 +38,9 @@ def test_autotune_report(box):
     m, eps = box
     c = _ctx(m, eps)
     r = c.autotune(32, mw.MW_MODE_MIXED, 50)
-    assert set(r["spmm_ms"]) == {128, 256, 512}
+    assert set(r["spmm_ms"]) == {1, 128, 256, 512}        # 1: the halo-tiled SpMM (32 columns: even)
+    r5 = c.autotune(5, mw.MW_MODE_MIXED, 50)
+    assert set(r5["spmm_ms"]) == {128, 256, 512}          # odd column counts take the row-per-warp kernel only
     assert set(r["dots_ms"]) == {2, 3, 4, 5, 6} and set(r["update_ms"]) == {2, 3, 4, 5, 6}
     assert min(r["tc_ms"]) == 2 and max(r["tc_ms"]) >= 4
     for chosen, table in (("spmm_threads", "spmm_ms"), ("dots_stages", "dots_ms"), ("update_stages", "update_ms"),
