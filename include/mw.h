@@ -72,7 +72,9 @@ typedef struct {
  *   batch     columns per Krylov launch; 0 = all columns of a frequency in one block launch.
  *   max_it    cap on Arnoldi steps per column over the whole solve.
  *   tol       target FP64 true relative residual ||b - A x||_2 / ||b||_2 per column.
- *   inner_tol mixed mode: relative residual reduction asked of each inner cycle.
+ *   inner_tol mixed mode: relative residual reduction asked of each inner cycle (default 1e-2:
+ *             short inner cycles over a shallow basis; the outer FP64 residual decides
+ *             convergence, so the result's tolerance does not depend on it).
  *   max_outer mixed mode: cap on outer refinement steps.
  *   use_precond 1 = ORAS (mw_setup_preconditioner first), 0 = unpreconditioned. */
 typedef struct {

@@ -1515,14 +1515,14 @@ mw_solve_opts norm_opts(const mw_solve_opts* o) {
   d.batch = 0;
   d.max_it = 5000;
   d.tol = 1e-8;
-  d.inner_tol = 1e-4;
+  d.inner_tol = 1e-2;
   d.max_outer = 20;
   d.use_precond = 1;
   if (o) d = *o;
   require(d.mode == MW_MODE_FP64 || d.mode == MW_MODE_MIXED, MW_EINVAL, "unknown solve mode");
   require(d.restart >= 1 && d.restart <= kMaxRestart, MW_EINVAL, "restart must be in [1, 63]");
   require(d.tol > 0 && d.max_it >= 1, MW_EINVAL, "tol > 0 and max_it >= 1 required");
-  if (d.inner_tol <= 0) d.inner_tol = 1e-4;
+  if (d.inner_tol <= 0) d.inner_tol = 1e-2;
   if (d.max_outer <= 0) d.max_outer = 20;
   return d;
 }

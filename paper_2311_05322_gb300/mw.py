@@ -180,7 +180,7 @@ def _c(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
-def solve_opts(mode=MW_MODE_FP64, restart=50, batch=0, max_it=5000, tol=1e-8, inner_tol=1e-4, max_outer=20,
+def solve_opts(mode=MW_MODE_FP64, restart=50, batch=0, max_it=5000, tol=1e-8, inner_tol=1e-2, max_outer=20,
                use_precond=1) -> mw_solve_opts:
     return mw_solve_opts(mode, restart, batch, max_it, tol, inner_tol, max_outer, use_precond)
 
