@@ -51,8 +51,9 @@ __global__ void __launch_bounds__(512) spmm_kernel(const int64_t* __restrict__ r
     if (c0 + q < R) yr[q] = acc[q];
 }
 
-// r = b - A x in FP64 with per-block, per-column partial sums of |r|^2 (deterministic).
-template <int CPL>
+// r = b - A x in FP64 with per-block, per-column partial sums of |r|^2 (deterministic).  ZX: x = 0
+// (the first outer step): the row sums are +0 and the row loop is skipped.
+template <int CPL, bool ZX>
 __global__ void __launch_bounds__(256) residual_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                                        const double2* __restrict__ A, const double2* __restrict__ X,
                                                        const double2* __restrict__ B, double2* __restrict__ Rv,
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const int64_t* __restrict
     double2 acc[CPL];
 #pragma unroll
     for (int q = 0; q < CPL; ++q) acc[q] = make_double2(0.0, 0.0);
-    for (int64_t k = rp[row]; k < rp[row + 1]; ++k) {
+    for (int64_t k = ZX ? 0 : rp[row]; k < (ZX ? 0 : rp[row + 1]); ++k) {
       const double2 a = A[k];
       const double2* xr = X + (int64_t)ci[k] * R + c0;
 #pragma unroll
@@ -242,19 +243,28 @@ void spmm_plan_values(const SpmmDev& p, const float2* A32, int64_t nnz, float2* 
 }
 
 int residual_f64(const int64_t* rp, const int32_t* ci, const double2* A, const double2* X, const double2* B,
-                 double2* Rv, double* part, int64_t E, int R, cudaStream_t s) {
+                 double2* Rv, double* part, int64_t E, int R, cudaStream_t s, bool zero_x) {
   note_launch(1);
   Shape sh = shape_for(R);
   const int blocks = 152 * 4;
   switch (sh.cpl) {
     case 1:
-      residual_kernel<1><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
+      if (zero_x)
+        residual_kernel<1, true><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
+      else
+        residual_kernel<1, false><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
       break;
     case 2:
-      residual_kernel<2><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
+      if (zero_x)
+        residual_kernel<2, true><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
+      else
+        residual_kernel<2, false><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
       break;
     default:
-      residual_kernel<4><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
+      if (zero_x)
+        residual_kernel<4, true><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
+      else
+        residual_kernel<4, false><<<blocks, 256, 0, s>>>(rp, ci, A, X, B, Rv, part, E, R, sh.tpr_log2);
       break;
   }
   return blocks;
@@ -382,8 +392,9 @@ __device__ __forceinline__ void df_add(float& a_h, float& a_l, float b_h, float 
 // start vector is FP32) and |r|^2 of the rounded r promoted to FP64 per row (per-block,
 // per-column partials).  Two FP64 operations per element instead of eleven.  The nonzeros of a
 // row alternate between two independent double-float accumulators (two dependency chains in
-// flight), joined by a double-float add at the end of the row.
-template <int CPL>
+// flight), joined by a double-float add at the end of the row.  ZX: x = 0 (the first outer step),
+// so every product and sum of a row is +0 and the row loop is skipped: the same r and norms.
+template <int CPL, bool ZX>
 __global__ void __launch_bounds__(256) residual_df32_kernel(const int64_t* __restrict__ rp,
                                                             const int32_t* __restrict__ ci,
                                                             const float4* __restrict__ A, const float4* __restrict__ X,
@@ -403,7 +414,7 @@ __global__ void __launch_bounds__(256) residual_df32_kernel(const int64_t* __res
     float rh[CPL], rl[CPL], ih[CPL], il[CPL], rh2[CPL], rl2[CPL], ih2[CPL], il2[CPL];
 #pragma unroll
     for (int q = 0; q < CPL; ++q) rh[q] = rl[q] = ih[q] = il[q] = rh2[q] = rl2[q] = ih2[q] = il2[q] = 0.f;
-    const int64_t kb = rp[row], ke = rp[row + 1];
+    const int64_t kb = ZX ? 0 : rp[row], ke = ZX ? 0 : rp[row + 1];
     int64_t k = kb;
     for (; k + 1 < ke; k += 2) {
       const float4 a = A[k], a2 = A[k + 1];
@@ -493,19 +504,28 @@ int residual_df(const int64_t* rp, const int32_t* ci, const float4* A, const flo
 }
 
 int residual_df32(const int64_t* rp, const int32_t* ci, const float4* A, const float4* X, const float4* Bdf, float2* Rv,
-                  double* part, int64_t E, int R, cudaStream_t s) {
+                  double* part, int64_t E, int R, cudaStream_t s, bool zero_x) {
   note_launch(1);
   Shape sh = shape_for(R);
   const int blocks = 152 * 4;
   switch (sh.cpl) {
     case 1:
-      residual_df32_kernel<1><<<blocks, 256, 0, s>>>(rp, ci, A, X, Bdf, Rv, part, E, R, sh.tpr_log2);
+      if (zero_x)
+        residual_df32_kernel<1, true><<<blocks, 256, 0, s>>>(rp, ci, A, X, Bdf, Rv, part, E, R, sh.tpr_log2);
+      else
+        residual_df32_kernel<1, false><<<blocks, 256, 0, s>>>(rp, ci, A, X, Bdf, Rv, part, E, R, sh.tpr_log2);
       break;
     case 2:
-      residual_df32_kernel<2><<<blocks, 256, 0, s>>>(rp, ci, A, X, Bdf, Rv, part, E, R, sh.tpr_log2);
+      if (zero_x)
+        residual_df32_kernel<2, true><<<blocks, 256, 0, s>>>(rp, ci, A, X, Bdf, Rv, part, E, R, sh.tpr_log2);
+      else
+        residual_df32_kernel<2, false><<<blocks, 256, 0, s>>>(rp, ci, A, X, Bdf, Rv, part, E, R, sh.tpr_log2);
       break;
     default:
-      residual_df32_kernel<4><<<blocks, 256, 0, s>>>(rp, ci, A, X, Bdf, Rv, part, E, R, sh.tpr_log2);
+      if (zero_x)
+        residual_df32_kernel<4, true><<<blocks, 256, 0, s>>>(rp, ci, A, X, Bdf, Rv, part, E, R, sh.tpr_log2);
+      else
+        residual_df32_kernel<4, false><<<blocks, 256, 0, s>>>(rp, ci, A, X, Bdf, Rv, part, E, R, sh.tpr_log2);
       break;
   }
   return blocks;

@@ -1026,12 +1026,14 @@ int read_active(Ctx* c) {
 // mode double-float arithmetic on the FP32 pipes (same accuracy class) with b taken from w.bdf
 // (split once per block solve) and r rounded to FP32 into w.r32, which is all the inner solver's
 // start vector needs.
-int outer_residual(Ctx* c, int f, int wp, const double2* X, const double2* B, int R) {
+// zero_x: X is known to be 0 (the first outer step), so r = b without the products.
+int outer_residual(Ctx* c, int f, int wp, const double2* X, const double2* B, int R, bool zero_x = false) {
   Work& w = c->work;
   const int64_t E = c->topo.n_edge;
-  if (wp == 0) return mwk::residual_f64(c->d_row, c->d_col, c->A64[f], X, B, w.r, w.npart, E, R, c->stream);
-  mwk::split_df(X, w.xdf, E * R, c->stream);
-  return mwk::residual_df32(c->d_row, c->d_col, c->Adf[f], w.xdf, w.bdf, w.r32, w.npart, E, R, c->stream);
+  if (wp == 0)
+    return mwk::residual_f64(c->d_row, c->d_col, c->A64[f], X, B, w.r, w.npart, E, R, c->stream, zero_x);
+  if (!zero_x) mwk::split_df(X, w.xdf, E * R, c->stream);
+  return mwk::residual_df32(c->d_row, c->d_col, c->Adf[f], w.xdf, w.bdf, w.r32, w.npart, E, R, c->stream, zero_x);
 }
 
 struct BlockStats {
@@ -1454,8 +1456,10 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
   int total = 0;
   for (int outer = 0; outer < max_outer; ++outer) {
     {
-      ProfScope ps(c, MW_K_RESIDUAL, (double)c->topo.nnz * 20 + 8.0 * (E + 1) + 3.0 * 16 * E * R);
-      nb = outer_residual(c, f, wp, X, B, R);
+      // the first step starts from X = 0: r = b, no products
+      ProfScope ps(c, MW_K_RESIDUAL,
+                   outer == 0 ? 24.0 * E * R : (double)c->topo.nnz * 20 + 8.0 * (E + 1) + 3.0 * 16 * E * R);
+      nb = outer_residual(c, f, wp, X, B, R, outer == 0);
     }
     CK(cudaMemsetAsync(w.active, 0, sizeof(int32_t), s));
     mwk::start_state(w.npart, nb, R, w.bnorm, o.tol, o.inner_tol, wp == 0, w.rnorm, w.g, w.target, w.done, w.kcol,

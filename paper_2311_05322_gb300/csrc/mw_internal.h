@@ -197,13 +197,14 @@ int residual_df(const int64_t* rp, const int32_t* ci, const float4* A, const flo
 // The mixed solver's outer residual: b, A, x in double-float, r rounded to FP32 complex, partial
 // ||r||^2 (FP64) per block and column; returns the number of blocks.
 int residual_df32(const int64_t* rp, const int32_t* ci, const float4* A, const float4* X, const float4* Bdf,
-                  float2* Rv, double* part, int64_t E, int R, cudaStream_t s);
+                  float2* Rv, double* part, int64_t E, int R, cudaStream_t s, bool zero_x = false);
 // v0 = r / rnorm per column (0 for done columns) from an FP32 residual.
 void normalize_start32(const float2* r, const double* rnorm, const int32_t* done, int64_t E, int R, float2* v0,
                        cudaStream_t s);
 // r = b - A x (FP64) and per-column partial ||r||^2 into part[nblk][R]; returns nblk used.
+// zero_x: x is known to be 0 (the products are skipped; the same r and norms).
 int residual_f64(const int64_t* rp, const int32_t* ci, const double2* A, const double2* X, const double2* B,
-                 double2* Rv, double* part, int64_t E, int R, cudaStream_t s);
+                 double2* Rv, double* part, int64_t E, int R, cudaStream_t s, bool zero_x = false);
 
 // Krylov (K6-K8, K15)
 // h_part = V^H w per part; returns the number of parts written.  `err` (device int, may be null)
