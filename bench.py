@@ -51,6 +51,8 @@ def _args(argv=None):
                     help="subdomain solves: dense inverses applied in BF16 (tensor cores) or FP32, or sparse "
                          "multifrontal factors (large subdomains)")
     ap.add_argument("--alpha", type=float, default=1e-3)
+    ap.add_argument("--z-storage", default="bf16", choices=["bf16", "fp32"],
+                    help="storage of the preconditioned Krylov vectors on the tensor-core path")
     ap.add_argument("--inner-tol", type=float, default=1e-2,
                     help="residual reduction of each inner FGMRES cycle (GMRES-IR); 1e-2 measured fastest")
     ap.add_argument("--plain-cols", type=int, default=1, help="columns timed on the plain FP64 path (0 = skip)")
@@ -414,6 +416,7 @@ def _setup_leg(a, local, stream):
     prec = {"bf16": mw.MW_PREC_BF16, "fp32": mw.MW_PREC_FP32, "sparse": mw.MW_PREC_SPARSE,
             "sparse_bf16": mw.MW_PREC_SPARSE_BF16}[a.prec]
     c.profile_enable(1 << mw.MW_K_FACTOR)
+    c.set_z_storage(a.z_storage == "bf16")
     t = time.perf_counter()
     c.setup_preconditioner(n_sub, part, a.overlap, prec)
     torch.cuda.synchronize()
@@ -521,7 +524,7 @@ def config3_leg(a, local, stream, alu, hbm, src, steps=3, warmup=2):
     edges), 64 transmitters x 3 frequencies (0.8 / 1.0 / 1.2 GHz) as one block per frequency,
     BF16 tensor-core ORAS, GMRES-IR to 1e-8."""
     a3 = _args(["--cells", "55x55x24", "--n-src", "64", "--freqs", "0.8e9,1.0e9,1.2e9", "--parts", "11x11x5",
-                "--alpha", str(a.alpha)])
+                "--alpha", str(a.alpha), "--z-storage", a.z_storage])
     L = _setup_leg(a3, local, stream)
     sec, J, prof, launches, clocks = _timed_steps(L, a3, local, stream, steps, warmup, 1, None)
     units = 2 * a3.n_src * len(L["freqs"])
@@ -533,7 +536,8 @@ def config3_leg(a, local, stream, alu, hbm, src, steps=3, warmup=2):
             "config": {"workload": f"shoulder phantom 55x55x24 Kuhn cells ({info.n_edge} edges, {info.n_tet} tets), "
                                    f"64 z-dipoles x 3 frequencies, one inversion evaluation (forward+adjoint)",
                        "rhs_solves_per_step": units, "subdomains": L["n_sub"], "n_s_mean": float(sizes.mean()),
-                       "n_s_max": int(sizes.max()), "preconditioner_apply": "bf16 tcgen05"},
+                       "n_s_max": int(sizes.max()), "preconditioner_apply": "bf16 tcgen05",
+                       "z_storage": a3.z_storage},
             "roofline": roof, "classes": rate_classes(prof, hbm, alu), "gpu_launches": int(launches),
             "clocks": clocks, "setup_s": L["setup"], "J_last": J}
 
@@ -812,6 +816,7 @@ def run_mine(a):
                                                 4: "fp32 multifrontal sweeps",
                                                 5: "bf16 tcgen05 multifrontal sweeps"}.get(prec, str(prec)),
                        "tol": 1e-8, "inner_tol": a.inner_tol, "alpha": a.alpha,
+                       "z_storage": a.z_storage if prec == mw.MW_PREC_BF16 else "fp32",
                        "l2": "inputs larger than L2 (subdomain inverses and Krylov basis are GBs)"},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -183,7 +183,9 @@ mw_status mw_get_matrix(mw_ctx* ctx, int32_t f, double* values);
  * takes complex128 in and out and computes in double-float arithmetic on the FP32 pipes (the
  * mixed solver's outer residual); prec = 4 is the FP32 product of the halo-tiled kernel (rows
  * in Morton-ordered blocks whose columns of X are staged in shared memory; even n_cols, x
- * 16-byte aligned), bit-identical to MW_PREC_FP32. */
+ * 16-byte aligned), bit-identical to MW_PREC_FP32; prec = 5 takes x as complex BF16 pairs (4 bytes
+ * per value, real in the low half) and writes complex64 y, equal to MW_PREC_FP32 applied to the
+ * widened x. */
 mw_status mw_apply_matrix(mw_ctx* ctx, int32_t f, int32_t prec, const void* x_dev, void* y_dev,
                           int32_t n_cols);
 
@@ -404,6 +406,17 @@ mw_status mw_nn_grid_to_tets(mw_ctx* ctx, const float* grid, int32_t G, const do
  * MW_EINVAL for another value. */
 enum { MW_ADJOINT_SOLVE = 0, MW_ADJOINT_RECIPROCAL = 1 };
 mw_status mw_set_adjoint_mode(mw_ctx* ctx, int32_t mode);
+
+/* Storage of the preconditioned vectors z_j = M^-1 v_j of the inner FGMRES cycles when the
+ * preconditioner is the BF16 tensor-core apply (MW_APPLY_TC; elsewhere it has no effect):
+ *   1 (default): complex BF16 pairs, 4 bytes per value, written by the apply's epilogue and
+ *     widened to FP32 where they are read (the SpMM A z_j and the update x += Z y);
+ *   0: complex FP32, 8 bytes per value.
+ * Flexible GMRES takes the stored z_j as they are in both places, so the rounding only perturbs
+ * the preconditioner (already a BF16 product); the Arnoldi relation and the FP64 outer residual
+ * are unchanged.  The paper has no counterpart (its preconditioned vectors are FP64).  Drops the
+ * captured solve graphs when the setting changes.  MW_EINVAL for another value. */
+mw_status mw_set_z_storage(mw_ctx* ctx, int32_t bf16);
 
 /* ---- column-sharded evaluation (one evaluation split over processes by transmitters) ---
  * The transmitter columns of an evaluation are independent until the cost: process r solves

@@ -873,21 +873,58 @@ __global__ void update_x_kernel(const T* __restrict__ Z, int64_t zstride, const 
   }
 }
 
+// The same update with Z stored as complex BF16 pairs (4 bytes per value, real in the low half):
+// the correction is formed in FP32 from the widened values and added to x in FP64.
+__global__ void update_x_bx_kernel(const uint32_t* __restrict__ Z, int64_t zstride, const double2* __restrict__ y,
+                                   const int32_t* __restrict__ kcol, int m, double2* __restrict__ x, int64_t E, int R) {
+  const int64_t n = E * R;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % R);
+    const int k = kcol[c];
+    float dr = 0.f, di = 0.f;
+    for (int l = 0; l < k; ++l) {
+      const uint32_t u = Z[(int64_t)l * zstride + i];
+      const float zx = __uint_as_float(u << 16), zy = __uint_as_float(u & 0xffff0000u);
+      const double2 yy = y[(int64_t)c * m + l];
+      const float yr = (float)yy.x, yi = (float)yy.y;
+      dr = fmaf(yr, zx, dr);
+      dr = fmaf(-yi, zy, dr);
+      di = fmaf(yr, zy, di);
+      di = fmaf(yi, zx, di);
+    }
+    double2 xv = x[i];
+    xv.x += (double)dr;
+    xv.y += (double)di;
+    x[i] = xv;
+  }
+}
+
+// Stored value of Z widened to the arithmetic type: itself, or a complex BF16 pair (real in the
+// low half) as complex FP32.
+__device__ __forceinline__ float2 zval(float2 v) { return v; }
+__device__ __forceinline__ double2 zval(double2 v) { return v; }
+__device__ __forceinline__ float2 zval(uint32_t u) {
+  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+
 // Streaming form of the solution update for 16 <= R <= 128 with 16-byte aligned bases, on the tiles,
 // ring and thread map of cgs_dots_bulk_kernel: the producer streams Z_0 .. Z_{kmax-1} per tile
 // (kmax = the largest kcol of the block); consumer (c, g) forms the correction of its rows of
 // column c in the basis precision with the operations of update_x_kernel, in the same order
-// (bit-identical x), and adds it to x in FP64.  y is staged in shared memory as T.
-template <typename T>
+// (bit-identical x), and adds it to x in FP64.  y is staged in shared memory as T.  ZT is the
+// stored type of Z: T, or uint32_t for complex BF16 pairs (T = float2; the widened values enter
+// the same operations as update_x_bx_kernel's, bit-identical to it); the tiles hold
+// bd_rows<ZT>() rows per row group, 16 KB per stage either way.
+template <typename T, typename ZT = T>
 __global__ void __launch_bounds__(kBdThreads, 2)
-    update_x_bulk_kernel(const T* __restrict__ Z, int64_t zstride, const double2* __restrict__ y,
+    update_x_bulk_kernel(const ZT* __restrict__ Z, int64_t zstride, const double2* __restrict__ y,
                          const int32_t* __restrict__ kcol, int m, double2* __restrict__ x, int64_t E, int R, int G,
                          int NS, int32_t* __restrict__ err) {
   using Sc = typename Traits<T>::S;
-  constexpr int RPT = bd_rows<T>();
-  constexpr int kStageElems = kBdStageBytes / (int)sizeof(T);
+  constexpr int RPT = bd_rows<ZT>();
+  constexpr int kStageElems = kBdStageBytes / (int)sizeof(ZT);
   extern __shared__ __align__(128) uint8_t ux_smem[];
-  T* stage = reinterpret_cast<T*>(ux_smem);
+  ZT* stage = reinterpret_cast<ZT*>(ux_smem);
   T* ys = reinterpret_cast<T*>(ux_smem + (size_t)NS * kBdStageBytes);   // [m][R]
   int32_t* ks = reinterpret_cast<int32_t*>(ys + (size_t)m * R);          // [R]
   uint64_t* full = reinterpret_cast<uint64_t*>(ks + ((R + 3) & ~3));
@@ -929,7 +966,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
     for (int64_t t = t0; t < t1 && !stop; ++t) {
       const int64_t r0 = t * TR;
       const int64_t rows = E - r0 < TR ? E - r0 : (int64_t)TR;
-      const uint32_t bytes = (uint32_t)((rows * R * (int64_t)sizeof(T)) & ~(int64_t)15);
+      const uint32_t bytes = (uint32_t)((rows * R * (int64_t)sizeof(ZT)) & ~(int64_t)15);
       for (int l = 0; l < kmax; ++l) {
         if (it >= NS && !mbar_wait(&empty[st], ph ^ 1u)) {
           atomicCAS(err, 0, 31);
@@ -939,7 +976,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
           stop = true;
           break;
         }
-        const T* src = Z + (int64_t)l * zstride + r0 * R;
+        const ZT* src = Z + (int64_t)l * zstride + r0 * R;
         if (bytes > 0) {
           mbar_expect_tx(&full[st], bytes);
           bulk_g2s(stage + (size_t)st * kStageElems, src, bytes, &full[st]);
@@ -969,7 +1006,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
   for (int64_t t = t0; t < t1; ++t) {
     const int64_t r0 = t * TR;
     const int64_t rows = E - r0 < TR ? E - r0 : (int64_t)TR;
-    const int64_t ncop = ((rows * R * (int64_t)sizeof(T)) & ~(int64_t)15) / (int64_t)sizeof(T);
+    const int64_t ncop = ((rows * R * (int64_t)sizeof(ZT)) & ~(int64_t)15) / (int64_t)sizeof(ZT);
     Sc dr[RPT], di[RPT];
 #pragma unroll
     for (int k = 0; k < RPT; ++k) dr[k] = di[k] = 0;
@@ -979,15 +1016,15 @@ __global__ void __launch_bounds__(kBdThreads, 2)
         *abort_flag = 1;
       }
       if (act && l < kc) {
-        const T* sm = stage + (size_t)st * kStageElems;
-        const T* gl = Z + (int64_t)l * zstride + r0 * R;
+        const ZT* sm = stage + (size_t)st * kStageElems;
+        const ZT* gl = Z + (int64_t)l * zstride + r0 * R;
         const T yy = ys[l * R + c];
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
           const int row = k * G + g;
           const int f = row * R + c;
           if (row < rows) {
-            const T z = f < ncop ? sm[f] : gl[f];
+            const T z = zval(f < ncop ? sm[f] : gl[f]);
             dr[k] = fma(yy.x, z.x, dr[k]);
             dr[k] = fma(-yy.y, z.y, dr[k]);
             di[k] = fma(yy.x, z.y, di[k]);
@@ -1021,23 +1058,21 @@ inline size_t ux_smem_bytes(int R, int m, int NS) {
   return (size_t)NS * kBdStageBytes + (size_t)m * R * 16 + ((R + 3) & ~3) * 4 + 2 * NS * sizeof(uint64_t) + 16;
 }
 
-template <typename T>
-bool update_x_bulk(const T* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x, int64_t E,
+template <typename T, typename ZT = T>
+bool update_x_bulk(const ZT* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x, int64_t E,
                    int R, int32_t* err, cudaStream_t s) {
-  const bool aligned = ((uintptr_t)Z % 16 == 0) && ((zstride * sizeof(T)) % 16 == 0);
+  const bool aligned = ((uintptr_t)Z % 16 == 0) && ((zstride * sizeof(ZT)) % 16 == 0);
   if (!err || !aligned || R < 16 || R > 128 || m < 1) return false;
-  static bool attr = false;
+  static bool attr = false;   // one per instantiation
   if (!attr) {
     // 226 KB: the kernel's static shared memory shares the 227 KB per block
-    attr = cudaFuncSetAttribute(update_x_bulk_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                226 * 1024) == cudaSuccess &&
-           cudaFuncSetAttribute(update_x_bulk_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr = cudaFuncSetAttribute(update_x_bulk_kernel<T, ZT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 226 * 1024) == cudaSuccess;
   }
   int NS = kBdStages;
   while (NS > 2 && ux_smem_bytes(R, m, NS) > (size_t)226 * 1024) --NS;
-  update_x_bulk_kernel<T><<<152 * 2, kBdThreads, ux_smem_bytes(R, m, NS), s>>>(Z, zstride, y, kcol, m, x, E, R,
-                                                                              kBdConsumers / R, NS, err);
+  update_x_bulk_kernel<T, ZT><<<152 * 2, kBdThreads, ux_smem_bytes(R, m, NS), s>>>(Z, zstride, y, kcol, m, x, E, R,
+                                                                                  kBdConsumers / R, NS, err);
   return true;
 }
 
@@ -1270,6 +1305,12 @@ void update_x_f64(const double2* Z, int64_t zstride, const double2* y, const int
   note_launch(1);
   if (update_x_bulk<double2>(Z, zstride, y, kcol, m, x, E, R, err, s)) return;
   update_x_kernel<double2><<<gs_blocks(E * R), 256, 0, s>>>(Z, zstride, y, kcol, m, x, E, R);
+}
+void update_x_bx(const void* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x, int64_t E,
+                 int R, cudaStream_t s, int32_t* err) {
+  note_launch(1);
+  if (update_x_bulk<float2, uint32_t>((const uint32_t*)Z, zstride, y, kcol, m, x, E, R, err, s)) return;
+  update_x_bx_kernel<<<gs_blocks(E * R), 256, 0, s>>>((const uint32_t*)Z, zstride, y, kcol, m, x, E, R);
 }
 void update_x_f32(const float2* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x,
                   int64_t E, int R, cudaStream_t s, int32_t* err) {

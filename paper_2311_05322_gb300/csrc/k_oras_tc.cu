@@ -244,6 +244,7 @@ struct TcArgs {
   const int64_t* own_ptr;
   const int32_t* own_glob;
   const int32_t* c0_glob;   // optional: row of z added to each output row (-1: none)
+  int z_bf16;               // z holds complex BF16 pairs (4 bytes per value) instead of float2
   const uint8_t* W;
   const uint8_t* Bt;
   float2* z;
@@ -392,7 +393,10 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
           if (col >= a.R) continue;
           float2 v = make_float2(rr[i] - ii[i], ri[i] + ir[i]);
           if (c0r) v = make_float2(v.x + cur[i].x, v.y + cur[i].y);
-          zr[col] = v;
+          if (a.z_bf16)
+            reinterpret_cast<uint32_t*>(a.z)[og * a.R + col] = pack_bf16(v.x, v.y);
+          else
+            zr[col] = v;
         }
       }
     }
@@ -537,7 +541,8 @@ int tc_max_stages(int R) {
 }
 
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
-                   void* scratch, cudaStream_t s, int stages, const double* in_scale, const int32_t* c0_glob) {
+                   void* scratch, cudaStream_t s, int stages, const double* in_scale, const int32_t* c0_glob,
+                   bool z_bf16) {
   const int Rp = rpad(R);
   const int N = 2 * Rp;
   if (stages <= 0) stages = tc_stages(N);
@@ -562,6 +567,7 @@ void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const flo
   a.own_ptr = tp.own_ptr;
   a.own_glob = tp.own_glob;
   a.c0_glob = c0_glob;
+  a.z_bf16 = z_bf16 ? 1 : 0;
   a.W = (const uint8_t*)W;
   a.Bt = (const uint8_t*)scratch;
   a.z = z;

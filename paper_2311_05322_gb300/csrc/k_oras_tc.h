@@ -47,10 +47,11 @@ void tc_pack_blocks(const TcPlan& p, const MfTask* tasks, int n, int ktmax, int 
 // stages: shared-memory pipeline depth of the MMA kernel (0 = default; the result does not depend
 // on it, only the speed).  in_scale (may be null): per-column factor of r (z = M^{-1}(r * in_scale)).
 // Output row q of "subdomain" s goes to z row own_glob[own_ptr[s] + q] (skipped when negative);
-// c0_glob (may be null) lists, per output row, a row of z added to it (-1: none).
+// c0_glob (may be null) lists, per output row, a row of z added to it (-1: none).  z_bf16: z is
+// written as complex BF16 pairs (real in the low half), 4 bytes per value, row stride R values.
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
                    void* scratch, cudaStream_t s, int stages = 0, const double* in_scale = nullptr,
-                   const int32_t* c0_glob = nullptr);
+                   const int32_t* c0_glob = nullptr, bool z_bf16 = false);
 // Pipeline depths the MMA kernel accepts for R columns: [tc_min_stages, tc_max_stages(R)]; the
 // default depth for R columns.
 constexpr int tc_min_stages = 2;

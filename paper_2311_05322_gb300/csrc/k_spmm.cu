@@ -26,10 +26,26 @@ __device__ __forceinline__ void cmac(T& acc, T a, T x) {
   acc.y = fma(a.y, x.x, acc.y);
 }
 
-template <typename T, int CPL>
+// Stored X value as the arithmetic type: itself, or a complex BF16 pair (real in the low half)
+// widened to complex FP32.
+template <typename T>
+__device__ __forceinline__ T xval(T v) {
+  return v;
+}
+__device__ __forceinline__ float2 xval(uint32_t u) {
+  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+
+// A row's terms are taken in batches of NB: the NB column indices, then the NB gathers of X (all
+// in flight together), then the complex FMAs in term order.  The gathers are latency-bound
+// (about 16 terms per row, each a 128-256 byte row of X), so the batch raises the loads in
+// flight per warp; the sums keep the canonical term order.  XT is the stored type of X: T, or
+// uint32_t for complex BF16 pairs (T = float2).
+template <typename T, int CPL, typename XT = T>
 __global__ void __launch_bounds__(512) spmm_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                   const T* __restrict__ A, const T* __restrict__ X, T* __restrict__ Y,
+                                                   const T* __restrict__ A, const XT* __restrict__ X, T* __restrict__ Y,
                                                    int64_t E, int R, int tpr_log2) {
+  constexpr int NB = 8 / CPL;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t row = g >> tpr_log2;
   const int c0 = (int)(g & ((1 << tpr_log2) - 1)) * CPL;
@@ -38,12 +54,33 @@ __global__ void __launch_bounds__(512) spmm_kernel(const int64_t* __restrict__ r
 #pragma unroll
   for (int q = 0; q < CPL; ++q) acc[q] = T{0, 0};
   const int64_t b = rp[row], e = rp[row + 1];
-  for (int64_t k = b; k < e; ++k) {
+  int64_t k = b;
+  for (; k + NB <= e; k += NB) {
+    int cc[NB];
+    XT xv[NB][CPL];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) cc[u] = ci[k + u];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const XT* xr = X + (int64_t)cc[u] * R + c0;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+        if (c0 + q < R) xv[u][q] = xr[q];
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const T a = A[k + u];
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+        if (c0 + q < R) cmac(acc[q], a, xval(xv[u][q]));
+    }
+  }
+  for (; k < e; ++k) {
     const T a = A[k];
-    const T* xr = X + (int64_t)ci[k] * R + c0;
+    const XT* xr = X + (int64_t)ci[k] * R + c0;
 #pragma unroll
     for (int q = 0; q < CPL; ++q)
-      if (c0 + q < R) cmac(acc[q], a, xr[q]);
+      if (c0 + q < R) cmac(acc[q], a, xval(xr[q]));
   }
   T* yr = Y + row * R + c0;
 #pragma unroll
@@ -235,6 +272,28 @@ bool spmm_halo_f32(const SpmmDev& p, const float2* A, const float2* X, float2* Y
   spmm_halo_kernel<<<(unsigned)(p.n_block * nchunk), kHaloThreads, smem, s>>>(p.blk_row, p.blk_halo, p.halo, p.rows,
                                                                            p.rptr, p.lcol, A, X, Y, R, nchunk);
   return true;
+}
+
+void spmm_f32_bx(const int64_t* rp, const int32_t* ci, const float2* A, const void* X, float2* Y, int64_t E, int R,
+                 cudaStream_t s, int threads) {
+  if (threads != 128 && threads != 256 && threads != 512) threads = 256;
+  if (R > 128) return;
+  note_launch(1);
+  const Shape sh = shape_for(R);
+  const int64_t nthr = E << sh.tpr_log2;
+  const int blocks = (int)((nthr + threads - 1) / threads);
+  const uint32_t* Xb = (const uint32_t*)X;
+  switch (sh.cpl) {
+    case 1:
+      spmm_kernel<float2, 1, uint32_t><<<blocks, threads, 0, s>>>(rp, ci, A, Xb, Y, E, R, sh.tpr_log2);
+      break;
+    case 2:
+      spmm_kernel<float2, 2, uint32_t><<<blocks, threads, 0, s>>>(rp, ci, A, Xb, Y, E, R, sh.tpr_log2);
+      break;
+    default:
+      spmm_kernel<float2, 4, uint32_t><<<blocks, threads, 0, s>>>(rp, ci, A, Xb, Y, E, R, sh.tpr_log2);
+      break;
+  }
 }
 
 void spmm_plan_values(const SpmmDev& p, const float2* A32, int64_t nnz, float2* out, cudaStream_t s) {

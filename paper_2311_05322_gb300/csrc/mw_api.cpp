@@ -282,6 +282,7 @@ struct Ctx {
   // [n_freq][n_src][win_nl]
   int win_j0 = 0, win_nl = 0, win_nf = 0, win_ns = 0;
   int adjoint_mode = 0;          // MW_ADJOINT_SOLVE or MW_ADJOINT_RECIPROCAL
+  int z_bf16 = 1;                // preconditioned vectors of the tensor-core path stored in BF16
   double2* d_D = nullptr;        // reciprocity weights [n_src][n_src]
   std::vector<double2*> Xw, Lw, Bw, Bwa;
   double2* d_Sp = nullptr;
@@ -946,7 +947,7 @@ void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launch
 }
 
 void apply_prec(Ctx* c, int f, int work_prec, const void* v, void* z, int R, int stages = 0,
-                const double* in_scale = nullptr) {
+                const double* in_scale = nullptr, bool z_bf16 = false) {
   Prec& p = c->prec;
   cudaStream_t s = c->stream;
   if (p.apply_prec == 4 || p.apply_prec == 5) {
@@ -956,7 +957,8 @@ void apply_prec(Ctx* c, int f, int work_prec, const void* v, void* z, int R, int
     require(work_prec == 1, MW_EINVAL, "BF16 preconditioner needs the mixed-precision solve");
     Work& w = c->work;
     ensure_prec_scratch(c, R);
-    mwk::oras_apply_tc(p.tc, p.topo(), p.W[f], (const float2*)v, (float2*)z, R, w.tc_scratch, s, stages, in_scale);
+    mwk::oras_apply_tc(p.tc, p.topo(), p.W[f], (const float2*)v, (float2*)z, R, w.tc_scratch, s, stages, in_scale,
+                       nullptr, z_bf16);
   } else {
     const int need = work_prec;  // 0 FP64, 1 FP32
     require(p.apply_prec == need, MW_EINVAL,
@@ -1007,13 +1009,14 @@ void check_tc_wait(Ctx* c) {
 
 // Algorithmic bytes of one preconditioner apply on R columns: the owned-row inverses once,
 // the gathered subdomain inputs and the owned outputs.
-double oras_bytes(Ctx* c, int R) {
+// zb: the output z is stored as BF16 pairs (4 bytes per value)
+double oras_bytes(Ctx* c, int R, bool zb = false) {
   const Prec& p = c->prec;
   if (p.apply_prec == 4) return 8.0 * (double)p.mf.sym.fac_total + 8.0 * R * (p.sum_n + (double)c->topo.n_edge);
   if (p.apply_prec == 5) return 4.0 * (double)p.mf.sym.fac_total + 8.0 * R * (p.sum_n + (double)c->topo.n_edge);
   const double wb = p.apply_prec == 0 ? 16.0 : (p.apply_prec == 1 ? 8.0 : 4.0);
   const double vb = p.apply_prec == 0 ? 16.0 : 8.0;
-  return wb * p.sum_own_n + vb * R * (p.sum_n + (double)c->topo.n_edge);
+  return wb * p.sum_own_n + vb * R * (double)p.sum_n + (zb ? 4.0 : vb) * R * (double)c->topo.n_edge;
 }
 
 int read_active(Ctx* c) {
@@ -1054,8 +1057,14 @@ struct CycleArgs {
   // is applied where a vector is read (the apply's gather, the dots' reduction, the update's
   // coefficients) instead of in a separate pass over each new vector
   bool lazy;
+  // the preconditioned vectors Z are stored as complex BF16 pairs (tensor-core path): flexible
+  // GMRES uses the stored Z both in A Z and in x += Z y, so their rounding only changes the
+  // preconditioner
+  bool zb;
   void* Vp(const Work& w, int i) const { return (unsigned char*)w.V + es * vstride * i; }
-  void* Zp(const Work& w, int i) const { return use_p ? (unsigned char*)w.Z + es * vstride * i : Vp(w, i); }
+  void* Zp(const Work& w, int i) const {
+    return use_p ? (unsigned char*)w.Z + (zb ? (size_t)4 : es) * vstride * i : Vp(w, i);
+  }
 };
 
 // Arnoldi step j as segments (preconditioner apply, SpMM, Gram-Schmidt dots, Gram-Schmidt
@@ -1071,6 +1080,11 @@ void spmm32(Ctx* c, int f, const float2* X, float2* Y, int R, int threads) {
     return;
   mwk::spmm_f32(c->d_row, c->d_col, c->A32[f], X, Y, c->topo.n_edge, R, c->stream, threads < 128 ? 256 : threads);
 }
+// The same with X stored as complex BF16 pairs: the row-per-warp kernel (256 threads for the
+// halo shape, which has no BF16 form).
+void spmm32_bx(Ctx* c, int f, const void* X, float2* Y, int R, int threads) {
+  mwk::spmm_f32_bx(c->d_row, c->d_col, c->A32[f], X, Y, c->topo.n_edge, R, c->stream, threads < 128 ? 256 : threads);
+}
 
 template <class Seg>
 void arnoldi_step(Ctx* c, const CycleArgs& a, int j, Seg&& seg) {
@@ -1079,13 +1093,16 @@ void arnoldi_step(Ctx* c, const CycleArgs& a, int j, Seg&& seg) {
   const int R = a.R;
   const double* vs = a.lazy ? w.vscale : nullptr;
   if (a.use_p)
-    seg(MW_K_ORAS, oras_bytes(c, R), [&] {
-      apply_prec(c, a.f, a.wp, a.Vp(w, j), a.Zp(w, j), R, a.t.sh.tc_stages, vs ? vs + (size_t)j * R : nullptr);
+    seg(MW_K_ORAS, oras_bytes(c, R, a.zb), [&] {
+      apply_prec(c, a.f, a.wp, a.Vp(w, j), a.Zp(w, j), R, a.t.sh.tc_stages, vs ? vs + (size_t)j * R : nullptr,
+                 a.zb);
     });
-  seg(MW_K_SPMM, (double)c->topo.nnz * (a.es + 4) + 8.0 * (E + 1) + 2.0 * a.es * E * R, [&] {
+  seg(MW_K_SPMM, (double)c->topo.nnz * (a.es + 4) + 8.0 * (E + 1) + (double)(a.es + (a.zb ? 4 : a.es)) * E * R, [&] {
     if (a.wp == 0)
       mwk::spmm_f64(c->d_row, c->d_col, c->A64[a.f], (const double2*)a.Zp(w, j), (double2*)a.Vp(w, j + 1), E, R,
                     c->stream, a.t.sh.spmm_threads);
+    else if (a.zb)
+      spmm32_bx(c, a.f, a.Zp(w, j), (float2*)a.Vp(w, j + 1), R, a.t.sh.spmm_threads);
     else
       spmm32(c, a.f, (const float2*)a.Zp(w, j), (float2*)a.Vp(w, j + 1), R, a.t.sh.spmm_threads);
   });
@@ -1135,7 +1152,10 @@ void cycle_finish(Ctx* c, const CycleArgs& a) {
   if (a.wp == 0)
     mwk::update_x_f64((const double2*)a.Zp(w, 0), a.vstride, w.y, w.kcol, a.m, a.X, a.E, a.R, c->stream, w.kerr);
   else
-    mwk::update_x_f32((const float2*)a.Zp(w, 0), a.vstride, w.y, w.kcol, a.m, a.X, a.E, a.R, c->stream, w.kerr);
+    if (a.zb)
+      mwk::update_x_bx(a.Zp(w, 0), a.vstride, w.y, w.kcol, a.m, a.X, a.E, a.R, c->stream, w.kerr);
+    else
+      mwk::update_x_f32((const float2*)a.Zp(w, 0), a.vstride, w.y, w.kcol, a.m, a.X, a.E, a.R, c->stream, w.kerr);
   check_launch("solution update");
   CK(cudaMemcpyAsync(w.h_ivec, w.kcol, sizeof(int32_t) * a.R, cudaMemcpyDeviceToHost, c->stream));
 }
@@ -1443,7 +1463,8 @@ BlockStats solve_block(Ctx* c, int f, int R, const double2* B, double2* X, const
   Work& w = c->work;
   cudaStream_t s = c->stream;
   CycleArgs a{f, R, m, wp, use_p, X, E, krylov_stride(E, R), wp == 0 ? sizeof(double2) : sizeof(float2),
-              tuned_for(c, R, wp, m, use_p), use_p && c->prec.ready && c->prec.apply_prec == 2 && wp == 1};
+              tuned_for(c, R, wp, m, use_p), use_p && c->prec.ready && c->prec.apply_prec == 2 && wp == 1, false};
+  a.zb = a.lazy && c->z_bf16;
 
   CK(cudaMemsetAsync(X, 0, sizeof(double2) * E * R, s));
   if (wp == 1) mwk::split_df(B, w.bdf, E * R, s);
@@ -1740,11 +1761,13 @@ void reassemble_all(Ctx* c) {
   const int nc = 2 + c->n_port;
   const int64_t T = c->topo.n_tet, Fb = c->topo.n_bface;
   // pull map and offsets, element matrices and eps read once, FP64 and FP32 values written;
-  // the double-float split reads the FP64 values and writes their (hi, lo) pairs
+  // the double-float split reads the FP64 values and writes their (hi, lo) pairs (32 B per
+  // nonzero); the SpMM plan's blocked copy reads a source index and an FP32 value and writes it
+  // (20 B)
   const double rbytes = 8.0 * (nnz + 1) + 4.0 * (36.0 * T + 9.0 * Fb) + (42.0 * 8 + 16) * T + 48.0 * Fb + 24.0 * nnz;
   for (int f = 0; f < c->n_freq; ++f) {
     const double k0 = k0_of(c->freqs[f]);
-    ProfScope ps(c, MW_K_REASSEMBLE, rbytes + 32.0 * nnz);
+    ProfScope ps(c, MW_K_REASSEMBLE, rbytes + (32.0 + 20.0) * nnz);
     mwk::reassemble(c->d_cptr, c->d_contrib, nnz, c->d_KM, c->d_Bf, c->d_eps, k0 * k0, -k0 * si, k0 * sr,
                     c->d_bface_cls, c->d_zc ? c->d_zc + (size_t)f * nc : nullptr, c->d_nzmask, c->A64[f], c->A32[f],
                     c->stream);
@@ -2231,6 +2254,8 @@ mw_status mw_apply_matrix(mw_ctx* c, int32_t f, int32_t prec, const void* x, voi
       require(mwk::spmm_halo_f32(c->spmm, c->A32b[f], (const float2*)x, (float2*)y, n_cols, c->stream), MW_EINVAL,
               "halo-tiled SpMM: unsupported shape");
     }
+    else if (prec == 5)
+      mwk::spmm_f32_bx(c->d_row, c->d_col, c->A32[f], x, (float2*)y, c->topo.n_edge, n_cols, c->stream);
     else if (prec == 3) {
       const int64_t n = c->topo.n_edge * (int64_t)n_cols;
       float4* xd = dalloc<float4>(c, n);
@@ -2969,6 +2994,14 @@ mw_status mw_set_adjoint_mode(mw_ctx* c, int32_t mode) {
   return guard(c, [&] {
     require(mode == MW_ADJOINT_SOLVE || mode == MW_ADJOINT_RECIPROCAL, MW_EINVAL, "bad adjoint mode");
     c->adjoint_mode = mode;
+  });
+}
+
+mw_status mw_set_z_storage(mw_ctx* c, int32_t bf16) {
+  return guard(c, [&] {
+    require(bf16 == 0 || bf16 == 1, MW_EINVAL, "bad Z storage");
+    if (c->z_bf16 != bf16) drop_graphs(c);
+    c->z_bf16 = bf16;
   });
 }
 

@@ -186,6 +186,9 @@ struct SpmmDev {
 // Returns false (nothing launched) when the shape is not supported: R odd or above 128, or X
 // not 16-byte aligned.  Bit-identical to spmm_f32.
 bool spmm_halo_f32(const SpmmDev& p, const float2* A_blk, const float2* X, float2* Y, int R, cudaStream_t s);
+// Y = A X (FP32) with X stored as complex BF16 pairs [E][R] (real in the low half).
+void spmm_f32_bx(const int64_t* rp, const int32_t* ci, const float2* A, const void* X, float2* Y, int64_t E, int R,
+                 cudaStream_t s, int threads = 256);
 // A_blk[q] = A32[src[q]].
 void spmm_plan_values(const SpmmDev& p, const float2* A32, int64_t nnz, float2* A_blk, cudaStream_t s);
 // Split complex FP64 values into double-float (re_hi, re_lo, im_hi, im_lo).
@@ -258,6 +261,10 @@ void update_x_f64(const double2* Z, int64_t zstride, const double2* y, const int
                   int64_t E, int R, cudaStream_t s, int32_t* err = nullptr);
 void update_x_f32(const float2* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x,
                   int64_t E, int R, cudaStream_t s, int32_t* err = nullptr);
+// The same with Z stored as complex BF16 pairs [E][R] per vector (real in the low half), vectors
+// zstride values apart.
+void update_x_bx(const void* Z, int64_t zstride, const double2* y, const int32_t* kcol, int m, double2* x, int64_t E,
+                 int R, cudaStream_t s, int32_t* err);
 void reduce_cols(const double* part, int nparts, int R, double* out, cudaStream_t s);
 
 // layout conversions

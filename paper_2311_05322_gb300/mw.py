@@ -113,6 +113,7 @@ _SIGS = {
     "mw_invert": (C.c_int32, [_P, C.POINTER(mw_inv_opts), C.POINTER(mw_solve_opts), _P, _P, _P,
                               C.POINTER(mw_inv_history)]),
     "mw_set_adjoint_mode": (C.c_int32, [_P, C.c_int32]),
+    "mw_set_z_storage": (C.c_int32, [_P, C.c_int32]),
     "mw_forward_cols": (C.c_int32, [_P, C.POINTER(mw_solve_opts), C.c_int32, C.c_int32, _P]),
     "mw_gradient_cols": (C.c_int32, [_P, C.POINTER(mw_solve_opts), _P, _P, _P, C.POINTER(C.c_double), _P]),
     "mw_assemble_dev": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
@@ -395,6 +396,10 @@ class Context:
     def set_adjoint_mode(self, reciprocal: bool):
         """Adjoint fields by explicit solves (default) or by reciprocity from the forward fields."""
         self._check(self.lib.mw_set_adjoint_mode(self.h, MW_ADJOINT_RECIPROCAL if reciprocal else MW_ADJOINT_SOLVE))
+
+    def set_z_storage(self, bf16: bool):
+        """Preconditioned Krylov vectors of the tensor-core path stored in BF16 (default) or FP32."""
+        self._check(self.lib.mw_set_z_storage(self.h, 1 if bf16 else 0))
 
     def forward_cols(self, j0: int, n_cols: int, opts: mw_solve_opts | None = None) -> np.ndarray:
         """Forward solves of transmitters j0 .. j0+n_cols-1; returns their S columns

@@ -114,6 +114,18 @@ def test_spmm(ragged, ncols):
         yh = torch.full_like(x32, float("nan"))
         c.apply_matrix(0, 4, x32, yh, ncols)
         assert torch.equal(yh, y32)
+    # x as complex BF16 pairs (real in the low half): equal to the FP32 product of the widened x
+    # bit for bit, and to the FP64 product of the widened x within the FP32 bar
+    xr, xi = x32.real.to(torch.bfloat16), x32.imag.to(torch.bfloat16)
+    xb = (xi.view(torch.int16).to(torch.int32) << 16) | (xr.view(torch.int16).to(torch.int32) & 0xFFFF)
+    xw = torch.complex(xr.float(), xi.float())
+    yw = torch.empty_like(x32)
+    c.apply_matrix(0, mw.MW_PREC_FP32, xw.contiguous(), yw, ncols)
+    refw = sysm.csr(asm.assemble(sysm, eps, 1e9, EPS_MATCHING)) @ xw.cpu().numpy().astype(np.complex128)
+    yb = torch.full_like(x32, float("nan"))
+    c.apply_matrix(0, 5, xb.contiguous(), yb, ncols)
+    assert torch.equal(yb, yw)
+    assert _relerr(yw.cpu().numpy().astype(np.complex128), refw) <= 2e-6
 
 
 @pytest.mark.parametrize("cells,ncols", [((7, 6, 5), 2), ((7, 6, 5), 18), ((9, 8, 7), 32), ((9, 8, 7), 48),
@@ -251,6 +263,33 @@ def test_solve_rhs_wide_blocks(ragged, ncols, mode, prec):
     vals = asm.assemble(sysm, eps, 1e9, EPS_MATCHING)
     Xref = solve.solve_direct(sysm, vals, B.T)
     assert _relerr(xd.cpu().numpy().T, Xref) <= (1e-8 if mode == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("ncols", [5, 40])
+def test_z_storage_bf16_and_fp32(ragged, ncols):
+    """The preconditioned vectors of the tensor-core path stored as BF16 pairs (default) or FP32.
+    Flexible GMRES uses the stored z in both A z and x += Z y, so either storage reaches the
+    tolerance and the oracle's direct solve; BF16 rounding of z only perturbs the (already BF16)
+    preconditioner, so the Arnoldi step counts stay within 15% of each other."""
+    mw = _mw()
+    m, eps, pos, direc, sysm = ragged
+    c = _ctx(m, eps, [1e9], pos, direc)
+    c.setup_preconditioner(4, box_partition(m, (2, 2, 1), seed=7), 1, mw.MW_PREC_BF16)
+    E = sysm.topo.n_edge
+    rng = np.random.default_rng(500 + ncols)
+    B = rng.normal(size=(ncols, E)) + 1j * rng.normal(size=(ncols, E))
+    bd = torch.from_numpy(B).cuda()
+    Xref = solve.solve_direct(sysm, asm.assemble(sysm, eps, 1e9, EPS_MATCHING), B.T)
+    steps = {}
+    for bf16 in (True, False):
+        c.set_z_storage(bf16)
+        xd = torch.empty_like(bd)
+        st = c.solve_rhs(ncols, bd, xd, mw.solve_opts(mode=mw.MW_MODE_MIXED, tol=1e-10))
+        assert st["n_converged"] == ncols and st["max_relres"] <= 1e-10
+        assert _relerr(xd.cpu().numpy().T, Xref) <= 1e-6
+        steps[bf16] = st["arnoldi_steps"]
+    assert abs(steps[True] - steps[False]) <= 0.15 * steps[False], steps
+    assert c.lib.mw_set_z_storage(c.h, 2) == mw.MW_EINVAL
 
 
 @pytest.mark.parametrize("mode,prec,ncols", [(0, 0, 5), (1, 2, 5), (1, 2, 32)])

@@ -70,14 +70,16 @@ def test_launch_shapes_bit_identical(box):
     B = rng.normal(size=(32, E)) + 1j * rng.normal(size=(32, E))
     bd = torch.from_numpy(B).cuda()
     opts = mw.solve_opts(mode=mw.MW_MODE_MIXED, tol=1e-10)
-    c.set_autotune(False)
-    x_ref = torch.empty_like(bd)
-    st_ref = c.solve_rhs(32, bd, x_ref, opts)
-    assert st_ref["n_converged"] == 32
-    c.set_autotune(True)
-    for tc, dots, upd, spmm in [(2, 2, 6, 128), (tc_max, 6, 2, 512), (3, 5, 3, 256), (4, 4, 4, 1)]:
-        c.set_launch_shapes(32, mw.MW_MODE_MIXED, 50, tc, dots, upd, spmm)
-        x = torch.empty_like(bd)
-        st = c.solve_rhs(32, bd, x, opts)
-        assert torch.equal(x, x_ref), (tc, dots, upd, spmm)
-        assert np.array_equal(st["iters"], st_ref["iters"])
+    for z_bf16 in (True, False):                          # preconditioned vectors in BF16 or FP32
+        c.set_z_storage(z_bf16)
+        c.set_autotune(False)
+        x_ref = torch.empty_like(bd)
+        st_ref = c.solve_rhs(32, bd, x_ref, opts)
+        assert st_ref["n_converged"] == 32
+        c.set_autotune(True)
+        for tc, dots, upd, spmm in [(2, 2, 6, 128), (tc_max, 6, 2, 512), (3, 5, 3, 256), (4, 4, 4, 1)]:
+            c.set_launch_shapes(32, mw.MW_MODE_MIXED, 50, tc, dots, upd, spmm)
+            x = torch.empty_like(bd)
+            st = c.solve_rhs(32, bd, x, opts)
+            assert torch.equal(x, x_ref), (z_bf16, tc, dots, upd, spmm)
+            assert np.array_equal(st["iters"], st_ref["iters"])
