@@ -913,15 +913,15 @@ __device__ __forceinline__ float2 zval(uint32_t u) {
 // column c in the basis precision with the operations of update_x_kernel, in the same order
 // (bit-identical x), and adds it to x in FP64.  y is staged in shared memory as T.  ZT is the
 // stored type of Z: T, or uint32_t for complex BF16 pairs (T = float2; the widened values enter
-// the same operations as update_x_bx_kernel's, bit-identical to it); the tiles hold
-// bd_rows<ZT>() rows per row group, 16 KB per stage either way.
+// the same operations as update_x_bx_kernel's, bit-identical to it); the tiles keep
+// bd_rows<T>() rows per row group, so BF16 tiles fill half a stage.
 template <typename T, typename ZT = T>
 __global__ void __launch_bounds__(kBdThreads, 2)
     update_x_bulk_kernel(const ZT* __restrict__ Z, int64_t zstride, const double2* __restrict__ y,
                          const int32_t* __restrict__ kcol, int m, double2* __restrict__ x, int64_t E, int R, int G,
                          int NS, int32_t* __restrict__ err) {
   using Sc = typename Traits<T>::S;
-  constexpr int RPT = bd_rows<ZT>();
+  constexpr int RPT = bd_rows<T>();
   constexpr int kStageElems = kBdStageBytes / (int)sizeof(ZT);
   extern __shared__ __align__(128) uint8_t ux_smem[];
   ZT* stage = reinterpret_cast<ZT*>(ux_smem);
