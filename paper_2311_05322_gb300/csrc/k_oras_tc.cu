@@ -131,17 +131,22 @@ __global__ void pack_w_kernel(const int64_t* __restrict__ nmat, const int64_t* _
   }
 }
 
-// The same tiles from strided FP32 blocks: "subdomain" q of the plan is the product sign_q A_q
-// [m][k] (row stride lda, at element a_off of src; the sign of the task, +1 or -1, is exact in
-// BF16), one block per (q, m tile, k tile).
-__global__ void pack_w_blocks_kernel(const MfTask* __restrict__ tasks, int q0, const int64_t* __restrict__ sub_wtile,
-                                     const int32_t* __restrict__ sub_kt, const float2* __restrict__ src,
-                                     uint8_t* __restrict__ W) {
+// The same tiles from strided FP32 blocks: "subdomain" q of the plan stacks up to two products
+// with the same B, rows [0, m1) the product sign_1 A_1 of task first[q] and rows [m1, m1 + m2)
+// the product sign_2 A_2 of task second[q] (second[q] < 0: none); A_i [m_i][k] has row stride
+// lda_i at element a_off_i of src, both tasks have the same k, and the signs (+1 or -1) are
+// exact in BF16.  One block per (q, m tile, k tile).
+__global__ void pack_w_stacked_kernel(const MfTask* __restrict__ tasks, const int32_t* __restrict__ first,
+                                      const int32_t* __restrict__ second, int q0,
+                                      const int64_t* __restrict__ sub_wtile, const int32_t* __restrict__ sub_kt,
+                                      const float2* __restrict__ src, uint8_t* __restrict__ W) {
   const int q = q0 + (int)blockIdx.z;
-  const MfTask t = tasks[q];
+  const MfTask t1 = tasks[first[q]];
+  const int j2 = second[q];
+  const int64_t m2 = j2 >= 0 ? tasks[j2].m : 0;
   const int mt = blockIdx.y, kt = blockIdx.x;
   const int KT = sub_kt[q];
-  if (kt >= KT || (int64_t)mt * kTileM >= t.m) return;
+  if (kt >= KT || (int64_t)mt * kTileM >= t1.m + m2) return;
   uint8_t* tr = W + ((size_t)sub_wtile[q] + ((size_t)mt * KT + kt) * 2) * kATileBytes;
   uint8_t* ti = tr + kATileBytes;
   constexpr int kPairs = kTileKd / 2;
@@ -149,8 +154,9 @@ __global__ void pack_w_blocks_kernel(const MfTask* __restrict__ tasks, int q0, c
     const int r = w / kPairs, kp = w % kPairs;
     const int64_t row = (int64_t)mt * kTileM + r, k = (int64_t)kt * kTileKd + 2 * kp;
     float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
-    if (row < t.m) {
-      const float2* a = src + t.a_off + row * t.lda;
+    if (row < t1.m + m2) {
+      const MfTask t = row < t1.m ? t1 : tasks[j2];
+      const float2* a = src + t.a_off + (row < t1.m ? row : row - t1.m) * t.lda;
       if (k < t.k) {
         re0 = t.sign * a[k].x;
         im0 = t.sign * a[k].y;
@@ -508,13 +514,13 @@ void tc_extract(const TcPlan& p, const OrasBatch& bt, const OrasTopo& tp, int ws
                                                 tp.own_local, p.sub_wtile, p.sub_kt, (uint8_t*)W);
 }
 
-void tc_pack_blocks(const TcPlan& p, const MfTask* tasks, int n, int ktmax, int mtmax, const float2* src, void* W,
-                    cudaStream_t s) {
+void tc_pack_stacked(const TcPlan& p, const MfTask* tasks, const int32_t* first, const int32_t* second, int n,
+                     int ktmax, int mtmax, const float2* src, void* W, cudaStream_t s) {
   for (int q0 = 0; q0 < n; q0 += 65535) {
     const int cnt = std::min(65535, n - q0);
     note_launch(1);
     dim3 grid((unsigned)std::max(ktmax, 1), (unsigned)std::max(mtmax, 1), (unsigned)cnt);
-    pack_w_blocks_kernel<<<grid, 256, 0, s>>>(tasks, q0, p.sub_wtile, p.sub_kt, src, (uint8_t*)W);
+    pack_w_stacked_kernel<<<grid, 256, 0, s>>>(tasks, first, second, q0, p.sub_wtile, p.sub_kt, src, (uint8_t*)W);
   }
 }
 

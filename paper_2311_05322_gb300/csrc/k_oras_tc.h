@@ -40,10 +40,13 @@ size_t tc_scratch_bytes(const TcPlan& p, int R);
 void tc_extract(const TcPlan& p, const OrasBatch& bt, const OrasTopo& tp, int ws_prec, const void* ws, void* W,
                 cudaStream_t s);
 struct MfTask;
-// Packs the FP32 blocks of tasks[0 .. n) (A = src + a_off, [m][k], row stride lda) into the
-// plan's BF16 tiles (plan "subdomain" q = task q); ktmax / mtmax: the largest tile counts.
-void tc_pack_blocks(const TcPlan& p, const MfTask* tasks, int n, int ktmax, int mtmax, const float2* src, void* W,
-                    cudaStream_t s);
+// Packs the FP32 blocks of tasks (A = src + a_off, [m][k], row stride lda, times the task's
+// sign) into the plan's BF16 tiles for n plan "subdomains" that each stack up to two products
+// with the same B (same k): subdomain q is task first[q] over task second[q] (rows of the second
+// after those of the first; second[q] < 0: the first alone); ktmax / mtmax: the largest tile
+// counts of the stacked products.
+void tc_pack_stacked(const TcPlan& p, const MfTask* tasks, const int32_t* first, const int32_t* second, int n,
+                     int ktmax, int mtmax, const float2* src, void* W, cudaStream_t s);
 // stages: shared-memory pipeline depth of the MMA kernel (0 = default; the result does not depend
 // on it, only the speed).  in_scale (may be null): per-column factor of r (z = M^{-1}(r * in_scale)).
 // Output row q of "subdomain" s goes to z row own_glob[own_ptr[s] + q] (skipped when negative);

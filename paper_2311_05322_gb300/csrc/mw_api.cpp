@@ -105,7 +105,11 @@ struct Prec {
       int32_t* c0_glob = nullptr;    // per output row: arena row of C0, or -1
       mwk::MfTask* tasks = nullptr;  // products with K > 0 (plan order), then those with K = 0
       mwk::MfSplit* splits = nullptr;
+      int32_t *pk_first = nullptr, *pk_second = nullptr;   // tasks stacked in each plan "subdomain"
       int n_tc = 0, n_splits = 0, ktmax = 0, mtmax = 0;
+      // the plan's B rows are rows of the input vector (the leaves' pivot entries), not arena
+      // rows: the launch gathers straight from the input and the leaves' pull is skipped
+      bool from_input = false;
       std::vector<void*> W;          // BF16 tiles per frequency
     };
     std::vector<TcLaunch> tcl;       // [2 (H + 1)]: forward heights, then backward heights
@@ -528,14 +532,16 @@ void apply_sparse(Ctx* c, int f, const float2* v, float2* z, int R) {
         // C = C0 + (sign A) B straight from the MMA epilogue into the arena
         const mwk::OrasTopo tp{L.dof_ptr, L.dofs, L.own_ptr, L.own_local, L.own_glob, nullptr, nullptr, nullptr,
                                nullptr, nullptr, nullptr};
-        mwk::oras_apply_tc(L.plan, tp, L.W[f], arena, arena, R, w.tc_scratch, s, 0, nullptr, L.c0_glob);
+        mwk::oras_apply_tc(L.plan, tp, L.W[f], L.from_input ? v : arena, arena, R, w.tc_scratch, s, 0, nullptr,
+                           L.c0_glob);
       }
       // products with K = 0: C = C0
       if (L.n_splits > 0) mwk::mf_reduce(L.tasks, L.splits, L.n_splits, partial, m.idx, R, arena, s);
     };
     for (int h = 0; h <= H; ++h) {
-      mwk::mf_pull(m.pull_out + m.pull_h[h], m.pull_ptr + m.pull_h[h], m.pull_src, m.pull_h[h + 1] - m.pull_h[h], v,
-                   R, arena, s);
+      if (!m.tcl[h].from_input)
+        mwk::mf_pull(m.pull_out + m.pull_h[h], m.pull_ptr + m.pull_h[h], m.pull_src, m.pull_h[h + 1] - m.pull_h[h],
+                     v, R, arena, s);
       run(m.tcl[h]);
     }
     for (int h = H; h >= 0; --h) run(m.tcl[H + 1 + h]);
@@ -564,7 +570,8 @@ T* mf_up(Ctx* c, Prec::Mf& m, const std::vector<T>& h) {
   return d;
 }
 
-void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launches, const std::vector<int32_t>& idx);
+void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launches, const std::vector<int32_t>& idx,
+                     const std::vector<int32_t>& leaf_in);
 
 // Symbolic factorisation on the host, device tables, then the numeric factorisation of every
 // subdomain for every frequency (FP32 fronts in a workspace, partial Gauss-Jordan per height).
@@ -865,7 +872,19 @@ void setup_sparse(Ctx* c) {
   dfree(c, ws);
   dfree(c, dinv);
   dfree(c, status);
-  if (P.apply_prec == 5) build_sparse_tc(c, launches, idx);
+  if (P.apply_prec == 5) {
+    // input row of each arena row that the leaves' pull fills (-1: an identity-padded pivot,
+    // zero; -2: not such a row)
+    std::vector<int32_t> leaf_in((size_t)rows, -2);
+    for (int64_t i = m.pull_h[0]; i < m.pull_h[1]; ++i) {
+      const int64_t n_src = pull_ptr[i + 1] - pull_ptr[i];
+      if (n_src == 0)
+        leaf_in[pull_out[i]] = -1;
+      else if (n_src == 1 && pull_src[pull_ptr[i]] < 0)
+        leaf_in[pull_out[i]] = (int32_t)(-pull_src[pull_ptr[i]] - 1);
+    }
+    build_sparse_tc(c, launches, idx, leaf_in);
+  }
 }
 
 // BF16 tensor-core form of the sweeps: per launch, a tile plan whose "subdomains" are the
@@ -873,7 +892,8 @@ void setup_sparse(Ctx* c) {
 // arena rows of C0 added in the MMA epilogue), the BF16 tiles of their FP32 factor blocks times
 // the product's sign for every frequency, and one reduction split per 64-row tile of the
 // products with K = 0 (C = C0).  The FP32 factors are then freed.
-void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launches, const std::vector<int32_t>& idx) {
+void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launches, const std::vector<int32_t>& idx,
+                     const std::vector<int32_t>& leaf_in) {
   Prec& P = c->prec;
   Prec::Mf& m = P.mf;
   const char* bad = "internal: sparse tensor-core table out of range";
@@ -886,43 +906,75 @@ void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launch
     T.n_tc = (int)ord.size();
     for (const auto& t : launches[L])
       if (t.k <= 0) ord.push_back(t);
+    auto b_row_of = [&](const mwk::MfTask& t, int64_t i) {
+      return t.b_idx >= 0 ? (int64_t)idx[t.b_idx + i] : t.b_row + i;
+    };
+    // the first forward launch (the leaves) reads its B rows from the input when every one of
+    // them is a leaf pivot row that the pull would only copy
+    T.from_input = L == 0 && T.n_tc > 0;
+    for (int q = 0; q < T.n_tc && T.from_input; ++q)
+      for (int64_t i = 0; i < ord[q].k && T.from_input; ++i) {
+        const int64_t row = b_row_of(ord[q], i);
+        T.from_input = row >= 0 && row < (int64_t)leaf_in.size() && leaf_in[row] >= -1;
+      }
+    // plan "subdomains": consecutive products with the same B (the forward t and w products of
+    // a front) are stacked, so B is gathered once and their rows share the MMA tiles
     mw::Subdomains fake;
-    fake.n_sub = T.n_tc;
     fake.dof_ptr.assign(1, 0);
     fake.own_ptr.assign(1, 0);
-    std::vector<int32_t> own_glob, c0_glob;
+    std::vector<int32_t> own_glob, c0_glob, first, second;
     std::vector<mwk::MfSplit> sp;
     int64_t slot = 0;
-    for (int q = 0; q < (int)ord.size(); ++q) {
+    for (int q = 0; q < T.n_tc;) {
       const mwk::MfTask& t = ord[q];
-      if (q < T.n_tc) {
-        for (int64_t i = 0; i < t.k; ++i) {
-          const int64_t row = t.b_idx >= 0 ? (int64_t)idx[t.b_idx + i] : t.b_row + i;
-          require(row >= 0 && row < m.arena_rows, MW_EINVAL, bad);
+      int q2 = -1;
+      if (q + 1 < T.n_tc) {
+        const mwk::MfTask& u = ord[q + 1];
+        if (u.k == t.k && u.b_idx == t.b_idx && (t.b_idx >= 0 || u.b_row == t.b_row)) q2 = q + 1;
+      }
+      first.push_back(q);
+      second.push_back(q2);
+      for (int64_t i = 0; i < t.k; ++i) {
+        const int64_t row = b_row_of(t, i);
+        require(row >= 0 && row < m.arena_rows, MW_EINVAL, bad);
+        if (T.from_input) {
+          const int32_t in = leaf_in[row];
+          require(in >= -1 && in < c->topo.n_edge, MW_EINVAL, bad);
+          fake.dofs.push_back(in);
+        } else {
           fake.dofs.push_back((int32_t)row);
         }
-        fake.dof_ptr.push_back((int64_t)fake.dofs.size());
-        for (int64_t r = 0; r < t.m; ++r) {
-          const int64_t crow = t.c_idx >= 0 ? (int64_t)idx[t.c_idx + r] : t.c_row + r;
-          const int64_t c0 = t.c0_row >= 0 ? t.c0_row + r : -1;
+      }
+      fake.dof_ptr.push_back((int64_t)fake.dofs.size());
+      int64_t r_out = 0;
+      for (int qq : {q, q2}) {
+        if (qq < 0) continue;
+        const mwk::MfTask& tt = ord[qq];
+        for (int64_t r = 0; r < tt.m; ++r, ++r_out) {
+          const int64_t crow = tt.c_idx >= 0 ? (int64_t)idx[tt.c_idx + r] : tt.c_row + r;
+          const int64_t c0 = tt.c0_row >= 0 ? tt.c0_row + r : -1;
           require(crow >= -1 && crow < m.arena_rows && c0 >= -1 && c0 < m.arena_rows, MW_EINVAL, bad);
-          fake.own_local.push_back((int32_t)r);
+          fake.own_local.push_back((int32_t)r_out);
           own_glob.push_back((int32_t)crow);
           c0_glob.push_back((int32_t)c0);
         }
-        fake.own_ptr.push_back((int64_t)fake.own_local.size());
-        T.ktmax = std::max<int>(T.ktmax, (int)((t.k + 63) / 64));
-        T.mtmax = std::max<int>(T.mtmax, (int)((t.m + 127) / 128));
-        continue;
       }
-      for (int64_t r0 = 0; r0 < t.m; r0 += mwk::kMfTileRows) sp.push_back({q, (int32_t)r0, 0, 0});
+      fake.own_ptr.push_back((int64_t)fake.own_local.size());
+      T.ktmax = std::max<int>(T.ktmax, (int)((t.k + 63) / 64));
+      T.mtmax = std::max<int>(T.mtmax, (int)((r_out + 127) / 128));
+      q += q2 >= 0 ? 2 : 1;
     }
+    fake.n_sub = (int)first.size();
+    for (int q = T.n_tc; q < (int)ord.size(); ++q)
+      for (int64_t r0 = 0; r0 < ord[q].m; r0 += mwk::kMfTileRows) sp.push_back({q, (int32_t)r0, 0, 0});
     require(slot * mwk::kMfTileRows < INT32_MAX, MW_EINVAL, bad);
     m.tc_slots = std::max<int64_t>(m.tc_slots, slot);
     T.n_splits = (int)sp.size();
     T.tasks = mf_up(c, m, ord);
     T.splits = mf_up(c, m, sp);
     if (T.n_tc == 0) continue;
+    T.pk_first = mf_up(c, m, first);
+    T.pk_second = mf_up(c, m, second);
     T.dof_ptr = mf_up(c, m, fake.dof_ptr);
     T.dofs = mf_up(c, m, fake.dofs);
     T.own_ptr = mf_up(c, m, fake.own_ptr);
@@ -935,7 +987,8 @@ void build_sparse_tc(Ctx* c, const std::vector<std::vector<mwk::MfTask>>& launch
     T.W.assign(c->n_freq, nullptr);
     for (int f = 0; f < c->n_freq; ++f) {
       T.W[f] = dalloc<unsigned char>(c, std::max<size_t>(mwk::tc_w_bytes(T.plan), 16));
-      mwk::tc_pack_blocks(T.plan, T.tasks, T.n_tc, T.ktmax, T.mtmax, (const float2*)m.fac[f], T.W[f], c->stream);
+      mwk::tc_pack_stacked(T.plan, T.tasks, T.pk_first, T.pk_second, fake.n_sub, T.ktmax, T.mtmax,
+                           (const float2*)m.fac[f], T.W[f], c->stream);
     }
     check_launch("sparse tensor-core packing");
   }
