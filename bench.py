@@ -843,7 +843,7 @@ def inversion_leg(scale):
     inv = r["inversion"]
     return {"metric": "inversion time-to-misfit", "unit": "s", "higher_is_better": False, "scale": scale,
             "config": r["config"], "time_to_target_s": {k: v["time_to_target_s"] for k, v in inv.items()},
-            "target_J": r["target_J"], "target_from": r["target_from"],
+            "target_J": r["target_J"], "target_rel_band": r["target_rel_band"], "target_from": r["target_from"],
             "J_first_last": {k: [v["J"][0], v["J"][-1]] for k, v in inv.items()},
             "seconds_total": {k: v["seconds"][-1] for k, v in inv.items()},
             "plain_fp64_setup_s": r.get("plain_fp64_setup_s"), "network": r["network"],

@@ -46,6 +46,12 @@ TARGET_SCALE = 20.0      # Delta eps is trained in units of 20
 # inner-cycle reduction of the mixed solves (GMRES-IR; 1e-8 is decided by the outer FP64 residual):
 # on the inverse meshes 1e-4 measured faster than 1e-2 (4.63 s against 4.79 s at full scale)
 INNER_TOL = 1e-4
+# An arm reaches the target misfit when its J is within this relative band of it.  The arms'
+# J agree only to the forward solves' tolerance (relres 1e-8): the misfit is a small difference
+# of S-matrices, so its relative error is far larger; measured between the plain FP64 and the
+# mixed arm at the same eps (iteration 0) 5e-6, and 1.3e-5 after ten L-BFGS iterations.  The
+# band is ten times that.
+TARGET_REL_BAND = 1e-4
 TARGET_BLUR_M = 0.003    # targets are blurred to about the resolution the inverse mesh can carry
 FLUID_RANGE = ((60.0, 75.0), (25.0, 40.0))
 
@@ -264,10 +270,10 @@ def run(scale: str = "reduced", seed: int = 3, plain: bool | None = None, snr_db
         if given:
             target = target_J
         for v in res.values():
-            v["time_to_target_s"] = first_time_below(v["J"], v["seconds"], target)
+            v["time_to_target_s"] = first_time_below(v["J"], v["seconds"], target * (1.0 + TARGET_REL_BAND))
         cases.append({"tear": {"center": tear.center, "semi_axes": tear.semi_axes,
                                "eps": [tear.eps.real, tear.eps.imag]},
-                      "inversion": res, "target_J": target,
+                      "inversion": res, "target_J": target, "target_rel_band": TARGET_REL_BAND,
                       "target_from": "plain_fp64 after max_it" if "plain_fp64" in res else
                       ("plain_fp64 after max_it, given" if given else "mixed after max_it"),
                       "learned_start_dJ0": res["mixed_learned"]["J"][0] - res["mixed"]["J"][0],
@@ -276,7 +282,8 @@ def run(scale: str = "reduced", seed: int = 3, plain: bool | None = None, snr_db
         if verbose:
             print(json.dumps(cases[-1]), flush=True)
     # the first tear's record keeps the single-tear keys
-    out.update({k: cases[0][k] for k in ("inversion", "target_J", "target_from", "tear", "learned_start_dJ0")})
+    out.update({k: cases[0][k] for k in ("inversion", "target_J", "target_rel_band", "target_from", "tear",
+                                         "learned_start_dJ0")})
     out["cases"] = cases
     out["summary"] = {
         "tears": len(cases),
@@ -286,7 +293,8 @@ def run(scale: str = "reduced", seed: int = 3, plain: bool | None = None, snr_db
         "learned_start_rel_dJ0": _stats([c["learned_start_rel_dJ0"] for c in cases]),
         "learned_reaches_target_first": sum(
             1 for c in cases if c["inversion"]["mixed_learned"]["time_to_target_s"] is not None
-            and c["inversion"]["mixed_learned"]["time_to_target_s"] < c["inversion"]["mixed"]["time_to_target_s"]),
+            and (c["inversion"]["mixed"]["time_to_target_s"] is None
+                 or c["inversion"]["mixed_learned"]["time_to_target_s"] < c["inversion"]["mixed"]["time_to_target_s"])),
     }
     sweep = []
     for a in alphas:
