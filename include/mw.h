@@ -418,6 +418,14 @@ mw_status mw_set_adjoint_mode(mw_ctx* ctx, int32_t mode);
  * captured solve graphs when the setting changes.  MW_EINVAL for another value. */
 mw_status mw_set_z_storage(mw_ctx* ctx, int32_t bf16);
 
+/* Schedule of the BF16 tensor-core sweeps of MW_PREC_SPARSE_BF16 (Sec. IV-C's subdomain solves;
+ * elsewhere no effect).  1 (default): each sweep launch runs persistent CTAs that take its
+ * 128-row output tiles in turn, with one copy ring across their tiles and the accumulators
+ * double-buffered in tensor memory, so one tile's epilogue overlaps the next tile's copies and
+ * MMAs (up to 64 columns; wider blocks use the other schedule); 0: one CTA per tile.  The same
+ * products in the same order either way: bit-identical results.  MW_EINVAL for another value. */
+mw_status mw_set_sweep_schedule(mw_ctx* ctx, int32_t persistent);
+
 /* ---- column-sharded evaluation (one evaluation split over processes by transmitters) ---
  * The transmitter columns of an evaluation are independent until the cost: process r solves
  * its own window of columns (mw_forward_cols), the S columns of all windows are all-gathered

@@ -414,6 +414,200 @@ __global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_kernel(const TcArgs a) 
   }
 }
 
+// Persistent form of oras_tc_kernel for plans of many short tiles (the sparse sweeps): the CTAs
+// take the 128-row output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; one copy ring runs
+// across the CTA's tiles, and the accumulators are double-buffered in tensor memory (buffer
+// i % 2 for the CTA's i-th tile), so the epilogue of one tile overlaps the copies and MMAs of
+// the next.  Per tile: the same copies, MMAs in the same order and the same epilogue arithmetic
+// as oras_tc_kernel, so z is bit-identical.  Waits are bounded: a wait that runs out records an
+// error code and sets the abort flag, every role then stops, the producer drains its copies and
+// the MMA warp waits (bounded) for its last MMAs before the accumulators are freed.
+__global__ void __launch_bounds__(kThreadsTc, 2) oras_tc_persistent_kernel(const TcArgs a, int n_tiles) {
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t full_bar[8];
+  __shared__ __align__(8) uint64_t empty_bar[8];
+  __shared__ __align__(8) uint64_t acc_full[2];
+  __shared__ __align__(8) uint64_t acc_empty[2];
+  __shared__ __align__(8) uint64_t fin_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = a.stages;
+  const uint32_t b_bytes = (uint32_t)a.N * 128u;
+  const uint32_t a_bytes = 2u * kATileBytes;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  volatile int* abort_v = &abort_flag;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&empty_bar[i], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);   // one arrival per epilogue warp
+    }
+    mbar_init(&fin_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(2u * a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t it = 0;   // k tiles issued by this CTA (running ring position)
+      for (int t = blockIdx.x; t < n_tiles && !*abort_v; t += gridDim.x) {
+        const int s = a.mt_sub[t];
+        const int row0 = a.mt_row0[t];
+        const int KT = a.sub_kt[s];
+        const uint8_t* Wt = a.W + ((size_t)a.sub_wtile[s] + (size_t)(row0 / kTileM) * KT * 2) * kATileBytes;
+        const uint8_t* Bs = a.Bt + (size_t)a.sub_gtile[s] * b_bytes;
+        const int64_t nown_p = a.own_ptr[s + 1] - a.own_ptr[s];
+        const int rows_valid = (int)min((int64_t)kTileM, nown_p - (int64_t)row0);
+        const uint32_t a_part = (uint32_t)((rows_valid + 7) / 8) * 1024u;
+        for (int kt = 0; kt < KT; ++kt, ++it) {
+          const int st = (int)(it % S);
+          if (it >= S && !mbar_wait(&empty_bar[st], (uint32_t)(((it / S) + 1) & 1))) {
+            atomicCAS(a.err, 0, 11);
+            *abort_v = 1;
+          }
+          if (*abort_v) break;
+          uint8_t* sa = base + (size_t)st * stage_bytes;
+          uint8_t* sb = sa + a_bytes;
+          mbar_expect_tx(&full_bar[st], 2u * a_part + b_bytes);
+          bulk_g2s(sa, Wt + (size_t)kt * a_bytes, a_part, &full_bar[st]);
+          bulk_g2s(sa + kATileBytes, Wt + (size_t)kt * a_bytes + kATileBytes, a_part, &full_bar[st]);
+          bulk_g2s(sb, Bs + (size_t)kt * b_bytes, b_bytes, &full_bar[st]);
+        }
+      }
+      // drain: every issued copy has completed before this thread leaves
+      for (int64_t k = (it > S ? it - S : 0); k < it; ++k)
+        if (!mbar_wait(&full_bar[k % S], (uint32_t)((k / S) & 1))) atomicCAS(a.err, 0, 12);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(a.N);
+      int64_t it = 0;
+      int i = 0;   // tiles of this CTA
+      for (int t = blockIdx.x; t < n_tiles && !*abort_v; t += gridDim.x, ++i) {
+        const int KT = a.sub_kt[a.mt_sub[t]];
+        const int buf = i & 1;
+        if (i >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)(((i >> 1) + 1) & 1))) {
+          atomicCAS(a.err, 0, 13);
+          *abort_v = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc0 = tmem + (uint32_t)buf * a.tmem_cols;
+        bool stop = false;
+        for (int kt = 0; kt < KT; ++kt, ++it) {
+          const int st = (int)(it % S);
+          if (!mbar_wait(&full_bar[st], (uint32_t)((it / S) & 1))) {
+            atomicCAS(a.err, 0, 14);
+            *abort_v = 1;
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sar = smem_u32(base + (size_t)st * stage_bytes);
+          const uint32_t sai = sar + kATileBytes;
+          const uint32_t sb = sar + a_bytes;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
+            mma_bf16(acc0, smem_desc(sar + 32u * k), smem_desc(sb + 32u * k), idesc, acc);
+            mma_bf16(acc0 + (uint32_t)a.N, smem_desc(sai + 32u * k), smem_desc(sb + 32u * k), idesc, acc);
+          }
+          mma_commit(&empty_bar[st]);
+        }
+        if (stop) break;
+        mma_commit(&acc_full[buf]);
+      }
+      // every MMA issued by this CTA has completed before the accumulators are freed
+      mma_commit(&fin_bar);
+      if (!mbar_wait(&fin_bar, 0)) atomicCAS(a.err, 0, 15);
+    }
+  } else {
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    const int Rp = a.N / 2;
+    int i = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
+      const int s = a.mt_sub[t];
+      const int row0 = a.mt_row0[t];
+      const int buf = i & 1;
+      const int64_t nown = a.own_ptr[s + 1] - a.own_ptr[s];
+      const int64_t q = (int64_t)row0 + row;
+      const int64_t og = q < nown ? (int64_t)a.own_glob[a.own_ptr[s] + q] : -1;
+      const int64_t c0 = (og >= 0 && a.c0_glob) ? (int64_t)a.c0_glob[a.own_ptr[s] + q] : -1;
+      const float2* c0r = c0 >= 0 ? a.z + c0 * a.R : nullptr;
+      float2 nxt[8];
+      auto fetch_c0 = [&](int cb) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) nxt[j] = (c0r && cb + j < a.R) ? c0r[cb + j] : make_float2(0.f, 0.f);
+      };
+      fetch_c0(0);
+      bool ok = !*abort_v && mbar_wait(&acc_full[buf], (uint32_t)((i >> 1) & 1));
+      ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
+      if (!ok) {
+        if (lane == 0) {
+          atomicCAS(a.err, 0, 16);
+          *abort_v = 1;
+        }
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const bool valid = og >= 0;
+      float2* zr = valid ? a.z + og * a.R : nullptr;
+      const uint32_t lanes = tmem + (uint32_t)buf * a.tmem_cols + ((uint32_t)(quad * 32) << 16);
+      for (int cb = 0; cb < Rp; cb += 8) {
+        float2 cur[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cur[j] = nxt[j];
+        if (cb + 8 < Rp) fetch_c0(cb + 8);
+        float rr[8], ri[8], ir[8], ii[8];
+        tmem_ld8(lanes + (uint32_t)cb, rr);
+        tmem_ld8(lanes + (uint32_t)(Rp + cb), ri);
+        tmem_ld8(lanes + (uint32_t)(a.N + cb), ir);
+        tmem_ld8(lanes + (uint32_t)(a.N + Rp + cb), ii);
+        if (valid) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int col = cb + j;
+            if (col >= a.R) continue;
+            float2 v = make_float2(rr[j] - ii[j], ri[j] + ir[j]);
+            if (c0r) v = make_float2(v.x + cur[j].x, v.y + cur[j].y);
+            if (a.z_bf16)
+              reinterpret_cast<uint32_t*>(a.z)[og * a.R + col] = pack_bf16(v.x, v.y);
+            else
+              zr[col] = v;
+          }
+        }
+      }
+      // this warp's reads of the buffer are done: the MMA warp may overwrite it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * a.tmem_cols)
+                 : "memory");
+  }
+}
+
 // Self-test of the bounded wait: waits on an mbarrier that expects two arrivals but receives
 // one, so the phase never completes; the wait gives up after `limit` polls and the kernel
 // reports MW_ETIMEOUT (5) in *code instead of hanging.
@@ -548,7 +742,7 @@ int tc_max_stages(int R) {
 
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
                    void* scratch, cudaStream_t s, int stages, const double* in_scale, const int32_t* c0_glob,
-                   bool z_bf16) {
+                   bool z_bf16, bool persistent) {
   const int Rp = rpad(R);
   const int N = 2 * Rp;
   if (stages <= 0) stages = tc_stages(N);
@@ -584,6 +778,20 @@ void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const flo
   while ((int)cols < 2 * N) cols <<= 1;   // two accumulators of N columns
   a.tmem_cols = cols;
   a.err = p.err;
+  if (persistent && 2 * cols <= 512) {
+    // two accumulator buffers per CTA; two CTAs per SM while both fit the 512 columns
+    const int per_sm = 4 * cols <= 512 ? 2 : 1;
+    size_t smem = tc_smem_bytes(N, stages);
+    if (per_sm == 1 && smem < (size_t)120 * 1024) smem = (size_t)120 * 1024;
+    static size_t pattr = 0;
+    if (smem > pattr) {
+      cudaFuncSetAttribute(oras_tc_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      pattr = smem;
+    }
+    const int grid = (int)std::min<int64_t>(p.n_mtiles, (int64_t)per_sm * 152);
+    oras_tc_persistent_kernel<<<(unsigned)std::max(grid, 1), kThreadsTc, smem, s>>>(a, (int)p.n_mtiles);
+    return;
+  }
   // two CTAs of an SM must fit their tensor memory (512 columns per SM): above 256 columns the
   // shared-memory request keeps one CTA per SM
   size_t smem = tc_smem_bytes(N, stages);

@@ -52,9 +52,12 @@ void tc_pack_stacked(const TcPlan& p, const MfTask* tasks, const int32_t* first,
 // Output row q of "subdomain" s goes to z row own_glob[own_ptr[s] + q] (skipped when negative);
 // c0_glob (may be null) lists, per output row, a row of z added to it (-1: none).  z_bf16: z is
 // written as complex BF16 pairs (real in the low half), 4 bytes per value, row stride R values.
+// persistent: CTAs loop over the output tiles with one copy ring and double-buffered
+// accumulators (for plans of many short tiles; up to 64 columns, else the one-tile-per-CTA
+// kernel runs); the same bits either way.
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
                    void* scratch, cudaStream_t s, int stages = 0, const double* in_scale = nullptr,
-                   const int32_t* c0_glob = nullptr, bool z_bf16 = false);
+                   const int32_t* c0_glob = nullptr, bool z_bf16 = false, bool persistent = false);
 // Pipeline depths the MMA kernel accepts for R columns: [tc_min_stages, tc_max_stages(R)]; the
 // default depth for R columns.
 constexpr int tc_min_stages = 2;

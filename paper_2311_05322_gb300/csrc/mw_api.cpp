@@ -286,6 +286,7 @@ struct Ctx {
   // [n_freq][n_src][win_nl]
   int win_j0 = 0, win_nl = 0, win_nf = 0, win_ns = 0;
   int adjoint_mode = 0;          // MW_ADJOINT_SOLVE or MW_ADJOINT_RECIPROCAL
+  int sweep_persistent = 1;      // tensor-core sweeps: persistent CTAs over the tiles of a launch
   int z_bf16 = 1;                // preconditioned vectors of the tensor-core path stored in BF16
   double2* d_D = nullptr;        // reciprocity weights [n_src][n_src]
   std::vector<double2*> Xw, Lw, Bw, Bwa;
@@ -533,7 +534,7 @@ void apply_sparse(Ctx* c, int f, const float2* v, float2* z, int R) {
         const mwk::OrasTopo tp{L.dof_ptr, L.dofs, L.own_ptr, L.own_local, L.own_glob, nullptr, nullptr, nullptr,
                                nullptr, nullptr, nullptr};
         mwk::oras_apply_tc(L.plan, tp, L.W[f], L.from_input ? v : arena, arena, R, w.tc_scratch, s, 0, nullptr,
-                           L.c0_glob);
+                           L.c0_glob, false, c->sweep_persistent != 0);
       }
       // products with K = 0: C = C0
       if (L.n_splits > 0) mwk::mf_reduce(L.tasks, L.splits, L.n_splits, partial, m.idx, R, arena, s);
@@ -3055,6 +3056,14 @@ mw_status mw_set_z_storage(mw_ctx* c, int32_t bf16) {
     require(bf16 == 0 || bf16 == 1, MW_EINVAL, "bad Z storage");
     if (c->z_bf16 != bf16) drop_graphs(c);
     c->z_bf16 = bf16;
+  });
+}
+
+mw_status mw_set_sweep_schedule(mw_ctx* c, int32_t persistent) {
+  return guard(c, [&] {
+    require(persistent == 0 || persistent == 1, MW_EINVAL, "bad sweep schedule");
+    if (c->sweep_persistent != persistent) drop_graphs(c);
+    c->sweep_persistent = persistent;
   });
 }
 

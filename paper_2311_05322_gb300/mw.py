@@ -114,6 +114,7 @@ _SIGS = {
                               C.POINTER(mw_inv_history)]),
     "mw_set_adjoint_mode": (C.c_int32, [_P, C.c_int32]),
     "mw_set_z_storage": (C.c_int32, [_P, C.c_int32]),
+    "mw_set_sweep_schedule": (C.c_int32, [_P, C.c_int32]),
     "mw_forward_cols": (C.c_int32, [_P, C.POINTER(mw_solve_opts), C.c_int32, C.c_int32, _P]),
     "mw_gradient_cols": (C.c_int32, [_P, C.POINTER(mw_solve_opts), _P, _P, _P, C.POINTER(C.c_double), _P]),
     "mw_assemble_dev": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
@@ -396,6 +397,11 @@ class Context:
     def set_adjoint_mode(self, reciprocal: bool):
         """Adjoint fields by explicit solves (default) or by reciprocity from the forward fields."""
         self._check(self.lib.mw_set_adjoint_mode(self.h, MW_ADJOINT_RECIPROCAL if reciprocal else MW_ADJOINT_SOLVE))
+
+    def set_sweep_schedule(self, persistent: bool):
+        """Tensor-core sweeps of the sparse preconditioner: persistent CTAs (default) or one CTA
+        per output tile (bit-identical)."""
+        self._check(self.lib.mw_set_sweep_schedule(self.h, 1 if persistent else 0))
 
     def set_z_storage(self, bf16: bool):
         """Preconditioned Krylov vectors of the tensor-core path stored in BF16 (default) or FP32."""

@@ -74,6 +74,14 @@ def test_sparse_apply_matches_oracle(cells, parts, overlap, R, tol, bf16):
     # repeated applies are bit-identical
     _, Z2 = _apply(c, sysm.topo.n_edge, R)
     assert np.array_equal(Z, Z2)
+    if bf16:
+        # the tensor-core sweeps' two schedules (persistent CTAs, the default, and one CTA per
+        # output tile) run the same products in the same order
+        c.set_sweep_schedule(False)
+        _, Z3 = _apply(c, sysm.topo.n_edge, R)
+        c.set_sweep_schedule(True)
+        assert np.array_equal(Z, Z3)
+        assert c.lib.mw_set_sweep_schedule(c.h, 2) == mw.MW_EINVAL
 
 
 def test_sparse_apply_with_ports_and_metal():
