@@ -45,7 +45,7 @@ def _args(argv=None):
     ap.add_argument("--antennas", default="dipoles", choices=["dipoles", "waveguides"],
                     help="z-dipole ring, or ceramic-filled TE10 waveguides on three side walls (Eq. m1 ports)")
     ap.add_argument("--freqs", default="1.0e9", help="comma-separated frequencies (Hz)")
-    ap.add_argument("--parts", default="16x16x7")
+    ap.add_argument("--parts", default="22x22x10")
     ap.add_argument("--overlap", type=int, default=1)
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32", "sparse", "sparse_bf16"],
                     help="subdomain solves: dense inverses applied in BF16 (tensor cores) or FP32, or sparse "
@@ -161,15 +161,18 @@ def make_workload(a):
     return healthy, injured, parts, part
 
 
-def oras_traffic_ratio():
+def oras_traffic_ratio(parts: str):
     """DRAM traffic per algorithmic byte of the ORAS apply from the committed ncu summary, or
-    None when the two kernels' source no longer matches the one the counters were taken on."""
+    None when the summary was taken on another partition or the two kernels' source no longer
+    matches the one the counters were taken on."""
     import hashlib
     prof = os.path.join(ROOT, "profiles", "oras_apply_traffic_shoulder80x80x34.md")
     src = os.path.join(ROOT, "paper_2311_05322_gb300", "csrc", "k_oras_tc.cu")
     if not (os.path.exists(prof) and os.path.exists(src)):
         return None
     kv = dict(l.split(": ", 1) for l in open(prof).read().splitlines() if ": " in l and not l.startswith("|"))
+    if kv.get("partition", "").strip() != parts:
+        return None
     text = open(src).read()
 
     def body(sig):
@@ -487,8 +490,8 @@ def _dominant_roofline(prof, ms_step_total, hbm, src, prec, a, L):
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-    ratio = oras_traffic_ratio() if dom == "oras_apply" and prec == mw.MW_PREC_BF16 and a.cells == "80x80x34" \
-        and a.parts == "16x16x7" and a.antennas == "dipoles" and a.n_src == 32 else None
+    ratio = oras_traffic_ratio(a.parts) if dom == "oras_apply" and prec == mw.MW_PREC_BF16 and a.cells == "80x80x34" \
+        and a.antennas == "dipoles" and a.n_src == 32 else None
     traffic = ratio * d["bytes"] / max(d["launches"], 1) if ratio else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_source": src, "traffic": traffic,
@@ -722,7 +725,7 @@ def run_mine(a):
                      "solve_ms": st["solve_ms"], "arnoldi_steps": st["arnoldi_steps"],
                      "max_relres": st["max_relres"], "preconditioner_setup_s": ps,
                      "note": "FP64 operator, FP64 Krylov basis, FP64 apply of FP32-factorised subdomain inverses "
-                             "(an FP64 factorisation of these 1792 subdomains takes minutes at GB300's FP64 rate), "
+                             f"(an FP64 factorisation of these {n_sub} subdomains takes minutes at GB300's FP64 rate), "
                              "one column per launch"}
         except Exception as e:  # report, do not hide
             plain = {"error": str(e)}
