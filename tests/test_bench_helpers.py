@@ -39,3 +39,13 @@ def test_variant_options_parse(bench):
     assert bench._dims(a.parts) == (4, 4, 1)
     d = bench._args([])
     assert d.prec == "bf16" and d.antennas == "dipoles" and d.gpus == 1 and d.steps >= 1 and d.warmup >= 3
+
+
+def test_oras_traffic_ratio_follows_its_partition(bench):
+    """The roofline's DRAM traffic comes from the committed ncu summary only for the partition
+    and kernel sources it was taken on; the default line's partition is that partition."""
+    d = bench._args([])
+    r = bench.oras_traffic_ratio(d.parts)
+    assert r is not None and 1.0 <= r < 1.2
+    assert bench.oras_traffic_ratio("16x16x7" if d.parts != "16x16x7" else "22x22x10") is None
+    assert d.plain_factor == "fp64" and d.z_storage == "bf16" and d.inner_tol == 1e-2
