@@ -162,17 +162,20 @@ def _stats(v):
 
 
 def run(scale: str = "reduced", seed: int = 3, plain: bool | None = None, snr_db: float = 40.0, tears: int = 1,
-        alphas=(), verbose=False, reciprocal: bool = True, target_J: float | None = None):
+        alphas=(), verbose=False, reciprocal: bool = True, target_J: float | None = None, pinv=None):
     """Train the network once, then invert `tears` held-out tears from the healthy start and from
     the network's start (mixed solver; the plain FP64 inversion too on the first tear when
     `plain`).  Per tear: the target is the reference inversion's J after max_it (plain FP64 on the
     first tear when run, else the mixed inversion from the healthy start), and each variant's
     time to reach it.  `alphas`: Tikhonov sweep of the mixed inversion on the first tear.
+    `pinv`: box partition of the inverse mesh, replacing the scale's.
     `reciprocal`: on the first tear, also the mixed inversions whose adjoint fields come from the
     forward fields by reciprocity (mw_set_adjoint_mode) instead of adjoint solves.
     `target_J`: the first tear's target when the plain FP64 inversion is not run here (its J
     after max_it from an earlier run with the same seeds: the inputs are deterministic)."""
-    cfg = SCALES[scale]
+    cfg = dict(SCALES[scale])
+    if pinv is not None:
+        cfg["pinv"] = tuple(int(v) for v in pinv)
     out = {"scale": scale, "config": {k: v for k, v in cfg.items()}}
     f_nn = len(cfg["freqs"]) // 2                       # network sees the middle frequency
     t0 = time.time()
@@ -317,10 +320,13 @@ if __name__ == "__main__":
     ap.add_argument("--plain", action="store_true")
     ap.add_argument("--tears", type=int, default=1)
     ap.add_argument("--alphas", default="", help="comma-separated Tikhonov weights for the sweep")
+    ap.add_argument("--pinv", default=None, help="box partition of the inverse mesh, e.g. 12x12x5")
     ap.add_argument("--target", type=float, default=None,
                     help="first tear's target J (the plain FP64 inversion's, from an earlier run)")
     a = ap.parse_args()
     plain = False if a.no_plain else (True if a.plain else None)
     alphas = [float(x) for x in a.alphas.split(",") if x]
-    print(json.dumps(run(a.scale, a.seed, plain=plain, tears=a.tears, alphas=alphas, verbose=True, target_J=a.target)),
+    pinv = tuple(int(v) for v in a.pinv.split("x")) if a.pinv else None
+    print(json.dumps(run(a.scale, a.seed, plain=plain, tears=a.tears, alphas=alphas, verbose=True, target_J=a.target,
+                         pinv=pinv)),
           flush=True)
