@@ -177,6 +177,12 @@ __global__ void __launch_bounds__(kDotThreads) cgs_dots_kernel(const T* __restri
 // kernel records an error code, skips the remaining waits and copies (still executing the
 // same named barriers), drains its outstanding copies and returns.
 constexpr int kBdConsumers = 256;
+// A consumer warp releases a ring stage once all its lanes are done with it: one arrival per
+// warp on the stage's empty barrier (which expects kBdConsumers / 32) instead of one per thread.
+__device__ __forceinline__ void release_stage(uint64_t* bar) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+}
 constexpr int kBdThreads = kBdConsumers + 32;
 constexpr int kBdStages = 4;      // default ring depth; 2..kBdMaxStages accepted (same result)
 constexpr int kBdMaxStages = 6;
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
   if (tid == 0) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kBdConsumers);
+      mbar_init(&empty[i], kBdConsumers / 32);   // one arrival per consumer warp
     }
     *abort_flag = 0;
     mbar_init_fence();
@@ -315,7 +321,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
           wr[k] = T{0, 0};
           if (act && row < rows) wr[k] = f < ncop ? sm[f] : gl[f];
         }
-        mbar_arrive(&empty[st]);
+        release_stage(&empty[st]);
         advance();
       }
       // partials of up to kBdGroup consecutive vectors, then one barrier and their reductions
@@ -339,7 +345,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
               pi = fma(-v.y, wr[k].x, pi);
             }
           }
-          mbar_arrive(&empty[st]);
+          release_stage(&empty[st]);
           advance();
           rb[u * kBdConsumers + ct] = T{pr, pi};
         }
@@ -487,7 +493,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
   if (tid == 0) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kBdConsumers);
+      mbar_init(&empty[i], kBdConsumers / 32);   // one arrival per consumer warp
     }
     *abort_flag = 0;
     mbar_init_fence();
@@ -580,7 +586,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
         acc[k] = T{0, 0};
         if (act && row < rows) acc[k] = f < ncop ? sm[f] : gl[f];
       }
-      mbar_arrive(&empty[st]);
+      release_stage(&empty[st]);
       advance();
     }
     for (int i = 0; i < nvec; ++i) {
@@ -600,7 +606,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
           acc[k].y = fma(-hh.y, v.x, acc[k].y);
         }
       }
-      mbar_arrive(&empty[st]);
+      release_stage(&empty[st]);
       advance();
     }
     if (act && !*abort_flag) {
@@ -936,7 +942,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
   if (tid == 0) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kBdConsumers);
+      mbar_init(&empty[i], kBdConsumers / 32);   // one arrival per consumer warp
     }
     *abort_flag = 0;
     int km = 0;
@@ -1032,7 +1038,7 @@ __global__ void __launch_bounds__(kBdThreads, 2)
           }
         }
       }
-      mbar_arrive(&empty[st]);
+      release_stage(&empty[st]);
       if (++st == NS) {
         st = 0;
         ph ^= 1u;
