@@ -65,7 +65,7 @@ def _args(argv=None):
     ap.add_argument("--graphs", action="store_true", help="replay restart cycles from captured CUDA graphs")
     ap.add_argument("--cpu-sample-subdomains", type=int, default=24)
     ap.add_argument("--cpu-cores", type=int, default=0, help="host processes of the oracle baseline (0 = all cores)")
-    ap.add_argument("--no-legs", action="store_true", help="skip the config-3, training and time-to-misfit legs")
+    ap.add_argument("--no-legs", action="store_true", help="skip the three-frequency, sparse, training and time-to-misfit legs")
     ap.add_argument("--replicas", action="store_true",
                     help="N > 1: independent evaluations per rank instead of the column split of one evaluation")
     ap.add_argument("--inversion-leg", default="bench", choices=["none", "tiny", "bench", "test", "reduced"],
@@ -525,7 +525,7 @@ def nn_leg(local, stream, alu, hbm, n_in=8192, batch=64, samples=1024):
             "train_s": secs, "steps": samples // batch, "classes": rate_classes(prof, hbm, alu)}
 
 
-def config3_leg(a, local, stream, alu, hbm, src, steps=3, warmup=2):
+def shoulder55_3f_leg(a, local, stream, alu, hbm, src, steps=3, warmup=2):
     """The mixed-precision batched forward/adjoint configuration: 55x55x24 shoulder (525,329
     edges), 64 transmitters x 3 frequencies (0.8 / 1.0 / 1.2 GHz) as one block per frequency,
     BF16 tensor-core ORAS, GMRES-IR to 1e-8."""
@@ -548,7 +548,7 @@ def config3_leg(a, local, stream, alu, hbm, src, steps=3, warmup=2):
             "clocks": clocks, "setup_s": L["setup"], "J_last": J}
 
 
-def config2_sparse_leg(a, local, stream, alu, hbm, src, steps=3, warmup=3):
+def sparse16_leg(a, local, stream, alu, hbm, src, steps=3, warmup=3):
     """The shoulder-scale configuration with its specified decomposition: 80x80x34 (1,558,914
     edges), 32 dipoles, 16 subdomains of about 132k unknowns with 2 overlap layers, sparse
     multifrontal subdomain solves with their sweeps on the tensor cores, GMRES-IR to 1e-8.  Inner
@@ -777,8 +777,8 @@ def run_mine(a):
     # ---- extra legs (rank 0 only, each on its own context) -----------------------------------
     legs = {}
     if rank == 0 and world == 1 and not a.no_legs and ports is None and a.cells == "80x80x34" and a.prec == "bf16":
-        for name, fn in (("config3", lambda: config3_leg(a, local, stream, alu, hbm, src)),
-                         ("config2_sparse", lambda: config2_sparse_leg(a, local, stream, alu, hbm, src)),
+        for name, fn in (("shoulder55_64tx_3f", lambda: shoulder55_3f_leg(a, local, stream, alu, hbm, src)),
+                         ("shoulder80_sparse16", lambda: sparse16_leg(a, local, stream, alu, hbm, src)),
                          ("nn_training", lambda: nn_leg(local, stream, alu, hbm))):
             try:
                 legs[name] = fn()

@@ -360,7 +360,7 @@ mw_status mw_invert(mw_ctx* ctx, const mw_inv_opts* opts, const mw_solve_opts* s
                     const double* S_obs, const double* S_empty, double* eps_inout,
                     mw_inv_history* hist);
 
-/* ---- learned initialiser (BASELINE config 5; the paper has no learned part) ----------- */
+/* ---- learned initialiser (the paper has no learned part) -------------------------------- */
 /* Network: x [n_in] -> relu(W1 x + b1) -> relu(W2 . + b2) (1024 wide) -> reshape 16x4x4x4 ->
  * convT(16->16) -> relu -> convT(16->8) -> relu -> convT(8->2) -> [2][32][32][32] (Re, Im of
  * Delta eps on a grid); convT = 3D transposed convolution, kernel 4, stride 2, padding 1.

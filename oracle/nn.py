@@ -1,5 +1,5 @@
-"""FP64 forward and backward of the learned initialiser network (BASELINE config 5; the paper
-has no learned part).
+"""FP64 forward and backward of the learned initialiser network (the paper has no
+learned part).
 
 Network: x [n_in] (normalised Delta S, real parts then imaginary parts)
   h1 = relu(W1 x + b1)            W1 [1024][n_in]

@@ -187,60 +187,58 @@ __global__ void mf_pull_kernel(const int64_t* __restrict__ out, const int64_t* _
   }
 }
 
-// The same pull with 4 consecutive complex columns per thread (R a multiple of 4) and two rows
-// per thread, rows i and i + n2 (n2 = ceil(n / 2)): 32-byte loads and stores, and the two rows'
-// index chains run side by side.  Each row's sums are the same, in the same order.
+// The same pull with 4 consecutive complex columns per thread (R a multiple of 4) and NR rows
+// per thread, rows i, i + nq, i + 2 nq, ... (nq = ceil(n / NR)): 32-byte loads and stores, and
+// the rows' index chains run side by side.  Each row's sums are the same, in the same order.
+template <int NR>
 __global__ void mf_pull4_kernel(const int64_t* __restrict__ out, const int64_t* __restrict__ ptr,
                                 const int64_t* __restrict__ src, int64_t n, const float2* __restrict__ in, int R,
                                 float2* __restrict__ arena) {
   const int tpr = R / 4;
-  const int64_t n2 = (n + 1) / 2;
+  const int64_t nq = (n + NR - 1) / NR;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n2 * tpr) return;
-  const int64_t i = t / tpr;
-  const int c = (int)(t - i * tpr) * 4;
-  const int64_t i2 = i + n2;
-  const bool two = i2 < n;
-  float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, a2 = a, b2 = a;   // columns c, c+1 | c+2, c+3
-  int64_t q = ptr[i];
-  const int64_t qe = ptr[i + 1];
-  int64_t q2 = two ? ptr[i2] : 0;
-  const int64_t qe2 = two ? ptr[i2 + 1] : 0;
-  while (q < qe || q2 < qe2) {
-    if (q < qe) {
-      const int64_t g = src[q++];
-      const float4* v = reinterpret_cast<const float4*>(g >= 0 ? arena + g * R + c : in + (-g - 1) * R + c);
-      const float4 v0 = v[0], v1 = v[1];
-      a.x += v0.x;
-      a.y += v0.y;
-      a.z += v0.z;
-      a.w += v0.w;
-      b.x += v1.x;
-      b.y += v1.y;
-      b.z += v1.z;
-      b.w += v1.w;
-    }
-    if (q2 < qe2) {
-      const int64_t g = src[q2++];
-      const float4* v = reinterpret_cast<const float4*>(g >= 0 ? arena + g * R + c : in + (-g - 1) * R + c);
-      const float4 v0 = v[0], v1 = v[1];
-      a2.x += v0.x;
-      a2.y += v0.y;
-      a2.z += v0.z;
-      a2.w += v0.w;
-      b2.x += v1.x;
-      b2.y += v1.y;
-      b2.z += v1.z;
-      b2.w += v1.w;
+  if (t >= nq * tpr) return;
+  const int64_t i0 = t / tpr;
+  const int c = (int)(t - i0 * tpr) * 4;
+  float4 a[NR], b[NR];   // columns c, c+1 | c+2, c+3 of each row
+  int64_t q[NR], qe[NR];
+  bool more = false;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int64_t i = i0 + r * nq;
+    a[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    b[r] = a[r];
+    q[r] = i < n ? ptr[i] : 0;
+    qe[r] = i < n ? ptr[i + 1] : 0;
+    more |= q[r] < qe[r];
+  }
+  while (more) {
+    more = false;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (q[r] < qe[r]) {
+        const int64_t g = src[q[r]++];
+        const float4* v = reinterpret_cast<const float4*>(g >= 0 ? arena + g * R + c : in + (-g - 1) * R + c);
+        const float4 v0 = v[0], v1 = v[1];
+        a[r].x += v0.x;
+        a[r].y += v0.y;
+        a[r].z += v0.z;
+        a[r].w += v0.w;
+        b[r].x += v1.x;
+        b[r].y += v1.y;
+        b[r].z += v1.z;
+        b[r].w += v1.w;
+      }
+      more |= q[r] < qe[r];
     }
   }
-  float4* o = reinterpret_cast<float4*>(arena + out[i] * R + c);
-  o[0] = a;
-  o[1] = b;
-  if (two) {
-    float4* o2 = reinterpret_cast<float4*>(arena + out[i2] * R + c);
-    o2[0] = a2;
-    o2[1] = b2;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int64_t i = i0 + r * nq;
+    if (i >= n) continue;
+    float4* o = reinterpret_cast<float4*>(arena + out[i] * R + c);
+    o[0] = a[r];
+    o[1] = b[r];
   }
 }
 
@@ -484,10 +482,11 @@ void mf_pull(const int64_t* out, const int64_t* ptr, const int64_t* src, int64_t
   if (n <= 0) return;
   note_launch(1);
   if (R % 4 == 0 && R <= 128 && (((uintptr_t)in | (uintptr_t)arena) & 15) == 0) {
-    // 4 complex columns and two rows per thread: a warp takes 64 / (R / 4) rows with
-    // independent load chains
-    const int64_t thr = (n + 1) / 2 * (R / 4);
-    mf_pull4_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(out, ptr, src, n, in, R, arena);
+    // 4 complex columns and kPullRows rows per thread: a warp takes 32 kPullRows / (R / 4) rows
+    // with independent load chains
+    constexpr int kPullRows = 2;   // measured on the 16-subdomain shoulder: faster than 4 rows
+    const int64_t thr = (n + kPullRows - 1) / kPullRows * (R / 4);
+    mf_pull4_kernel<kPullRows><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(out, ptr, src, n, in, R, arena);
     return;
   }
   const int64_t thr = n * R;

@@ -1,4 +1,4 @@
-// Learned initialiser (BASELINE config 5; no counterpart in the paper): forward and backward
+// Learned initialiser (no counterpart in the paper): forward and backward
 // kernels of  x -> relu(W1 x + b1) -> relu(W2 . + b2) -> reshape 16x4^3 -> convT(16->16) -> relu
 // -> convT(16->8) -> relu -> convT(8->2) -> 32^3 x 2,  convT = 3D transposed convolution with
 // kernel 4, stride 2, padding 1:  out[co][o] = b[co] + sum_ci sum_k in[ci][i] w[ci][co][k],

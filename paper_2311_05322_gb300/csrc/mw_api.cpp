@@ -3428,7 +3428,7 @@ mw_status mw_apply_preconditioner_noalloc(mw_ctx* c, int32_t f, const void* r, v
 
 
 // =======================================================================================
-// Learned initialiser (BASELINE config 5): MLP + transposed-convolution decoder
+// Learned initialiser (no counterpart in the paper): MLP + transposed-convolution decoder
 // =======================================================================================
 static constexpr int kHid = 1024, kG = 32, kOut = 2 * kG * kG * kG;
 

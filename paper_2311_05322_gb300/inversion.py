@@ -1,4 +1,4 @@
-"""Inversion time-to-misfit and the learned initialiser (Sec. IV-D; BASELINE configs 4 and 5).
+"""Inversion time-to-misfit and the learned initialiser (Sec. IV-D).
 
 Differential reading of the inversion: the healthy anatomy is known (a prior scan), the data are
 the S-parameters of the injured shoulder computed on a finer "data" mesh with complex Gaussian

@@ -1,4 +1,4 @@
-"""What the trained network gains over the inversion without it (BASELINE config 5).
+"""What the trained network gains over the inversion without it.
 
 Seeded and deterministic (every kernel reduces in a fixed order): forward solves on the data
 mesh generate noisy injured-minus-healthy S differences and tear targets, the network trains on
