@@ -180,14 +180,16 @@ __global__ void __launch_bounds__(256) convT_fwd_kernel(const float* __restrict_
 }
 
 // convT backward-data: dx[b][ci][i] = sum_co sum_k w[ci][co][k] dy[b][co][2i - 1 + k]; one thread
-// per input position (b, i), all Ci channels at once, weights in shared memory.  Per output the
-// sum runs over co, then kz, ky, kx ascending.
-template <int CI>
+// per input position (b, i) and group of CIG channels (the group is blockIdx.y, so layers with
+// few positions still fill the GPU), the group's weights in shared memory.  Per output the sum
+// runs over co, then kz, ky, kx ascending.
+template <int CIG>
 __global__ void __launch_bounds__(256) convT_bwd_data_kernel(const float* __restrict__ dy,
                                                              const float* __restrict__ w, float* __restrict__ dx,
-                                                             int B, int Co, int D) {
-  extern __shared__ float sw[];                     // [CI][Co][64]
-  for (int q = threadIdx.x; q < CI * Co * 64; q += blockDim.x) sw[q] = w[q];
+                                                             int B, int Co, int D, int Ci) {
+  extern __shared__ float sw[];                     // [CIG][Co][64] of channels ci0 ..
+  const int ci0 = blockIdx.y * CIG;
+  for (int q = threadIdx.x; q < CIG * Co * 64; q += blockDim.x) sw[q] = w[(size_t)ci0 * Co * 64 + q];
   __syncthreads();
   const int Do = 2 * D;
   const int64_t V = (int64_t)D * D * D;
@@ -196,9 +198,9 @@ __global__ void __launch_bounds__(256) convT_bwd_data_kernel(const float* __rest
     const int64_t i = t % V;
     const int bb = (int)(t / V);
     const int ix = (int)(i % D), iy = (int)((i / D) % D), iz = (int)(i / ((int64_t)D * D));
-    float s[CI];
+    float s[CIG];
 #pragma unroll
-    for (int ci = 0; ci < CI; ++ci) s[ci] = 0.f;
+    for (int ci = 0; ci < CIG; ++ci) s[ci] = 0.f;
     for (int co = 0; co < Co; ++co) {
       const float* yc = dy + ((int64_t)bb * Co + co) * Do * Do * Do;
       for (int kz = 0; kz < 4; ++kz) {
@@ -213,68 +215,62 @@ __global__ void __launch_bounds__(256) convT_bwd_data_kernel(const float* __rest
             const float yv = yc[(oz * Do + oy) * Do + ox];
             const int kk = (kz * 4 + ky) * 4 + kx;
 #pragma unroll
-            for (int ci = 0; ci < CI; ++ci) s[ci] = fmaf(yv, sw[(ci * Co + co) * 64 + kk], s[ci]);
+            for (int ci = 0; ci < CIG; ++ci) s[ci] = fmaf(yv, sw[(ci * Co + co) * 64 + kk], s[ci]);
           }
         }
       }
     }
 #pragma unroll
-    for (int ci = 0; ci < CI; ++ci) dx[((int64_t)bb * CI + ci) * V + i] = s[ci];
+    for (int ci = 0; ci < CIG; ++ci) dx[((int64_t)bb * Ci + ci0 + ci) * V + i] = s[ci];
   }
 }
 
 // convT backward-weights, dW[ci][co][k] = sum_b sum_i x[b][ci][i] dy[b][co][2i - 1 + k], in two
-// fixed-order passes.  Pass 1: block (ci, co, chunk) walks its chunk of the B D^3 input positions;
-// thread t takes positions t, t + 256, ... and keeps the 64 tap sums in registers; the block
-// then sums the 256 threads' values tap by tap (thread order, 32 taps at a time through shared
-// memory) into part[chunk][ci][co][k].
+// fixed-order passes.  Pass 1: block (ci, co, kz, chunk) walks its chunk of the B D^3 input
+// positions for the 16 taps of one kz plane; thread t takes positions t, t + 256, ... and keeps
+// the 16 tap sums in registers; the block then sums the 256 threads' values tap by tap (thread
+// order, through shared memory) into part[chunk][ci][co][k].
 // Pass 2 sums the chunks in order.
 constexpr int kBwdWThreads = 256;
 __global__ void __launch_bounds__(kBwdWThreads) convT_bwd_w_kernel(const float* __restrict__ x,
                                                                    const float* __restrict__ dy,
                                                                    float* __restrict__ part, int B, int Ci, int Co,
                                                                    int D, int64_t chunk) {
-  __shared__ float red[kBwdWThreads][33];
-  const int ci = blockIdx.x / Co, co = blockIdx.x % Co;
+  __shared__ float red[kBwdWThreads][17];
+  const int pair = blockIdx.x >> 2, kz = blockIdx.x & 3;
+  const int ci = pair / Co, co = pair % Co;
   const int Do = 2 * D;
   const int64_t V = (int64_t)D * D * D, total = (int64_t)B * V;
   const int64_t p0 = (int64_t)blockIdx.y * chunk, p1 = min(total, p0 + chunk);
-  float acc[64];
+  float acc[16];
 #pragma unroll
-  for (int k = 0; k < 64; ++k) acc[k] = 0.f;
+  for (int k = 0; k < 16; ++k) acc[k] = 0.f;
   for (int64_t t = p0 + threadIdx.x; t < p1; t += kBwdWThreads) {
     const int64_t i = t % V;
     const int bb = (int)(t / V);
     const int ix = (int)(i % D), iy = (int)((i / D) % D), iz = (int)(i / ((int64_t)D * D));
+    const int oz = 2 * iz - 1 + kz;
+    if (oz < 0 || oz >= Do) continue;
     const float xv = x[((int64_t)bb * Ci + ci) * V + i];
-    const float* yc = dy + ((int64_t)bb * Co + co) * Do * Do * Do;
+    const float* yc = dy + ((int64_t)bb * Co + co) * Do * Do * Do + (int64_t)oz * Do * Do;
 #pragma unroll
-    for (int kz = 0; kz < 4; ++kz) {
-      const int oz = 2 * iz - 1 + kz;
+    for (int ky = 0; ky < 4; ++ky) {
+      const int oy = 2 * iy - 1 + ky;
 #pragma unroll
-      for (int ky = 0; ky < 4; ++ky) {
-        const int oy = 2 * iy - 1 + ky;
-#pragma unroll
-        for (int kx = 0; kx < 4; ++kx) {
-          const int ox = 2 * ix - 1 + kx;
-          if (oz >= 0 && oz < Do && oy >= 0 && oy < Do && ox >= 0 && ox < Do)
-            acc[(kz * 4 + ky) * 4 + kx] = fmaf(xv, yc[((int64_t)oz * Do + oy) * Do + ox], acc[(kz * 4 + ky) * 4 + kx]);
-        }
+      for (int kx = 0; kx < 4; ++kx) {
+        const int ox = 2 * ix - 1 + kx;
+        if (oy >= 0 && oy < Do && ox >= 0 && ox < Do)
+          acc[ky * 4 + kx] = fmaf(xv, yc[(int64_t)oy * Do + ox], acc[ky * 4 + kx]);
       }
     }
   }
-  // two halves of 32 taps through shared memory
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-#pragma unroll
-    for (int k = 0; k < 32; ++k) red[threadIdx.x][k] = acc[32 * h + k];
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      float s = 0.f;
-      for (int q = 0; q < kBwdWThreads; ++q) s += red[q][threadIdx.x];
-      part[(((int64_t)blockIdx.y * Ci + ci) * Co + co) * 64 + 32 * h + threadIdx.x] = s;
-    }
-    __syncthreads();
+  for (int k = 0; k < 16; ++k) red[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    float sum = 0.f;
+    for (int q = 0; q < kBwdWThreads; ++q) sum += red[q][threadIdx.x];
+    part[(((int64_t)blockIdx.y * Ci + ci) * Co + co) * 64 + kz * 16 + threadIdx.x] = sum;
   }
 }
 
@@ -479,8 +475,9 @@ static void allow_conv_smem() {
   cudaFuncSetAttribute(convT_fwd_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(convT_fwd_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(convT_fwd_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(convT_bwd_data_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(convT_bwd_data_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(convT_bwd_data_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(convT_bwd_data_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   done = true;
 }
 
@@ -507,12 +504,18 @@ void nn_convT_bwd(const float* x, const float* w, const float* dy, float* dx, fl
   allow_conv_smem();
   note_launch(dx ? 5 : 4);
   if (dx) {
+    // channel groups so that every layer launches about two waves of blocks
     const int64_t n = (int64_t)B * D * D * D;
-    const size_t sm = sizeof(float) * Ci * Co * 64;
-    if (Ci == 8)
-      convT_bwd_data_kernel<8><<<gsb(n), 256, sm, s>>>(dy, w, dx, B, Co, D);
+    const int nb = gsb(n);
+    const int cig = nb * (Ci / 8) >= 2 * 152 ? 8 : (nb * (Ci / 4) >= 2 * 152 ? 4 : 1);
+    const dim3 grid((unsigned)nb, (unsigned)(Ci / cig));
+    const size_t sm = sizeof(float) * cig * Co * 64;
+    if (cig == 8)
+      convT_bwd_data_kernel<8><<<grid, 256, sm, s>>>(dy, w, dx, B, Co, D, Ci);
+    else if (cig == 4)
+      convT_bwd_data_kernel<4><<<grid, 256, sm, s>>>(dy, w, dx, B, Co, D, Ci);
     else
-      convT_bwd_data_kernel<16><<<gsb(n), 256, sm, s>>>(dy, w, dx, B, Co, D);
+      convT_bwd_data_kernel<1><<<grid, 256, sm, s>>>(dy, w, dx, B, Co, D, Ci);
   }
   {
     // enough (ci, co, chunk) blocks for every SM twice, chunks of whole thread rounds, at most
@@ -522,7 +525,7 @@ void nn_convT_bwd(const float* x, const float* w, const float* dy, float* dx, fl
     int64_t chunk = (total + nchunk - 1) / nchunk;
     chunk = (chunk + kBwdWThreads - 1) / kBwdWThreads * kBwdWThreads;
     nchunk = (int)((total + chunk - 1) / chunk);
-    convT_bwd_w_kernel<<<dim3(Ci * Co, nchunk), kBwdWThreads, 0, s>>>(x, dy, wpart, B, Ci, Co, D, chunk);
+    convT_bwd_w_kernel<<<dim3(Ci * Co * 4, nchunk), kBwdWThreads, 0, s>>>(x, dy, wpart, B, Ci, Co, D, chunk);
     const int64_t n = (int64_t)Ci * Co * 64;
     convT_bwd_w_final_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(wpart, nchunk, n, dw);
   }
