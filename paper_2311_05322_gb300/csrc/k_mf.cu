@@ -130,42 +130,6 @@ __global__ void mf_extract_kernel(const int32_t* __restrict__ nodes, const int64
   }
 }
 
-// rhs rows of node nodes[blockIdx.y]: r(pivot) for the real pivots, zero elsewhere, plus the
-// children's w rows that map into the front (children in order).
-__global__ void mf_rhs_kernel(const int32_t* __restrict__ nodes, const int64_t* __restrict__ f,
-                              const int32_t* __restrict__ preal, const int64_t* __restrict__ piv_ptr,
-                              const int32_t* __restrict__ piv_glob, const int64_t* __restrict__ child_ptr,
-                              const int32_t* __restrict__ child, const int64_t* __restrict__ inv_off,
-                              const int32_t* __restrict__ inv, const int64_t* __restrict__ rhs_row,
-                              const int64_t* __restrict__ w_row, const float2* __restrict__ in, int R,
-                              float2* __restrict__ arena) {
-  const int32_t k = nodes[blockIdx.y];
-  const int64_t fk = f[k];
-  const int64_t c0 = child_ptr[k], c1 = child_ptr[k + 1];
-  const int col = threadIdx.x % 32;
-  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; r < fk;
-       r += (int64_t)gridDim.x * (blockDim.x / 32)) {
-    for (int cc = col; cc < R; cc += 32) {
-      float sx = 0.f, sy = 0.f;
-      if (r < preal[k]) {
-        const float2 v = in[(int64_t)piv_glob[piv_ptr[k] + r] * R + cc];
-        sx = v.x;
-        sy = v.y;
-      }
-      for (int64_t q = c0; q < c1; ++q) {
-        const int32_t ch = child[q];
-        const int32_t a = inv[inv_off[ch] + r];
-        if (a >= 0) {
-          const float2 v = arena[(w_row[ch] + a) * R + cc];
-          sx += v.x;
-          sy += v.y;
-        }
-      }
-      arena[(rhs_row[k] + r) * R + cc] = make_float2(sx, sy);
-    }
-  }
-}
-
 // Front right-hand sides as a pull: arena row out[i] = sum over src[ptr[i] .. ptr[i+1]) of the
 // arena row src (>= 0) or input row -(src + 1), in list order (input first, then the children
 // in child order, as the multifrontal forward sweep assembles them).  One thread per (row,
@@ -440,17 +404,6 @@ void mf_extract(const int32_t* nodes, int n_nodes, int64_t max_entries, const in
   note_launch(1);
   dim3 g(grid_for(max_entries, 256, 1024), n_nodes);
   mf_extract_kernel<<<g, 256, 0, s>>>(nodes, f, p, ws_off, fac_off, ws, fac);
-}
-
-void mf_rhs(const int32_t* nodes, int n_nodes, int64_t fmax, const int64_t* f, const int32_t* preal,
-            const int64_t* piv_ptr, const int32_t* piv_glob, const int64_t* child_ptr, const int32_t* child,
-            const int64_t* inv_off, const int32_t* inv, const int64_t* rhs_row, const int64_t* w_row,
-            const float2* in, int R, float2* arena, cudaStream_t s) {
-  if (n_nodes <= 0) return;
-  note_launch(1);
-  dim3 g(grid_for(fmax, 8, 512), n_nodes);
-  mf_rhs_kernel<<<g, 256, 0, s>>>(nodes, f, preal, piv_ptr, piv_glob, child_ptr, child, inv_off, inv, rhs_row, w_row,
-                                  in, R, arena);
 }
 
 void mf_gemm(const MfTask* tasks, const MfTile* tiles, int n_tiles, const MfSplit* splits, int n_splits,

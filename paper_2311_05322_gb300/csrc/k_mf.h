@@ -47,11 +47,6 @@ void mf_extend_add(const int32_t* nodes, int n_nodes, int64_t fmax, const int64_
 // Copies TL | TR and BL of the factored fronts into the factor store (max_entries = largest p f + u p).
 void mf_extract(const int32_t* nodes, int n_nodes, int64_t max_entries, const int64_t* f, const int32_t* p,
                 const int64_t* ws_off, const int64_t* fac_off, const float2* ws, float2* fac, cudaStream_t s);
-// Forward right-hand sides of nodes[0 .. n_nodes): arena rows rhs_row[k] .. + f[k].
-void mf_rhs(const int32_t* nodes, int n_nodes, int64_t fmax, const int64_t* f, const int32_t* preal,
-            const int64_t* piv_ptr, const int32_t* piv_glob, const int64_t* child_ptr, const int32_t* child,
-            const int64_t* inv_off, const int32_t* inv, const int64_t* rhs_row, const int64_t* w_row,
-            const float2* in, int R, float2* arena, cudaStream_t s);
 // Front right-hand sides of one forward height as pull lists: arena row out[i] = sum of its
 // listed arena rows (src >= 0) and input rows (-(src + 1)), for i < n (ptr relative to src).
 void mf_pull(const int64_t* out, const int64_t* ptr, const int64_t* src, int64_t n, const float2* in, int R,
