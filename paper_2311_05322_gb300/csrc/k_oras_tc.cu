@@ -730,7 +730,6 @@ int tc_stages(int N) {
 
 size_t tc_smem_bytes(int N, int stages) { return (size_t)stages * (2 * kATileBytes + N * 128) + 1024; }
 
-int tc_default_stages(int R) { return tc_stages(2 * rpad(R)); }
 
 int tc_max_stages(int R) {
   // the kernel holds 8 stage barriers; 1 KB of the 227 KB is left for its static shared memory

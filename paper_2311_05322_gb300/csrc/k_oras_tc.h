@@ -58,11 +58,9 @@ void tc_pack_stacked(const TcPlan& p, const MfTask* tasks, const int32_t* first,
 void oras_apply_tc(const TcPlan& p, const OrasTopo& tp, const void* W, const float2* r, float2* z, int R,
                    void* scratch, cudaStream_t s, int stages = 0, const double* in_scale = nullptr,
                    const int32_t* c0_glob = nullptr, bool z_bf16 = false, bool persistent = false);
-// Pipeline depths the MMA kernel accepts for R columns: [tc_min_stages, tc_max_stages(R)]; the
-// default depth for R columns.
+// Pipeline depths the MMA kernel accepts for R columns: [tc_min_stages, tc_max_stages(R)].
 constexpr int tc_min_stages = 2;
 int tc_max_stages(int R);
-int tc_default_stages(int R);
 
 // Launches the bounded-wait self-test (see k_oras_tc.cu); *code (device) gets 0 or 5.
 void bounded_wait_probe(long long limit, int32_t* code, cudaStream_t s);

@@ -248,12 +248,6 @@ void givens_step(const double2* h, const double* npart, int nparts, int j, int m
                  int32_t* active_count, cudaStream_t s);
 void scale_cols_f64(double2* v, const double* scale, int64_t E, int R, cudaStream_t s);
 void scale_cols_f32(float2* v, const double* scale, int64_t E, int R, cudaStream_t s);
-// v0 = r / ||r|| per column (with cast); norms from npart.
-void start_cycle_f64(const double2* r, const double* npart, int nparts, int R, const double* bnorm, double tol,
-                     double inner_tol, int fp64_mode, double2* v0, double* rnorm, double2* gvec, double* target,
-                     int32_t* done, int32_t* kcol, int m, cudaStream_t s);
-void start_cycle_f32(const double2* r, const double* rnorm, int64_t E, int R, float2* v0, cudaStream_t s);
-void copy_v0_f64(const double2* r, const double* rnorm, int64_t E, int R, double2* v0, cudaStream_t s);
 void solve_hessenberg(const double2* H, const double2* gvec, const int32_t* kcol, int m, int R, double2* y,
                       cudaStream_t s);
 // x += sum_{l < kcol[c]} y[c][l] Z_l per column; err as for cgs_dots (null: the non-streaming kernel).
